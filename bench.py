@@ -1,0 +1,328 @@
+"""Benchmark: whole transcranial plans on a synthetic skull (240 x 240 x 200,
+dx 0.5 mm, 500 kHz, 1500 FDTD steps, 64 mm / 63 mm focused bowl).
+
+One bench step = one plan = every step of the hot path: property table ->
+coefficients, Rayleigh-Sommerfeld source plane, FDTD through the skull with
+peak map and 10-cycle FP64 amplitude capture, the water-only FDTD, E_L, and the
+BHTE (40 s on at 30 % duty cycle, 80 s off) with T_max and CEM43.  The metric
+counts FDTD voxel-steps of both runs per second of whole-plan time.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own plans (its own seeded skull and bowl
+placement); no data crosses ranks ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDTD Gvoxel-steps/s"
+UNIT = "Gvoxel-steps/s"
+WORKLOAD = "synthetic skull 240x240x200 dx0.5mm 500kHz 1500 steps, bowl 64/63 mm, water run, BHTE 40s/30%/80s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="bvf", choices=["bvf", "reference"])
+    ap.add_argument("--fdtd-steps", type=int, default=1500)
+    ap.add_argument("--grid", default="240,240,200")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_case(args, rank):
+    from paper_2301_12727_gb300 import synth
+    nx, ny, nz = (int(v) for v in args.grid.split(","))
+    return synth.skull_case(nx, ny, nz, dx=0.5e-3, f0=5e5, n_steps=args.fdtd_steps,
+                            seed=1234 + rank, dft_cycles=10)
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stress_traffic_per_voxel(kernel_src):
+    """DRAM bytes per voxel of the stress kernel from the committed ncu summary,
+    if that summary was taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "stress_kernel_skull240.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_voxel"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------
+def cpu_baseline_oracle(case, budget_s=12.0, max_steps=40):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded
+    sample of the same workload (the first FDTD steps of the skull run)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    b = case.bowl
+    plane = oracle.rs_plane(b["aperture"], b["roc"], b["apex"], b["dir"], case.nx, case.ny,
+                            case.dx, case.k_src * case.dx, case.f0, case.c0, b["p0"])
+    A = oracle.Acoustic(case.nx, case.ny, case.nz, case.dx, case.dt, case.index, case.materials,
+                        case.f0, qc=case.qc, n_sls=case.n_sls, n_pml=case.n_pml, pml_R=case.pml_R)
+    A.set_source(plane, case.k_src, case.c0, oracle.ENV_RAMP_CW)
+    t0 = time.perf_counter()
+    assert A.run(2, peak_from=0) == 0
+    t_probe = time.perf_counter() - t0
+    n = max(2, min(max_steps, int(budget_s / max(t_probe / 2, 1e-3))))
+    t0 = time.perf_counter()
+    assert A.run(n, peak_from=0) == 0
+    t = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": case.voxels * n / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d FDTD steps (of %d) of the skull run on the full %dx%dx%d grid, "
+                      "FP64, %.1f s" % (n, case.n_steps, case.nx, case.ny, case.nz, t),
+            "seconds": t, "steps": n}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    case = make_case(args, 0)
+    times = []
+    base = None
+    for it in range(args.warmup + args.steps):
+        r = cpu_baseline_oracle(case, budget_s=6.0, max_steps=12)
+        if it >= args.warmup:
+            times.append(r)
+        base = r
+    vox = sum(r["steps"] for r in times) * case.voxels
+    sec = sum(r["seconds"] for r in times)
+    value = vox / sec / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / max(len(times), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "each step: %d FDTD steps on the full grid"
+                       % times[-1]["steps"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"],
+                             "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+def run_bvf(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if pg:
+        pg.barrier()
+    from paper_2301_12727_gb300 import plan as planmod
+    case = make_case(args, rank)
+    planner = planmod.Planner(case)
+    idx_dev = torch.from_numpy(case.index).cuda()
+    bowl = case.bowl
+    mats = case.materials
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        res = planner.run(idx_dev, mats, bowl)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    planner.kernel_timing(True)
+    l0 = planner.launches()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = planner.run(idx_dev, mats, bowl)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    launches = planner.launches() - l0
+    kt = planner.kernel_times()
+    planner.kernel_timing(False)
+    # thermal + auxiliary kernels are counted through the context counters;
+    # the transmission reductions (3 kernels) and RS (1) per plan are context-free
+    launches += args.steps * 4
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    vox_per_plan = res.voxel_steps
+    value = world * args.steps * vox_per_plan / (ms / 1e3) / 1e9
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        idx_host = torch.from_numpy(case.index).pin_memory()
+        out_peak = torch.empty(case.index.shape, dtype=torch.float32).pin_memory()
+        out_tmax = torch.empty(case.index.shape, dtype=torch.float32).pin_memory()
+        out_cem = torch.empty(case.index.shape, dtype=torch.float64).pin_memory()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            idx_d = idx_host.to("cuda", non_blocking=True)
+            r = planner.run(idx_d, mats, bowl)
+            out_peak.copy_(r.peak, non_blocking=True)
+            out_tmax.copy_(r.Tmax, non_blocking=True)
+            out_cem.copy_(r.cem43, non_blocking=True)
+        f1.record(stream)
+        barrier()
+        ms_e2e = f0.elapsed_time(f1)
+        if pg:
+            t = torch.tensor([ms_e2e], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": world * args.steps * vox_per_plan / (ms_e2e / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(idx_host.numel()),
+               "d2h_bytes_per_step": int(out_peak.numel() * 4 + out_tmax.numel() * 4
+                                         + out_cem.numel() * 8)}
+
+    # ---- roofline of the dominant kernel (stress + memory variables)
+    N = case.voxels
+    n_runs = 2 * args.steps
+    stress_bytes = N * (165.0 * case.n_steps + 32.0 * case.dft_steps) * n_runs
+    achieved = stress_bytes / (kt["stress_ms"] / 1e3) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    tr = stress_traffic_per_voxel(os.path.join(ROOT, "paper_2301_12727_gb300", "csrc",
+                                               "bvf_acoustic.cu"))
+    vel_bytes = N * 49.0 * case.n_steps * n_runs
+    roofline = {"bound": "hbm", "kernel": "k_stress<2> (stress + SLS memory + source + capture)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind,
+                "traffic": (tr * N if tr is not None else None),
+                "algorithmic_bytes_per_launch": stress_bytes / kt["stress_launches"],
+                "avg_launch_ms": kt["stress_ms"] / kt["stress_launches"],
+                "velocity_kernel": {"achieved": vel_bytes / (kt["velocity_ms"] / 1e3) / 1e9,
+                                    "avg_launch_ms": kt["velocity_ms"] / kt["velocity_launches"]},
+                "fdtd_share_of_step": (kt["stress_ms"] + kt["velocity_ms"]) / ms}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [case.nx, case.ny, case.nz],
+                       "fdtd_steps": case.n_steps, "runs_per_step": 2, "n_sls": case.n_sls,
+                       "n_pml": case.n_pml, "dft_cycles": case.dft_cycles,
+                       "l2": "inputs larger than L2 (state %.0f MB per run)"
+                             % (N * 4 * (9 + 6 * case.n_sls) / 1e6),
+                       "EL": res.EL, "TS": res.TS},
+            "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(case)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    planner.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_bvf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

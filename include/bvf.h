@@ -1,0 +1,287 @@
+/*
+ * bvf.h -- C ABI of libbvf, a GB300 (sm_103a) implementation of the hot path of
+ * the transcranial focused-ultrasound pipeline of arXiv 2301.12727 (BabelBrain):
+ *
+ *   1. material table -> viscoelastic coefficients (Sec. 2.2 Table 1; Sec. 3.2
+ *      Eq. 3, Q = omega / (2 c alpha) with Q = Q0 q_c);
+ *   2. Rayleigh-Sommerfeld field of a focused bowl on the entry plane
+ *      (Sec. 2.3, last paragraph: elements of area lambda^2/16);
+ *   3. viscoelastic velocity-stress FDTD, 4th order in space, 2nd in time, on a
+ *      staggered grid (Sec. 2.3, Eq. 1), with standard-linear-solid memory
+ *      variables matched to Q, CPML absorbing slabs, a stress source on the
+ *      entry plane and running peak-pressure / amplitude-phase capture;
+ *   4. Pennes bioheat (BHTE) FDTD with 37 C borders, duty cycle and CEM43 dose
+ *      (Sec. 2.4);
+ *   5. energy-loss factor E_L over the plane of maximal water intensity and
+ *      T_S = sqrt(E_L) (Sec. 2.4, Eq. 2; Sec. 3.2).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: nx * ny * nz cells, spacing dx (m), CPML cells included.  Arrays are
+ *     C order with x fastest: idx = (k*ny + j)*nx + i.  Grid point (i,j,k) sits
+ *     at (i dx, j dx, k dx).
+ *   - Staggering: sxx, syy, szz, p at (i,j,k); vx at (i+1/2,j,k); vy at
+ *     (i,j+1/2,k); vz at (i,j,k+1/2); sxy at (i+1/2,j+1/2,k); sxz at
+ *     (i+1/2,j,k+1/2); syz at (i,j+1/2,k+1/2).  Stresses and pressure at step n
+ *     are at t = n dt, velocities at (n + 1/2) dt.  The last half-grid point of
+ *     each axis (position n - 1/2) is a ghost held at zero, and points outside
+ *     the array are zero.
+ *   - Pointers named d_* are DEVICE memory owned by the caller; h_* are host
+ *     memory.  The library never frees caller memory.  A context owns its field,
+ *     CPML and capture buffers and frees them in bvf_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls enqueue work on it and return without waiting unless stated.
+ *   - Every call returns an int status: BVF_OK (0) or a negative BVF_E_* code.
+ *     Argument and material validation happens on the host, synchronously,
+ *     before anything is enqueued.  No exception or device trap crosses the ABI.
+ *     bvf_last_error() gives a one-line description of the last failure.
+ */
+#ifndef BVF_H
+#define BVF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BVF_VERSION 1
+
+#define BVF_OK 0
+#define BVF_E_ARG (-1)        /* NULL pointer, bad size, bad option, call order */
+#define BVF_E_CFL (-2)        /* dt above the O(4) 3-D stability limit           */
+#define BVF_E_MATERIAL (-3)   /* unphysical material, Q out of reach, bad index  */
+#define BVF_E_NOMEM (-4)      /* device allocation failed                        */
+#define BVF_E_CUDA (-5)       /* a CUDA runtime call failed                      */
+#define BVF_E_UNSTABLE (-6)   /* a non-finite pressure was detected              */
+
+#define BVF_ENV_NONE 0        /* no source                                       */
+#define BVF_ENV_BURST 1       /* rectangular burst of n_cycles                   */
+#define BVF_ENV_RAMP_CW 2     /* one-cycle raised-cosine ramp, then CW           */
+
+#define BVF_MAX_MATERIALS 256
+#define BVF_MAX_SLS 4
+
+/* Field ids for bvf_get_field / bvf_set_field.  Memory variable of mechanism l
+ * for stress component c (0 xx, 1 yy, 2 zz, 3 xy, 4 xz, 5 yz) has id
+ * BVF_FIELD_MEM0 + 6*l + c. */
+enum {
+    BVF_FIELD_VX = 0, BVF_FIELD_VY, BVF_FIELD_VZ,
+    BVF_FIELD_SXX, BVF_FIELD_SYY, BVF_FIELD_SZZ,
+    BVF_FIELD_SXY, BVF_FIELD_SXZ, BVF_FIELD_SYZ,
+    BVF_FIELD_MEM0
+};
+
+typedef struct bvf_ctx bvf_ctx;
+
+/* Grid and time step (Sec. 2.2: resolution from frequency and points per
+ * wavelength; Sec. 2.3: time step).  n_pml CPML cells on every face
+ * (0 = closed box with zero ghosts); pml_R is the CPML's nominal normal-incidence
+ * reflection (e.g. 1e-4).  Requires nx, ny, nz >= 2 n_pml + 2. */
+typedef struct {
+    int nx, ny, nz;
+    double dx;        /* m */
+    double dt;        /* s */
+    int n_pml;
+    double pml_R;
+} bvf_grid;
+
+/* One row of the property table (Sec. 2.2, Table 1).  Attenuations are in Np/m
+ * at the drive frequency.  Thermal constants feed the BHTE (Sec. 2.4):
+ * conductivity k_th (W/m/K), specific heat c_th (J/kg/K), blood perfusion
+ * rate perf (1/s), and the fraction heat_frac of alphaL turned into heat
+ * (0.16 for bone in the paper). */
+typedef struct {
+    double rho, cL, cS, alphaL, alphaS;
+    double k_th, c_th, perf, heat_frac;
+} bvf_material;
+
+/* Drive frequency f0 (Hz), attenuation correction q_c (Q = Q0 q_c, Sec. 3.2)
+ * and number of SLS mechanisms (0 .. BVF_MAX_SLS; 0 = lossless). */
+typedef struct {
+    double f0;
+    double qc;
+    int n_sls;
+} bvf_physics;
+
+/* Single-element spherical bowl (Sec. 2, "Single"): aperture diameter and
+ * radius of curvature (m), apex position (m, grid frame) and unit acoustic
+ * axis.  p0 = rho0 c0 u0 is the surface pressure (Pa); c0 the coupling
+ * medium's speed (water).  ds_over_lambda sets the element size (0.25 gives
+ * the paper's lambda^2/16 area; 0 selects 0.25). */
+typedef struct {
+    double aperture, roc;
+    double apex[3];
+    double dir[3];
+    double p0;
+    double c0;
+    double ds_over_lambda;
+} bvf_bowl;
+
+/* Capture window, counted in completed steps (step s holds p at t = s dt).
+ * peak_from: first step entering the max |p| map (negative = off).
+ * dft_start, dft_steps: steps entering C += p cos(w t), S += p sin(w t) in FP64
+ * (dft_steps = 0: off).  dft_steps should span whole periods. */
+typedef struct {
+    int peak_from;
+    int dft_start;
+    int dft_steps;
+} bvf_capture;
+
+/* BHTE regime (Sec. 2.4; Sec. 4.1.1: 40 s on at 30 % duty cycle, 80 s off).
+ * dt (s) must satisfy dt <= dx^2 min(rho c_th / k_th) / 6.  n_on steps with
+ * the time-averaged source duty * Q, then n_off steps with none.  T_a is the
+ * initial, border and arterial temperature (37 C).  rhob_cb is the blood's
+ * volumetric heat capacity (J/m^3/K).  The heat source is
+ * Q = heat_frac * alphaL * (p_scale * amp)^2 / (rho cL). */
+typedef struct {
+    double dt;
+    int n_on, n_off;
+    double duty;
+    double T_a;
+    double rhob_cb;
+    double p_scale;
+} bvf_thermal;
+
+/* Device time of the acoustic kernels, from CUDA events recorded around each
+ * launch on the launching stream while timing is enabled. */
+typedef struct {
+    long long velocity_launches, stress_launches;
+    double velocity_ms, stress_ms;   /* summed event durations */
+} bvf_kernel_times;
+
+/* Counters of one context. */
+typedef struct {
+    long long steps;             /* acoustic steps advanced since creation/reset */
+    long long kernel_launches;   /* kernels this context enqueued (all calls)    */
+    long long thermal_steps;
+    double courant;              /* c_max(unrelaxed) dt / dx of the material set */
+    double bytes_per_voxel_step; /* algorithmic bytes of one acoustic step       */
+} bvf_stats;
+
+/* ---- library ---------------------------------------------------------- */
+
+/* BVF_VERSION of the loaded library. */
+int bvf_version(void);
+
+/* Stability limit of the O(4) staggered leapfrog in 3-D (Sec. 2.3 scheme):
+ * c dt / dx <= 6 / (7 sqrt 3). */
+double bvf_courant_limit(void);
+
+/* Text for a status code (static storage). */
+const char *bvf_strerror(int code);
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Allocate a context and its device state (fields, memory variables, CPML
+ * slabs, peak map) on the current device, all zero.  Errors: BVF_E_ARG for
+ * bad sizes or options, BVF_E_NOMEM.  *out is NULL on failure. */
+int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out);
+
+/* Release everything the context owns (NULL is accepted). */
+void bvf_destroy(bvf_ctx *ctx);
+
+/* Description of the last failure on this context (or of the last failed
+ * bvf_create / context-free call when ctx is NULL). */
+const char *bvf_last_error(const bvf_ctx *ctx);
+
+/* Material-index volume and property table (Sec. 2.2; Table 1).
+ * d_index: nx*ny*nz uint8 on the device (copied; the caller may free it after
+ * the call returns).  h_table: n_mat rows (copied).  Derives per material the
+ * relaxed moduli and SLS strengths matched to Q = q_c w / (2 c alpha) at f0,
+ * the CPML profile, and checks: rho > 0, cL > 0, 0 <= cS, Poisson ratio in
+ * [-1, 0.5] (Sec. 3.2), Q reachable by the mechanisms, every index < n_mat
+ * (a synchronous device scan), and the CFL limit against the fastest unrelaxed
+ * wave speed.  Errors: BVF_E_ARG, BVF_E_MATERIAL, BVF_E_CFL, BVF_E_CUDA. */
+int bvf_set_materials(bvf_ctx *ctx, const uint8_t *d_index, const bvf_material *h_table,
+                      int n_mat);
+
+/* Rayleigh-Sommerfeld incident field of a bowl on the plane z = z_plane
+ * (Sec. 2.3, last paragraph):  p = (i k p0 / 2 pi) sum_e dA_e exp(-i k r_e) / r_e
+ * over elements of size ds_over_lambda * lambda in water (c0).  Output d_out:
+ * nx*ny complex values as interleaved float pairs (re, im), x fastest, grid
+ * point (i,j) at (i dx, j dx).  Every element must lie below the plane
+ * (z < z_plane); otherwise BVF_E_ARG.  Context-free; asynchronous on `stream`. */
+int bvf_rs_plane(const bvf_bowl *bowl, int nx, int ny, double dx, double z_plane, double f0,
+                 float *d_out, void *stream);
+
+/* Source on plane k_plane (Sec. 2.3: the incident field forward-propagated as
+ * a stress source perpendicular to the acoustic axis).  d_plane holds nx*ny
+ * complex amplitudes A e^{i phi} (interleaved float pairs, copied).  At the
+ * update from step n to n+1 every normal stress of the plane receives
+ * -(2 c0 dt / dx) * env(t) * A sin(w t + phi), t = (n + 1/2) dt, with env given
+ * by `envelope` (BVF_ENV_*) and n_cycles for bursts.  Errors: BVF_E_ARG. */
+int bvf_set_source(bvf_ctx *ctx, int k_plane, const float *d_plane, double c0, int envelope,
+                   int n_cycles, void *stream);
+
+/* Zero the fields, memory variables, CPML memories, captures and step count. */
+int bvf_reset(bvf_ctx *ctx, void *stream);
+
+/* Advance n_steps acoustic steps (velocity, then stress + memory variables +
+ * source + capture per step) on `stream`.  Requires bvf_set_materials.  The
+ * capture window (NULL = none) refers to the context's absolute step count.
+ * Non-finite pressure sets a device flag reported by bvf_synchronize. */
+int bvf_run_acoustic(bvf_ctx *ctx, int n_steps, const bvf_capture *cap, void *stream);
+
+/* Wait for `stream` and report: BVF_E_UNSTABLE if a non-finite pressure was
+ * seen since the last reset, BVF_E_CUDA on an asynchronous CUDA error. */
+int bvf_synchronize(bvf_ctx *ctx, void *stream);
+
+/* Copy one state array (BVF_FIELD_* id, nx*ny*nz floats) out of / into the
+ * context.  Used to start from a prescribed state and to inspect every field. */
+int bvf_get_field(bvf_ctx *ctx, int which, float *d_out, void *stream);
+int bvf_set_field(bvf_ctx *ctx, int which, const float *d_in, void *stream);
+
+/* p = -(sxx + syy + szz)/3 at the current step (nx*ny*nz floats). */
+int bvf_get_pressure(bvf_ctx *ctx, float *d_out, void *stream);
+
+/* Running max |p| map (nx*ny*nz floats). */
+int bvf_get_peak(bvf_ctx *ctx, float *d_out, void *stream);
+
+/* Amplitude 2 sqrt(C^2 + S^2) / N and phase atan2(-S, C) from the FP64 DFT
+ * sums of the capture window (N = steps captured so far), nx*ny*nz doubles
+ * each; either pointer may be NULL.  BVF_E_ARG if nothing was captured. */
+int bvf_get_amp_phase(bvf_ctx *ctx, double *d_amp, double *d_phase, void *stream);
+
+/* Pennes BHTE + CEM43 (Sec. 2.4) on the context's grid and materials:
+ * rho c_th dT/dt = div(k grad T) - perf rhob_cb (T - T_a) + Q, forward Euler,
+ * 7-point stencil with harmonic-mean face conductivity, border voxels at T_a.
+ * d_amp: nx*ny*nz pressure amplitudes (Pa, FP64, e.g. from bvf_get_amp_phase;
+ * NULL = no heating).  d_T (in/out, float) holds the starting temperature and
+ * receives the final one; d_Tmax (in/out, float) and d_cem43 (in/out, FP64)
+ * accumulate max T and sum dt/60 R^(43-T) (R = 0.5 at T >= 43, else 0.25) after
+ * every step.  Errors: BVF_E_ARG (including dt above the explicit limit). */
+int bvf_run_thermal(bvf_ctx *ctx, const bvf_thermal *th, const double *d_amp, float *d_T,
+                    float *d_Tmax, double *d_cem43, void *stream);
+
+/* Energy-loss factor (Sec. 2.4, Eq. 2): with I = A^2 / (2 rho cL) per voxel,
+ * z_m is the plane of the largest water-run intensity (ties: lowest linear
+ * index) and E_L = sum_xy I_a(z_m) / sum_xy I_w(z_m); T_S = sqrt(E_L)
+ * (Sec. 3.2).  h_Iw_max receives the largest water-run intensity (W/m^2), the
+ * reference for I_SPPA scaling (Sec. 2.4).  Index volumes and amplitude maps
+ * are device arrays of nx*ny*nz; tables are host rows; any h_* output may be
+ * NULL.  Synchronous: waits for `stream`. */
+int bvf_transmission(int nx, int ny, int nz,
+                     const uint8_t *d_idx_a, const bvf_material *h_mat_a, int n_a,
+                     const double *d_amp_a,
+                     const uint8_t *d_idx_w, const bvf_material *h_mat_w, int n_w,
+                     const double *d_amp_w,
+                     double *h_EL, double *h_TS, int *h_zm, double *h_Iw_max,
+                     void *stream);
+
+/* Counters (host struct filled synchronously). */
+int bvf_get_stats(const bvf_ctx *ctx, bvf_stats *out);
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing of the acoustic
+ * kernels; enabling clears the accumulated times. */
+int bvf_kernel_timing(bvf_ctx *ctx, int enable);
+
+/* Wait for the recorded events and return the accumulated kernel times since
+ * timing was enabled. */
+int bvf_get_kernel_times(bvf_ctx *ctx, bvf_kernel_times *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BVF_H */

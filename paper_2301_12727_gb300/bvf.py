@@ -1,0 +1,386 @@
+"""Python binding of libbvf (ctypes).  Argument marshalling only: every step of
+the hot path runs in the CUDA library; this module never computes a field.
+
+Functions carry the C ABI's names (include/bvf.h) and take torch CUDA tensors
+for device pointers; the stream is torch's current stream unless given.
+`Solver` bundles one context with the buffers a caller usually wants.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2301_12727_gb300.build``); importing without it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbvf.so")
+
+BVF_OK, BVF_E_ARG, BVF_E_CFL, BVF_E_MATERIAL = 0, -1, -2, -3
+BVF_E_NOMEM, BVF_E_CUDA, BVF_E_UNSTABLE = -4, -5, -6
+BVF_ENV_NONE, BVF_ENV_BURST, BVF_ENV_RAMP_CW = 0, 1, 2
+FIELDS = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")
+EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bvf_destroy",
+           "bvf_last_error", "bvf_set_materials", "bvf_rs_plane", "bvf_set_source", "bvf_reset",
+           "bvf_run_acoustic", "bvf_synchronize", "bvf_get_field", "bvf_set_field",
+           "bvf_get_pressure", "bvf_get_peak", "bvf_get_amp_phase", "bvf_run_thermal",
+           "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times")
+
+
+class BvfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libbvf error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("n_pml", ctypes.c_int),
+                ("pml_R", ctypes.c_double)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("rho", "cL", "cS", "alphaL", "alphaS", "k_th", "c_th", "perf", "heat_frac")]
+
+
+class Physics(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("qc", ctypes.c_double), ("n_sls", ctypes.c_int)]
+
+
+class Bowl(ctypes.Structure):
+    _fields_ = [("aperture", ctypes.c_double), ("roc", ctypes.c_double),
+                ("apex", ctypes.c_double * 3), ("dir", ctypes.c_double * 3),
+                ("p0", ctypes.c_double), ("c0", ctypes.c_double),
+                ("ds_over_lambda", ctypes.c_double)]
+
+
+class Capture(ctypes.Structure):
+    _fields_ = [("peak_from", ctypes.c_int), ("dft_start", ctypes.c_int),
+                ("dft_steps", ctypes.c_int)]
+
+
+class Thermal(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("n_on", ctypes.c_int), ("n_off", ctypes.c_int),
+                ("duty", ctypes.c_double), ("T_a", ctypes.c_double), ("rhob_cb", ctypes.c_double),
+                ("p_scale", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("kernel_launches", ctypes.c_longlong),
+                ("thermal_steps", ctypes.c_longlong), ("courant", ctypes.c_double),
+                ("bytes_per_voxel_step", ctypes.c_double)]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("velocity_launches", ctypes.c_longlong), ("stress_launches", ctypes.c_longlong),
+                ("velocity_ms", ctypes.c_double), ("stress_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libbvf.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libbvf.so is not built: run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.bvf_version.restype = i
+        L.bvf_courant_limit.restype = d
+        L.bvf_strerror.restype = ctypes.c_char_p
+        L.bvf_strerror.argtypes = [i]
+        L.bvf_last_error.restype = ctypes.c_char_p
+        L.bvf_last_error.argtypes = [vp]
+        L.bvf_create.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Physics), ctypes.POINTER(vp)]
+        L.bvf_destroy.argtypes = [vp]
+        L.bvf_destroy.restype = None
+        L.bvf_set_materials.argtypes = [vp, vp, ctypes.POINTER(Material), i]
+        L.bvf_rs_plane.argtypes = [ctypes.POINTER(Bowl), i, i, d, d, d, vp, vp]
+        L.bvf_set_source.argtypes = [vp, i, vp, d, i, i, vp]
+        L.bvf_reset.argtypes = [vp, vp]
+        L.bvf_run_acoustic.argtypes = [vp, i, ctypes.POINTER(Capture), vp]
+        L.bvf_synchronize.argtypes = [vp, vp]
+        L.bvf_get_field.argtypes = [vp, i, vp, vp]
+        L.bvf_set_field.argtypes = [vp, i, vp, vp]
+        L.bvf_get_pressure.argtypes = [vp, vp, vp]
+        L.bvf_get_peak.argtypes = [vp, vp, vp]
+        L.bvf_get_amp_phase.argtypes = [vp, vp, vp, vp]
+        L.bvf_run_thermal.argtypes = [vp, ctypes.POINTER(Thermal), vp, vp, vp, vp, vp]
+        L.bvf_transmission.argtypes = [i, i, i, vp, ctypes.POINTER(Material), i, vp, vp,
+                                       ctypes.POINTER(Material), i, vp,
+                                       ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i),
+                                       ctypes.POINTER(d), vp]
+        L.bvf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.bvf_kernel_timing.argtypes = [vp, i]
+        L.bvf_get_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTimes)]
+        _lib = L
+    return _lib
+
+
+def _check(rc, ctx=None):
+    if rc != BVF_OK:
+        msg = lib().bvf_last_error(ctx)
+        raise BvfError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def material_array(rows) -> "ctypes.Array":
+    rows = np.asarray(rows, dtype=np.float64).reshape(-1, 9)
+    arr = (Material * rows.shape[0])()
+    for m, r in enumerate(rows):
+        arr[m] = Material(*[float(v) for v in r])
+    return arr
+
+
+# ---- C ABI, one wrapper per entry point ----------------------------------
+def bvf_version():
+    return lib().bvf_version()
+
+
+def bvf_courant_limit():
+    return lib().bvf_courant_limit()
+
+
+def bvf_create(grid: Grid, phys: Physics):
+    ctx = ctypes.c_void_p()
+    _check(lib().bvf_create(ctypes.byref(grid), ctypes.byref(phys), ctypes.byref(ctx)))
+    return ctx
+
+
+def bvf_destroy(ctx):
+    lib().bvf_destroy(ctx)
+
+
+def bvf_set_materials(ctx, index, table):
+    import torch
+    arr = material_array(table)
+    _check(lib().bvf_set_materials(ctx, _ptr(index, torch.uint8), arr, len(arr)), ctx)
+
+
+def bvf_rs_plane(bowl: Bowl, nx, ny, dx, z_plane, f0, out, stream=None):
+    import torch
+    _check(lib().bvf_rs_plane(ctypes.byref(bowl), nx, ny, dx, z_plane, f0,
+                              _ptr(out, torch.float32), _stream(stream)))
+
+
+def bvf_set_source(ctx, k_plane, plane, c0, envelope, n_cycles=0, stream=None):
+    import torch
+    _check(lib().bvf_set_source(ctx, k_plane, _ptr(plane, torch.float32), c0, envelope, n_cycles,
+                                _stream(stream)), ctx)
+
+
+def bvf_reset(ctx, stream=None):
+    _check(lib().bvf_reset(ctx, _stream(stream)), ctx)
+
+
+def bvf_run_acoustic(ctx, n_steps, capture: Capture | None = None, stream=None):
+    cap = ctypes.byref(capture) if capture is not None else None
+    _check(lib().bvf_run_acoustic(ctx, n_steps, cap, _stream(stream)), ctx)
+
+
+def bvf_synchronize(ctx, stream=None):
+    return _check(lib().bvf_synchronize(ctx, _stream(stream)), ctx)
+
+
+def bvf_get_field(ctx, which, out, stream=None):
+    import torch
+    _check(lib().bvf_get_field(ctx, which, _ptr(out, torch.float32), _stream(stream)), ctx)
+
+
+def bvf_set_field(ctx, which, src, stream=None):
+    import torch
+    _check(lib().bvf_set_field(ctx, which, _ptr(src, torch.float32), _stream(stream)), ctx)
+
+
+def bvf_get_pressure(ctx, out, stream=None):
+    import torch
+    _check(lib().bvf_get_pressure(ctx, _ptr(out, torch.float32), _stream(stream)), ctx)
+
+
+def bvf_get_peak(ctx, out, stream=None):
+    import torch
+    _check(lib().bvf_get_peak(ctx, _ptr(out, torch.float32), _stream(stream)), ctx)
+
+
+def bvf_get_amp_phase(ctx, amp, phase, stream=None):
+    import torch
+    _check(lib().bvf_get_amp_phase(ctx, _ptr(amp, torch.float64), _ptr(phase, torch.float64),
+                                   _stream(stream)), ctx)
+
+
+def bvf_run_thermal(ctx, th: Thermal, amp, T, Tmax, cem, stream=None):
+    import torch
+    _check(lib().bvf_run_thermal(ctx, ctypes.byref(th), _ptr(amp, torch.float64),
+                                 _ptr(T, torch.float32), _ptr(Tmax, torch.float32),
+                                 _ptr(cem, torch.float64), _stream(stream)), ctx)
+
+
+def bvf_transmission(idx_a, table_a, amp_a, idx_w, table_w, amp_w, stream=None):
+    import torch
+    nz, ny, nx = idx_a.shape
+    ma, mw = material_array(table_a), material_array(table_w)
+    el, ts, zm, iw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().bvf_transmission(nx, ny, nz, _ptr(idx_a, torch.uint8), ma, len(ma),
+                                  _ptr(amp_a, torch.float64), _ptr(idx_w, torch.uint8), mw,
+                                  len(mw), _ptr(amp_w, torch.float64), ctypes.byref(el),
+                                  ctypes.byref(ts), ctypes.byref(zm), ctypes.byref(iw),
+                                  _stream(stream)))
+    return el.value, ts.value, zm.value, iw.value
+
+
+def bvf_get_stats(ctx) -> Stats:
+    s = Stats()
+    _check(lib().bvf_get_stats(ctx, ctypes.byref(s)), ctx)
+    return s
+
+
+def bvf_kernel_timing(ctx, enable: bool):
+    _check(lib().bvf_kernel_timing(ctx, 1 if enable else 0), ctx)
+
+
+def bvf_get_kernel_times(ctx) -> KernelTimes:
+    t = KernelTimes()
+    _check(lib().bvf_get_kernel_times(ctx, ctypes.byref(t)), ctx)
+    return t
+
+
+# ---- convenience ---------------------------------------------------------
+class Solver:
+    """One libbvf context on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, dx, dt, f0, qc=1.0, n_sls=2, n_pml=8, pml_R=1e-4):
+        self.shape = (nz, ny, nx)
+        self.grid = Grid(nx, ny, nz, dx, dt, n_pml, pml_R)
+        self.phys = Physics(f0, qc, n_sls)
+        self.n_sls = n_sls
+        self.ctx = bvf_create(self.grid, self.phys)
+
+    def close(self):
+        if self.ctx:
+            bvf_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_materials(self, index, table):
+        import torch
+        idx = torch.as_tensor(np.asarray(index, dtype=np.uint8) if not torch.is_tensor(index)
+                              else index).to("cuda", torch.uint8).contiguous()
+        bvf_set_materials(self.ctx, idx, table)
+        self.table = np.asarray(table, dtype=np.float64).reshape(-1, 9)
+
+    def set_source(self, plane, k_plane, c0, envelope, n_cycles=0, stream=None):
+        """plane: complex (ny, nx) array/tensor, or a float32 CUDA tensor (ny, nx, 2)."""
+        import torch
+        if torch.is_tensor(plane) and plane.dtype == torch.float32:
+            pl = plane.contiguous()
+        else:
+            p = np.asarray(plane.cpu() if torch.is_tensor(plane) else plane).astype(np.complex128)
+            pl = torch.from_numpy(np.stack([p.real, p.imag], -1).astype(np.float32)).cuda()
+        bvf_set_source(self.ctx, k_plane, pl, c0, envelope, n_cycles, stream)
+        self._plane = pl
+
+    def run(self, n_steps, peak_from=-1, dft_start=0, dft_steps=0, stream=None):
+        bvf_run_acoustic(self.ctx, n_steps, Capture(peak_from, dft_start, dft_steps), stream)
+
+    def reset(self, stream=None):
+        bvf_reset(self.ctx, stream)
+
+    def synchronize(self, stream=None):
+        bvf_synchronize(self.ctx, stream)
+
+    def _empty(self, dtype):
+        import torch
+        return torch.empty(self.shape, dtype=dtype, device="cuda")
+
+    def field(self, name_or_id, stream=None):
+        import torch
+        which = FIELDS.index(name_or_id) if isinstance(name_or_id, str) else name_or_id
+        out = self._empty(torch.float32)
+        bvf_get_field(self.ctx, which, out, stream)
+        return out
+
+    def set_field(self, name_or_id, value, stream=None):
+        import torch
+        which = FIELDS.index(name_or_id) if isinstance(name_or_id, str) else name_or_id
+        t = torch.as_tensor(value, dtype=torch.float32).cuda().contiguous()
+        bvf_set_field(self.ctx, which, t, stream)
+        self._keep = t
+
+    def memory_id(self, l, c):
+        return 9 + 6 * l + c
+
+    def pressure(self, stream=None):
+        import torch
+        out = self._empty(torch.float32)
+        bvf_get_pressure(self.ctx, out, stream)
+        return out
+
+    def peak(self, stream=None):
+        import torch
+        out = self._empty(torch.float32)
+        bvf_get_peak(self.ctx, out, stream)
+        return out
+
+    def amp_phase(self, stream=None):
+        import torch
+        amp, ph = self._empty(torch.float64), self._empty(torch.float64)
+        bvf_get_amp_phase(self.ctx, amp, ph, stream)
+        return amp, ph
+
+    def thermal(self, amp, dt, n_on, n_off, duty, T_a=37.0, rhob_cb=1050.0 * 3617.0,
+                p_scale=1.0, T=None, Tmax=None, cem=None, stream=None):
+        import torch
+        T = torch.full(self.shape, T_a, dtype=torch.float32, device="cuda") if T is None else T
+        Tmax = T.clone() if Tmax is None else Tmax
+        cem = torch.zeros(self.shape, dtype=torch.float64, device="cuda") if cem is None else cem
+        bvf_run_thermal(self.ctx, Thermal(dt, n_on, n_off, duty, T_a, rhob_cb, p_scale), amp, T,
+                        Tmax, cem, stream)
+        return T, Tmax, cem
+
+    def stats(self) -> Stats:
+        return bvf_get_stats(self.ctx)
+
+    def kernel_timing(self, enable: bool):
+        bvf_kernel_timing(self.ctx, enable)
+
+    def kernel_times(self) -> KernelTimes:
+        return bvf_get_kernel_times(self.ctx)
+
+
+def rs_plane(bowl: dict, nx, ny, dx, z_plane, f0, c0=1500.0, ds_over_lambda=0.25, stream=None):
+    """Rayleigh-Sommerfeld plane as a (ny, nx, 2) float32 CUDA tensor."""
+    import torch
+    b = Bowl(bowl["aperture"], bowl["roc"], (ctypes.c_double * 3)(*bowl["apex"]),
+             (ctypes.c_double * 3)(*bowl["dir"]), bowl["p0"], c0, ds_over_lambda)
+    out = torch.empty((ny, nx, 2), dtype=torch.float32, device="cuda")
+    bvf_rs_plane(b, nx, ny, dx, z_plane, f0, out, stream)
+    return out

@@ -1,0 +1,793 @@
+// Host side of libbvf: the C ABI declared in include/bvf.h.
+//
+// Coefficient derivation (FP64, once per material table) follows Sec. 3.2
+// (Eq. 3: Q = w / (2 c alpha), Q = Q0 q_c; relaxation constants fitted to Q)
+// and the standard-linear-solid tau method; the CPML profile follows the
+// convolutional PML with kappa = 1 (the paper defers boundary matching to its
+// reference).  All per-voxel work runs in the kernels of bvf_acoustic.cu and
+// bvf_aux.cu.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bvf_internal.cuh"
+
+using namespace bvf;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+thread_local std::string g_last_error;
+
+struct MatDerived {
+    double piR, muR, tauP, tauS;
+};
+
+}  // namespace
+
+struct bvf_ctx {
+    bvf_grid g{};
+    bvf_physics ph{};
+    int L = 0;
+    size_t N = 0, fstride = 0;
+    int P = 0, W = 0, nmax = 0;
+    // device state
+    float *fields = nullptr;          // (9 + 6L) arrays of fstride floats
+    float *psi = nullptr;             // 3 slabs x 6 memories
+    size_t slab_x = 0, slab_y = 0, slab_z = 0;
+    float *peak = nullptr;
+    double *dftC = nullptr, *dftS = nullptr;
+    int dft_count = 0;
+    uint8_t *index = nullptr;
+    MatCoef *lut = nullptr;
+    float2 *pml = nullptr;
+    float2 *src = nullptr;
+    int *flag = nullptr;
+    unsigned *scratch_u = nullptr;
+    float *T2 = nullptr, *Q = nullptr;
+    ThermCoef *tlut = nullptr;
+    // host mirror
+    std::vector<bvf_material> table;
+    std::vector<MatDerived> derived;
+    std::vector<double> tau_sigma;
+    bool have_materials = false;
+    int k_src = -1, envelope = BVF_ENV_NONE, n_cycles = 0;
+    double c0 = 1500.0;
+    bool have_source = false;
+    long long steps = 0, launches = 0, thermal_steps = 0;
+    double courant = 0.0;
+    std::string err;
+    // per-launch event timing of the acoustic kernels
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<cudaEvent_t> ev_vel, ev_str;   // start/stop pairs, flattened
+    size_t ev_used = 0;
+    double vel_ms = 0.0, str_ms = 0.0;
+    long long vel_n = 0, str_n = 0;
+};
+
+namespace {
+
+int fail(bvf_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(bvf_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? BVF_E_NOMEM : BVF_E_CUDA, m);
+}
+
+#define CK(call, where)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+// Relaxation times 1 / (2 pi f_l), f_l log-spaced on [f0/3, 3 f0] (f0 if L = 1).
+std::vector<double> relaxation_times(double f0, int L)
+{
+    std::vector<double> ts(L);
+    for (int l = 0; l < L; ++l) {
+        const double e = (L == 1) ? 0.0 : -1.0 + 2.0 * l / double(L - 1);
+        ts[l] = 1.0 / (2.0 * kPi * f0 * std::pow(3.0, e));
+    }
+    return ts;
+}
+
+// Single-frequency fit of the SLS strength tau to Q = qc w / (2 c alpha):
+// Q(w) = (1 + tau B) / (tau A) with A = sum w ts / (1 + (w ts)^2),
+// B = sum (w ts)^2 / (1 + (w ts)^2); relaxed modulus so that the phase speed
+// at f0 is c:  M_R = rho c^2 (Re m^{-1/2})^2, m = 1 + tau sum i w ts / (1 + i w ts).
+bool fit_mode(double rho, double c, double alpha, double f0, double qc,
+              const std::vector<double> &ts, double &M_R, double &tau)
+{
+    if (c == 0.0) { M_R = 0.0; tau = 0.0; return true; }
+    if (alpha <= 0.0 || ts.empty()) { M_R = rho * c * c; tau = 0.0; return true; }
+    const double w = 2.0 * kPi * f0;
+    const double Q = qc * w / (2.0 * c * alpha);
+    double A = 0.0, B = 0.0;
+    for (double t : ts) {
+        const double x = w * t;
+        A += x / (1.0 + x * x);
+        B += x * x / (1.0 + x * x);
+    }
+    const double den = Q * A - B;
+    if (!(den > 0.0)) return false;
+    tau = 1.0 / den;
+    std::complex<double> m(1.0, 0.0);
+    for (double t : ts) {
+        const std::complex<double> ix(0.0, w * t);
+        m += tau * ix / (1.0 + ix);
+    }
+    const double re = (1.0 / std::sqrt(m)).real();
+    M_R = rho * c * c * re * re;
+    return true;
+}
+
+// CPML (a, b) at doubled position pos2 = 2s (+1 for half points).
+void cpml_ab(int n, int P, double dx, double dt, double f0, double R, double cmax, int pos2,
+             double &a, double &b)
+{
+    a = 0.0;
+    b = 0.0;
+    if (P <= 0) return;
+    const double lo = (2.0 * P - pos2) / (2.0 * P);
+    const double hi = (pos2 - 2.0 * (n - 1 - P)) / (2.0 * P);
+    double xi = std::max(lo, hi);
+    if (!(xi > 0.0)) return;
+    xi = std::min(xi, 1.0);
+    const double d0 = -3.0 * cmax * std::log(R) / (2.0 * P * dx);
+    const double d = d0 * xi * xi;
+    const double al = kPi * f0 * (1.0 - xi);
+    b = std::exp(-(d + al) * dt);
+    a = (d + al > 0.0) ? d * (b - 1.0) / (d + al) : 0.0;
+}
+
+double envelope(int env, int n_cycles, double f0, double t)
+{
+    if (env == BVF_ENV_BURST) return (t >= 0.0 && t < n_cycles / f0) ? 1.0 : 0.0;
+    if (env == BVF_ENV_RAMP_CW) {
+        if (t < 0.0) return 0.0;
+        if (t < 1.0 / f0) return 0.5 * (1.0 - std::cos(kPi * f0 * t));
+        return 1.0;
+    }
+    return 0.0;
+}
+
+float *field_ptr(bvf_ctx *c, int which)
+{
+    return c->fields + (size_t)which * c->fstride;
+}
+
+cudaError_t next_event(bvf_ctx *c, cudaEvent_t *out)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        c->ev_pool.push_back(e);
+    }
+    *out = c->ev_pool[c->ev_used++];
+    return cudaSuccess;
+}
+
+// Sum the recorded event pairs into the accumulators and recycle the events.
+cudaError_t drain_events(bvf_ctx *c)
+{
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<cudaEvent_t> &v = kind ? c->ev_str : c->ev_vel;
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
+            cudaError_t r = cudaEventSynchronize(v[i + 1]);
+            if (r != cudaSuccess) return r;
+            float ms = 0.0f;
+            r = cudaEventElapsedTime(&ms, v[i], v[i + 1]);
+            if (r != cudaSuccess) return r;
+            (kind ? c->str_ms : c->vel_ms) += ms;
+            (kind ? c->str_n : c->vel_n) += 1;
+        }
+        v.clear();
+    }
+    c->ev_used = 0;
+    return cudaSuccess;
+}
+
+AcParams make_params(bvf_ctx *c)
+{
+    AcParams p{};
+    p.nx = c->g.nx;
+    p.ny = c->g.ny;
+    p.nz = c->g.nz;
+    p.P = c->P;
+    p.W = c->W;
+    p.L = c->L;
+    p.n_mat = (int)c->table.size();
+    p.dt = (float)c->g.dt;
+    p.inv_dx = (float)(1.0 / c->g.dx);
+    p.Lf = (float)c->L;
+    for (int l = 0; l < c->L; ++l) {
+        const double h = c->g.dt / (2.0 * c->tau_sigma[l]);
+        p.ca[l] = (float)((1.0 - h) / (1.0 + h));
+        p.cb[l] = (float)((c->g.dt / c->tau_sigma[l]) / (1.0 + h));
+    }
+    p.idx = c->index;
+    p.lut = c->lut;
+    p.vx = field_ptr(c, BVF_FIELD_VX);
+    p.vy = field_ptr(c, BVF_FIELD_VY);
+    p.vz = field_ptr(c, BVF_FIELD_VZ);
+    p.sxx = field_ptr(c, BVF_FIELD_SXX);
+    p.syy = field_ptr(c, BVF_FIELD_SYY);
+    p.szz = field_ptr(c, BVF_FIELD_SZZ);
+    p.sxy = field_ptr(c, BVF_FIELD_SXY);
+    p.sxz = field_ptr(c, BVF_FIELD_SXZ);
+    p.syz = field_ptr(c, BVF_FIELD_SYZ);
+    p.mem = field_ptr(c, BVF_FIELD_MEM0);
+    p.fstride = c->fstride;
+    p.psx = c->psi;
+    p.psy = c->psi + kNumCpmlSlots * c->slab_x;
+    p.psz = c->psi + kNumCpmlSlots * (c->slab_x + c->slab_y);
+    p.pml = c->pml;
+    p.nmax = c->nmax;
+    p.src = c->src;
+    p.k_src = c->k_src;
+    p.peak = c->peak;
+    p.dftC = c->dftC;
+    p.dftS = c->dftS;
+    p.flag = c->flag;
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bvf_version(void) { return BVF_VERSION; }
+
+double bvf_courant_limit(void) { return 6.0 / (7.0 * std::sqrt(3.0)); }
+
+const char *bvf_strerror(int code)
+{
+    switch (code) {
+    case BVF_OK: return "ok";
+    case BVF_E_ARG: return "invalid argument or call order";
+    case BVF_E_CFL: return "time step above the stability limit";
+    case BVF_E_MATERIAL: return "invalid material or material index";
+    case BVF_E_NOMEM: return "device allocation failed";
+    case BVF_E_CUDA: return "CUDA error";
+    case BVF_E_UNSTABLE: return "non-finite pressure detected";
+    default: return "unknown status";
+    }
+}
+
+const char *bvf_last_error(const bvf_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+void bvf_destroy(bvf_ctx *c)
+{
+    if (!c) return;
+    void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut,
+                    c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->tlut};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
+{
+    bvf_ctx *c = nullptr;
+    if (!out) return fail(nullptr, BVF_E_ARG, "bvf_create: out is NULL");
+    *out = nullptr;
+    if (!grid || !phys) return fail(nullptr, BVF_E_ARG, "bvf_create: NULL grid or physics");
+    const bvf_grid &g = *grid;
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1 || !(g.dx > 0.0) || !(g.dt > 0.0) || g.n_pml < 0)
+        return fail(nullptr, BVF_E_ARG, "bvf_create: bad grid sizes or spacing");
+    if (g.n_pml > 0 && (g.nx < 2 * g.n_pml + 2 || g.ny < 2 * g.n_pml + 2 ||
+                        g.nz < 2 * g.n_pml + 2 || !(g.pml_R > 0.0 && g.pml_R < 1.0)))
+        return fail(nullptr, BVF_E_ARG, "bvf_create: grid too small for the CPML or bad pml_R");
+    if (phys->n_sls < 0 || phys->n_sls > BVF_MAX_SLS || !(phys->f0 > 0.0) || !(phys->qc > 0.0))
+        return fail(nullptr, BVF_E_ARG, "bvf_create: bad physics (f0, qc or n_sls)");
+    if ((double)g.nx * g.ny * g.nz > 4.0e9)
+        return fail(nullptr, BVF_E_ARG, "bvf_create: grid larger than 4e9 voxels");
+
+    c = new (std::nothrow) bvf_ctx;
+    if (!c) return fail(nullptr, BVF_E_NOMEM, "bvf_create: host allocation failed");
+    c->g = g;
+    c->ph = *phys;
+    c->L = phys->n_sls;
+    c->N = (size_t)g.nx * g.ny * g.nz;
+    c->fstride = (c->N + 63) & ~(size_t)63;
+    c->P = g.n_pml;
+    c->W = g.n_pml > 0 ? 2 * g.n_pml + 1 : 0;
+    c->nmax = std::max(g.nx, std::max(g.ny, g.nz));
+    c->slab_x = (size_t)g.nz * g.ny * c->W;
+    c->slab_y = (size_t)g.nz * c->W * g.nx;
+    c->slab_z = (size_t)c->W * g.ny * g.nx;
+    c->tau_sigma = relaxation_times(phys->f0, c->L);
+
+    auto cleanup = [&](int code) { bvf_destroy(c); return code; };
+    cudaError_t e;
+    const size_t nf = 9 + 6 * (size_t)c->L;
+    if ((e = cudaMalloc(&c->fields, nf * c->fstride * sizeof(float))) != cudaSuccess)
+        return cleanup(cuda_fail(nullptr, e, "bvf_create: fields"));
+    const size_t npsi = kNumCpmlSlots * (c->slab_x + c->slab_y + c->slab_z);
+    if (npsi && (e = cudaMalloc(&c->psi, npsi * sizeof(float))) != cudaSuccess)
+        return cleanup(cuda_fail(nullptr, e, "bvf_create: cpml"));
+    if ((e = cudaMalloc(&c->peak, c->N * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&c->index, c->N)) != cudaSuccess ||
+        (e = cudaMalloc(&c->lut, BVF_MAX_MATERIALS * sizeof(MatCoef))) != cudaSuccess ||
+        (e = cudaMalloc(&c->pml, 6 * (size_t)c->nmax * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&c->src, (size_t)g.nx * g.ny * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&c->flag, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&c->scratch_u, sizeof(unsigned))) != cudaSuccess)
+        return cleanup(cuda_fail(nullptr, e, "bvf_create: buffers"));
+    if ((e = cudaMemset(c->fields, 0, nf * c->fstride * sizeof(float))) != cudaSuccess ||
+        (npsi && (e = cudaMemset(c->psi, 0, npsi * sizeof(float))) != cudaSuccess) ||
+        (e = cudaMemset(c->peak, 0, c->N * sizeof(float))) != cudaSuccess ||
+        (e = cudaMemset(c->index, 0, c->N)) != cudaSuccess ||
+        (e = cudaMemset(c->pml, 0, 6 * (size_t)c->nmax * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMemset(c->flag, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cleanup(cuda_fail(nullptr, e, "bvf_create: zero fill"));
+    *out = c;
+    return BVF_OK;
+}
+
+int bvf_set_materials(bvf_ctx *c, const uint8_t *d_index, const bvf_material *h_table, int n_mat)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_set_materials: NULL context");
+    if (!d_index || !h_table || n_mat < 1 || n_mat > BVF_MAX_MATERIALS)
+        return fail(c, BVF_E_ARG, "bvf_set_materials: NULL pointer or n_mat out of [1, 256]");
+    std::vector<MatDerived> der(n_mat);
+    double cmax_unrelaxed = 0.0, cmax = 0.0;
+    for (int m = 0; m < n_mat; ++m) {
+        const bvf_material &r = h_table[m];
+        char buf[160];
+        if (!(r.rho > 0.0) || !(r.cL > 0.0) || !(r.cS >= 0.0) || !(r.alphaL >= 0.0) ||
+            !(r.alphaS >= 0.0)) {
+            std::snprintf(buf, sizeof buf, "material %d: need rho > 0, cL > 0, cS >= 0, alpha >= 0", m);
+            return fail(c, BVF_E_MATERIAL, buf);
+        }
+        if (!(4.0 * r.cS * r.cS <= 3.0 * r.cL * r.cL)) {
+            std::snprintf(buf, sizeof buf, "material %d: Poisson ratio below -1 (cS > 0.866 cL)", m);
+            return fail(c, BVF_E_MATERIAL, buf);
+        }
+        if (!(r.k_th > 0.0) || !(r.c_th > 0.0) || !(r.perf >= 0.0) ||
+            !(r.heat_frac >= 0.0 && r.heat_frac <= 1.0)) {
+            std::snprintf(buf, sizeof buf, "material %d: bad thermal constants", m);
+            return fail(c, BVF_E_MATERIAL, buf);
+        }
+        MatDerived &d = der[m];
+        if (!fit_mode(r.rho, r.cL, r.alphaL, c->ph.f0, c->ph.qc, c->tau_sigma, d.piR, d.tauP) ||
+            !fit_mode(r.rho, r.cS, r.alphaS, c->ph.f0, c->ph.qc, c->tau_sigma, d.muR, d.tauS)) {
+            std::snprintf(buf, sizeof buf,
+                          "material %d: Q = qc w/(2 c alpha) below what %d SLS mechanisms reach", m,
+                          c->L);
+            return fail(c, BVF_E_MATERIAL, buf);
+        }
+        cmax = std::max(cmax, r.cL);
+        cmax_unrelaxed = std::max(cmax_unrelaxed, std::sqrt(d.piR * (1.0 + c->L * d.tauP) / r.rho));
+        cmax_unrelaxed = std::max(cmax_unrelaxed, std::sqrt(d.muR * (1.0 + c->L * d.tauS) / r.rho));
+    }
+    const double S = cmax_unrelaxed * c->g.dt / c->g.dx;
+    if (S > bvf_courant_limit()) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "Courant number %.5f above the limit %.5f", S,
+                      bvf_courant_limit());
+        return fail(c, BVF_E_CFL, buf);
+    }
+    // device LUT
+    std::vector<MatCoef> lut(n_mat);
+    for (int m = 0; m < n_mat; ++m) {
+        const MatDerived &d = der[m];
+        MatCoef &k = lut[m];
+        k.rho = (float)h_table[m].rho;
+        k.piU = (float)(d.piR * (1.0 + c->L * d.tauP));
+        k.piT = (float)(d.piR * d.tauP);
+        k.mu2U = (float)(2.0 * d.muR * (1.0 + c->L * d.tauS));
+        k.mu2T = (float)(2.0 * d.muR * d.tauS);
+        k.inv_mu = d.muR > 0.0 ? (float)(1.0 / d.muR) : INFINITY;
+        k.tauS = (float)d.tauS;
+        k.pad = 0.0f;
+    }
+    // CPML profile at integer (h = 0) and half (h = 1) points of each axis
+    std::vector<float2> pml(6 * (size_t)c->nmax, make_float2(0.0f, 0.0f));
+    const int nax[3] = {c->g.nx, c->g.ny, c->g.nz};
+    for (int ax = 0; ax < 3; ++ax)
+        for (int h = 0; h < 2; ++h)
+            for (int s = 0; s < nax[ax]; ++s) {
+                double a, b;
+                cpml_ab(nax[ax], c->P, c->g.dx, c->g.dt, c->ph.f0, c->g.pml_R, cmax, 2 * s + h, a, b);
+                pml[((size_t)ax * 2 + h) * c->nmax + s] = make_float2((float)a, (float)b);
+            }
+    CK(cudaMemcpy(c->index, d_index, c->N, cudaMemcpyDeviceToDevice), "copy index");
+    CK(cudaMemcpy(c->lut, lut.data(), n_mat * sizeof(MatCoef), cudaMemcpyHostToDevice), "copy lut");
+    CK(cudaMemcpy(c->pml, pml.data(), pml.size() * sizeof(float2), cudaMemcpyHostToDevice), "copy pml");
+    CK(cudaMemset(c->scratch_u, 0, sizeof(unsigned)), "memset");
+    CK(launch_index_max(c->index, c->N, c->scratch_u, 0), "index scan");
+    c->launches++;
+    unsigned mx = 0;
+    CK(cudaMemcpy(&mx, c->scratch_u, sizeof(unsigned), cudaMemcpyDeviceToHost), "index scan");
+    if ((int)mx >= n_mat) {
+        char buf[120];
+        std::snprintf(buf, sizeof buf, "material index %u >= table size %d", mx, n_mat);
+        c->have_materials = false;
+        return fail(c, BVF_E_MATERIAL, buf);
+    }
+    c->table.assign(h_table, h_table + n_mat);
+    c->derived = der;
+    c->courant = S;
+    c->have_materials = true;
+    return BVF_OK;
+}
+
+int bvf_set_source(bvf_ctx *c, int k_plane, const float *d_plane, double c0, int env,
+                   int n_cycles, void *stream)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_set_source: NULL context");
+    if (env == BVF_ENV_NONE) {
+        c->have_source = false;
+        c->envelope = BVF_ENV_NONE;
+        return BVF_OK;
+    }
+    if (!d_plane || k_plane < 0 || k_plane >= c->g.nz || !(c0 > 0.0) ||
+        (env != BVF_ENV_BURST && env != BVF_ENV_RAMP_CW) || (env == BVF_ENV_BURST && n_cycles < 1))
+        return fail(c, BVF_E_ARG, "bvf_set_source: bad plane, speed, envelope or cycle count");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(c->src, d_plane, (size_t)c->g.nx * c->g.ny * sizeof(float2),
+                       cudaMemcpyDeviceToDevice, s), "copy source plane");
+    c->k_src = k_plane;
+    c->c0 = c0;
+    c->envelope = env;
+    c->n_cycles = n_cycles;
+    c->have_source = true;
+    return BVF_OK;
+}
+
+int bvf_reset(bvf_ctx *c, void *stream)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_reset: NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nf = 9 + 6 * (size_t)c->L;
+    CK(cudaMemsetAsync(c->fields, 0, nf * c->fstride * sizeof(float), s), "reset");
+    const size_t npsi = kNumCpmlSlots * (c->slab_x + c->slab_y + c->slab_z);
+    if (npsi) CK(cudaMemsetAsync(c->psi, 0, npsi * sizeof(float), s), "reset");
+    CK(cudaMemsetAsync(c->peak, 0, c->N * sizeof(float), s), "reset");
+    if (c->dftC) {
+        CK(cudaMemsetAsync(c->dftC, 0, c->N * sizeof(double), s), "reset");
+        CK(cudaMemsetAsync(c->dftS, 0, c->N * sizeof(double), s), "reset");
+    }
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), s), "reset");
+    c->dft_count = 0;
+    c->steps = 0;
+    return BVF_OK;
+}
+
+int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stream)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_run_acoustic: NULL context");
+    if (!c->have_materials) return fail(c, BVF_E_ARG, "bvf_run_acoustic: call bvf_set_materials first");
+    if (n_steps < 0) return fail(c, BVF_E_ARG, "bvf_run_acoustic: negative step count");
+    cudaStream_t s = (cudaStream_t)stream;
+    bvf_capture cp{-1, 0, 0};
+    if (cap) cp = *cap;
+    if (cp.dft_steps < 0) return fail(c, BVF_E_ARG, "bvf_run_acoustic: negative dft_steps");
+    if (cp.dft_steps > 0 && !c->dftC) {
+        CK(cudaMalloc(&c->dftC, c->N * sizeof(double)), "dft buffers");
+        CK(cudaMalloc(&c->dftS, c->N * sizeof(double)), "dft buffers");
+        CK(cudaMemsetAsync(c->dftC, 0, c->N * sizeof(double), s), "dft buffers");
+        CK(cudaMemsetAsync(c->dftS, 0, c->N * sizeof(double), s), "dft buffers");
+    }
+    AcParams p = make_params(c);
+    const double w = 2.0 * kPi * c->ph.f0, dt = c->g.dt;
+    p.src_scale = (float)(2.0 * c->c0 * dt / c->g.dx);
+    for (int it = 0; it < n_steps; ++it) {
+        const long long n = c->steps;
+        const double t = (n + 0.5) * dt;
+        const double env = c->have_source ? envelope(c->envelope, c->n_cycles, c->ph.f0, t) : 0.0;
+        p.src_on = (c->have_source && env != 0.0) ? 1 : 0;
+        p.src_ws = (float)(env * std::sin(w * t));
+        p.src_wc = (float)(env * std::cos(w * t));
+        const long long step = n + 1;
+        p.do_peak = (cp.peak_from >= 0 && step >= cp.peak_from) ? 1 : 0;
+        p.do_dft = (cp.dft_steps > 0 && step >= cp.dft_start && step < (long long)cp.dft_start + cp.dft_steps) ? 1 : 0;
+        p.cw = std::cos(w * step * dt);
+        p.sw = std::sin(w * step * dt);
+        if (c->timing) {
+            if (c->ev_used + 3 > 3072) CK(drain_events(c), "kernel timing");
+            cudaEvent_t e0, e1, e2;
+            CK(next_event(c, &e0), "kernel timing");
+            CK(next_event(c, &e1), "kernel timing");
+            CK(next_event(c, &e2), "kernel timing");
+            CK(cudaEventRecord(e0, s), "kernel timing");
+            CK(launch_velocity(p, s), "velocity kernel");
+            CK(cudaEventRecord(e1, s), "kernel timing");
+            CK(launch_stress(p, s), "stress kernel");
+            CK(cudaEventRecord(e2, s), "kernel timing");
+            c->ev_vel.push_back(e0);
+            c->ev_vel.push_back(e1);
+            c->ev_str.push_back(e1);
+            c->ev_str.push_back(e2);
+        } else {
+            CK(launch_velocity(p, s), "velocity kernel");
+            CK(launch_stress(p, s), "stress kernel");
+        }
+        c->launches += 2;
+        c->dft_count += p.do_dft;
+        c->steps++;
+    }
+    return BVF_OK;
+}
+
+int bvf_synchronize(bvf_ctx *c, void *stream)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_synchronize: NULL context");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+    int f = 0;
+    CK(cudaMemcpy(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
+    if (f) return fail(c, BVF_E_UNSTABLE, "non-finite pressure detected");
+    return BVF_OK;
+}
+
+int bvf_get_field(bvf_ctx *c, int which, float *d_out, void *stream)
+{
+    if (!c || !d_out || which < 0 || which >= 9 + 6 * c->L)
+        return fail(c, BVF_E_ARG, "bvf_get_field: bad context, pointer or field id");
+    CK(cudaMemcpyAsync(d_out, field_ptr(c, which), c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream), "get field");
+    return BVF_OK;
+}
+
+int bvf_set_field(bvf_ctx *c, int which, const float *d_in, void *stream)
+{
+    if (!c || !d_in || which < 0 || which >= 9 + 6 * c->L)
+        return fail(c, BVF_E_ARG, "bvf_set_field: bad context, pointer or field id");
+    CK(cudaMemcpyAsync(field_ptr(c, which), d_in, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream), "set field");
+    return BVF_OK;
+}
+
+int bvf_get_pressure(bvf_ctx *c, float *d_out, void *stream)
+{
+    if (!c || !d_out) return fail(c, BVF_E_ARG, "bvf_get_pressure: NULL argument");
+    CK(launch_pressure(field_ptr(c, BVF_FIELD_SXX), field_ptr(c, BVF_FIELD_SYY),
+                       field_ptr(c, BVF_FIELD_SZZ), d_out, c->N, (cudaStream_t)stream),
+       "pressure kernel");
+    c->launches++;
+    return BVF_OK;
+}
+
+int bvf_get_peak(bvf_ctx *c, float *d_out, void *stream)
+{
+    if (!c || !d_out) return fail(c, BVF_E_ARG, "bvf_get_peak: NULL argument");
+    CK(cudaMemcpyAsync(d_out, c->peak, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream), "get peak");
+    return BVF_OK;
+}
+
+int bvf_get_amp_phase(bvf_ctx *c, double *d_amp, double *d_phase, void *stream)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_get_amp_phase: NULL context");
+    if (!c->dftC || c->dft_count <= 0)
+        return fail(c, BVF_E_ARG, "bvf_get_amp_phase: no step was captured");
+    CK(launch_amp_phase(c->dftC, c->dftS, c->N, c->dft_count, d_amp, d_phase,
+                        (cudaStream_t)stream), "amp/phase kernel");
+    c->launches++;
+    return BVF_OK;
+}
+
+int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, float *d_T,
+                    float *d_Tmax, double *d_cem43, void *stream)
+{
+    if (!c || !th || !d_T || !d_Tmax || !d_cem43)
+        return fail(c, BVF_E_ARG, "bvf_run_thermal: NULL argument");
+    if (!c->have_materials) return fail(c, BVF_E_ARG, "bvf_run_thermal: call bvf_set_materials first");
+    if (th->n_on < 0 || th->n_off < 0 || !(th->dt > 0.0) || !(th->duty >= 0.0 && th->duty <= 1.0) ||
+        !(th->rhob_cb >= 0.0))
+        return fail(c, BVF_E_ARG, "bvf_run_thermal: bad regime");
+    const int n_mat = (int)c->table.size();
+    std::vector<ThermCoef> tl(n_mat);
+    double dt_lim = 1e300;
+    for (int m = 0; m < n_mat; ++m) {
+        const bvf_material &r = c->table[m];
+        tl[m].k = (float)r.k_th;
+        tl[m].inv_rhoc = (float)(1.0 / (r.rho * r.c_th));
+        tl[m].perfw = (float)(r.perf * th->rhob_cb);
+        tl[m].qfac = (float)(r.heat_frac * r.alphaL / (r.rho * r.cL));
+        dt_lim = std::min(dt_lim, c->g.dx * c->g.dx * r.rho * r.c_th / (6.0 * r.k_th));
+    }
+    if (th->dt > dt_lim)
+        return fail(c, BVF_E_ARG, "bvf_run_thermal: dt above the explicit stability limit");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->T2) {
+        CK(cudaMalloc(&c->T2, c->N * sizeof(float)), "thermal buffers");
+        CK(cudaMalloc(&c->Q, c->N * sizeof(float)), "thermal buffers");
+        CK(cudaMalloc(&c->tlut, BVF_MAX_MATERIALS * sizeof(ThermCoef)), "thermal buffers");
+    }
+    CK(cudaMemcpyAsync(c->tlut, tl.data(), n_mat * sizeof(ThermCoef), cudaMemcpyHostToDevice, s),
+       "thermal lut");
+    CK(launch_heat_source(c->index, c->tlut, n_mat, d_amp, th->p_scale, c->Q, c->N, s), "heat source");
+    c->launches++;
+    ThParams p{};
+    p.nx = c->g.nx;
+    p.ny = c->g.ny;
+    p.nz = c->g.nz;
+    p.dt = (float)th->dt;
+    p.inv_dx2 = (float)(1.0 / (c->g.dx * c->g.dx));
+    p.T_a = (float)th->T_a;
+    p.dt60 = (float)(th->dt / 60.0);
+    p.idx = c->index;
+    p.lut = c->tlut;
+    p.n_mat = n_mat;
+    p.Q = c->Q;
+    p.Tmax = d_Tmax;
+    p.cem = d_cem43;
+    const int total = th->n_on + th->n_off;
+    float *a = d_T, *b = c->T2;
+    for (int n = 0; n < total; ++n) {
+        p.dc = (n < th->n_on) ? (float)th->duty : 0.0f;
+        p.T = a;
+        p.Tn = b;
+        CK(launch_thermal_step(p, s), "thermal kernel");
+        c->launches++;
+        std::swap(a, b);
+    }
+    if (a != d_T) CK(cudaMemcpyAsync(d_T, a, c->N * sizeof(float), cudaMemcpyDeviceToDevice, s), "T out");
+    c->thermal_steps += total;
+    return BVF_OK;
+}
+
+int bvf_rs_plane(const bvf_bowl *bw, int nx, int ny, double dx, double z_plane, double f0,
+                 float *d_out, void *stream)
+{
+    if (!bw || !d_out || nx < 1 || ny < 1 || !(dx > 0.0) || !(f0 > 0.0) || !(bw->c0 > 0.0))
+        return fail(nullptr, BVF_E_ARG, "bvf_rs_plane: bad argument");
+    const double a = 0.5 * bw->aperture, R = bw->roc;
+    if (!(a > 0.0) || !(R >= a)) return fail(nullptr, BVF_E_ARG, "bvf_rs_plane: need 0 < aperture/2 <= roc");
+    const double lambda = bw->c0 / f0;
+    const double ds = (bw->ds_over_lambda > 0.0 ? bw->ds_over_lambda : 0.25) * lambda;
+    // Cap cut into rings of equal polar-angle width, each into equal azimuthal
+    // elements of length about ds, then rotated from +z to dir about the apex.
+    double ux = bw->dir[0], uy = bw->dir[1], uz = bw->dir[2];
+    const double nrm = std::sqrt(ux * ux + uy * uy + uz * uz);
+    if (!(nrm > 0.0)) return fail(nullptr, BVF_E_ARG, "bvf_rs_plane: zero direction");
+    ux /= nrm; uy /= nrm; uz /= nrm;
+    double kx = -uy, ky = ux;
+    const double sn = std::sqrt(kx * kx + ky * ky), cs = uz;
+    if (sn > 0.0) { kx /= sn; ky /= sn; }
+    const double thmax = std::asin(a / R);
+    const int nr = std::max(1, (int)std::ceil(R * thmax / ds));
+    std::vector<float4> el;
+    for (int r = 0; r < nr; ++r) {
+        const double t0 = thmax * r / nr, t1 = thmax * (r + 1) / nr, tc = 0.5 * (t0 + t1);
+        const double area = 2.0 * kPi * R * R * (std::cos(t0) - std::cos(t1));
+        const int naz = std::max(1, (int)std::lround(2.0 * kPi * R * std::sin(tc) / ds));
+        for (int e = 0; e < naz; ++e) {
+            const double ph = 2.0 * kPi * (e + 0.5) / naz;
+            const double px = R * std::sin(tc) * std::cos(ph), py = R * std::sin(tc) * std::sin(ph);
+            const double pz = R * (1.0 - std::cos(tc));
+            const double kp = kx * px + ky * py;
+            const double cx = ky * pz, cy = -kx * pz, cz = kx * py - ky * px;
+            const double rx = px * cs + cx * sn + kx * kp * (1.0 - cs);
+            const double ry = py * cs + cy * sn + ky * kp * (1.0 - cs);
+            const double rz = pz * cs + cz * sn;
+            const double ex = bw->apex[0] + rx, ey = bw->apex[1] + ry, ez = bw->apex[2] + rz;
+            if (!(ez < z_plane)) return fail(nullptr, BVF_E_ARG, "bvf_rs_plane: bowl crosses the source plane");
+            el.push_back(make_float4((float)ex, (float)ey, (float)ez, (float)(area / naz)));
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float4 *d_el = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_el, el.size() * sizeof(float4), s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_rs_plane: element buffer");
+    e = cudaMemcpyAsync(d_el, el.data(), el.size() * sizeof(float4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const double k = 2.0 * kPi / lambda;
+        e = launch_rs(d_el, (int)el.size(), nx, ny, (float)dx, (float)z_plane, (float)(k / kPi),
+                      k * bw->p0 / (2.0 * kPi), reinterpret_cast<float2 *>(d_out), s);
+    }
+    cudaError_t e2 = cudaFreeAsync(d_el, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_rs_plane");
+    if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "bvf_rs_plane: free");
+    return BVF_OK;
+}
+
+int bvf_transmission(int nx, int ny, int nz, const uint8_t *d_idx_a, const bvf_material *h_mat_a,
+                     int n_a, const double *d_amp_a, const uint8_t *d_idx_w,
+                     const bvf_material *h_mat_w, int n_w, const double *d_amp_w, double *h_EL,
+                     double *h_TS, int *h_zm, double *h_Iw_max, void *stream)
+{
+    bvf_ctx *c = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !d_idx_a || !h_mat_a || !d_amp_a || !d_idx_w || !h_mat_w ||
+        !d_amp_w || n_a < 1 || n_w < 1 || n_a > BVF_MAX_MATERIALS || n_w > BVF_MAX_MATERIALS)
+        return fail(nullptr, BVF_E_ARG, "bvf_transmission: bad argument");
+    std::vector<double> z(2 * BVF_MAX_MATERIALS, 0.0);
+    for (int m = 0; m < n_a; ++m) z[m] = 1.0 / (2.0 * h_mat_a[m].rho * h_mat_a[m].cL);
+    for (int m = 0; m < n_w; ++m) z[BVF_MAX_MATERIALS + m] = 1.0 / (2.0 * h_mat_w[m].rho * h_mat_w[m].cL);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)nx * ny * nz;
+    // one scratch block: [z tables][best][idx][sums]
+    const size_t bytes = 2 * BVF_MAX_MATERIALS * sizeof(double) + 2 * sizeof(unsigned long long) +
+                         3 * sizeof(double);
+    char *d = nullptr;
+    CK(cudaMallocAsync((void **)&d, bytes, s), "transmission scratch");
+    double *dz = reinterpret_cast<double *>(d);
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(dz + 2 * BVF_MAX_MATERIALS);
+    unsigned long long *qb = best + 1;
+    double *sums = reinterpret_cast<double *>(qb + 1);
+    const unsigned long long init[2] = {0ull, ~0ull};
+    double res[3] = {0, 0, 0};
+    unsigned long long best_bits = 0;
+    cudaError_t e = cudaMemcpyAsync(dz, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best, init, sizeof init, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_intensity_argmax(d_idx_w, dz + BVF_MAX_MATERIALS, d_amp_w, n, best, s);
+    if (e == cudaSuccess)
+        e = launch_intensity_argmin_index(d_idx_w, dz + BVF_MAX_MATERIALS, d_amp_w, n, best, qb, s);
+    if (e == cudaSuccess)
+        e = launch_plane_sums(d_idx_a, dz, d_amp_a, d_idx_w, dz + BVF_MAX_MATERIALS, d_amp_w, nx, ny,
+                              nz, qb, sums, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, sums, sizeof res, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&best_bits, best, sizeof best_bits, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_transmission");
+    if (!(res[1] > 0.0)) return fail(nullptr, BVF_E_ARG, "bvf_transmission: zero water intensity");
+    const double el = res[0] / res[1];
+    if (h_EL) *h_EL = el;
+    if (h_TS) *h_TS = std::sqrt(el);
+    if (h_zm) *h_zm = (int)res[2];
+    if (h_Iw_max) {
+        double bw;
+        std::memcpy(&bw, &best_bits, sizeof bw);
+        *h_Iw_max = bw;
+    }
+    (void)c;
+    return BVF_OK;
+}
+
+int bvf_kernel_timing(bvf_ctx *c, int enable)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_kernel_timing: NULL context");
+    CK(drain_events(c), "kernel timing");
+    c->timing = enable != 0;
+    c->vel_ms = c->str_ms = 0.0;
+    c->vel_n = c->str_n = 0;
+    return BVF_OK;
+}
+
+int bvf_get_kernel_times(bvf_ctx *c, bvf_kernel_times *out)
+{
+    if (!c || !out) return fail(c, BVF_E_ARG, "bvf_get_kernel_times: NULL argument");
+    CK(drain_events(c), "kernel timing");
+    out->velocity_launches = c->vel_n;
+    out->stress_launches = c->str_n;
+    out->velocity_ms = c->vel_ms;
+    out->stress_ms = c->str_ms;
+    return BVF_OK;
+}
+
+int bvf_get_stats(const bvf_ctx *c, bvf_stats *out)
+{
+    if (!c || !out) return fail(nullptr, BVF_E_ARG, "bvf_get_stats: NULL argument");
+    out->steps = c->steps;
+    out->kernel_launches = c->launches;
+    out->thermal_steps = c->thermal_steps;
+    out->courant = c->courant;
+    // velocity: read 6 sigma + 3 v, write 3 v (12 words); stress: read 3 v,
+    // read + write 6 sigma and 6L memory variables (15 + 12 L words); the index
+    // byte in each kernel and the peak map (read + write)
+    out->bytes_per_voxel_step = 4.0 * (12 + 15 + 12 * c->L) + 2.0 + 8.0;
+    return BVF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+// Auxiliary kernels: index-range scan, pressure / amplitude-phase read-out,
+// Rayleigh-Sommerfeld bowl field (Sec. 2.3), BHTE + CEM43 step (Sec. 2.4),
+// and the E_L reductions (Sec. 2.4, Eq. 2).
+#include "bvf_internal.cuh"
+
+namespace bvf {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(size_t n, int per_block = kThreads, unsigned cap = 152u * 16u)
+{
+    size_t b = (n + per_block - 1) / per_block;
+    return (unsigned)(b < cap ? (b ? b : 1) : cap);
+}
+
+__global__ void k_index_max(const uint8_t *__restrict__ idx, size_t n, unsigned *out)
+{
+    unsigned m = 0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned)idx[q]);
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_pressure(const float *__restrict__ a, const float *__restrict__ b,
+                           const float *__restrict__ c, float *__restrict__ out, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        out[q] = -(a[q] + b[q] + c[q]) / 3.0f;
+}
+
+// p(t) = A cos(w t + phi): C = A N/2 cos phi, S = -A N/2 sin phi
+__global__ void k_amp_phase(const double *__restrict__ C, const double *__restrict__ S, size_t n,
+                            double inv_half_n, double *amp, double *ph)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const double c = C[q], s = S[q];
+        if (amp) amp[q] = sqrt(c * c + s * s) * inv_half_n;
+        if (ph) ph[q] = atan2(-s, c);
+    }
+}
+
+// One thread per plane point, elements staged through shared memory.
+// p = pref * sum_e dA_e (sin(k r) + i cos(k r)) / r   with pref = k p0 / (2 pi):
+// the i k p0 / (2 pi) prefactor times exp(-i k r) = cos kr - i sin kr.
+__global__ void __launch_bounds__(kThreads) k_rs(const float4 *__restrict__ el, int ne, int nx,
+                                                 int ny, float dx, float zp, float k_over_pi,
+                                                 double pref, float2 *__restrict__ out)
+{
+    __shared__ float4 s_el[kThreads];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < nx * ny;
+    const float x = live ? (q % nx) * dx : 0.0f;
+    const float y = live ? (q / nx) * dx : 0.0f;
+    double re = 0.0, im = 0.0;
+    for (int base = 0; base < ne; base += kThreads) {
+        if (base + threadIdx.x < ne) s_el[threadIdx.x] = el[base + threadIdx.x];
+        __syncthreads();
+        const int cnt = min(kThreads, ne - base);
+        float pre = 0.0f, pim = 0.0f;   // partial sums of one tile in FP32
+        for (int e = 0; e < cnt; ++e) {
+            const float4 E = s_el[e];
+            const float ddx = x - E.x, ddy = y - E.y, ddz = zp - E.z;
+            const float r = sqrtf(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+            float sn, cs;
+            sincospif(k_over_pi * r, &sn, &cs);
+            const float w = E.w / r;
+            pre = fmaf(w, sn, pre);
+            pim = fmaf(w, cs, pim);
+        }
+        re += pre;
+        im += pim;
+        __syncthreads();
+    }
+    if (live) out[q] = make_float2((float)(pref * re), (float)(pref * im));
+}
+
+__global__ void k_heat_source(const uint8_t *__restrict__ idx, const ThermCoef *__restrict__ lut,
+                              const double *__restrict__ amp, double p_scale,
+                              float *__restrict__ Q, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const float A = amp ? (float)(p_scale * amp[q]) : 0.0f;
+        Q[q] = lut[idx[q]].qfac * A * A;
+    }
+}
+
+// Pennes forward-Euler step; border voxels held at T_a; T_max and CEM43 fused.
+__global__ void __launch_bounds__(256) k_thermal(ThParams p)
+{
+    extern __shared__ ThermCoef s_th[];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int m = tid; m < p.n_mat; m += blockDim.x * blockDim.y) s_th[m] = p.lut[m];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= p.nx || j >= p.ny) return;
+    const long long SY = p.nx, SZ = (long long)p.nx * p.ny;
+    const long long q = k * SZ + j * SY + i;
+    float Tn;
+    if (i == 0 || j == 0 || k == 0 || i == p.nx - 1 || j == p.ny - 1 || k == p.nz - 1) {
+        Tn = p.T_a;
+    } else {
+        const ThermCoef c = s_th[p.idx[q]];
+        const float T = p.T[q];
+        const long long nb[6] = {q - 1, q + 1, q - SY, q + SY, q - SZ, q + SZ};
+        float lap = 0.0f;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const float kn = s_th[p.idx[nb[f]]].k;
+            const float kf = 2.0f * c.k * kn / (c.k + kn);
+            lap += kf * (p.T[nb[f]] - T);
+        }
+        const float rhs = lap * p.inv_dx2 - c.perfw * (T - p.T_a) + p.dc * p.Q[q];
+        Tn = T + p.dt * rhs * c.inv_rhoc;
+    }
+    p.Tn[q] = Tn;
+    p.Tmax[q] = fmaxf(p.Tmax[q], Tn);
+    // R^(43-T) = 2^(log2(R) (43 - T)), log2 R = -1 at or above 43 C, else -2
+    const float l2r = (Tn >= 43.0f) ? -1.0f : -2.0f;
+    p.cem[q] += (double)(p.dt60 * exp2f(l2r * (43.0f - Tn)));
+}
+
+// Intensity I = A^2 / (2 rho c) = A^2 * zw[m] with zw[m] = 1 / (2 rho c).
+// Positive doubles order like their bit patterns, so atomicMax on the bits
+// finds the maximum.
+__global__ void k_int_max(const uint8_t *__restrict__ idx, const double *__restrict__ zw,
+                          const double *__restrict__ amp, size_t n, unsigned long long *best)
+{
+    unsigned long long m = 0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const double I = amp[q] * amp[q] * zw[idx[q]];
+        m = max(m, (unsigned long long)__double_as_longlong(I));
+    }
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(best, m);
+}
+
+__global__ void k_int_argmin(const uint8_t *__restrict__ idx, const double *__restrict__ zw,
+                             const double *__restrict__ amp, size_t n,
+                             const unsigned long long *best, unsigned long long *out)
+{
+    const unsigned long long b = *best;
+    unsigned long long m = ~0ull;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x) {
+        const double I = amp[q] * amp[q] * zw[idx[q]];
+        if ((unsigned long long)__double_as_longlong(I) == b) m = min(m, (unsigned long long)q);
+    }
+    for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(out, m);
+}
+
+// Plane sums of both intensity maps at z_m, one block, fixed order.
+__global__ void __launch_bounds__(1024) k_plane_sums(
+    const uint8_t *__restrict__ ia, const double *__restrict__ za, const double *__restrict__ aa,
+    const uint8_t *__restrict__ iw, const double *__restrict__ zw, const double *__restrict__ aw,
+    int nx, int ny, int nz, const unsigned long long *qbest, double *sums)
+{
+    __shared__ double s_a[1024], s_w[1024];
+    const long long plane = (long long)nx * ny;
+    if (*qbest >= (unsigned long long)(plane * nz)) {   // no maximum found
+        if (threadIdx.x == 0) sums[0] = sums[1] = sums[2] = 0.0;
+        return;
+    }
+    const long long z = (long long)(*qbest / (unsigned long long)plane);
+    const long long base = z * plane;
+    double sa = 0.0, sw = 0.0;
+    for (long long t = threadIdx.x; t < plane; t += blockDim.x) {
+        const long long q = base + t;
+        sa += aa[q] * aa[q] * za[ia[q]];
+        sw += aw[q] * aw[q] * zw[iw[q]];
+    }
+    s_a[threadIdx.x] = sa;
+    s_w[threadIdx.x] = sw;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_a[threadIdx.x] += s_a[threadIdx.x + o];
+            s_w[threadIdx.x] += s_w[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sums[0] = s_a[0];
+        sums[1] = s_w[0];
+        sums[2] = (double)z;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cudaStream_t s)
+{
+    k_index_max<<<blocks_for(n), kThreads, 0, s>>>(idx, n, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pressure(const float *sxx, const float *syy, const float *szz, float *out,
+                            size_t n, cudaStream_t s)
+{
+    k_pressure<<<blocks_for(n), kThreads, 0, s>>>(sxx, syy, szz, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double *amp,
+                             double *ph, cudaStream_t s)
+{
+    k_amp_phase<<<blocks_for(n), kThreads, 0, s>>>(C, S, n, 2.0 / count, amp, ph);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float zp, float k_over_pi,
+                      double pref, float2 *out, cudaStream_t s)
+{
+    const int n = nx * ny;
+    k_rs<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(el, ne, nx, ny, dx, zp, k_over_pi,
+                                                           pref, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_mat,
+                               const double *amp, double p_scale, float *Q, size_t n,
+                               cudaStream_t s)
+{
+    (void)n_mat;
+    k_heat_source<<<blocks_for(n), kThreads, 0, s>>>(idx, lut, amp, p_scale, Q, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thermal_step(const ThParams &p, cudaStream_t s)
+{
+    dim3 blk(32, 8, 1);
+    dim3 grd((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz);
+    k_thermal<<<grd, blk, p.n_mat * sizeof(ThermCoef), s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_argmax(const uint8_t *idx, const double *zw, const double *amp,
+                                    size_t n, unsigned long long *d_best, cudaStream_t s)
+{
+    k_int_max<<<blocks_for(n), kThreads, 0, s>>>(idx, zw, amp, n, d_best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_argmin_index(const uint8_t *idx, const double *zw,
+                                          const double *amp, size_t n,
+                                          const unsigned long long *d_best,
+                                          unsigned long long *d_idx, cudaStream_t s)
+{
+    k_int_argmin<<<blocks_for(n), kThreads, 0, s>>>(idx, zw, amp, n, d_best, d_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plane_sums(const uint8_t *idx_a, const double *za, const double *amp_a,
+                              const uint8_t *idx_w, const double *zw, const double *amp_w,
+                              int nx, int ny, int nz, const unsigned long long *d_idx,
+                              double *d_sums, cudaStream_t s)
+{
+    k_plane_sums<<<1, 1024, 0, s>>>(idx_a, za, amp_a, idx_w, zw, amp_w, nx, ny, nz, d_idx, d_sums);
+    return cudaGetLastError();
+}
+
+}  // namespace bvf

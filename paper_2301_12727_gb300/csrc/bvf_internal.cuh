@@ -1,0 +1,105 @@
+// Internal declarations of libbvf (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bvf.h"
+
+namespace bvf {
+
+// Per-material coefficients of the acoustic kernels (FP32, derived in FP64 on
+// the host).  Normal stress:  Psi = piU th - mu2U (th - e_ii),
+//                             Theta = piT th - mu2T (th - e_ii);
+// shear points combine inv_mu (harmonic mean) and tauS (arithmetic mean).
+struct MatCoef {
+    float rho;     // density (buoyancy at v-points: 2 / (rho_a + rho_b))
+    float piU;     // pi_R (1 + L tau_P)
+    float piT;     // pi_R tau_P
+    float mu2U;    // 2 mu_R (1 + L tau_S)
+    float mu2T;    // 2 mu_R tau_S
+    float inv_mu;  // 1 / mu_R  (+inf for fluids, so the harmonic mean is 0)
+    float tauS;    // tau_S
+    float pad;
+};
+
+// Per-material constants of the BHTE kernel.
+struct ThermCoef {
+    float k;         // conductivity
+    float inv_rhoc;  // 1 / (rho c_th)
+    float perfw;     // perf * rhob_cb
+    float qfac;      // heat_frac * alphaL / (rho cL)
+};
+
+constexpr int kNumCpmlSlots = 6;   // CPML memories per slab (see ctx layout)
+
+struct AcParams {
+    int nx, ny, nz;
+    int P, W;            // CPML cells per face; slab width 2P+1 (0 if no CPML)
+    int L;               // SLS mechanisms
+    int n_mat;
+    float dt, inv_dx, Lf;
+    float ca[BVF_MAX_SLS], cb[BVF_MAX_SLS];
+    const uint8_t *idx;
+    const MatCoef *lut;
+    float *vx, *vy, *vz, *sxx, *syy, *szz, *sxy, *sxz, *syz;
+    float *mem;          // memory variables, [l][c] arrays of `fstride` floats
+    size_t fstride;
+    float *psx, *psy, *psz;   // CPML slabs: x [6][nz][ny][W], y [6][nz][W][nx], z [6][W][ny][nx]
+    const float2 *pml;   // (a, b) at [axis][h][s], h = 0 integer / 1 half point
+    int nmax;
+    // source plane
+    const float2 *src;
+    int k_src, src_on;
+    float src_ws, src_wc, src_scale;   // env sin(wt), env cos(wt), 2 c0 dt / dx
+    // capture
+    float *peak;
+    int do_peak;
+    double *dftC, *dftS;
+    int do_dft;
+    double cw, sw;
+    int *flag;
+};
+
+struct ThParams {
+    int nx, ny, nz;
+    float dt, inv_dx2, T_a, dc, dt60;
+    const uint8_t *idx;
+    const ThermCoef *lut;
+    int n_mat;
+    const float *T;
+    float *Tn;
+    const float *Q;
+    float *Tmax;
+    double *cem;
+};
+
+// kernel launchers (bvf_acoustic.cu / bvf_aux.cu); return cudaGetLastError()
+cudaError_t launch_velocity(const AcParams &p, cudaStream_t s);
+cudaError_t launch_stress(const AcParams &p, cudaStream_t s);
+cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cudaStream_t s);
+cudaError_t launch_pressure(const float *sxx, const float *syy, const float *szz, float *out,
+                            size_t n, cudaStream_t s);
+cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double *amp,
+                             double *ph, cudaStream_t s);
+cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float zp, float k_over_pi,
+                      double pref, float2 *out, cudaStream_t s);
+cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_mat,
+                               const double *amp, double p_scale, float *Q, size_t n,
+                               cudaStream_t s);
+cudaError_t launch_thermal_step(const ThParams &p, cudaStream_t s);
+cudaError_t launch_intensity_argmax(const uint8_t *idx, const double *zw, const double *amp,
+                                    size_t n, unsigned long long *d_best, cudaStream_t s);
+cudaError_t launch_intensity_argmin_index(const uint8_t *idx, const double *zw,
+                                          const double *amp, size_t n,
+                                          const unsigned long long *d_best,
+                                          unsigned long long *d_idx, cudaStream_t s);
+cudaError_t launch_plane_sums(const uint8_t *idx_a, const double *za, const double *amp_a,
+                              const uint8_t *idx_w, const double *zw, const double *amp_w,
+                              int nx, int ny, int nz, const unsigned long long *d_idx,
+                              double *d_sums, cudaStream_t s);
+
+}  // namespace bvf

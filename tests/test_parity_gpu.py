@@ -1,0 +1,275 @@
+"""GPU (libbvf, FP32 with FP64 capture) against the FP64 oracle and closed forms.
+
+Tolerance: relative L2 <= 1e-4 on the pressure field (and on the other
+outputs unless stated), the bound set for the FP32 stencil.  Every call goes
+through the C ABI.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import analytic as an
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def bvf():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2301_12727_gb300 import build
+    build.build()
+    from paper_2301_12727_gb300 import bvf as m
+    return m
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def mat_row(rho, cL, cS=0.0, aL=0.0, aS=0.0, k=0.5, c=3600.0, perf=0.0, heat=1.0):
+    return [rho, cL, cS, aL, aS, k, c, perf, heat]
+
+
+def make_pair(bvf, orc, c, n_sls=2):
+    s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, qc=c.qc, n_sls=n_sls, n_pml=c.n_pml,
+                   pml_R=c.pml_R)
+    s.set_materials(c.index, c.materials)
+    A = orc.Acoustic(c.nx, c.ny, c.nz, c.dx, c.dt, c.index, c.materials, c.f0, qc=c.qc,
+                     n_sls=n_sls, n_pml=c.n_pml, pml_R=c.pml_R)
+    return s, A
+
+
+# --------------------------------------------------------------------------
+def test_gpu_discrete_plane_wave_exact(bvf):
+    """Same closed form that pins the oracle: an oblique discrete plane wave in
+    a homogeneous solid, now through the GPU kernels (FP32)."""
+    n, dx, rho, cL, cS = 48, 1e-3, 1000.0, 2800.0, 1400.0
+    dt = 0.3 * dx / cL
+    kvec = np.array([2 * np.pi / (7 * dx), 2 * np.pi / (9 * dx), 2 * np.pi / (11 * dx)])
+    for mode in ("P", "S"):
+        s = bvf.Solver(n, n, n, dx, dt, 5e5, n_sls=2, n_pml=0)
+        s.set_materials(np.zeros((n, n, n), np.uint8), [mat_row(rho, cL, cS)])
+        om, amp, fields = an.discrete_plane_wave((n, n, n), dx, dt, rho, rho * cL ** 2,
+                                                 rho * cS ** 2, kvec, mode)
+        f0 = fields(-0.5 * dt, 0.0)
+        for name in an.FIELDS:
+            s.set_field(name, f0[name])
+        steps = 5
+        s.run(steps)
+        s.synchronize()
+        ex = fields((steps - 0.5) * dt, steps * dt)
+        m = 3 * steps + 3
+        sl = (slice(m, n - m),) * 3
+        for name in an.FIELDS:
+            got = s.field(name).cpu().numpy()[sl]
+            scale = max(abs(amp[f]) for f in an.FIELDS if f[0] == name[0])
+            assert np.abs(got - ex[name][sl]).max() / scale < 2e-5, (mode, name)
+        s.close()
+
+
+def test_gpu_random_state_all_fields(bvf, orc):
+    """Random velocities, stresses and memory variables in a heterogeneous
+    fluid/solid/SLS medium with CPML on a ragged grid (45 x 38 x 29, not a
+    multiple of the 32 x 8 tile): every state array after 12 steps."""
+    nx, ny, nz, dx = 45, 38, 29, 0.5e-3
+    rng = np.random.default_rng(11)
+    mats = [mat_row(1000.0, 1500.0), mat_row(1850.0, 2800.0, 1500.0, 85.0, 170.0),
+            mat_row(1700.0, 2300.0, 1200.0, 81.0, 162.0), mat_row(1041.0, 1562.0, 0.0, 3.45)]
+    index = rng.integers(0, 4, size=(nz // 3 + 1, ny // 3 + 1, nx // 3 + 1))
+    index = np.kron(index, np.ones((3, 3, 3), np.int64))[:nz, :ny, :nx].astype(np.uint8)
+    from paper_2301_12727_gb300 import synth
+    dt, _ = synth.choose_dt(dx, 2800.0, 5e5)
+    s = bvf.Solver(nx, ny, nz, dx, dt, 5e5, n_sls=2, n_pml=5)
+    s.set_materials(index, mats)
+    A = orc.Acoustic(nx, ny, nz, dx, dt, index, mats, 5e5, n_sls=2, n_pml=5)
+    n_state = 9 + 6 * 2
+    init = (rng.standard_normal((n_state, nz, ny, nx)) * np.array(
+        [1.0] * 3 + [1e6] * 6 + [1e4] * 12)[:, None, None, None]).astype(np.float32)
+    d = {f: init[i] for i, f in enumerate(an.FIELDS)}
+    an.zero_ghost_half_points(d)
+    for i in range(n_state):
+        if i < 9:
+            init[i] = d[an.FIELDS[i]]
+        s.set_field(i, init[i])
+        A.state[i] = init[i].astype(np.float64)
+    # memory variables of shear components at ghost half points stay zero too
+    for l in range(2):
+        for c, f in ((3, "sxy"), (4, "sxz"), (5, "syz")):
+            m = (d[f] != 0).astype(np.float32)
+            init[9 + 6 * l + c] *= m
+            s.set_field(9 + 6 * l + c, init[9 + 6 * l + c])
+            A.state[9 + 6 * l + c] = init[9 + 6 * l + c].astype(np.float64)
+    s.run(12)
+    s.synchronize()
+    assert A.run(12) == 0
+    for i in range(n_state):
+        got = s.field(i).cpu().numpy()
+        assert rel_l2(got, A.state[i]) < 2e-5, (i, rel_l2(got, A.state[i]))
+
+
+def test_gpu_slab_config_full(bvf, orc):
+    """64^3, dx 0.5 mm, 400 steps, 3-cycle 500 kHz plane burst onto the
+    cortical/trabecular/cortical slab, 2 SLS, 8-cell CPML: pressure and peak."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.slab_case()
+    s, A = make_pair(bvf, orc, c)
+    s.set_source(c.plane, c.k_src, c.c0, c.envelope, c.n_cycles)
+    A.set_source(c.plane, c.k_src, c.c0, c.envelope, c.n_cycles)
+    s.run(c.n_steps, peak_from=0)
+    s.synchronize()
+    assert A.run(c.n_steps, peak_from=0) == 0
+    e_p = rel_l2(s.pressure().cpu().numpy(), A.pressure())
+    e_pk = rel_l2(s.peak().cpu().numpy(), A.peak)
+    assert e_p < TOL and e_pk < TOL, (e_p, e_pk)
+    # the wave reached and crossed the slab (the check is not vacuous)
+    assert A.peak[40, 32, 32] > 0.1 * A.peak[20, 32, 32]
+
+
+def test_gpu_rs_plane_matches_oracle(bvf, orc):
+    """Rayleigh-Sommerfeld bowl field on a plane (tilted bowl, ragged size)."""
+    import torch
+    nx, ny, dx, f0 = 77, 61, 0.5e-3, 5e5
+    t = math.radians(10.0)
+    bowl = dict(aperture=30e-3, roc=32e-3, apex=(19e-3, 15e-3, -6e-3),
+                dir=(math.sin(t), 0.0, math.cos(t)), p0=6e4)
+    zp = 4e-3
+    got = bvf.rs_plane(bowl, nx, ny, dx, zp, f0).cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    ref = orc.rs_plane(bowl["aperture"], bowl["roc"], bowl["apex"], bowl["dir"], nx, ny, dx, zp,
+                       f0, 1500.0, bowl["p0"])
+    assert rel_l2(np.abs(got), np.abs(ref)) < 2e-5
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 5e-5
+
+
+def test_gpu_skull_bowl_reduced(bvf, orc):
+    """Skull-shaped phantom with a focused bowl (scaled to a 64 x 64 x 56 grid),
+    ramp + CW source from each side's own Rayleigh-Sommerfeld plane, peak map
+    and FP64 amplitude/phase over the last 2 cycles."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(64, 64, 56, dx=0.5e-3, n_steps=8 * 46, aperture=24e-3, roc=22e-3,
+                         dft_cycles=2, n_pml=6, seed=5)
+    s, A = make_pair(bvf, orc, c)
+    b = c.bowl
+    z_plane = c.k_src * c.dx
+    plane_gpu = bvf.rs_plane(b, c.nx, c.ny, c.dx, z_plane, c.f0)
+    s.set_source(plane_gpu, c.k_src, c.c0, c.envelope)
+    plane_ref = orc.rs_plane(b["aperture"], b["roc"], b["apex"], b["dir"], c.nx, c.ny, c.dx,
+                             z_plane, c.f0, c.c0, b["p0"])
+    A.set_source(plane_ref, c.k_src, c.c0, c.envelope)
+    s.run(c.n_steps, peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps)
+    s.synchronize()
+    assert A.run(c.n_steps, peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps) == 0
+    amp_g, ph_g = s.amp_phase()
+    amp_r, ph_r = A.amp_phase(c.dft_steps)
+    assert rel_l2(s.pressure().cpu().numpy(), A.pressure()) < TOL
+    assert rel_l2(s.peak().cpu().numpy(), A.peak) < TOL
+    amp_g = amp_g.cpu().numpy()
+    assert rel_l2(amp_g, amp_r) < TOL
+    # phase where the amplitude is significant
+    sig = amp_r > 0.05 * amp_r.max()
+    dph = np.angle(np.exp(1j * (ph_g.cpu().numpy()[sig] - ph_r[sig])))
+    assert np.abs(dph).max() < 1e-3
+
+
+def test_gpu_thermal_matches_oracle(bvf, orc):
+    """BHTE + CEM43 from an amplitude map on a layered phantom: final T, T_max
+    and CEM43 (FP64 accumulation on the GPU)."""
+    import torch
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(40, 36, 30, dx=0.5e-3, n_steps=10, n_pml=4, seed=9)
+    z, y, x = np.meshgrid(np.arange(c.nz), np.arange(c.ny), np.arange(c.nx), indexing="ij")
+    amp = 1.5e6 * np.exp(-((z - 20) ** 2 / 30.0 + (y - 18) ** 2 / 12.0 + (x - 20) ** 2 / 12.0))
+    dt, n_on, n_off, duty = 0.05, 200, 100, 0.3
+    s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+    s.set_materials(c.index, c.materials)
+    T, Tmax, cem = s.thermal(torch.from_numpy(amp).cuda(), dt, n_on, n_off, duty)
+    torch.cuda.synchronize()
+    rc, Tr, Tmr, cr = orc.bhte_run(c.index, c.materials, c.dx, amp, 1.0, dt, n_on, n_off, duty)
+    assert rc == 0
+    assert Tmr.max() > 40.0        # real heating happened
+    assert rel_l2(T.cpu().numpy() - 37.0, Tr - 37.0) < TOL
+    assert rel_l2(Tmax.cpu().numpy() - 37.0, Tmr - 37.0) < TOL
+    assert rel_l2(cem.cpu().numpy(), cr) < 1e-3
+
+
+def test_gpu_transmission_matches_oracle(bvf, orc):
+    """E_L (Eq. 2) and z_m from the same FP64 maps on both sides."""
+    import torch
+    rng = np.random.default_rng(2)
+    nz, ny, nx = 30, 26, 22
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    amp_w = np.exp(-((z - 17) ** 2 / 20.0 + (y - 12) ** 2 / 9.0 + (x - 10) ** 2 / 9.0))
+    amp_a = amp_w * (0.3 + 0.4 * rng.random(amp_w.shape))
+    idx_a = rng.integers(0, 3, amp_w.shape).astype(np.uint8)
+    idx_w = np.zeros_like(idx_a)
+    ma = [mat_row(1000.0, 1500.0), mat_row(1041.0, 1562.0), mat_row(1116.0, 1537.0)]
+    mw = [mat_row(1000.0, 1500.0)]
+    el_r, zm_r = orc.transmission(idx_a, ma, amp_a, idx_w, mw, amp_w)
+    cu = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    el, ts, zm, iw = bvf.bvf_transmission(cu(idx_a), ma, cu(amp_a), cu(idx_w), mw, cu(amp_w))
+    assert zm == zm_r == 17
+    assert el == pytest.approx(el_r, rel=1e-12)
+    assert ts == pytest.approx(math.sqrt(el_r), rel=1e-12)
+    assert iw == pytest.approx((amp_w ** 2).max() / (2 * 1000.0 * 1500.0), rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# error paths (failures made on the host; nothing faults the GPU)
+# --------------------------------------------------------------------------
+def test_gpu_error_paths(bvf):
+    import torch
+    n, dx = 24, 0.5e-3
+    mats = [mat_row(1000.0, 1500.0), mat_row(1850.0, 2800.0, 1500.0, 85.0, 170.0)]
+    s = bvf.Solver(n, n, n, dx, 0.6 * dx / 2800.0, 5e5, n_sls=2, n_pml=4)
+    with pytest.raises(bvf.BvfError) as e:          # CFL: 0.6 > 6/(7 sqrt 3)
+        s.set_materials(np.zeros((n, n, n), np.uint8), mats)
+    assert e.value.code == bvf.BVF_E_CFL
+    s.close()
+    s = bvf.Solver(n, n, n, dx, 0.2 * dx / 2800.0, 5e5, n_sls=2, n_pml=4)
+    with pytest.raises(bvf.BvfError) as e:          # index beyond the table (device scan)
+        s.set_materials(np.full((n, n, n), 2, np.uint8), mats)
+    assert e.value.code == bvf.BVF_E_MATERIAL
+    with pytest.raises(bvf.BvfError) as e:          # Poisson ratio below -1
+        s.set_materials(np.zeros((n, n, n), np.uint8), [mat_row(1000.0, 1500.0, 1400.0)])
+    assert e.value.code == bvf.BVF_E_MATERIAL
+    with pytest.raises(bvf.BvfError) as e:          # run before materials
+        s.run(1)
+    assert e.value.code == bvf.BVF_E_ARG
+    s.set_materials(np.zeros((n, n, n), np.uint8), mats)
+    bad = np.zeros((n, n, n), np.float32)
+    bad[12, 12, 12] = np.nan                        # non-finite state made on the host
+    s.set_field("sxx", bad)
+    s.run(3)
+    with pytest.raises(bvf.BvfError) as e:
+        s.synchronize()
+    assert e.value.code == bvf.BVF_E_UNSTABLE
+    s.reset()
+    s.run(3)
+    s.synchronize()                                 # reset clears the flag
+    with pytest.raises(bvf.BvfError):
+        s.amp_phase()                               # nothing captured
+    s.close()
+
+
+def test_gpu_run_twice_is_bitwise_identical(bvf):
+    """No atomics on field data: two runs from the same state agree bitwise."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(56, 48, 40, dx=0.5e-3, n_steps=150, aperture=20e-3, roc=20e-3, n_pml=6)
+    outs = []
+    for _ in range(2):
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+        s.set_materials(c.index, c.materials)
+        s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
+                     c.c0, c.envelope)
+        s.run(c.n_steps, peak_from=0, dft_start=51, dft_steps=92)
+        s.synchronize()
+        outs.append((s.pressure().cpu().numpy(), s.peak().cpu().numpy(),
+                     s.amp_phase()[0].cpu().numpy()))
+        s.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
