@@ -137,7 +137,7 @@ def stress_traffic_per_voxel(kernel_src):
 
 
 # --------------------------------------------------------------------------
-def cpu_baseline_oracle(case, budget_s=12.0, max_steps=40):
+def cpu_baseline_oracle(case, budget_s=15.0, max_steps=200):
     """The FP64 oracle as it stands, on this host's cores, over a bounded
     sample of the same workload (the first FDTD steps of the skull run)."""
     import numpy as np
@@ -149,10 +149,15 @@ def cpu_baseline_oracle(case, budget_s=12.0, max_steps=40):
     A = oracle.Acoustic(case.nx, case.ny, case.nz, case.dx, case.dt, case.index, case.materials,
                         case.f0, qc=case.qc, n_sls=case.n_sls, n_pml=case.n_pml, pml_R=case.pml_R)
     A.set_source(plane, case.k_src, case.c0, oracle.ENV_RAMP_CW)
+    # two probes separate the per-call copy overhead from the per-step cost
     t0 = time.perf_counter()
-    assert A.run(2, peak_from=0) == 0
-    t_probe = time.perf_counter() - t0
-    n = max(2, min(max_steps, int(budget_s / max(t_probe / 2, 1e-3))))
+    assert A.run(1, peak_from=0) == 0
+    t1 = time.perf_counter()
+    assert A.run(3, peak_from=0) == 0
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-3) / 2.0
+    overhead = max((t1 - t0) - per_step, 0.0)
+    n = max(2, min(max_steps, int((budget_s - overhead) / per_step)))
     t0 = time.perf_counter()
     assert A.run(n, peak_from=0) == 0
     t = time.perf_counter() - t0
@@ -171,7 +176,7 @@ def run_reference(args):
     times = []
     base = None
     for it in range(args.warmup + args.steps):
-        r = cpu_baseline_oracle(case, budget_s=6.0, max_steps=12)
+        r = cpu_baseline_oracle(case, budget_s=8.0, max_steps=100)
         if it >= args.warmup:
             times.append(r)
         base = r

@@ -1,10 +1,19 @@
 // Acoustic step kernels: velocity update, then stress + SLS memory variables +
 // source + capture (arXiv 2301.12727, Sec. 2.3, Eq. 1; Sec. 3.2, Eq. 3).
 //
-// One thread per voxel, blocks of 32 x 8 (x, y) on one z-plane.  Neighbours
-// are read through the read-only path; points outside the grid read as zero
-// (two ghost layers), and the last half-grid point of each axis is a ghost
-// that is never written.  CPML memories exist only in the edge slabs.
+// Both kernels march along z.  A block of 32 x 8 threads owns one x-y tile and
+// walks a chunk of z-planes; every thread owns one column of the tile:
+//   * the 4-point z-stencils come from per-thread register queues, so each
+//     plane of a z-differenced array is read from memory once;
+//   * the x- and y-stencils of the current plane come from a shared-memory
+//     tile with a 2-cell halo (strips only: the stencils never touch corners),
+//     double-buffered so one barrier per plane suffices;
+//   * the next plane's queue tails and halo values are loaded one iteration
+//     ahead of use.
+// Zero ghosts (points outside the grid) are produced when the tiles and queues
+// are filled, so the arithmetic has no bounds tests.  The last half-grid point
+// of each axis is a ghost that is never written.  CPML memories exist only in
+// the edge slabs.
 #include "bvf_internal.cuh"
 
 namespace bvf {
@@ -13,6 +22,13 @@ namespace {
 
 constexpr float kC1 = 1.125f;            // 9/8
 constexpr float kC2 = -1.0f / 24.0f;     // -1/24
+constexpr int TX = 32, TY = 8, H = 2;
+constexpr int SW = TX + 2 * H;           // tile row length (36)
+constexpr int SH = TY + 2 * H;           // tile rows (12)
+constexpr int TILE = SW * SH;
+constexpr int NTH = TX * TY;
+constexpr int NX_HALO = 4 * TY;          // x-strips: 2 columns each side of the TY rows
+constexpr int NHALO = NX_HALO + 4 * TX;  // + y-strips: 2 rows above and below the TX columns
 
 // D+ : integer-point field -> derivative at s + 1/2
 __device__ __forceinline__ float dfw(float fm1, float f0, float f1, float f2, float ix)
@@ -25,12 +41,20 @@ __device__ __forceinline__ float dbw(float fm2, float fm1, float f0, float f1, f
     return fmaf(kC2, f1 - fm2, kC1 * (f0 - fm1)) * ix;
 }
 
-// zero-ghost load of f at linear index q + d * stride, coordinate c + d in [0, n)
-__device__ __forceinline__ float ldg0(const float *__restrict__ f, long long q, int c, int d,
-                                      int n, long long stride)
+// Tile coordinates (hx, hy) of halo element t: t < NX_HALO are the x-strips,
+// the rest the y-strips.
+__device__ __forceinline__ void halo_coord(int t, int &hx, int &hy)
 {
-    int cc = c + d;
-    return (cc >= 0 && cc < n) ? __ldg(f + q + (long long)d * stride) : 0.0f;
+    if (t < NX_HALO) {
+        const int r = t >> 2, c = t & 3;
+        hy = H + r;
+        hx = (c < 2) ? c : TX + c;
+    } else {
+        t -= NX_HALO;
+        const int r = t / TX, c = t % TX;
+        hx = H + c;
+        hy = (r < 2) ? r : TY + r;
+    }
 }
 
 // position of coordinate c in its axis' CPML slab (-1 outside):
@@ -46,213 +70,384 @@ __device__ __forceinline__ int slab_pos(int c, int n, int P)
 // CPML recursion psi <- b psi + a d; the derivative used is d + psi.
 __device__ __forceinline__ float cpml(float *__restrict__ psi, float2 ab, float d)
 {
-    float v = fmaf(ab.x, d, ab.y * *psi);
+    const float v = fmaf(ab.x, d, ab.y * *psi);
     *psi = v;
     return d + v;
 }
 
-__global__ void __launch_bounds__(256) k_velocity(AcParams p)
-{
-    extern __shared__ float s_rho[];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int m = tid; m < p.n_mat; m += blockDim.x * blockDim.y) s_rho[m] = p.lut[m].rho;
-    __syncthreads();
+struct Geo {
+    int nx, ny, nz;
+    long long SZ;
+    int i, j, tx, ty, tid;
+    bool live;
+    long long col;      // j*nx + i
+    bool hal, hin;      // this thread fills a halo element / it lies inside the grid
+    int hslot;          // its index in the tile
+    bool hxstrip;       // the element belongs to an x-strip
+    long long hcol;     // its gy*nx + gx
+};
 
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+__device__ __forceinline__ Geo make_geo(int nx, int ny, int nz)
+{
+    Geo g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.SZ = (long long)nx * ny;
+    g.tx = threadIdx.x;
+    g.ty = threadIdx.y;
+    g.tid = g.ty * TX + g.tx;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    g.i = x0 + g.tx;
+    g.j = y0 + g.ty;
+    g.live = g.i < nx && g.j < ny;
+    g.col = (long long)g.j * nx + g.i;
+    g.hal = g.tid < NHALO;
+    int hx = 0, hy = 0;
+    if (g.hal) halo_coord(g.tid, hx, hy);
+    g.hxstrip = g.tid < NX_HALO;
+    const int gx = x0 - H + hx, gy = y0 - H + hy;
+    g.hin = g.hal && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+    g.hslot = hy * SW + hx;
+    g.hcol = (long long)gy * nx + gx;
+    return g;
+}
+
+// column value f(i, j, k), zero outside the grid
+__device__ __forceinline__ float colv(const float *__restrict__ f, const Geo &g, int k)
+{
+    return (g.live && k >= 0 && k < g.nz) ? __ldg(f + k * g.SZ + g.col) : 0.0f;
+}
+// halo value of this thread's halo element at plane k, zero outside the grid
+__device__ __forceinline__ float halv(const float *__restrict__ f, const Geo &g, int k, bool want)
+{
+    return (want && g.hin && k >= 0 && k < g.nz) ? __ldg(f + k * g.SZ + g.hcol) : 0.0f;
+}
+
+__global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
+{
+    extern __shared__ __align__(16) float sm_v[];
+    float *s_rho = sm_v;                               // n_mat (rounded to 4)
+    float *tiles = sm_v + ((p.n_mat + 3) & ~3);        // [2 buffers][5 arrays][TILE]
+    const Geo g = make_geo(p.nx, p.ny, p.nz);
+    for (int m = g.tid; m < p.n_mat; m += NTH) s_rho[m] = p.lut[m].rho;
+
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    if (i >= nx || j >= ny) return;
-    const long long SX = 1, SY = nx, SZ = (long long)nx * ny;
-    const long long q = k * SZ + j * SY + i;
+    const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
     const float ix = p.inv_dx, dt = p.dt;
-    const float rho0 = s_rho[p.idx[q]];
-    const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P), zs = slab_pos(k, nz, p.P);
+    const int c = (g.ty + H) * SW + (g.tx + H);
+    const int xs = slab_pos(g.i, nx, p.P), ys = slab_pos(g.j, ny, p.P);
     const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
                     Szs = (long long)p.W * ny * nx;
-    const long long qx = ((long long)k * ny + j) * p.W + xs;
-    const long long qy = ((long long)k * p.W + ys) * nx + i;
-    const long long qz = ((long long)zs * ny + j) * nx + i;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
+    const bool hx_ = g.hxstrip, hy_ = !g.hxstrip;
+    const uint8_t *__restrict__ idx = p.idx;
+    float *__restrict__ vx = p.vx;
+    float *__restrict__ vy = p.vy;
+    float *__restrict__ vz = p.vz;
 
-#define LX(f, d) ldg0(f, q, i, d, nx, SX)
-#define LY(f, d) ldg0(f, q, j, d, ny, SY)
-#define LZ(f, d) ldg0(f, q, k, d, nz, SZ)
-    if (i < nx - 1) {
-        const float b = 2.0f / (rho0 + s_rho[p.idx[q + SX]]);
-        float d1 = dfw(LX(p.sxx, -1), LX(p.sxx, 0), LX(p.sxx, 1), LX(p.sxx, 2), ix);
-        float d2 = dbw(LY(p.sxy, -2), LY(p.sxy, -1), LY(p.sxy, 0), LY(p.sxy, 1), ix);
-        float d3 = dbw(LZ(p.sxz, -2), LZ(p.sxz, -1), LZ(p.sxz, 0), LZ(p.sxz, 1), ix);
-        if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + qx, pmlx[p.nmax + i], d1);
-        if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + qy, pmly[j], d2);
-        if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + qz, pmlz[k], d3);
-        p.vx[q] += dt * b * (d1 + d2 + d3);
-    }
-    if (j < ny - 1) {
-        const float b = 2.0f / (rho0 + s_rho[p.idx[q + SY]]);
-        float d1 = dbw(LX(p.sxy, -2), LX(p.sxy, -1), LX(p.sxy, 0), LX(p.sxy, 1), ix);
-        float d2 = dfw(LY(p.syy, -1), LY(p.syy, 0), LY(p.syy, 1), LY(p.syy, 2), ix);
-        float d3 = dbw(LZ(p.syz, -2), LZ(p.syz, -1), LZ(p.syz, 0), LZ(p.syz, 1), ix);
-        if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + qx, pmlx[i], d1);
-        if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + qy, pmly[p.nmax + j], d2);
-        if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + qz, pmlz[k], d3);
-        p.vy[q] += dt * b * (d1 + d2 + d3);
-    }
-    if (k < nz - 1) {
-        const float b = 2.0f / (rho0 + s_rho[p.idx[q + SZ]]);
-        float d1 = dbw(LX(p.sxz, -2), LX(p.sxz, -1), LX(p.sxz, 0), LX(p.sxz, 1), ix);
-        float d2 = dbw(LY(p.syz, -2), LY(p.syz, -1), LY(p.syz, 0), LY(p.syz, 1), ix);
-        float d3 = dfw(LZ(p.szz, -1), LZ(p.szz, 0), LZ(p.szz, 1), LZ(p.szz, 2), ix);
-        if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + qx, pmlx[i], d1);
-        if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + qy, pmly[j], d2);
-        if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + qz, pmlz[p.nmax + k], d3);
-        p.vz[q] += dt * b * (d1 + d2 + d3);
+    // z-queues: sxz, syz at k-2 .. k+1 ; szz at k-1 .. k+2
+    float bz0 = colv(p.sxz, g, k0 - 2), bz1 = colv(p.sxz, g, k0 - 1);
+    float bz2 = colv(p.sxz, g, k0), bz3 = colv(p.sxz, g, k0 + 1);
+    float cz0 = colv(p.syz, g, k0 - 2), cz1 = colv(p.syz, g, k0 - 1);
+    float cz2 = colv(p.syz, g, k0), cz3 = colv(p.syz, g, k0 + 1);
+    float dz0 = colv(p.szz, g, k0 - 1), dz1 = colv(p.szz, g, k0);
+    float dz2 = colv(p.szz, g, k0 + 1), dz3 = colv(p.szz, g, k0 + 2);
+    // plane-k centres of the x/y-differenced arrays and this thread's halo values
+    float cxx = colv(p.sxx, g, k0), cyy = colv(p.syy, g, k0), cxy = colv(p.sxy, g, k0);
+    float hxx = halv(p.sxx, g, k0, hx_), hyy = halv(p.syy, g, k0, hy_);
+    float hxy = halv(p.sxy, g, k0, true), hxz = halv(p.sxz, g, k0, hx_);
+    float hyz = halv(p.syz, g, k0, hy_);
+    __syncthreads();
+
+    for (int k = k0; k < k1; ++k) {
+        float *t = tiles + (k & 1) * 5 * TILE;
+        float *txx = t, *tyy = t + TILE, *txy = t + 2 * TILE, *txz = t + 3 * TILE, *tyz = t + 4 * TILE;
+        txx[c] = cxx; tyy[c] = cyy; txy[c] = cxy; txz[c] = bz2; tyz[c] = cz2;
+        if (g.hal) {
+            txx[g.hslot] = hxx; tyy[g.hslot] = hyy; txy[g.hslot] = hxy;
+            txz[g.hslot] = hxz; tyz[g.hslot] = hyz;
+        }
+        __syncthreads();
+        // loads for plane k+1, consumed in the next iteration
+        const float nbz = colv(p.sxz, g, k + 2), ncz = colv(p.syz, g, k + 2);
+        const float ndz = colv(p.szz, g, k + 3);
+        const float nxx = colv(p.sxx, g, k + 1), nyy = colv(p.syy, g, k + 1);
+        const float nxy = colv(p.sxy, g, k + 1);
+        const float nhxx = halv(p.sxx, g, k + 1, hx_), nhyy = halv(p.syy, g, k + 1, hy_);
+        const float nhxy = halv(p.sxy, g, k + 1, true), nhxz = halv(p.sxz, g, k + 1, hx_);
+        const float nhyz = halv(p.syz, g, k + 1, hy_);
+
+        if (g.live) {
+            const long long q = k * g.SZ + g.col;
+            const int zs = slab_pos(k, nz, p.P);
+            const long long qx = ((long long)k * ny + g.j) * p.W + xs;
+            const long long qy = ((long long)k * p.W + ys) * nx + g.i;
+            const long long qz = ((long long)zs * ny + g.j) * nx + g.i;
+            const bool ix1 = g.i < nx - 1, jy1 = g.j < ny - 1, kz1 = k < nz - 1;
+            // every global load of this voxel first
+            const int m0 = __ldg(idx + q), mx = __ldg(idx + q + (ix1 ? 1 : 0));
+            const int my = __ldg(idx + q + (jy1 ? nx : 0)), mz = __ldg(idx + q + (kz1 ? g.SZ : 0));
+            float ux = vx[q], uy = vy[q], uz = vz[q];
+            const float rho0 = s_rho[m0];
+            if (ix1) {
+                const float b = 2.0f / (rho0 + s_rho[mx]);
+                float d1 = dfw(txx[c - 1], txx[c], txx[c + 1], txx[c + 2], ix);
+                float d2 = dbw(txy[c - 2 * SW], txy[c - SW], txy[c], txy[c + SW], ix);
+                float d3 = dbw(bz0, bz1, bz2, bz3, ix);
+                if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + qx, pmlx[p.nmax + g.i], d1);
+                if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + qy, pmly[g.j], d2);
+                if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + qz, pmlz[k], d3);
+                ux += dt * b * (d1 + d2 + d3);
+                vx[q] = ux;
+            }
+            if (jy1) {
+                const float b = 2.0f / (rho0 + s_rho[my]);
+                float d1 = dbw(txy[c - 2], txy[c - 1], txy[c], txy[c + 1], ix);
+                float d2 = dfw(tyy[c - SW], tyy[c], tyy[c + SW], tyy[c + 2 * SW], ix);
+                float d3 = dbw(cz0, cz1, cz2, cz3, ix);
+                if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + qx, pmlx[g.i], d1);
+                if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + qy, pmly[p.nmax + g.j], d2);
+                if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + qz, pmlz[k], d3);
+                uy += dt * b * (d1 + d2 + d3);
+                vy[q] = uy;
+            }
+            if (kz1) {
+                const float b = 2.0f / (rho0 + s_rho[mz]);
+                float d1 = dbw(txz[c - 2], txz[c - 1], txz[c], txz[c + 1], ix);
+                float d2 = dbw(tyz[c - 2 * SW], tyz[c - SW], tyz[c], tyz[c + SW], ix);
+                float d3 = dfw(dz0, dz1, dz2, dz3, ix);
+                if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + qx, pmlx[g.i], d1);
+                if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + qy, pmly[g.j], d2);
+                if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + qz, pmlz[p.nmax + k], d3);
+                uz += dt * b * (d1 + d2 + d3);
+                vz[q] = uz;
+            }
+        }
+        bz0 = bz1; bz1 = bz2; bz2 = bz3; bz3 = nbz;
+        cz0 = cz1; cz1 = cz2; cz2 = cz3; cz3 = ncz;
+        dz0 = dz1; dz1 = dz2; dz2 = dz3; dz3 = ndz;
+        cxx = nxx; cyy = nyy; cxy = nxy;
+        hxx = nhxx; hyy = nhyy; hxy = nhxy; hxz = nhxz; hyz = nhyz;
     }
 }
 
-// Memory-variable update of one stress component (Crank-Nicolson):
-// r_l <- ca_l r_l - cb_l Theta ; returns sum_l (r_l^{n+1} + r_l^n).
+// Memory-variable update of one stress component (Crank-Nicolson), on the
+// registers of this voxel: r_l <- ca_l r_l - cb_l Theta ; returns
+// sum_l (r_l^{n+1} + r_l^n).
 template <int L>
-__device__ __forceinline__ float sls_update(const AcParams &p, long long q, int c, float The)
+__device__ __forceinline__ float sls_update(const AcParams &p, float (&rv)[L > 0 ? L : 1][6],
+                                            int c, float The)
 {
     float sum = 0.0f;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        float *r = p.mem + (size_t)(l * 6 + c) * p.fstride + q;
-        float r0 = *r;
-        float rn = p.ca[l] * r0 - p.cb[l] * The;
+        const float r0 = rv[l][c];
+        const float rn = p.ca[l] * r0 - p.cb[l] * The;
         sum += rn + r0;
-        *r = rn;
+        rv[l][c] = rn;
     }
     return sum;
 }
 
 template <int L>
-__global__ void __launch_bounds__(256) k_stress(AcParams p)
+__global__ void __launch_bounds__(NTH, 3) k_stress(AcParams p, int kchunk)
 {
-    extern __shared__ MatCoef s_lut[];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int m = tid; m < p.n_mat; m += blockDim.x * blockDim.y) s_lut[m] = p.lut[m];
-    __syncthreads();
+    extern __shared__ __align__(16) float sm_s[];
+    MatCoef *s_lut = reinterpret_cast<MatCoef *>(sm_s);
+    float *tiles = sm_s + p.n_mat * (sizeof(MatCoef) / sizeof(float));   // [2][3][TILE]
+    const Geo g = make_geo(p.nx, p.ny, p.nz);
+    for (int m = g.tid; m < p.n_mat; m += NTH) s_lut[m] = p.lut[m];
 
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    if (i >= nx || j >= ny) return;
-    const long long SX = 1, SY = nx, SZ = (long long)nx * ny;
-    const long long q = k * SZ + j * SY + i;
+    const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
     const float ix = p.inv_dx, dt = p.dt;
-    const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P), zs = slab_pos(k, nz, p.P);
+    const int c = (g.ty + H) * SW + (g.tx + H);
+    const int xs = slab_pos(g.i, nx, p.P), ys = slab_pos(g.j, ny, p.P);
     const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
                     Szs = (long long)p.W * ny * nx;
-    const long long qx = ((long long)k * ny + j) * p.W + xs;
-    const long long qy = ((long long)k * p.W + ys) * nx + i;
-    const long long qz = ((long long)zs * ny + j) * nx + i;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
-    const int m00 = p.idx[q];
-    const MatCoef c0 = s_lut[m00];
+    const uint8_t *__restrict__ idx = p.idx;
+    float *__restrict__ mem = p.mem;
+    float *__restrict__ peak = p.peak;
+    float *const sig[6] = {p.sxx, p.syy, p.szz, p.sxy, p.sxz, p.syz};
 
-    // ---- normal stresses at (i, j, k)
-    float exx = dbw(LX(p.vx, -2), LX(p.vx, -1), LX(p.vx, 0), LX(p.vx, 1), ix);
-    float eyy = dbw(LY(p.vy, -2), LY(p.vy, -1), LY(p.vy, 0), LY(p.vy, 1), ix);
-    float ezz = dbw(LZ(p.vz, -2), LZ(p.vz, -1), LZ(p.vz, 0), LZ(p.vz, 1), ix);
-    if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + qx, pmlx[i], exx);
-    if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + qy, pmly[j], eyy);
-    if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + qz, pmlz[k], ezz);
-    const float th = exx + eyy + ezz;
+    // z-queues: vx, vy at k-1 .. k+2 ; vz at k-2 .. k+1
+    float ax0 = colv(p.vx, g, k0 - 1), ax1 = colv(p.vx, g, k0);
+    float ax2 = colv(p.vx, g, k0 + 1), ax3 = colv(p.vx, g, k0 + 2);
+    float ay0 = colv(p.vy, g, k0 - 1), ay1 = colv(p.vy, g, k0);
+    float ay2 = colv(p.vy, g, k0 + 1), ay3 = colv(p.vy, g, k0 + 2);
+    float az0 = colv(p.vz, g, k0 - 2), az1 = colv(p.vz, g, k0 - 1);
+    float az2 = colv(p.vz, g, k0), az3 = colv(p.vz, g, k0 + 1);
+    float hvx = halv(p.vx, g, k0, true), hvy = halv(p.vy, g, k0, true);
+    float hvz = halv(p.vz, g, k0, true);
+    __syncthreads();
 
-    float srcv = 0.0f;
-    if (p.src_on && k == p.k_src) {
-        const float2 a = p.src[(long long)j * nx + i];
-        srcv = p.src_scale * fmaf(a.x, p.src_ws, a.y * p.src_wc);
-    }
-    float snew[3];
-    const float ev[3] = {exx, eyy, ezz};
-    float *sig[3] = {p.sxx, p.syy, p.szz};
+    for (int k = k0; k < k1; ++k) {
+        float *t = tiles + (k & 1) * 3 * TILE;
+        float *tvx = t, *tvy = t + TILE, *tvz = t + 2 * TILE;
+        tvx[c] = ax1; tvy[c] = ay1; tvz[c] = az2;
+        if (g.hal) { tvx[g.hslot] = hvx; tvy[g.hslot] = hvy; tvz[g.hslot] = hvz; }
+        __syncthreads();
+        const float nax = colv(p.vx, g, k + 3), nay = colv(p.vy, g, k + 3);
+        const float naz = colv(p.vz, g, k + 2);
+        const float nhx = halv(p.vx, g, k + 1, true), nhy = halv(p.vy, g, k + 1, true);
+        const float nhz = halv(p.vz, g, k + 1, true);
+
+        if (g.live) {
+            const long long q = k * g.SZ + g.col;
+            const int zs = slab_pos(k, nz, p.P);
+            const long long qx = ((long long)k * ny + g.j) * p.W + xs;
+            const long long qy = ((long long)k * p.W + ys) * nx + g.i;
+            const long long qz = ((long long)zs * ny + g.j) * nx + g.i;
+            // ---- every global load of this voxel first (independent, in flight together)
+            const bool ix1 = g.i < nx - 1, jy1 = g.j < ny - 1, kz1 = k < nz - 1;
+            const long long o1 = ix1 ? 1 : 0, oy = jy1 ? nx : 0, oz = kz1 ? g.SZ : 0;
+            const int m00 = __ldg(idx + q), m10 = __ldg(idx + q + o1);
+            const int m01 = __ldg(idx + q + oy), m11 = __ldg(idx + q + o1 + oy);
+            const int mz0 = __ldg(idx + q + oz), mz1 = __ldg(idx + q + o1 + oz);
+            const int mzy = __ldg(idx + q + oy + oz);
+            float sv[6], rv[L > 0 ? L : 1][6];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float dev = th - ev[c];
-        const float Psi = c0.piU * th - c0.mu2U * dev;
-        const float The = c0.piT * th - c0.mu2T * dev;
-        const float sum = sls_update<L>(p, q, c, The);
-        float s = sig[c][q] + dt * (Psi + 0.5f * sum);
-        s -= srcv;
-        sig[c][q] = s;
-        snew[c] = s;
-    }
+            for (int cc = 0; cc < 6; ++cc) sv[cc] = sig[cc][q];
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) rv[l][cc] = mem[(size_t)(l * 6 + cc) * p.fstride + q];
+            const float pk = p.do_peak ? peak[q] : 0.0f;
+            double dC = 0.0, dS = 0.0;
+            if (p.do_dft) { dC = p.dftC[q]; dS = p.dftS[q]; }
+            const MatCoef c0 = s_lut[m00];
 
-    // ---- capture: p = -(sxx + syy + szz) / 3
-    const float pr = -(snew[0] + snew[1] + snew[2]) / 3.0f;
-    if (!isfinite(pr)) atomicOr(p.flag, 1);
-    if (p.do_peak) p.peak[q] = fmaxf(p.peak[q], fabsf(pr));
-    if (p.do_dft) {
-        p.dftC[q] += (double)pr * p.cw;
-        p.dftS[q] += (double)pr * p.sw;
-    }
+            // ---- normal stresses at (i, j, k)
+            float exx = dbw(tvx[c - 2], tvx[c - 1], tvx[c], tvx[c + 1], ix);
+            float eyy = dbw(tvy[c - 2 * SW], tvy[c - SW], tvy[c], tvy[c + SW], ix);
+            float ezz = dbw(az0, az1, az2, az3, ix);
+            if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + qx, pmlx[g.i], exx);
+            if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + qy, pmly[g.j], eyy);
+            if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + qz, pmlz[k], ezz);
+            const float th = exx + eyy + ezz;
 
-    // ---- shear stresses: harmonic-mean mu and mean tau_S of the four cells
-    // (pairs along the first axis summed first, to keep mirror symmetry)
-    auto shear = [&](float *s, int c, long long o1, long long o2, float e) {
-        const MatCoef a = s_lut[m00], b = s_lut[p.idx[q + o1]];
-        const MatCoef cc = s_lut[p.idx[q + o2]], d = s_lut[p.idx[q + o1 + o2]];
-        const float muh = 4.0f / ((a.inv_mu + b.inv_mu) + (cc.inv_mu + d.inv_mu));
-        const float tsh = 0.25f * ((a.tauS + b.tauS) + (cc.tauS + d.tauS));
-        const float Psi = muh * (1.0f + p.Lf * tsh) * e;
-        const float The = muh * tsh * e;
-        const float sum = sls_update<L>(p, q, c, The);
-        s[q] += dt * (Psi + 0.5f * sum);
-    };
-    if (i < nx - 1 && j < ny - 1) {     // sxy at (i+1/2, j+1/2, k)
-        float a = dfw(LY(p.vx, -1), LY(p.vx, 0), LY(p.vx, 1), LY(p.vx, 2), ix);
-        float b = dfw(LX(p.vy, -1), LX(p.vy, 0), LX(p.vy, 1), LX(p.vy, 2), ix);
-        if (ys >= 0) a = cpml(p.psy + 4 * Sys + qy, pmly[p.nmax + j], a);
-        if (xs >= 0) b = cpml(p.psx + 4 * Sxs + qx, pmlx[p.nmax + i], b);
-        shear(p.sxy, 3, SX, SY, a + b);
+            float srcv = 0.0f;
+            if (p.src_on && k == p.k_src) {
+                const float2 a = p.src[g.col];
+                srcv = p.src_scale * fmaf(a.x, p.src_ws, a.y * p.src_wc);
+            }
+            const float ev[3] = {exx, eyy, ezz};
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const float dev = th - ev[cc];
+                const float Psi = c0.piU * th - c0.mu2U * dev;
+                const float The = c0.piT * th - c0.mu2T * dev;
+                const float sum = sls_update<L>(p, rv, cc, The);
+                float s = sv[cc] + dt * (Psi + 0.5f * sum);
+                s -= srcv;
+                sv[cc] = s;
+            }
+
+            // ---- capture: p = -(sxx + syy + szz) / 3
+            const float pr = -(sv[0] + sv[1] + sv[2]) / 3.0f;
+            if (!isfinite(pr)) atomicOr(p.flag, 1);
+
+            // ---- shear stresses: harmonic-mean mu and mean tau_S of the four
+            // cells (pairs along the first axis summed first: mirror symmetry)
+            auto shear = [&](int cc, int mb, int md, int mf, float e) {
+                const MatCoef a = c0, b = s_lut[mb], d = s_lut[md], f = s_lut[mf];
+                const float muh = 4.0f / ((a.inv_mu + b.inv_mu) + (d.inv_mu + f.inv_mu));
+                const float tsh = 0.25f * ((a.tauS + b.tauS) + (d.tauS + f.tauS));
+                const float Psi = muh * (1.0f + p.Lf * tsh) * e;
+                const float The = muh * tsh * e;
+                const float sum = sls_update<L>(p, rv, cc, The);
+                sv[cc] += dt * (Psi + 0.5f * sum);
+            };
+            const bool dxy = ix1 && jy1, dxz = ix1 && kz1, dyz = jy1 && kz1;
+            if (dxy) {                               // sxy at (i+1/2, j+1/2, k)
+                float a = dfw(tvx[c - SW], tvx[c], tvx[c + SW], tvx[c + 2 * SW], ix);
+                float b = dfw(tvy[c - 1], tvy[c], tvy[c + 1], tvy[c + 2], ix);
+                if (ys >= 0) a = cpml(p.psy + 4 * Sys + qy, pmly[p.nmax + g.j], a);
+                if (xs >= 0) b = cpml(p.psx + 4 * Sxs + qx, pmlx[p.nmax + g.i], b);
+                shear(3, m10, m01, m11, a + b);
+            }
+            if (dxz) {                               // sxz at (i+1/2, j, k+1/2)
+                float a = dfw(ax0, ax1, ax2, ax3, ix);
+                float b = dfw(tvz[c - 1], tvz[c], tvz[c + 1], tvz[c + 2], ix);
+                if (zs >= 0) a = cpml(p.psz + 4 * Szs + qz, pmlz[p.nmax + k], a);
+                if (xs >= 0) b = cpml(p.psx + 5 * Sxs + qx, pmlx[p.nmax + g.i], b);
+                shear(4, m10, mz0, mz1, a + b);
+            }
+            if (dyz) {                               // syz at (i, j+1/2, k+1/2)
+                float a = dfw(ay0, ay1, ay2, ay3, ix);
+                float b = dfw(tvz[c - SW], tvz[c], tvz[c + SW], tvz[c + 2 * SW], ix);
+                if (zs >= 0) a = cpml(p.psz + 5 * Szs + qz, pmlz[p.nmax + k], a);
+                if (ys >= 0) b = cpml(p.psy + 5 * Sys + qy, pmly[p.nmax + g.j], b);
+                shear(5, m01, mz0, mzy, a + b);
+            }
+
+            // ---- stores
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) sig[cc][q] = sv[cc];
+            if (dxy) sig[3][q] = sv[3];
+            if (dxz) sig[4][q] = sv[4];
+            if (dyz) sig[5][q] = sv[5];
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) {
+                    const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
+                    if (w) mem[(size_t)(l * 6 + cc) * p.fstride + q] = rv[l][cc];
+                }
+            if (p.do_peak) peak[q] = fmaxf(pk, fabsf(pr));
+            if (p.do_dft) {
+                p.dftC[q] = fma((double)pr, p.cw, dC);
+                p.dftS[q] = fma((double)pr, p.sw, dS);
+            }
+        }
+        ax0 = ax1; ax1 = ax2; ax2 = ax3; ax3 = nax;
+        ay0 = ay1; ay1 = ay2; ay2 = ay3; ay3 = nay;
+        az0 = az1; az1 = az2; az2 = az3; az3 = naz;
+        hvx = nhx; hvy = nhy; hvz = nhz;
     }
-    if (i < nx - 1 && k < nz - 1) {     // sxz at (i+1/2, j, k+1/2)
-        float a = dfw(LZ(p.vx, -1), LZ(p.vx, 0), LZ(p.vx, 1), LZ(p.vx, 2), ix);
-        float b = dfw(LX(p.vz, -1), LX(p.vz, 0), LX(p.vz, 1), LX(p.vz, 2), ix);
-        if (zs >= 0) a = cpml(p.psz + 4 * Szs + qz, pmlz[p.nmax + k], a);
-        if (xs >= 0) b = cpml(p.psx + 5 * Sxs + qx, pmlx[p.nmax + i], b);
-        shear(p.sxz, 4, SX, SZ, a + b);
-    }
-    if (j < ny - 1 && k < nz - 1) {     // syz at (i, j+1/2, k+1/2)
-        float a = dfw(LZ(p.vy, -1), LZ(p.vy, 0), LZ(p.vy, 1), LZ(p.vy, 2), ix);
-        float b = dfw(LY(p.vz, -1), LY(p.vz, 0), LY(p.vz, 1), LY(p.vz, 2), ix);
-        if (zs >= 0) a = cpml(p.psz + 5 * Szs + qz, pmlz[p.nmax + k], a);
-        if (ys >= 0) b = cpml(p.psy + 5 * Sys + qy, pmly[p.nmax + j], b);
-        shear(p.syz, 5, SY, SZ, a + b);
-    }
-#undef LX
-#undef LY
-#undef LZ
 }
 
 }  // namespace
 
-static dim3 grid_of(const AcParams &p, dim3 blk)
+// z-chunk length: about two waves of four resident blocks per SM on 152 SMs,
+// at least 8 planes per chunk (queue start-up costs 3 planes).
+int default_kchunk(int nx, int ny, int nz)
 {
-    return dim3((p.nx + blk.x - 1) / blk.x, (p.ny + blk.y - 1) / blk.y, p.nz);
+    const long long tiles = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    const long long target = 152LL * 4 * 2;
+    long long chunks = (target + tiles - 1) / tiles;
+    if (chunks < 1) chunks = 1;
+    int kc = (int)((nz + chunks - 1) / chunks);
+    if (kc < 8) kc = 8;
+    return kc > nz ? nz : kc;
+}
+
+static dim3 grid_of(const AcParams &p, int kchunk)
+{
+    return dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + kchunk - 1) / kchunk);
 }
 
 cudaError_t launch_velocity(const AcParams &p, cudaStream_t s)
 {
-    dim3 blk(32, 8, 1);
-    k_velocity<<<grid_of(p, blk), blk, p.n_mat * sizeof(float), s>>>(p);
+    const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk(p.nx, p.ny, p.nz);
+    const size_t sm = ((p.n_mat + 3) & ~3) * sizeof(float) + 2 * 5 * TILE * sizeof(float);
+    k_velocity<<<grid_of(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stress(const AcParams &p, cudaStream_t s)
 {
-    dim3 blk(32, 8, 1);
-    size_t sm = p.n_mat * sizeof(MatCoef);
+    const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk(p.nx, p.ny, p.nz);
+    const size_t sm = p.n_mat * sizeof(MatCoef) + 2 * 3 * TILE * sizeof(float);
+    const dim3 grd = grid_of(p, kc), blk(TX, TY, 1);
     switch (p.L) {
-    case 0: k_stress<0><<<grid_of(p, blk), blk, sm, s>>>(p); break;
-    case 1: k_stress<1><<<grid_of(p, blk), blk, sm, s>>>(p); break;
-    case 2: k_stress<2><<<grid_of(p, blk), blk, sm, s>>>(p); break;
-    case 3: k_stress<3><<<grid_of(p, blk), blk, sm, s>>>(p); break;
-    case 4: k_stress<4><<<grid_of(p, blk), blk, sm, s>>>(p); break;
+    case 0: k_stress<0><<<grd, blk, sm, s>>>(p, kc); break;
+    case 1: k_stress<1><<<grd, blk, sm, s>>>(p, kc); break;
+    case 2: k_stress<2><<<grd, blk, sm, s>>>(p, kc); break;
+    case 3: k_stress<3><<<grd, blk, sm, s>>>(p, kc); break;
+    case 4: k_stress<4><<<grd, blk, sm, s>>>(p, kc); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -61,6 +62,7 @@ struct bvf_ctx {
     bool have_source = false;
     long long steps = 0, launches = 0, thermal_steps = 0;
     double courant = 0.0;
+    int kchunk = 0;                   // z-planes per block (0 = default)
     std::string err;
     // per-launch event timing of the acoustic kernels
     bool timing = false;
@@ -242,6 +244,7 @@ AcParams make_params(bvf_ctx *c)
     p.dftC = c->dftC;
     p.dftS = c->dftS;
     p.flag = c->flag;
+    p.kchunk = c->kchunk;
     return p;
 }
 
@@ -314,6 +317,7 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
     c->slab_y = (size_t)g.nz * c->W * g.nx;
     c->slab_z = (size_t)c->W * g.ny * g.nx;
     c->tau_sigma = relaxation_times(phys->f0, c->L);
+    if (const char *kc = std::getenv("BVF_KCHUNK")) c->kchunk = std::max(0, std::atoi(kc));
 
     auto cleanup = [&](int code) { bvf_destroy(c); return code; };
     cudaError_t e;

@@ -62,6 +62,7 @@ struct AcParams {
     int do_dft;
     double cw, sw;
     int *flag;
+    int kchunk;          // z-planes per block (0 = default_kchunk)
 };
 
 struct ThParams {
@@ -76,6 +77,9 @@ struct ThParams {
     float *Tmax;
     double *cem;
 };
+
+// z-planes per block of the z-marching acoustic kernels for a grid
+int default_kchunk(int nx, int ny, int nz);
 
 // kernel launchers (bvf_acoustic.cu / bvf_aux.cu); return cudaGetLastError()
 cudaError_t launch_velocity(const AcParams &p, cudaStream_t s);
