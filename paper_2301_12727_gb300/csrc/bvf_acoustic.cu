@@ -1,5 +1,7 @@
-// Acoustic step kernels: velocity update, then stress + SLS memory variables +
-// source + capture (arXiv 2301.12727, Sec. 2.3, Eq. 1; Sec. 3.2, Eq. 3).
+// Direct acoustic step kernels (any grid shape, any L): velocity update, then
+// stress + SLS memory variables + source + capture (arXiv 2301.12727,
+// Sec. 2.3, Eq. 1; Sec. 3.2, Eq. 3).  Grids whose rows suit the TMA use the
+// kernels of bvf_acoustic_tma.cu instead.
 //
 // Both kernels march along z.  A block of 32 x 8 threads owns one x-y tile and
 // walks a chunk of z-planes; every thread owns one column of the tile:
@@ -14,14 +16,17 @@
 // are filled, so the arithmetic has no bounds tests.  The last half-grid point
 // of each axis is a ghost that is never written.  CPML memories exist only in
 // the edge slabs.
-#include "bvf_internal.cuh"
+#include "bvf_stencil.cuh"
 
 namespace bvf {
 
 namespace {
 
-constexpr float kC1 = 1.125f;            // 9/8
-constexpr float kC2 = -1.0f / 24.0f;     // -1/24
+using st::dbw;
+using st::dfw;
+using st::cpml;
+using st::slab_pos;
+
 constexpr int TX = 32, TY = 8, H = 2;
 constexpr int SW = TX + 2 * H;           // tile row length (36)
 constexpr int SH = TY + 2 * H;           // tile rows (12)
@@ -29,17 +34,6 @@ constexpr int TILE = SW * SH;
 constexpr int NTH = TX * TY;
 constexpr int NX_HALO = 4 * TY;          // x-strips: 2 columns each side of the TY rows
 constexpr int NHALO = NX_HALO + 4 * TX;  // + y-strips: 2 rows above and below the TX columns
-
-// D+ : integer-point field -> derivative at s + 1/2
-__device__ __forceinline__ float dfw(float fm1, float f0, float f1, float f2, float ix)
-{
-    return fmaf(kC2, f2 - fm1, kC1 * (f1 - f0)) * ix;
-}
-// D- : half-point field -> derivative at s
-__device__ __forceinline__ float dbw(float fm2, float fm1, float f0, float f1, float ix)
-{
-    return fmaf(kC2, f1 - fm2, kC1 * (f0 - fm1)) * ix;
-}
 
 // Tile coordinates (hx, hy) of halo element t: t < NX_HALO are the x-strips,
 // the rest the y-strips.
@@ -55,24 +49,6 @@ __device__ __forceinline__ void halo_coord(int t, int &hx, int &hy)
         hx = H + c;
         hy = (r < 2) ? r : TY + r;
     }
-}
-
-// position of coordinate c in its axis' CPML slab (-1 outside):
-// [0, P) on the low side, [n-P-1, n) on the high side.
-__device__ __forceinline__ int slab_pos(int c, int n, int P)
-{
-    if (P <= 0) return -1;
-    if (c < P) return c;
-    if (c >= n - P - 1) return c - (n - P - 1) + P;
-    return -1;
-}
-
-// CPML recursion psi <- b psi + a d; the derivative used is d + psi.
-__device__ __forceinline__ float cpml(float *__restrict__ psi, float2 ab, float d)
-{
-    const float v = fmaf(ab.x, d, ab.y * *psi);
-    *psi = v;
-    return d + v;
 }
 
 struct Geo {
@@ -191,36 +167,33 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
             float ux = vx[q], uy = vy[q], uz = vz[q];
             const float rho0 = s_rho[m0];
             if (ix1) {
-                const float b = 2.0f / (rho0 + s_rho[mx]);
                 float d1 = dfw(txx[c - 1], txx[c], txx[c + 1], txx[c + 2], ix);
                 float d2 = dbw(txy[c - 2 * SW], txy[c - SW], txy[c], txy[c + SW], ix);
                 float d3 = dbw(bz0, bz1, bz2, bz3, ix);
                 if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + qx, pmlx[p.nmax + g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + qz, pmlz[k], d3);
-                ux += dt * b * (d1 + d2 + d3);
+                ux += st::vel_increment(dt, rho0, s_rho[mx], d1, d2, d3);
                 vx[q] = ux;
             }
             if (jy1) {
-                const float b = 2.0f / (rho0 + s_rho[my]);
                 float d1 = dbw(txy[c - 2], txy[c - 1], txy[c], txy[c + 1], ix);
                 float d2 = dfw(tyy[c - SW], tyy[c], tyy[c + SW], tyy[c + 2 * SW], ix);
                 float d3 = dbw(cz0, cz1, cz2, cz3, ix);
                 if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + qx, pmlx[g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + qy, pmly[p.nmax + g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + qz, pmlz[k], d3);
-                uy += dt * b * (d1 + d2 + d3);
+                uy += st::vel_increment(dt, rho0, s_rho[my], d1, d2, d3);
                 vy[q] = uy;
             }
             if (kz1) {
-                const float b = 2.0f / (rho0 + s_rho[mz]);
                 float d1 = dbw(txz[c - 2], txz[c - 1], txz[c], txz[c + 1], ix);
                 float d2 = dbw(tyz[c - 2 * SW], tyz[c - SW], tyz[c], tyz[c + SW], ix);
                 float d3 = dfw(dz0, dz1, dz2, dz3, ix);
                 if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + qx, pmlx[g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + qz, pmlz[p.nmax + k], d3);
-                uz += dt * b * (d1 + d2 + d3);
+                uz += st::vel_increment(dt, rho0, s_rho[mz], d1, d2, d3);
                 vz[q] = uz;
             }
         }
@@ -232,26 +205,8 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
     }
 }
 
-// Memory-variable update of one stress component (Crank-Nicolson), on the
-// registers of this voxel: r_l <- ca_l r_l - cb_l Theta ; returns
-// sum_l (r_l^{n+1} + r_l^n).
 template <int L>
-__device__ __forceinline__ float sls_update(const AcParams &p, float (&rv)[L > 0 ? L : 1][6],
-                                            int c, float The)
-{
-    float sum = 0.0f;
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        const float r0 = rv[l][c];
-        const float rn = p.ca[l] * r0 - p.cb[l] * The;
-        sum += rn + r0;
-        rv[l][c] = rn;
-    }
-    return sum;
-}
-
-template <int L>
-__global__ void __launch_bounds__(NTH, 3) k_stress(AcParams p, int kchunk)
+__global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int kchunk)
 {
     extern __shared__ __align__(16) float sm_s[];
     MatCoef *s_lut = reinterpret_cast<MatCoef *>(sm_s);
@@ -261,7 +216,7 @@ __global__ void __launch_bounds__(NTH, 3) k_stress(AcParams p, int kchunk)
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
-    const float ix = p.inv_dx, dt = p.dt;
+    const float ix = p.inv_dx;
     const int c = (g.ty + H) * SW + (g.tx + H);
     const int xs = slab_pos(g.i, nx, p.P), ys = slab_pos(g.j, ny, p.P);
     const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
@@ -326,39 +281,20 @@ __global__ void __launch_bounds__(NTH, 3) k_stress(AcParams p, int kchunk)
             if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + qx, pmlx[g.i], exx);
             if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + qy, pmly[g.j], eyy);
             if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + qz, pmlz[k], ezz);
-            const float th = exx + eyy + ezz;
-
             float srcv = 0.0f;
             if (p.src_on && k == p.k_src) {
                 const float2 a = p.src[g.col];
                 srcv = p.src_scale * fmaf(a.x, p.src_ws, a.y * p.src_wc);
             }
-            const float ev[3] = {exx, eyy, ezz};
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const float dev = th - ev[cc];
-                const float Psi = c0.piU * th - c0.mu2U * dev;
-                const float The = c0.piT * th - c0.mu2T * dev;
-                const float sum = sls_update<L>(p, rv, cc, The);
-                float s = sv[cc] + dt * (Psi + 0.5f * sum);
-                s -= srcv;
-                sv[cc] = s;
-            }
-
-            // ---- capture: p = -(sxx + syy + szz) / 3
-            const float pr = -(sv[0] + sv[1] + sv[2]) / 3.0f;
+            st::normal_update<L>(p, c0, exx, eyy, ezz, srcv, sv, rv);
+            const float pr = st::pressure(sv);
             if (!isfinite(pr)) atomicOr(p.flag, 1);
 
-            // ---- shear stresses: harmonic-mean mu and mean tau_S of the four
-            // cells (pairs along the first axis summed first: mirror symmetry)
+            // ---- shear stresses
+            const float2 q00 = st::shear_pair(s_lut, m00);
             auto shear = [&](int cc, int mb, int md, int mf, float e) {
-                const MatCoef a = c0, b = s_lut[mb], d = s_lut[md], f = s_lut[mf];
-                const float muh = 4.0f / ((a.inv_mu + b.inv_mu) + (d.inv_mu + f.inv_mu));
-                const float tsh = 0.25f * ((a.tauS + b.tauS) + (d.tauS + f.tauS));
-                const float Psi = muh * (1.0f + p.Lf * tsh) * e;
-                const float The = muh * tsh * e;
-                const float sum = sls_update<L>(p, rv, cc, The);
-                sv[cc] += dt * (Psi + 0.5f * sum);
+                st::shear_update<L>(p, q00, st::shear_pair(s_lut, mb), st::shear_pair(s_lut, md),
+                                    st::shear_pair(s_lut, mf), e, cc, sv, rv);
             };
             const bool dxy = ix1 && jy1, dxz = ix1 && kz1, dyz = jy1 && kz1;
             if (dxy) {                               // sxy at (i+1/2, j+1/2, k)

@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "bvf_internal.cuh"
 
 using namespace bvf;
@@ -63,6 +65,10 @@ struct bvf_ctx {
     long long steps = 0, launches = 0, thermal_steps = 0;
     double courant = 0.0;
     int kchunk = 0;                   // z-planes per block (0 = default)
+    bool tma = false;                 // velocity kernel fed by TMA
+    bool tma_stress = false;          // stress kernel fed by TMA
+    StressTmaMaps smaps{};
+    VelocityTmaMaps vmaps{};
     std::string err;
     // per-launch event timing of the acoustic kernels
     bool timing = false;
@@ -200,6 +206,79 @@ cudaError_t drain_events(bvf_ctx *c)
     }
     c->ev_used = 0;
     return cudaSuccess;
+}
+
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// 3-D map of an nx*ny*nz array (x fastest) with a bx x by x 1 box; points
+// outside the array read as zero.
+bool encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, CUtensorMapDataType type,
+                size_t es, unsigned bx, unsigned by)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es};
+    const cuuint32_t box[3] = {bx, by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps of the TMA-fed kernels.  They need rows of the 1-byte index that
+// are whole multiples of 16 bytes (nx % 16 == 0) and at most 2 SLS mechanisms;
+// other grids use the direct kernels.
+void setup_maps(bvf_ctx *c)
+{
+    c->tma = false;
+    c->tma_stress = false;
+    const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+    if (nx % 16 != 0 || c->L > 2 || std::getenv("BVF_NO_TMA")) return;
+    const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, F64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    auto fld = [&](int f) { return (void *)(c->fields + (size_t)f * c->fstride); };
+    bool ok = true;
+    int a = 0;
+    for (int f = BVF_FIELD_SXX; f <= BVF_FIELD_SYZ; ++f)
+        ok = ok && encode_map(&c->smaps.s[a++], fld(f), nx, ny, nz, F32, 4, 32, 8);
+    for (int l = 0; l < c->L; ++l)
+        for (int cc = 0; cc < 6; ++cc)
+            ok = ok && encode_map(&c->smaps.s[a++], fld(BVF_FIELD_MEM0 + 6 * l + cc), nx, ny, nz,
+                                  F32, 4, 32, 8);
+    ok = ok && encode_map(&c->smaps.s[a++], c->peak, nx, ny, nz, F32, 4, 32, 8);
+    if (c->dftC) {
+        ok = ok && encode_map(&c->smaps.s[a++], c->dftC, nx, ny, nz, F64, 8, 32, 8);
+        ok = ok && encode_map(&c->smaps.s[a++], c->dftS, nx, ny, nz, F64, 8, 32, 8);
+    }
+    for (int v = 0; v < 3; ++v) {
+        ok = ok && encode_map(&c->smaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, F32, 4, 40, 12);
+        ok = ok && encode_map(&c->vmaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, F32, 4, 32, 8);
+    }
+    for (int g6 = 0; g6 < 6; ++g6)
+        ok = ok && encode_map(&c->vmaps.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, F32, 4, 40, 12);
+    ok = ok && encode_map(&c->smaps.idx, c->index, nx, ny, nz, U8, 1, 48, 9);
+    c->vmaps.idx = c->smaps.idx;
+    c->tma = ok;
+    // the direct stress kernel measures faster on the 240 x 240 x 200 skull;
+    // BVF_STRESS_TMA=1 selects the TMA-fed one
+    const char *st = std::getenv("BVF_STRESS_TMA");
+    c->tma_stress = ok && st && st[0] == '1';
 }
 
 AcParams make_params(bvf_ctx *c)
@@ -343,6 +422,7 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
         (e = cudaMemset(c->flag, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess)
         return cleanup(cuda_fail(nullptr, e, "bvf_create: zero fill"));
+    setup_maps(c);
     *out = c;
     return BVF_OK;
 }
@@ -491,6 +571,7 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
         CK(cudaMalloc(&c->dftS, c->N * sizeof(double)), "dft buffers");
         CK(cudaMemsetAsync(c->dftC, 0, c->N * sizeof(double), s), "dft buffers");
         CK(cudaMemsetAsync(c->dftS, 0, c->N * sizeof(double), s), "dft buffers");
+        setup_maps(c);
     }
     AcParams p = make_params(c);
     const double w = 2.0 * kPi * c->ph.f0, dt = c->g.dt;
@@ -507,6 +588,12 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
         p.do_dft = (cp.dft_steps > 0 && step >= cp.dft_start && step < (long long)cp.dft_start + cp.dft_steps) ? 1 : 0;
         p.cw = std::cos(w * step * dt);
         p.sw = std::sin(w * step * dt);
+        auto vel = [&]() {
+            return c->tma ? launch_velocity_tma(p, c->vmaps, s) : launch_velocity(p, s);
+        };
+        auto str = [&]() {
+            return c->tma_stress ? launch_stress_tma(p, c->smaps, s) : launch_stress(p, s);
+        };
         if (c->timing) {
             if (c->ev_used + 3 > 3072) CK(drain_events(c), "kernel timing");
             cudaEvent_t e0, e1, e2;
@@ -514,17 +601,17 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
             CK(next_event(c, &e1), "kernel timing");
             CK(next_event(c, &e2), "kernel timing");
             CK(cudaEventRecord(e0, s), "kernel timing");
-            CK(launch_velocity(p, s), "velocity kernel");
+            CK(vel(), "velocity kernel");
             CK(cudaEventRecord(e1, s), "kernel timing");
-            CK(launch_stress(p, s), "stress kernel");
+            CK(str(), "stress kernel");
             CK(cudaEventRecord(e2, s), "kernel timing");
             c->ev_vel.push_back(e0);
             c->ev_vel.push_back(e1);
             c->ev_str.push_back(e1);
             c->ev_str.push_back(e2);
         } else {
-            CK(launch_velocity(p, s), "velocity kernel");
-            CK(launch_stress(p, s), "stress kernel");
+            CK(vel(), "velocity kernel");
+            CK(str(), "stress kernel");
         }
         c->launches += 2;
         c->dft_count += p.do_dft;
@@ -539,6 +626,7 @@ int bvf_synchronize(bvf_ctx *c, void *stream)
     CK(cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
     int f = 0;
     CK(cudaMemcpy(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
+    if (f & 2) return fail(c, BVF_E_CUDA, "a TMA copy did not complete within its wait limit");
     if (f) return fail(c, BVF_E_UNSTABLE, "non-finite pressure detected");
     return BVF_OK;
 }

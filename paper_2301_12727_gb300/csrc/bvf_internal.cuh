@@ -1,6 +1,7 @@
 // Internal declarations of libbvf (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,15 +15,16 @@ namespace bvf {
 // Per-material coefficients of the acoustic kernels (FP32, derived in FP64 on
 // the host).  Normal stress:  Psi = piU th - mu2U (th - e_ii),
 //                             Theta = piT th - mu2T (th - e_ii);
-// shear points combine inv_mu (harmonic mean) and tauS (arithmetic mean).
+// shear points combine inv_mu (harmonic mean) and tauS (arithmetic mean),
+// stored next to each other so one 8-byte load fetches both.
 struct MatCoef {
     float rho;     // density (buoyancy at v-points: 2 / (rho_a + rho_b))
     float piU;     // pi_R (1 + L tau_P)
     float piT;     // pi_R tau_P
     float mu2U;    // 2 mu_R (1 + L tau_S)
-    float mu2T;    // 2 mu_R tau_S
     float inv_mu;  // 1 / mu_R  (+inf for fluids, so the harmonic mean is 0)
     float tauS;    // tau_S
+    float mu2T;    // 2 mu_R tau_S
     float pad;
 };
 
@@ -65,6 +67,23 @@ struct AcParams {
     int kchunk;          // z-planes per block (0 = default_kchunk)
 };
 
+// Tensor maps of the TMA-fed acoustic kernels (x-y boxes of one z-plane).
+// Stress kernel: streaming arrays in stage order (6 stresses, 6 L memory
+// variables, the peak map, FP64 DFT sums C and S) with 32 x 8 boxes; the
+// velocities with 40 x 12 halo boxes; the material index with 48 x 9 boxes.
+struct StressTmaMaps {
+    CUtensorMap s[6 + 6 * 2 + 1 + 2];
+    CUtensorMap v[3];
+    CUtensorMap idx;
+};
+// Velocity kernel: the six stresses (sxx, syy, szz, sxy, sxz, syz) with
+// 40 x 12 halo boxes; the velocities with 32 x 8 boxes; the material index.
+struct VelocityTmaMaps {
+    CUtensorMap sg[6];
+    CUtensorMap v[3];
+    CUtensorMap idx;
+};
+
 struct ThParams {
     int nx, ny, nz;
     float dt, inv_dx2, T_a, dc, dt60;
@@ -80,10 +99,13 @@ struct ThParams {
 
 // z-planes per block of the z-marching acoustic kernels for a grid
 int default_kchunk(int nx, int ny, int nz);
+int default_kchunk_tma(int nx, int ny, int nz);
 
 // kernel launchers (bvf_acoustic.cu / bvf_aux.cu); return cudaGetLastError()
 cudaError_t launch_velocity(const AcParams &p, cudaStream_t s);
 cudaError_t launch_stress(const AcParams &p, cudaStream_t s);
+cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s);
+cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s);
 cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cudaStream_t s);
 cudaError_t launch_pressure(const float *sxx, const float *syy, const float *szz, float *out,
                             size_t n, cudaStream_t s);

@@ -1,0 +1,105 @@
+// Inline-PTX helpers for the tensor-memory accelerator (TMA) and mbarriers
+// used by the TMA-fed acoustic kernels (sm_90 and later, here sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+namespace bvf {
+namespace tma {
+
+__device__ __forceinline__ unsigned saddr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// arrive once and add `bytes` to the transaction count of the current phase
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; on time-out sets bit 2 of
+// *flag and returns false (the caller skips its work but keeps every barrier).
+constexpr unsigned kWaitLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *flag)
+{
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(flag, 2);
+    return false;
+}
+
+// order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (TMA) accesses
+__device__ __forceinline__ void fence_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// global -> shared tile load of a 3-D tensor map box at (x, y, z); completion
+// is counted in bytes on `bar`.  Out-of-range elements are zero-filled.
+__device__ __forceinline__ void load3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                       uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
+        : "memory");
+}
+
+// shared -> global tile store; out-of-range elements are not written
+__device__ __forceinline__ void store3d(const CUtensorMap *map, int x, int y, int z, const void *src)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+        "r"(x), "r"(y), "r"(z), "r"(saddr(src))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// wait until at most N committed store groups are still reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// wait until at most N committed store groups are still in flight
+template <int N>
+__device__ __forceinline__ void bulk_wait()
+{
+    asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+}  // namespace tma
+}  // namespace bvf

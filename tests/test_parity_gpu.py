@@ -296,3 +296,36 @@ def test_gpu_zchunk_invariance(bvf, monkeypatch):
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
+
+
+def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch):
+    """Grids with nx % 16 == 0 run the TMA-fed kernels (tiles, rings and
+    in-place stages moved by the tensor-memory accelerator); other shapes, or
+    BVF_NO_TMA, run the direct kernels.  Same arithmetic, so every field, the
+    peak map and the FP64 DFT agree bit for bit, across z-chunk lengths (chunk
+    prologues) and a partial x-tile (nx = 80)."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(80, 48, 40, dx=0.5e-3, n_steps=120, aperture=16e-3, roc=16e-3, n_pml=5)
+    outs = []
+    for no_tma, st_tma, kc in (("", "1", "0"), ("", "1", "3"), ("", "1", "1"), ("", "", "0"),
+                               ("1", "", "0")):
+        monkeypatch.setenv("BVF_KCHUNK", kc)
+        monkeypatch.setenv("BVF_STRESS_TMA", st_tma)
+        if no_tma:
+            monkeypatch.setenv("BVF_NO_TMA", "1")
+        else:
+            monkeypatch.delenv("BVF_NO_TMA", raising=False)
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+        s.set_materials(c.index, c.materials)
+        s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
+                     c.c0, c.envelope)
+        s.run(c.n_steps, peak_from=10, dft_start=c.n_steps - 45, dft_steps=46)
+        s.synchronize()
+        amp, ph = s.amp_phase()
+        outs.append([s.field(f).cpu().numpy() for f in range(21)] +
+                    [s.peak().cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy()])
+        s.close()
+    assert np.abs(outs[0][21]).max() > 0
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
