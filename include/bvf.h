@@ -269,6 +269,25 @@ int bvf_transmission(int nx, int ny, int nz,
                      double *h_EL, double *h_TS, int *h_zm, double *h_Iw_max,
                      void *stream);
 
+/* bvf_transmission without any device allocation (the paper has no
+ * counterpart: this serves callers that cannot allocate device memory when
+ * they need E_L, e.g. because their own pool already reserves the GPU's memory
+ * or an allocation would stall a latency-bound loop).  Same arguments,
+ * results and errors as bvf_transmission; each table may hold at most
+ * BVF_MAX_MATERIALS rows (BVF_E_ARG beyond that).  Its temporaries live in one
+ * fixed array of about 4 KiB inside the library, present on every GPU that
+ * loads it until the process exits; the first call on a device looks up that
+ * array's address, so make it before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (e.g. unordered streams) race.
+ * Synchronous: waits for `stream`. */
+int bvf_transmission_noalloc(int nx, int ny, int nz,
+                             const uint8_t *d_idx_a, const bvf_material *h_mat_a, int n_a,
+                             const double *d_amp_a,
+                             const uint8_t *d_idx_w, const bvf_material *h_mat_w, int n_w,
+                             const double *d_amp_w,
+                             double *h_EL, double *h_TS, int *h_zm, double *h_Iw_max,
+                             void *stream);
+
 /* Counters (host struct filled synchronously). */
 int bvf_get_stats(const bvf_ctx *ctx, bvf_stats *out);
 

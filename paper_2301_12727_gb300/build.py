@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbvf.so")
-SOURCES = ("bvf_api.cu", "bvf_acoustic.cu", "bvf_acoustic_tma.cu", "bvf_aux.cu")
+SOURCES = ("bvf_api.cu", "bvf_acoustic.cu", "bvf_acoustic_tma.cu", "bvf_aux.cu",
+           "bvf_noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-cudart", "shared", "--expt-relaxed-constexpr"]

@@ -26,7 +26,8 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_last_error", "bvf_set_materials", "bvf_rs_plane", "bvf_set_source", "bvf_reset",
            "bvf_run_acoustic", "bvf_synchronize", "bvf_get_field", "bvf_set_field",
            "bvf_get_pressure", "bvf_get_peak", "bvf_get_amp_phase", "bvf_run_thermal",
-           "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times")
+           "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times",
+           "bvf_transmission_noalloc")
 
 
 class BvfError(RuntimeError):
@@ -115,6 +116,7 @@ def lib():
                                        ctypes.POINTER(Material), i, vp,
                                        ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(i),
                                        ctypes.POINTER(d), vp]
+        L.bvf_transmission_noalloc.argtypes = L.bvf_transmission.argtypes
         L.bvf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.bvf_kernel_timing.argtypes = [vp, i]
         L.bvf_get_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTimes)]
@@ -249,6 +251,21 @@ def bvf_transmission(idx_a, table_a, amp_a, idx_w, table_w, amp_w, stream=None):
                                   len(mw), _ptr(amp_w, torch.float64), ctypes.byref(el),
                                   ctypes.byref(ts), ctypes.byref(zm), ctypes.byref(iw),
                                   _stream(stream)))
+    return el.value, ts.value, zm.value, iw.value
+
+
+def bvf_transmission_noalloc(idx_a, table_a, amp_a, idx_w, table_w, amp_w, stream=None):
+    """bvf_transmission for callers that cannot allocate device memory: the
+    library keeps the reduction's temporaries in a fixed array (see bvf.h)."""
+    import torch
+    nz, ny, nx = idx_a.shape
+    ma, mw = material_array(table_a), material_array(table_w)
+    el, ts, zm, iw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().bvf_transmission_noalloc(nx, ny, nz, _ptr(idx_a, torch.uint8), ma, len(ma),
+                                          _ptr(amp_a, torch.float64), _ptr(idx_w, torch.uint8),
+                                          mw, len(mw), _ptr(amp_w, torch.float64),
+                                          ctypes.byref(el), ctypes.byref(ts), ctypes.byref(zm),
+                                          ctypes.byref(iw), _stream(stream)))
     return el.value, ts.value, zm.value, iw.value
 
 

@@ -33,6 +33,8 @@ struct MatDerived {
 
 }  // namespace
 
+void bvf::set_context_free_error(const char *msg) { g_last_error = msg; }
+
 struct bvf_ctx {
     bvf_grid g{};
     bvf_physics ph{};

@@ -97,6 +97,9 @@ struct ThParams {
     double *cem;
 };
 
+// message returned by bvf_last_error(NULL) for a failed context-free call
+void set_context_free_error(const char *msg);
+
 // z-planes per block of the z-marching acoustic kernels for a grid
 int default_kchunk(int nx, int ny, int nz);
 int default_kchunk_tma(int nx, int ny, int nz);
