@@ -53,14 +53,14 @@ __device__ __forceinline__ void halo_coord(int t, int &hx, int &hy)
 
 struct Geo {
     int nx, ny, nz;
-    long long SZ;
+    int SZ;
     int i, j, tx, ty, tid;
     bool live;
-    long long col;      // j*nx + i
+    int col;            // j*nx + i
     bool hal, hin;      // this thread fills a halo element / it lies inside the grid
     int hslot;          // its index in the tile
     bool hxstrip;       // the element belongs to an x-strip
-    long long hcol;     // its gy*nx + gx
+    int hcol;           // its gy*nx + gx
 };
 
 __device__ __forceinline__ Geo make_geo(int nx, int ny, int nz)
@@ -69,7 +69,7 @@ __device__ __forceinline__ Geo make_geo(int nx, int ny, int nz)
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.SZ = (long long)nx * ny;
+    g.SZ = nx * ny;
     g.tx = threadIdx.x;
     g.ty = threadIdx.y;
     g.tid = g.ty * TX + g.tx;
@@ -77,7 +77,7 @@ __device__ __forceinline__ Geo make_geo(int nx, int ny, int nz)
     g.i = x0 + g.tx;
     g.j = y0 + g.ty;
     g.live = g.i < nx && g.j < ny;
-    g.col = (long long)g.j * nx + g.i;
+    g.col = g.j * nx + g.i;
     g.hal = g.tid < NHALO;
     int hx = 0, hy = 0;
     if (g.hal) halo_coord(g.tid, hx, hy);
@@ -85,7 +85,7 @@ __device__ __forceinline__ Geo make_geo(int nx, int ny, int nz)
     const int gx = x0 - H + hx, gy = y0 - H + hy;
     g.hin = g.hal && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
     g.hslot = hy * SW + hx;
-    g.hcol = (long long)gy * nx + gx;
+    g.hcol = gy * nx + gx;
     return g;
 }
 
@@ -110,11 +110,11 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
-    const float ix = p.inv_dx, dt = p.dt;
+    const st::Dx ix = st::make_dx(p.inv_dx);
+    const float dt = p.dt;
     const int c = (g.ty + H) * SW + (g.tx + H);
     const int xs = slab_pos(g.i, nx, p.P), ys = slab_pos(g.j, ny, p.P);
-    const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
-                    Szs = (long long)p.W * ny * nx;
+    const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
     const bool hx_ = g.hxstrip, hy_ = !g.hxstrip;
     const uint8_t *__restrict__ idx = p.idx;
@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
         const float nhyz = halv(p.syz, g, k + 1, hy_);
 
         if (g.live) {
-            const long long q = k * g.SZ + g.col;
+            const int q = k * g.SZ + g.col;
             const int zs = slab_pos(k, nz, p.P);
-            const long long qx = ((long long)k * ny + g.j) * p.W + xs;
-            const long long qy = ((long long)k * p.W + ys) * nx + g.i;
-            const long long qz = ((long long)zs * ny + g.j) * nx + g.i;
+            const int qx = (k * ny + g.j) * p.W + xs;
+            const int qy = (k * p.W + ys) * nx + g.i;
+            const int qz = (zs * ny + g.j) * nx + g.i;
             const bool ix1 = g.i < nx - 1, jy1 = g.j < ny - 1, kz1 = k < nz - 1;
             // every global load of this voxel first
             const int m0 = __ldg(idx + q), mx = __ldg(idx + q + (ix1 ? 1 : 0));
@@ -209,18 +209,17 @@ template <int L>
 __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int kchunk)
 {
     extern __shared__ __align__(16) float sm_s[];
-    MatCoef *s_lut = reinterpret_cast<MatCoef *>(sm_s);
-    float *tiles = sm_s + p.n_mat * (sizeof(MatCoef) / sizeof(float));   // [2][3][TILE]
+    st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(sm_s);
+    float *tiles = sm_s + p.n_mat * (sizeof(st::StressCoef) / sizeof(float));   // [2][3][TILE]
     const Geo g = make_geo(p.nx, p.ny, p.nz);
-    for (int m = g.tid; m < p.n_mat; m += NTH) s_lut[m] = p.lut[m];
+    for (int m = g.tid; m < p.n_mat; m += NTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
-    const float ix = p.inv_dx;
+    const st::Dx ix = st::make_dx(p.inv_dx);
     const int c = (g.ty + H) * SW + (g.tx + H);
     const int xs = slab_pos(g.i, nx, p.P), ys = slab_pos(g.j, ny, p.P);
-    const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
-                    Szs = (long long)p.W * ny * nx;
+    const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
     const uint8_t *__restrict__ idx = p.idx;
     float *__restrict__ mem = p.mem;
@@ -250,14 +249,14 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
         const float nhz = halv(p.vz, g, k + 1, true);
 
         if (g.live) {
-            const long long q = k * g.SZ + g.col;
+            const int q = k * g.SZ + g.col;
             const int zs = slab_pos(k, nz, p.P);
-            const long long qx = ((long long)k * ny + g.j) * p.W + xs;
-            const long long qy = ((long long)k * p.W + ys) * nx + g.i;
-            const long long qz = ((long long)zs * ny + g.j) * nx + g.i;
+            const int qx = (k * ny + g.j) * p.W + xs;
+            const int qy = (k * p.W + ys) * nx + g.i;
+            const int qz = (zs * ny + g.j) * nx + g.i;
             // ---- every global load of this voxel first (independent, in flight together)
             const bool ix1 = g.i < nx - 1, jy1 = g.j < ny - 1, kz1 = k < nz - 1;
-            const long long o1 = ix1 ? 1 : 0, oy = jy1 ? nx : 0, oz = kz1 ? g.SZ : 0;
+            const int o1 = ix1 ? 1 : 0, oy = jy1 ? nx : 0, oz = kz1 ? g.SZ : 0;
             const int m00 = __ldg(idx + q), m10 = __ldg(idx + q + o1);
             const int m01 = __ldg(idx + q + oy), m11 = __ldg(idx + q + o1 + oy);
             const int mz0 = __ldg(idx + q + oz), mz1 = __ldg(idx + q + o1 + oz);
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
             const float pk = p.do_peak ? peak[q] : 0.0f;
             double dC = 0.0, dS = 0.0;
             if (p.do_dft) { dC = p.dftC[q]; dS = p.dftS[q]; }
-            const MatCoef c0 = s_lut[m00];
+            const st::StressCoef c0 = s_lut[m00];
 
             // ---- normal stresses at (i, j, k)
             float exx = dbw(tvx[c - 2], tvx[c - 1], tvx[c], tvx[c + 1], ix);
@@ -291,10 +290,8 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
             if (!isfinite(pr)) atomicOr(p.flag, 1);
 
             // ---- shear stresses
-            const float2 q00 = st::shear_pair(s_lut, m00);
             auto shear = [&](int cc, int mb, int md, int mf, float e) {
-                st::shear_update<L>(p, q00, st::shear_pair(s_lut, mb), st::shear_pair(s_lut, md),
-                                    st::shear_pair(s_lut, mf), e, cc, sv, rv);
+                st::shear_update<L>(p, s_lut, c0, m00, mb, md, mf, e, cc, sv, rv);
             };
             const bool dxy = ix1 && jy1, dxz = ix1 && kz1, dyz = jy1 && kz1;
             if (dxy) {                               // sxy at (i+1/2, j+1/2, k)
@@ -376,7 +373,7 @@ cudaError_t launch_velocity(const AcParams &p, cudaStream_t s)
 cudaError_t launch_stress(const AcParams &p, cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk(p.nx, p.ny, p.nz);
-    const size_t sm = p.n_mat * sizeof(MatCoef) + 2 * 3 * TILE * sizeof(float);
+    const size_t sm = p.n_mat * sizeof(st::StressCoef) + 2 * 3 * TILE * sizeof(float);
     const dim3 grd = grid_of(p, kc), blk(TX, TY, 1);
     switch (p.L) {
     case 0: k_stress<0><<<grd, blk, sm, s>>>(p, kc); break;

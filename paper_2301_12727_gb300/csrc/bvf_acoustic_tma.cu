@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(NTH, 4)
         ldS(k0, stage(0), &bars[0]);
     }
 
-    const float ix = p.inv_dx, dt = p.dt;
+    const st::Dx ix = st::make_dx(p.inv_dx);
+    const float dt = p.dt;
     const int cv = (ty + 2) * VW + tx + 4;
     const int ci = ty * IW + tx;
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
-    const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
-                    Szs = (long long)p.W * ny * nx;
+    const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
 
     // ring slots, rotated once per plane: A holds plane k (slot a0) and k+1;
@@ -159,9 +159,9 @@ __global__ void __launch_bounds__(NTH, 4)
                 float d2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
                 float d3 = dbw(ringB[(bm2 * 2) * VT + cv], ringB[(bm1 * 2) * VT + cv], XZ[0],
                                ringB[(bp1 * 2) * VT + cv], ix);
-                if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + ((long long)k * ny + j) * p.W + xs, pmlx[p.nmax + i], d1);
-                if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + ((long long)k * p.W + ys) * nx + i, pmly[j], d2);
-                if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + ((long long)zs * ny + j) * nx + i, pmlz[k], d3);
+                if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], d1);
+                if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
+                if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
                 s[0] += st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
             }
             if (jy1) {
@@ -169,9 +169,9 @@ __global__ void __launch_bounds__(NTH, 4)
                 float d2 = dfw(YY[-VW], YY[0], YY[VW], YY[2 * VW], ix);
                 float d3 = dbw(ringB[(bm2 * 2 + 1) * VT + cv], ringB[(bm1 * 2 + 1) * VT + cv], YZ[0],
                                ringB[(bp1 * 2 + 1) * VT + cv], ix);
-                if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + ((long long)k * ny + j) * p.W + xs, pmlx[i], d1);
-                if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + ((long long)k * p.W + ys) * nx + i, pmly[p.nmax + j], d2);
-                if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + ((long long)zs * ny + j) * nx + i, pmlz[k], d3);
+                if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
+                if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], d2);
+                if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
                 s[NTH] += st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
             }
             if (kz1) {
@@ -180,9 +180,9 @@ __global__ void __launch_bounds__(NTH, 4)
                 float d2 = dbw(YZ[-2 * VW], YZ[-VW], YZ[0], YZ[VW], ix);
                 float d3 = dfw(ringC[cm1 * VT + cv], ringC[ck * VT + cv], ringC[cp1 * VT + cv],
                                ringC[cp2 * VT + cv], ix);
-                if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + ((long long)k * ny + j) * p.W + xs, pmlx[i], d1);
-                if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + ((long long)k * p.W + ys) * nx + i, pmly[j], d2);
-                if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + ((long long)zs * ny + j) * nx + i, pmlz[p.nmax + k], d3);
+                if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
+                if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
+                if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], d3);
                 s[2 * NTH] += st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
             }
         }
@@ -211,7 +211,7 @@ struct StressLayout {
     static constexpr size_t off_i = off_v + (size_t)RV * 3 * VT_BYTES;
     static constexpr size_t off_bar = off_i + RI * IT_SLOT;
     static constexpr size_t off_lut = off_bar + 16;
-    static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(MatCoef); }
+    static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(st::StressCoef); }
 };
 
 template <int L>
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NTH, 2)
     float *ringV = reinterpret_cast<float *>(sm + Lay::off_v);
     uint8_t *ringI = sm + Lay::off_i;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Lay::off_bar);
-    MatCoef *s_lut = reinterpret_cast<MatCoef *>(sm + Lay::off_lut);
+    st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(sm + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NTH, 2)
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
-    for (int m = tid; m < p.n_mat; m += NTH) s_lut[m] = p.lut[m];
+    for (int m = tid; m < p.n_mat; m += NTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
     if (tid == 0) {
         tma::mbar_init(&bars[0], 1);
         tma::mbar_init(&bars[1], 1);
@@ -278,12 +278,11 @@ __global__ void __launch_bounds__(NTH, 2)
         ldS(k0, stage(0), &bars[0]);
     }
 
-    const float ix = p.inv_dx;
+    const st::Dx ix = st::make_dx(p.inv_dx);
     const int cv = (ty + 2) * VW + tx + 4;
     const int ci = ty * IW + tx;
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
-    const long long Sxs = (long long)nz * ny * p.W, Sys = (long long)nz * p.W * nx,
-                    Szs = (long long)p.W * ny * nx;
+    const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
 
     // ring slots, rotated once per plane: the v ring holds planes k-2 .. k+3
@@ -326,19 +325,19 @@ __global__ void __launch_bounds__(NTH, 2)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) rv[l][cc] = s[(6 + 6 * l + cc) * NTH];
             const int m00 = I0[0];
-            const MatCoef c0 = s_lut[m00];
+            const st::StressCoef c0 = s_lut[m00];
 
             // ---- normal stresses at (i, j, k)
             float exx = dbw(VX[-2], VX[-1], VX[0], VX[1], ix);
             float eyy = dbw(VY[-2 * VW], VY[-VW], VY[0], VY[VW], ix);
             float ezz = dbw(ringV[(r0 * 3 + 2) * VT + cv], ringV[(r1 * 3 + 2) * VT + cv], VZ[0],
                             ringV[(r3 * 3 + 2) * VT + cv], ix);
-            if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + ((long long)k * ny + j) * p.W + xs, pmlx[i], exx);
-            if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + ((long long)k * p.W + ys) * nx + i, pmly[j], eyy);
-            if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + ((long long)zs * ny + j) * nx + i, pmlz[k], ezz);
+            if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], exx);
+            if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + (k * p.W + ys) * nx + i, pmly[j], eyy);
+            if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + (zs * ny + j) * nx + i, pmlz[k], ezz);
             float srcv = 0.0f;
             if (p.src_on && k == p.k_src) {
-                const float2 a = p.src[(long long)j * nx + i];
+                const float2 a = p.src[j * nx + i];
                 srcv = p.src_scale * fmaf(a.x, p.src_ws, a.y * p.src_wc);
             }
             st::normal_update<L>(p, c0, exx, eyy, ezz, srcv, sv, rv);
@@ -346,33 +345,29 @@ __global__ void __launch_bounds__(NTH, 2)
             if (!isfinite(pr)) atomicOr(p.flag, 1);
 
             // ---- shear stresses
-            const float2 q00 = st::shear_pair(s_lut, m00);
             const bool dxy = ix1 && jy1, dxz = ix1 && kz1, dyz = jy1 && kz1;
             if (dxy) {                               // sxy at (i+1/2, j+1/2, k)
                 float a = dfw(VX[-VW], VX[0], VX[VW], VX[2 * VW], ix);
                 float b = dfw(VY[-1], VY[0], VY[1], VY[2], ix);
-                if (ys >= 0) a = cpml(p.psy + 4 * Sys + ((long long)k * p.W + ys) * nx + i, pmly[p.nmax + j], a);
-                if (xs >= 0) b = cpml(p.psx + 4 * Sxs + ((long long)k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
-                st::shear_update<L>(p, q00, st::shear_pair(s_lut, I0[1]), st::shear_pair(s_lut, I0[IW]),
-                                    st::shear_pair(s_lut, I0[IW + 1]), a + b, 3, sv, rv);
+                if (ys >= 0) a = cpml(p.psy + 4 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], a);
+                if (xs >= 0) b = cpml(p.psx + 4 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
+                st::shear_update<L>(p, s_lut, c0, m00, I0[1], I0[IW], I0[IW + 1], a + b, 3, sv, rv);
             }
             if (dxz) {                               // sxz at (i+1/2, j, k+1/2)
                 float a = dfw(ringV[(r1 * 3 + 0) * VT + cv], VX[0], ringV[(r3 * 3 + 0) * VT + cv],
                               ringV[(r4 * 3 + 0) * VT + cv], ix);
                 float b = dfw(VZ[-1], VZ[0], VZ[1], VZ[2], ix);
-                if (zs >= 0) a = cpml(p.psz + 4 * Szs + ((long long)zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
-                if (xs >= 0) b = cpml(p.psx + 5 * Sxs + ((long long)k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
-                st::shear_update<L>(p, q00, st::shear_pair(s_lut, I0[1]), st::shear_pair(s_lut, I1[0]),
-                                    st::shear_pair(s_lut, I1[1]), a + b, 4, sv, rv);
+                if (zs >= 0) a = cpml(p.psz + 4 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
+                if (xs >= 0) b = cpml(p.psx + 5 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
+                st::shear_update<L>(p, s_lut, c0, m00, I0[1], I1[0], I1[1], a + b, 4, sv, rv);
             }
             if (dyz) {                               // syz at (i, j+1/2, k+1/2)
                 float a = dfw(ringV[(r1 * 3 + 1) * VT + cv], VY[0], ringV[(r3 * 3 + 1) * VT + cv],
                               ringV[(r4 * 3 + 1) * VT + cv], ix);
                 float b = dfw(VZ[-VW], VZ[0], VZ[VW], VZ[2 * VW], ix);
-                if (zs >= 0) a = cpml(p.psz + 5 * Szs + ((long long)zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
-                if (ys >= 0) b = cpml(p.psy + 5 * Sys + ((long long)k * p.W + ys) * nx + i, pmly[p.nmax + j], b);
-                st::shear_update<L>(p, q00, st::shear_pair(s_lut, I0[IW]), st::shear_pair(s_lut, I1[0]),
-                                    st::shear_pair(s_lut, I1[IW]), a + b, 5, sv, rv);
+                if (zs >= 0) a = cpml(p.psz + 5 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
+                if (ys >= 0) b = cpml(p.psy + 5 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], b);
+                st::shear_update<L>(p, s_lut, c0, m00, I0[IW], I1[0], I1[IW], a + b, 5, sv, rv);
             }
 
             // ---- results back into the stage (ghost points keep their zeros)

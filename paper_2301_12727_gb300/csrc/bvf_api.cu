@@ -277,10 +277,9 @@ void setup_maps(bvf_ctx *c)
     ok = ok && encode_map(&c->smaps.idx, c->index, nx, ny, nz, U8, 1, 48, 9);
     c->vmaps.idx = c->smaps.idx;
     c->tma = ok;
-    // the direct stress kernel measures faster on the 240 x 240 x 200 skull;
-    // BVF_STRESS_TMA=1 selects the TMA-fed one
+    // BVF_STRESS_TMA=0 keeps the stress kernel on the direct path
     const char *st = std::getenv("BVF_STRESS_TMA");
-    c->tma_stress = ok && st && st[0] == '1';
+    c->tma_stress = ok && !(st && st[0] == '0');
 }
 
 AcParams make_params(bvf_ctx *c)
@@ -381,8 +380,8 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
         return fail(nullptr, BVF_E_ARG, "bvf_create: grid too small for the CPML or bad pml_R");
     if (phys->n_sls < 0 || phys->n_sls > BVF_MAX_SLS || !(phys->f0 > 0.0) || !(phys->qc > 0.0))
         return fail(nullptr, BVF_E_ARG, "bvf_create: bad physics (f0, qc or n_sls)");
-    if ((double)g.nx * g.ny * g.nz > 4.0e9)
-        return fail(nullptr, BVF_E_ARG, "bvf_create: grid larger than 4e9 voxels");
+    if ((double)g.nx * g.ny * g.nz >= 2147483648.0)
+        return fail(nullptr, BVF_E_ARG, "bvf_create: grid of 2^31 voxels or more");
 
     c = new (std::nothrow) bvf_ctx;
     if (!c) return fail(nullptr, BVF_E_NOMEM, "bvf_create: host allocation failed");

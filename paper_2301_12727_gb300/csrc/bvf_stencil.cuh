@@ -11,15 +11,21 @@ namespace st {
 constexpr float kC1 = 1.125f;            // 9/8
 constexpr float kC2 = -1.0f / 24.0f;     // -1/24
 
+// Difference coefficients with 1/dx folded in.
+struct Dx {
+    float c1, c2;
+};
+__device__ __forceinline__ Dx make_dx(float inv_dx) { return Dx{kC1 * inv_dx, kC2 * inv_dx}; }
+
 // D+ : integer-point field -> derivative at s + 1/2
-__device__ __forceinline__ float dfw(float fm1, float f0, float f1, float f2, float ix)
+__device__ __forceinline__ float dfw(float fm1, float f0, float f1, float f2, Dx d)
 {
-    return fmaf(kC2, f2 - fm1, kC1 * (f1 - f0)) * ix;
+    return fmaf(d.c2, f2 - fm1, d.c1 * (f1 - f0));
 }
 // D- : half-point field -> derivative at s
-__device__ __forceinline__ float dbw(float fm2, float fm1, float f0, float f1, float ix)
+__device__ __forceinline__ float dbw(float fm2, float fm1, float f0, float f1, Dx d)
 {
-    return fmaf(kC2, f1 - fm2, kC1 * (f0 - fm1)) * ix;
+    return fmaf(d.c2, f1 - fm2, d.c1 * (f0 - fm1));
 }
 
 // position of coordinate c in its axis' CPML slab (-1 outside):
@@ -66,10 +72,51 @@ __device__ __forceinline__ float vel_increment(float dt, float rho_a, float rho_
     return dt * (2.0f * __frcp_rn(rho_a + rho_b)) * (d1 + d2 + d3);
 }
 
+// Per-material coefficients as the stress kernels hold them in shared memory.
+// psiS/theS are the shear coefficients of a shear point whose four cells are
+// all this material, computed with exactly the operations of the general
+// four-cell path below, so taking them is bit-identical to that path.
+struct alignas(16) StressCoef {
+    float piU, piT, mu2U, mu2T;
+    float inv_mu, tauS;    // adjacent: one 8-byte load
+    float psiS, theS;
+};
+
+__device__ __forceinline__ float shear_mu(float2 a, float2 b, float2 d, float2 f)
+{
+    return 4.0f * __frcp_rn((a.x + b.x) + (d.x + f.x));
+}
+__device__ __forceinline__ float shear_tau(float2 a, float2 b, float2 d, float2 f)
+{
+    return 0.25f * ((a.y + b.y) + (d.y + f.y));
+}
+
+__device__ __forceinline__ StressCoef make_stress_coef(const MatCoef &m, float Lf)
+{
+    StressCoef c;
+    c.piU = m.piU;
+    c.piT = m.piT;
+    c.mu2U = m.mu2U;
+    c.mu2T = m.mu2T;
+    c.inv_mu = m.inv_mu;
+    c.tauS = m.tauS;
+    const float2 q = make_float2(m.inv_mu, m.tauS);
+    const float muh = shear_mu(q, q, q, q), tsh = shear_tau(q, q, q, q);
+    c.psiS = muh * fmaf(Lf, tsh, 1.0f);
+    c.theS = muh * tsh;
+    return c;
+}
+
+// (inv_mu, tauS) of a table entry as one 8-byte load
+__device__ __forceinline__ float2 shear_pair(const StressCoef *lut, int m)
+{
+    return *reinterpret_cast<const float2 *>(&lut[m].inv_mu);
+}
+
 // normal stresses + their memory variables at one voxel (the source, already
 // scaled, is subtracted from each normal stress)
 template <int L>
-__device__ __forceinline__ void normal_update(const AcParams &p, const MatCoef &c0, float exx,
+__device__ __forceinline__ void normal_update(const AcParams &p, const StressCoef &c0, float exx,
                                               float eyy, float ezz, float srcv, float (&sv)[6],
                                               float (&rv)[L > 0 ? L : 1][6])
 {
@@ -93,26 +140,31 @@ __device__ __forceinline__ float pressure(const float (&sv)[6])
     return -(sv[0] + sv[1] + sv[2]) * (1.0f / 3.0f);
 }
 
-// shear stress cc at a shear point whose four cells carry (inv_mu, tauS) in
-// a, b (first axis pair) and d, f (second); harmonic-mean mu, mean tau_S,
-// pairs along the first axis summed first (mirror symmetry)
+// shear stress cc at a shear point with cells m00, mb (first-axis pair) and
+// md, mf (second): harmonic-mean mu, mean tau_S, pairs along the first axis
+// summed first (mirror symmetry).  One material in all four cells takes the
+// per-material constants.
 template <int L>
-__device__ __forceinline__ void shear_update(const AcParams &p, float2 a, float2 b, float2 d,
-                                             float2 f, float e, int cc, float (&sv)[6],
+__device__ __forceinline__ void shear_update(const AcParams &p, const StressCoef *lut,
+                                             const StressCoef &c0, int m00, int mb, int md, int mf,
+                                             float e, int cc, float (&sv)[6],
                                              float (&rv)[L > 0 ? L : 1][6])
 {
-    const float muh = 4.0f * __frcp_rn((a.x + b.x) + (d.x + f.x));
-    const float tsh = 0.25f * ((a.y + b.y) + (d.y + f.y));
-    const float Psi = muh * (1.0f + p.Lf * tsh) * e;
-    const float The = muh * tsh * e;
+    float psic, thec;
+    if (mb == m00 && md == m00 && mf == m00) {
+        psic = c0.psiS;
+        thec = c0.theS;
+    } else {
+        const float2 a = make_float2(c0.inv_mu, c0.tauS), b = shear_pair(lut, mb);
+        const float2 d = shear_pair(lut, md), f = shear_pair(lut, mf);
+        const float muh = shear_mu(a, b, d, f), tsh = shear_tau(a, b, d, f);
+        psic = muh * fmaf(p.Lf, tsh, 1.0f);
+        thec = muh * tsh;
+    }
+    const float Psi = psic * e;
+    const float The = thec * e;
     const float sum = sls_update<L>(p, rv, cc, The);
     sv[cc] += p.dt * (Psi + 0.5f * sum);
-}
-
-// (inv_mu, tauS) of a table entry as one 8-byte load
-__device__ __forceinline__ float2 shear_pair(const MatCoef *lut, int m)
-{
-    return *reinterpret_cast<const float2 *>(&lut[m].inv_mu);
 }
 
 }  // namespace st

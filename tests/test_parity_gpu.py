@@ -307,7 +307,7 @@ def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch):
     from paper_2301_12727_gb300 import synth
     c = synth.skull_case(80, 48, 40, dx=0.5e-3, n_steps=120, aperture=16e-3, roc=16e-3, n_pml=5)
     outs = []
-    for no_tma, st_tma, kc in (("", "1", "0"), ("", "1", "3"), ("", "1", "1"), ("", "", "0"),
+    for no_tma, st_tma, kc in (("", "1", "0"), ("", "1", "3"), ("", "1", "1"), ("", "0", "0"),
                                ("1", "", "0")):
         monkeypatch.setenv("BVF_KCHUNK", kc)
         monkeypatch.setenv("BVF_STRESS_TMA", st_tma)
