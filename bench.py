@@ -113,11 +113,13 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def stress_traffic_per_voxel(kernel_src):
-    """DRAM bytes per voxel of the stress kernel from the committed ncu summary,
-    if that summary was taken on the current kernel source (else None)."""
+def stress_traffic_per_voxel(kernel_src, window_fraction):
+    """Measured DRAM bytes per voxel of the stress kernel, averaged over launches
+    inside and outside the DFT window like the algorithmic bytes, from the
+    committed ncu summary; None unless that summary was taken on the current
+    kernel source and holds both figures."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "stress_kernel_skull240.md")
+    path = os.path.join(ROOT, "profiles", "stress_kernel.md")
     try:
         text = open(path).read()
     except OSError:
@@ -131,9 +133,11 @@ def stress_traffic_per_voxel(kernel_src):
     if vals.get("kernel_source_sha256_16") != sha:
         return None
     try:
-        return float(vals["dram_bytes_per_voxel"])
+        win = float(vals["dram_bytes_per_voxel_dft_window"])
+        out = float(vals["dram_bytes_per_voxel_outside_window"])
     except (KeyError, ValueError):
         return None
+    return window_fraction * win + (1.0 - window_fraction) * out
 
 
 # --------------------------------------------------------------------------
@@ -289,9 +293,10 @@ def run_bvf(args):
     achieved = stress_bytes / (kt["stress_ms"] / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
     tr = stress_traffic_per_voxel(os.path.join(ROOT, "paper_2301_12727_gb300", "csrc",
-                                               "bvf_acoustic.cu"))
+                                               "bvf_acoustic_tma.cu"),
+                                  case.dft_steps / case.n_steps)
     vel_bytes = N * 49.0 * case.n_steps * n_runs
-    roofline = {"bound": "hbm", "kernel": "k_stress<2> (stress + SLS memory + source + capture)",
+    roofline = {"bound": "hbm", "kernel": "k_stress_tma<2> (stress + SLS memory + source + capture)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind,
                 "traffic": (tr * N if tr is not None else None),
