@@ -8,12 +8,16 @@
 //     the zero ghosts) held in per-array rings of z-planes that serve the
 //     4-point z-stencils as well;
 //   * the 1-byte material index arrives as 48 x 9 boxes (planes k and k+1);
-//   * the arrays each voxel reads and rewrites (velocities in the velocity
-//     kernel; stresses, memory variables, peak map and FP64 DFT sums in the
-//     stress kernel) are staged in a ring of three buffers, updated in place
-//     and written back with TMA stores;
-//   * one thread issues every copy for plane k+1 while plane k is computed;
-//     one __syncthreads and one bounded mbarrier wait per plane.
+//   * velocity kernel: the velocities are staged per plane, updated in place
+//     and written back with TMA stores; copies for plane k+1 are issued while
+//     plane k is computed (four resident blocks per SM);
+//   * stress kernel: the velocity and index rings run two planes ahead; the
+//     per-voxel arrays (stresses, memory variables, peak map, FP64 DFT sums)
+//     go straight to registers with loads issued at the top of each plane and
+//     back with coalesced stores, which keeps shared memory small enough for
+//     four resident blocks per SM;
+//   * one thread issues every copy; one __syncthreads and one bounded mbarrier
+//     wait per plane.
 // Used when rows are whole multiples of 16 bytes of the index (nx % 16 == 0)
 // and L <= 2.
 #include "bvf_stencil.cuh"
@@ -33,34 +37,35 @@ constexpr int VW = 40, VH = 12, VT = VW * VH;       // halo'd box: x0-4 .. x0+35
 constexpr unsigned VT_BYTES = VT * 4;               // 1920 = 15 * 128
 constexpr int IW = 48, IH = 9, IT = IW * IH;        // index box: x0 .. x0+47, y0 .. y0+8
 constexpr int IT_SLOT = 512;                        // bytes per index slot
-constexpr int NSTG = 3;                             // staging buffers
 
 // ---------------------------------------------------------------- velocity
+// Shared-memory layout (bytes) for loads issued D planes ahead; every TMA
+// destination is 128-byte aligned.
+template <int D>
 struct VelLayout {
-    static constexpr int STAGE_BYTES = 3 * NTH * 4;        // vx, vy, vz
-    static constexpr int RA = 2, RB = 5, RC = 5, RI = 3;  // ring depths
-    static constexpr size_t off_a = NSTG * STAGE_BYTES;   // sxx, syy, sxy (plane k, k+1)
-    static constexpr size_t off_b = off_a + RA * 3 * VT_BYTES;   // sxz, syz (k-2 .. k+2)
-    static constexpr size_t off_c = off_b + RB * 2 * VT_BYTES;   // szz (k-1 .. k+3)
-    static constexpr size_t off_i = off_c + RC * VT_BYTES;
-    static constexpr size_t off_bar = off_i + RI * IT_SLOT;
-    static constexpr size_t off_lut = off_bar + 16;
+    static constexpr int NS = 2 + D;                          // stages (vx, vy, vz)
+    static constexpr int RA = 1 + D, RB = 4 + D, RC = 4 + D, RI = 2 + D;   // ring depths
+    static constexpr int STAGE_F = 3 * NTH;                   // floats per stage
+    static constexpr int off_s = 0;
+    static constexpr int off_a = off_s + NS * STAGE_F * 4;    // sxx, syy, sxy: k .. k+D
+    static constexpr int off_b = off_a + RA * 3 * VT * 4;     // sxz, syz: k-2 .. k+1+D
+    static constexpr int off_c = off_b + RB * 2 * VT * 4;     // szz: k-1 .. k+2+D
+    static constexpr int off_i = off_c + RC * VT * 4;         // index: k .. k+1+D
+    static constexpr int off_bar = off_i + RI * IT_SLOT;
+    static constexpr int off_lut = off_bar + 32;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(float); }
 };
 
-__global__ void __launch_bounds__(NTH, 4)
+template <int D>
+__global__ void __launch_bounds__(NTH, D == 1 ? 4 : 3)
     k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
                    const __grid_constant__ VelocityTmaMaps tm)
 {
-    using Lay = VelLayout;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float *stages = reinterpret_cast<float *>(sm);
-    float *ringA = reinterpret_cast<float *>(sm + Lay::off_a);
-    float *ringB = reinterpret_cast<float *>(sm + Lay::off_b);
-    float *ringC = reinterpret_cast<float *>(sm + Lay::off_c);
-    uint8_t *ringI = sm + Lay::off_i;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Lay::off_bar);
-    float *s_rho = reinterpret_cast<float *>(sm + Lay::off_lut);
+    using Lay = VelLayout<D>;
+    extern __shared__ __align__(1024) float smf[];
+    unsigned char *smb = reinterpret_cast<unsigned char *>(smf);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
+    float *s_rho = smf + Lay::off_lut / 4;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -70,44 +75,44 @@ __global__ void __launch_bounds__(NTH, 4)
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
     for (int m = tid; m < p.n_mat; m += NTH) s_rho[m] = p.lut[m].rho;
     if (tid == 0) {
-        tma::mbar_init(&bars[0], 1);
-        tma::mbar_init(&bars[1], 1);
+        for (int b = 0; b <= D; ++b) tma::mbar_init(&bars[b], 1);
         tma::mbar_init_fence();
     }
     __syncthreads();
 
-    auto stage = [&](int it) { return stages + (it % NSTG) * (Lay::STAGE_BYTES / 4); };
-    auto tA = [&](int pl, int a) { return ringA + (((pl - k0) & 1) * 3 + a) * VT; };
-    auto tB = [&](int pl, int a) { return ringB + (((pl - k0 + 2) % Lay::RB) * 2 + a) * VT; };
-    auto tC = [&](int pl) { return ringC + ((pl - k0 + 1) % Lay::RC) * VT; };
-    auto tI = [&](int pl) { return ringI + ((pl - k0) % Lay::RI) * IT_SLOT; };
-    auto ldA = [&](int pl, uint64_t *bar) {
-        tma::load3d(tA(pl, 0), &tm.sg[0], x0 - 4, y0 - 2, pl, bar);   // sxx
-        tma::load3d(tA(pl, 1), &tm.sg[1], x0 - 4, y0 - 2, pl, bar);   // syy
-        tma::load3d(tA(pl, 2), &tm.sg[3], x0 - 4, y0 - 2, pl, bar);   // sxy
+    // float offsets of ring slots / stages for plane pl
+    auto oA = [&](int pl) { return Lay::off_a / 4 + ((pl - k0) % Lay::RA) * 3 * VT; };
+    auto oB = [&](int pl) { return Lay::off_b / 4 + ((pl - k0 + 2) % Lay::RB) * 2 * VT; };
+    auto oC = [&](int pl) { return Lay::off_c / 4 + ((pl - k0 + 1) % Lay::RC) * VT; };
+    auto oI = [&](int pl) { return Lay::off_i + ((pl - k0) % Lay::RI) * IT_SLOT; };   // bytes
+    auto oS = [&](int pl) { return Lay::off_s / 4 + ((pl - k0) % Lay::NS) * Lay::STAGE_F; };
+    // loads that plane kk needs first (everything for kk = k0)
+    auto issue = [&](int kk, uint64_t *bar, bool first) {
+        const unsigned nb = first ? 4 : 1;   // new B planes
+        const unsigned nc = first ? 4 : 1;   // new C planes
+        tma::mbar_expect_tx(bar, (3 + 2 * nb + nc) * VT_BYTES + (first ? 2 : 1) * IT +
+                                     Lay::STAGE_F * 4);
+        tma::load3d(smf + oA(kk), &tm.sg[0], x0 - 4, y0 - 2, kk, bar);            // sxx
+        tma::load3d(smf + oA(kk) + VT, &tm.sg[1], x0 - 4, y0 - 2, kk, bar);       // syy
+        tma::load3d(smf + oA(kk) + 2 * VT, &tm.sg[3], x0 - 4, y0 - 2, kk, bar);   // sxy
+        for (int pl = first ? kk - 2 : kk + 1; pl <= kk + 1; ++pl) {
+            tma::load3d(smf + oB(pl), &tm.sg[4], x0 - 4, y0 - 2, pl, bar);        // sxz
+            tma::load3d(smf + oB(pl) + VT, &tm.sg[5], x0 - 4, y0 - 2, pl, bar);   // syz
+        }
+        for (int pl = first ? kk - 1 : kk + 2; pl <= kk + 2; ++pl)
+            tma::load3d(smf + oC(pl), &tm.sg[2], x0 - 4, y0 - 2, pl, bar);        // szz
+        for (int pl = first ? kk : kk + 1; pl <= kk + 1; ++pl)
+            tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar);
+        for (int a = 0; a < 3; ++a) tma::load3d(smf + oS(kk) + a * NTH, &tm.v[a], x0, y0, kk, bar);
     };
-    auto ldB = [&](int pl, uint64_t *bar) {
-        tma::load3d(tB(pl, 0), &tm.sg[4], x0 - 4, y0 - 2, pl, bar);   // sxz
-        tma::load3d(tB(pl, 1), &tm.sg[5], x0 - 4, y0 - 2, pl, bar);   // syz
-    };
-    auto ldC = [&](int pl, uint64_t *bar) { tma::load3d(tC(pl), &tm.sg[2], x0 - 4, y0 - 2, pl, bar); };
-    auto ldI = [&](int pl, uint64_t *bar) { tma::load3d(tI(pl), &tm.idx, x0, y0, pl, bar); };
-    auto ldS = [&](int pl, float *s, uint64_t *bar) {
-        for (int a = 0; a < 3; ++a) tma::load3d(s + a * NTH, &tm.v[a], x0, y0, pl, bar);
-    };
-    auto stS = [&](int pl, const float *s) {
-        for (int a = 0; a < 3; ++a) tma::store3d(&tm.v[a], x0, y0, pl, s + a * NTH);
+    auto store_stage = [&](int kk) {
+        for (int a = 0; a < 3; ++a) tma::store3d(&tm.v[a], x0, y0, kk, smf + oS(kk) + a * NTH);
         tma::bulk_commit();
     };
-
     if (tid == 0) {
-        tma::mbar_expect_tx(&bars[0], (3 + 4 * 2 + 4) * VT_BYTES + 2 * IT + Lay::STAGE_BYTES);
-        ldA(k0, &bars[0]);
-        for (int pl = k0 - 2; pl <= k0 + 1; ++pl) ldB(pl, &bars[0]);
-        for (int pl = k0 - 1; pl <= k0 + 2; ++pl) ldC(pl, &bars[0]);
-        ldI(k0, &bars[0]);
-        ldI(k0 + 1, &bars[0]);
-        ldS(k0, stage(0), &bars[0]);
+        issue(k0, &bars[0], true);
+        for (int d = 1; d < D; ++d)
+            if (k0 + d < k1) issue(k0 + d, &bars[d], false);
     }
 
     const st::Dx ix = st::make_dx(p.inv_dx);
@@ -118,115 +123,95 @@ __global__ void __launch_bounds__(NTH, 4)
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
 
-    // ring slots, rotated once per plane: A holds plane k (slot a0) and k+1;
-    // B holds planes k-2 .. k+2 from slot b0; C holds k-1 .. k+3 from slot c0;
-    // the index ring holds k, k+1, k+2 from slot i0; stage of plane k: s0.
-    int a0 = 0, b0 = 0, c0 = 0, i0 = 0, s0 = 0;
-    auto wrap = [](int v, int n) { return v >= n ? v - n : v; };
     int it = 0;
     for (int k = k0; k < k1; ++k, ++it) {
         __syncthreads();
         if (tid == 0) {
-            if (it > 0) stS(k - 1, stage(it - 1));
-            if (k + 1 < k1) {
+            if (it > 0) store_stage(k - 1);
+            if (k + D < k1) {
                 tma::bulk_wait_read<1>();
                 tma::fence_async_smem();
-                uint64_t *bar = &bars[(it + 1) & 1];
-                tma::mbar_expect_tx(bar, 6 * VT_BYTES + IT + Lay::STAGE_BYTES);
-                ldA(k + 1, bar);
-                ldB(k + 2, bar);
-                ldC(k + 3, bar);
-                ldI(k + 2, bar);
-                ldS(k + 1, stage(it + 1), bar);
+                issue(k + D, &bars[(it + D) % (D + 1)], false);
             }
         }
-        const bool ready = tma::mbar_wait(&bars[it & 1], (it >> 1) & 1, p.flag);
+        const bool ready = tma::mbar_wait(&bars[it % (D + 1)], (it / (D + 1)) & 1, p.flag);
         if (ready && live) {
-            float *s = stages + s0 * (Lay::STAGE_BYTES / 4) + tid;
-            const float *XX = ringA + (a0 * 3 + 0) * VT + cv;
-            const float *YY = ringA + (a0 * 3 + 1) * VT + cv;
-            const float *XY = ringA + (a0 * 3 + 2) * VT + cv;
-            const int bm2 = b0, bm1 = wrap(b0 + 1, 5), bk = wrap(b0 + 2, 5), bp1 = wrap(b0 + 3, 5);
-            const float *XZ = ringB + (bk * 2 + 0) * VT + cv;
-            const float *YZ = ringB + (bk * 2 + 1) * VT + cv;
-            const uint8_t *I0 = ringI + i0 * IT_SLOT + ci;
-            const uint8_t *I1 = ringI + wrap(i0 + 1, 3) * IT_SLOT + ci;
+            const int s = oS(k) + tid;
+            const int a = oA(k) + cv;                 // sxx at a, syy at a + VT, sxy at a + 2 VT
+            const int bk = oB(k) + cv, bm2 = oB(k - 2) + cv, bm1 = oB(k - 1) + cv,
+                      bp1 = oB(k + 1) + cv;           // sxz at +0, syz at +VT
+            const unsigned char *I0 = smb + oI(k) + ci;
+            const unsigned char *I1 = smb + oI(k + 1) + ci;
             const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
             const int zs = slab_pos(k, nz, p.P);
             const float rho0 = s_rho[I0[0]];
             if (ix1) {
-                float d1 = dfw(XX[-1], XX[0], XX[1], XX[2], ix);
-                float d2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
-                float d3 = dbw(ringB[(bm2 * 2) * VT + cv], ringB[(bm1 * 2) * VT + cv], XZ[0],
-                               ringB[(bp1 * 2) * VT + cv], ix);
+                float d1 = dfw(smf[a - 1], smf[a], smf[a + 1], smf[a + 2], ix);
+                const int xy = a + 2 * VT;
+                float d2 = dbw(smf[xy - 2 * VW], smf[xy - VW], smf[xy], smf[xy + VW], ix);
+                float d3 = dbw(smf[bm2], smf[bm1], smf[bk], smf[bp1], ix);
                 if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
-                s[0] += st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
+                smf[s] += st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
             }
             if (jy1) {
-                float d1 = dbw(XY[-2], XY[-1], XY[0], XY[1], ix);
-                float d2 = dfw(YY[-VW], YY[0], YY[VW], YY[2 * VW], ix);
-                float d3 = dbw(ringB[(bm2 * 2 + 1) * VT + cv], ringB[(bm1 * 2 + 1) * VT + cv], YZ[0],
-                               ringB[(bp1 * 2 + 1) * VT + cv], ix);
+                const int xy = a + 2 * VT, yy = a + VT;
+                float d1 = dbw(smf[xy - 2], smf[xy - 1], smf[xy], smf[xy + 1], ix);
+                float d2 = dfw(smf[yy - VW], smf[yy], smf[yy + VW], smf[yy + 2 * VW], ix);
+                float d3 = dbw(smf[bm2 + VT], smf[bm1 + VT], smf[bk + VT], smf[bp1 + VT], ix);
                 if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
-                s[NTH] += st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
+                smf[s + NTH] += st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
             }
             if (kz1) {
-                const int cm1 = c0, ck = wrap(c0 + 1, 5), cp1 = wrap(c0 + 2, 5), cp2 = wrap(c0 + 3, 5);
-                float d1 = dbw(XZ[-2], XZ[-1], XZ[0], XZ[1], ix);
-                float d2 = dbw(YZ[-2 * VW], YZ[-VW], YZ[0], YZ[VW], ix);
-                float d3 = dfw(ringC[cm1 * VT + cv], ringC[ck * VT + cv], ringC[cp1 * VT + cv],
-                               ringC[cp2 * VT + cv], ix);
+                const int xz = bk, yz = bk + VT;
+                float d1 = dbw(smf[xz - 2], smf[xz - 1], smf[xz], smf[xz + 1], ix);
+                float d2 = dbw(smf[yz - 2 * VW], smf[yz - VW], smf[yz], smf[yz + VW], ix);
+                float d3 = dfw(smf[oC(k - 1) + cv], smf[oC(k) + cv], smf[oC(k + 1) + cv],
+                               smf[oC(k + 2) + cv], ix);
                 if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], d3);
-                s[2 * NTH] += st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
+                smf[s + 2 * NTH] += st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
             }
         }
         tma::fence_async_smem();
-        a0 ^= 1;
-        b0 = wrap(b0 + 1, 5);
-        c0 = wrap(c0 + 1, 5);
-        i0 = wrap(i0 + 1, 3);
-        s0 = wrap(s0 + 1, 3);
     }
     __syncthreads();
     if (tid == 0 && it > 0) {
-        stS(k1 - 1, stage(it - 1));
+        store_stage(k1 - 1);
         tma::bulk_wait<0>();
     }
 }
 
 // ------------------------------------------------------------------ stress
+// The stencil inputs (velocity tiles with halos, material index) come through
+// TMA rings two planes ahead; the per-voxel arrays (stresses, memory
+// variables, peak map, FP64 DFT sums) are read straight into registers at the
+// top of each plane, so their latency overlaps the ring wait and the
+// derivatives, and written back with coalesced stores.
 template <int L>
 struct StressLayout {
-    static constexpr int NS = 6 + 6 * L + 1;               // staged float arrays
-    static constexpr int STAGE_F = NS * NTH;
-    static constexpr int STAGE_BYTES = STAGE_F * 4 + 2 * NTH * 8;   // + FP64 C, S
-    static constexpr int RV = 6, RI = 3;
-    static constexpr size_t off_v = (size_t)NSTG * STAGE_BYTES;     // vx, vy, vz (k-2 .. k+3)
-    static constexpr size_t off_i = off_v + (size_t)RV * 3 * VT_BYTES;
-    static constexpr size_t off_bar = off_i + RI * IT_SLOT;
-    static constexpr size_t off_lut = off_bar + 16;
+    static constexpr int RV = 7, RI = 4;                      // ring depths
+    static constexpr int off_v = 0;                           // vx, vy, vz: k-2 .. k+4
+    static constexpr int off_i = off_v + RV * 3 * VT * 4;     // index: k .. k+3
+    static constexpr int off_bar = off_i + RI * IT_SLOT;
+    static constexpr int off_lut = off_bar + 32;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(st::StressCoef); }
 };
 
-template <int L>
-__global__ void __launch_bounds__(NTH, 2)
+template <int L, int MINB>
+__global__ void __launch_bounds__(NTH, MINB)
     k_stress_tma(const __grid_constant__ AcParams p, int kchunk,
                  const __grid_constant__ StressTmaMaps tm)
 {
     using Lay = StressLayout<L>;
-    constexpr int NS = Lay::NS;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    float *stages = reinterpret_cast<float *>(sm);
-    float *ringV = reinterpret_cast<float *>(sm + Lay::off_v);
-    uint8_t *ringI = sm + Lay::off_i;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + Lay::off_bar);
-    st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(sm + Lay::off_lut);
+    extern __shared__ __align__(1024) float smf[];
+    unsigned char *smb = reinterpret_cast<unsigned char *>(smf);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
+    st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -236,46 +221,25 @@ __global__ void __launch_bounds__(NTH, 2)
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
     for (int m = tid; m < p.n_mat; m += NTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
     if (tid == 0) {
-        tma::mbar_init(&bars[0], 1);
-        tma::mbar_init(&bars[1], 1);
+        for (int b = 0; b < 3; ++b) tma::mbar_init(&bars[b], 1);
         tma::mbar_init_fence();
     }
     __syncthreads();
 
-    const unsigned sbytes = (NS - 1) * NTH * 4 + (p.do_peak ? NTH * 4 : 0) + (p.do_dft ? 2 * NTH * 8 : 0);
-    auto stage = [&](int it) { return stages + (size_t)(it % NSTG) * (Lay::STAGE_BYTES / 4); };
-    auto tV = [&](int pl, int a) { return ringV + (((pl - k0 + 2) % Lay::RV) * 3 + a) * VT; };
-    auto tI = [&](int pl) { return ringI + ((pl - k0) % Lay::RI) * IT_SLOT; };
-    auto ldV = [&](int pl, uint64_t *bar) {
-        for (int a = 0; a < 3; ++a) tma::load3d(tV(pl, a), &tm.v[a], x0 - 4, y0 - 2, pl, bar);
+    auto oV = [&](int pl) { return Lay::off_v / 4 + ((pl - k0 + 2) % Lay::RV) * 3 * VT; };
+    auto oI = [&](int pl) { return Lay::off_i + ((pl - k0) % Lay::RI) * IT_SLOT; };   // bytes
+    auto issue = [&](int kk, uint64_t *bar, bool first) {
+        const unsigned nv = first ? 5 : 1;
+        tma::mbar_expect_tx(bar, nv * 3 * VT_BYTES + (first ? 2 : 1) * IT);
+        for (int pl = first ? kk - 2 : kk + 2; pl <= kk + 2; ++pl)
+            for (int a = 0; a < 3; ++a)
+                tma::load3d(smf + oV(pl) + a * VT, &tm.v[a], x0 - 4, y0 - 2, pl, bar);
+        for (int pl = first ? kk : kk + 1; pl <= kk + 1; ++pl)
+            tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar);
     };
-    auto ldI = [&](int pl, uint64_t *bar) { tma::load3d(tI(pl), &tm.idx, x0, y0, pl, bar); };
-    auto ldS = [&](int pl, float *s, uint64_t *bar) {
-        for (int a = 0; a < NS - 1; ++a) tma::load3d(s + a * NTH, &tm.s[a], x0, y0, pl, bar);
-        if (p.do_peak) tma::load3d(s + (NS - 1) * NTH, &tm.s[NS - 1], x0, y0, pl, bar);
-        if (p.do_dft) {
-            double *dd = reinterpret_cast<double *>(s + Lay::STAGE_F);
-            tma::load3d(dd, &tm.s[NS], x0, y0, pl, bar);
-            tma::load3d(dd + NTH, &tm.s[NS + 1], x0, y0, pl, bar);
-        }
-    };
-    auto stS = [&](int pl, const float *s) {
-        for (int a = 0; a < NS - 1; ++a) tma::store3d(&tm.s[a], x0, y0, pl, s + a * NTH);
-        if (p.do_peak) tma::store3d(&tm.s[NS - 1], x0, y0, pl, s + (NS - 1) * NTH);
-        if (p.do_dft) {
-            const double *dd = reinterpret_cast<const double *>(s + Lay::STAGE_F);
-            tma::store3d(&tm.s[NS], x0, y0, pl, dd);
-            tma::store3d(&tm.s[NS + 1], x0, y0, pl, dd + NTH);
-        }
-        tma::bulk_commit();
-    };
-
     if (tid == 0) {
-        tma::mbar_expect_tx(&bars[0], 5 * 3 * VT_BYTES + 2 * IT + sbytes);
-        for (int pl = k0 - 2; pl <= k0 + 2; ++pl) ldV(pl, &bars[0]);
-        ldI(k0, &bars[0]);
-        ldI(k0 + 1, &bars[0]);
-        ldS(k0, stage(0), &bars[0]);
+        issue(k0, &bars[0], true);
+        if (k0 + 1 < k1) issue(k0 + 1, &bars[1], false);
     }
 
     const st::Dx ix = st::make_dx(p.inv_dx);
@@ -284,54 +248,52 @@ __global__ void __launch_bounds__(NTH, 2)
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
+    float *const gs[6] = {p.sxx, p.syy, p.szz, p.sxy, p.sxz, p.syz};
+    float *__restrict__ mem = p.mem;
 
-    // ring slots, rotated once per plane: the v ring holds planes k-2 .. k+3
-    // from slot v0; the index ring k .. k+2 from slot i0; stage of plane k: s0.
-    int v0 = 0, i0 = 0, s0 = 0;
-    auto wrap = [](int v, int n) { return v >= n ? v - n : v; };
     int it = 0;
     for (int k = k0; k < k1; ++k, ++it) {
         __syncthreads();
-        if (tid == 0) {
-            if (it > 0) stS(k - 1, stage(it - 1));
-            if (k + 1 < k1) {
-                tma::bulk_wait_read<1>();
-                tma::fence_async_smem();
-                uint64_t *bar = &bars[(it + 1) & 1];
-                tma::mbar_expect_tx(bar, 3 * VT_BYTES + IT + sbytes);
-                ldV(k + 3, bar);
-                ldI(k + 2, bar);
-                ldS(k + 1, stage(it + 1), bar);
-            }
+        if (tid == 0 && k + 2 < k1) {
+            tma::fence_async_smem();
+            issue(k + 2, &bars[(it + 2) % 3], false);
         }
-        const bool ready = tma::mbar_wait(&bars[it & 1], (it >> 1) & 1, p.flag);
-        if (ready && live) {
-            float *s = stages + s0 * (Lay::STAGE_BYTES / 4) + tid;
-            // plane k-2+r of velocity component a, at this thread's column
-            const int r0 = v0, r1 = wrap(v0 + 1, 6), r2 = wrap(v0 + 2, 6), r3 = wrap(v0 + 3, 6),
-                      r4 = wrap(v0 + 4, 6);
-            const float *VX = ringV + (r2 * 3 + 0) * VT + cv;
-            const float *VY = ringV + (r2 * 3 + 1) * VT + cv;
-            const float *VZ = ringV + (r2 * 3 + 2) * VT + cv;
-            const uint8_t *I0 = ringI + i0 * IT_SLOT + ci;
-            const uint8_t *I1 = ringI + wrap(i0 + 1, 3) * IT_SLOT + ci;
-            const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
-            const int zs = slab_pos(k, nz, p.P);
-            float sv[6], rv[L > 0 ? L : 1][6];
+        const int q = k * (nx * ny) + j * nx + i;
+        // per-voxel loads first, in flight while the ring wait and the
+        // derivatives proceed
+        float sv[6], rv[L > 0 ? L : 1][6];
+        float pk = 0.0f;
+        double dC = 0.0, dS = 0.0;
+        if (live) {
 #pragma unroll
-            for (int cc = 0; cc < 6; ++cc) sv[cc] = s[cc * NTH];
+            for (int cc = 0; cc < 6; ++cc) sv[cc] = gs[cc][q];
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
-                for (int cc = 0; cc < 6; ++cc) rv[l][cc] = s[(6 + 6 * l + cc) * NTH];
+                for (int cc = 0; cc < 6; ++cc) rv[l][cc] = mem[(size_t)(l * 6 + cc) * p.fstride + q];
+            if (p.do_peak) pk = p.peak[q];
+            if (p.do_dft) {
+                dC = p.dftC[q];
+                dS = p.dftS[q];
+            }
+        }
+        const bool ready = tma::mbar_wait(&bars[it % 3], (it / 3) & 1, p.flag);
+        if (ready && live) {
+            const int v0 = oV(k) + cv;                       // vx at v0, vy v0 + VT, vz v0 + 2 VT
+            const int vm2 = oV(k - 2) + cv, vm1 = oV(k - 1) + cv, vp1 = oV(k + 1) + cv,
+                      vp2 = oV(k + 2) + cv;
+            const unsigned char *I0 = smb + oI(k) + ci;
+            const unsigned char *I1 = smb + oI(k + 1) + ci;
+            const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
+            const int zs = slab_pos(k, nz, p.P);
             const int m00 = I0[0];
             const st::StressCoef c0 = s_lut[m00];
+            const int vx = v0, vy = v0 + VT, vz = v0 + 2 * VT;
 
             // ---- normal stresses at (i, j, k)
-            float exx = dbw(VX[-2], VX[-1], VX[0], VX[1], ix);
-            float eyy = dbw(VY[-2 * VW], VY[-VW], VY[0], VY[VW], ix);
-            float ezz = dbw(ringV[(r0 * 3 + 2) * VT + cv], ringV[(r1 * 3 + 2) * VT + cv], VZ[0],
-                            ringV[(r3 * 3 + 2) * VT + cv], ix);
+            float exx = dbw(smf[vx - 2], smf[vx - 1], smf[vx], smf[vx + 1], ix);
+            float eyy = dbw(smf[vy - 2 * VW], smf[vy - VW], smf[vy], smf[vy + VW], ix);
+            float ezz = dbw(smf[vm2 + 2 * VT], smf[vm1 + 2 * VT], smf[vz], smf[vp1 + 2 * VT], ix);
             if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], exx);
             if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + (k * p.W + ys) * nx + i, pmly[j], eyy);
             if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + (zs * ny + j) * nx + i, pmlz[k], ezz);
@@ -347,119 +309,105 @@ __global__ void __launch_bounds__(NTH, 2)
             // ---- shear stresses
             const bool dxy = ix1 && jy1, dxz = ix1 && kz1, dyz = jy1 && kz1;
             if (dxy) {                               // sxy at (i+1/2, j+1/2, k)
-                float a = dfw(VX[-VW], VX[0], VX[VW], VX[2 * VW], ix);
-                float b = dfw(VY[-1], VY[0], VY[1], VY[2], ix);
+                float a = dfw(smf[vx - VW], smf[vx], smf[vx + VW], smf[vx + 2 * VW], ix);
+                float b = dfw(smf[vy - 1], smf[vy], smf[vy + 1], smf[vy + 2], ix);
                 if (ys >= 0) a = cpml(p.psy + 4 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], a);
                 if (xs >= 0) b = cpml(p.psx + 4 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
                 st::shear_update<L>(p, s_lut, c0, m00, I0[1], I0[IW], I0[IW + 1], a + b, 3, sv, rv);
             }
             if (dxz) {                               // sxz at (i+1/2, j, k+1/2)
-                float a = dfw(ringV[(r1 * 3 + 0) * VT + cv], VX[0], ringV[(r3 * 3 + 0) * VT + cv],
-                              ringV[(r4 * 3 + 0) * VT + cv], ix);
-                float b = dfw(VZ[-1], VZ[0], VZ[1], VZ[2], ix);
+                float a = dfw(smf[vm1], smf[vx], smf[vp1], smf[vp2], ix);
+                float b = dfw(smf[vz - 1], smf[vz], smf[vz + 1], smf[vz + 2], ix);
                 if (zs >= 0) a = cpml(p.psz + 4 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
                 if (xs >= 0) b = cpml(p.psx + 5 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
                 st::shear_update<L>(p, s_lut, c0, m00, I0[1], I1[0], I1[1], a + b, 4, sv, rv);
             }
             if (dyz) {                               // syz at (i, j+1/2, k+1/2)
-                float a = dfw(ringV[(r1 * 3 + 1) * VT + cv], VY[0], ringV[(r3 * 3 + 1) * VT + cv],
-                              ringV[(r4 * 3 + 1) * VT + cv], ix);
-                float b = dfw(VZ[-VW], VZ[0], VZ[VW], VZ[2 * VW], ix);
+                float a = dfw(smf[vm1 + VT], smf[vy], smf[vp1 + VT], smf[vp2 + VT], ix);
+                float b = dfw(smf[vz - VW], smf[vz], smf[vz + VW], smf[vz + 2 * VW], ix);
                 if (zs >= 0) a = cpml(p.psz + 5 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
                 if (ys >= 0) b = cpml(p.psy + 5 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], b);
                 st::shear_update<L>(p, s_lut, c0, m00, I0[IW], I1[0], I1[IW], a + b, 5, sv, rv);
             }
 
-            // ---- results back into the stage (ghost points keep their zeros)
+            // ---- results (ghost points are not written)
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) s[cc * NTH] = sv[cc];
-            if (dxy) s[3 * NTH] = sv[3];
-            if (dxz) s[4 * NTH] = sv[4];
-            if (dyz) s[5 * NTH] = sv[5];
+            for (int cc = 0; cc < 3; ++cc) gs[cc][q] = sv[cc];
+            if (dxy) gs[3][q] = sv[3];
+            if (dxz) gs[4][q] = sv[4];
+            if (dyz) gs[5][q] = sv[5];
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) {
                     const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
-                    if (w) s[(6 + 6 * l + cc) * NTH] = rv[l][cc];
+                    if (w) mem[(size_t)(l * 6 + cc) * p.fstride + q] = rv[l][cc];
                 }
-            if (p.do_peak) s[(NS - 1) * NTH] = fmaxf(s[(NS - 1) * NTH], fabsf(pr));
+            if (p.do_peak) p.peak[q] = fmaxf(pk, fabsf(pr));
             if (p.do_dft) {
-                double *dd = reinterpret_cast<double *>(stages + s0 * (Lay::STAGE_BYTES / 4) + Lay::STAGE_F) + tid;
-                dd[0] = fma((double)pr, p.cw, dd[0]);
-                dd[NTH] = fma((double)pr, p.sw, dd[NTH]);
+                p.dftC[q] = fma((double)pr, p.cw, dC);
+                p.dftS[q] = fma((double)pr, p.sw, dS);
             }
         }
-        tma::fence_async_smem();
-        v0 = wrap(v0 + 1, 6);
-        i0 = wrap(i0 + 1, 3);
-        s0 = wrap(s0 + 1, 3);
-    }
-    __syncthreads();
-    if (tid == 0 && it > 0) {
-        stS(k1 - 1, stage(it - 1));
-        tma::bulk_wait<0>();
     }
 }
 
 }  // namespace
-
-size_t velocity_tma_smem(int n_mat) { return VelLayout::bytes(n_mat); }
-
-size_t stress_tma_smem(int L, int n_mat)
-{
-    switch (L) {
-    case 0: return StressLayout<0>::bytes(n_mat);
-    case 1: return StressLayout<1>::bytes(n_mat);
-    default: return StressLayout<2>::bytes(n_mat);
-    }
-}
 
 static dim3 grid_tma(const AcParams &p, int kc)
 {
     return dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + kc - 1) / kc);
 }
 
-cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
+template <int D>
+static cudaError_t launch_velocity_tma_t(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
-    const size_t sm = velocity_tma_smem(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    const size_t sm = VelLayout<D>::bytes(p.n_mat);
+    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma<D>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_velocity_tma<<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    k_velocity_tma<D><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
 }
 
-template <int L>
+// One plane of lead (four resident blocks per SM) measures faster than two
+// planes of lead at three blocks per SM.
+cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
+{
+    return launch_velocity_tma_t<1>(p, tm, s);
+}
+
+template <int L, int MINB>
 static cudaError_t launch_stress_tma_t(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
     const size_t sm = StressLayout<L>::bytes(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_stress_tma<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_stress_tma<L, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_stress_tma<L><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    k_stress_tma<L, MINB><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
 }
 
+// Four resident blocks per SM (64 registers, about 46 KB of shared memory).
 cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     switch (p.L) {
-    case 0: return launch_stress_tma_t<0>(p, tm, s);
-    case 1: return launch_stress_tma_t<1>(p, tm, s);
-    case 2: return launch_stress_tma_t<2>(p, tm, s);
+    case 0: return launch_stress_tma_t<0, 4>(p, tm, s);
+    case 1: return launch_stress_tma_t<1, 4>(p, tm, s);
+    case 2: return launch_stress_tma_t<2, 4>(p, tm, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-// z-chunk length of the TMA kernels: each chunk pays a prologue of five
-// v-planes, so chunks are longer than for the direct kernels; about six waves
-// of two resident blocks per SM.
+// z-chunk length of the TMA kernels: about six waves of four resident blocks
+// per SM on 152 SMs (13 planes on the 240 x 240 x 200 grid; 8 to 16 measure
+// within 3 % of each other there, 25 is 13 % slower).
 int default_kchunk_tma(int nx, int ny, int nz)
 {
     const long long tiles = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
-    const long long target = 152LL * 2 * 6;
+    const long long target = 152LL * 4 * 6;
     long long chunks = (target + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;
     int kc = (int)((nz + chunks - 1) / chunks);
