@@ -8,9 +8,9 @@
 //     the zero ghosts) held in per-array rings of z-planes that serve the
 //     4-point z-stencils as well;
 //   * the 1-byte material index arrives as 48 x 9 boxes (planes k and k+1);
-//   * velocity kernel: the velocities are staged per plane, updated in place
-//     and written back with TMA stores; copies for plane k+1 are issued while
-//     plane k is computed (four resident blocks per SM);
+//   * velocity kernel: each stress array arrives in a box with exactly the
+//     halo its stencil needs; the velocities go straight to registers and
+//     back; copies for plane k+1 are issued while plane k is computed;
 //   * stress kernel: the velocity and index rings run two planes ahead; the
 //     per-voxel arrays (stresses, memory variables, peak map, FP64 DFT sums)
 //     go straight to registers with loads issued at the top of each plane and
@@ -39,29 +39,30 @@ constexpr int IW = 48, IH = 9, IT = IW * IH;        // index box: x0 .. x0+47, y
 constexpr int IT_SLOT = 512;                        // bytes per index slot
 
 // ---------------------------------------------------------------- velocity
-// Shared-memory layout (bytes) for loads issued D planes ahead; every TMA
-// destination is 128-byte aligned.
-template <int D>
+// Each stress array arrives in a box holding exactly the halo its stencil
+// reads: sxx 40 x 8 (x-halo), syy 32 x 12 (y-halo), sxy 40 x 12, sxz 40 x 8,
+// syz 32 x 12, szz 32 x 8 (z only).  The velocities go straight to registers
+// and back.  Loads for plane k+1 are issued while plane k is computed.
+constexpr int XW = 40, XH = 8, YW = 32, YH = 12;             // x-halo / y-halo boxes
+constexpr int TXX = XW * XH, TYY = YW * YH, TXY = VW * VH, TZZ = TX * TY;
 struct VelLayout {
-    static constexpr int NS = 2 + D;                          // stages (vx, vy, vz)
-    static constexpr int RA = 1 + D, RB = 4 + D, RC = 4 + D, RI = 2 + D;   // ring depths
-    static constexpr int STAGE_F = 3 * NTH;                   // floats per stage
-    static constexpr int off_s = 0;
-    static constexpr int off_a = off_s + NS * STAGE_F * 4;    // sxx, syy, sxy: k .. k+D
-    static constexpr int off_b = off_a + RA * 3 * VT * 4;     // sxz, syz: k-2 .. k+1+D
-    static constexpr int off_c = off_b + RB * 2 * VT * 4;     // szz: k-1 .. k+2+D
-    static constexpr int off_i = off_c + RC * VT * 4;         // index: k .. k+1+D
+    static constexpr int RA = 2, RB = 5, RC = 5, RI = 3;      // ring depths
+    static constexpr int SA = TXX + TYY + TXY;                // floats per A slot (sxx, syy, sxy)
+    static constexpr int SB = TXX + TYY;                      // B slot (sxz, syz)
+    static constexpr int off_a = 0;                           // plane k, k+1
+    static constexpr int off_b = off_a + RA * SA * 4;         // k-2 .. k+2
+    static constexpr int off_c = off_b + RB * SB * 4;         // szz: k-1 .. k+3
+    static constexpr int off_i = off_c + RC * TZZ * 4;        // index: k .. k+2
     static constexpr int off_bar = off_i + RI * IT_SLOT;
-    static constexpr int off_lut = off_bar + 32;
+    static constexpr int off_lut = off_bar + 16;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(float); }
 };
 
-template <int D>
-__global__ void __launch_bounds__(NTH, D == 1 ? 4 : 3)
+__global__ void __launch_bounds__(NTH, 5)
     k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
                    const __grid_constant__ VelocityTmaMaps tm)
 {
-    using Lay = VelLayout<D>;
+    using Lay = VelLayout;
     extern __shared__ __align__(1024) float smf[];
     unsigned char *smb = reinterpret_cast<unsigned char *>(smf);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
@@ -75,114 +76,138 @@ __global__ void __launch_bounds__(NTH, D == 1 ? 4 : 3)
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
     for (int m = tid; m < p.n_mat; m += NTH) s_rho[m] = p.lut[m].rho;
     if (tid == 0) {
-        for (int b = 0; b <= D; ++b) tma::mbar_init(&bars[b], 1);
+        tma::mbar_init(&bars[0], 1);
+        tma::mbar_init(&bars[1], 1);
         tma::mbar_init_fence();
     }
     __syncthreads();
 
-    // float offsets of ring slots / stages for plane pl
-    auto oA = [&](int pl) { return Lay::off_a / 4 + ((pl - k0) % Lay::RA) * 3 * VT; };
-    auto oB = [&](int pl) { return Lay::off_b / 4 + ((pl - k0 + 2) % Lay::RB) * 2 * VT; };
-    auto oC = [&](int pl) { return Lay::off_c / 4 + ((pl - k0 + 1) % Lay::RC) * VT; };
+    auto oA = [&](int pl) { return Lay::off_a / 4 + ((pl - k0) & 1) * Lay::SA; };
+    auto oB = [&](int pl) { return Lay::off_b / 4 + ((pl - k0 + 2) % Lay::RB) * Lay::SB; };
+    auto oC = [&](int pl) { return Lay::off_c / 4 + ((pl - k0 + 1) % Lay::RC) * TZZ; };
     auto oI = [&](int pl) { return Lay::off_i + ((pl - k0) % Lay::RI) * IT_SLOT; };   // bytes
-    auto oS = [&](int pl) { return Lay::off_s / 4 + ((pl - k0) % Lay::NS) * Lay::STAGE_F; };
-    // loads that plane kk needs first (everything for kk = k0)
-    auto issue = [&](int kk, uint64_t *bar, bool first) {
-        const unsigned nb = first ? 4 : 1;   // new B planes
-        const unsigned nc = first ? 4 : 1;   // new C planes
-        tma::mbar_expect_tx(bar, (3 + 2 * nb + nc) * VT_BYTES + (first ? 2 : 1) * IT +
-                                     Lay::STAGE_F * 4);
-        tma::load3d(smf + oA(kk), &tm.sg[0], x0 - 4, y0 - 2, kk, bar);            // sxx
-        tma::load3d(smf + oA(kk) + VT, &tm.sg[1], x0 - 4, y0 - 2, kk, bar);       // syy
-        tma::load3d(smf + oA(kk) + 2 * VT, &tm.sg[3], x0 - 4, y0 - 2, kk, bar);   // sxy
-        for (int pl = first ? kk - 2 : kk + 1; pl <= kk + 1; ++pl) {
-            tma::load3d(smf + oB(pl), &tm.sg[4], x0 - 4, y0 - 2, pl, bar);        // sxz
-            tma::load3d(smf + oB(pl) + VT, &tm.sg[5], x0 - 4, y0 - 2, pl, bar);   // syz
-        }
-        for (int pl = first ? kk - 1 : kk + 2; pl <= kk + 2; ++pl)
-            tma::load3d(smf + oC(pl), &tm.sg[2], x0 - 4, y0 - 2, pl, bar);        // szz
-        for (int pl = first ? kk : kk + 1; pl <= kk + 1; ++pl)
-            tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar);
-        for (int a = 0; a < 3; ++a) tma::load3d(smf + oS(kk) + a * NTH, &tm.v[a], x0, y0, kk, bar);
+    constexpr unsigned A_BYTES = Lay::SA * 4, B_BYTES = Lay::SB * 4, C_BYTES = TZZ * 4;
+    auto ldA = [&](int pl, uint64_t *bar) {
+        const int o = oA(pl);
+        tma::load3d(smf + o, &tm.sg[0], x0 - 4, y0, pl, bar);                    // sxx
+        tma::load3d(smf + o + TXX, &tm.sg[1], x0, y0 - 2, pl, bar);              // syy
+        tma::load3d(smf + o + TXX + TYY, &tm.sg[3], x0 - 4, y0 - 2, pl, bar);    // sxy
     };
-    auto store_stage = [&](int kk) {
-        for (int a = 0; a < 3; ++a) tma::store3d(&tm.v[a], x0, y0, kk, smf + oS(kk) + a * NTH);
-        tma::bulk_commit();
+    auto ldB = [&](int pl, uint64_t *bar) {
+        const int o = oB(pl);
+        tma::load3d(smf + o, &tm.sg[4], x0 - 4, y0, pl, bar);                    // sxz
+        tma::load3d(smf + o + TXX, &tm.sg[5], x0, y0 - 2, pl, bar);              // syz
     };
+    auto ldC = [&](int pl, uint64_t *bar) { tma::load3d(smf + oC(pl), &tm.sg[2], x0, y0, pl, bar); };
+    auto ldI = [&](int pl, uint64_t *bar) { tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar); };
+
     if (tid == 0) {
-        issue(k0, &bars[0], true);
-        for (int d = 1; d < D; ++d)
-            if (k0 + d < k1) issue(k0 + d, &bars[d], false);
+        tma::mbar_expect_tx(&bars[0], A_BYTES + 4 * B_BYTES + 4 * C_BYTES + 2 * IT);
+        ldA(k0, &bars[0]);
+        for (int pl = k0 - 2; pl <= k0 + 1; ++pl) ldB(pl, &bars[0]);
+        for (int pl = k0 - 1; pl <= k0 + 2; ++pl) ldC(pl, &bars[0]);
+        ldI(k0, &bars[0]);
+        ldI(k0 + 1, &bars[0]);
     }
 
     const st::Dx ix = st::make_dx(p.inv_dx);
     const float dt = p.dt;
-    const int cv = (ty + 2) * VW + tx + 4;
+    const int cx = ty * XW + tx + 4;            // centre in x-halo boxes
+    const int cy = (ty + 2) * YW + tx;          // centre in y-halo boxes
+    const int cxy = (ty + 2) * VW + tx + 4;     // centre in the full-halo box
+    const int cz = tid;                         // centre in a plain box
     const int ci = ty * IW + tx;
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
+    float *__restrict__ vxg = p.vx;
+    float *__restrict__ vyg = p.vy;
+    float *__restrict__ vzg = p.vz;
+    const int plane = nx * ny, col = j * nx + i;
+    // velocities of the plane being computed, loaded one plane ahead
+    float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+    if (live) {
+        ux = vxg[k0 * plane + col];
+        uy = vyg[k0 * plane + col];
+        uz = vzg[k0 * plane + col];
+    }
+
+    // Ring positions of this thread's column, rotated once per plane (no
+    // modulo in the loop): A at plane k; B at planes k-2 .. k+1; C at
+    // k-1 .. k+2; index at k, k+1.  All float offsets except the index (bytes).
+    const int bbase = Lay::off_b / 4, bend = bbase + Lay::RB * Lay::SB;
+    const int cbase = Lay::off_c / 4, cend = cbase + Lay::RC * TZZ;
+    const int ibase = Lay::off_i, iend = ibase + Lay::RI * IT_SLOT;
+    int aK = Lay::off_a / 4 + cx, aO = Lay::off_a / 4 + Lay::SA + cx;   // sxx centre, both slots
+    int bM2 = bbase + cx, bM1 = bM2 + Lay::SB, bK = bM1 + Lay::SB, bP1 = bK + Lay::SB;
+    int cM1 = cbase + cz, cK = cM1 + TZZ, cP1 = cK + TZZ, cP2 = cP1 + TZZ;
+    int iK = ibase + ci, iK1 = iK + IT_SLOT;
+    const int dyy = TXX + cy - cx, dxy = TXX + TYY + cxy - cx;   // from the sxx centre
+    const int dyz = TXX + cy - cx;                                 // syz from the sxz centre
 
     int it = 0;
     for (int k = k0; k < k1; ++k, ++it) {
         __syncthreads();
-        if (tid == 0) {
-            if (it > 0) store_stage(k - 1);
-            if (k + D < k1) {
-                tma::bulk_wait_read<1>();
-                tma::fence_async_smem();
-                issue(k + D, &bars[(it + D) % (D + 1)], false);
-            }
+        if (tid == 0 && k + 1 < k1) {
+            tma::fence_async_smem();
+            uint64_t *bar = &bars[(it + 1) & 1];
+            tma::mbar_expect_tx(bar, A_BYTES + B_BYTES + C_BYTES + IT);
+            ldA(k + 1, bar);
+            ldB(k + 2, bar);
+            ldC(k + 3, bar);
+            ldI(k + 2, bar);
         }
-        const bool ready = tma::mbar_wait(&bars[it % (D + 1)], (it / (D + 1)) & 1, p.flag);
+        const int q = k * plane + col;
+        float nux = 0.0f, nuy = 0.0f, nuz = 0.0f;
+        if (live && k + 1 < k1) {
+            nux = vxg[q + plane];
+            nuy = vyg[q + plane];
+            nuz = vzg[q + plane];
+        }
+        const bool ready = tma::mbar_wait(&bars[it & 1], (it >> 1) & 1, p.flag);
         if (ready && live) {
-            const int s = oS(k) + tid;
-            const int a = oA(k) + cv;                 // sxx at a, syy at a + VT, sxy at a + 2 VT
-            const int bk = oB(k) + cv, bm2 = oB(k - 2) + cv, bm1 = oB(k - 1) + cv,
-                      bp1 = oB(k + 1) + cv;           // sxz at +0, syz at +VT
-            const unsigned char *I0 = smb + oI(k) + ci;
-            const unsigned char *I1 = smb + oI(k + 1) + ci;
+            const float *XX = smf + aK, *YY = smf + aK + dyy, *XY = smf + aK + dxy;
+            const float *XZ = smf + bK, *YZ = smf + bK + dyz;
+            const unsigned char *I0 = smb + iK, *I1 = smb + iK1;
             const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
             const int zs = slab_pos(k, nz, p.P);
             const float rho0 = s_rho[I0[0]];
             if (ix1) {
-                float d1 = dfw(smf[a - 1], smf[a], smf[a + 1], smf[a + 2], ix);
-                const int xy = a + 2 * VT;
-                float d2 = dbw(smf[xy - 2 * VW], smf[xy - VW], smf[xy], smf[xy + VW], ix);
-                float d3 = dbw(smf[bm2], smf[bm1], smf[bk], smf[bp1], ix);
+                float d1 = dfw(XX[-1], XX[0], XX[1], XX[2], ix);
+                float d2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
+                float d3 = dbw(smf[bM2], smf[bM1], XZ[0], smf[bP1], ix);
                 if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
-                smf[s] += st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
+                vxg[q] = ux + st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
             }
             if (jy1) {
-                const int xy = a + 2 * VT, yy = a + VT;
-                float d1 = dbw(smf[xy - 2], smf[xy - 1], smf[xy], smf[xy + 1], ix);
-                float d2 = dfw(smf[yy - VW], smf[yy], smf[yy + VW], smf[yy + 2 * VW], ix);
-                float d3 = dbw(smf[bm2 + VT], smf[bm1 + VT], smf[bk + VT], smf[bp1 + VT], ix);
+                float d1 = dbw(XY[-2], XY[-1], XY[0], XY[1], ix);
+                float d2 = dfw(YY[-YW], YY[0], YY[YW], YY[2 * YW], ix);
+                float d3 = dbw(smf[bM2 + dyz], smf[bM1 + dyz], YZ[0], smf[bP1 + dyz], ix);
                 if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
-                smf[s + NTH] += st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
+                vyg[q] = uy + st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
             }
             if (kz1) {
-                const int xz = bk, yz = bk + VT;
-                float d1 = dbw(smf[xz - 2], smf[xz - 1], smf[xz], smf[xz + 1], ix);
-                float d2 = dbw(smf[yz - 2 * VW], smf[yz - VW], smf[yz], smf[yz + VW], ix);
-                float d3 = dfw(smf[oC(k - 1) + cv], smf[oC(k) + cv], smf[oC(k + 1) + cv],
-                               smf[oC(k + 2) + cv], ix);
+                float d1 = dbw(XZ[-2], XZ[-1], XZ[0], XZ[1], ix);
+                float d2 = dbw(YZ[-2 * YW], YZ[-YW], YZ[0], YZ[YW], ix);
+                float d3 = dfw(smf[cM1], smf[cK], smf[cP1], smf[cP2], ix);
                 if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], d3);
-                smf[s + 2 * NTH] += st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
+                vzg[q] = uz + st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
             }
         }
-        tma::fence_async_smem();
-    }
-    __syncthreads();
-    if (tid == 0 && it > 0) {
-        store_stage(k1 - 1);
-        tma::bulk_wait<0>();
+        ux = nux;
+        uy = nuy;
+        uz = nuz;
+        // rotate the ring positions to plane k+1
+        { const int t = aK; aK = aO; aO = t; }
+        bM2 = bM1; bM1 = bK; bK = bP1; bP1 += Lay::SB; if (bP1 >= bend) bP1 -= Lay::RB * Lay::SB;
+        cM1 = cK; cK = cP1; cP1 = cP2; cP2 += TZZ; if (cP2 >= cend) cP2 -= Lay::RC * TZZ;
+        iK = iK1; iK1 += IT_SLOT; if (iK1 >= iend) iK1 -= Lay::RI * IT_SLOT;
     }
 }
 
@@ -251,6 +276,15 @@ __global__ void __launch_bounds__(NTH, MINB)
     float *const gs[6] = {p.sxx, p.syy, p.szz, p.sxy, p.sxz, p.syz};
     float *__restrict__ mem = p.mem;
 
+    // Ring positions of this thread's column, rotated once per plane: the
+    // velocity ring at planes k-2 .. k+2 (float offsets of the vx centre) and
+    // the index ring at k, k+1 (bytes).
+    const int vbase = Lay::off_v / 4, vend = vbase + Lay::RV * 3 * VT;
+    const int ibase = Lay::off_i, iend = ibase + Lay::RI * IT_SLOT;
+    int vM2 = vbase + cv, vM1 = vM2 + 3 * VT, vK = vM1 + 3 * VT, vP1 = vK + 3 * VT,
+        vP2 = vP1 + 3 * VT;
+    int iK = ibase + ci, iK1 = iK + IT_SLOT;
+
     int it = 0;
     for (int k = k0; k < k1; ++k, ++it) {
         __syncthreads();
@@ -279,16 +313,14 @@ __global__ void __launch_bounds__(NTH, MINB)
         }
         const bool ready = tma::mbar_wait(&bars[it % 3], (it / 3) & 1, p.flag);
         if (ready && live) {
-            const int v0 = oV(k) + cv;                       // vx at v0, vy v0 + VT, vz v0 + 2 VT
-            const int vm2 = oV(k - 2) + cv, vm1 = oV(k - 1) + cv, vp1 = oV(k + 1) + cv,
-                      vp2 = oV(k + 2) + cv;
-            const unsigned char *I0 = smb + oI(k) + ci;
-            const unsigned char *I1 = smb + oI(k + 1) + ci;
+            const int vm2 = vM2, vm1 = vM1, vp1 = vP1, vp2 = vP2;
+            const unsigned char *I0 = smb + iK;
+            const unsigned char *I1 = smb + iK1;
             const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
-            const int zs = slab_pos(k, nz, p.P);
+        const int zs = slab_pos(k, nz, p.P);
             const int m00 = I0[0];
             const st::StressCoef c0 = s_lut[m00];
-            const int vx = v0, vy = v0 + VT, vz = v0 + 2 * VT;
+            const int vx = vK, vy = vK + VT, vz = vK + 2 * VT;
 
             // ---- normal stresses at (i, j, k)
             float exx = dbw(smf[vx - 2], smf[vx - 1], smf[vx], smf[vx + 1], ix);
@@ -349,6 +381,13 @@ __global__ void __launch_bounds__(NTH, MINB)
                 p.dftS[q] = fma((double)pr, p.sw, dS);
             }
         }
+        // rotate the ring positions to plane k+1
+        vM2 = vM1; vM1 = vK; vK = vP1; vP1 = vP2;
+        vP2 += 3 * VT;
+        if (vP2 >= vend) vP2 -= Lay::RV * 3 * VT;
+        iK = iK1;
+        iK1 += IT_SLOT;
+        if (iK1 >= iend) iK1 -= Lay::RI * IT_SLOT;
     }
 }
 
@@ -359,23 +398,15 @@ static dim3 grid_tma(const AcParams &p, int kc)
     return dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + kc - 1) / kc);
 }
 
-template <int D>
-static cudaError_t launch_velocity_tma_t(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
-{
-    const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
-    const size_t sm = VelLayout<D>::bytes(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma<D>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_velocity_tma<D><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
-    return cudaGetLastError();
-}
-
-// One plane of lead (four resident blocks per SM) measures faster than two
-// planes of lead at three blocks per SM.
 cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
 {
-    return launch_velocity_tma_t<1>(p, tm, s);
+    const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
+    const size_t sm = VelLayout::bytes(p.n_mat);
+    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_velocity_tma<<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    return cudaGetLastError();
 }
 
 template <int L, int MINB>

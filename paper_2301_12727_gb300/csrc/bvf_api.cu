@@ -272,8 +272,11 @@ void setup_maps(bvf_ctx *c)
         ok = ok && encode_map(&c->smaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, F32, 4, 40, 12);
         ok = ok && encode_map(&c->vmaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, F32, 4, 32, 8);
     }
+    // velocity kernel boxes: the halo each stress array's stencil reads
+    const unsigned bw[6] = {40, 32, 32, 40, 40, 32}, bh[6] = {8, 12, 8, 12, 8, 12};
     for (int g6 = 0; g6 < 6; ++g6)
-        ok = ok && encode_map(&c->vmaps.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, F32, 4, 40, 12);
+        ok = ok && encode_map(&c->vmaps.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, F32, 4, bw[g6],
+                              bh[g6]);
     ok = ok && encode_map(&c->smaps.idx, c->index, nx, ny, nz, U8, 1, 48, 9);
     c->vmaps.idx = c->smaps.idx;
     c->tma = ok;

@@ -76,8 +76,9 @@ struct StressTmaMaps {
     CUtensorMap v[3];
     CUtensorMap idx;
 };
-// Velocity kernel: the six stresses (sxx, syy, szz, sxy, sxz, syz) with
-// 40 x 12 halo boxes; the velocities with 32 x 8 boxes; the material index.
+// Velocity kernel: the six stresses (sxx, syy, szz, sxy, sxz, syz), each with
+// a box holding the halo its stencil reads (40x8, 32x12, 32x8, 40x12, 40x8,
+// 32x12); the velocities with 32 x 8 boxes; the material index.
 struct VelocityTmaMaps {
     CUtensorMap sg[6];
     CUtensorMap v[3];
