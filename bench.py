@@ -27,7 +27,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FDTD Gvoxel-steps/s"
 UNIT = "Gvoxel-steps/s"
-WORKLOAD = "synthetic skull 240x240x200 dx0.5mm 500kHz 1500 steps, bowl 64/63 mm, water run, BHTE 40s/30%/80s"
+WORKLOAD = ("synthetic skull {nx}x{ny}x{nz} dx0.5mm 500kHz {steps} steps, bowl 64/63 mm, water run, "
+            "BHTE 40s/30%/80s")
+
+
+def workload(case):
+    return WORKLOAD.format(nx=case.nx, ny=case.ny, nz=case.nz, steps=case.n_steps)
 
 
 def parse():
@@ -48,6 +53,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(ms, pg, device="cpu"):
+    """Slowest rank's time (ms): the job is as fast as its last rank."""
+    if pg is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, units_per_step, ms):
+    """Units all ranks processed per second, in billions (each rank runs its
+    own plans: weak scaling)."""
+    return world * steps * units_per_step / (ms / 1e3) / 1e9
 
 
 def make_case(args, rank):
@@ -113,18 +134,30 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def stress_traffic_per_voxel(kernel_src, window_fraction):
+KERNEL_SOURCES = ("bvf_acoustic_tma.cu", "bvf_stencil.cuh", "bvf_tma.cuh", "bvf_internal.cuh")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fdtd_stress_velocity_skull160.md")
+
+
+def kernel_source_sha():
+    """Hash of every source the TMA FDTD kernels compile from."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2301_12727_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stress_traffic_per_voxel(window_fraction):
     """Measured DRAM bytes per voxel of the stress kernel, averaged over launches
     inside and outside the DFT window like the algorithmic bytes, from the
     committed ncu summary; None unless that summary was taken on the current
-    kernel source and holds both figures."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "stress_kernel.md")
+    kernel sources and holds both figures."""
     try:
-        text = open(path).read()
+        text = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    sha = kernel_source_sha()
     vals = {}
     for line in text.splitlines():
         if ":" in line and line.strip().startswith("- "):
@@ -191,7 +224,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec / max(len(times), 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "each step: %d FDTD steps on the full grid"
+            "config": {"workload": workload(case), "sample": "each step: %d FDTD steps on the full grid"
                        % times[-1]["steps"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"],
                              "kind": "oracle", "sample": base["sample"]},
@@ -251,12 +284,9 @@ def run_bvf(args):
     # thermal + auxiliary kernels are counted through the context counters;
     # the transmission reductions (3 kernels) and RS (1) per plan are context-free
     launches += args.steps * 4
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg, "cuda")
     vox_per_plan = res.voxel_steps
-    value = world * args.steps * vox_per_plan / (ms / 1e3) / 1e9
+    value = whole_job_rate(world, args.steps, vox_per_plan, ms)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -276,12 +306,8 @@ def run_bvf(args):
             out_cem.copy_(r.cem43, non_blocking=True)
         f1.record(stream)
         barrier()
-        ms_e2e = f0.elapsed_time(f1)
-        if pg:
-            t = torch.tensor([ms_e2e], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms_e2e = float(t.item())
-        e2e = {"value": world * args.steps * vox_per_plan / (ms_e2e / 1e3) / 1e9, "unit": UNIT,
+        ms_e2e = max_over_ranks(f0.elapsed_time(f1), pg, "cuda")
+        e2e = {"value": whole_job_rate(world, args.steps, vox_per_plan, ms_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(idx_host.numel()),
                "d2h_bytes_per_step": int(out_peak.numel() * 4 + out_tmax.numel() * 4
                                          + out_cem.numel() * 8)}
@@ -292,9 +318,7 @@ def run_bvf(args):
     stress_bytes = N * (165.0 * case.n_steps + 32.0 * case.dft_steps) * n_runs
     achieved = stress_bytes / (kt["stress_ms"] / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
-    tr = stress_traffic_per_voxel(os.path.join(ROOT, "paper_2301_12727_gb300", "csrc",
-                                               "bvf_acoustic_tma.cu"),
-                                  case.dft_steps / case.n_steps)
+    tr = stress_traffic_per_voxel(case.dft_steps / case.n_steps)
     vel_bytes = N * 49.0 * case.n_steps * n_runs
     roofline = {"bound": "hbm", "kernel": "k_stress_tma<2> (stress + SLS memory + source + capture)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -309,7 +333,7 @@ def run_bvf(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [case.nx, case.ny, case.nz],
+            "config": {"workload": workload(case), "grid": [case.nx, case.ny, case.nz],
                        "fdtd_steps": case.n_steps, "runs_per_step": 2, "n_sls": case.n_sls,
                        "n_pml": case.n_pml, "dft_cycles": case.dft_cycles,
                        "l2": "inputs larger than L2 (state %.0f MB per run)"

@@ -55,9 +55,11 @@ _lib = None
 
 
 def lib():
+    """The oracle library; BVF_ORACLE_LIB names another build of bvf_oracle.c
+    (used to check that the pins catch planted mistakes)."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(os.environ.get("BVF_ORACLE_LIB") or build())
         d = ctypes.c_double
         _lib.orc_courant_limit.restype = d
         _lib.orc_bowl_elements.restype = ctypes.c_long

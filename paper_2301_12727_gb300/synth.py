@@ -218,6 +218,11 @@ def skull_case(nx: int = 240, ny: int = 240, nz: int = 200, dx: float = 0.5e-3,
     index[(depth < 0) & (depth >= -3e-3)] = 2
     index[depth >= thick] = 1
     index[bone] = (3 + bins[bone]).astype(np.uint8)
+    if symmetric:
+        # exact mirror symmetry: copy the low half of each lateral axis onto the high half
+        hx, hy = nx // 2, ny // 2
+        index[:, :, nx - hx:] = index[:, :, :hx][:, :, ::-1]
+        index[:, ny - hy:, :] = index[:, :hy, :][:, ::-1, :]
     rows = [water_row(f0), brain_row(f0), skin_row(f0)]
     for b in range(n_bins):
         rows.append(bone_row_from_hu(300.0 + (b + 0.5) * width, f0))

@@ -101,8 +101,50 @@ def oneil_on_axis(z, a, R, k, p0):
     return p0 * np.abs(2.0 / (1.0 - z / R)) * np.abs(np.sin(k * (re - z) / 2.0))
 
 
+def oneil_on_axis_complex(z, a, R, k, p0):
+    """The on-axis Rayleigh integral of a spherical cap in closed form (the
+    e^{+i w t} convention): p(z) = p0 R/(R - z) (e^{-ikz} - e^{-i k r_e})."""
+    h = R - np.sqrt(R * R - a * a)
+    re = np.sqrt((z - h) ** 2 + a * a)
+    return p0 * R / (R - z) * (np.exp(-1j * k * z) - np.exp(-1j * k * re))
+
+
 def pennes_gaussian(r2, t, theta0, s0, D, wprime):
     """Pennes equation with uniform perfusion rate w' and no source, Gaussian
     initial excess: theta = theta0 (s0^2/(s0^2 + 2Dt))^(3/2) exp(-r^2/(2(s0^2+2Dt))) exp(-w' t)."""
     s2 = s0 * s0 + 2.0 * D * t
     return theta0 * (s0 * s0 / s2) ** 1.5 * np.exp(-r2 / (2.0 * s2)) * np.exp(-wprime * t)
+
+
+def lattice_wavenumber(omega, dt, dx, c):
+    """theta = k dx of the propagating mode of the staggered O(4) leapfrog
+    scheme: (2/dt) sin(w dt/2) = (2c/dx) (c1 sin(theta/2) + c2 sin(3 theta/2)),
+    the root below the maximum of the right side (bisection)."""
+    target = (2.0 / dt) * np.sin(omega * dt / 2.0) * dx / (2.0 * c)
+    g = lambda th: C1 * np.sin(th / 2) + C2 * np.sin(3 * th / 2) - target
+    # c1 sin(x) + c2 sin(3x) increases on [0, pi/2] for the O(4) coefficients
+    lo, hi = 0.0, np.pi
+    assert g(hi) > 0 >= g(lo)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if g(mid) > 0:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+def soft_source_far_field(S, d, omega, dt, dx, c):
+    """Far field of a soft pressure source on one plane of the staggered O(4)
+    leapfrog scheme in a homogeneous fluid (exact for the discrete scheme).
+
+    The source adds 2 c S/dx to the pressure rate of its plane at half steps
+    (complex amplitude S, e^{+i w t} convention).  Taking the lattice Fourier
+    transform along the axis, the pressure is P(theta) = i s Omega /
+    (c^2 K(theta)^2 - Omega^2) with Omega = (2/dt) sin(w dt/2); the outgoing
+    pole at the lattice wavenumber theta_d gives, |d| cells away,
+    P(d) = S e^{-i theta_d |d|} / (c1 cos(theta_d/2) + 3 c2 cos(3 theta_d/2))
+    (evanescent roots of the 4th-order stencil decay within a few cells)."""
+    th = lattice_wavenumber(omega, dt, dx, c)
+    g = C1 * np.cos(th / 2) + 3 * C2 * np.cos(3 * th / 2)
+    return S * np.exp(-1j * th * np.abs(d)) / g
