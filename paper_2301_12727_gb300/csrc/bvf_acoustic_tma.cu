@@ -29,7 +29,6 @@ namespace {
 
 using st::dbw;
 using st::dfw;
-using st::cpml;
 using st::slab_pos;
 
 constexpr int TX = 32, TY = 8, NTH = TX * TY;
@@ -164,39 +163,58 @@ __global__ void __launch_bounds__(NTH, 5)
             nuy = vyg[q + plane];
             nuz = vzg[q + plane];
         }
+        // CPML memories of this voxel (components 0-2 of each slab it lies
+        // in), all loads issued together before the ring wait
+        const int zs = slab_pos(k, nz, p.P);
+        const int ox = (k * ny + j) * p.W + xs, oy = (k * p.W + ys) * nx + i,
+                  oz = (zs * ny + j) * nx + i;
+        float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[3] = {0.0f, 0.0f, 0.0f};
+        if (live) {
+            if (xs >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qx[c] = p.psx[c * Sxs + ox];
+            }
+            if (ys >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qy[c] = p.psy[c * Sys + oy];
+            }
+            if (zs >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qz[c] = p.psz[c * Szs + oz];
+            }
+        }
         const bool ready = tma::mbar_wait(&bars[it & 1], (it >> 1) & 1, p.flag);
         if (ready && live) {
             const float *XX = smf + aK, *YY = smf + aK + dyy, *XY = smf + aK + dxy;
             const float *XZ = smf + bK, *YZ = smf + bK + dyz;
             const unsigned char *I0 = smb + iK, *I1 = smb + iK1;
             const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
-            const int zs = slab_pos(k, nz, p.P);
             const float rho0 = s_rho[I0[0]];
             if (ix1) {
                 float d1 = dfw(XX[-1], XX[0], XX[1], XX[2], ix);
                 float d2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
                 float d3 = dbw(smf[bM2], smf[bM1], XZ[0], smf[bP1], ix);
-                if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], d1);
-                if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
-                if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
+                if (xs >= 0) d1 = st::cpml_pre(p.psx + 0 * Sxs + ox, qx[0], __ldg(&pmlx[p.nmax + i]), d1);
+                if (ys >= 0) d2 = st::cpml_pre(p.psy + 0 * Sys + oy, qy[0], __ldg(&pmly[j]), d2);
+                if (zs >= 0) d3 = st::cpml_pre(p.psz + 0 * Szs + oz, qz[0], __ldg(&pmlz[k]), d3);
                 vxg[q] = ux + st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
             }
             if (jy1) {
                 float d1 = dbw(XY[-2], XY[-1], XY[0], XY[1], ix);
                 float d2 = dfw(YY[-YW], YY[0], YY[YW], YY[2 * YW], ix);
                 float d3 = dbw(smf[bM2 + dyz], smf[bM1 + dyz], YZ[0], smf[bP1 + dyz], ix);
-                if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
-                if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], d2);
-                if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + (zs * ny + j) * nx + i, pmlz[k], d3);
+                if (xs >= 0) d1 = st::cpml_pre(p.psx + 1 * Sxs + ox, qx[1], __ldg(&pmlx[i]), d1);
+                if (ys >= 0) d2 = st::cpml_pre(p.psy + 1 * Sys + oy, qy[1], __ldg(&pmly[p.nmax + j]), d2);
+                if (zs >= 0) d3 = st::cpml_pre(p.psz + 1 * Szs + oz, qz[1], __ldg(&pmlz[k]), d3);
                 vyg[q] = uy + st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
             }
             if (kz1) {
                 float d1 = dbw(XZ[-2], XZ[-1], XZ[0], XZ[1], ix);
                 float d2 = dbw(YZ[-2 * YW], YZ[-YW], YZ[0], YZ[YW], ix);
                 float d3 = dfw(smf[cM1], smf[cK], smf[cP1], smf[cP2], ix);
-                if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], d1);
-                if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + (k * p.W + ys) * nx + i, pmly[j], d2);
-                if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], d3);
+                if (xs >= 0) d1 = st::cpml_pre(p.psx + 2 * Sxs + ox, qx[2], __ldg(&pmlx[i]), d1);
+                if (ys >= 0) d2 = st::cpml_pre(p.psy + 2 * Sys + oy, qy[2], __ldg(&pmly[j]), d2);
+                if (zs >= 0) d3 = st::cpml_pre(p.psz + 2 * Szs + oz, qz[2], __ldg(&pmlz[p.nmax + k]), d3);
                 vzg[q] = uz + st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
             }
         }
@@ -298,6 +316,25 @@ __global__ void __launch_bounds__(NTH, MINB)
         float sv[6], rv[L > 0 ? L : 1][6];
         float pk = 0.0f;
         double dC = 0.0, dS = 0.0;
+        // CPML memories of this voxel (components 3-5 of each slab it lies in)
+        const int zs = slab_pos(k, nz, p.P);
+        const int ox = (k * ny + j) * p.W + xs, oy = (k * p.W + ys) * nx + i,
+                  oz = (zs * ny + j) * nx + i;
+        float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[3] = {0.0f, 0.0f, 0.0f};
+        if (live) {
+            if (xs >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qx[c] = p.psx[(3 + c) * Sxs + ox];
+            }
+            if (ys >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qy[c] = p.psy[(3 + c) * Sys + oy];
+            }
+            if (zs >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qz[c] = p.psz[(3 + c) * Szs + oz];
+            }
+        }
         if (live) {
 #pragma unroll
             for (int cc = 0; cc < 6; ++cc) sv[cc] = gs[cc][q];
@@ -317,7 +354,6 @@ __global__ void __launch_bounds__(NTH, MINB)
             const unsigned char *I0 = smb + iK;
             const unsigned char *I1 = smb + iK1;
             const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
-        const int zs = slab_pos(k, nz, p.P);
             const int m00 = I0[0];
             const st::StressCoef c0 = s_lut[m00];
             const int vx = vK, vy = vK + VT, vz = vK + 2 * VT;
@@ -326,9 +362,9 @@ __global__ void __launch_bounds__(NTH, MINB)
             float exx = dbw(smf[vx - 2], smf[vx - 1], smf[vx], smf[vx + 1], ix);
             float eyy = dbw(smf[vy - 2 * VW], smf[vy - VW], smf[vy], smf[vy + VW], ix);
             float ezz = dbw(smf[vm2 + 2 * VT], smf[vm1 + 2 * VT], smf[vz], smf[vp1 + 2 * VT], ix);
-            if (xs >= 0) exx = cpml(p.psx + 3 * Sxs + (k * ny + j) * p.W + xs, pmlx[i], exx);
-            if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + (k * p.W + ys) * nx + i, pmly[j], eyy);
-            if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + (zs * ny + j) * nx + i, pmlz[k], ezz);
+            if (xs >= 0) exx = st::cpml_pre(p.psx + 3 * Sxs + ox, qx[0], __ldg(&pmlx[i]), exx);
+            if (ys >= 0) eyy = st::cpml_pre(p.psy + 3 * Sys + oy, qy[0], __ldg(&pmly[j]), eyy);
+            if (zs >= 0) ezz = st::cpml_pre(p.psz + 3 * Szs + oz, qz[0], __ldg(&pmlz[k]), ezz);
             float srcv = 0.0f;
             if (p.src_on && k == p.k_src) {
                 const float2 a = p.src[j * nx + i];
@@ -343,22 +379,22 @@ __global__ void __launch_bounds__(NTH, MINB)
             if (dxy) {                               // sxy at (i+1/2, j+1/2, k)
                 float a = dfw(smf[vx - VW], smf[vx], smf[vx + VW], smf[vx + 2 * VW], ix);
                 float b = dfw(smf[vy - 1], smf[vy], smf[vy + 1], smf[vy + 2], ix);
-                if (ys >= 0) a = cpml(p.psy + 4 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], a);
-                if (xs >= 0) b = cpml(p.psx + 4 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
+                if (ys >= 0) a = st::cpml_pre(p.psy + 4 * Sys + oy, qy[1], __ldg(&pmly[p.nmax + j]), a);
+                if (xs >= 0) b = st::cpml_pre(p.psx + 4 * Sxs + ox, qx[1], __ldg(&pmlx[p.nmax + i]), b);
                 st::shear_update<L>(p, s_lut, c0, m00, I0[1], I0[IW], I0[IW + 1], a + b, 3, sv, rv);
             }
             if (dxz) {                               // sxz at (i+1/2, j, k+1/2)
                 float a = dfw(smf[vm1], smf[vx], smf[vp1], smf[vp2], ix);
                 float b = dfw(smf[vz - 1], smf[vz], smf[vz + 1], smf[vz + 2], ix);
-                if (zs >= 0) a = cpml(p.psz + 4 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
-                if (xs >= 0) b = cpml(p.psx + 5 * Sxs + (k * ny + j) * p.W + xs, pmlx[p.nmax + i], b);
+                if (zs >= 0) a = st::cpml_pre(p.psz + 4 * Szs + oz, qz[1], __ldg(&pmlz[p.nmax + k]), a);
+                if (xs >= 0) b = st::cpml_pre(p.psx + 5 * Sxs + ox, qx[2], __ldg(&pmlx[p.nmax + i]), b);
                 st::shear_update<L>(p, s_lut, c0, m00, I0[1], I1[0], I1[1], a + b, 4, sv, rv);
             }
             if (dyz) {                               // syz at (i, j+1/2, k+1/2)
                 float a = dfw(smf[vm1 + VT], smf[vy], smf[vp1 + VT], smf[vp2 + VT], ix);
                 float b = dfw(smf[vz - VW], smf[vz], smf[vz + VW], smf[vz + 2 * VW], ix);
-                if (zs >= 0) a = cpml(p.psz + 5 * Szs + (zs * ny + j) * nx + i, pmlz[p.nmax + k], a);
-                if (ys >= 0) b = cpml(p.psy + 5 * Sys + (k * p.W + ys) * nx + i, pmly[p.nmax + j], b);
+                if (zs >= 0) a = st::cpml_pre(p.psz + 5 * Szs + oz, qz[2], __ldg(&pmlz[p.nmax + k]), a);
+                if (ys >= 0) b = st::cpml_pre(p.psy + 5 * Sys + oy, qy[2], __ldg(&pmly[p.nmax + j]), b);
                 st::shear_update<L>(p, s_lut, c0, m00, I0[IW], I1[0], I1[IW], a + b, 5, sv, rv);
             }
 

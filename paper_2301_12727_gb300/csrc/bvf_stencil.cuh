@@ -46,6 +46,15 @@ __device__ __forceinline__ float cpml(float *__restrict__ psi, float2 ab, float 
     return d + v;
 }
 
+// The same recursion with psi already loaded (old): lets a kernel issue the
+// loads of all its CPML memories at once, ahead of the derivatives.
+__device__ __forceinline__ float cpml_pre(float *__restrict__ psi, float old, float2 ab, float d)
+{
+    const float v = fmaf(ab.x, d, ab.y * old);
+    *psi = v;
+    return d + v;
+}
+
 // Memory variables of one stress component, on registers:
 // r_l <- ca_l r_l - cb_l Theta ; returns sum_l (r_l^{n+1} + r_l^n).
 template <int L>

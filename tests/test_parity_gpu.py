@@ -72,11 +72,14 @@ def test_gpu_discrete_plane_wave_exact(bvf):
         s.close()
 
 
-def test_gpu_random_state_all_fields(bvf, orc):
+@pytest.mark.parametrize("nx,ny,nz", [(45, 38, 29), (48, 37, 29)])
+def test_gpu_random_state_all_fields(bvf, orc, nx, ny, nz):
     """Random velocities, stresses and memory variables in a heterogeneous
-    fluid/solid/SLS medium with CPML on a ragged grid (45 x 38 x 29, not a
-    multiple of the 32 x 8 tile): every state array after 12 steps."""
-    nx, ny, nz, dx = 45, 38, 29, 0.5e-3
+    fluid/solid/SLS medium with CPML on ragged grids, not multiples of the
+    32 x 8 tile: 45 x 38 x 29 runs the direct kernels, 48 x 37 x 29 (a
+    half x-tile, ragged y and z) the TMA-fed ones.  Every state array after
+    12 steps."""
+    dx = 0.5e-3
     rng = np.random.default_rng(11)
     mats = [mat_row(1000.0, 1500.0), mat_row(1850.0, 2800.0, 1500.0, 85.0, 170.0),
             mat_row(1700.0, 2300.0, 1200.0, 81.0, 162.0), mat_row(1041.0, 1562.0, 0.0, 3.45)]
@@ -110,6 +113,33 @@ def test_gpu_random_state_all_fields(bvf, orc):
     for i in range(n_state):
         got = s.field(i).cpu().numpy()
         assert rel_l2(got, A.state[i]) < 2e-5, (i, rel_l2(got, A.state[i]))
+
+
+def test_gpu_soft_source_matches_lattice_green_function(bvf):
+    """The GPU path against a closed form directly (no oracle): the captured
+    complex amplitude of a CW plane source, 4-12 cells on both sides of it,
+    equals the exact far field of the discrete scheme (phase convention,
+    half-step source time, whole-step capture, DFT sign and the lattice
+    amplitude factor 1.027 at 6 points per wavelength)."""
+    from paper_2301_12727_gb300 import synth
+    f0, dx = 5e5, 0.5e-3
+    n, nz, P, ks = 32, 120, 8, 40
+    dt, M = synth.choose_dt(dx, 1500.0, f0)
+    s = bvf.Solver(n, n, nz, dx, dt, f0, n_sls=0, n_pml=P)
+    s.set_materials(np.zeros((nz, n, n), np.uint8), [mat_row(1000.0, 1500.0)])
+    a0, phi = 2.0, 0.7
+    s.set_source(np.full((n, n), a0 * np.exp(1j * phi), np.complex64), ks, 1500.0,
+                 bvf.BVF_ENV_RAMP_CW)
+    nsteps = 10 * M
+    s.run(nsteps, dft_start=nsteps - 2 * M + 1, dft_steps=2 * M)
+    s.synchronize()
+    amp, ph = (t.cpu().numpy() for t in s.amp_phase())
+    w = 2 * np.pi * f0
+    for d in (-12, -8, -4, 4, 8, 12):
+        got = amp[ks + d, n // 2, n // 2] * np.exp(1j * ph[ks + d, n // 2, n // 2])
+        ref = an.soft_source_far_field(-1j * a0 * np.exp(1j * phi), d, w, dt, dx, 1500.0)
+        assert abs(abs(got) / abs(ref) - 1) < 3e-3, d
+        assert abs(np.angle(got / ref)) < 3e-3, d
 
 
 def test_gpu_slab_config_full(bvf, orc):
@@ -275,12 +305,14 @@ def test_gpu_run_twice_is_bitwise_identical(bvf):
         assert np.array_equal(a, b)
 
 
-def test_gpu_zchunk_invariance(bvf, monkeypatch):
+@pytest.mark.parametrize("nx", [50, 64])
+def test_gpu_zchunk_invariance(bvf, monkeypatch, nx):
     """The z-marching kernels split z into chunks per block; the per-voxel
     arithmetic does not depend on the split, so any chunk length gives the
-    same fields bit for bit (covers queue start-up at every chunk edge)."""
+    same fields bit for bit (covers queue start-up at every chunk edge), for
+    the direct kernels (nx = 50) and the TMA-fed ones (nx = 64)."""
     from paper_2301_12727_gb300 import synth
-    c = synth.skull_case(50, 41, 37, dx=0.5e-3, n_steps=90, aperture=16e-3, roc=16e-3, n_pml=5)
+    c = synth.skull_case(nx, 41, 37, dx=0.5e-3, n_steps=90, aperture=16e-3, roc=16e-3, n_pml=5)
     outs = []
     for kc in ("1", "3", "37", "0"):
         monkeypatch.setenv("BVF_KCHUNK", kc)
