@@ -42,20 +42,33 @@ constexpr int IT_SLOT = 512;                        // bytes per index slot
 // reads: sxx 40 x 8 (x-halo), syy 32 x 12 (y-halo), sxy 40 x 12, sxz 40 x 8,
 // syz 32 x 12, szz 32 x 8 (z only).  The velocities go straight to registers
 // and back.  Loads for plane k+1 are issued while plane k is computed.
+//
+// The plane loop is unrolled by the ring period R = 6 (every ring depth
+// divides it), so each unrolled copy reads fixed ring slots: every shared
+// memory access is one of five per-thread centres plus a constant.
 constexpr int XW = 40, XH = 8, YW = 32, YH = 12;             // x-halo / y-halo boxes
 constexpr int TXX = XW * XH, TYY = YW * YH, TXY = VW * VH, TZZ = TX * TY;
 struct VelLayout {
-    static constexpr int RA = 2, RB = 5, RC = 5, RI = 3;      // ring depths
+    static constexpr int R = 6;                               // ring period = unroll
+    static constexpr int RA = 2, RB = 6, RC = 6, RI = 3;      // ring depths (divide R)
     static constexpr int SA = TXX + TYY + TXY;                // floats per A slot (sxx, syy, sxy)
     static constexpr int SB = TXX + TYY;                      // B slot (sxz, syz)
     static constexpr int off_a = 0;                           // plane k, k+1
-    static constexpr int off_b = off_a + RA * SA * 4;         // k-2 .. k+2
-    static constexpr int off_c = off_b + RB * SB * 4;         // szz: k-1 .. k+3
+    static constexpr int off_b = off_a + RA * SA * 4;         // k-2 .. k+2 (+1 spare)
+    static constexpr int off_c = off_b + RB * SB * 4;         // szz: k-1 .. k+3 (+1 spare)
     static constexpr int off_i = off_c + RC * TZZ * 4;        // index: k .. k+2
     static constexpr int off_bar = off_i + RI * IT_SLOT;
     static constexpr int off_lut = off_bar + 16;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(float); }
 };
+static_assert(VelLayout::R % VelLayout::RA == 0 && VelLayout::R % VelLayout::RB == 0 &&
+                  VelLayout::R % VelLayout::RC == 0 && VelLayout::R % VelLayout::RI == 0,
+              "ring depths must divide the unroll period");
+static_assert(VelLayout::off_b % 128 == 0 && VelLayout::off_c % 128 == 0 &&
+                  VelLayout::off_i % 128 == 0 && (VelLayout::SA * 4) % 128 == 0 &&
+                  (VelLayout::SB * 4) % 128 == 0 && (TXX * 4) % 128 == 0 &&
+                  (TYY * 4) % 128 == 0,
+              "TMA destinations must stay 128-byte aligned");
 
 __global__ void __launch_bounds__(NTH, 5)
     k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
@@ -81,47 +94,51 @@ __global__ void __launch_bounds__(NTH, 5)
     }
     __syncthreads();
 
-    auto oA = [&](int pl) { return Lay::off_a / 4 + ((pl - k0) & 1) * Lay::SA; };
-    auto oB = [&](int pl) { return Lay::off_b / 4 + ((pl - k0 + 2) % Lay::RB) * Lay::SB; };
-    auto oC = [&](int pl) { return Lay::off_c / 4 + ((pl - k0 + 1) % Lay::RC) * TZZ; };
-    auto oI = [&](int pl) { return Lay::off_i + ((pl - k0) % Lay::RI) * IT_SLOT; };   // bytes
+    // ring slots: A holds plane pl in slot (pl-k0)%2, B in (pl-k0+2)%6,
+    // C in (pl-k0+1)%6, the index in (pl-k0)%3
     constexpr unsigned A_BYTES = Lay::SA * 4, B_BYTES = Lay::SB * 4, C_BYTES = TZZ * 4;
-    auto ldA = [&](int pl, uint64_t *bar) {
-        const int o = oA(pl);
-        tma::load3d(smf + o, &tm.sg[0], x0 - 4, y0, pl, bar);                    // sxx
-        tma::load3d(smf + o + TXX, &tm.sg[1], x0, y0 - 2, pl, bar);              // syy
-        tma::load3d(smf + o + TXX + TYY, &tm.sg[3], x0 - 4, y0 - 2, pl, bar);    // sxy
+    auto ldA = [&](int pl, int slot, uint64_t *bar) {
+        float *d = smf + Lay::off_a / 4 + slot * Lay::SA;
+        tma::load3d(d, &tm.sg[0], x0 - 4, y0, pl, bar);                    // sxx
+        tma::load3d(d + TXX, &tm.sg[1], x0, y0 - 2, pl, bar);              // syy
+        tma::load3d(d + TXX + TYY, &tm.sg[3], x0 - 4, y0 - 2, pl, bar);    // sxy
     };
-    auto ldB = [&](int pl, uint64_t *bar) {
-        const int o = oB(pl);
-        tma::load3d(smf + o, &tm.sg[4], x0 - 4, y0, pl, bar);                    // sxz
-        tma::load3d(smf + o + TXX, &tm.sg[5], x0, y0 - 2, pl, bar);              // syz
+    auto ldB = [&](int pl, int slot, uint64_t *bar) {
+        float *d = smf + Lay::off_b / 4 + slot * Lay::SB;
+        tma::load3d(d, &tm.sg[4], x0 - 4, y0, pl, bar);                    // sxz
+        tma::load3d(d + TXX, &tm.sg[5], x0, y0 - 2, pl, bar);              // syz
     };
-    auto ldC = [&](int pl, uint64_t *bar) { tma::load3d(smf + oC(pl), &tm.sg[2], x0, y0, pl, bar); };
-    auto ldI = [&](int pl, uint64_t *bar) { tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar); };
+    auto ldC = [&](int pl, int slot, uint64_t *bar) {
+        tma::load3d(smf + Lay::off_c / 4 + slot * TZZ, &tm.sg[2], x0, y0, pl, bar);
+    };
+    auto ldI = [&](int pl, int slot, uint64_t *bar) {
+        tma::load3d(smb + Lay::off_i + slot * IT_SLOT, &tm.idx, x0, y0, pl, bar);
+    };
 
     if (tid == 0) {
         tma::mbar_expect_tx(&bars[0], A_BYTES + 4 * B_BYTES + 4 * C_BYTES + 2 * IT);
-        ldA(k0, &bars[0]);
-        for (int pl = k0 - 2; pl <= k0 + 1; ++pl) ldB(pl, &bars[0]);
-        for (int pl = k0 - 1; pl <= k0 + 2; ++pl) ldC(pl, &bars[0]);
-        ldI(k0, &bars[0]);
-        ldI(k0 + 1, &bars[0]);
+        ldA(k0, 0, &bars[0]);
+        for (int d = 0; d < 4; ++d) ldB(k0 - 2 + d, d, &bars[0]);
+        for (int d = 0; d < 4; ++d) ldC(k0 - 1 + d, d, &bars[0]);
+        ldI(k0, 0, &bars[0]);
+        ldI(k0 + 1, 1, &bars[0]);
     }
 
     const st::Dx ix = st::make_dx(p.inv_dx);
     const float dt = p.dt;
-    const int cx = ty * XW + tx + 4;            // centre in x-halo boxes
-    const int cy = (ty + 2) * YW + tx;          // centre in y-halo boxes
-    const int cxy = (ty + 2) * VW + tx + 4;     // centre in the full-halo box
-    const int cz = tid;                         // centre in a plain box
-    const int ci = ty * IW + tx;
+    // per-thread centres inside a slot: x-halo box, y-halo box, full-halo box,
+    // plain box, index box
+    const int cx = ty * XW + tx + 4;
+    const int cy = (ty + 2) * YW + tx;
+    const int cxy = (ty + 2) * VW + tx + 4;
+    const int cI = ty * IW + tx;
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
     float *__restrict__ vxg = p.vx;
     float *__restrict__ vyg = p.vy;
     float *__restrict__ vzg = p.vz;
+    const bool ix1 = i < nx - 1, jy1 = j < ny - 1;
     const int plane = nx * ny, col = j * nx + i;
     // velocities of the plane being computed, loaded one plane ahead
     float ux = 0.0f, uy = 0.0f, uz = 0.0f;
@@ -130,102 +147,133 @@ __global__ void __launch_bounds__(NTH, 5)
         uy = vyg[k0 * plane + col];
         uz = vzg[k0 * plane + col];
     }
+    int q = k0 * plane + col;                       // this voxel in plane k
+    int ox = (k0 * ny + j) * p.W + xs;              // in the x-slab (xs >= 0)
+    int oy = (k0 * p.W + ys) * nx + i;              // in the y-slab (ys >= 0)
+    const int dox = ny * p.W, doy = p.W * nx;
 
-    // Ring positions of this thread's column, rotated once per plane (no
-    // modulo in the loop): A at plane k; B at planes k-2 .. k+1; C at
-    // k-1 .. k+2; index at k, k+1.  All float offsets except the index (bytes).
-    const int bbase = Lay::off_b / 4, bend = bbase + Lay::RB * Lay::SB;
-    const int cbase = Lay::off_c / 4, cend = cbase + Lay::RC * TZZ;
-    const int ibase = Lay::off_i, iend = ibase + Lay::RI * IT_SLOT;
-    int aK = Lay::off_a / 4 + cx, aO = Lay::off_a / 4 + Lay::SA + cx;   // sxx centre, both slots
-    int bM2 = bbase + cx, bM1 = bM2 + Lay::SB, bK = bM1 + Lay::SB, bP1 = bK + Lay::SB;
-    int cM1 = cbase + cz, cK = cM1 + TZZ, cP1 = cK + TZZ, cP2 = cP1 + TZZ;
-    int iK = ibase + ci, iK1 = iK + IT_SLOT;
-    const int dyy = TXX + cy - cx, dxy = TXX + TYY + cxy - cx;   // from the sxx centre
-    const int dyz = TXX + cy - cx;                                 // syz from the sxz centre
+    unsigned mpar = 0;                              // parity of (k - k0) / R
+    for (int kb = k0; kb < k1; kb += Lay::R, mpar ^= 1u) {
+#pragma unroll
+        for (int u = 0; u < Lay::R; ++u) {
+            const int k = kb + u;
+            if (k >= k1) break;
+            __syncthreads();
+            if (tid == 0 && k + 1 < k1) {
+                tma::fence_async_smem();
+                uint64_t *bar = &bars[(u + 1) & 1];
+                tma::mbar_expect_tx(bar, A_BYTES + B_BYTES + C_BYTES + IT);
+                ldA(k + 1, (u + 1) % Lay::RA, bar);
+                ldB(k + 2, (u + 4) % Lay::RB, bar);
+                ldC(k + 3, (u + 4) % Lay::RC, bar);
+                ldI(k + 2, (u + 2) % Lay::RI, bar);
+            }
+            float nux = 0.0f, nuy = 0.0f, nuz = 0.0f;
+            if (live && k + 1 < k1) {
+                nux = vxg[q + plane];
+                nuy = vyg[q + plane];
+                nuz = vzg[q + plane];
+            }
+            // CPML memories of this voxel (components 0-2 of each slab it lies
+            // in), all loads issued together before the ring wait
+            const int zs = slab_pos(k, nz, p.P);
+            const int oz = zs * plane + col;
+            float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f},
+                  qz[3] = {0.0f, 0.0f, 0.0f};
+            if (live) {
+                if (xs >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) qx[c] = p.psx[c * Sxs + ox];
+                }
+                if (ys >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) qy[c] = p.psy[c * Sys + oy];
+                }
+                if (zs >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) qz[c] = p.psz[c * Szs + oz];
+                }
+            }
+            const bool ready = tma::mbar_wait(&bars[u & 1], mpar ^ ((u >> 1) & 1u), p.flag);
+            if (ready && live) {
+                // fixed slots of this unrolled copy
+                const float *A = smf + Lay::off_a / 4 + (u % Lay::RA) * Lay::SA;
+                const float *XX = A + cx, *YY = A + TXX + cy, *XY = A + TXX + TYY + cxy;
+                const float *Bm2 = smf + Lay::off_b / 4 + ((u + 0) % Lay::RB) * Lay::SB;
+                const float *Bm1 = smf + Lay::off_b / 4 + ((u + 1) % Lay::RB) * Lay::SB;
+                const float *B0 = smf + Lay::off_b / 4 + ((u + 2) % Lay::RB) * Lay::SB;
+                const float *Bp1 = smf + Lay::off_b / 4 + ((u + 3) % Lay::RB) * Lay::SB;
+                const float *Cm1 = smf + Lay::off_c / 4 + ((u + 0) % Lay::RC) * TZZ + tid;
+                const float *C0 = smf + Lay::off_c / 4 + ((u + 1) % Lay::RC) * TZZ + tid;
+                const float *Cp1 = smf + Lay::off_c / 4 + ((u + 2) % Lay::RC) * TZZ + tid;
+                const float *Cp2 = smf + Lay::off_c / 4 + ((u + 3) % Lay::RC) * TZZ + tid;
+                const unsigned char *I0 = smb + Lay::off_i + (u % Lay::RI) * IT_SLOT + cI;
+                const unsigned char *I1 = smb + Lay::off_i + ((u + 1) % Lay::RI) * IT_SLOT + cI;
+                const float *XZ = B0 + cx, *YZ = B0 + TXX + cy;
+                const bool kz1 = k < nz - 1;
 
-    int it = 0;
-    for (int k = k0; k < k1; ++k, ++it) {
-        __syncthreads();
-        if (tid == 0 && k + 1 < k1) {
-            tma::fence_async_smem();
-            uint64_t *bar = &bars[(it + 1) & 1];
-            tma::mbar_expect_tx(bar, A_BYTES + B_BYTES + C_BYTES + IT);
-            ldA(k + 1, bar);
-            ldB(k + 2, bar);
-            ldC(k + 3, bar);
-            ldI(k + 2, bar);
+                // all three components are computed; ghost points (the last
+                // half point of each axis) are simply not stored
+                float ax1 = dfw(XX[-1], XX[0], XX[1], XX[2], ix);
+                float ax2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
+                float ax3 = dbw(Bm2[cx], Bm1[cx], XZ[0], Bp1[cx], ix);
+                float ay1 = dbw(XY[-2], XY[-1], XY[0], XY[1], ix);
+                float ay2 = dfw(YY[-YW], YY[0], YY[YW], YY[2 * YW], ix);
+                float ay3 = dbw(Bm2[TXX + cy], Bm1[TXX + cy], YZ[0], Bp1[TXX + cy], ix);
+                float az1 = dbw(XZ[-2], XZ[-1], XZ[0], XZ[1], ix);
+                float az2 = dbw(YZ[-2 * YW], YZ[-YW], YZ[0], YZ[YW], ix);
+                float az3 = dfw(*Cm1, *C0, *Cp1, *Cp2, ix);
+                if (xs >= 0) {
+                    const float2 h = __ldg(&pmlx[p.nmax + i]), w = __ldg(&pmlx[i]);
+                    float t = fmaf(h.x, ax1, h.y * qx[0]);
+                    if (ix1) p.psx[ox] = t;
+                    ax1 += t;
+                    t = fmaf(w.x, ay1, w.y * qx[1]);
+                    if (jy1) p.psx[Sxs + ox] = t;
+                    ay1 += t;
+                    t = fmaf(w.x, az1, w.y * qx[2]);
+                    if (kz1) p.psx[2 * Sxs + ox] = t;
+                    az1 += t;
+                }
+                if (ys >= 0) {
+                    const float2 h = __ldg(&pmly[p.nmax + j]), w = __ldg(&pmly[j]);
+                    float t = fmaf(w.x, ax2, w.y * qy[0]);
+                    if (ix1) p.psy[oy] = t;
+                    ax2 += t;
+                    t = fmaf(h.x, ay2, h.y * qy[1]);
+                    if (jy1) p.psy[Sys + oy] = t;
+                    ay2 += t;
+                    t = fmaf(w.x, az2, w.y * qy[2]);
+                    if (kz1) p.psy[2 * Sys + oy] = t;
+                    az2 += t;
+                }
+                if (zs >= 0) {
+                    const float2 h = __ldg(&pmlz[p.nmax + k]), w = __ldg(&pmlz[k]);
+                    float t = fmaf(w.x, ax3, w.y * qz[0]);
+                    if (ix1) p.psz[oz] = t;
+                    ax3 += t;
+                    t = fmaf(w.x, ay3, w.y * qz[1]);
+                    if (jy1) p.psz[Szs + oz] = t;
+                    ay3 += t;
+                    t = fmaf(h.x, az3, h.y * qz[2]);
+                    if (kz1) p.psz[2 * Szs + oz] = t;
+                    az3 += t;
+                }
+                const float rho0 = s_rho[I0[0]];
+                const float nvx = ux + st::vel_increment(dt, rho0, s_rho[I0[1]], ax1, ax2, ax3);
+                const float nvy = uy + st::vel_increment(dt, rho0, s_rho[I0[IW]], ay1, ay2, ay3);
+                const float nvz = uz + st::vel_increment(dt, rho0, s_rho[I1[0]], az1, az2, az3);
+                if (ix1) vxg[q] = nvx;
+                if (jy1) vyg[q] = nvy;
+                if (kz1) vzg[q] = nvz;
+            }
+            ux = nux;
+            uy = nuy;
+            uz = nuz;
+            q += plane;
+            ox += dox;
+            oy += doy;
         }
-        const int q = k * plane + col;
-        float nux = 0.0f, nuy = 0.0f, nuz = 0.0f;
-        if (live && k + 1 < k1) {
-            nux = vxg[q + plane];
-            nuy = vyg[q + plane];
-            nuz = vzg[q + plane];
-        }
-        // CPML memories of this voxel (components 0-2 of each slab it lies
-        // in), all loads issued together before the ring wait
-        const int zs = slab_pos(k, nz, p.P);
-        const int ox = (k * ny + j) * p.W + xs, oy = (k * p.W + ys) * nx + i,
-                  oz = (zs * ny + j) * nx + i;
-        float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[3] = {0.0f, 0.0f, 0.0f};
-        if (live) {
-            if (xs >= 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) qx[c] = p.psx[c * Sxs + ox];
-            }
-            if (ys >= 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) qy[c] = p.psy[c * Sys + oy];
-            }
-            if (zs >= 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) qz[c] = p.psz[c * Szs + oz];
-            }
-        }
-        const bool ready = tma::mbar_wait(&bars[it & 1], (it >> 1) & 1, p.flag);
-        if (ready && live) {
-            const float *XX = smf + aK, *YY = smf + aK + dyy, *XY = smf + aK + dxy;
-            const float *XZ = smf + bK, *YZ = smf + bK + dyz;
-            const unsigned char *I0 = smb + iK, *I1 = smb + iK1;
-            const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
-            const float rho0 = s_rho[I0[0]];
-            if (ix1) {
-                float d1 = dfw(XX[-1], XX[0], XX[1], XX[2], ix);
-                float d2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
-                float d3 = dbw(smf[bM2], smf[bM1], XZ[0], smf[bP1], ix);
-                if (xs >= 0) d1 = st::cpml_pre(p.psx + 0 * Sxs + ox, qx[0], __ldg(&pmlx[p.nmax + i]), d1);
-                if (ys >= 0) d2 = st::cpml_pre(p.psy + 0 * Sys + oy, qy[0], __ldg(&pmly[j]), d2);
-                if (zs >= 0) d3 = st::cpml_pre(p.psz + 0 * Szs + oz, qz[0], __ldg(&pmlz[k]), d3);
-                vxg[q] = ux + st::vel_increment(dt, rho0, s_rho[I0[1]], d1, d2, d3);
-            }
-            if (jy1) {
-                float d1 = dbw(XY[-2], XY[-1], XY[0], XY[1], ix);
-                float d2 = dfw(YY[-YW], YY[0], YY[YW], YY[2 * YW], ix);
-                float d3 = dbw(smf[bM2 + dyz], smf[bM1 + dyz], YZ[0], smf[bP1 + dyz], ix);
-                if (xs >= 0) d1 = st::cpml_pre(p.psx + 1 * Sxs + ox, qx[1], __ldg(&pmlx[i]), d1);
-                if (ys >= 0) d2 = st::cpml_pre(p.psy + 1 * Sys + oy, qy[1], __ldg(&pmly[p.nmax + j]), d2);
-                if (zs >= 0) d3 = st::cpml_pre(p.psz + 1 * Szs + oz, qz[1], __ldg(&pmlz[k]), d3);
-                vyg[q] = uy + st::vel_increment(dt, rho0, s_rho[I0[IW]], d1, d2, d3);
-            }
-            if (kz1) {
-                float d1 = dbw(XZ[-2], XZ[-1], XZ[0], XZ[1], ix);
-                float d2 = dbw(YZ[-2 * YW], YZ[-YW], YZ[0], YZ[YW], ix);
-                float d3 = dfw(smf[cM1], smf[cK], smf[cP1], smf[cP2], ix);
-                if (xs >= 0) d1 = st::cpml_pre(p.psx + 2 * Sxs + ox, qx[2], __ldg(&pmlx[i]), d1);
-                if (ys >= 0) d2 = st::cpml_pre(p.psy + 2 * Sys + oy, qy[2], __ldg(&pmly[j]), d2);
-                if (zs >= 0) d3 = st::cpml_pre(p.psz + 2 * Szs + oz, qz[2], __ldg(&pmlz[p.nmax + k]), d3);
-                vzg[q] = uz + st::vel_increment(dt, rho0, s_rho[I1[0]], d1, d2, d3);
-            }
-        }
-        ux = nux;
-        uy = nuy;
-        uz = nuz;
-        // rotate the ring positions to plane k+1
-        { const int t = aK; aK = aO; aO = t; }
-        bM2 = bM1; bM1 = bK; bK = bP1; bP1 += Lay::SB; if (bP1 >= bend) bP1 -= Lay::RB * Lay::SB;
-        cM1 = cK; cK = cP1; cP1 = cP2; cP2 += TZZ; if (cP2 >= cend) cP2 -= Lay::RC * TZZ;
-        iK = iK1; iK1 += IT_SLOT; if (iK1 >= iend) iK1 -= Lay::RI * IT_SLOT;
     }
 }
 
