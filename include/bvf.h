@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define BVF_VERSION 1
+#define BVF_VERSION 2
 
 #define BVF_OK 0
 #define BVF_E_ARG (-1)        /* NULL pointer, bad size, bad option, call order */
@@ -97,11 +97,24 @@ typedef struct {
 } bvf_material;
 
 /* Drive frequency f0 (Hz), attenuation correction q_c (Q = Q0 q_c, Sec. 3.2)
- * and number of SLS mechanisms (0 .. BVF_MAX_SLS; 0 = lossless). */
+ * and number of SLS mechanisms (0 .. BVF_MAX_SLS; 0 = lossless).
+ *
+ * storage selects how the acoustic state (velocities, stresses, memory
+ * variables) is held between steps; the arithmetic is FP32 either way.
+ * BVF_STORAGE_F16 halves the state's bytes: stresses are stored as
+ * sigma / p_ref, velocities as v rho_w c_w / p_ref (rho_w c_w = 1.5e6 Pa s/m),
+ * memory variables in matching units, each rounded to FP16.  p_ref (Pa, 0 =
+ * 1e5) should be near the largest pressure expected; FP16 keeps 11
+ * significant bits from 6e-5 p_ref to 6.5e4 p_ref.  Every accessor returns
+ * and takes physical units in FP32/FP64 regardless of storage.  FP16 storage
+ * is an extension beyond the paper, whose solvers run in FP32. */
+enum { BVF_STORAGE_F32 = 0, BVF_STORAGE_F16 = 1 };
 typedef struct {
     double f0;
     double qc;
     int n_sls;
+    int storage;
+    double p_ref;
 } bvf_physics;
 
 /* Single-element spherical bowl (Sec. 2, "Single"): aperture diameter and

@@ -47,8 +47,13 @@ class Material(ctypes.Structure):
                 ("rho", "cL", "cS", "alphaL", "alphaS", "k_th", "c_th", "perf", "heat_frac")]
 
 
+BVF_STORAGE_F32, BVF_STORAGE_F16 = 0, 1
+STORAGE = {"f32": BVF_STORAGE_F32, "f16": BVF_STORAGE_F16}
+
+
 class Physics(ctypes.Structure):
-    _fields_ = [("f0", ctypes.c_double), ("qc", ctypes.c_double), ("n_sls", ctypes.c_int)]
+    _fields_ = [("f0", ctypes.c_double), ("qc", ctypes.c_double), ("n_sls", ctypes.c_int),
+                ("storage", ctypes.c_int), ("p_ref", ctypes.c_double)]
 
 
 class Bowl(ctypes.Structure):
@@ -289,10 +294,14 @@ def bvf_get_kernel_times(ctx) -> KernelTimes:
 class Solver:
     """One libbvf context on the current CUDA device."""
 
-    def __init__(self, nx, ny, nz, dx, dt, f0, qc=1.0, n_sls=2, n_pml=8, pml_R=1e-4):
+    def __init__(self, nx, ny, nz, dx, dt, f0, qc=1.0, n_sls=2, n_pml=8, pml_R=1e-4,
+                 storage="f32", p_ref=0.0):
+        """storage "f32", or "f16" (scaled FP16 state, FP32 arithmetic; p_ref in Pa
+        near the largest expected pressure, 0 = 1e5)."""
         self.shape = (nz, ny, nx)
         self.grid = Grid(nx, ny, nz, dx, dt, n_pml, pml_R)
-        self.phys = Physics(f0, qc, n_sls)
+        self.phys = Physics(f0, qc, n_sls, STORAGE[storage], p_ref)
+        self.storage = storage
         self.n_sls = n_sls
         self.ctx = bvf_create(self.grid, self.phys)
 

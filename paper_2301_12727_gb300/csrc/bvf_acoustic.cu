@@ -90,16 +90,19 @@ __device__ __forceinline__ Geo make_geo(int nx, int ny, int nz)
 }
 
 // column value f(i, j, k), zero outside the grid
-__device__ __forceinline__ float colv(const float *__restrict__ f, const Geo &g, int k)
+template <typename T>
+__device__ __forceinline__ float colv(const T *__restrict__ f, const Geo &g, int k)
 {
-    return (g.live && k >= 0 && k < g.nz) ? __ldg(f + k * g.SZ + g.col) : 0.0f;
+    return (g.live && k >= 0 && k < g.nz) ? st::tof(__ldg(f + k * g.SZ + g.col)) : 0.0f;
 }
 // halo value of this thread's halo element at plane k, zero outside the grid
-__device__ __forceinline__ float halv(const float *__restrict__ f, const Geo &g, int k, bool want)
+template <typename T>
+__device__ __forceinline__ float halv(const T *__restrict__ f, const Geo &g, int k, bool want)
 {
-    return (want && g.hin && k >= 0 && k < g.nz) ? __ldg(f + k * g.SZ + g.hcol) : 0.0f;
+    return (want && g.hin && k >= 0 && k < g.nz) ? st::tof(__ldg(f + k * g.SZ + g.hcol)) : 0.0f;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
 {
     extern __shared__ __align__(16) float sm_v[];
@@ -111,29 +114,32 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
     const st::Dx ix = st::make_dx(p.inv_dx);
-    const float dt = p.dt;
+    const float dt = p.dtv;
     const int c = (g.ty + H) * SW + (g.tx + H);
     const int xs = slab_pos(g.i, nx, p.P), ys = slab_pos(g.j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
     const bool hx_ = g.hxstrip, hy_ = !g.hxstrip;
     const uint8_t *__restrict__ idx = p.idx;
-    float *__restrict__ vx = p.vx;
-    float *__restrict__ vy = p.vy;
-    float *__restrict__ vz = p.vz;
+    T *__restrict__ vx = static_cast<T *>(p.vx);
+    T *__restrict__ vy = static_cast<T *>(p.vy);
+    T *__restrict__ vz = static_cast<T *>(p.vz);
+    const T *sxx = static_cast<const T *>(p.sxx), *syy = static_cast<const T *>(p.syy);
+    const T *szz = static_cast<const T *>(p.szz), *sxy = static_cast<const T *>(p.sxy);
+    const T *sxz = static_cast<const T *>(p.sxz), *syz = static_cast<const T *>(p.syz);
 
     // z-queues: sxz, syz at k-2 .. k+1 ; szz at k-1 .. k+2
-    float bz0 = colv(p.sxz, g, k0 - 2), bz1 = colv(p.sxz, g, k0 - 1);
-    float bz2 = colv(p.sxz, g, k0), bz3 = colv(p.sxz, g, k0 + 1);
-    float cz0 = colv(p.syz, g, k0 - 2), cz1 = colv(p.syz, g, k0 - 1);
-    float cz2 = colv(p.syz, g, k0), cz3 = colv(p.syz, g, k0 + 1);
-    float dz0 = colv(p.szz, g, k0 - 1), dz1 = colv(p.szz, g, k0);
-    float dz2 = colv(p.szz, g, k0 + 1), dz3 = colv(p.szz, g, k0 + 2);
+    float bz0 = colv(sxz, g, k0 - 2), bz1 = colv(sxz, g, k0 - 1);
+    float bz2 = colv(sxz, g, k0), bz3 = colv(sxz, g, k0 + 1);
+    float cz0 = colv(syz, g, k0 - 2), cz1 = colv(syz, g, k0 - 1);
+    float cz2 = colv(syz, g, k0), cz3 = colv(syz, g, k0 + 1);
+    float dz0 = colv(szz, g, k0 - 1), dz1 = colv(szz, g, k0);
+    float dz2 = colv(szz, g, k0 + 1), dz3 = colv(szz, g, k0 + 2);
     // plane-k centres of the x/y-differenced arrays and this thread's halo values
-    float cxx = colv(p.sxx, g, k0), cyy = colv(p.syy, g, k0), cxy = colv(p.sxy, g, k0);
-    float hxx = halv(p.sxx, g, k0, hx_), hyy = halv(p.syy, g, k0, hy_);
-    float hxy = halv(p.sxy, g, k0, true), hxz = halv(p.sxz, g, k0, hx_);
-    float hyz = halv(p.syz, g, k0, hy_);
+    float cxx = colv(sxx, g, k0), cyy = colv(syy, g, k0), cxy = colv(sxy, g, k0);
+    float hxx = halv(sxx, g, k0, hx_), hyy = halv(syy, g, k0, hy_);
+    float hxy = halv(sxy, g, k0, true), hxz = halv(sxz, g, k0, hx_);
+    float hyz = halv(syz, g, k0, hy_);
     __syncthreads();
 
     for (int k = k0; k < k1; ++k) {
@@ -146,13 +152,13 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
         }
         __syncthreads();
         // loads for plane k+1, consumed in the next iteration
-        const float nbz = colv(p.sxz, g, k + 2), ncz = colv(p.syz, g, k + 2);
-        const float ndz = colv(p.szz, g, k + 3);
-        const float nxx = colv(p.sxx, g, k + 1), nyy = colv(p.syy, g, k + 1);
-        const float nxy = colv(p.sxy, g, k + 1);
-        const float nhxx = halv(p.sxx, g, k + 1, hx_), nhyy = halv(p.syy, g, k + 1, hy_);
-        const float nhxy = halv(p.sxy, g, k + 1, true), nhxz = halv(p.sxz, g, k + 1, hx_);
-        const float nhyz = halv(p.syz, g, k + 1, hy_);
+        const float nbz = colv(sxz, g, k + 2), ncz = colv(syz, g, k + 2);
+        const float ndz = colv(szz, g, k + 3);
+        const float nxx = colv(sxx, g, k + 1), nyy = colv(syy, g, k + 1);
+        const float nxy = colv(sxy, g, k + 1);
+        const float nhxx = halv(sxx, g, k + 1, hx_), nhyy = halv(syy, g, k + 1, hy_);
+        const float nhxy = halv(sxy, g, k + 1, true), nhxz = halv(sxz, g, k + 1, hx_);
+        const float nhyz = halv(syz, g, k + 1, hy_);
 
         if (g.live) {
             const int q = k * g.SZ + g.col;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
             // every global load of this voxel first
             const int m0 = __ldg(idx + q), mx = __ldg(idx + q + (ix1 ? 1 : 0));
             const int my = __ldg(idx + q + (jy1 ? nx : 0)), mz = __ldg(idx + q + (kz1 ? g.SZ : 0));
-            float ux = vx[q], uy = vy[q], uz = vz[q];
+            float ux = st::tof(vx[q]), uy = st::tof(vy[q]), uz = st::tof(vz[q]);
             const float rho0 = s_rho[m0];
             if (ix1) {
                 float d1 = dfw(txx[c - 1], txx[c], txx[c + 1], txx[c + 2], ix);
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + qz, pmlz[k], d3);
                 ux += st::vel_increment(dt, rho0, s_rho[mx], d1, d2, d3);
-                vx[q] = ux;
+                st::stv(vx + q, ux);
             }
             if (jy1) {
                 float d1 = dbw(txy[c - 2], txy[c - 1], txy[c], txy[c + 1], ix);
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + qy, pmly[p.nmax + g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + qz, pmlz[k], d3);
                 uy += st::vel_increment(dt, rho0, s_rho[my], d1, d2, d3);
-                vy[q] = uy;
+                st::stv(vy + q, uy);
             }
             if (kz1) {
                 float d1 = dbw(txz[c - 2], txz[c - 1], txz[c], txz[c + 1], ix);
@@ -194,7 +200,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + qz, pmlz[p.nmax + k], d3);
                 uz += st::vel_increment(dt, rho0, s_rho[mz], d1, d2, d3);
-                vz[q] = uz;
+                st::stv(vz + q, uz);
             }
         }
         bz0 = bz1; bz1 = bz2; bz2 = bz3; bz3 = nbz;
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
     }
 }
 
-template <int L>
+template <int L, typename T>
 __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int kchunk)
 {
     extern __shared__ __align__(16) float sm_s[];
@@ -222,19 +228,22 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
     const uint8_t *__restrict__ idx = p.idx;
-    float *__restrict__ mem = p.mem;
+    T *__restrict__ mem = static_cast<T *>(p.mem);
+    const T *vxg = static_cast<const T *>(p.vx), *vyg = static_cast<const T *>(p.vy);
+    const T *vzg = static_cast<const T *>(p.vz);
     float *__restrict__ peak = p.peak;
-    float *const sig[6] = {p.sxx, p.syy, p.szz, p.sxy, p.sxz, p.syz};
+    T *const sig[6] = {static_cast<T *>(p.sxx), static_cast<T *>(p.syy), static_cast<T *>(p.szz),
+                       static_cast<T *>(p.sxy), static_cast<T *>(p.sxz), static_cast<T *>(p.syz)};
 
     // z-queues: vx, vy at k-1 .. k+2 ; vz at k-2 .. k+1
-    float ax0 = colv(p.vx, g, k0 - 1), ax1 = colv(p.vx, g, k0);
-    float ax2 = colv(p.vx, g, k0 + 1), ax3 = colv(p.vx, g, k0 + 2);
-    float ay0 = colv(p.vy, g, k0 - 1), ay1 = colv(p.vy, g, k0);
-    float ay2 = colv(p.vy, g, k0 + 1), ay3 = colv(p.vy, g, k0 + 2);
-    float az0 = colv(p.vz, g, k0 - 2), az1 = colv(p.vz, g, k0 - 1);
-    float az2 = colv(p.vz, g, k0), az3 = colv(p.vz, g, k0 + 1);
-    float hvx = halv(p.vx, g, k0, true), hvy = halv(p.vy, g, k0, true);
-    float hvz = halv(p.vz, g, k0, true);
+    float ax0 = colv(vxg, g, k0 - 1), ax1 = colv(vxg, g, k0);
+    float ax2 = colv(vxg, g, k0 + 1), ax3 = colv(vxg, g, k0 + 2);
+    float ay0 = colv(vyg, g, k0 - 1), ay1 = colv(vyg, g, k0);
+    float ay2 = colv(vyg, g, k0 + 1), ay3 = colv(vyg, g, k0 + 2);
+    float az0 = colv(vzg, g, k0 - 2), az1 = colv(vzg, g, k0 - 1);
+    float az2 = colv(vzg, g, k0), az3 = colv(vzg, g, k0 + 1);
+    float hvx = halv(vxg, g, k0, true), hvy = halv(vyg, g, k0, true);
+    float hvz = halv(vzg, g, k0, true);
     __syncthreads();
 
     for (int k = k0; k < k1; ++k) {
@@ -243,10 +252,10 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
         tvx[c] = ax1; tvy[c] = ay1; tvz[c] = az2;
         if (g.hal) { tvx[g.hslot] = hvx; tvy[g.hslot] = hvy; tvz[g.hslot] = hvz; }
         __syncthreads();
-        const float nax = colv(p.vx, g, k + 3), nay = colv(p.vy, g, k + 3);
-        const float naz = colv(p.vz, g, k + 2);
-        const float nhx = halv(p.vx, g, k + 1, true), nhy = halv(p.vy, g, k + 1, true);
-        const float nhz = halv(p.vz, g, k + 1, true);
+        const float nax = colv(vxg, g, k + 3), nay = colv(vyg, g, k + 3);
+        const float naz = colv(vzg, g, k + 2);
+        const float nhx = halv(vxg, g, k + 1, true), nhy = halv(vyg, g, k + 1, true);
+        const float nhz = halv(vzg, g, k + 1, true);
 
         if (g.live) {
             const int q = k * g.SZ + g.col;
@@ -263,11 +272,12 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
             const int mzy = __ldg(idx + q + oy + oz);
             float sv[6], rv[L > 0 ? L : 1][6];
 #pragma unroll
-            for (int cc = 0; cc < 6; ++cc) sv[cc] = sig[cc][q];
+            for (int cc = 0; cc < 6; ++cc) sv[cc] = st::tof(sig[cc][q]);
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
-                for (int cc = 0; cc < 6; ++cc) rv[l][cc] = mem[(size_t)(l * 6 + cc) * p.fstride + q];
+                for (int cc = 0; cc < 6; ++cc)
+                    rv[l][cc] = st::tof(mem[(size_t)(l * 6 + cc) * p.fstride + q]);
             const float pk = p.do_peak ? peak[q] : 0.0f;
             double dC = 0.0, dS = 0.0;
             if (p.do_dft) { dC = p.dftC[q]; dS = p.dftS[q]; }
@@ -318,16 +328,16 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
 
             // ---- stores
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) sig[cc][q] = sv[cc];
-            if (dxy) sig[3][q] = sv[3];
-            if (dxz) sig[4][q] = sv[4];
-            if (dyz) sig[5][q] = sv[5];
+            for (int cc = 0; cc < 3; ++cc) st::stv(sig[cc] + q, sv[cc]);
+            if (dxy) st::stv(sig[3] + q, sv[3]);
+            if (dxz) st::stv(sig[4] + q, sv[4]);
+            if (dyz) st::stv(sig[5] + q, sv[5]);
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) {
                     const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
-                    if (w) mem[(size_t)(l * 6 + cc) * p.fstride + q] = rv[l][cc];
+                    if (w) st::stv(mem + (size_t)(l * 6 + cc) * p.fstride + q, rv[l][cc]);
                 }
             if (p.do_peak) peak[q] = fmaxf(pk, fabsf(pr));
             if (p.do_dft) {
@@ -366,7 +376,25 @@ cudaError_t launch_velocity(const AcParams &p, cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk(p.nx, p.ny, p.nz);
     const size_t sm = ((p.n_mat + 3) & ~3) * sizeof(float) + 2 * 5 * TILE * sizeof(float);
-    k_velocity<<<grid_of(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc);
+    if (p.h16)
+        k_velocity<__half><<<grid_of(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc);
+    else
+        k_velocity<float><<<grid_of(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_stress_t(const AcParams &p, int kc, dim3 grd, dim3 blk, size_t sm,
+                                   cudaStream_t s)
+{
+    switch (p.L) {
+    case 0: k_stress<0, T><<<grd, blk, sm, s>>>(p, kc); break;
+    case 1: k_stress<1, T><<<grd, blk, sm, s>>>(p, kc); break;
+    case 2: k_stress<2, T><<<grd, blk, sm, s>>>(p, kc); break;
+    case 3: k_stress<3, T><<<grd, blk, sm, s>>>(p, kc); break;
+    case 4: k_stress<4, T><<<grd, blk, sm, s>>>(p, kc); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -375,15 +403,8 @@ cudaError_t launch_stress(const AcParams &p, cudaStream_t s)
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk(p.nx, p.ny, p.nz);
     const size_t sm = p.n_mat * sizeof(st::StressCoef) + 2 * 3 * TILE * sizeof(float);
     const dim3 grd = grid_of(p, kc), blk(TX, TY, 1);
-    switch (p.L) {
-    case 0: k_stress<0><<<grd, blk, sm, s>>>(p, kc); break;
-    case 1: k_stress<1><<<grd, blk, sm, s>>>(p, kc); break;
-    case 2: k_stress<2><<<grd, blk, sm, s>>>(p, kc); break;
-    case 3: k_stress<3><<<grd, blk, sm, s>>>(p, kc); break;
-    case 4: k_stress<4><<<grd, blk, sm, s>>>(p, kc); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    return p.h16 ? launch_stress_t<__half>(p, kc, grd, blk, sm, s)
+                 : launch_stress_t<float>(p, kc, grd, blk, sm, s);
 }
 
 }  // namespace bvf

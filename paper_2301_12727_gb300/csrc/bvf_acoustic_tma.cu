@@ -3,10 +3,10 @@
 // Same arithmetic as the direct kernels in bvf_acoustic.cu, but every array
 // moves between HBM and shared memory through the tensor-memory accelerator:
 //   * a block of 32 x 8 threads owns one x-y tile and walks a chunk of z;
-//   * stencil inputs arrive as 40 x 12 boxes (the tile plus a 4-column /
-//     2-row halo; out-of-range elements zero-filled by the TMA, which gives
-//     the zero ghosts) held in per-array rings of z-planes that serve the
-//     4-point z-stencils as well;
+//   * stencil inputs arrive as halo'd boxes (the tile plus XO columns on each
+//     side in x and 2 rows in y; out-of-range elements zero-filled by the TMA,
+//     which gives the zero ghosts) held in per-array rings of z-planes that
+//     serve the 4-point z-stencils as well;
 //   * the 1-byte material index arrives as 48 x 9 boxes (planes k and k+1);
 //   * velocity kernel: each stress array arrives in a box with exactly the
 //     halo its stencil needs; the velocities go straight to registers and
@@ -18,8 +18,13 @@
 //     four resident blocks per SM;
 //   * one thread issues every copy; one __syncthreads and one bounded mbarrier
 //     wait per plane.
+// The state is stored as T = float or __half (scaled FP16 storage; the
+// arithmetic is FP32 either way).  A TMA box must start on a 16-byte boundary
+// in x, so the x-halo is XO = 16 / sizeof(T) columns: 4 floats or 8 halves.
 // Used when rows are whole multiples of 16 bytes of the index (nx % 16 == 0)
 // and L <= 2.
+#include <cuda_fp16.h>
+
 #include "bvf_stencil.cuh"
 #include "bvf_tma.cuh"
 
@@ -30,55 +35,69 @@ namespace {
 using st::dbw;
 using st::dfw;
 using st::slab_pos;
+using st::tof;
 
 constexpr int TX = 32, TY = 8, NTH = TX * TY;
-constexpr int VW = 40, VH = 12, VT = VW * VH;       // halo'd box: x0-4 .. x0+35, y0-2 .. y0+9
-constexpr unsigned VT_BYTES = VT * 4;               // 1920 = 15 * 128
 constexpr int IW = 48, IH = 9, IT = IW * IH;        // index box: x0 .. x0+47, y0 .. y0+8
 constexpr int IT_SLOT = 512;                        // bytes per index slot
 
+// Box geometry of a storage type: x-halo XO columns each side, so halo'd
+// boxes are BW = 32 + 2 XO wide (40 floats / 48 halves = 160 / 96 bytes).
+template <typename T>
+struct Box {
+    static constexpr int XO = 16 / (int)sizeof(T);
+    static constexpr int BW = TX + 2 * XO;
+    static constexpr int VH = TY + 4;                 // 2 rows each side
+    static constexpr int VT = BW * VH;                // full-halo box (elements)
+};
+
 // ---------------------------------------------------------------- velocity
-// Each stress array arrives in a box holding exactly the halo its stencil
-// reads: sxx 40 x 8 (x-halo), syy 32 x 12 (y-halo), sxy 40 x 12, sxz 40 x 8,
+// Each stress array arrives in a box holding the halo its stencil reads:
+// sxx BW x 8 (x-halo), syy 32 x 12 (y-halo), sxy BW x 12, sxz BW x 8,
 // syz 32 x 12, szz 32 x 8 (z only).  The velocities go straight to registers
 // and back.  Loads for plane k+1 are issued while plane k is computed.
 //
 // The plane loop is unrolled by the ring period R = 6 (every ring depth
 // divides it), so each unrolled copy reads fixed ring slots: every shared
 // memory access is one of five per-thread centres plus a constant.
-constexpr int XW = 40, XH = 8, YW = 32, YH = 12;             // x-halo / y-halo boxes
-constexpr int TXX = XW * XH, TYY = YW * YH, TXY = VW * VH, TZZ = TX * TY;
+template <typename T>
 struct VelLayout {
+    using B = Box<T>;
     static constexpr int R = 6;                               // ring period = unroll
     static constexpr int RA = 2, RB = 6, RC = 6, RI = 3;      // ring depths (divide R)
-    static constexpr int SA = TXX + TYY + TXY;                // floats per A slot (sxx, syy, sxy)
+    static constexpr int XW = B::BW, XH = TY, YW = TX, YH = TY + 4;
+    static constexpr int TXX = XW * XH, TYY = YW * YH, TXY = B::VT, TZZ = TX * TY;
+    static constexpr int SA = TXX + TYY + TXY;                // elements per A slot (sxx, syy, sxy)
     static constexpr int SB = TXX + TYY;                      // B slot (sxz, syz)
-    static constexpr int off_a = 0;                           // plane k, k+1
-    static constexpr int off_b = off_a + RA * SA * 4;         // k-2 .. k+2 (+1 spare)
-    static constexpr int off_c = off_b + RB * SB * 4;         // szz: k-1 .. k+3 (+1 spare)
-    static constexpr int off_i = off_c + RC * TZZ * 4;        // index: k .. k+2
+    static constexpr int ES = (int)sizeof(T);
+    static constexpr int off_a = 0;                           // bytes; plane k, k+1
+    static constexpr int off_b = off_a + RA * SA * ES;        // k-2 .. k+2 (+1 spare)
+    static constexpr int off_c = off_b + RB * SB * ES;        // szz: k-1 .. k+3 (+1 spare)
+    static constexpr int off_i = off_c + RC * TZZ * ES;       // index: k .. k+2
     static constexpr int off_bar = off_i + RI * IT_SLOT;
     static constexpr int off_lut = off_bar + 16;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(float); }
+    static_assert(R % RA == 0 && R % RB == 0 && R % RC == 0 && R % RI == 0,
+                  "ring depths must divide the unroll period");
+    static_assert(off_b % 128 == 0 && off_c % 128 == 0 && off_i % 128 == 0 &&
+                      (SA * ES) % 128 == 0 && (SB * ES) % 128 == 0 && (TXX * ES) % 128 == 0 &&
+                      (TYY * ES) % 128 == 0 && (TZZ * ES) % 128 == 0,
+                  "TMA destinations must stay 128-byte aligned");
 };
-static_assert(VelLayout::R % VelLayout::RA == 0 && VelLayout::R % VelLayout::RB == 0 &&
-                  VelLayout::R % VelLayout::RC == 0 && VelLayout::R % VelLayout::RI == 0,
-              "ring depths must divide the unroll period");
-static_assert(VelLayout::off_b % 128 == 0 && VelLayout::off_c % 128 == 0 &&
-                  VelLayout::off_i % 128 == 0 && (VelLayout::SA * 4) % 128 == 0 &&
-                  (VelLayout::SB * 4) % 128 == 0 && (TXX * 4) % 128 == 0 &&
-                  (TYY * 4) % 128 == 0,
-              "TMA destinations must stay 128-byte aligned");
 
+template <typename T>
 __global__ void __launch_bounds__(NTH, 5)
     k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
                    const __grid_constant__ VelocityTmaMaps tm)
 {
-    using Lay = VelLayout;
-    extern __shared__ __align__(1024) float smf[];
-    unsigned char *smb = reinterpret_cast<unsigned char *>(smf);
+    using Lay = VelLayout<T>;
+    using Bx = Box<T>;
+    constexpr int XW = Lay::XW, YW = Lay::YW, VW = Bx::BW;
+    constexpr int TXX = Lay::TXX, TYY = Lay::TYY, TZZ = Lay::TZZ;
+    extern __shared__ __align__(1024) unsigned char smb[];
+    const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
-    float *s_rho = smf + Lay::off_lut / 4;
+    float *s_rho = reinterpret_cast<float *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -96,20 +115,21 @@ __global__ void __launch_bounds__(NTH, 5)
 
     // ring slots: A holds plane pl in slot (pl-k0)%2, B in (pl-k0+2)%6,
     // C in (pl-k0+1)%6, the index in (pl-k0)%3
-    constexpr unsigned A_BYTES = Lay::SA * 4, B_BYTES = Lay::SB * 4, C_BYTES = TZZ * 4;
+    constexpr unsigned A_BYTES = Lay::SA * Lay::ES, B_BYTES = Lay::SB * Lay::ES;
+    constexpr unsigned C_BYTES = TZZ * Lay::ES;
     auto ldA = [&](int pl, int slot, uint64_t *bar) {
-        float *d = smf + Lay::off_a / 4 + slot * Lay::SA;
-        tma::load3d(d, &tm.sg[0], x0 - 4, y0, pl, bar);                    // sxx
-        tma::load3d(d + TXX, &tm.sg[1], x0, y0 - 2, pl, bar);              // syy
-        tma::load3d(d + TXX + TYY, &tm.sg[3], x0 - 4, y0 - 2, pl, bar);    // sxy
+        unsigned char *d = smb + Lay::off_a + slot * A_BYTES;
+        tma::load3d(d, &tm.sg[0], x0 - Bx::XO, y0, pl, bar);                            // sxx
+        tma::load3d(d + TXX * Lay::ES, &tm.sg[1], x0, y0 - 2, pl, bar);                  // syy
+        tma::load3d(d + (TXX + TYY) * Lay::ES, &tm.sg[3], x0 - Bx::XO, y0 - 2, pl, bar); // sxy
     };
     auto ldB = [&](int pl, int slot, uint64_t *bar) {
-        float *d = smf + Lay::off_b / 4 + slot * Lay::SB;
-        tma::load3d(d, &tm.sg[4], x0 - 4, y0, pl, bar);                    // sxz
-        tma::load3d(d + TXX, &tm.sg[5], x0, y0 - 2, pl, bar);              // syz
+        unsigned char *d = smb + Lay::off_b + slot * B_BYTES;
+        tma::load3d(d, &tm.sg[4], x0 - Bx::XO, y0, pl, bar);                            // sxz
+        tma::load3d(d + TXX * Lay::ES, &tm.sg[5], x0, y0 - 2, pl, bar);                  // syz
     };
     auto ldC = [&](int pl, int slot, uint64_t *bar) {
-        tma::load3d(smf + Lay::off_c / 4 + slot * TZZ, &tm.sg[2], x0, y0, pl, bar);
+        tma::load3d(smb + Lay::off_c + slot * C_BYTES, &tm.sg[2], x0, y0, pl, bar);
     };
     auto ldI = [&](int pl, int slot, uint64_t *bar) {
         tma::load3d(smb + Lay::off_i + slot * IT_SLOT, &tm.idx, x0, y0, pl, bar);
@@ -125,27 +145,27 @@ __global__ void __launch_bounds__(NTH, 5)
     }
 
     const st::Dx ix = st::make_dx(p.inv_dx);
-    const float dt = p.dt;
-    // per-thread centres inside a slot: x-halo box, y-halo box, full-halo box,
-    // plain box, index box
-    const int cx = ty * XW + tx + 4;
+    const float dt = p.dtv;
+    // per-thread centres inside a slot (elements): x-halo box, y-halo box,
+    // full-halo box, plain box; index box (bytes)
+    const int cx = ty * XW + tx + Bx::XO;
     const int cy = (ty + 2) * YW + tx;
-    const int cxy = (ty + 2) * VW + tx + 4;
+    const int cxy = (ty + 2) * VW + tx + Bx::XO;
     const int cI = ty * IW + tx;
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
-    float *__restrict__ vxg = p.vx;
-    float *__restrict__ vyg = p.vy;
-    float *__restrict__ vzg = p.vz;
+    T *__restrict__ vxg = static_cast<T *>(p.vx);
+    T *__restrict__ vyg = static_cast<T *>(p.vy);
+    T *__restrict__ vzg = static_cast<T *>(p.vz);
     const bool ix1 = i < nx - 1, jy1 = j < ny - 1;
     const int plane = nx * ny, col = j * nx + i;
     // velocities of the plane being computed, loaded one plane ahead
     float ux = 0.0f, uy = 0.0f, uz = 0.0f;
     if (live) {
-        ux = vxg[k0 * plane + col];
-        uy = vyg[k0 * plane + col];
-        uz = vzg[k0 * plane + col];
+        ux = tof(vxg[k0 * plane + col]);
+        uy = tof(vyg[k0 * plane + col]);
+        uz = tof(vzg[k0 * plane + col]);
     }
     int q = k0 * plane + col;                       // this voxel in plane k
     int ox = (k0 * ny + j) * p.W + xs;              // in the x-slab (xs >= 0)
@@ -170,9 +190,9 @@ __global__ void __launch_bounds__(NTH, 5)
             }
             float nux = 0.0f, nuy = 0.0f, nuz = 0.0f;
             if (live && k + 1 < k1) {
-                nux = vxg[q + plane];
-                nuy = vyg[q + plane];
-                nuz = vzg[q + plane];
+                nux = tof(vxg[q + plane]);
+                nuy = tof(vyg[q + plane]);
+                nuz = tof(vzg[q + plane]);
             }
             // CPML memories of this voxel (components 0-2 of each slab it lies
             // in), all loads issued together before the ring wait
@@ -197,32 +217,33 @@ __global__ void __launch_bounds__(NTH, 5)
             const bool ready = tma::mbar_wait(&bars[u & 1], mpar ^ ((u >> 1) & 1u), p.flag);
             if (ready && live) {
                 // fixed slots of this unrolled copy
-                const float *A = smf + Lay::off_a / 4 + (u % Lay::RA) * Lay::SA;
-                const float *XX = A + cx, *YY = A + TXX + cy, *XY = A + TXX + TYY + cxy;
-                const float *Bm2 = smf + Lay::off_b / 4 + ((u + 0) % Lay::RB) * Lay::SB;
-                const float *Bm1 = smf + Lay::off_b / 4 + ((u + 1) % Lay::RB) * Lay::SB;
-                const float *B0 = smf + Lay::off_b / 4 + ((u + 2) % Lay::RB) * Lay::SB;
-                const float *Bp1 = smf + Lay::off_b / 4 + ((u + 3) % Lay::RB) * Lay::SB;
-                const float *Cm1 = smf + Lay::off_c / 4 + ((u + 0) % Lay::RC) * TZZ + tid;
-                const float *C0 = smf + Lay::off_c / 4 + ((u + 1) % Lay::RC) * TZZ + tid;
-                const float *Cp1 = smf + Lay::off_c / 4 + ((u + 2) % Lay::RC) * TZZ + tid;
-                const float *Cp2 = smf + Lay::off_c / 4 + ((u + 3) % Lay::RC) * TZZ + tid;
+                const T *A = smt + (Lay::off_a / Lay::ES) + (u % Lay::RA) * Lay::SA;
+                const T *XX = A + cx, *YY = A + TXX + cy, *XY = A + TXX + TYY + cxy;
+                const T *Bm2 = smt + Lay::off_b / Lay::ES + ((u + 0) % Lay::RB) * Lay::SB;
+                const T *Bm1 = smt + Lay::off_b / Lay::ES + ((u + 1) % Lay::RB) * Lay::SB;
+                const T *B0 = smt + Lay::off_b / Lay::ES + ((u + 2) % Lay::RB) * Lay::SB;
+                const T *Bp1 = smt + Lay::off_b / Lay::ES + ((u + 3) % Lay::RB) * Lay::SB;
+                const T *Cm1 = smt + Lay::off_c / Lay::ES + ((u + 0) % Lay::RC) * TZZ + tid;
+                const T *C0 = smt + Lay::off_c / Lay::ES + ((u + 1) % Lay::RC) * TZZ + tid;
+                const T *Cp1 = smt + Lay::off_c / Lay::ES + ((u + 2) % Lay::RC) * TZZ + tid;
+                const T *Cp2 = smt + Lay::off_c / Lay::ES + ((u + 3) % Lay::RC) * TZZ + tid;
                 const unsigned char *I0 = smb + Lay::off_i + (u % Lay::RI) * IT_SLOT + cI;
                 const unsigned char *I1 = smb + Lay::off_i + ((u + 1) % Lay::RI) * IT_SLOT + cI;
-                const float *XZ = B0 + cx, *YZ = B0 + TXX + cy;
+                const T *XZ = B0 + cx, *YZ = B0 + TXX + cy;
                 const bool kz1 = k < nz - 1;
 
                 // all three components are computed; ghost points (the last
                 // half point of each axis) are simply not stored
-                float ax1 = dfw(XX[-1], XX[0], XX[1], XX[2], ix);
-                float ax2 = dbw(XY[-2 * VW], XY[-VW], XY[0], XY[VW], ix);
-                float ax3 = dbw(Bm2[cx], Bm1[cx], XZ[0], Bp1[cx], ix);
-                float ay1 = dbw(XY[-2], XY[-1], XY[0], XY[1], ix);
-                float ay2 = dfw(YY[-YW], YY[0], YY[YW], YY[2 * YW], ix);
-                float ay3 = dbw(Bm2[TXX + cy], Bm1[TXX + cy], YZ[0], Bp1[TXX + cy], ix);
-                float az1 = dbw(XZ[-2], XZ[-1], XZ[0], XZ[1], ix);
-                float az2 = dbw(YZ[-2 * YW], YZ[-YW], YZ[0], YZ[YW], ix);
-                float az3 = dfw(*Cm1, *C0, *Cp1, *Cp2, ix);
+                float ax1 = dfw(tof(XX[-1]), tof(XX[0]), tof(XX[1]), tof(XX[2]), ix);
+                float ax2 = dbw(tof(XY[-2 * VW]), tof(XY[-VW]), tof(XY[0]), tof(XY[VW]), ix);
+                float ax3 = dbw(tof(Bm2[cx]), tof(Bm1[cx]), tof(XZ[0]), tof(Bp1[cx]), ix);
+                float ay1 = dbw(tof(XY[-2]), tof(XY[-1]), tof(XY[0]), tof(XY[1]), ix);
+                float ay2 = dfw(tof(YY[-YW]), tof(YY[0]), tof(YY[YW]), tof(YY[2 * YW]), ix);
+                float ay3 = dbw(tof(Bm2[TXX + cy]), tof(Bm1[TXX + cy]), tof(YZ[0]),
+                                tof(Bp1[TXX + cy]), ix);
+                float az1 = dbw(tof(XZ[-2]), tof(XZ[-1]), tof(XZ[0]), tof(XZ[1]), ix);
+                float az2 = dbw(tof(YZ[-2 * YW]), tof(YZ[-YW]), tof(YZ[0]), tof(YZ[YW]), ix);
+                float az3 = dfw(tof(*Cm1), tof(*C0), tof(*Cp1), tof(*Cp2), ix);
                 if (xs >= 0) {
                     const float2 h = __ldg(&pmlx[p.nmax + i]), w = __ldg(&pmlx[i]);
                     float t = fmaf(h.x, ax1, h.y * qx[0]);
@@ -263,9 +284,9 @@ __global__ void __launch_bounds__(NTH, 5)
                 const float nvx = ux + st::vel_increment(dt, rho0, s_rho[I0[1]], ax1, ax2, ax3);
                 const float nvy = uy + st::vel_increment(dt, rho0, s_rho[I0[IW]], ay1, ay2, ay3);
                 const float nvz = uz + st::vel_increment(dt, rho0, s_rho[I1[0]], az1, az2, az3);
-                if (ix1) vxg[q] = nvx;
-                if (jy1) vyg[q] = nvy;
-                if (kz1) vzg[q] = nvz;
+                if (ix1) st::stv(vxg + q, nvx);
+                if (jy1) st::stv(vyg + q, nvy);
+                if (kz1) st::stv(vzg + q, nvz);
             }
             ux = nux;
             uy = nuy;
@@ -283,24 +304,29 @@ __global__ void __launch_bounds__(NTH, 5)
 // variables, peak map, FP64 DFT sums) are read straight into registers at the
 // top of each plane, so their latency overlaps the ring wait and the
 // derivatives, and written back with coalesced stores.
-template <int L>
+template <int L, typename T>
 struct StressLayout {
+    static constexpr int VT = Box<T>::VT, ES = (int)sizeof(T);
     static constexpr int RV = 7, RI = 4;                      // ring depths
     static constexpr int off_v = 0;                           // vx, vy, vz: k-2 .. k+4
-    static constexpr int off_i = off_v + RV * 3 * VT * 4;     // index: k .. k+3
+    static constexpr int off_i = off_v + RV * 3 * VT * ES;    // index: k .. k+3
     static constexpr int off_bar = off_i + RI * IT_SLOT;
     static constexpr int off_lut = off_bar + 32;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(st::StressCoef); }
+    static_assert((VT * ES) % 128 == 0 && off_i % 128 == 0,
+                  "TMA destinations must stay 128-byte aligned");
 };
 
-template <int L, int MINB>
+template <int L, int MINB, typename T>
 __global__ void __launch_bounds__(NTH, MINB)
     k_stress_tma(const __grid_constant__ AcParams p, int kchunk,
                  const __grid_constant__ StressTmaMaps tm)
 {
-    using Lay = StressLayout<L>;
-    extern __shared__ __align__(1024) float smf[];
-    unsigned char *smb = reinterpret_cast<unsigned char *>(smf);
+    using Lay = StressLayout<L, T>;
+    using Bx = Box<T>;
+    constexpr int VW = Bx::BW, VT = Bx::VT;
+    extern __shared__ __align__(1024) unsigned char smb[];
+    const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
     st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(smb + Lay::off_lut);
 
@@ -317,14 +343,15 @@ __global__ void __launch_bounds__(NTH, MINB)
     }
     __syncthreads();
 
-    auto oV = [&](int pl) { return Lay::off_v / 4 + ((pl - k0 + 2) % Lay::RV) * 3 * VT; };
+    constexpr unsigned VT_BYTES = VT * Lay::ES;
+    auto oV = [&](int pl) { return Lay::off_v + ((pl - k0 + 2) % Lay::RV) * 3 * (int)VT_BYTES; };
     auto oI = [&](int pl) { return Lay::off_i + ((pl - k0) % Lay::RI) * IT_SLOT; };   // bytes
     auto issue = [&](int kk, uint64_t *bar, bool first) {
         const unsigned nv = first ? 5 : 1;
         tma::mbar_expect_tx(bar, nv * 3 * VT_BYTES + (first ? 2 : 1) * IT);
         for (int pl = first ? kk - 2 : kk + 2; pl <= kk + 2; ++pl)
             for (int a = 0; a < 3; ++a)
-                tma::load3d(smf + oV(pl) + a * VT, &tm.v[a], x0 - 4, y0 - 2, pl, bar);
+                tma::load3d(smb + oV(pl) + a * VT_BYTES, &tm.v[a], x0 - Bx::XO, y0 - 2, pl, bar);
         for (int pl = first ? kk : kk + 1; pl <= kk + 1; ++pl)
             tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar);
     };
@@ -334,18 +361,19 @@ __global__ void __launch_bounds__(NTH, MINB)
     }
 
     const st::Dx ix = st::make_dx(p.inv_dx);
-    const int cv = (ty + 2) * VW + tx + 4;
+    const int cv = (ty + 2) * VW + tx + Bx::XO;
     const int ci = ty * IW + tx;
     const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
-    float *const gs[6] = {p.sxx, p.syy, p.szz, p.sxy, p.sxz, p.syz};
-    float *__restrict__ mem = p.mem;
+    T *const gs[6] = {static_cast<T *>(p.sxx), static_cast<T *>(p.syy), static_cast<T *>(p.szz),
+                      static_cast<T *>(p.sxy), static_cast<T *>(p.sxz), static_cast<T *>(p.syz)};
+    T *__restrict__ mem = static_cast<T *>(p.mem);
 
     // Ring positions of this thread's column, rotated once per plane: the
-    // velocity ring at planes k-2 .. k+2 (float offsets of the vx centre) and
-    // the index ring at k, k+1 (bytes).
-    const int vbase = Lay::off_v / 4, vend = vbase + Lay::RV * 3 * VT;
+    // velocity ring at planes k-2 .. k+2 (element offsets of the vx centre)
+    // and the index ring at k, k+1 (bytes).
+    const int vbase = Lay::off_v / Lay::ES, vend = vbase + Lay::RV * 3 * VT;
     const int ibase = Lay::off_i, iend = ibase + Lay::RI * IT_SLOT;
     int vM2 = vbase + cv, vM1 = vM2 + 3 * VT, vK = vM1 + 3 * VT, vP1 = vK + 3 * VT,
         vP2 = vP1 + 3 * VT;
@@ -364,7 +392,8 @@ __global__ void __launch_bounds__(NTH, MINB)
         float sv[6], rv[L > 0 ? L : 1][6];
         float pk = 0.0f;
         double dC = 0.0, dS = 0.0;
-        // CPML memories of this voxel (components 3-5 of each slab it lies in)
+        // CPML memories of this voxel: components 3-5 of each slab it lies in,
+        // i.e. [normal, then the two shear derivatives along that axis]
         const int zs = slab_pos(k, nz, p.P);
         const int ox = (k * ny + j) * p.W + xs, oy = (k * p.W + ys) * nx + i,
                   oz = (zs * ny + j) * nx + i;
@@ -385,11 +414,12 @@ __global__ void __launch_bounds__(NTH, MINB)
         }
         if (live) {
 #pragma unroll
-            for (int cc = 0; cc < 6; ++cc) sv[cc] = gs[cc][q];
+            for (int cc = 0; cc < 6; ++cc) sv[cc] = tof(gs[cc][q]);
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
-                for (int cc = 0; cc < 6; ++cc) rv[l][cc] = mem[(size_t)(l * 6 + cc) * p.fstride + q];
+                for (int cc = 0; cc < 6; ++cc)
+                    rv[l][cc] = tof(mem[(size_t)(l * 6 + cc) * p.fstride + q]);
             if (p.do_peak) pk = p.peak[q];
             if (p.do_dft) {
                 dC = p.dftC[q];
@@ -407,9 +437,11 @@ __global__ void __launch_bounds__(NTH, MINB)
             const int vx = vK, vy = vK + VT, vz = vK + 2 * VT;
 
             // ---- normal stresses at (i, j, k)
-            float exx = dbw(smf[vx - 2], smf[vx - 1], smf[vx], smf[vx + 1], ix);
-            float eyy = dbw(smf[vy - 2 * VW], smf[vy - VW], smf[vy], smf[vy + VW], ix);
-            float ezz = dbw(smf[vm2 + 2 * VT], smf[vm1 + 2 * VT], smf[vz], smf[vp1 + 2 * VT], ix);
+            float exx = dbw(tof(smt[vx - 2]), tof(smt[vx - 1]), tof(smt[vx]), tof(smt[vx + 1]), ix);
+            float eyy = dbw(tof(smt[vy - 2 * VW]), tof(smt[vy - VW]), tof(smt[vy]),
+                            tof(smt[vy + VW]), ix);
+            float ezz = dbw(tof(smt[vm2 + 2 * VT]), tof(smt[vm1 + 2 * VT]), tof(smt[vz]),
+                            tof(smt[vp1 + 2 * VT]), ix);
             if (xs >= 0) exx = st::cpml_pre(p.psx + 3 * Sxs + ox, qx[0], __ldg(&pmlx[i]), exx);
             if (ys >= 0) eyy = st::cpml_pre(p.psy + 3 * Sys + oy, qy[0], __ldg(&pmly[j]), eyy);
             if (zs >= 0) ezz = st::cpml_pre(p.psz + 3 * Szs + oz, qz[0], __ldg(&pmlz[k]), ezz);
@@ -422,42 +454,75 @@ __global__ void __launch_bounds__(NTH, MINB)
             const float pr = st::pressure(sv);
             if (!isfinite(pr)) atomicOr(p.flag, 1);
 
-            // ---- shear stresses
+            // ---- shear stresses (ghost points computed, not stored)
             const bool dxy = ix1 && jy1, dxz = ix1 && kz1, dyz = jy1 && kz1;
-            if (dxy) {                               // sxy at (i+1/2, j+1/2, k)
-                float a = dfw(smf[vx - VW], smf[vx], smf[vx + VW], smf[vx + 2 * VW], ix);
-                float b = dfw(smf[vy - 1], smf[vy], smf[vy + 1], smf[vy + 2], ix);
-                if (ys >= 0) a = st::cpml_pre(p.psy + 4 * Sys + oy, qy[1], __ldg(&pmly[p.nmax + j]), a);
-                if (xs >= 0) b = st::cpml_pre(p.psx + 4 * Sxs + ox, qx[1], __ldg(&pmlx[p.nmax + i]), b);
+            {                                        // sxy at (i+1/2, j+1/2, k)
+                float a = dfw(tof(smt[vx - VW]), tof(smt[vx]), tof(smt[vx + VW]),
+                              tof(smt[vx + 2 * VW]), ix);
+                float b = dfw(tof(smt[vy - 1]), tof(smt[vy]), tof(smt[vy + 1]), tof(smt[vy + 2]), ix);
+                if (ys >= 0) {
+                    const float2 h = __ldg(&pmly[p.nmax + j]);
+                    const float t = fmaf(h.x, a, h.y * qy[1]);
+                    if (dxy) p.psy[4 * Sys + oy] = t;
+                    a += t;
+                }
+                if (xs >= 0) {
+                    const float2 h = __ldg(&pmlx[p.nmax + i]);
+                    const float t = fmaf(h.x, b, h.y * qx[1]);
+                    if (dxy) p.psx[4 * Sxs + ox] = t;
+                    b += t;
+                }
                 st::shear_update<L>(p, s_lut, c0, m00, I0[1], I0[IW], I0[IW + 1], a + b, 3, sv, rv);
             }
-            if (dxz) {                               // sxz at (i+1/2, j, k+1/2)
-                float a = dfw(smf[vm1], smf[vx], smf[vp1], smf[vp2], ix);
-                float b = dfw(smf[vz - 1], smf[vz], smf[vz + 1], smf[vz + 2], ix);
-                if (zs >= 0) a = st::cpml_pre(p.psz + 4 * Szs + oz, qz[1], __ldg(&pmlz[p.nmax + k]), a);
-                if (xs >= 0) b = st::cpml_pre(p.psx + 5 * Sxs + ox, qx[2], __ldg(&pmlx[p.nmax + i]), b);
+            {                                        // sxz at (i+1/2, j, k+1/2)
+                float a = dfw(tof(smt[vm1]), tof(smt[vx]), tof(smt[vp1]), tof(smt[vp2]), ix);
+                float b = dfw(tof(smt[vz - 1]), tof(smt[vz]), tof(smt[vz + 1]), tof(smt[vz + 2]), ix);
+                if (zs >= 0) {
+                    const float2 h = __ldg(&pmlz[p.nmax + k]);
+                    const float t = fmaf(h.x, a, h.y * qz[1]);
+                    if (dxz) p.psz[4 * Szs + oz] = t;
+                    a += t;
+                }
+                if (xs >= 0) {
+                    const float2 h = __ldg(&pmlx[p.nmax + i]);
+                    const float t = fmaf(h.x, b, h.y * qx[2]);
+                    if (dxz) p.psx[5 * Sxs + ox] = t;
+                    b += t;
+                }
                 st::shear_update<L>(p, s_lut, c0, m00, I0[1], I1[0], I1[1], a + b, 4, sv, rv);
             }
-            if (dyz) {                               // syz at (i, j+1/2, k+1/2)
-                float a = dfw(smf[vm1 + VT], smf[vy], smf[vp1 + VT], smf[vp2 + VT], ix);
-                float b = dfw(smf[vz - VW], smf[vz], smf[vz + VW], smf[vz + 2 * VW], ix);
-                if (zs >= 0) a = st::cpml_pre(p.psz + 5 * Szs + oz, qz[2], __ldg(&pmlz[p.nmax + k]), a);
-                if (ys >= 0) b = st::cpml_pre(p.psy + 5 * Sys + oy, qy[2], __ldg(&pmly[p.nmax + j]), b);
+            {                                        // syz at (i, j+1/2, k+1/2)
+                float a = dfw(tof(smt[vm1 + VT]), tof(smt[vy]), tof(smt[vp1 + VT]),
+                              tof(smt[vp2 + VT]), ix);
+                float b = dfw(tof(smt[vz - VW]), tof(smt[vz]), tof(smt[vz + VW]),
+                              tof(smt[vz + 2 * VW]), ix);
+                if (zs >= 0) {
+                    const float2 h = __ldg(&pmlz[p.nmax + k]);
+                    const float t = fmaf(h.x, a, h.y * qz[2]);
+                    if (dyz) p.psz[5 * Szs + oz] = t;
+                    a += t;
+                }
+                if (ys >= 0) {
+                    const float2 h = __ldg(&pmly[p.nmax + j]);
+                    const float t = fmaf(h.x, b, h.y * qy[2]);
+                    if (dyz) p.psy[5 * Sys + oy] = t;
+                    b += t;
+                }
                 st::shear_update<L>(p, s_lut, c0, m00, I0[IW], I1[0], I1[IW], a + b, 5, sv, rv);
             }
 
             // ---- results (ghost points are not written)
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) gs[cc][q] = sv[cc];
-            if (dxy) gs[3][q] = sv[3];
-            if (dxz) gs[4][q] = sv[4];
-            if (dyz) gs[5][q] = sv[5];
+            for (int cc = 0; cc < 3; ++cc) st::stv(gs[cc] + q, sv[cc]);
+            if (dxy) st::stv(gs[3] + q, sv[3]);
+            if (dxz) st::stv(gs[4] + q, sv[4]);
+            if (dyz) st::stv(gs[5] + q, sv[5]);
 #pragma unroll
             for (int l = 0; l < L; ++l)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) {
                     const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
-                    if (w) mem[(size_t)(l * 6 + cc) * p.fstride + q] = rv[l][cc];
+                    if (w) st::stv(mem + (size_t)(l * 6 + cc) * p.fstride + q, rv[l][cc]);
                 }
             if (p.do_peak) p.peak[q] = fmaxf(pk, fabsf(pr));
             if (p.do_dft) {
@@ -482,38 +547,52 @@ static dim3 grid_tma(const AcParams &p, int kc)
     return dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + kc - 1) / kc);
 }
 
-cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
+template <typename T>
+static cudaError_t launch_velocity_tma_t(const AcParams &p, const VelocityTmaMaps &tm,
+                                         cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
-    const size_t sm = VelLayout::bytes(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
+    const size_t sm = VelLayout<T>::bytes(p.n_mat);
+    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_velocity_tma<<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    k_velocity_tma<T><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
 }
 
-template <int L, int MINB>
+cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
+{
+    return p.h16 ? launch_velocity_tma_t<__half>(p, tm, s) : launch_velocity_tma_t<float>(p, tm, s);
+}
+
+template <int L, int MINB, typename T>
 static cudaError_t launch_stress_tma_t(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
-    const size_t sm = StressLayout<L>::bytes(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_stress_tma<L, MINB>,
+    const size_t sm = StressLayout<L, T>::bytes(p.n_mat);
+    cudaError_t e = cudaFuncSetAttribute(k_stress_tma<L, MINB, T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_stress_tma<L, MINB><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    k_stress_tma<L, MINB, T><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
 }
 
-// Four resident blocks per SM (64 registers, about 46 KB of shared memory).
-cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
+template <typename T>
+static cudaError_t launch_stress_tma_l(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     switch (p.L) {
-    case 0: return launch_stress_tma_t<0, 4>(p, tm, s);
-    case 1: return launch_stress_tma_t<1, 4>(p, tm, s);
-    case 2: return launch_stress_tma_t<2, 4>(p, tm, s);
+    case 0: return launch_stress_tma_t<0, 4, T>(p, tm, s);
+    case 1: return launch_stress_tma_t<1, 4, T>(p, tm, s);
+    case 2: return launch_stress_tma_t<2, 4, T>(p, tm, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// Four resident blocks per SM (64 registers, about 46 KB of shared memory in
+// FP32 storage).
+cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
+{
+    return p.h16 ? launch_stress_tma_l<__half>(p, tm, s) : launch_stress_tma_l<float>(p, tm, s);
 }
 
 // z-chunk length of the TMA kernels: about six waves of four resident blocks

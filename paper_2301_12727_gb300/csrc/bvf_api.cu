@@ -40,9 +40,12 @@ struct bvf_ctx {
     bvf_physics ph{};
     int L = 0;
     size_t N = 0, fstride = 0;
+    int h16 = 0;                      // state stored as scaled FP16
+    size_t es = 4;                    // bytes per state element
+    double s_sig = 1.0, s_v = 1.0, s_r = 1.0;   // storage scales of sigma, v, r
     int P = 0, W = 0, nmax = 0;
     // device state
-    float *fields = nullptr;          // (9 + 6L) arrays of fstride floats
+    void *fields = nullptr;           // (9 + 6L) arrays of fstride elements
     float *psi = nullptr;             // 3 slabs x 6 memories
     size_t slab_x = 0, slab_y = 0, slab_z = 0;
     float *peak = nullptr;
@@ -173,9 +176,17 @@ double envelope(int env, int n_cycles, double f0, double t)
     return 0.0;
 }
 
-float *field_ptr(bvf_ctx *c, int which)
+void *field_ptr(bvf_ctx *c, int which)
 {
-    return c->fields + (size_t)which * c->fstride;
+    return static_cast<char *>(c->fields) + (size_t)which * c->fstride * c->es;
+}
+
+// storage scale of state array `which` (physical value = stored value * scale)
+double field_scale(const bvf_ctx *c, int which)
+{
+    if (which < BVF_FIELD_SXX) return c->s_v;
+    if (which < BVF_FIELD_MEM0) return c->s_sig;
+    return c->s_r;
 }
 
 cudaError_t next_event(bvf_ctx *c, cudaEvent_t *out)
@@ -252,31 +263,19 @@ void setup_maps(bvf_ctx *c)
     c->tma_stress = false;
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
     if (nx % 16 != 0 || c->L > 2 || std::getenv("BVF_NO_TMA")) return;
-    const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, F64 = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const auto ST = c->h16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
-    auto fld = [&](int f) { return (void *)(c->fields + (size_t)f * c->fstride); };
+    const size_t es = c->es;
+    const unsigned bw = 32 + 2 * (unsigned)(16 / es);   // halo'd box width: 16 bytes each side
+    auto fld = [&](int f) { return field_ptr(c, f); };
     bool ok = true;
-    int a = 0;
-    for (int f = BVF_FIELD_SXX; f <= BVF_FIELD_SYZ; ++f)
-        ok = ok && encode_map(&c->smaps.s[a++], fld(f), nx, ny, nz, F32, 4, 32, 8);
-    for (int l = 0; l < c->L; ++l)
-        for (int cc = 0; cc < 6; ++cc)
-            ok = ok && encode_map(&c->smaps.s[a++], fld(BVF_FIELD_MEM0 + 6 * l + cc), nx, ny, nz,
-                                  F32, 4, 32, 8);
-    ok = ok && encode_map(&c->smaps.s[a++], c->peak, nx, ny, nz, F32, 4, 32, 8);
-    if (c->dftC) {
-        ok = ok && encode_map(&c->smaps.s[a++], c->dftC, nx, ny, nz, F64, 8, 32, 8);
-        ok = ok && encode_map(&c->smaps.s[a++], c->dftS, nx, ny, nz, F64, 8, 32, 8);
-    }
-    for (int v = 0; v < 3; ++v) {
-        ok = ok && encode_map(&c->smaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, F32, 4, 40, 12);
-        ok = ok && encode_map(&c->vmaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, F32, 4, 32, 8);
-    }
+    for (int v = 0; v < 3; ++v)
+        ok = ok && encode_map(&c->smaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, ST, es, bw, 12);
     // velocity kernel boxes: the halo each stress array's stencil reads
-    const unsigned bw[6] = {40, 32, 32, 40, 40, 32}, bh[6] = {8, 12, 8, 12, 8, 12};
+    const unsigned w6[6] = {bw, 32, 32, bw, bw, 32}, h6[6] = {8, 12, 8, 12, 8, 12};
     for (int g6 = 0; g6 < 6; ++g6)
-        ok = ok && encode_map(&c->vmaps.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, F32, 4, bw[g6],
-                              bh[g6]);
+        ok = ok && encode_map(&c->vmaps.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, ST, es, w6[g6],
+                              h6[g6]);
     ok = ok && encode_map(&c->smaps.idx, c->index, nx, ny, nz, U8, 1, 48, 9);
     c->vmaps.idx = c->smaps.idx;
     c->tma = ok;
@@ -295,13 +294,18 @@ AcParams make_params(bvf_ctx *c)
     p.W = c->W;
     p.L = c->L;
     p.n_mat = (int)c->table.size();
-    p.dt = (float)c->g.dt;
+    p.h16 = c->h16;
+    // storage scales folded into the constants (all 1 for float storage, so
+    // the float path computes exactly dt, 0.5 and cb)
+    p.dt = (float)(c->g.dt * c->s_v / c->s_sig);
+    p.dtv = (float)(c->g.dt * c->s_sig / c->s_v);
+    p.rh = (float)(0.5 * c->s_r / c->s_v);
     p.inv_dx = (float)(1.0 / c->g.dx);
     p.Lf = (float)c->L;
     for (int l = 0; l < c->L; ++l) {
         const double h = c->g.dt / (2.0 * c->tau_sigma[l]);
         p.ca[l] = (float)((1.0 - h) / (1.0 + h));
-        p.cb[l] = (float)((c->g.dt / c->tau_sigma[l]) / (1.0 + h));
+        p.cb[l] = (float)((c->g.dt / c->tau_sigma[l]) / (1.0 + h) * (c->s_v / c->s_r));
     }
     p.idx = c->index;
     p.lut = c->lut;
@@ -385,6 +389,9 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
         return fail(nullptr, BVF_E_ARG, "bvf_create: bad physics (f0, qc or n_sls)");
     if ((double)g.nx * g.ny * g.nz >= 2147483648.0)
         return fail(nullptr, BVF_E_ARG, "bvf_create: grid of 2^31 voxels or more");
+    if ((phys->storage != BVF_STORAGE_F32 && phys->storage != BVF_STORAGE_F16) ||
+        !(phys->p_ref >= 0.0) || std::isinf(phys->p_ref))
+        return fail(nullptr, BVF_E_ARG, "bvf_create: bad storage or p_ref");
 
     c = new (std::nothrow) bvf_ctx;
     if (!c) return fail(nullptr, BVF_E_NOMEM, "bvf_create: host allocation failed");
@@ -393,6 +400,16 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
     c->L = phys->n_sls;
     c->N = (size_t)g.nx * g.ny * g.nz;
     c->fstride = (c->N + 63) & ~(size_t)63;
+    c->h16 = phys->storage == BVF_STORAGE_F16;
+    c->es = c->h16 ? 2 : 4;
+    if (c->h16) {
+        // sigma / p_ref, v rho_w c_w / p_ref; memory variables r (a stress
+        // rate) times 8 dt / p_ref, i.e. r' = r / S_v and S_r = S_v Z_w / (8 dt)
+        const double zw = 1.5e6;
+        c->s_sig = phys->p_ref > 0.0 ? phys->p_ref : 1e5;
+        c->s_v = c->s_sig / zw;
+        c->s_r = c->s_v * zw / (8.0 * g.dt);
+    }
     c->P = g.n_pml;
     c->W = g.n_pml > 0 ? 2 * g.n_pml + 1 : 0;
     c->nmax = std::max(g.nx, std::max(g.ny, g.nz));
@@ -405,7 +422,7 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
     auto cleanup = [&](int code) { bvf_destroy(c); return code; };
     cudaError_t e;
     const size_t nf = 9 + 6 * (size_t)c->L;
-    if ((e = cudaMalloc(&c->fields, nf * c->fstride * sizeof(float))) != cudaSuccess)
+    if ((e = cudaMalloc(&c->fields, nf * c->fstride * c->es)) != cudaSuccess)
         return cleanup(cuda_fail(nullptr, e, "bvf_create: fields"));
     const size_t npsi = kNumCpmlSlots * (c->slab_x + c->slab_y + c->slab_z);
     if (npsi && (e = cudaMalloc(&c->psi, npsi * sizeof(float))) != cudaSuccess)
@@ -418,7 +435,7 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
         (e = cudaMalloc(&c->flag, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&c->scratch_u, sizeof(unsigned))) != cudaSuccess)
         return cleanup(cuda_fail(nullptr, e, "bvf_create: buffers"));
-    if ((e = cudaMemset(c->fields, 0, nf * c->fstride * sizeof(float))) != cudaSuccess ||
+    if ((e = cudaMemset(c->fields, 0, nf * c->fstride * c->es)) != cudaSuccess ||
         (npsi && (e = cudaMemset(c->psi, 0, npsi * sizeof(float))) != cudaSuccess) ||
         (e = cudaMemset(c->peak, 0, c->N * sizeof(float))) != cudaSuccess ||
         (e = cudaMemset(c->index, 0, c->N)) != cudaSuccess ||
@@ -547,7 +564,7 @@ int bvf_reset(bvf_ctx *c, void *stream)
     if (!c) return fail(nullptr, BVF_E_ARG, "bvf_reset: NULL context");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t nf = 9 + 6 * (size_t)c->L;
-    CK(cudaMemsetAsync(c->fields, 0, nf * c->fstride * sizeof(float), s), "reset");
+    CK(cudaMemsetAsync(c->fields, 0, nf * c->fstride * c->es, s), "reset");
     const size_t npsi = kNumCpmlSlots * (c->slab_x + c->slab_y + c->slab_z);
     if (npsi) CK(cudaMemsetAsync(c->psi, 0, npsi * sizeof(float), s), "reset");
     CK(cudaMemsetAsync(c->peak, 0, c->N * sizeof(float), s), "reset");
@@ -579,7 +596,7 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
     }
     AcParams p = make_params(c);
     const double w = 2.0 * kPi * c->ph.f0, dt = c->g.dt;
-    p.src_scale = (float)(2.0 * c->c0 * dt / c->g.dx);
+    p.src_scale = (float)(2.0 * c->c0 * dt / c->g.dx / c->s_sig);
     for (int it = 0; it < n_steps; ++it) {
         const long long n = c->steps;
         const double t = (n + 0.5) * dt;
@@ -639,8 +656,14 @@ int bvf_get_field(bvf_ctx *c, int which, float *d_out, void *stream)
 {
     if (!c || !d_out || which < 0 || which >= 9 + 6 * c->L)
         return fail(c, BVF_E_ARG, "bvf_get_field: bad context, pointer or field id");
-    CK(cudaMemcpyAsync(d_out, field_ptr(c, which), c->N * sizeof(float), cudaMemcpyDeviceToDevice,
-                       (cudaStream_t)stream), "get field");
+    if (!c->h16)
+        CK(cudaMemcpyAsync(d_out, field_ptr(c, which), c->N * sizeof(float),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "get field");
+    else {
+        CK(launch_field_out(field_ptr(c, which), 1, (float)field_scale(c, which), d_out, c->N,
+                            (cudaStream_t)stream), "get field");
+        c->launches++;
+    }
     return BVF_OK;
 }
 
@@ -648,8 +671,14 @@ int bvf_set_field(bvf_ctx *c, int which, const float *d_in, void *stream)
 {
     if (!c || !d_in || which < 0 || which >= 9 + 6 * c->L)
         return fail(c, BVF_E_ARG, "bvf_set_field: bad context, pointer or field id");
-    CK(cudaMemcpyAsync(field_ptr(c, which), d_in, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
-                       (cudaStream_t)stream), "set field");
+    if (!c->h16)
+        CK(cudaMemcpyAsync(field_ptr(c, which), d_in, c->N * sizeof(float),
+                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "set field");
+    else {
+        CK(launch_field_in(d_in, 1, (float)(1.0 / field_scale(c, which)), field_ptr(c, which),
+                           c->N, (cudaStream_t)stream), "set field");
+        c->launches++;
+    }
     return BVF_OK;
 }
 
@@ -657,7 +686,8 @@ int bvf_get_pressure(bvf_ctx *c, float *d_out, void *stream)
 {
     if (!c || !d_out) return fail(c, BVF_E_ARG, "bvf_get_pressure: NULL argument");
     CK(launch_pressure(field_ptr(c, BVF_FIELD_SXX), field_ptr(c, BVF_FIELD_SYY),
-                       field_ptr(c, BVF_FIELD_SZZ), d_out, c->N, (cudaStream_t)stream),
+                       field_ptr(c, BVF_FIELD_SZZ), c->h16, (float)c->s_sig, d_out, c->N,
+                       (cudaStream_t)stream),
        "pressure kernel");
     c->launches++;
     return BVF_OK;
@@ -666,8 +696,14 @@ int bvf_get_pressure(bvf_ctx *c, float *d_out, void *stream)
 int bvf_get_peak(bvf_ctx *c, float *d_out, void *stream)
 {
     if (!c || !d_out) return fail(c, BVF_E_ARG, "bvf_get_peak: NULL argument");
-    CK(cudaMemcpyAsync(d_out, c->peak, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
-                       (cudaStream_t)stream), "get peak");
+    if (!c->h16)
+        CK(cudaMemcpyAsync(d_out, c->peak, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream), "get peak");
+    else {
+        CK(launch_scale_copy(c->peak, (float)c->s_sig, d_out, c->N, (cudaStream_t)stream),
+           "get peak");
+        c->launches++;
+    }
     return BVF_OK;
 }
 
@@ -676,7 +712,7 @@ int bvf_get_amp_phase(bvf_ctx *c, double *d_amp, double *d_phase, void *stream)
     if (!c) return fail(nullptr, BVF_E_ARG, "bvf_get_amp_phase: NULL context");
     if (!c->dftC || c->dft_count <= 0)
         return fail(c, BVF_E_ARG, "bvf_get_amp_phase: no step was captured");
-    CK(launch_amp_phase(c->dftC, c->dftS, c->N, c->dft_count, d_amp, d_phase,
+    CK(launch_amp_phase(c->dftC, c->dftS, c->N, c->dft_count, c->s_sig, d_amp, d_phase,
                         (cudaStream_t)stream), "amp/phase kernel");
     c->launches++;
     return BVF_OK;
@@ -881,8 +917,8 @@ int bvf_get_stats(const bvf_ctx *c, bvf_stats *out)
     out->courant = c->courant;
     // velocity: read 6 sigma + 3 v, write 3 v (12 words); stress: read 3 v,
     // read + write 6 sigma and 6L memory variables (15 + 12 L words); the index
-    // byte in each kernel and the peak map (read + write)
-    out->bytes_per_voxel_step = 4.0 * (12 + 15 + 12 * c->L) + 2.0 + 8.0;
+    // byte in each kernel and the FP32 peak map (read + write)
+    out->bytes_per_voxel_step = (double)c->es * (12 + 15 + 12 * c->L) + 2.0 + 8.0;
     return BVF_OK;
 }
 

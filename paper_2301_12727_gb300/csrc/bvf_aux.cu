@@ -1,7 +1,9 @@
 // Auxiliary kernels: index-range scan, pressure / amplitude-phase read-out,
 // Rayleigh-Sommerfeld bowl field (Sec. 2.3), BHTE + CEM43 step (Sec. 2.4),
 // and the E_L reductions (Sec. 2.4, Eq. 2).
-#include "bvf_internal.cuh"
+#include <cuda_fp16.h>
+
+#include "bvf_stencil.cuh"
 
 namespace bvf {
 
@@ -25,22 +27,46 @@ __global__ void k_index_max(const uint8_t *__restrict__ idx, size_t n, unsigned 
     if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-__global__ void k_pressure(const float *__restrict__ a, const float *__restrict__ b,
-                           const float *__restrict__ c, float *__restrict__ out, size_t n)
+template <typename T>
+__global__ void k_pressure(const T *__restrict__ a, const T *__restrict__ b,
+                           const T *__restrict__ c, float scale, float *__restrict__ out, size_t n)
 {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
          q += (size_t)gridDim.x * blockDim.x)
-        out[q] = -(a[q] + b[q] + c[q]) / 3.0f;
+        out[q] = -(st::tof(a[q]) + st::tof(b[q]) + st::tof(c[q])) / 3.0f * scale;
+}
+
+// state array <-> FP32 values in physical units (scale = the storage scale)
+template <typename T>
+__global__ void k_field_out(const T *__restrict__ f, float scale, float *__restrict__ out, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        out[q] = st::tof(f[q]) * scale;
+}
+template <typename T>
+__global__ void k_field_in(const float *__restrict__ in, float inv_scale, T *__restrict__ f, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        st::stv(f + q, in[q] * inv_scale);
+}
+__global__ void k_scale_copy(const float *__restrict__ in, float scale, float *__restrict__ out,
+                             size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        out[q] = in[q] * scale;
 }
 
 // p(t) = A cos(w t + phi): C = A N/2 cos phi, S = -A N/2 sin phi
 __global__ void k_amp_phase(const double *__restrict__ C, const double *__restrict__ S, size_t n,
-                            double inv_half_n, double *amp, double *ph)
+                            double inv_half_n, double scale, double *amp, double *ph)
 {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
          q += (size_t)gridDim.x * blockDim.x) {
         const double c = C[q], s = S[q];
-        if (amp) amp[q] = sqrt(c * c + s * s) * inv_half_n;
+        if (amp) amp[q] = sqrt(c * c + s * s) * inv_half_n * scale;
         if (ph) ph[q] = atan2(-s, c);
     }
 }
@@ -204,17 +230,54 @@ cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_pressure(const float *sxx, const float *syy, const float *szz, float *out,
-                            size_t n, cudaStream_t s)
+cudaError_t launch_pressure(const void *sxx, const void *syy, const void *szz, int h16,
+                            float scale, float *out, size_t n, cudaStream_t s)
 {
-    k_pressure<<<blocks_for(n), kThreads, 0, s>>>(sxx, syy, szz, out, n);
+    if (h16)
+        k_pressure<__half><<<blocks_for(n), kThreads, 0, s>>>(
+            static_cast<const __half *>(sxx), static_cast<const __half *>(syy),
+            static_cast<const __half *>(szz), scale, out, n);
+    else
+        k_pressure<float><<<blocks_for(n), kThreads, 0, s>>>(
+            static_cast<const float *>(sxx), static_cast<const float *>(syy),
+            static_cast<const float *>(szz), scale, out, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double *amp,
-                             double *ph, cudaStream_t s)
+cudaError_t launch_field_out(const void *f, int h16, float scale, float *out, size_t n,
+                             cudaStream_t s)
 {
-    k_amp_phase<<<blocks_for(n), kThreads, 0, s>>>(C, S, n, 2.0 / count, amp, ph);
+    if (h16)
+        k_field_out<__half><<<blocks_for(n), kThreads, 0, s>>>(static_cast<const __half *>(f),
+                                                              scale, out, n);
+    else
+        k_field_out<float><<<blocks_for(n), kThreads, 0, s>>>(static_cast<const float *>(f), scale,
+                                                             out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_in(const float *in, int h16, float inv_scale, void *f, size_t n,
+                            cudaStream_t s)
+{
+    if (h16)
+        k_field_in<__half><<<blocks_for(n), kThreads, 0, s>>>(in, inv_scale,
+                                                             static_cast<__half *>(f), n);
+    else
+        k_field_in<float><<<blocks_for(n), kThreads, 0, s>>>(in, inv_scale,
+                                                            static_cast<float *>(f), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(const float *in, float scale, float *out, size_t n, cudaStream_t s)
+{
+    k_scale_copy<<<blocks_for(n), kThreads, 0, s>>>(in, scale, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double scale,
+                             double *amp, double *ph, cudaStream_t s)
+{
+    k_amp_phase<<<blocks_for(n), kThreads, 0, s>>>(C, S, n, 2.0 / count, scale, amp, ph);
     return cudaGetLastError();
 }
 

@@ -38,17 +38,28 @@ struct ThermCoef {
 
 constexpr int kNumCpmlSlots = 6;   // CPML memories per slab (see ctx layout)
 
+// The state (v, sigma, memory variables) is stored as float, or as FP16
+// scaled so that stored values stay well inside FP16's range: v / S_v,
+// sigma / S_sigma and r / S_r.  The equations are linear in the state, so the
+// scales fold into the constants below and the kernels run the same FP32
+// arithmetic on the stored values (all scales 1 for float storage):
+//   velocity  dtv = dt S_sigma / S_v
+//   stress    dt (the stress step) = dt S_v / S_sigma, memory-variable sum
+//             weight rh = S_r / (2 S_v), cb_l divided by S_r / S_v
+//   source    src_scale divided by S_sigma
+// Captured p (peak map, DFT sums) is in units of S_sigma.
 struct AcParams {
     int nx, ny, nz;
     int P, W;            // CPML cells per face; slab width 2P+1 (0 if no CPML)
     int L;               // SLS mechanisms
     int n_mat;
-    float dt, inv_dx, Lf;
+    int h16;             // state stored as scaled FP16
+    float dt, dtv, inv_dx, Lf, rh;
     float ca[BVF_MAX_SLS], cb[BVF_MAX_SLS];
     const uint8_t *idx;
     const MatCoef *lut;
-    float *vx, *vy, *vz, *sxx, *syy, *szz, *sxy, *sxz, *syz;
-    float *mem;          // memory variables, [l][c] arrays of `fstride` floats
+    void *vx, *vy, *vz, *sxx, *syy, *szz, *sxy, *sxz, *syz;   // float or __half
+    void *mem;           // memory variables, [l][c] arrays of `fstride` elements
     size_t fstride;
     float *psx, *psy, *psz;   // CPML slabs: x [6][nz][ny][W], y [6][nz][W][nx], z [6][W][ny][nx]
     const float2 *pml;   // (a, b) at [axis][h][s], h = 0 integer / 1 half point
@@ -68,20 +79,17 @@ struct AcParams {
 };
 
 // Tensor maps of the TMA-fed acoustic kernels (x-y boxes of one z-plane).
-// Stress kernel: streaming arrays in stage order (6 stresses, 6 L memory
-// variables, the peak map, FP64 DFT sums C and S) with 32 x 8 boxes; the
-// velocities with 40 x 12 halo boxes; the material index with 48 x 9 boxes.
+// Stress kernel: the velocities with (32 + 2 XO) x 12 halo boxes and the
+// material index with 48 x 9 boxes.  Velocity kernel: the six stresses (sxx,
+// syy, szz, sxy, sxz, syz), each with a box holding the halo its stencil
+// reads: (32 + 2 XO) x 8, 32 x 12, 32 x 8, (32 + 2 XO) x 12, (32 + 2 XO) x 8,
+// 32 x 12; the material index.  XO = 16 bytes of the storage type.
 struct StressTmaMaps {
-    CUtensorMap s[6 + 6 * 2 + 1 + 2];
     CUtensorMap v[3];
     CUtensorMap idx;
 };
-// Velocity kernel: the six stresses (sxx, syy, szz, sxy, sxz, syz), each with
-// a box holding the halo its stencil reads (40x8, 32x12, 32x8, 40x12, 40x8,
-// 32x12); the velocities with 32 x 8 boxes; the material index.
 struct VelocityTmaMaps {
     CUtensorMap sg[6];
-    CUtensorMap v[3];
     CUtensorMap idx;
 };
 
@@ -111,10 +119,15 @@ cudaError_t launch_stress(const AcParams &p, cudaStream_t s);
 cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s);
 cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s);
 cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cudaStream_t s);
-cudaError_t launch_pressure(const float *sxx, const float *syy, const float *szz, float *out,
-                            size_t n, cudaStream_t s);
-cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double *amp,
-                             double *ph, cudaStream_t s);
+cudaError_t launch_pressure(const void *sxx, const void *syy, const void *szz, int h16,
+                            float scale, float *out, size_t n, cudaStream_t s);
+cudaError_t launch_field_out(const void *f, int h16, float scale, float *out, size_t n,
+                             cudaStream_t s);
+cudaError_t launch_field_in(const float *in, int h16, float inv_scale, void *f, size_t n,
+                            cudaStream_t s);
+cudaError_t launch_scale_copy(const float *in, float scale, float *out, size_t n, cudaStream_t s);
+cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double scale,
+                             double *amp, double *ph, cudaStream_t s);
 cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float zp, float k_over_pi,
                       double pref, float2 *out, cudaStream_t s);
 cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_mat,

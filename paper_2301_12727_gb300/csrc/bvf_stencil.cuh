@@ -3,10 +3,19 @@
 // memory variables (Sec. 3.2).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "bvf_internal.cuh"
 
 namespace bvf {
 namespace st {
+
+// State storage: float, or scaled FP16 converted to FP32 on load and rounded
+// to nearest on store.
+__device__ __forceinline__ float tof(float v) { return v; }
+__device__ __forceinline__ float tof(__half v) { return __half2float(v); }
+__device__ __forceinline__ void stv(float *p, float v) { *p = v; }
+__device__ __forceinline__ void stv(__half *p, float v) { *p = __float2half_rn(v); }
 
 constexpr float kC1 = 1.125f;            // 9/8
 constexpr float kC2 = -1.0f / 24.0f;     // -1/24
@@ -137,7 +146,7 @@ __device__ __forceinline__ void normal_update(const AcParams &p, const StressCoe
         const float Psi = c0.piU * th - c0.mu2U * dev;
         const float The = c0.piT * th - c0.mu2T * dev;
         const float sum = sls_update<L>(p, rv, cc, The);
-        float v = sv[cc] + p.dt * (Psi + 0.5f * sum);
+        float v = sv[cc] + p.dt * (Psi + p.rh * sum);
         v -= srcv;
         sv[cc] = v;
     }
@@ -173,7 +182,7 @@ __device__ __forceinline__ void shear_update(const AcParams &p, const StressCoef
     const float Psi = psic * e;
     const float The = thec * e;
     const float sum = sls_update<L>(p, rv, cc, The);
-    sv[cc] += p.dt * (Psi + 0.5f * sum);
+    sv[cc] += p.dt * (Psi + p.rh * sum);
 }
 
 }  // namespace st

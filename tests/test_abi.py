@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(bvf):
 
 
 def test_version_and_constants(bvf):
-    assert bvf.bvf_version() == 1
+    assert bvf.bvf_version() == 2
     assert bvf.bvf_courant_limit() == pytest.approx(6 / (7 * 3 ** 0.5), rel=1e-15)
     assert bvf.lib().bvf_strerror(-2).decode().startswith("time step")
 
@@ -49,6 +49,8 @@ def test_version_and_constants(bvf):
     ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (5e5, 1.0, 9)),   # too many SLS mechanisms
     ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (-5e5, 1.0, 2)),  # negative f0
     ((16, 16, 16, 1e-3, 1e-7, 2, 2.0), (5e5, 1.0, 2)),    # pml_R outside (0,1)
+    ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (5e5, 1.0, 2, 7, 0.0)),     # unknown storage
+    ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (5e5, 1.0, 2, 1, -1e5)),    # negative p_ref
 ])
 def test_create_rejects_bad_arguments_on_host(bvf, grid, phys):
     ctx = ctypes.c_void_p()

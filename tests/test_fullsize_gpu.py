@@ -80,3 +80,28 @@ def test_fullsize_transmission_is_one_for_water(mods):
     r = pl.run(torch.from_numpy(w.index).cuda(), w.materials, w.bowl)
     pl.close()
     assert r.EL == 1.0 and r.TS == 1.0
+
+
+def test_fullsize_f16_storage_within_one_percent_of_f32(mods):
+    """FP16 storage at the benchmark's workload (skull run, 1500 steps): peak
+    map within 1 % of the FP32 run's largest peak everywhere, focal peak and
+    FP64 amplitude within 1 %, phase within 0.01 rad in the beam."""
+    bvf, plan, synth = mods
+    c = synth.skull_case(240, 240, 200, n_steps=1500)
+    out = {}
+    for st in ("f32", "f16"):
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml, storage=st)
+        s.set_materials(c.index, c.materials)
+        s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
+                     c.c0, c.envelope)
+        s.run(c.n_steps, peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps)
+        s.synchronize()
+        amp, ph = s.amp_phase()
+        out[st] = (s.peak().cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy())
+        s.close()
+    (p32, a32, f32), (p16, a16, f16) = out["f32"], out["f16"]
+    assert abs(p16.max() - p32.max()) < 1e-2 * p32.max()
+    assert np.abs(p16 - p32).max() < 1e-2 * p32.max()
+    assert np.abs(a16 - a32).max() < 1e-2 * a32.max()
+    beam = a32 > 0.1 * a32.max()
+    assert np.abs(np.angle(np.exp(1j * (f16 - f32))))[beam].max() < 1e-2

@@ -35,9 +35,9 @@ def mat_row(rho, cL, cS=0.0, aL=0.0, aS=0.0, k=0.5, c=3600.0, perf=0.0, heat=1.0
     return [rho, cL, cS, aL, aS, k, c, perf, heat]
 
 
-def make_pair(bvf, orc, c, n_sls=2):
+def make_pair(bvf, orc, c, n_sls=2, storage="f32"):
     s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, qc=c.qc, n_sls=n_sls, n_pml=c.n_pml,
-                   pml_R=c.pml_R)
+                   pml_R=c.pml_R, storage=storage)
     s.set_materials(c.index, c.materials)
     A = orc.Acoustic(c.nx, c.ny, c.nz, c.dx, c.dt, c.index, c.materials, c.f0, qc=c.qc,
                      n_sls=n_sls, n_pml=c.n_pml, pml_R=c.pml_R)
@@ -330,12 +330,13 @@ def test_gpu_zchunk_invariance(bvf, monkeypatch, nx):
             assert np.array_equal(a, b)
 
 
-def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch):
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch, storage):
     """Grids with nx % 16 == 0 run the TMA-fed kernels (tiles, rings and
     in-place stages moved by the tensor-memory accelerator); other shapes, or
     BVF_NO_TMA, run the direct kernels.  Same arithmetic, so every field, the
     peak map and the FP64 DFT agree bit for bit, across z-chunk lengths (chunk
-    prologues) and a partial x-tile (nx = 80)."""
+    prologues) and a partial x-tile (nx = 80), in both storage types."""
     from paper_2301_12727_gb300 import synth
     c = synth.skull_case(80, 48, 40, dx=0.5e-3, n_steps=120, aperture=16e-3, roc=16e-3, n_pml=5)
     outs = []
@@ -347,7 +348,8 @@ def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch):
             monkeypatch.setenv("BVF_NO_TMA", "1")
         else:
             monkeypatch.delenv("BVF_NO_TMA", raising=False)
-        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml,
+                       storage=storage)
         s.set_materials(c.index, c.materials)
         s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
                      c.c0, c.envelope)
@@ -361,3 +363,72 @@ def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch):
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# FP16 storage: the state rounded to FP16 between steps, FP32 arithmetic.
+# A stored value carries a relative rounding error of at most 2^-11; the
+# steps of a run add such errors in random directions and transport them with
+# the wave, so the accepted error is the one the storage format is meant to
+# meet: 1 % of the peak pressure (relative L2 of a whole field below 1 %).
+F16_TOL = 1e-2
+
+
+def test_gpu_f16_slab_matches_oracle(bvf, orc):
+    """The 64^3 slab burst with FP16 storage against the FP64 oracle."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.slab_case()
+    s, A = make_pair(bvf, orc, c, storage="f16")
+    s.set_source(c.plane, c.k_src, c.c0, c.envelope, c.n_cycles)
+    A.set_source(c.plane, c.k_src, c.c0, c.envelope, c.n_cycles)
+    s.run(c.n_steps, peak_from=0)
+    s.synchronize()
+    assert A.run(c.n_steps, peak_from=0) == 0
+    peak = s.peak().cpu().numpy()
+    assert rel_l2(s.pressure().cpu().numpy(), A.pressure()) < F16_TOL
+    assert np.abs(peak - A.peak).max() < F16_TOL * A.peak.max()
+    assert rel_l2(peak, A.peak) < F16_TOL
+
+
+def test_gpu_f16_skull_bowl_matches_oracle(bvf, orc):
+    """Focused bowl through the reduced skull phantom with FP16 storage: peak
+    map and FP64 amplitude within 1 %, phase within 0.01 rad where the beam
+    carries at least 10 % of the largest amplitude."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(64, 64, 56, dx=0.5e-3, n_steps=8 * 46, aperture=24e-3, roc=22e-3,
+                         dft_cycles=2, n_pml=6, seed=5)
+    s, A = make_pair(bvf, orc, c, storage="f16")
+    b = c.bowl
+    z_plane = c.k_src * c.dx
+    s.set_source(bvf.rs_plane(b, c.nx, c.ny, c.dx, z_plane, c.f0), c.k_src, c.c0, c.envelope)
+    A.set_source(orc.rs_plane(b["aperture"], b["roc"], b["apex"], b["dir"], c.nx, c.ny, c.dx,
+                              z_plane, c.f0, c.c0, b["p0"]), c.k_src, c.c0, c.envelope)
+    s.run(c.n_steps, peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps)
+    s.synchronize()
+    assert A.run(c.n_steps, peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps) == 0
+    amp_g, ph_g = (t.cpu().numpy() for t in s.amp_phase())
+    amp_r, ph_r = A.amp_phase(c.dft_steps)
+    peak = s.peak().cpu().numpy()
+    assert np.abs(peak - A.peak).max() < F16_TOL * A.peak.max()
+    assert np.abs(amp_g - amp_r).max() < F16_TOL * amp_r.max()
+    beam = amp_r > 0.1 * amp_r.max()
+    assert np.abs(np.angle(np.exp(1j * (ph_g - ph_r))))[beam].max() < 1e-2
+
+
+def test_gpu_f16_fields_round_trip_through_the_storage_scales(bvf):
+    """bvf_set_field / bvf_get_field in FP16 storage: physical FP32 values in
+    and out, stored as the FP16 rounding of value / scale (scales p_ref for
+    stresses, p_ref / 1.5e6 for velocities)."""
+    import torch
+    p_ref = 2.0 ** 15
+    s = bvf.Solver(32, 16, 16, 1e-3, 1e-7, 5e5, n_sls=2, n_pml=0, storage="f16", p_ref=p_ref)
+    rng = np.random.default_rng(3)
+    for fid, scale in ((0, p_ref / 1.5e6), (3, p_ref), (7, p_ref)):
+        v = (rng.standard_normal((16, 16, 32)) * 40.0 * scale).astype(np.float32)
+        s.set_field(fid, torch.from_numpy(v).cuda())
+        got = s.field(fid).cpu().numpy()
+        inv = np.float32(1.0 / scale)
+        expect = (v * inv).astype(np.float16).astype(np.float32) * np.float32(scale)
+        assert np.array_equal(got, expect), fid
+        assert np.abs(got - v).max() <= 2.0 ** -11 * np.abs(v).max() * 1.001
+    s.close()
