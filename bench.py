@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--grid", default="240,240,200")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16"],
+                    help="acoustic state storage of the headline measurement")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the scaled-FP16-storage leg reported under mixed_precision")
     return ap.parse_args()
 
 
@@ -251,7 +255,7 @@ def run_bvf(args):
         pg.barrier()
     from paper_2301_12727_gb300 import plan as planmod
     case = make_case(args, rank)
-    planner = planmod.Planner(case)
+    planner = planmod.Planner(case, storage=args.storage)
     idx_dev = torch.from_numpy(case.index).cuda()
     bowl = case.bowl
     mats = case.materials
@@ -312,14 +316,57 @@ def run_bvf(args):
                "d2h_bytes_per_step": int(out_peak.numel() * 4 + out_tmax.numel() * 4
                                          + out_cem.numel() * 8)}
 
+    # ---- the same plans with the other state storage: throughput and the
+    # differences of every plan output from the headline run
+    mixed = None
+    if not args.no_mixed:
+        other = "f16" if args.storage == "f32" else "f32"
+        pl2 = planmod.Planner(case, storage=other)
+        for _ in range(max(1, args.warmup)):
+            r2 = pl2.run(idx_dev, mats, bowl)
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            r2 = pl2.run(idx_dev, mats, bowl)
+        g1.record(stream)
+        barrier()
+        ms2 = max_over_ranks(g0.elapsed_time(g1), pg, "cuda")
+        ref, tst = (res, r2) if other == "f16" else (r2, res)
+        pk32 = float(ref.peak.max())
+        am32 = float(ref.amp.max())
+        mixed = {"storage": "f16", "arithmetic": "f32",
+                 "value": whole_job_rate(world, args.steps, vox_per_plan,
+                                         ms2 if other == "f16" else ms),
+                 "speedup_vs_f32": (ms / ms2) if other == "f16" else (ms2 / ms),
+                 "errors_vs_f32": {
+                     "focal_peak_rel": abs(float(tst.peak.max()) - pk32) / pk32,
+                     "peak_max_abs_rel": float((tst.peak - ref.peak).abs().max()) / pk32,
+                     "amp_max_abs_rel": float((tst.amp - ref.amp).abs().max()) / am32,
+                     "EL_rel": abs(tst.EL - ref.EL) / ref.EL,
+                     "Tmax_max_abs_C": float((tst.Tmax - ref.Tmax).abs().max()),
+                     "cem43_at_max_rel": abs(float(tst.cem43.max()) - float(ref.cem43.max()))
+                                         / max(float(ref.cem43.max()), 1e-300)}}
+        pl2.close()
+
     # ---- roofline of the dominant kernel (stress + memory variables)
     N = case.voxels
     n_runs = 2 * args.steps
-    stress_bytes = N * (165.0 * case.n_steps + 32.0 * case.dft_steps) * n_runs
+    es = 4.0 if args.storage == "f32" else 2.0      # bytes per state element
+    # stress: read 3 v, read + write 6 sigma and 12 memory variables, index
+    # byte, FP32 peak read + write (+ FP64 C, S read + write in the DFT window);
+    # velocity: read 6 sigma + 3 v, write 3 v, index byte
+    b_str, b_vel = 39.0 * es + 9.0, 12.0 * es + 1.0
+    stress_bytes = N * (b_str * case.n_steps + 32.0 * case.dft_steps) * n_runs
     achieved = stress_bytes / (kt["stress_ms"] / 1e3) / 1e9
     peak, peak_kind = measured_peak_hbm()
-    tr = stress_traffic_per_voxel(case.dft_steps / case.n_steps)
-    vel_bytes = N * 49.0 * case.n_steps * n_runs
+    tr = stress_traffic_per_voxel(case.dft_steps / case.n_steps) if args.storage == "f32" else None
+    vel_bytes = N * b_vel * case.n_steps * n_runs
+    # whole FDTD step: the two-kernel design's bytes, and the minimum one
+    # read + write of the 21-word state plus index and peak
+    fdtd_s = (kt["stress_ms"] + kt["velocity_ms"]) / 1e3
+    design = (stress_bytes + vel_bytes) / fdtd_s / 1e9
+    minimum = N * ((42.0 * es + 9.0) * case.n_steps + 32.0 * case.dft_steps) * n_runs / fdtd_s / 1e9
     roofline = {"bound": "hbm", "kernel": "k_stress_tma<2> (stress + SLS memory + source + capture)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind,
@@ -327,19 +374,27 @@ def run_bvf(args):
                 "algorithmic_bytes_per_launch": stress_bytes / kt["stress_launches"],
                 "avg_launch_ms": kt["stress_ms"] / kt["stress_launches"],
                 "velocity_kernel": {"achieved": vel_bytes / (kt["velocity_ms"] / 1e3) / 1e9,
+                                    "frac": vel_bytes / (kt["velocity_ms"] / 1e3) / 1e9 / peak,
                                     "avg_launch_ms": kt["velocity_ms"] / kt["velocity_launches"]},
+                "fdtd_step": {"design_bytes_per_voxel": b_str + b_vel,
+                              "min_bytes_per_voxel": 42.0 * es + 9.0,
+                              "achieved_design": design, "frac_design": design / peak,
+                              "achieved_min": minimum, "frac_min": minimum / peak},
                 "fdtd_share_of_step": (kt["stress_ms"] + kt["velocity_ms"]) / ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "f32" else "f16 storage, f32 arithmetic",
             "data": "synthetic",
             "config": {"workload": workload(case), "grid": [case.nx, case.ny, case.nz],
                        "fdtd_steps": case.n_steps, "runs_per_step": 2, "n_sls": case.n_sls,
                        "n_pml": case.n_pml, "dft_cycles": case.dft_cycles,
+                       "storage": args.storage,
                        "l2": "inputs larger than L2 (state %.0f MB per run)"
-                             % (N * 4 * (9 + 6 * case.n_sls) / 1e6),
+                             % (N * es * (9 + 6 * case.n_sls) / 1e6),
                        "EL": res.EL, "TS": res.TS},
-            "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks}
+            "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks,
+            "mixed_precision": mixed}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(case)
     if rank == 0:

@@ -25,6 +25,8 @@
 // and L <= 2.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "bvf_stencil.cuh"
 #include "bvf_tma.cuh"
 
@@ -379,6 +381,13 @@ __global__ void __launch_bounds__(NTH, MINB)
         vP2 = vP1 + 3 * VT;
     int iK = ibase + ci, iK1 = iK + IT_SLOT;
 
+    // Blocks whose tile touches no CPML slab in x or y and holds no ghost
+    // or out-of-grid point run a copy of the loop without that code.
+    const bool edge = !(x0 >= p.P && x0 + TX - 1 < nx - p.P - 1 && y0 >= p.P &&
+                        y0 + TY - 1 < ny - p.P - 1);
+    auto march = [&](auto edge_tag) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    const bool lv = EDGE ? live : true;
     int it = 0;
     for (int k = k0; k < k1; ++k, ++it) {
         __syncthreads();
@@ -398,12 +407,12 @@ __global__ void __launch_bounds__(NTH, MINB)
         const int ox = (k * ny + j) * p.W + xs, oy = (k * p.W + ys) * nx + i,
                   oz = (zs * ny + j) * nx + i;
         float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f}, qz[3] = {0.0f, 0.0f, 0.0f};
-        if (live) {
-            if (xs >= 0) {
+        if (lv) {
+            if (EDGE && xs >= 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) qx[c] = p.psx[(3 + c) * Sxs + ox];
             }
-            if (ys >= 0) {
+            if (EDGE && ys >= 0) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) qy[c] = p.psy[(3 + c) * Sys + oy];
             }
@@ -412,7 +421,7 @@ __global__ void __launch_bounds__(NTH, MINB)
                 for (int c = 0; c < 3; ++c) qz[c] = p.psz[(3 + c) * Szs + oz];
             }
         }
-        if (live) {
+        if (lv) {
 #pragma unroll
             for (int cc = 0; cc < 6; ++cc) sv[cc] = tof(gs[cc][q]);
 #pragma unroll
@@ -427,11 +436,11 @@ __global__ void __launch_bounds__(NTH, MINB)
             }
         }
         const bool ready = tma::mbar_wait(&bars[it % 3], (it / 3) & 1, p.flag);
-        if (ready && live) {
+        if (ready && lv) {
             const int vm2 = vM2, vm1 = vM1, vp1 = vP1, vp2 = vP2;
             const unsigned char *I0 = smb + iK;
             const unsigned char *I1 = smb + iK1;
-            const bool ix1 = i < nx - 1, jy1 = j < ny - 1, kz1 = k < nz - 1;
+            const bool ix1 = !EDGE || i < nx - 1, jy1 = !EDGE || j < ny - 1, kz1 = k < nz - 1;
             const int m00 = I0[0];
             const st::StressCoef c0 = s_lut[m00];
             const int vx = vK, vy = vK + VT, vz = vK + 2 * VT;
@@ -442,8 +451,8 @@ __global__ void __launch_bounds__(NTH, MINB)
                             tof(smt[vy + VW]), ix);
             float ezz = dbw(tof(smt[vm2 + 2 * VT]), tof(smt[vm1 + 2 * VT]), tof(smt[vz]),
                             tof(smt[vp1 + 2 * VT]), ix);
-            if (xs >= 0) exx = st::cpml_pre(p.psx + 3 * Sxs + ox, qx[0], __ldg(&pmlx[i]), exx);
-            if (ys >= 0) eyy = st::cpml_pre(p.psy + 3 * Sys + oy, qy[0], __ldg(&pmly[j]), eyy);
+            if (EDGE && xs >= 0) exx = st::cpml_pre(p.psx + 3 * Sxs + ox, qx[0], __ldg(&pmlx[i]), exx);
+            if (EDGE && ys >= 0) eyy = st::cpml_pre(p.psy + 3 * Sys + oy, qy[0], __ldg(&pmly[j]), eyy);
             if (zs >= 0) ezz = st::cpml_pre(p.psz + 3 * Szs + oz, qz[0], __ldg(&pmlz[k]), ezz);
             float srcv = 0.0f;
             if (p.src_on && k == p.k_src) {
@@ -460,13 +469,13 @@ __global__ void __launch_bounds__(NTH, MINB)
                 float a = dfw(tof(smt[vx - VW]), tof(smt[vx]), tof(smt[vx + VW]),
                               tof(smt[vx + 2 * VW]), ix);
                 float b = dfw(tof(smt[vy - 1]), tof(smt[vy]), tof(smt[vy + 1]), tof(smt[vy + 2]), ix);
-                if (ys >= 0) {
+                if (EDGE && ys >= 0) {
                     const float2 h = __ldg(&pmly[p.nmax + j]);
                     const float t = fmaf(h.x, a, h.y * qy[1]);
                     if (dxy) p.psy[4 * Sys + oy] = t;
                     a += t;
                 }
-                if (xs >= 0) {
+                if (EDGE && xs >= 0) {
                     const float2 h = __ldg(&pmlx[p.nmax + i]);
                     const float t = fmaf(h.x, b, h.y * qx[1]);
                     if (dxy) p.psx[4 * Sxs + ox] = t;
@@ -483,7 +492,7 @@ __global__ void __launch_bounds__(NTH, MINB)
                     if (dxz) p.psz[4 * Szs + oz] = t;
                     a += t;
                 }
-                if (xs >= 0) {
+                if (EDGE && xs >= 0) {
                     const float2 h = __ldg(&pmlx[p.nmax + i]);
                     const float t = fmaf(h.x, b, h.y * qx[2]);
                     if (dxz) p.psx[5 * Sxs + ox] = t;
@@ -502,7 +511,7 @@ __global__ void __launch_bounds__(NTH, MINB)
                     if (dyz) p.psz[5 * Szs + oz] = t;
                     a += t;
                 }
-                if (ys >= 0) {
+                if (EDGE && ys >= 0) {
                     const float2 h = __ldg(&pmly[p.nmax + j]);
                     const float t = fmaf(h.x, b, h.y * qy[2]);
                     if (dyz) p.psy[5 * Sys + oy] = t;
@@ -538,6 +547,11 @@ __global__ void __launch_bounds__(NTH, MINB)
         iK1 += IT_SLOT;
         if (iK1 >= iend) iK1 -= Lay::RI * IT_SLOT;
     }
+    };
+    if (edge)
+        march(std::true_type{});
+    else
+        march(std::false_type{});
 }
 
 }  // namespace

@@ -16,6 +16,20 @@ __device__ __forceinline__ float tof(float v) { return v; }
 __device__ __forceinline__ float tof(__half v) { return __half2float(v); }
 __device__ __forceinline__ void stv(float *p, float v) { *p = v; }
 __device__ __forceinline__ void stv(__half *p, float v) { *p = __float2half_rn(v); }
+// two neighbouring elements (x, x+1) at an even element offset
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld2(const __half *p)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(p));
+}
+__device__ __forceinline__ void st2(float *p, float a, float b)
+{
+    *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st2(__half *p, float a, float b)
+{
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+}
 
 constexpr float kC1 = 1.125f;            // 9/8
 constexpr float kC2 = -1.0f / 24.0f;     // -1/24

@@ -60,16 +60,17 @@ class PlanResult:
 
 
 class Planner:
-    """Two contexts (skull run, water run) on one grid, reused across plans."""
+    """Two contexts (skull run, water run) on one grid, reused across plans.
+    storage: "f32" or "f16" (scaled FP16 acoustic state, FP32 arithmetic)."""
 
-    def __init__(self, case: Case):
+    def __init__(self, case: Case, storage: str = "f32"):
         import torch
         self.case = case
         c = case
         self.skull = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, qc=c.qc, n_sls=c.n_sls,
-                                n_pml=c.n_pml, pml_R=c.pml_R)
+                                n_pml=c.n_pml, pml_R=c.pml_R, storage=storage)
         self.water = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, qc=c.qc, n_sls=c.n_sls,
-                                n_pml=c.n_pml, pml_R=c.pml_R)
+                                n_pml=c.n_pml, pml_R=c.pml_R, storage=storage)
         self.water_idx = torch.zeros((c.nz, c.ny, c.nx), dtype=torch.uint8, device="cuda")
         self.water_table = np.array([water_row(c.f0)])
         self.water.set_materials(self.water_idx, self.water_table)
