@@ -312,6 +312,51 @@ int bvf_kernel_timing(bvf_ctx *ctx, int enable);
  * timing was enabled. */
 int bvf_get_kernel_times(bvf_ctx *ctx, bvf_kernel_times *out);
 
+/* ---- batched planning sweeps -------------------------------------------
+ * Several contexts (different grids, materials, sources, frequencies; the
+ * paper repeats its acoustic step for each transducer placement, Sec. 2.3)
+ * advanced in lockstep.  Each step is two persistent launches that share the
+ * GPU among all domains: one velocity and one stress kernel over a work list
+ * of (domain, 32 x 8 tile, z-chunk) items, plus a one-thread kernel advancing
+ * the step counter the kernels read.  Results are those of bvf_run_acoustic
+ * on each context, bit for bit.  The paper has no counterpart of this call;
+ * it serves sweeps over placements and frequencies.
+ *
+ * bvf_batch_create: the contexts stay owned by the caller and must outlive
+ * the batch; each needs its materials set, nx % 16 == 0 and at most 2 SLS
+ * mechanisms, and all share the SLS count and storage type (BVF_E_ARG
+ * otherwise).  Sources are taken from the contexts at each run. */
+typedef struct bvf_batch bvf_batch;
+int bvf_batch_create(bvf_ctx *const *ctxs, int n, bvf_batch **out);
+void bvf_batch_destroy(bvf_batch *b);
+
+/* Advance context d by n_steps[d] steps (lockstep; a domain whose count is
+ * reached is skipped by later steps), with capture windows caps[d] (NULL: no
+ * capture for any domain).  kchunk: z-planes per work item for every domain
+ * (0: each context's default).  graph_steps > 0 captures that many steps in
+ * a CUDA graph and replays it (launch overhead of one graph per graph_steps
+ * steps); 0 launches the kernels directly.  Asynchronous on `stream`;
+ * bvf_synchronize on each context reports its errors. */
+int bvf_batch_run(bvf_batch *b, const int *n_steps, const bvf_capture *caps, int kchunk,
+                  int graph_steps, void *stream);
+
+/* The same sweep as separate per-context launches (bvf_run_acoustic) spread
+ * over n_streams streams of the batch: contexts dealt round-robin, each
+ * stream running its contexts one after another, so kernels of different
+ * domains overlap (the stream-level alternative to the persistent batch
+ * kernels).  Forks from and joins back into `stream`. */
+int bvf_batch_run_streams(bvf_batch *b, const int *n_steps, const bvf_capture *caps,
+                          int n_streams, void *stream);
+
+/* Tile autotuner: times trial_steps steps of every domain for each candidate
+ * z-chunk length, returns the fastest and its time per step (ms), and leaves
+ * every context reset (bvf_reset: state, captures and step counts zeroed). */
+int bvf_batch_tune(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,
+                   int *best_kchunk, double *best_ms_per_step, void *stream);
+
+/* Kernel launches enqueued by this batch so far (3 per step). */
+int bvf_batch_launches(const bvf_batch *b, long long *out);
+
 #ifdef __cplusplus
 }
 #endif

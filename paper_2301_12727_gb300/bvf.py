@@ -27,7 +27,8 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_run_acoustic", "bvf_synchronize", "bvf_get_field", "bvf_set_field",
            "bvf_get_pressure", "bvf_get_peak", "bvf_get_amp_phase", "bvf_run_thermal",
            "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times",
-           "bvf_transmission_noalloc")
+           "bvf_transmission_noalloc", "bvf_batch_create", "bvf_batch_destroy", "bvf_batch_run",
+           "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams")
 
 
 class BvfError(RuntimeError):
@@ -125,6 +126,14 @@ def lib():
         L.bvf_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.bvf_kernel_timing.argtypes = [vp, i]
         L.bvf_get_kernel_times.argtypes = [vp, ctypes.POINTER(KernelTimes)]
+        L.bvf_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+        L.bvf_batch_destroy.argtypes = [vp]
+        L.bvf_batch_destroy.restype = None
+        L.bvf_batch_run.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, i, vp]
+        L.bvf_batch_tune.argtypes = [vp, i, ctypes.POINTER(i), i, ctypes.POINTER(i),
+                                     ctypes.POINTER(d), vp]
+        L.bvf_batch_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.bvf_batch_run_streams.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
         _lib = L
     return _lib
 
@@ -410,3 +419,73 @@ def rs_plane(bowl: dict, nx, ny, dx, z_plane, f0, c0=1500.0, ds_over_lambda=0.25
     out = torch.empty((ny, nx, 2), dtype=torch.float32, device="cuda")
     bvf_rs_plane(b, nx, ny, dx, z_plane, f0, out, stream)
     return out
+
+
+# ---- batched sweeps ---------------------------------------------------------
+def bvf_batch_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c
+                                          for c in ctxs])
+    out = ctypes.c_void_p()
+    _check(lib().bvf_batch_create(arr, len(ctxs), ctypes.byref(out)))
+    return out
+
+
+def bvf_batch_run(batch, n_steps, caps=None, kchunk=0, graph_steps=0, stream=None):
+    n = len(n_steps)
+    steps = (ctypes.c_int * n)(*[int(v) for v in n_steps])
+    cp = None
+    if caps is not None:
+        cp = (Capture * n)(*[c if isinstance(c, Capture) else Capture(*c) for c in caps])
+    _check(lib().bvf_batch_run(batch, steps, cp, int(kchunk), int(graph_steps), _stream(stream)))
+
+
+def bvf_batch_tune(batch, trial_steps, candidates, stream=None):
+    cand = (ctypes.c_int * len(candidates))(*[int(v) for v in candidates])
+    best, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib().bvf_batch_tune(batch, int(trial_steps), cand, len(candidates), ctypes.byref(best),
+                                ctypes.byref(ms), _stream(stream)))
+    return best.value, ms.value
+
+
+class Batch:
+    """Several Solvers advanced in lockstep by the persistent batch kernels
+    (optionally replayed from a CUDA graph)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.handle = bvf_batch_create([s.ctx for s in self.solvers])
+
+    def run(self, n_steps, caps=None, kchunk=0, graph_steps=0, stream=None):
+        if isinstance(n_steps, int):
+            n_steps = [n_steps] * len(self.solvers)
+        bvf_batch_run(self.handle, n_steps, caps, kchunk, graph_steps, stream)
+
+    def run_streams(self, n_steps, caps=None, n_streams=4, stream=None):
+        n = len(self.solvers)
+        if isinstance(n_steps, int):
+            n_steps = [n_steps] * n
+        steps = (ctypes.c_int * n)(*[int(v) for v in n_steps])
+        cp = None
+        if caps is not None:
+            cp = (Capture * n)(*[c if isinstance(c, Capture) else Capture(*c) for c in caps])
+        _check(lib().bvf_batch_run_streams(self.handle, steps, cp, int(n_streams),
+                                           _stream(stream)))
+
+    def tune(self, trial_steps=20, candidates=(6, 8, 10, 13, 16, 24), stream=None):
+        return bvf_batch_tune(self.handle, trial_steps, candidates, stream)
+
+    def launches(self):
+        out = ctypes.c_longlong()
+        _check(lib().bvf_batch_launches(self.handle, ctypes.byref(out)))
+        return out.value
+
+    def close(self):
+        if self.handle:
+            lib().bvf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

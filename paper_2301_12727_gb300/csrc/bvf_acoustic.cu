@@ -278,9 +278,9 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc)
                     rv[l][cc] = st::tof(mem[(size_t)(l * 6 + cc) * p.fstride + q]);
-            const float pk = p.do_peak ? peak[q] : 0.0f;
+            const float pk = (p.st.flags & kStepPeak) ? peak[q] : 0.0f;
             double dC = 0.0, dS = 0.0;
-            if (p.do_dft) { dC = p.dftC[q]; dS = p.dftS[q]; }
+            if (p.st.flags & kStepDft) { dC = p.dftC[q]; dS = p.dftS[q]; }
             const st::StressCoef c0 = s_lut[m00];
 
             // ---- normal stresses at (i, j, k)
@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
             if (ys >= 0) eyy = cpml(p.psy + 3 * Sys + qy, pmly[g.j], eyy);
             if (zs >= 0) ezz = cpml(p.psz + 3 * Szs + qz, pmlz[k], ezz);
             float srcv = 0.0f;
-            if (p.src_on && k == p.k_src) {
+            if ((p.st.flags & kStepSource) && k == p.k_src) {
                 const float2 a = p.src[g.col];
-                srcv = p.src_scale * fmaf(a.x, p.src_ws, a.y * p.src_wc);
+                srcv = p.src_scale * fmaf(a.x, p.st.src_ws, a.y * p.st.src_wc);
             }
             st::normal_update<L>(p, c0, exx, eyy, ezz, srcv, sv, rv);
             const float pr = st::pressure(sv);
@@ -339,10 +339,10 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
                     const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
                     if (w) st::stv(mem + (size_t)(l * 6 + cc) * p.fstride + q, rv[l][cc]);
                 }
-            if (p.do_peak) peak[q] = fmaxf(pk, fabsf(pr));
-            if (p.do_dft) {
-                p.dftC[q] = fma((double)pr, p.cw, dC);
-                p.dftS[q] = fma((double)pr, p.sw, dS);
+            if (p.st.flags & kStepPeak) peak[q] = fmaxf(pk, fabsf(pr));
+            if (p.st.flags & kStepDft) {
+                p.dftC[q] = fma((double)pr, p.st.cw, dC);
+                p.dftS[q] = fma((double)pr, p.st.sw, dS);
             }
         }
         ax0 = ax1; ax1 = ax2; ax2 = ax3; ax3 = nax;

@@ -87,26 +87,29 @@ struct VelLayout {
                   "TMA destinations must stay 128-byte aligned");
 };
 
-template <typename T>
-__global__ void __launch_bounds__(NTH, 5)
-    k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
-                   const __grid_constant__ VelocityTmaMaps tm)
+// One tile (bx, by) of the grid over z-chunk bz.  REUSE: the block runs
+// further tiles afterwards (persistent batch kernel), so its mbarriers are
+// invalidated at the end and the first copies are fenced against the
+// previous tile's reads of the same shared memory.
+template <typename T, bool REUSE>
+__device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityTmaMaps &tm,
+                                              int kchunk, int bx, int by, int bz,
+                                              unsigned char *smb)
 {
     using Lay = VelLayout<T>;
     using Bx = Box<T>;
     constexpr int XW = Lay::XW, YW = Lay::YW, VW = Bx::BW;
     constexpr int TXX = Lay::TXX, TYY = Lay::TYY, TZZ = Lay::TZZ;
-    extern __shared__ __align__(1024) unsigned char smb[];
     const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
     float *s_rho = reinterpret_cast<float *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int i = x0 + tx, j = y0 + ty;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;
-    const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
+    const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
     for (int m = tid; m < p.n_mat; m += NTH) s_rho[m] = p.lut[m].rho;
     if (tid == 0) {
         tma::mbar_init(&bars[0], 1);
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(NTH, 5)
     };
 
     if (tid == 0) {
+        if (REUSE) tma::fence_async_smem();
         tma::mbar_expect_tx(&bars[0], A_BYTES + 4 * B_BYTES + 4 * C_BYTES + 2 * IT);
         ldA(k0, 0, &bars[0]);
         for (int d = 0; d < 4; ++d) ldB(k0 - 2 + d, d, &bars[0]);
@@ -298,6 +302,22 @@ __global__ void __launch_bounds__(NTH, 5)
             oy += doy;
         }
     }
+    if (REUSE) {
+        __syncthreads();
+        if (tid == 0) {
+            tma::mbar_inval(&bars[0]);
+            tma::mbar_inval(&bars[1]);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH, 5)
+    k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
+                   const __grid_constant__ VelocityTmaMaps tm)
+{
+    extern __shared__ __align__(1024) unsigned char smb[];
+    velocity_tile<T, false>(p, tm, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
 }
 
 // ------------------------------------------------------------------ stress
@@ -319,25 +339,25 @@ struct StressLayout {
                   "TMA destinations must stay 128-byte aligned");
 };
 
-template <int L, int MINB, typename T>
-__global__ void __launch_bounds__(NTH, MINB)
-    k_stress_tma(const __grid_constant__ AcParams p, int kchunk,
-                 const __grid_constant__ StressTmaMaps tm)
+// One tile (bx, by) over z-chunk bz; REUSE as for velocity_tile.
+template <int L, typename T, bool REUSE>
+__device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMaps &tm,
+                                            const StepParam &st, int kchunk, int bx, int by,
+                                            int bz, unsigned char *smb)
 {
     using Lay = StressLayout<L, T>;
     using Bx = Box<T>;
     constexpr int VW = Bx::BW, VT = Bx::VT;
-    extern __shared__ __align__(1024) unsigned char smb[];
     const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
     st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int i = x0 + tx, j = y0 + ty;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;
-    const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
+    const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
     for (int m = tid; m < p.n_mat; m += NTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
     if (tid == 0) {
         for (int b = 0; b < 3; ++b) tma::mbar_init(&bars[b], 1);
@@ -358,6 +378,7 @@ __global__ void __launch_bounds__(NTH, MINB)
             tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar);
     };
     if (tid == 0) {
+        if (REUSE) tma::fence_async_smem();
         issue(k0, &bars[0], true);
         if (k0 + 1 < k1) issue(k0 + 1, &bars[1], false);
     }
@@ -429,8 +450,8 @@ __global__ void __launch_bounds__(NTH, MINB)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc)
                     rv[l][cc] = tof(mem[(size_t)(l * 6 + cc) * p.fstride + q]);
-            if (p.do_peak) pk = p.peak[q];
-            if (p.do_dft) {
+            if (st.flags & kStepPeak) pk = p.peak[q];
+            if (st.flags & kStepDft) {
                 dC = p.dftC[q];
                 dS = p.dftS[q];
             }
@@ -455,9 +476,9 @@ __global__ void __launch_bounds__(NTH, MINB)
             if (EDGE && ys >= 0) eyy = st::cpml_pre(p.psy + 3 * Sys + oy, qy[0], __ldg(&pmly[j]), eyy);
             if (zs >= 0) ezz = st::cpml_pre(p.psz + 3 * Szs + oz, qz[0], __ldg(&pmlz[k]), ezz);
             float srcv = 0.0f;
-            if (p.src_on && k == p.k_src) {
+            if ((st.flags & kStepSource) && k == p.k_src) {
                 const float2 a = p.src[j * nx + i];
-                srcv = p.src_scale * fmaf(a.x, p.src_ws, a.y * p.src_wc);
+                srcv = p.src_scale * fmaf(a.x, st.src_ws, a.y * st.src_wc);
             }
             st::normal_update<L>(p, c0, exx, eyy, ezz, srcv, sv, rv);
             const float pr = st::pressure(sv);
@@ -533,10 +554,10 @@ __global__ void __launch_bounds__(NTH, MINB)
                     const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
                     if (w) st::stv(mem + (size_t)(l * 6 + cc) * p.fstride + q, rv[l][cc]);
                 }
-            if (p.do_peak) p.peak[q] = fmaxf(pk, fabsf(pr));
-            if (p.do_dft) {
-                p.dftC[q] = fma((double)pr, p.cw, dC);
-                p.dftS[q] = fma((double)pr, p.sw, dS);
+            if (st.flags & kStepPeak) p.peak[q] = fmaxf(pk, fabsf(pr));
+            if (st.flags & kStepDft) {
+                p.dftC[q] = fma((double)pr, st.cw, dC);
+                p.dftS[q] = fma((double)pr, st.sw, dS);
             }
         }
         // rotate the ring positions to plane k+1
@@ -552,7 +573,122 @@ __global__ void __launch_bounds__(NTH, MINB)
         march(std::true_type{});
     else
         march(std::false_type{});
+    if (REUSE) {
+        __syncthreads();
+        if (tid == 0)
+            for (int b = 0; b < 3; ++b) tma::mbar_inval(&bars[b]);
+    }
 }
+
+template <int L, int MINB, typename T>
+__global__ void __launch_bounds__(NTH, MINB)
+    k_stress_tma(const __grid_constant__ AcParams p, int kchunk,
+                 const __grid_constant__ StressTmaMaps tm)
+{
+    extern __shared__ __align__(1024) unsigned char smb[];
+    stress_tile<L, T, false>(p, tm, p.st, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
+}
+
+// ------------------------------------------------------------------ batch
+// Persistent kernels over a work list spanning several domains: block b takes
+// items b, b + gridDim.x, ...; an item is one tile and z-chunk of one domain.
+// The domain's parameters are copied to shared memory and the tile runs the
+// same code as the single-domain kernels.  Domains whose run has ended by
+// this step are skipped.
+
+// Per-block walk over the work list, kept in shared memory so that nothing
+// but the tile's own state is live in registers during a tile.  A block's
+// items ascend, so its domain index only moves forward: thread 0 scans on
+// from the previous domain and skips items of domains that have finished.
+struct WalkState {
+    int w, d, loaded, step;
+    int fresh;          // the item's domain differs from the previous item's
+};
+
+__device__ __forceinline__ void walk_begin(WalkState &ws, const int *step_ctr, int tid)
+{
+    if (tid == 0) {
+        ws.w = (int)blockIdx.x - (int)gridDim.x;
+        ws.d = 0;
+        ws.loaded = -1;
+        ws.step = *step_ctr;
+    }
+}
+
+// thread 0: move to the next item of an unfinished domain (w = -1 at the end)
+__device__ __forceinline__ void walk_next(WalkState &ws, const BatchParams &bp)
+{
+    int w = ws.w, d = ws.d;
+    for (;;) {
+        w += gridDim.x;
+        if (w >= bp.total) {
+            w = -1;
+            break;
+        }
+        while (d + 1 < bp.n_dom && bp.block0[d + 1] <= w) ++d;
+        if (ws.step < bp.n_steps[d]) break;
+    }
+    ws.w = w;
+    ws.d = d;
+    ws.fresh = (w >= 0 && d != ws.loaded) ? 1 : 0;
+    if (ws.fresh) ws.loaded = d;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTH, 5)
+    k_velocity_batch(const __grid_constant__ BatchParams bp, const int *step_ctr)
+{
+    extern __shared__ __align__(1024) unsigned char smb[];
+    __shared__ WalkState ws;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    walk_begin(ws, step_ctr, tid);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) walk_next(ws, bp);
+        __syncthreads();
+        if (ws.w < 0) break;
+        const int d = ws.d;
+        if (tid == 0 && ws.fresh) {
+            // tensor maps in device memory, written before the launch
+            for (int g = 0; g < 6; ++g) tma::tensormap_acquire(&bp.vm[d].sg[g]);
+            tma::tensormap_acquire(&bp.vm[d].idx);
+        }
+        const int li = ws.w - bp.block0[d], tx_ = bp.tiles_x[d], txy = tx_ * bp.tiles_y[d];
+        velocity_tile<T, true>(bp.p[d], bp.vm[d], bp.kchunk[d], li % tx_, (li % txy) / tx_,
+                               li / txy, smb);
+    }
+}
+
+template <int L, int MINB, typename T>
+__global__ void __launch_bounds__(NTH, MINB)
+    k_stress_batch(const __grid_constant__ BatchParams bp, const int *step_ctr)
+{
+    extern __shared__ __align__(1024) unsigned char smb[];
+    __shared__ WalkState ws;
+    __shared__ StepParam sq;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    walk_begin(ws, step_ctr, tid);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) walk_next(ws, bp);
+        __syncthreads();
+        if (ws.w < 0) break;
+        const int d = ws.d;
+        if (ws.fresh) {      // the same value for every thread (set before the barrier)
+            if (tid == 0) {
+                sq = bp.steps[bp.step_off[d] + ws.step];
+                for (int g = 0; g < 3; ++g) tma::tensormap_acquire(&bp.sm[d].v[g]);
+                tma::tensormap_acquire(&bp.sm[d].idx);
+            }
+            __syncthreads();
+        }
+        const int li = ws.w - bp.block0[d], tx_ = bp.tiles_x[d], txy = tx_ * bp.tiles_y[d];
+        stress_tile<L, T, true>(bp.p[d], bp.sm[d], sq, bp.kchunk[d], li % tx_,
+                                (li % txy) / tx_, li / txy, smb);
+    }
+}
+
+__global__ void k_step_advance(int *ctr) { *ctr += 1; }
 
 }  // namespace
 
@@ -607,6 +743,66 @@ static cudaError_t launch_stress_tma_l(const AcParams &p, const StressTmaMaps &t
 cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     return p.h16 ? launch_stress_tma_l<__half>(p, tm, s) : launch_stress_tma_l<float>(p, tm, s);
+}
+
+template <int L, typename T>
+static cudaError_t batch_prepare_t(int n_mat_max, int *gv, int *gs)
+{
+    const size_t smv = VelLayout<T>::bytes(n_mat_max), sms = StressLayout<L, T>::bytes(n_mat_max);
+    cudaError_t e = cudaFuncSetAttribute(k_velocity_batch<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_stress_batch<L, 4, T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+    int dev = 0, sm_count = 0, bv = 0, bs = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bv, k_velocity_batch<T>, NTH, smv);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stress_batch<L, 4, T>, NTH, sms);
+    if (e != cudaSuccess) return e;
+    *gv = sm_count * (bv > 0 ? bv : 1);
+    *gs = sm_count * (bs > 0 ? bs : 1);
+    return cudaSuccess;
+}
+
+template <int L, typename T>
+static cudaError_t launch_batch_t(const BatchParams &bp, int n_mat_max, int *d_step, int gv, int gs,
+                                  cudaStream_t s)
+{
+    const size_t smv = VelLayout<T>::bytes(n_mat_max), sms = StressLayout<L, T>::bytes(n_mat_max);
+    k_velocity_batch<T><<<gv, dim3(TX, TY, 1), smv, s>>>(bp, d_step);
+    k_stress_batch<L, 4, T><<<gs, dim3(TX, TY, 1), sms, s>>>(bp, d_step);
+    k_step_advance<<<1, 1, 0, s>>>(d_step);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_prepare(int L, int h16, int n_mat_max, int *gv, int *gs)
+{
+    switch (L * 2 + (h16 ? 1 : 0)) {
+    case 0: return batch_prepare_t<0, float>(n_mat_max, gv, gs);
+    case 1: return batch_prepare_t<0, __half>(n_mat_max, gv, gs);
+    case 2: return batch_prepare_t<1, float>(n_mat_max, gv, gs);
+    case 3: return batch_prepare_t<1, __half>(n_mat_max, gv, gs);
+    case 4: return batch_prepare_t<2, float>(n_mat_max, gv, gs);
+    case 5: return batch_prepare_t<2, __half>(n_mat_max, gv, gs);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_step(const BatchParams &bp, int L, int h16, int n_mat_max, int *d_step,
+                              int gv, int gs, cudaStream_t s)
+{
+    switch (L * 2 + (h16 ? 1 : 0)) {
+    case 0: return launch_batch_t<0, float>(bp, n_mat_max, d_step, gv, gs, s);
+    case 1: return launch_batch_t<0, __half>(bp, n_mat_max, d_step, gv, gs, s);
+    case 2: return launch_batch_t<1, float>(bp, n_mat_max, d_step, gv, gs, s);
+    case 3: return launch_batch_t<1, __half>(bp, n_mat_max, d_step, gv, gs, s);
+    case 4: return launch_batch_t<2, float>(bp, n_mat_max, d_step, gv, gs, s);
+    case 5: return launch_batch_t<2, __half>(bp, n_mat_max, d_step, gv, gs, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // z-chunk length of the TMA kernels: about six waves of four resident blocks

@@ -84,6 +84,26 @@ struct bvf_ctx {
     long long vel_n = 0, str_n = 0;
 };
 
+struct bvf_batch {
+    std::vector<bvf_ctx *> ctx;       // not owned
+    int L = 0, h16 = 0, n_mat_max = 1;
+    int grid_vel = 0, grid_str = 0;   // persistent grid sizes
+    StressTmaMaps *d_sm = nullptr;    // [ctx.size()]
+    VelocityTmaMaps *d_vm = nullptr;
+    StepParam *d_steps = nullptr;
+    size_t steps_cap = 0;
+    int *d_step = nullptr;            // step counter read by the kernels
+    cudaStream_t cap = nullptr;       // stream the graph is captured on
+    cudaGraphExec_t exec = nullptr;
+    BatchParams bp{};
+    std::vector<StepParam> h_steps;
+    long long launches = 0;
+    // side streams of bvf_batch_run_streams, with their join events
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_ev;
+    cudaEvent_t fork = nullptr;
+};
+
 namespace {
 
 int fail(bvf_ctx *c, int code, const std::string &msg)
@@ -98,6 +118,13 @@ int cuda_fail(bvf_ctx *c, cudaError_t e, const char *where)
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     return fail(c, e == cudaErrorMemoryAllocation ? BVF_E_NOMEM : BVF_E_CUDA, m);
 }
+
+// context-free variant of CK (batch calls report through bvf_last_error(NULL))
+#define CK_FREE(call, where)                                       \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(nullptr, e_, where); \
+    } while (0)
 
 #define CK(call, where)                                      \
     do {                                                     \
@@ -332,7 +359,39 @@ AcParams make_params(bvf_ctx *c)
     p.dftS = c->dftS;
     p.flag = c->flag;
     p.kchunk = c->kchunk;
+    p.src_scale = (float)(2.0 * c->c0 * c->g.dt / c->g.dx / c->s_sig);
     return p;
+}
+
+// Source and capture parameters of the update n -> n+1 (source sampled at
+// (n + 1/2) dt, capture of p at (n + 1) dt).
+StepParam step_param(const bvf_ctx *c, const bvf_capture &cp, long long n)
+{
+    const double w = 2.0 * kPi * c->ph.f0, dt = c->g.dt;
+    const double t = (n + 0.5) * dt;
+    const double env = c->have_source ? envelope(c->envelope, c->n_cycles, c->ph.f0, t) : 0.0;
+    const long long step = n + 1;
+    const bool peak = cp.peak_from >= 0 && step >= cp.peak_from;
+    const bool dft = cp.dft_steps > 0 && step >= cp.dft_start &&
+                     step < (long long)cp.dft_start + cp.dft_steps;
+    StepParam q{};
+    q.flags = ((c->have_source && env != 0.0) ? 1 : 0) | (peak ? 2 : 0) | (dft ? 4 : 0);
+    q.src_ws = (float)(env * std::sin(w * t));
+    q.src_wc = (float)(env * std::cos(w * t));
+    q.cw = std::cos(w * step * dt);
+    q.sw = std::sin(w * step * dt);
+    return q;
+}
+
+// FP64 DFT sums of a context, allocated and zeroed on first use
+int ensure_dft(bvf_ctx *c, cudaStream_t s)
+{
+    if (c->dftC) return BVF_OK;
+    CK(cudaMalloc(&c->dftC, c->N * sizeof(double)), "dft buffers");
+    CK(cudaMalloc(&c->dftS, c->N * sizeof(double)), "dft buffers");
+    CK(cudaMemsetAsync(c->dftC, 0, c->N * sizeof(double), s), "dft buffers");
+    CK(cudaMemsetAsync(c->dftS, 0, c->N * sizeof(double), s), "dft buffers");
+    return BVF_OK;
 }
 
 }  // namespace
@@ -587,28 +646,13 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
     bvf_capture cp{-1, 0, 0};
     if (cap) cp = *cap;
     if (cp.dft_steps < 0) return fail(c, BVF_E_ARG, "bvf_run_acoustic: negative dft_steps");
-    if (cp.dft_steps > 0 && !c->dftC) {
-        CK(cudaMalloc(&c->dftC, c->N * sizeof(double)), "dft buffers");
-        CK(cudaMalloc(&c->dftS, c->N * sizeof(double)), "dft buffers");
-        CK(cudaMemsetAsync(c->dftC, 0, c->N * sizeof(double), s), "dft buffers");
-        CK(cudaMemsetAsync(c->dftS, 0, c->N * sizeof(double), s), "dft buffers");
-        setup_maps(c);
+    if (cp.dft_steps > 0) {
+        const int rc = ensure_dft(c, s);
+        if (rc != BVF_OK) return rc;
     }
     AcParams p = make_params(c);
-    const double w = 2.0 * kPi * c->ph.f0, dt = c->g.dt;
-    p.src_scale = (float)(2.0 * c->c0 * dt / c->g.dx / c->s_sig);
     for (int it = 0; it < n_steps; ++it) {
-        const long long n = c->steps;
-        const double t = (n + 0.5) * dt;
-        const double env = c->have_source ? envelope(c->envelope, c->n_cycles, c->ph.f0, t) : 0.0;
-        p.src_on = (c->have_source && env != 0.0) ? 1 : 0;
-        p.src_ws = (float)(env * std::sin(w * t));
-        p.src_wc = (float)(env * std::cos(w * t));
-        const long long step = n + 1;
-        p.do_peak = (cp.peak_from >= 0 && step >= cp.peak_from) ? 1 : 0;
-        p.do_dft = (cp.dft_steps > 0 && step >= cp.dft_start && step < (long long)cp.dft_start + cp.dft_steps) ? 1 : 0;
-        p.cw = std::cos(w * step * dt);
-        p.sw = std::sin(w * step * dt);
+        p.st = step_param(c, cp, c->steps);
         auto vel = [&]() {
             return c->tma ? launch_velocity_tma(p, c->vmaps, s) : launch_velocity(p, s);
         };
@@ -635,7 +679,7 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
             CK(str(), "stress kernel");
         }
         c->launches += 2;
-        c->dft_count += p.do_dft;
+        c->dft_count += (p.st.flags & kStepDft) ? 1 : 0;
         c->steps++;
     }
     return BVF_OK;
@@ -905,6 +949,259 @@ int bvf_get_kernel_times(bvf_ctx *c, bvf_kernel_times *out)
     out->stress_launches = c->str_n;
     out->velocity_ms = c->vel_ms;
     out->stress_ms = c->str_ms;
+    return BVF_OK;
+}
+
+// ---- batched runs --------------------------------------------------------
+
+int bvf_batch_create(bvf_ctx *const *ctxs, int n, bvf_batch **out)
+{
+    if (!out) return fail(nullptr, BVF_E_ARG, "bvf_batch_create: out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1 || n > kMaxBatch)
+        return fail(nullptr, BVF_E_ARG, "bvf_batch_create: need 1 to 64 contexts");
+    for (int d = 0; d < n; ++d) {
+        const bvf_ctx *c = ctxs[d];
+        if (!c || !c->have_materials)
+            return fail(nullptr, BVF_E_ARG, "bvf_batch_create: NULL context or materials not set");
+        if (!c->tma || !c->tma_stress)
+            return fail(nullptr, BVF_E_ARG,
+                        "bvf_batch_create: every grid needs nx % 16 == 0 and at most 2 SLS");
+        if (c->L != ctxs[0]->L || c->h16 != ctxs[0]->h16)
+            return fail(nullptr, BVF_E_ARG,
+                        "bvf_batch_create: contexts differ in SLS count or storage");
+    }
+    bvf_batch *b = new (std::nothrow) bvf_batch;
+    if (!b) return fail(nullptr, BVF_E_NOMEM, "bvf_batch_create: host allocation failed");
+    b->ctx.assign(ctxs, ctxs + n);
+    b->L = ctxs[0]->L;
+    b->h16 = ctxs[0]->h16;
+    for (const bvf_ctx *c : b->ctx) b->n_mat_max = std::max(b->n_mat_max, (int)c->table.size());
+    cudaError_t e = cudaMalloc(&b->d_step, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sm, n * sizeof(StressTmaMaps));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_vm, n * sizeof(VelocityTmaMaps));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = batch_prepare(b->L, b->h16, b->n_mat_max, &b->grid_vel, &b->grid_str);
+    if (e != cudaSuccess) {
+        bvf_batch_destroy(b);
+        return cuda_fail(nullptr, e, "bvf_batch_create");
+    }
+    *out = b;
+    return BVF_OK;
+}
+
+void bvf_batch_destroy(bvf_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaStream_t t : b->side) cudaStreamDestroy(t);
+    for (cudaEvent_t ev : b->side_ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    void *bufs[] = {b->d_sm, b->d_vm, b->d_steps, b->d_step};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+int bvf_batch_run(bvf_batch *b, const int *n_steps, const bvf_capture *caps, int kchunk,
+                  int graph_steps, void *stream)
+{
+    if (!b || !n_steps) return fail(nullptr, BVF_E_ARG, "bvf_batch_run: NULL argument");
+    const int n = (int)b->ctx.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    long long total_steps = 0;
+    int n_max = 0;
+    for (int d = 0; d < n; ++d) {
+        if (n_steps[d] < 0) return fail(nullptr, BVF_E_ARG, "bvf_batch_run: negative step count");
+        if (caps && caps[d].dft_steps < 0)
+            return fail(nullptr, BVF_E_ARG, "bvf_batch_run: negative dft_steps");
+        total_steps += n_steps[d];
+        n_max = std::max(n_max, n_steps[d]);
+    }
+    if (kchunk < 0) return fail(nullptr, BVF_E_ARG, "bvf_batch_run: negative kchunk");
+    // device buffers: tensor maps and per-step tables
+    if (b->steps_cap < (size_t)std::max<long long>(total_steps, 1)) {
+        if (b->d_steps) cudaFree(b->d_steps);
+        b->d_steps = nullptr;
+        b->steps_cap = 0;
+        cudaError_t e = cudaMalloc(&b->d_steps, std::max<long long>(total_steps, 1) * sizeof(StepParam));
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_batch_run: step tables");
+        b->steps_cap = std::max<long long>(total_steps, 1);
+    }
+    std::vector<StressTmaMaps> hsm(n);
+    std::vector<VelocityTmaMaps> hvm(n);
+    b->h_steps.resize(std::max<long long>(total_steps, 1));
+    BatchParams &bp = b->bp;
+    bp = BatchParams{};
+    bp.sm = b->d_sm;
+    bp.vm = b->d_vm;
+    bp.steps = b->d_steps;
+    bp.n_dom = n;
+    int total = 0;
+    long long off = 0;
+    for (int d = 0; d < n; ++d) {
+        bvf_ctx *c = b->ctx[d];
+        bvf_capture cp{-1, 0, 0};
+        if (caps) cp = caps[d];
+        if (cp.dft_steps > 0) {
+            const int rc = ensure_dft(c, s);
+            if (rc != BVF_OK) return rc;
+        }
+        hsm[d] = c->smaps;
+        hvm[d] = c->vmaps;
+        bp.p[d] = make_params(c);
+        const int kc0 = kchunk > 0 ? kchunk : (c->kchunk > 0 ? c->kchunk
+                                                             : default_kchunk_tma(c->g.nx, c->g.ny, c->g.nz));
+        bp.kchunk[d] = std::min(kc0, c->g.nz);
+        bp.tiles_x[d] = (c->g.nx + 31) / 32;
+        bp.tiles_y[d] = (c->g.ny + 7) / 8;
+        const int chunks = (c->g.nz + bp.kchunk[d] - 1) / bp.kchunk[d];
+        bp.block0[d] = total;
+        total += bp.tiles_x[d] * bp.tiles_y[d] * chunks;
+        bp.n_steps[d] = n_steps[d];
+        bp.step_off[d] = (int)off;
+        for (int k = 0; k < n_steps[d]; ++k) b->h_steps[off + k] = step_param(c, cp, c->steps + k);
+        off += n_steps[d];
+    }
+    bp.total = total;
+    CK_FREE(cudaMemcpyAsync(b->d_sm, hsm.data(), n * sizeof(StressTmaMaps), cudaMemcpyHostToDevice,
+                            s), "bvf_batch_run: tensor maps");
+    CK_FREE(cudaMemcpyAsync(b->d_vm, hvm.data(), n * sizeof(VelocityTmaMaps),
+                            cudaMemcpyHostToDevice, s), "bvf_batch_run: tensor maps");
+    if (total_steps)
+        CK_FREE(cudaMemcpyAsync(b->d_steps, b->h_steps.data(), total_steps * sizeof(StepParam),
+                                cudaMemcpyHostToDevice, s), "bvf_batch_run: step tables");
+    CK_FREE(cudaMemsetAsync(b->d_step, 0, sizeof(int), s), "bvf_batch_run: step counter");
+    if (graph_steps <= 0) {
+        for (int k = 0; k < n_max; ++k)
+            CK_FREE(launch_batch_step(bp, b->L, b->h16, b->n_mat_max, b->d_step, b->grid_vel,
+                                      b->grid_str, s), "bvf_batch_run: kernels");
+        b->launches += 3LL * n_max;
+    } else if (n_max > 0) {
+        // one graph of G steps (3 kernels each), replayed; steps past a domain's
+        // end find it finished and skip it
+        const int G = std::min(graph_steps, n_max);
+        if (b->exec) {
+            CK_FREE(cudaStreamSynchronize(s), "bvf_batch_run: previous graph");
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CK_FREE(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal),
+                "bvf_batch_run: capture");
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < G && e == cudaSuccess; ++k)
+            e = launch_batch_step(bp, b->L, b->h16, b->n_mat_max, b->d_step, b->grid_vel,
+                                  b->grid_str, b->cap);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_batch_run: graph");
+        const int reps = (n_max + G - 1) / G;
+        for (int r = 0; r < reps; ++r)
+            CK_FREE(cudaGraphLaunch(b->exec, s), "bvf_batch_run: graph launch");
+        b->launches += 3LL * G * reps;
+    }
+    off = 0;
+    for (int d = 0; d < n; ++d) {
+        bvf_ctx *c = b->ctx[d];
+        for (int k = 0; k < n_steps[d]; ++k) c->dft_count += (b->h_steps[off + k].flags >> 2) & 1;
+        off += n_steps[d];
+        c->steps += n_steps[d];
+    }
+    return BVF_OK;
+}
+
+int bvf_batch_run_streams(bvf_batch *b, const int *n_steps, const bvf_capture *caps,
+                          int n_streams, void *stream)
+{
+    if (!b || !n_steps || n_streams < 1)
+        return fail(nullptr, BVF_E_ARG, "bvf_batch_run_streams: bad argument");
+    const int n = (int)b->ctx.size();
+    for (int d = 0; d < n; ++d)
+        if (n_steps[d] < 0) return fail(nullptr, BVF_E_ARG, "bvf_batch_run_streams: negative step count");
+    cudaStream_t s = (cudaStream_t)stream;
+    while ((int)b->side.size() < n_streams) {
+        cudaStream_t t = nullptr;
+        CK_FREE(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "bvf_batch_run_streams");
+        b->side.push_back(t);
+        cudaEvent_t ev = nullptr;
+        CK_FREE(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "bvf_batch_run_streams");
+        b->side_ev.push_back(ev);
+    }
+    if (!b->fork) CK_FREE(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "bvf_batch_run_streams");
+    // fork: every side stream waits for the caller's stream
+    CK_FREE(cudaEventRecord(b->fork, s), "bvf_batch_run_streams");
+    for (int k = 0; k < n_streams; ++k)
+        CK_FREE(cudaStreamWaitEvent(b->side[k], b->fork, 0), "bvf_batch_run_streams");
+    // domains dealt round-robin; each side stream runs its domains one after another
+    for (int d = 0; d < n; ++d) {
+        const int rc = bvf_run_acoustic(b->ctx[d], n_steps[d], caps ? &caps[d] : nullptr,
+                                        b->side[d % n_streams]);
+        if (rc != BVF_OK) return rc;
+        b->launches += 2LL * n_steps[d];
+    }
+    // join: the caller's stream waits for every side stream
+    for (int k = 0; k < n_streams; ++k) {
+        CK_FREE(cudaEventRecord(b->side_ev[k], b->side[k]), "bvf_batch_run_streams");
+        CK_FREE(cudaStreamWaitEvent(s, b->side_ev[k], 0), "bvf_batch_run_streams");
+    }
+    return BVF_OK;
+}
+
+int bvf_batch_tune(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,
+                   int *best_kchunk, double *best_ms_per_step, void *stream)
+{
+    if (!b || !candidates || n_candidates < 1 || trial_steps < 1 || !best_kchunk)
+        return fail(nullptr, BVF_E_ARG, "bvf_batch_tune: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)b->ctx.size();
+    std::vector<int> steps(n, trial_steps);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK_FREE(cudaEventCreate(&e0), "bvf_batch_tune");
+    CK_FREE(cudaEventCreate(&e1), "bvf_batch_tune");
+    double best = 1e300;
+    int best_kc = candidates[0];
+    int rc = BVF_OK;
+    for (int ci = 0; ci < n_candidates && rc == BVF_OK; ++ci) {
+        for (bvf_ctx *c : b->ctx)
+            if ((rc = bvf_reset(c, stream)) != BVF_OK) break;
+        if (rc != BVF_OK) break;
+        // one untimed pass builds the graph's first replay path, the second is timed
+        rc = bvf_batch_run(b, steps.data(), nullptr, candidates[ci], trial_steps, stream);
+        if (rc != BVF_OK) break;
+        cudaEventRecord(e0, s);
+        rc = bvf_batch_run(b, steps.data(), nullptr, candidates[ci], trial_steps, stream);
+        if (rc != BVF_OK) break;
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(nullptr, e, "bvf_batch_tune");
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            best_kc = candidates[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != BVF_OK) return rc;
+    for (bvf_ctx *c : b->ctx)
+        if ((rc = bvf_reset(c, stream)) != BVF_OK) return rc;
+    *best_kchunk = best_kc;
+    if (best_ms_per_step) *best_ms_per_step = best / trial_steps;
+    return BVF_OK;
+}
+
+int bvf_batch_launches(const bvf_batch *b, long long *out)
+{
+    if (!b || !out) return fail(nullptr, BVF_E_ARG, "bvf_batch_launches: NULL argument");
+    *out = b->launches;
     return BVF_OK;
 }
 

@@ -38,6 +38,15 @@ struct ThermCoef {
 
 constexpr int kNumCpmlSlots = 6;   // CPML memories per slab (see ctx layout)
 
+// Source and capture parameters of one step (the update n -> n+1):
+struct StepParam {
+    double cw, sw;          // DFT weights cos / sin(w t) of the captured step
+    float src_ws, src_wc;   // source envelope times sin / cos(w t)
+    int flags;              // 1: source on, 2: peak capture, 4: DFT capture
+    int pad;
+};
+enum { kStepSource = 1, kStepPeak = 2, kStepDft = 4 };
+
 // The state (v, sigma, memory variables) is stored as float, or as FP16
 // scaled so that stored values stay well inside FP16's range: v / S_v,
 // sigma / S_sigma and r / S_r.  The equations are linear in the state, so the
@@ -66,14 +75,12 @@ struct AcParams {
     int nmax;
     // source plane
     const float2 *src;
-    int k_src, src_on;
-    float src_ws, src_wc, src_scale;   // env sin(wt), env cos(wt), 2 c0 dt / dx
+    int k_src;
+    float src_scale;     // 2 c0 dt / dx (over the stress storage scale)
     // capture
     float *peak;
-    int do_peak;
     double *dftC, *dftS;
-    int do_dft;
-    double cw, sw;
+    StepParam st;        // this step's source and capture parameters
     int *flag;
     int kchunk;          // z-planes per block (0 = default_kchunk)
 };
@@ -92,6 +99,25 @@ struct VelocityTmaMaps {
     CUtensorMap sg[6];
     CUtensorMap idx;
 };
+
+// Batched runs: up to kMaxBatch contexts advanced in lockstep by persistent
+// kernels that take their work from a list of (domain, tile, z-chunk) items.
+// Everything per domain travels in the kernel parameter (read-only constant
+// space, so the compiler reloads instead of spilling); the tensor maps and the
+// per-step tables sit in device memory.
+constexpr int kMaxBatch = 64;
+struct BatchParams {
+    AcParams p[kMaxBatch];
+    const StressTmaMaps *sm;     // [n_dom]
+    const VelocityTmaMaps *vm;   // [n_dom]
+    const StepParam *steps;      // domain d, step s: steps[step_off[d] + s]
+    int step_off[kMaxBatch];
+    int block0[kMaxBatch];       // first work item of each domain (ascending)
+    int tiles_x[kMaxBatch], tiles_y[kMaxBatch], kchunk[kMaxBatch];
+    int n_steps[kMaxBatch];      // steps of this run; later steps skip the domain
+    int n_dom, total;            // domains, work items
+};
+static_assert(sizeof(BatchParams) <= 32000, "batch parameters must fit a kernel parameter");
 
 struct ThParams {
     int nx, ny, nz;
@@ -112,6 +138,14 @@ void set_context_free_error(const char *msg);
 // z-planes per block of the z-marching acoustic kernels for a grid
 int default_kchunk(int nx, int ny, int nz);
 int default_kchunk_tma(int nx, int ny, int nz);
+
+// Persistent batch kernels: one velocity and one stress launch advance every
+// domain of `dom` by one step (the step number is read from *d_step, which a
+// third one-thread kernel then increments).  batch_prepare sets the kernels'
+// shared-memory limits and returns the persistent grid sizes.
+cudaError_t batch_prepare(int L, int h16, int n_mat_max, int *grid_vel, int *grid_str);
+cudaError_t launch_batch_step(const BatchParams &bp, int L, int h16, int n_mat_max, int *d_step,
+                              int grid_vel, int grid_str, cudaStream_t s);
 
 // kernel launchers (bvf_acoustic.cu / bvf_aux.cu); return cudaGetLastError()
 cudaError_t launch_velocity(const AcParams &p, cudaStream_t s);

@@ -18,6 +18,20 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
 }
 
+// return an mbarrier's shared memory to plain use (before re-initialising it
+// for the next tile of a persistent block)
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+// make a tensor map that sits in global memory (written before the launch)
+// visible to the tensor-map proxy before this thread's copies use it
+__device__ __forceinline__ void tensormap_acquire(const void *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 __device__ __forceinline__ void mbar_init_fence()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

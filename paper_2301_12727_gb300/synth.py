@@ -247,3 +247,38 @@ def water_like(case: Case) -> Case:
     c.index = np.zeros_like(case.index)
     c.materials = np.array([water_row(case.f0)])
     return c
+
+
+def sweep_specs(n: int = 64, seed: int = 4321, n_min: int = 96, n_max: int = 200,
+                ppw: float = 6.0):
+    """Domains of a planning sweep: per domain, sizes drawn uniformly from
+    [n_min, n_max] per axis (nx rounded up to a multiple of 16, the TMA row
+    rule), a drive frequency from {250, 500, 700} kHz with dx = lambda_water /
+    ppw, and a bowl tilt uniform in [-15, 15] degrees; seeded."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(n):
+        nx, ny, nz = (int(v) for v in rng.integers(n_min, n_max + 1, size=3))
+        nx = min(((nx + 15) // 16) * 16, ((n_max + 15) // 16) * 16)
+        f0 = float(rng.choice([2.5e5, 5e5, 7e5]))
+        tilt = float(rng.uniform(-15.0, 15.0))
+        out.append(dict(nx=nx, ny=ny, nz=nz, f0=f0, dx=1500.0 / f0 / ppw, tilt_deg=tilt,
+                        seed=int(seed) * 1000 + d))
+    return out
+
+
+def sweep_case(spec: dict, n_steps: int | None = None, dft_cycles: int = 10) -> Case:
+    """The synthetic skull of one sweep domain (see skull_case).  The tilted
+    bowl's apex is lowered so that its rim stays 2 mm below the source plane."""
+    c = skull_case(spec["nx"], spec["ny"], spec["nz"], dx=spec["dx"], f0=spec["f0"],
+                   n_steps=n_steps, seed=spec["seed"], tilt_deg=spec["tilt_deg"],
+                   dft_cycles=dft_cycles)
+    b = dict(c.bowl)
+    a, R = 0.5 * b["aperture"], b["roc"]
+    h = R - math.sqrt(R * R - a * a)
+    t = math.radians(abs(spec["tilt_deg"]))
+    top = h * math.cos(t) + a * math.sin(t)
+    ax, ay, az = b["apex"]
+    b["apex"] = (ax, ay, min(az, c.k_src * c.dx - 2e-3 - top))
+    c.bowl = b
+    return c
