@@ -263,7 +263,9 @@ int bvf_get_amp_phase(bvf_ctx *ctx, double *d_amp, double *d_phase, void *stream
  * NULL = no heating).  d_T (in/out, float) holds the starting temperature and
  * receives the final one; d_Tmax (in/out, float) and d_cem43 (in/out, FP64)
  * accumulate max T and sum dt/60 R^(43-T) (R = 0.5 at T >= 43, else 0.25) after
- * every step.  Errors: BVF_E_ARG (including dt above the explicit limit). */
+ * every step (the dose increments of up to 32 consecutive steps are summed in
+ * FP32 before each addition to the FP64 dose).  Errors: BVF_E_ARG (including
+ * dt above the explicit limit). */
 int bvf_run_thermal(bvf_ctx *ctx, const bvf_thermal *th, const double *d_amp, float *d_T,
                     float *d_Tmax, double *d_cem43, void *stream);
 

@@ -57,7 +57,7 @@ struct bvf_ctx {
     float2 *src = nullptr;
     int *flag = nullptr;
     unsigned *scratch_u = nullptr;
-    float *T2 = nullptr, *Q = nullptr;
+    float *T2 = nullptr, *Q = nullptr, *cemf = nullptr;
     ThermCoef *tlut = nullptr;
     // host mirror
     std::vector<bvf_material> table;
@@ -425,7 +425,7 @@ void bvf_destroy(bvf_ctx *c)
 {
     if (!c) return;
     void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut,
-                    c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->tlut};
+                    c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->cemf, c->tlut};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -788,8 +788,10 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     if (!c->T2) {
         CK(cudaMalloc(&c->T2, c->N * sizeof(float)), "thermal buffers");
         CK(cudaMalloc(&c->Q, c->N * sizeof(float)), "thermal buffers");
+        CK(cudaMalloc(&c->cemf, c->N * sizeof(float)), "thermal buffers");
         CK(cudaMalloc(&c->tlut, BVF_MAX_MATERIALS * sizeof(ThermCoef)), "thermal buffers");
     }
+    CK(cudaMemsetAsync(c->cemf, 0, c->N * sizeof(float), s), "thermal buffers");
     CK(cudaMemcpyAsync(c->tlut, tl.data(), n_mat * sizeof(ThermCoef), cudaMemcpyHostToDevice, s),
        "thermal lut");
     CK(launch_heat_source(c->index, c->tlut, n_mat, d_amp, th->p_scale, c->Q, c->N, s), "heat source");
@@ -807,11 +809,13 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     p.n_mat = n_mat;
     p.Q = c->Q;
     p.Tmax = d_Tmax;
+    p.cemf = c->cemf;
     p.cem = d_cem43;
     const int total = th->n_on + th->n_off;
     float *a = d_T, *b = c->T2;
     for (int n = 0; n < total; ++n) {
         p.dc = (n < th->n_on) ? (float)th->duty : 0.0f;
+        p.flush = ((n + 1) % 32 == 0 || n + 1 == total) ? 1 : 0;
         p.T = a;
         p.Tn = b;
         CK(launch_thermal_step(p, s), "thermal kernel");

@@ -118,6 +118,18 @@ __global__ void k_heat_source(const uint8_t *__restrict__ idx, const ThermCoef *
 }
 
 // Pennes forward-Euler step; border voxels held at T_a; T_max and CEM43 fused.
+// A 32 x 8 block walks a chunk of z.  Every value plane k needs (T and the
+// material of the voxel and its four in-plane neighbours, Q, T_max, the dose
+// partial) is loaded one plane ahead, so those loads are in flight while the
+// previous plane is computed; the z-neighbours come from the planes already
+// held.  Face conductivity: harmonic mean 2 k_c k_n / (k_c + k_n).
+constexpr int kThermChunk = 16;
+
+__device__ __forceinline__ float face_k(float kc, float kn)
+{
+    return 2.0f * kc * kn * __frcp_rn(kc + kn);
+}
+
 __global__ void __launch_bounds__(256) k_thermal(ThParams p)
 {
     extern __shared__ ThermCoef s_th[];
@@ -126,32 +138,69 @@ __global__ void __launch_bounds__(256) k_thermal(ThParams p)
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= p.nx || j >= p.ny) return;
-    const long long SY = p.nx, SZ = (long long)p.nx * p.ny;
-    const long long q = k * SZ + j * SY + i;
-    float Tn;
-    if (i == 0 || j == 0 || k == 0 || i == p.nx - 1 || j == p.ny - 1 || k == p.nz - 1) {
-        Tn = p.T_a;
-    } else {
-        const ThermCoef c = s_th[p.idx[q]];
-        const float T = p.T[q];
-        const long long nb[6] = {q - 1, q + 1, q - SY, q + SY, q - SZ, q + SZ};
-        float lap = 0.0f;
-#pragma unroll
-        for (int f = 0; f < 6; ++f) {
-            const float kn = s_th[p.idx[nb[f]]].k;
-            const float kf = 2.0f * c.k * kn / (c.k + kn);
-            lap += kf * (p.T[nb[f]] - T);
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    if (i >= nx || j >= ny) return;
+    const int k0 = blockIdx.z * kThermChunk, k1 = min(nz, k0 + kThermChunk);
+    const int SZ = nx * ny, col = j * nx + i;
+    const bool xy_border = i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
+    const float *__restrict__ T = p.T;
+    const uint8_t *__restrict__ idx = p.idx;
+    // everything plane k needs, loaded one plane ahead
+    struct Plane {
+        float Tc, Tw, Te, Ts, Tq, Q, Tmax, cemf;
+        int mc, mw, me, ms, mq;
+    };
+    auto load = [&](int k, Plane &P) {
+        const int q = k * SZ + col;
+        P.Tc = __ldg(T + q);
+        P.mc = __ldg(idx + q);
+        P.Q = p.Q[q];
+        P.Tmax = p.Tmax[q];
+        P.cemf = p.cemf[q];
+        if (!xy_border) {
+            P.Tw = __ldg(T + q - 1); P.Te = __ldg(T + q + 1);
+            P.Ts = __ldg(T + q - nx); P.Tq = __ldg(T + q + nx);
+            P.mw = __ldg(idx + q - 1); P.me = __ldg(idx + q + 1);
+            P.ms = __ldg(idx + q - nx); P.mq = __ldg(idx + q + nx);
         }
-        const float rhs = lap * p.inv_dx2 - c.perfw * (T - p.T_a) + p.dc * p.Q[q];
-        Tn = T + p.dt * rhs * c.inv_rhoc;
+    };
+    float Tm = k0 > 0 ? __ldg(T + (k0 - 1) * SZ + col) : 0.0f;
+    int mm = k0 > 0 ? __ldg(idx + (k0 - 1) * SZ + col) : 0;
+    Plane cur, nxt;
+    load(k0, cur);
+    for (int k = k0; k < k1; ++k) {
+        const int q = k * SZ + col;
+        if (k + 1 < nz) load(k + 1, nxt);
+        else { nxt.Tc = 0.0f; nxt.mc = 0; }
+        float Tn;
+        if (xy_border || k == 0 || k == nz - 1) {
+            Tn = p.T_a;
+        } else {
+            const ThermCoef c = s_th[cur.mc];
+            const float kc = c.k, Tc = cur.Tc;
+            float lap = face_k(kc, s_th[cur.mw].k) * (cur.Tw - Tc);
+            lap += face_k(kc, s_th[cur.me].k) * (cur.Te - Tc);
+            lap += face_k(kc, s_th[cur.ms].k) * (cur.Ts - Tc);
+            lap += face_k(kc, s_th[cur.mq].k) * (cur.Tq - Tc);
+            lap += face_k(kc, s_th[mm].k) * (Tm - Tc);
+            lap += face_k(kc, s_th[nxt.mc].k) * (nxt.Tc - Tc);
+            const float rhs = lap * p.inv_dx2 - c.perfw * (Tc - p.T_a) + p.dc * cur.Q;
+            Tn = Tc + p.dt * rhs * c.inv_rhoc;
+        }
+        p.Tn[q] = Tn;
+        p.Tmax[q] = fmaxf(cur.Tmax, Tn);
+        const float l2r = (Tn >= 43.0f) ? -1.0f : -2.0f;
+        const float part = cur.cemf + p.dt60 * exp2f(l2r * (43.0f - Tn));
+        if (p.flush) {
+            p.cem[q] += (double)part;
+            p.cemf[q] = 0.0f;
+        } else {
+            p.cemf[q] = part;
+        }
+        Tm = cur.Tc;
+        mm = cur.mc;
+        cur = nxt;
     }
-    p.Tn[q] = Tn;
-    p.Tmax[q] = fmaxf(p.Tmax[q], Tn);
-    // R^(43-T) = 2^(log2(R) (43 - T)), log2 R = -1 at or above 43 C, else -2
-    const float l2r = (Tn >= 43.0f) ? -1.0f : -2.0f;
-    p.cem[q] += (double)(p.dt60 * exp2f(l2r * (43.0f - Tn)));
 }
 
 // Intensity I = A^2 / (2 rho c) = A^2 * zw[m] with zw[m] = 1 / (2 rho c).
@@ -302,7 +351,7 @@ cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_m
 cudaError_t launch_thermal_step(const ThParams &p, cudaStream_t s)
 {
     dim3 blk(32, 8, 1);
-    dim3 grd((p.nx + 31) / 32, (p.ny + 7) / 8, p.nz);
+    dim3 grd((p.nx + 31) / 32, (p.ny + 7) / 8, (p.nz + kThermChunk - 1) / kThermChunk);
     k_thermal<<<grd, blk, p.n_mat * sizeof(ThermCoef), s>>>(p);
     return cudaGetLastError();
 }

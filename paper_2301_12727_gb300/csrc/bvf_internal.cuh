@@ -119,6 +119,9 @@ struct BatchParams {
 };
 static_assert(sizeof(BatchParams) <= 32000, "batch parameters must fit a kernel parameter");
 
+// One BHTE step.  The CEM43 increments of consecutive steps are summed in an
+// FP32 partial (cemf) and added to the FP64 dose on `flush` steps (every 32
+// steps and the last), which keeps FP64 arithmetic out of most steps.
 struct ThParams {
     int nx, ny, nz;
     float dt, inv_dx2, T_a, dc, dt60;
@@ -129,7 +132,9 @@ struct ThParams {
     float *Tn;
     const float *Q;
     float *Tmax;
+    float *cemf;
     double *cem;
+    int flush;
 };
 
 // message returned by bvf_last_error(NULL) for a failed context-free call
