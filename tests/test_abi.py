@@ -50,6 +50,7 @@ def test_version_and_constants(bvf):
     ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (-5e5, 1.0, 2)),  # negative f0
     ((16, 16, 16, 1e-3, 1e-7, 2, 2.0), (5e5, 1.0, 2)),    # pml_R outside (0,1)
     ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (5e5, 1.0, 2, 7, 0.0)),     # unknown storage
+    ((2048, 2048, 512, 1e-3, 1e-7, 0, 1e-4), (5e5, 1.0, 2)),       # 2^31 voxels (32-bit indexing)
     ((16, 16, 16, 1e-3, 1e-7, 0, 1e-4), (5e5, 1.0, 2, 1, -1e5)),    # negative p_ref
 ])
 def test_create_rejects_bad_arguments_on_host(bvf, grid, phys):

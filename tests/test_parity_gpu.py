@@ -286,6 +286,61 @@ def test_gpu_error_paths(bvf):
     s.close()
 
 
+@pytest.mark.parametrize("shape,n_sls", [((1, 1, 1), 2), ((2, 3, 4), 2), ((16, 1, 5), 2),
+                                         ((3, 2, 1), 1), ((32, 9, 7), 0), ((24, 20, 18), 3)])
+def test_gpu_degenerate_grids_match_oracle(bvf, orc, shape, n_sls):
+    """Grids with single-cell axes (everything a ghost or a boundary), a TMA
+    grid one row high, a lossless medium and three SLS mechanisms (direct
+    kernels): every state array after 5 steps from a random state equals the
+    oracle's to FP32 rounding."""
+    nx, ny, nz = shape
+    dx = 0.5e-3
+    rng = np.random.default_rng(sum(shape) + n_sls)
+    mats = [mat_row(1000.0, 1500.0), mat_row(1850.0, 2800.0, 1500.0, 85.0, 170.0)]
+    index = rng.integers(0, 2, size=(nz, ny, nx)).astype(np.uint8)
+    from paper_2301_12727_gb300 import synth
+    dt, _ = synth.choose_dt(dx, 2800.0, 5e5)
+    s = bvf.Solver(nx, ny, nz, dx, dt, 5e5, n_sls=n_sls, n_pml=0)
+    s.set_materials(index, mats)
+    A = orc.Acoustic(nx, ny, nz, dx, dt, index, mats, 5e5, n_sls=n_sls, n_pml=0)
+    n_state = 9 + 6 * n_sls
+    d = {f: (rng.standard_normal((nz, ny, nx)) * (1.0 if f[0] == "v" else 1e6)).astype(np.float32)
+         for f in an.FIELDS}
+    an.zero_ghost_half_points(d)
+    for i in range(n_state):
+        if i < 9:
+            v = d[an.FIELDS[i]]
+        else:       # memory variables vanish where their stress is a ghost
+            c = (i - 9) % 6
+            v = (rng.standard_normal((nz, ny, nx)) * 1e4).astype(np.float32)
+            if c >= 3:
+                v *= (d[an.FIELDS[3 + c]] != 0)
+        s.set_field(i, v)
+        A.state[i] = v.astype(np.float64)
+    s.run(5)
+    s.synchronize()
+    assert A.run(5) == 0
+    for i in range(n_state):
+        got = s.field(i).cpu().numpy()
+        ref = A.state[i]
+        scale = max(np.abs(ref).max(), 1e-30)
+        assert np.abs(got - ref).max() <= 2e-5 * scale, (i, np.abs(got - ref).max() / scale)
+    s.close()
+
+
+def test_gpu_zero_steps_change_nothing(bvf):
+    n = 16
+    s = bvf.Solver(n, n, n, 0.5e-3, 5e-8, 5e5, n_sls=2, n_pml=0)
+    s.set_materials(np.zeros((n, n, n), np.uint8), [mat_row(1000.0, 1500.0)])
+    v = np.random.default_rng(0).standard_normal((n, n, n)).astype(np.float32)
+    s.set_field("sxx", v)
+    s.run(0)
+    s.synchronize()
+    assert np.array_equal(s.field("sxx").cpu().numpy(), v)
+    assert s.stats().steps == 0
+    s.close()
+
+
 def test_gpu_run_twice_is_bitwise_identical(bvf):
     """No atomics on field data: two runs from the same state agree bitwise."""
     from paper_2301_12727_gb300 import synth
