@@ -314,6 +314,41 @@ int bvf_kernel_timing(bvf_ctx *ctx, int enable);
  * timing was enabled. */
 int bvf_get_kernel_times(bvf_ctx *ctx, bvf_kernel_times *out);
 
+/* ---- one placement end to end --------------------------------------------
+ * The paper's transcranial and thermal steps for one transducer placement
+ * (Sec. 2.3, 2.4): materials of the skull run; Rayleigh-Sommerfeld field of
+ * the bowl on source plane k_src; the FDTD through the skull and the same FDTD
+ * in water only (ramped CW source, peak map from step 1, FP64 amplitude over
+ * the capture window); E_L and T_S on the plane of maximal water intensity
+ * (Eq. 2); the skull field scaled to the requested brain intensity,
+ * p_scale = sqrt(I_SPPA / (E_L I_w,max)); the BHTE with CEM43 from T_a. */
+typedef struct {
+    int n_steps;                 /* FDTD steps of each run */
+    int dft_start, dft_steps;    /* amplitude window, whole periods (see bvf_capture) */
+    double i_sppa;               /* requested brain I_SPPA (W/m^2); <= 0 selects 5e4 */
+    bvf_thermal thermal;         /* regime; its p_scale is ignored (computed) */
+} bvf_plan_params;
+
+typedef struct {
+    double EL, TS;               /* energy-loss factor and its square root */
+    double Iw_max;               /* largest water-run intensity (W/m^2) */
+    double p_scale;              /* factor applied to the skull amplitude */
+    int z_m;                     /* plane of the largest water intensity */
+} bvf_plan_result;
+
+/* skull, water: two contexts on the same grid (the water context's materials
+ * are set here to the one row h_water with an all-zero index).  d_index
+ * (nx*ny*nz bytes) and h_table/n_mat: the skull run's material volume and
+ * table.  Outputs, caller-owned device buffers of nx*ny*nz elements: d_peak
+ * (float, max |p| of the skull run), d_amp (FP64 skull amplitude at the drive
+ * level of the bowl's p0, before scaling), d_T, d_Tmax (float) and d_cem43
+ * (FP64) of the thermal step; *out on the host.  Synchronous (returns after
+ * the stream has finished).  Errors as the calls it makes. */
+int bvf_plan(bvf_ctx *skull, bvf_ctx *water, const uint8_t *d_index, const bvf_material *h_table,
+             int n_mat, const bvf_material *h_water, const bvf_bowl *bowl, int k_src,
+             const bvf_plan_params *pp, float *d_peak, double *d_amp, float *d_T, float *d_Tmax,
+             double *d_cem43, bvf_plan_result *out, void *stream);
+
 /* ---- batched planning sweeps -------------------------------------------
  * Several contexts (different grids, materials, sources, frequencies; the
  * paper repeats its acoustic step for each transducer placement, Sec. 2.3)

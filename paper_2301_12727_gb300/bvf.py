@@ -28,7 +28,7 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_get_pressure", "bvf_get_peak", "bvf_get_amp_phase", "bvf_run_thermal",
            "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times",
            "bvf_transmission_noalloc", "bvf_batch_create", "bvf_batch_destroy", "bvf_batch_run",
-           "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams")
+           "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams", "bvf_plan")
 
 
 class BvfError(RuntimeError):
@@ -73,6 +73,16 @@ class Thermal(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("n_on", ctypes.c_int), ("n_off", ctypes.c_int),
                 ("duty", ctypes.c_double), ("T_a", ctypes.c_double), ("rhob_cb", ctypes.c_double),
                 ("p_scale", ctypes.c_double)]
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int), ("dft_start", ctypes.c_int), ("dft_steps", ctypes.c_int),
+                ("i_sppa", ctypes.c_double), ("thermal", Thermal)]
+
+
+class PlanOut(ctypes.Structure):
+    _fields_ = [("EL", ctypes.c_double), ("TS", ctypes.c_double), ("Iw_max", ctypes.c_double),
+                ("p_scale", ctypes.c_double), ("z_m", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -134,6 +144,9 @@ def lib():
                                      ctypes.POINTER(d), vp]
         L.bvf_batch_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.bvf_batch_run_streams.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
+        L.bvf_plan.argtypes = [vp, vp, vp, ctypes.POINTER(Material), i, ctypes.POINTER(Material),
+                               ctypes.POINTER(Bowl), i, ctypes.POINTER(PlanParams), vp, vp, vp, vp,
+                               vp, ctypes.POINTER(PlanOut), vp]
         _lib = L
     return _lib
 
@@ -411,11 +424,15 @@ class Solver:
         return bvf_get_kernel_times(self.ctx)
 
 
+def make_bowl(bowl: dict, c0=1500.0, ds_over_lambda=0.25) -> Bowl:
+    return Bowl(bowl["aperture"], bowl["roc"], (ctypes.c_double * 3)(*bowl["apex"]),
+                (ctypes.c_double * 3)(*bowl["dir"]), bowl["p0"], c0, ds_over_lambda)
+
+
 def rs_plane(bowl: dict, nx, ny, dx, z_plane, f0, c0=1500.0, ds_over_lambda=0.25, stream=None):
     """Rayleigh-Sommerfeld plane as a (ny, nx, 2) float32 CUDA tensor."""
     import torch
-    b = Bowl(bowl["aperture"], bowl["roc"], (ctypes.c_double * 3)(*bowl["apex"]),
-             (ctypes.c_double * 3)(*bowl["dir"]), bowl["p0"], c0, ds_over_lambda)
+    b = make_bowl(bowl, c0, ds_over_lambda)
     out = torch.empty((ny, nx, 2), dtype=torch.float32, device="cuda")
     bvf_rs_plane(b, nx, ny, dx, z_plane, f0, out, stream)
     return out
@@ -489,3 +506,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- one placement end to end ----------------------------------------------
+def bvf_plan(skull, water, index, table, water_row, bowl, k_src, params, peak, amp, T, Tmax, cem,
+             stream=None):
+    """Returns a PlanOut; outputs land in the given CUDA tensors."""
+    import torch
+    tab = material_array(table)
+    wat = material_array([water_row])
+    b = bowl if isinstance(bowl, Bowl) else make_bowl(bowl)
+    out = PlanOut()
+    _check(lib().bvf_plan(skull.ctx, water.ctx, _ptr(index, torch.uint8), tab, len(tab), wat,
+                          ctypes.byref(b), int(k_src), ctypes.byref(params),
+                          _ptr(peak, torch.float32), _ptr(amp, torch.float64),
+                          _ptr(T, torch.float32), _ptr(Tmax, torch.float32),
+                          _ptr(cem, torch.float64), ctypes.byref(out), _stream(stream)))
+    return out

@@ -956,6 +956,86 @@ int bvf_get_kernel_times(bvf_ctx *c, bvf_kernel_times *out)
     return BVF_OK;
 }
 
+// ---- one placement end to end ---------------------------------------------
+
+int bvf_plan(bvf_ctx *skull, bvf_ctx *water, const uint8_t *d_index, const bvf_material *h_table,
+             int n_mat, const bvf_material *h_water, const bvf_bowl *bowl, int k_src,
+             const bvf_plan_params *pp, float *d_peak, double *d_amp, float *d_T, float *d_Tmax,
+             double *d_cem43, bvf_plan_result *out, void *stream)
+{
+    if (!skull || !water || !d_index || !h_table || !h_water || !bowl || !pp || !d_peak ||
+        !d_amp || !d_T || !d_Tmax || !d_cem43 || !out)
+        return fail(nullptr, BVF_E_ARG, "bvf_plan: NULL argument");
+    if (skull->g.nx != water->g.nx || skull->g.ny != water->g.ny || skull->g.nz != water->g.nz ||
+        skull->g.dx != water->g.dx || skull->g.dt != water->g.dt || skull->ph.f0 != water->ph.f0)
+        return fail(nullptr, BVF_E_ARG, "bvf_plan: the two contexts differ in grid or frequency");
+    if (pp->n_steps < 1 || pp->dft_steps < 1)
+        return fail(nullptr, BVF_E_ARG, "bvf_plan: need n_steps >= 1 and a capture window");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bvf_grid &g = skull->g;
+    const size_t N = skull->N, plane = (size_t)g.nx * g.ny;
+    int rc = bvf_set_materials(skull, d_index, h_table, n_mat);
+    if (rc != BVF_OK) return rc;
+    // temporaries: the water run's zero index and amplitude, the source plane
+    uint8_t *zidx = nullptr;
+    double *amp_w = nullptr;
+    float *src = nullptr;
+    auto release = [&]() {
+        if (zidx) cudaFreeAsync(zidx, s);
+        if (amp_w) cudaFreeAsync(amp_w, s);
+        if (src) cudaFreeAsync(src, s);
+    };
+    cudaError_t e = cudaMallocAsync((void **)&zidx, N, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&amp_w, N * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&src, plane * 2 * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(zidx, 0, N, s);
+    // bvf_set_materials copies the index with a blocking copy: finish the fill first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(nullptr, e, "bvf_plan: temporaries");
+    }
+    auto done = [&](int code) {
+        release();
+        return code;
+    };
+    if ((rc = bvf_set_materials(water, zidx, h_water, 1)) != BVF_OK) return done(rc);
+    if ((rc = bvf_rs_plane(bowl, g.nx, g.ny, g.dx, k_src * g.dx, skull->ph.f0, src, stream)) != BVF_OK)
+        return done(rc);
+    const bvf_capture cap{0, pp->dft_start, pp->dft_steps};
+    bvf_ctx *runs[2] = {skull, water};
+    for (bvf_ctx *c : runs) {
+        if ((rc = bvf_reset(c, stream)) != BVF_OK) return done(rc);
+        if ((rc = bvf_set_source(c, k_src, src, bowl->c0, BVF_ENV_RAMP_CW, 0, stream)) != BVF_OK)
+            return done(rc);
+        if ((rc = bvf_run_acoustic(c, pp->n_steps, &cap, stream)) != BVF_OK) return done(rc);
+    }
+    if ((rc = bvf_get_amp_phase(skull, d_amp, nullptr, stream)) != BVF_OK) return done(rc);
+    if ((rc = bvf_get_amp_phase(water, amp_w, nullptr, stream)) != BVF_OK) return done(rc);
+    if ((rc = bvf_get_peak(skull, d_peak, stream)) != BVF_OK) return done(rc);
+    for (bvf_ctx *c : runs)
+        if ((rc = bvf_synchronize(c, stream)) != BVF_OK) return done(rc);
+    bvf_plan_result r{};
+    rc = bvf_transmission(g.nx, g.ny, g.nz, d_index, h_table, n_mat, d_amp, zidx, h_water, 1,
+                          amp_w, &r.EL, &r.TS, &r.z_m, &r.Iw_max, stream);
+    if (rc != BVF_OK) return done(rc);
+    const double i_sppa = pp->i_sppa > 0.0 ? pp->i_sppa : 5.0e4;
+    r.p_scale = (r.EL > 0.0 && r.Iw_max > 0.0) ? std::sqrt(i_sppa / (r.EL * r.Iw_max)) : 0.0;
+    bvf_thermal th = pp->thermal;
+    th.p_scale = r.p_scale;
+    e = launch_fill(d_T, (float)th.T_a, N, s);
+    if (e == cudaSuccess) e = launch_fill(d_Tmax, (float)th.T_a, N, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cem43, 0, N * sizeof(double), s);
+    if (e != cudaSuccess) return done(cuda_fail(nullptr, e, "bvf_plan: thermal start"));
+    skull->launches += 2;
+    if ((rc = bvf_run_thermal(skull, &th, d_amp, d_T, d_Tmax, d_cem43, stream)) != BVF_OK)
+        return done(rc);
+    release();
+    CK_FREE(cudaStreamSynchronize(s), "bvf_plan");
+    *out = r;
+    return BVF_OK;
+}
+
 // ---- batched runs --------------------------------------------------------
 
 int bvf_batch_create(bvf_ctx *const *ctxs, int n, bvf_batch **out)

@@ -51,12 +51,13 @@ __global__ void k_field_in(const float *__restrict__ in, float inv_scale, T *__r
          q += (size_t)gridDim.x * blockDim.x)
         st::stv(f + q, in[q] * inv_scale);
 }
+// out = in * scale, or out = scale where in is NULL (fill)
 __global__ void k_scale_copy(const float *__restrict__ in, float scale, float *__restrict__ out,
                              size_t n)
 {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
          q += (size_t)gridDim.x * blockDim.x)
-        out[q] = in[q] * scale;
+        out[q] = in ? in[q] * scale : scale;
 }
 
 // p(t) = A cos(w t + phi): C = A N/2 cos phi, S = -A N/2 sin phi
@@ -314,6 +315,12 @@ cudaError_t launch_field_in(const float *in, int h16, float inv_scale, void *f, 
     else
         k_field_in<float><<<blocks_for(n), kThreads, 0, s>>>(in, inv_scale,
                                                             static_cast<float *>(f), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float *out, float value, size_t n, cudaStream_t s)
+{
+    k_scale_copy<<<blocks_for(n), kThreads, 0, s>>>(nullptr, value, out, n);
     return cudaGetLastError();
 }
 

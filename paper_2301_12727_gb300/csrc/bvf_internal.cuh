@@ -165,6 +165,7 @@ cudaError_t launch_field_out(const void *f, int h16, float scale, float *out, si
 cudaError_t launch_field_in(const float *in, int h16, float inv_scale, void *f, size_t n,
                             cudaStream_t s);
 cudaError_t launch_scale_copy(const float *in, float scale, float *out, size_t n, cudaStream_t s);
+cudaError_t launch_fill(float *out, float value, size_t n, cudaStream_t s);
 cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double scale,
                              double *amp, double *ph, cudaStream_t s);
 cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float zp, float k_over_pi,

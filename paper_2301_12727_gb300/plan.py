@@ -48,7 +48,7 @@ class ThermalRegime:
 class PlanResult:
     peak: "object"          # max |p| map of the skull run (float32, device or host)
     amp: "object"           # FP64 pressure amplitude of the skull run (device)
-    amp_water: "object"     # FP64 pressure amplitude of the water run (device)
+    amp_water: "object"     # FP64 amplitude of the water run (not kept by bvf_plan: None)
     Tmax: "object"          # float32 max temperature map
     cem43: "object"         # FP64 thermal dose map (minutes at 43 C)
     EL: float
@@ -96,27 +96,21 @@ class Planner:
     def run(self, index, materials, bowl: dict, regime: ThermalRegime | None = None,
             i_sppa_brain: float = I_SPPA_BRAIN_DEFAULT) -> PlanResult:
         """index: (nz, ny, nx) uint8 CUDA tensor; materials: (n, 9) rows; bowl:
-        aperture, roc, apex, dir, p0 (see bvf_bowl)."""
+        aperture, roc, apex, dir, p0 (see bvf_bowl).  One bvf_plan call; the
+        outputs are fresh tensors of this run."""
+        import torch
         c = self.case
         regime = regime or ThermalRegime()
-        self.skull.set_materials(index, materials)
-        plane = bvf.rs_plane(bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0, c0=c.c0)
-        cap = dict(peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps)
-        for s in (self.skull, self.water):
-            s.reset()
-            s.set_source(plane, c.k_src, c.c0, bvf.BVF_ENV_RAMP_CW)
-            s.run(c.n_steps, **cap)
-        amp, _ = self.skull.amp_phase()
-        amp_w, _ = self.water.amp_phase()
-        self.skull.synchronize()
-        self.water.synchronize()
-        EL, TS, zm, Iw_max = bvf.bvf_transmission(index, materials, amp, self.water_idx,
-                                                  self.water_table, amp_w)
-        # the skull-run field at the plan's drive level gives a brain intensity
-        # of about E_L * Iw_max; scale it to the requested I_SPPA-brain
-        p_scale = math.sqrt(i_sppa_brain / (EL * Iw_max)) if EL > 0 and Iw_max > 0 else 0.0
-        T, Tmax, cem = self.skull.thermal(amp, regime.dt, regime.n_on, regime.n_off, regime.duty,
-                                          T_a=regime.T_a, rhob_cb=regime.rhob_cb,
-                                          p_scale=p_scale)
-        return PlanResult(self.skull.peak(), amp, amp_w, Tmax, cem, EL, TS, zm, Iw_max, p_scale,
+        shape = (c.nz, c.ny, c.nx)
+        peak = torch.empty(shape, dtype=torch.float32, device="cuda")
+        amp = torch.empty(shape, dtype=torch.float64, device="cuda")
+        T = torch.empty(shape, dtype=torch.float32, device="cuda")
+        Tmax = torch.empty(shape, dtype=torch.float32, device="cuda")
+        cem = torch.empty(shape, dtype=torch.float64, device="cuda")
+        th = bvf.Thermal(regime.dt, regime.n_on, regime.n_off, regime.duty, regime.T_a,
+                         regime.rhob_cb, 0.0)
+        pp = bvf.PlanParams(c.n_steps, c.dft_start, c.dft_steps, i_sppa_brain, th)
+        r = bvf.bvf_plan(self.skull, self.water, index, materials, self.water_table[0],
+                         dict(bowl), c.k_src, pp, peak, amp, T, Tmax, cem)
+        return PlanResult(peak, amp, None, Tmax, cem, r.EL, r.TS, r.z_m, r.Iw_max, r.p_scale,
                           2 * c.n_steps * c.voxels)

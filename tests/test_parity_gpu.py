@@ -487,3 +487,41 @@ def test_gpu_f16_fields_round_trip_through_the_storage_scales(bvf):
         assert np.array_equal(got, expect), fid
         assert np.abs(got - v).max() <= 2.0 ** -11 * np.abs(v).max() * 1.001
     s.close()
+
+
+def test_gpu_plan_call_equals_the_step_by_step_sequence(bvf):
+    """bvf_plan (one C-ABI call) gives exactly what the separate calls give:
+    skull and water runs, E_L, T_S, z_m, I_w,max, the scaling and the BHTE."""
+    import torch
+    from paper_2301_12727_gb300 import plan, synth
+    c = synth.skull_case(64, 64, 56, dx=0.5e-3, n_steps=5 * 46, aperture=24e-3, roc=22e-3,
+                         dft_cycles=2, n_pml=6, seed=5)
+    regime = plan.ThermalRegime(t_on=2.0, t_off=1.0, dt=0.1)
+    idx = torch.from_numpy(c.index).cuda()
+    pl = plan.Planner(c)
+    r = pl.run(idx, c.materials, c.bowl, regime=regime)
+    pl.close()
+    # the same steps, one call at a time
+    sk = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+    wa = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+    sk.set_materials(idx, c.materials)
+    widx = torch.zeros_like(idx)
+    wtab = np.array([synth.water_row(c.f0)])
+    wa.set_materials(widx, wtab)
+    plane = bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0)
+    for s in (sk, wa):
+        s.set_source(plane, c.k_src, 1500.0, bvf.BVF_ENV_RAMP_CW)
+        s.run(c.n_steps, peak_from=0, dft_start=c.dft_start, dft_steps=c.dft_steps)
+    amp, _ = sk.amp_phase()
+    amp_w, _ = wa.amp_phase()
+    EL, TS, zm, Iw = bvf.bvf_transmission(idx, c.materials, amp, widx, wtab, amp_w)
+    assert (EL, TS, zm, Iw) == (r.EL, r.TS, r.z_m, r.Iw_max)
+    p_scale = float(np.sqrt(5.0e4 / (EL * Iw)))
+    assert p_scale == r.p_scale
+    T, Tmax, cem = sk.thermal(amp, regime.dt, regime.n_on, regime.n_off, regime.duty,
+                              T_a=regime.T_a, rhob_cb=regime.rhob_cb, p_scale=p_scale)
+    assert torch.equal(sk.peak(), r.peak) and torch.equal(amp, r.amp)
+    assert torch.equal(Tmax, r.Tmax) and torch.equal(cem, r.cem43)
+    assert float(r.Tmax.max()) > 37.0 and 0.0 < r.EL < 1.0
+    sk.close()
+    wa.close()
