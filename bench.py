@@ -142,7 +142,7 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("bvf_acoustic_tma.cu", "bvf_stencil.cuh", "bvf_tma.cuh", "bvf_internal.cuh")
+KERNEL_SOURCES = ("bvf_acoustic_tma.cu", "bvf_stencil.cuh", "bvf_tma.cuh")
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fdtd_stress_velocity_skull160.md")
 
 
