@@ -314,6 +314,17 @@ int bvf_kernel_timing(bvf_ctx *ctx, int enable);
  * timing was enabled. */
 int bvf_get_kernel_times(bvf_ctx *ctx, bvf_kernel_times *out);
 
+/* Rayleigh-Sommerfeld field of a phased array given as elements (the paper's
+ * devices are single bowls; multi-element layouts serve steering and
+ * time-reversal refocusing):  p = (i k p0 / 2 pi) sum_e w_e dA_e exp(-i k r_e) / r_e
+ * on the plane z = z_plane.  h_elem: ne rows of six doubles on the host,
+ * (x, y, z, area, w_re, w_im) in metres, square metres and the complex weight
+ * (1 + 0i for an unsteered element).  c0: coupling-medium speed.  Output as
+ * bvf_rs_plane.  Every element must lie below the plane; ne >= 1.
+ * Context-free; asynchronous on `stream` (the elements are copied first). */
+int bvf_rs_elements(const double *h_elem, int ne, double p0, double c0, int nx, int ny,
+                    double dx, double z_plane, double f0, float *d_out, void *stream);
+
 /* ---- one placement end to end --------------------------------------------
  * The paper's transcranial and thermal steps for one transducer placement
  * (Sec. 2.3, 2.4): materials of the skull run; Rayleigh-Sommerfeld field of

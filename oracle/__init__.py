@@ -11,6 +11,8 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
                    SLS relaxation vs the continuum ODE, attenuation of a point
                    source, normal-incidence reflection, CFL, mirror symmetry)
   rs_plane         pinned (O'Neil on-axis field of a spherical bowl)
+  rs_elements      pinned (single-element magnitude; coherent sum of a steered
+                   array at its target)
   bhte_run         pinned (Gaussian diffusion with perfusion; constant-T CEM43)
   transmission     pinned (constructed maps with known E_L; identical runs)
 """
@@ -182,6 +184,19 @@ def rs_plane(aperture, roc, apex, direction, nx, ny, dx, z_plane, f0, c0, p0,
                             ctypes.c_double(c0), ctypes.c_double(p0), _p(out))
     if rc:
         raise ValueError("orc_rs_plane failed: %d" % rc)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def rs_elements(elements, p0, c0, nx, ny, dx, z_plane, f0):
+    """Complex (ny, nx) field of weighted elements, rows (x, y, z, area, w_re, w_im)."""
+    el = np.ascontiguousarray(np.asarray(elements, dtype=np.float64).reshape(-1, 6))
+    out = np.zeros((ny, nx, 2))
+    rc = lib().orc_rs_elements(_p(el), ctypes.c_long(el.shape[0]), ctypes.c_double(p0),
+                               ctypes.c_double(c0), ctypes.c_int(nx), ctypes.c_int(ny),
+                               ctypes.c_double(dx), ctypes.c_double(z_plane), ctypes.c_double(f0),
+                               _p(out))
+    if rc:
+        raise ValueError("orc_rs_elements failed: %d" % rc)
     return out[..., 0] + 1j * out[..., 1]
 
 

@@ -590,6 +590,33 @@ int orc_rs_plane(double aperture, double roc, const double *apex, const double *
     return ORC_OK;
 }
 
+/* Elements with complex weights (phased arrays): rows (x, y, z, area, w_re,
+ * w_im); p(x) = (i k p0 / 2 pi) sum_e w_e dA_e exp(-i k r_e) / r_e on the plane
+ * z = z_plane, grid point (i,j) at (i dx, j dx). */
+int orc_rs_elements(const double *elem, long ne, double p0, double c0, int nx, int ny,
+                    double dx, double z_plane, double f0, double *out)
+{
+    if (ne < 1) return ORC_E_ARG;
+    double k = 2.0 * M_PI * f0 / c0;
+    double complex pref = I * k * p0 / (2.0 * M_PI);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double x = i * dx, y = j * dx;
+            double complex acc = 0.0;
+            for (long e = 0; e < ne; ++e) {
+                const double *r = elem + 6 * e;
+                double ddx = x - r[0], ddy = y - r[1], ddz = z_plane - r[2];
+                double d = sqrt(ddx * ddx + ddy * ddy + ddz * ddz);
+                acc += (r[4] + I * r[5]) * r[3] * cexp(-I * k * d) / d;
+            }
+            double complex p = pref * acc;
+            out[2 * ((size_t)j * nx + i)] = creal(p);
+            out[2 * ((size_t)j * nx + i) + 1] = cimag(p);
+        }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* BHTE (Pennes) with CEM43 dose (Sec. 2.4).                                  */
 /* ------------------------------------------------------------------------ */

@@ -28,7 +28,8 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_get_pressure", "bvf_get_peak", "bvf_get_amp_phase", "bvf_run_thermal",
            "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times",
            "bvf_transmission_noalloc", "bvf_batch_create", "bvf_batch_destroy", "bvf_batch_run",
-           "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams", "bvf_plan")
+           "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams", "bvf_plan",
+           "bvf_rs_elements")
 
 
 class BvfError(RuntimeError):
@@ -144,6 +145,7 @@ def lib():
                                      ctypes.POINTER(d), vp]
         L.bvf_batch_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.bvf_batch_run_streams.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
+        L.bvf_rs_elements.argtypes = [vp, i, d, d, i, i, d, d, d, vp, vp]
         L.bvf_plan.argtypes = [vp, vp, vp, ctypes.POINTER(Material), i, ctypes.POINTER(Material),
                                ctypes.POINTER(Bowl), i, ctypes.POINTER(PlanParams), vp, vp, vp, vp,
                                vp, ctypes.POINTER(PlanOut), vp]
@@ -435,6 +437,18 @@ def rs_plane(bowl: dict, nx, ny, dx, z_plane, f0, c0=1500.0, ds_over_lambda=0.25
     b = make_bowl(bowl, c0, ds_over_lambda)
     out = torch.empty((ny, nx, 2), dtype=torch.float32, device="cuda")
     bvf_rs_plane(b, nx, ny, dx, z_plane, f0, out, stream)
+    return out
+
+
+def bvf_rs_elements(elements, p0, c0, nx, ny, dx, z_plane, f0, stream=None):
+    """Field of weighted elements (rows x, y, z, area, w_re, w_im) as a
+    (ny, nx, 2) float32 CUDA tensor."""
+    import torch
+    el = np.ascontiguousarray(np.asarray(elements, dtype=np.float64).reshape(-1, 6))
+    out = torch.empty((ny, nx, 2), dtype=torch.float32, device="cuda")
+    _check(lib().bvf_rs_elements(el.ctypes.data_as(ctypes.c_void_p), el.shape[0], float(p0),
+                                 float(c0), int(nx), int(ny), float(dx), float(z_plane), float(f0),
+                                 _ptr(out, torch.float32), _stream(stream)))
     return out
 
 

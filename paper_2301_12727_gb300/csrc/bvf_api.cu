@@ -882,6 +882,43 @@ int bvf_rs_plane(const bvf_bowl *bw, int nx, int ny, double dx, double z_plane, 
     return BVF_OK;
 }
 
+int bvf_rs_elements(const double *h_elem, int ne, double p0, double c0, int nx, int ny,
+                    double dx, double z_plane, double f0, float *d_out, void *stream)
+{
+    if (!h_elem || ne < 1 || !d_out || nx < 1 || ny < 1 || !(dx > 0.0) || !(f0 > 0.0) ||
+        !(c0 > 0.0))
+        return fail(nullptr, BVF_E_ARG, "bvf_rs_elements: bad argument");
+    std::vector<float4> el(ne);
+    std::vector<float2> wt(ne);
+    for (int e = 0; e < ne; ++e) {
+        const double *r = h_elem + 6 * (size_t)e;
+        if (!(r[2] < z_plane) || !(r[3] >= 0.0))
+            return fail(nullptr, BVF_E_ARG,
+                        "bvf_rs_elements: an element lies on or above the plane, or has negative area");
+        el[e] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+        wt[e] = make_float2((float)r[4], (float)r[5]);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    char *buf = nullptr;
+    const size_t bytes = ne * (sizeof(float4) + sizeof(float2));
+    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_rs_elements: element buffer");
+    float4 *d_el = reinterpret_cast<float4 *>(buf);
+    float2 *d_wt = reinterpret_cast<float2 *>(buf + ne * sizeof(float4));
+    e = cudaMemcpyAsync(d_el, el.data(), ne * sizeof(float4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_wt, wt.data(), ne * sizeof(float2), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        const double k = 2.0 * kPi * f0 / c0;
+        e = launch_rs_weighted(d_el, d_wt, ne, nx, ny, (float)dx, (float)z_plane, (float)(k / kPi),
+                               k * p0 / (2.0 * kPi), reinterpret_cast<float2 *>(d_out), s);
+    }
+    cudaError_t e2 = cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_rs_elements");
+    if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "bvf_rs_elements: free");
+    return BVF_OK;
+}
+
 int bvf_transmission(int nx, int ny, int nz, const uint8_t *d_idx_a, const bvf_material *h_mat_a,
                      int n_a, const double *d_amp_a, const uint8_t *d_idx_w,
                      const bvf_material *h_mat_w, int n_w, const double *d_amp_w, double *h_EL,

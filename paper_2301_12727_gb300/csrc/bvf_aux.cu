@@ -75,6 +75,48 @@ __global__ void k_amp_phase(const double *__restrict__ C, const double *__restri
 // One thread per plane point, elements staged through shared memory.
 // p = pref * sum_e dA_e (sin(k r) + i cos(k r)) / r   with pref = k p0 / (2 pi):
 // the i k p0 / (2 pi) prefactor times exp(-i k r) = cos kr - i sin kr.
+// Elements with complex weights w_e (phased arrays): the element's term is
+// multiplied by w_e = wr + i wi.
+__global__ void __launch_bounds__(kThreads) k_rs_weighted(const float4 *__restrict__ el,
+                                                          const float2 *__restrict__ wt, int ne,
+                                                          int nx, int ny, float dx, float zp,
+                                                          float k_over_pi, double pref,
+                                                          float2 *__restrict__ out)
+{
+    __shared__ float4 s_el[kThreads];
+    __shared__ float2 s_w[kThreads];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = q < nx * ny;
+    const float x = live ? (q % nx) * dx : 0.0f;
+    const float y = live ? (q / nx) * dx : 0.0f;
+    double re = 0.0, im = 0.0;
+    for (int base = 0; base < ne; base += kThreads) {
+        if (base + threadIdx.x < ne) {
+            s_el[threadIdx.x] = el[base + threadIdx.x];
+            s_w[threadIdx.x] = wt[base + threadIdx.x];
+        }
+        __syncthreads();
+        const int cnt = min(kThreads, ne - base);
+        float pre = 0.0f, pim = 0.0f;
+        for (int e = 0; e < cnt; ++e) {
+            const float4 E = s_el[e];
+            const float2 W = s_w[e];
+            const float ddx = x - E.x, ddy = y - E.y, ddz = zp - E.z;
+            const float r = sqrtf(fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz)));
+            float sn, cs;
+            sincospif(k_over_pi * r, &sn, &cs);
+            const float w = E.w / r;
+            // (wr + i wi)(sin kr + i cos kr)
+            pre = fmaf(w, fmaf(W.x, sn, -W.y * cs), pre);
+            pim = fmaf(w, fmaf(W.x, cs, W.y * sn), pim);
+        }
+        re += pre;
+        im += pim;
+        __syncthreads();
+    }
+    if (live) out[q] = make_float2((float)(pref * re), (float)(pref * im));
+}
+
 __global__ void __launch_bounds__(kThreads) k_rs(const float4 *__restrict__ el, int ne, int nx,
                                                  int ny, float dx, float zp, float k_over_pi,
                                                  double pref, float2 *__restrict__ out)
@@ -343,6 +385,16 @@ cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float 
     const int n = nx * ny;
     k_rs<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(el, ne, nx, ny, dx, zp, k_over_pi,
                                                            pref, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rs_weighted(const float4 *el, const float2 *wt, int ne, int nx, int ny,
+                               float dx, float zp, float k_over_pi, double pref, float2 *out,
+                               cudaStream_t s)
+{
+    const int n = nx * ny;
+    k_rs_weighted<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(el, wt, ne, nx, ny, dx, zp,
+                                                                    k_over_pi, pref, out);
     return cudaGetLastError();
 }
 

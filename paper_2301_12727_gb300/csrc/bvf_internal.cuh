@@ -170,6 +170,9 @@ cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int cou
                              double *amp, double *ph, cudaStream_t s);
 cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float zp, float k_over_pi,
                       double pref, float2 *out, cudaStream_t s);
+cudaError_t launch_rs_weighted(const float4 *el, const float2 *wt, int ne, int nx, int ny,
+                               float dx, float zp, float k_over_pi, double pref, float2 *out,
+                               cudaStream_t s);
 cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_mat,
                                const double *amp, double p_scale, float *Q, size_t n,
                                cudaStream_t s);

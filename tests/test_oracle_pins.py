@@ -549,6 +549,34 @@ def test_bhte_insulating_sheet_blocks_conduction(orc):
     assert np.abs(T[16:] - 37.0).max() < 1e-6      # and nothing crossed it
 
 
+def test_rs_elements_single_element_and_steered_array(orc):
+    """Weighted-element Rayleigh sum: one element of area dA gives
+    |p| = k p0 dA / (2 pi r) everywhere; an array whose weights are
+    exp(+i k r_t,e) (steered at target t) adds coherently there:
+    p(t) = i k p0 / (2 pi) sum_e dA_e / r_t,e."""
+    f0, c0, p0 = 5e5, 1500.0, 1e4
+    k = 2 * np.pi * f0 / c0
+    dx, nx, ny, zp = 0.5e-3, 9, 7, 0.03
+    one = np.array([[1e-3, 2e-3, 0.0, 4e-6, 1.0, 0.0]])
+    p = orc.rs_elements(one, p0, c0, nx, ny, dx, zp, f0)
+    X, Y = np.meshgrid(np.arange(nx) * dx, np.arange(ny) * dx)
+    r = np.sqrt((X - 1e-3) ** 2 + (Y - 2e-3) ** 2 + zp ** 2)
+    assert np.abs(np.abs(p) - k * p0 * 4e-6 / (2 * np.pi * r)).max() < 1e-12 * np.abs(p).max()
+    rng = np.random.default_rng(4)
+    ne = 64
+    pos = np.stack([rng.uniform(-0.02, 0.02, ne), rng.uniform(-0.02, 0.02, ne),
+                    rng.uniform(-0.01, 0.0, ne)], axis=1)
+    area = rng.uniform(1e-6, 4e-6, ne)
+    tgt = np.array([3 * dx, 2 * dx, zp])                   # grid point (3, 2) of the plane
+    rt = np.linalg.norm(pos - tgt, axis=1)
+    w = np.exp(1j * k * rt)
+    el = np.column_stack([pos, area, w.real, w.imag])
+    p = orc.rs_elements(el, p0, c0, nx, ny, dx, zp, f0)
+    expect = 1j * k * p0 / (2 * np.pi) * np.sum(area / rt)
+    assert abs(p[2, 3] - expect) < 1e-12 * abs(expect)
+    assert np.abs(p).max() == pytest.approx(abs(p[2, 3]), rel=1e-12)   # the target is the maximum
+
+
 def _table1_rows(f):
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "table1_materials.txt")
