@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
             for (int l = 0; l < L; ++l)
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc)
-                    rv[l][cc] = st::tof(mem[(size_t)(l * 6 + cc) * p.fstride + q]);
+                    rv[l][cc] = st::tof(mem[mem_index(l, cc, q, p.fstride, L)]);
             const float pk = (p.st.flags & kStepPeak) ? peak[q] : 0.0f;
             double dC = 0.0, dS = 0.0;
             if (p.st.flags & kStepDft) { dC = p.dftC[q]; dS = p.dftS[q]; }
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) {
                     const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
-                    if (w) st::stv(mem + (size_t)(l * 6 + cc) * p.fstride + q, rv[l][cc]);
+                    if (w) st::stv(mem + mem_index(l, cc, q, p.fstride, L), rv[l][cc]);
                 }
             if (p.st.flags & kStepPeak) peak[q] = fmaxf(pk, fabsf(pr));
             if (p.st.flags & kStepDft) {

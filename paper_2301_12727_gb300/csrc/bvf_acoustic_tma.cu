@@ -446,10 +446,15 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
 #pragma unroll
             for (int cc = 0; cc < 6; ++cc) sv[cc] = tof(gs[cc][q]);
 #pragma unroll
-            for (int l = 0; l < L; ++l)
-#pragma unroll
-                for (int cc = 0; cc < 6; ++cc)
-                    rv[l][cc] = tof(mem[(size_t)(l * 6 + cc) * p.fstride + q]);
+            for (int cc = 0; cc < 6; ++cc) {
+                if constexpr (L == 2) {   // the two mechanisms of a component: one paired load
+                    const float2 r2 = st::ld2(mem + mem_index(0, cc, q, p.fstride, 2));
+                    rv[0][cc] = r2.x;
+                    rv[1][cc] = r2.y;
+                } else if constexpr (L == 1) {
+                    rv[0][cc] = tof(mem[mem_index(0, cc, q, p.fstride, 1)]);
+                }
+            }
             if (st.flags & kStepPeak) pk = p.peak[q];
             if (st.flags & kStepDft) {
                 dC = p.dftC[q];
@@ -548,12 +553,14 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
             if (dxz) st::stv(gs[4] + q, sv[4]);
             if (dyz) st::stv(gs[5] + q, sv[5]);
 #pragma unroll
-            for (int l = 0; l < L; ++l)
-#pragma unroll
-                for (int cc = 0; cc < 6; ++cc) {
-                    const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
-                    if (w) st::stv(mem + (size_t)(l * 6 + cc) * p.fstride + q, rv[l][cc]);
-                }
+            for (int cc = 0; cc < 6; ++cc) {
+                const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
+                if (!w) continue;
+                if constexpr (L == 2)
+                    st::st2(mem + mem_index(0, cc, q, p.fstride, 2), rv[0][cc], rv[1][cc]);
+                else if constexpr (L == 1)
+                    st::stv(mem + mem_index(0, cc, q, p.fstride, 1), rv[0][cc]);
+            }
             if (st.flags & kStepPeak) p.peak[q] = fmaxf(pk, fabsf(pr));
             if (st.flags & kStepDft) {
                 p.dftC[q] = fma((double)pr, st.cw, dC);

@@ -203,9 +203,19 @@ double envelope(int env, int n_cycles, double f0, double t)
     return 0.0;
 }
 
+// First element of state array `which`; its elements are field_stride apart.
+// v and sigma: plain arrays; memory variable (l, c): element mem_index(l, c, q).
 void *field_ptr(bvf_ctx *c, int which)
 {
-    return static_cast<char *>(c->fields) + (size_t)which * c->fstride * c->es;
+    if (which < BVF_FIELD_MEM0)
+        return static_cast<char *>(c->fields) + (size_t)which * c->fstride * c->es;
+    const int l = (which - BVF_FIELD_MEM0) / 6, cc = (which - BVF_FIELD_MEM0) % 6;
+    return static_cast<char *>(c->fields) +
+           ((size_t)BVF_FIELD_MEM0 * c->fstride + mem_index(l, cc, 0, c->fstride, c->L)) * c->es;
+}
+size_t field_stride(const bvf_ctx *c, int which)
+{
+    return which < BVF_FIELD_MEM0 ? 1 : (size_t)c->L;
 }
 
 // storage scale of state array `which` (physical value = stored value * scale)
@@ -700,12 +710,13 @@ int bvf_get_field(bvf_ctx *c, int which, float *d_out, void *stream)
 {
     if (!c || !d_out || which < 0 || which >= 9 + 6 * c->L)
         return fail(c, BVF_E_ARG, "bvf_get_field: bad context, pointer or field id");
-    if (!c->h16)
+    if (!c->h16 && field_stride(c, which) == 1)
         CK(cudaMemcpyAsync(d_out, field_ptr(c, which), c->N * sizeof(float),
                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "get field");
     else {
-        CK(launch_field_out(field_ptr(c, which), 1, (float)field_scale(c, which), d_out, c->N,
-                            (cudaStream_t)stream), "get field");
+        CK(launch_field_out(field_ptr(c, which), c->h16, field_stride(c, which),
+                            (float)field_scale(c, which), d_out, c->N, (cudaStream_t)stream),
+           "get field");
         c->launches++;
     }
     return BVF_OK;
@@ -715,12 +726,13 @@ int bvf_set_field(bvf_ctx *c, int which, const float *d_in, void *stream)
 {
     if (!c || !d_in || which < 0 || which >= 9 + 6 * c->L)
         return fail(c, BVF_E_ARG, "bvf_set_field: bad context, pointer or field id");
-    if (!c->h16)
+    if (!c->h16 && field_stride(c, which) == 1)
         CK(cudaMemcpyAsync(field_ptr(c, which), d_in, c->N * sizeof(float),
                            cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "set field");
     else {
-        CK(launch_field_in(d_in, 1, (float)(1.0 / field_scale(c, which)), field_ptr(c, which),
-                           c->N, (cudaStream_t)stream), "set field");
+        CK(launch_field_in(d_in, c->h16, field_stride(c, which),
+                           (float)(1.0 / field_scale(c, which)), field_ptr(c, which), c->N,
+                           (cudaStream_t)stream), "set field");
         c->launches++;
     }
     return BVF_OK;

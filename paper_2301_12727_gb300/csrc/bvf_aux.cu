@@ -36,20 +36,23 @@ __global__ void k_pressure(const T *__restrict__ a, const T *__restrict__ b,
         out[q] = -(st::tof(a[q]) + st::tof(b[q]) + st::tof(c[q])) / 3.0f * scale;
 }
 
-// state array <-> FP32 values in physical units (scale = the storage scale)
+// state array (element q at f[q * stride]) <-> FP32 values in physical units
+// (scale = the storage scale)
 template <typename T>
-__global__ void k_field_out(const T *__restrict__ f, float scale, float *__restrict__ out, size_t n)
+__global__ void k_field_out(const T *__restrict__ f, size_t stride, float scale,
+                            float *__restrict__ out, size_t n)
 {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
          q += (size_t)gridDim.x * blockDim.x)
-        out[q] = st::tof(f[q]) * scale;
+        out[q] = st::tof(f[q * stride]) * scale;
 }
 template <typename T>
-__global__ void k_field_in(const float *__restrict__ in, float inv_scale, T *__restrict__ f, size_t n)
+__global__ void k_field_in(const float *__restrict__ in, size_t stride, float inv_scale,
+                           T *__restrict__ f, size_t n)
 {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
          q += (size_t)gridDim.x * blockDim.x)
-        st::stv(f + q, in[q] * inv_scale);
+        st::stv(f + q * stride, in[q] * inv_scale);
 }
 // out = in * scale, or out = scale where in is NULL (fill)
 __global__ void k_scale_copy(const float *__restrict__ in, float scale, float *__restrict__ out,
@@ -336,26 +339,26 @@ cudaError_t launch_pressure(const void *sxx, const void *syy, const void *szz, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_out(const void *f, int h16, float scale, float *out, size_t n,
-                             cudaStream_t s)
+cudaError_t launch_field_out(const void *f, int h16, size_t stride, float scale, float *out,
+                             size_t n, cudaStream_t s)
 {
     if (h16)
         k_field_out<__half><<<blocks_for(n), kThreads, 0, s>>>(static_cast<const __half *>(f),
-                                                              scale, out, n);
+                                                              stride, scale, out, n);
     else
-        k_field_out<float><<<blocks_for(n), kThreads, 0, s>>>(static_cast<const float *>(f), scale,
-                                                             out, n);
+        k_field_out<float><<<blocks_for(n), kThreads, 0, s>>>(static_cast<const float *>(f),
+                                                             stride, scale, out, n);
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_in(const float *in, int h16, float inv_scale, void *f, size_t n,
-                            cudaStream_t s)
+cudaError_t launch_field_in(const float *in, int h16, size_t stride, float inv_scale, void *f,
+                            size_t n, cudaStream_t s)
 {
     if (h16)
-        k_field_in<__half><<<blocks_for(n), kThreads, 0, s>>>(in, inv_scale,
+        k_field_in<__half><<<blocks_for(n), kThreads, 0, s>>>(in, stride, inv_scale,
                                                              static_cast<__half *>(f), n);
     else
-        k_field_in<float><<<blocks_for(n), kThreads, 0, s>>>(in, inv_scale,
+        k_field_in<float><<<blocks_for(n), kThreads, 0, s>>>(in, stride, inv_scale,
                                                             static_cast<float *>(f), n);
     return cudaGetLastError();
 }

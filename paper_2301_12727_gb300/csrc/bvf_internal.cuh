@@ -38,6 +38,14 @@ struct ThermCoef {
 
 constexpr int kNumCpmlSlots = 6;   // CPML memories per slab (see ctx layout)
 
+// Memory variable of mechanism l for stress component c at voxel q: the L
+// mechanisms of one component and voxel are adjacent (one paired access for
+// L = 2), components are fstride * L elements apart.
+__host__ __device__ __forceinline__ size_t mem_index(int l, int c, size_t q, size_t fstride, int L)
+{
+    return ((size_t)c * fstride + q) * (size_t)L + (size_t)l;
+}
+
 // Source and capture parameters of one step (the update n -> n+1):
 struct StepParam {
     double cw, sw;          // DFT weights cos / sin(w t) of the captured step
@@ -68,7 +76,7 @@ struct AcParams {
     const uint8_t *idx;
     const MatCoef *lut;
     void *vx, *vy, *vz, *sxx, *syy, *szz, *sxy, *sxz, *syz;   // float or __half
-    void *mem;           // memory variables, [l][c] arrays of `fstride` elements
+    void *mem;           // memory variables, element mem_index(l, c, q)
     size_t fstride;
     float *psx, *psy, *psz;   // CPML slabs: x [6][nz][ny][W], y [6][nz][W][nx], z [6][W][ny][nx]
     const float2 *pml;   // (a, b) at [axis][h][s], h = 0 integer / 1 half point
@@ -160,10 +168,10 @@ cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaSt
 cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cudaStream_t s);
 cudaError_t launch_pressure(const void *sxx, const void *syy, const void *szz, int h16,
                             float scale, float *out, size_t n, cudaStream_t s);
-cudaError_t launch_field_out(const void *f, int h16, float scale, float *out, size_t n,
-                             cudaStream_t s);
-cudaError_t launch_field_in(const float *in, int h16, float inv_scale, void *f, size_t n,
-                            cudaStream_t s);
+cudaError_t launch_field_out(const void *f, int h16, size_t stride, float scale, float *out,
+                             size_t n, cudaStream_t s);
+cudaError_t launch_field_in(const float *in, int h16, size_t stride, float inv_scale, void *f,
+                            size_t n, cudaStream_t s);
 cudaError_t launch_scale_copy(const float *in, float scale, float *out, size_t n, cudaStream_t s);
 cudaError_t launch_fill(float *out, float value, size_t n, cudaStream_t s);
 cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double scale,
