@@ -106,10 +106,8 @@ template <typename T>
 __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
 {
     extern __shared__ __align__(16) float sm_v[];
-    float *s_rho = sm_v;                               // n_mat (rounded to 4)
-    float *tiles = sm_v + ((p.n_mat + 3) & ~3);        // [2 buffers][5 arrays][TILE]
+    float *tiles = sm_v;                               // [2 buffers][5 arrays][TILE]
     const Geo g = make_geo(p.nx, p.ny, p.nz);
-    for (int m = g.tid; m < p.n_mat; m += NTH) s_rho[m] = p.lut[m].rho;
 
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int k0 = blockIdx.z * kchunk, k1 = min(nz, k0 + kchunk);
@@ -171,7 +169,6 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
             const int m0 = __ldg(idx + q), mx = __ldg(idx + q + (ix1 ? 1 : 0));
             const int my = __ldg(idx + q + (jy1 ? nx : 0)), mz = __ldg(idx + q + (kz1 ? g.SZ : 0));
             float ux = st::tof(vx[q]), uy = st::tof(vy[q]), uz = st::tof(vz[q]);
-            const float rho0 = s_rho[m0];
             if (ix1) {
                 float d1 = dfw(txx[c - 1], txx[c], txx[c + 1], txx[c + 2], ix);
                 float d2 = dbw(txy[c - 2 * SW], txy[c - SW], txy[c], txy[c + SW], ix);
@@ -179,7 +176,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + qx, pmlx[p.nmax + g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + qz, pmlz[k], d3);
-                ux += st::vel_increment(dt, rho0, s_rho[mx], d1, d2, d3);
+                ux += st::vel_increment(dt, p.buoy, p.n_mat, m0, mx, d1, d2, d3);
                 st::stv(vx + q, ux);
             }
             if (jy1) {
@@ -189,7 +186,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + qx, pmlx[g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + qy, pmly[p.nmax + g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + qz, pmlz[k], d3);
-                uy += st::vel_increment(dt, rho0, s_rho[my], d1, d2, d3);
+                uy += st::vel_increment(dt, p.buoy, p.n_mat, m0, my, d1, d2, d3);
                 st::stv(vy + q, uy);
             }
             if (kz1) {
@@ -199,7 +196,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + qx, pmlx[g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + qz, pmlz[p.nmax + k], d3);
-                uz += st::vel_increment(dt, rho0, s_rho[mz], d1, d2, d3);
+                uz += st::vel_increment(dt, p.buoy, p.n_mat, m0, mz, d1, d2, d3);
                 st::stv(vz + q, uz);
             }
         }
@@ -375,7 +372,7 @@ static dim3 grid_of(const AcParams &p, int kchunk)
 cudaError_t launch_velocity(const AcParams &p, cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk(p.nx, p.ny, p.nz);
-    const size_t sm = ((p.n_mat + 3) & ~3) * sizeof(float) + 2 * 5 * TILE * sizeof(float);
+    const size_t sm = 2 * 5 * TILE * sizeof(float);
     if (p.h16)
         k_velocity<__half><<<grid_of(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc);
     else

@@ -77,8 +77,8 @@ struct VelLayout {
     static constexpr int off_c = off_b + RB * SB * ES;        // szz: k-1 .. k+3 (+1 spare)
     static constexpr int off_i = off_c + RC * TZZ * ES;       // index: k .. k+2
     static constexpr int off_bar = off_i + RI * IT_SLOT;
-    static constexpr int off_lut = off_bar + 16;
-    static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(float); }
+    static constexpr int off_end = off_bar + 16;
+    static size_t bytes(int) { return off_end; }
     static_assert(R % RA == 0 && R % RB == 0 && R % RC == 0 && R % RI == 0,
                   "ring depths must divide the unroll period");
     static_assert(off_b % 128 == 0 && off_c % 128 == 0 && off_i % 128 == 0 &&
@@ -102,7 +102,6 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
     constexpr int TXX = Lay::TXX, TYY = Lay::TYY, TZZ = Lay::TZZ;
     const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
-    float *s_rho = reinterpret_cast<float *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = bx * TX, y0 = by * TY;
@@ -110,7 +109,6 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;
     const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
-    for (int m = tid; m < p.n_mat; m += NTH) s_rho[m] = p.lut[m].rho;
     if (tid == 0) {
         tma::mbar_init(&bars[0], 1);
         tma::mbar_init(&bars[1], 1);
@@ -286,10 +284,10 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
                     if (kz1) p.psz[2 * Szs + oz] = t;
                     az3 += t;
                 }
-                const float rho0 = s_rho[I0[0]];
-                const float nvx = ux + st::vel_increment(dt, rho0, s_rho[I0[1]], ax1, ax2, ax3);
-                const float nvy = uy + st::vel_increment(dt, rho0, s_rho[I0[IW]], ay1, ay2, ay3);
-                const float nvz = uz + st::vel_increment(dt, rho0, s_rho[I1[0]], az1, az2, az3);
+                const int m0 = I0[0], nm = p.n_mat;
+                const float nvx = ux + st::vel_increment(dt, p.buoy, nm, m0, I0[1], ax1, ax2, ax3);
+                const float nvy = uy + st::vel_increment(dt, p.buoy, nm, m0, I0[IW], ay1, ay2, ay3);
+                const float nvz = uz + st::vel_increment(dt, p.buoy, nm, m0, I1[0], az1, az2, az3);
                 if (ix1) st::stv(vxg + q, nvx);
                 if (jy1) st::stv(vyg + q, nvy);
                 if (kz1) st::stv(vzg + q, nvz);

@@ -53,6 +53,7 @@ struct bvf_ctx {
     int dft_count = 0;
     uint8_t *index = nullptr;
     MatCoef *lut = nullptr;
+    float *buoy = nullptr;            // material-pair buoyancy table
     float2 *pml = nullptr;
     float2 *src = nullptr;
     int *flag = nullptr;
@@ -346,6 +347,7 @@ AcParams make_params(bvf_ctx *c)
     }
     p.idx = c->index;
     p.lut = c->lut;
+    p.buoy = c->buoy;
     p.vx = field_ptr(c, BVF_FIELD_VX);
     p.vy = field_ptr(c, BVF_FIELD_VY);
     p.vz = field_ptr(c, BVF_FIELD_VZ);
@@ -434,7 +436,7 @@ const char *bvf_last_error(const bvf_ctx *ctx)
 void bvf_destroy(bvf_ctx *c)
 {
     if (!c) return;
-    void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut,
+    void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut, c->buoy,
                     c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->cemf, c->tlut};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -499,6 +501,8 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
     if ((e = cudaMalloc(&c->peak, c->N * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&c->index, c->N)) != cudaSuccess ||
         (e = cudaMalloc(&c->lut, BVF_MAX_MATERIALS * sizeof(MatCoef))) != cudaSuccess ||
+        (e = cudaMalloc(&c->buoy, (size_t)BVF_MAX_MATERIALS * BVF_MAX_MATERIALS * sizeof(float))) !=
+            cudaSuccess ||
         (e = cudaMalloc(&c->pml, 6 * (size_t)c->nmax * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&c->src, (size_t)g.nx * g.ny * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&c->flag, sizeof(int))) != cudaSuccess ||
@@ -586,6 +590,13 @@ int bvf_set_materials(bvf_ctx *c, const uint8_t *d_index, const bvf_material *h_
             }
     CK(cudaMemcpy(c->index, d_index, c->N, cudaMemcpyDeviceToDevice), "copy index");
     CK(cudaMemcpy(c->lut, lut.data(), n_mat * sizeof(MatCoef), cudaMemcpyHostToDevice), "copy lut");
+    // buoyancy at a velocity point between cells of materials a and b: 2 / (rho_a + rho_b)
+    std::vector<float> buoy((size_t)n_mat * n_mat);
+    for (int a = 0; a < n_mat; ++a)
+        for (int b = 0; b < n_mat; ++b)
+            buoy[(size_t)a * n_mat + b] = (float)(2.0 / (h_table[a].rho + h_table[b].rho));
+    CK(cudaMemcpy(c->buoy, buoy.data(), buoy.size() * sizeof(float), cudaMemcpyHostToDevice),
+       "copy buoyancy");
     CK(cudaMemcpy(c->pml, pml.data(), pml.size() * sizeof(float2), cudaMemcpyHostToDevice), "copy pml");
     CK(cudaMemset(c->scratch_u, 0, sizeof(unsigned)), "memset");
     CK(launch_index_max(c->index, c->N, c->scratch_u, 0), "index scan");

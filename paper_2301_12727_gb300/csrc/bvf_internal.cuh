@@ -75,6 +75,7 @@ struct AcParams {
     float ca[BVF_MAX_SLS], cb[BVF_MAX_SLS];
     const uint8_t *idx;
     const MatCoef *lut;
+    const float *buoy;   // 2 / (rho_a + rho_b) of every material pair, [a * n_mat + b]
     void *vx, *vy, *vz, *sxx, *syy, *szz, *sxy, *sxz, *syz;   // float or __half
     void *mem;           // memory variables, element mem_index(l, c, q)
     size_t fstride;

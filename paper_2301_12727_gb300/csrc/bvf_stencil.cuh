@@ -97,11 +97,12 @@ __device__ __forceinline__ float sls_update(const AcParams &p, float (&rv)[L > 0
 
 // ---- per-voxel updates shared by the direct and the TMA-fed kernels -------
 
-// velocity increment dt b (d1 + d2 + d3), buoyancy b = 2 / (rho_a + rho_b)
-__device__ __forceinline__ float vel_increment(float dt, float rho_a, float rho_b, float d1,
-                                               float d2, float d3)
+// velocity increment dt b (d1 + d2 + d3) with the buoyancy b of the two
+// cells' materials from the pair table (FP64-derived, one load)
+__device__ __forceinline__ float vel_increment(float dt, const float *buoy, int n_mat, int ma,
+                                               int mb, float d1, float d2, float d3)
 {
-    return dt * (2.0f * __frcp_rn(rho_a + rho_b)) * (d1 + d2 + d3);
+    return dt * __ldg(buoy + ma * n_mat + mb) * (d1 + d2 + d3);
 }
 
 // Per-material coefficients as the stress kernels hold them in shared memory.
