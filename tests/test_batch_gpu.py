@@ -17,9 +17,9 @@ def mods():
     return bvf, synth
 
 
-def make(bvf, synth, spec, n_steps):
+def make(bvf, synth, spec, n_steps, storage="f32"):
     c = synth.sweep_case(spec, n_steps=n_steps, dft_cycles=2)
-    s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+    s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml, storage=storage)
     s.set_materials(c.index, c.materials)
     s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src, c.c0,
                  c.envelope)
@@ -34,22 +34,24 @@ def outputs(s):
             [s.peak().cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy()])
 
 
-@pytest.mark.parametrize("kchunk,graph_steps", [(0, 0), (5, 16), (13, 7)])
-def test_gpu_batch_matches_single_runs_bitwise(mods, kchunk, graph_steps):
+@pytest.mark.parametrize("kchunk,graph_steps,storage", [(0, 0, "f32"), (5, 16, "f32"),
+                                                         (13, 7, "f32"), (6, 9, "f16")])
+def test_gpu_batch_matches_single_runs_bitwise(mods, kchunk, graph_steps, storage):
     """Four domains of different sizes (ragged y and z, two x-tiles or one),
     frequencies, tilts and step counts: every state array, the peak map and
-    the FP64 amplitude and phase equal those of single-context runs."""
+    the FP64 amplitude and phase equal those of single-context runs (FP32 and
+    FP16 storage)."""
     bvf, synth = mods
     specs = synth.sweep_specs(n=4, seed=7, n_min=40, n_max=72)
     n_steps = [60, 90, 75, 40]
     ref = []
     for spec, n in zip(specs, n_steps):
-        c, s, cap = make(bvf, synth, spec, n)
+        c, s, cap = make(bvf, synth, spec, n, storage)
         s.run(n, peak_from=cap[0], dft_start=cap[1], dft_steps=cap[2])
         s.synchronize()
         ref.append(outputs(s))
         s.close()
-    made = [make(bvf, synth, spec, n) for spec, n in zip(specs, n_steps)]
+    made = [make(bvf, synth, spec, n, storage) for spec, n in zip(specs, n_steps)]
     solvers = [m[1] for m in made]
     b = bvf.Batch(solvers)
     b.run(n_steps, caps=[m[2] for m in made], kchunk=kchunk, graph_steps=graph_steps)
