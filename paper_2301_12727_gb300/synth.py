@@ -282,3 +282,40 @@ def sweep_case(spec: dict, n_steps: int | None = None, dft_cycles: int = 10) -> 
     b["apex"] = (ax, ay, min(az, c.k_src * c.dx - 2e-3 - top))
     c.bowl = b
     return c
+
+
+def fno_weights(dims: dict, seed: int, gain: float = 1.0) -> np.ndarray:
+    """Seeded float32 weights in the surrogate's flat blob layout (lift, then
+    per layer spectral R, pointwise W and b, then the projection), scaled by
+    fan-in so that every layer keeps O(1) activations; the spectral weights
+    take 1/width."""
+    rng = np.random.default_rng(seed)
+    ci, w, m, L, h, co = (dims["c_in"], dims["width"], dims["modes"], dims["n_layers"],
+                          dims["hidden"], dims["c_out"])
+    m3 = (2 * m) * (2 * m) * m
+    parts = [rng.standard_normal(w * ci) * gain / np.sqrt(ci), rng.standard_normal(w) * 0.1]
+    for _ in range(L):
+        parts += [rng.standard_normal(m3 * w * w * 2) * gain / w,
+                  rng.standard_normal(w * w) * gain / np.sqrt(w), rng.standard_normal(w) * 0.1]
+    parts += [rng.standard_normal(h * w) * gain / np.sqrt(w), rng.standard_normal(h) * 0.1,
+              rng.standard_normal(co * h) * gain / np.sqrt(h), rng.standard_normal(co) * 0.1]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def fno_inputs(c_in: int, nx: int, ny: int, nz: int, seed: int) -> np.ndarray:
+    """Seeded float32 feature volume [c_in, nz, ny, nx]: smooth random fields
+    (sums of a few low Fourier modes) plus white noise, like material maps."""
+    rng = np.random.default_rng(seed)
+    z = np.arange(nz)[:, None, None] / nz
+    y = np.arange(ny)[None, :, None] / ny
+    x = np.arange(nx)[None, None, :] / nx
+    out = np.empty((c_in, nz, ny, nx), dtype=np.float32)
+    for c in range(c_in):
+        f = 0.1 * rng.standard_normal((nz, ny, nx))
+        for _ in range(4):
+            a, b, k = rng.integers(-3, 4, size=3)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += rng.standard_normal() * np.cos(2 * np.pi * (a * z + b * y + k * x) + ph)
+        out[c] = f
+    return out
+
