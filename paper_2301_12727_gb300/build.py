@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbvf.so")
 SOURCES = ("bvf_api.cu", "bvf_acoustic.cu", "bvf_acoustic_tma.cu", "bvf_aux.cu",
-           "bvf_noalloc.cu")
+           "bvf_noalloc.cu", "bvf_fno.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-cudart", "shared", "--expt-relaxed-constexpr"]
@@ -36,7 +36,7 @@ def _stale(target: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
-    headers.append(os.path.join(HERE, "..", "include", "bvf.h"))
+    headers += [os.path.join(HERE, "..", "include", h) for h in ("bvf.h", "bvf_fno.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -1,0 +1,748 @@
+// Fourier-neural-operator surrogate: inference kernels and the C ABI of
+// bvf_fno.h.  The network is the Fourier neural operator of Li et al. (ICLR
+// 2021, Sec. 4); the paper's Discussion names learned models as the route to
+// interactive planning, with the FDTD as the reference they are judged by.
+//
+// The truncated FFT of a Fourier layer is done as direct DFT sums over the
+// kept modes, one axis at a time, because only m of the n frequencies of
+// each axis survive: along x a block stages 128 rows in chunks of 32 samples
+// in shared memory and each thread owns one frequency of 8 rows; the y and z
+// stages and their inverses run on the truncated spectra (a few MB,
+// L2-resident).  Twiddles come from per-grid tables e^{2 pi i f j / n}
+// computed in FP64 on the host.  The last
+// inverse (along x) is fused with the pointwise channel mix W v + b and the
+// GELU into one pass that reads v and writes the next layer's v once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bvf_fno.h"
+#include "bvf_internal.cuh"
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+int fno_fail(int code, const std::string &msg)
+{
+    bvf::set_context_free_error(msg.c_str());
+    return code;
+}
+
+int fno_cuda(cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fno_fail(e == cudaErrorMemoryAllocation ? BVF_E_NOMEM : BVF_E_CUDA, m);
+}
+
+#define FCK(call, where)                                \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return fno_cuda(e_, where); \
+    } while (0)
+
+bool dims_valid(const bvf_fno_dims *d)
+{
+    return d && d->c_in >= 1 && d->c_in <= BVF_FNO_MAX_CIN && d->width >= 4 &&
+           d->width <= BVF_FNO_MAX_WIDTH && d->width % 4 == 0 && d->modes >= 1 &&
+           d->modes <= BVF_FNO_MAX_MODES && d->n_layers >= 1 &&
+           d->n_layers <= BVF_FNO_MAX_LAYERS && d->hidden >= 1 &&
+           d->hidden <= BVF_FNO_MAX_HIDDEN && d->c_out >= 1 && d->c_out <= BVF_FNO_MAX_COUT;
+}
+
+size_t layer_floats(const bvf_fno_dims &d)
+{
+    const size_t m3 = (size_t)(2 * d.modes) * (2 * d.modes) * d.modes;
+    return m3 * d.width * d.width * 2 + (size_t)d.width * d.width + d.width;
+}
+
+// signed frequency of mode slot j in [0, 2m) of a y or z axis
+__host__ __device__ __forceinline__ int slot_freq(int j, int m) { return j < m ? j : j - 2 * m; }
+
+__device__ __forceinline__ float gelu(float s)
+{
+    return 0.5f * s * (1.0f + erff(s * 0.70710678118654752f));
+}
+
+// ------------------------------------------------------------------ lift
+__global__ void k_lift(const float *__restrict__ a, int c_in, int width,
+                       const float *__restrict__ Wp, const float *__restrict__ bp,
+                       float *__restrict__ v, int N)
+{
+    extern __shared__ float s_w[];
+    const int nw = width * c_in;
+    for (int t = threadIdx.x; t < nw + width; t += blockDim.x)
+        s_w[t] = t < nw ? Wp[t] : bp[t - nw];
+    __syncthreads();
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    float x[BVF_FNO_MAX_CIN];
+#pragma unroll
+    for (int i = 0; i < BVF_FNO_MAX_CIN; ++i) x[i] = i < c_in ? a[(size_t)i * N + p] : 0.0f;
+    for (int o = 0; o < width; ++o) {
+        float acc = s_w[nw + o];
+#pragma unroll
+        for (int i = 0; i < BVF_FNO_MAX_CIN; ++i)
+            if (i < c_in) acc = fmaf(s_w[o * c_in + i], x[i], acc);
+        v[(size_t)o * N + p] = acc;
+    }
+}
+
+// ------------------------------------------------------ forward DFT along x
+// A[r][kx] = sum_x v[r][x] e^{-2 pi i kx x / nx} for the rows r = (c, z, y):
+// a [rows x nx] by [nx x m] complex product.  A block takes TR = 128 rows and
+// walks x in chunks of 32: the chunk of its rows (coalesced, row pitch 34
+// floats) and of the twiddle table go to shared memory, then each thread
+// accumulates one frequency of 8 rows, two x at a time.
+constexpr int kXR = 8;          // rows per thread
+constexpr int kXT = 128;        // rows per block
+constexpr int kXC = 32;         // x per chunk
+constexpr int kXP = kXC + 2;    // row pitch in shared memory
+
+__global__ void k_dftx(const float *__restrict__ v, int rows, int nx, int m,
+                       const float2 *__restrict__ tx, float2 *__restrict__ A)
+{
+    __shared__ __align__(16) float s_u[kXT * kXP];
+    __shared__ __align__(16) float2 s_t[BVF_FNO_MAX_MODES * kXC];
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const long r0 = (long)blockIdx.x * kXT;
+    const int kx = tid % m, g = tid / m;       // g < kXT / kXR
+    float re[kXR], im[kXR];
+#pragma unroll
+    for (int q = 0; q < kXR; ++q) re[q] = im[q] = 0.0f;
+    for (int x0 = 0; x0 < nx; x0 += kXC) {
+        const int w = min(kXC, nx - x0);
+        __syncthreads();
+        for (int e = tid; e < kXT * kXC; e += nth) {
+            const int r = e / kXC, x = e - r * kXC;
+            const long rr = r0 + r;
+            s_u[r * kXP + x] = (x < w && rr < rows) ? v[rr * nx + x0 + x] : 0.0f;
+        }
+        for (int e = tid; e < m * kXC; e += nth) {
+            const int k = e / kXC, x = e - k * kXC;
+            s_t[e] = x < w ? tx[(long)k * nx + x0 + x] : make_float2(0.0f, 0.0f);
+        }
+        __syncthreads();
+        const float *u = s_u + g * kXR * kXP;
+        const float2 *t = s_t + kx * kXC;
+#pragma unroll 4
+        for (int x = 0; x < kXC; x += 2) {
+            const float2 t0 = t[x], t1 = t[x + 1];
+#pragma unroll
+            for (int q = 0; q < kXR; ++q) {
+                const float2 uu = *reinterpret_cast<const float2 *>(u + q * kXP + x);
+                re[q] = fmaf(uu.x, t0.x, fmaf(uu.y, t1.x, re[q]));
+                im[q] = fmaf(-uu.x, t0.y, fmaf(-uu.y, t1.y, im[q]));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kXR; ++q) {
+        const long r = r0 + g * kXR + q;
+        if (r < rows) A[r * m + kx] = make_float2(re[q], im[q]);
+    }
+}
+
+// complex a * e^{s i theta} with the table entry t = (cos, sin) and s = +-1
+__device__ __forceinline__ float2 cmul_tw(float2 a, float2 t, float s)
+{
+    return make_float2(a.x * t.x - s * a.y * t.y, a.y * t.x + s * a.x * t.y);
+}
+
+// ------------------------------------------------------ forward DFT along y
+// B[c][z][jy][kx] = sum_y A[c][z][y][kx] e^{-2 pi i f(jy) y / ny}; one block
+// per (c, z) slab, one thread per (jy, kx).
+__global__ void k_dfty(const float2 *__restrict__ A, int ny, int m,
+                       const float2 *__restrict__ ty, float2 *__restrict__ B)
+{
+    extern __shared__ float2 s_y[];
+    float2 *s_a = s_y;                  // [ny][m]
+    const long slab = blockIdx.x;
+    const float2 *a = A + slab * ny * m;
+    for (int e = threadIdx.x; e < ny * m; e += blockDim.x) s_a[e] = a[e];
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t >= 2 * m * m) return;
+    const int jy = t / m, kx = t - jy * m;
+    const float2 *tw = ty + (long)jy * ny;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int y = 0; y < ny; ++y) {
+        const float2 p = cmul_tw(s_a[y * m + kx], __ldg(tw + y), -1.0f);
+        acc.x += p.x;
+        acc.y += p.y;
+    }
+    B[(slab * 2 * m + jy) * m + kx] = acc;
+}
+
+// ------------------------------------------------------ forward DFT along z
+// H[c][jz][q] = sum_z B[c][z][q] e^{-2 pi i f(jz) z / nz}, q = (jy, kx).
+__global__ void k_dftz(const float2 *__restrict__ B, int nz, int m, int width,
+                       const float2 *__restrict__ tz, float2 *__restrict__ H)
+{
+    const int M2 = 2 * m * m;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)width * 2 * m * M2) return;
+    const int q = (int)(t % M2);
+    const long rest = t / M2;
+    const int jz = (int)(rest % (2 * m)), c = (int)(rest / (2 * m));
+    const float2 *b = B + (long)c * nz * M2 + q;
+    const float2 *tw = tz + (long)jz * nz;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int z = 0; z < nz; ++z) {
+        const float2 p = cmul_tw(b[(long)z * M2], __ldg(tw + z), -1.0f);
+        acc.x += p.x;
+        acc.y += p.y;
+    }
+    H[t] = acc;     // t = (c * 2m + jz) * M2 + q
+}
+
+// ------------------------------------------------------------ mode mixing
+// G[o][mode] = sum_c R[mode][c][o] H[c][mode]; block (width, 256/width modes).
+__global__ void k_mix(const float2 *__restrict__ H, const float2 *__restrict__ R, int width,
+                      int n_modes, float2 *__restrict__ G)
+{
+    extern __shared__ float2 s_h[];              // [blockDim.y][width]
+    const int o = threadIdx.x, ty = threadIdx.y;
+    const int mode = blockIdx.x * blockDim.y + ty;
+    for (int c = o; c < width; c += blockDim.x)
+        s_h[ty * width + c] = mode < n_modes ? H[(long)c * n_modes + mode] : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (mode >= n_modes) return;
+    const float2 *r = R + (long)mode * width * width + o;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int c = 0; c < width; ++c) {
+        const float2 w = r[(long)c * width], h = s_h[ty * width + c];
+        acc.x = fmaf(w.x, h.x, fmaf(-w.y, h.y, acc.x));
+        acc.y = fmaf(w.x, h.y, fmaf(w.y, h.x, acc.y));
+    }
+    G[(long)o * n_modes + mode] = acc;
+}
+
+// ------------------------------------------------------ inverse along z
+// B'[o][z][q] = sum_jz G[o][jz][q] e^{+2 pi i f(jz) z / nz}
+__global__ void k_idftz(const float2 *__restrict__ G, int nz, int m, int width,
+                        const float2 *__restrict__ tz, float2 *__restrict__ Bp)
+{
+    const int M2 = 2 * m * m;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)width * nz * M2) return;
+    const int q = (int)(t % M2);
+    const long rest = t / M2;
+    const int z = (int)(rest % nz), o = (int)(rest / nz);
+    const float2 *g = G + (long)o * 2 * m * M2 + q;
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int jz = 0; jz < 2 * m; ++jz) {
+        const float2 p = cmul_tw(g[(long)jz * M2], __ldg(tz + (long)jz * nz + z), 1.0f);
+        acc.x += p.x;
+        acc.y += p.y;
+    }
+    Bp[t] = acc;    // t = (o * nz + z) * M2 + q
+}
+
+// ------------------------------------------------------ inverse along y
+// A'[o][z][y][kx] = sum_jy B'[o][z][jy][kx] e^{+2 pi i f(jy) y / ny}; one block
+// per (o, z) slab.
+__global__ void k_idfty(const float2 *__restrict__ Bp, int ny, int m,
+                        const float2 *__restrict__ ty, float2 *__restrict__ Ap)
+{
+    extern __shared__ float2 s_y[];
+    const int M2 = 2 * m * m;
+    float2 *s_b = s_y;               // [2m][m]
+    const long slab = blockIdx.x;
+    for (int e = threadIdx.x; e < M2; e += blockDim.x) s_b[e] = Bp[slab * M2 + e];
+    __syncthreads();
+    float2 *out = Ap + slab * ny * m;
+    for (int e = threadIdx.x; e < ny * m; e += blockDim.x) {
+        const int y = e / m, kx = e - y * m;
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int jy = 0; jy < 2 * m; ++jy) {
+            const float2 p = cmul_tw(s_b[jy * m + kx], __ldg(ty + (long)jy * ny + y), 1.0f);
+            acc.x += p.x;
+            acc.y += p.y;
+        }
+        out[e] = acc;
+    }
+}
+
+// ------------------------------- inverse along x + pointwise mix + GELU
+// v'[o][p] = act( (1/N)[Re A'_0 + 2 sum_{kx>=1} Re(A'_kx e^{+2 pi i kx x/nx})]
+//                 + sum_c W[o][c] v[c][p] + b[o] ); one block per (z, y) row.
+template <int WMAX>
+__global__ void k_layer_out(const float *__restrict__ v, const float2 *__restrict__ Ap,
+                            const float *__restrict__ W, const float *__restrict__ b, int nx,
+                            int rows, int m, int width, float invN, int act,
+                            const float2 *__restrict__ tx, float *__restrict__ vout, int N)
+{
+    extern __shared__ float s_o[];
+    float *s_w = s_o;                                   // [width][width]
+    float *s_b = s_w + width * width;                   // [width]
+    float2 *s_a = reinterpret_cast<float2 *>(s_b + width + (width & 1));   // [width][m]
+    const int row = blockIdx.x;                         // z * ny + y
+    for (int e = threadIdx.x; e < width * width; e += blockDim.x) s_w[e] = W[e];
+    for (int e = threadIdx.x; e < width; e += blockDim.x) s_b[e] = b[e];
+    for (int e = threadIdx.x; e < width * m; e += blockDim.x) {
+        const int o = e / m, kx = e - o * m;
+        const float2 a = Ap[((long)o * rows + row) * m + kx];
+        const float s = (kx == 0 ? 1.0f : 2.0f) * invN;
+        s_a[e] = make_float2(a.x * s, a.y * s);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const long p = (long)row * nx + x;
+        float u[WMAX];
+#pragma unroll
+        for (int c = 0; c < WMAX; ++c) u[c] = c < width ? v[(long)c * N + p] : 0.0f;
+        float2 e[BVF_FNO_MAX_MODES];
+#pragma unroll
+        for (int k = 0; k < BVF_FNO_MAX_MODES; ++k)
+            e[k] = k < m ? __ldg(tx + (long)k * nx + x) : make_float2(0.0f, 0.0f);
+        for (int o = 0; o < width; ++o) {
+            float acc = s_b[o];
+            const float4 *w4 = reinterpret_cast<const float4 *>(s_w + o * width);
+#pragma unroll
+            for (int c = 0; c < WMAX; c += 4) {
+                if (c < width) {
+                    const float4 w = w4[c / 4];
+                    acc = fmaf(w.x, u[c], acc);
+                    acc = fmaf(w.y, u[c + 1], acc);
+                    acc = fmaf(w.z, u[c + 2], acc);
+                    acc = fmaf(w.w, u[c + 3], acc);
+                }
+            }
+            const float2 *a = s_a + o * m;
+#pragma unroll
+            for (int k = 0; k < BVF_FNO_MAX_MODES; ++k) {
+                if (k < m) {
+                    const float2 ak = a[k];
+                    acc = fmaf(ak.x, e[k].x, fmaf(-ak.y, e[k].y, acc));
+                }
+            }
+            vout[(long)o * N + p] = act ? gelu(acc) : acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- project
+// out[k][p] = q2[k] + sum_j Q2[k][j] GELU(q1[j] + sum_c Q1[j][c] v[c][p])
+template <int WMAX>
+__global__ void k_project(const float *__restrict__ v, const float *__restrict__ Q1,
+                          const float *__restrict__ q1, const float *__restrict__ Q2,
+                          const float *__restrict__ q2, int width, int hidden, int c_out,
+                          float *__restrict__ out, int N)
+{
+    extern __shared__ float s_p[];
+    float *s_q1w = s_p;                          // [hidden][width]
+    float *s_q1 = s_q1w + hidden * width;        // [hidden]
+    float *s_q2w = s_q1 + hidden;                // [c_out][hidden]
+    float *s_q2 = s_q2w + c_out * hidden;        // [c_out]
+    for (int e = threadIdx.x; e < hidden * width; e += blockDim.x) s_q1w[e] = Q1[e];
+    for (int e = threadIdx.x; e < hidden; e += blockDim.x) s_q1[e] = q1[e];
+    for (int e = threadIdx.x; e < c_out * hidden; e += blockDim.x) s_q2w[e] = Q2[e];
+    for (int e = threadIdx.x; e < c_out; e += blockDim.x) s_q2[e] = q2[e];
+    __syncthreads();
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    float u[WMAX];
+#pragma unroll
+    for (int c = 0; c < WMAX; ++c) u[c] = c < width ? v[(long)c * N + p] : 0.0f;
+    float o[BVF_FNO_MAX_COUT];
+#pragma unroll
+    for (int k = 0; k < BVF_FNO_MAX_COUT; ++k) o[k] = k < c_out ? s_q2[k] : 0.0f;
+    for (int j = 0; j < hidden; ++j) {
+        float acc = s_q1[j];
+        const float4 *w4 = reinterpret_cast<const float4 *>(s_q1w + j * width);
+#pragma unroll
+        for (int c = 0; c < WMAX; c += 4) {
+            if (c < width) {
+                const float4 w = w4[c / 4];
+                acc = fmaf(w.x, u[c], acc);
+                acc = fmaf(w.y, u[c + 1], acc);
+                acc = fmaf(w.z, u[c + 2], acc);
+                acc = fmaf(w.w, u[c + 3], acc);
+            }
+        }
+        const float h = gelu(acc);
+#pragma unroll
+        for (int k = 0; k < BVF_FNO_MAX_COUT; ++k)
+            if (k < c_out) o[k] = fmaf(s_q2w[k * hidden + j], h, o[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < BVF_FNO_MAX_COUT; ++k)
+        if (k < c_out) out[(long)k * N + p] = o[k];
+}
+
+// --------------------------------------------------------------- features
+struct FeatTable {
+    float f[BVF_MAX_MATERIALS][3];     // cL/cL_w - 1, rho/rho_w - 1, alphaL cL_w / f0
+};
+
+__global__ void k_features(const uint8_t *__restrict__ idx, const __grid_constant__ FeatTable tab,
+                           int nx, int ny, int nz, int k_src, const float2 *__restrict__ src,
+                           float inv_p, float *__restrict__ out)
+{
+    const long N = (long)nx * ny * nz;
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const int i = (int)(p % nx);
+    const long r = p / nx;
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const int mat = idx[p];
+    out[p] = tab.f[mat][0];
+    out[N + p] = tab.f[mat][1];
+    out[2 * N + p] = tab.f[mat][2];
+    float sr = 0.0f, si = 0.0f;
+    if (k == k_src) {
+        const float2 s = src[(long)j * nx + i];
+        sr = s.x * inv_p;
+        si = s.y * inv_p;
+    }
+    out[3 * N + p] = sr;
+    out[4 * N + p] = si;
+    out[5 * N + p] = ((float)i + 0.5f) / (float)nx;
+    out[6 * N + p] = ((float)j + 0.5f) / (float)ny;
+    out[7 * N + p] = ((float)k + 0.5f) / (float)nz;
+}
+
+}  // namespace
+
+// ================================================================== context
+struct bvf_fno {
+    bvf_fno_dims d{};
+    float *w = nullptr;                      // device copy of the blob
+    size_t n_w = 0;
+    // grid-dependent state
+    int nx = 0, ny = 0, nz = 0;
+    float2 *tw = nullptr;                    // twiddle tables [m][nx], [2m][ny], [2m][nz]
+    size_t tw_cap = 0;
+    float *v0 = nullptr, *v1 = nullptr;
+    size_t v_cap = 0;
+    float2 *A = nullptr, *B = nullptr, *H = nullptr, *G = nullptr;
+    size_t a_cap = 0, b_cap = 0, h_cap = 0;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_stage;
+    int n_ev = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+void free_ws(bvf_fno *f)
+{
+    cudaFree(f->tw);
+    cudaFree(f->v0);
+    cudaFree(f->v1);
+    cudaFree(f->A);
+    cudaFree(f->B);
+    cudaFree(f->H);
+    cudaFree(f->G);
+    f->tw = nullptr;
+    f->v0 = f->v1 = nullptr;
+    f->A = f->B = f->H = f->G = nullptr;
+    f->tw_cap = f->v_cap = f->a_cap = f->b_cap = f->h_cap = 0;
+    f->nx = f->ny = f->nz = 0;
+}
+
+template <typename T>
+int grow(T **p, size_t *cap, size_t n, const char *what)
+{
+    if (n <= *cap) return BVF_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    FCK(cudaMalloc(p, n * sizeof(T)), what);
+    *cap = n;
+    return BVF_OK;
+}
+
+// e^{+2 pi i f j / n} for j < n and each signed frequency f of `freqs`
+// (FP64 angle, reduced exactly as (f j mod n) / n before the multiplication)
+void mode_table(std::vector<float2> &t, const std::vector<int> &freqs, int n)
+{
+    for (int f : freqs)
+        for (int j = 0; j < n; ++j) {
+            const long r = (((long)f * j) % n + n) % n;
+            const double a = kTwoPi * (double)r / (double)n;
+            t.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+}
+
+int prepare_grid(bvf_fno *f, int nx, int ny, int nz)
+{
+    if (f->nx == nx && f->ny == ny && f->nz == nz) return BVF_OK;
+    const int m = f->d.modes, W = f->d.width;
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t M2 = (size_t)2 * m * m;
+    int rc;
+    // buffers of an earlier grid may still be in use on some stream
+    FCK(cudaDeviceSynchronize(), "bvf_fno_forward: sync before a grid change");
+    if ((size_t)W * N > f->v_cap) {
+        cudaFree(f->v0);
+        cudaFree(f->v1);
+        f->v0 = f->v1 = nullptr;
+        f->v_cap = 0;
+        FCK(cudaMalloc(&f->v0, (size_t)W * N * sizeof(float)), "workspace v0");
+        FCK(cudaMalloc(&f->v1, (size_t)W * N * sizeof(float)), "workspace v1");
+        f->v_cap = (size_t)W * N;
+    }
+    if ((rc = grow(&f->A, &f->a_cap, (size_t)W * nz * ny * m, "workspace A")) != BVF_OK) return rc;
+    if ((rc = grow(&f->B, &f->b_cap, (size_t)W * nz * M2, "workspace B")) != BVF_OK) return rc;
+    const size_t hn = (size_t)W * 2 * m * M2;      // H and G: the kept spectrum
+    if (hn > f->h_cap) {
+        cudaFree(f->H);
+        cudaFree(f->G);
+        f->H = f->G = nullptr;
+        f->h_cap = 0;
+        FCK(cudaMalloc(&f->H, hn * sizeof(float2)), "workspace H");
+        FCK(cudaMalloc(&f->G, hn * sizeof(float2)), "workspace G");
+        f->h_cap = hn;
+    }
+    // twiddle tables: [m][nx] for kx = 0 .. m-1, [2m][ny] and [2m][nz] for the
+    // signed slots of y and z
+    std::vector<int> fx(m), fs(2 * m);
+    for (int k = 0; k < m; ++k) fx[k] = k;
+    for (int j = 0; j < 2 * m; ++j) fs[j] = slot_freq(j, m);
+    std::vector<float2> t;
+    t.reserve((size_t)m * nx + (size_t)2 * m * (ny + nz));
+    mode_table(t, fx, nx);
+    mode_table(t, fs, ny);
+    mode_table(t, fs, nz);
+    if ((rc = grow(&f->tw, &f->tw_cap, t.size(), "twiddle table")) != BVF_OK) return rc;
+    FCK(cudaMemcpy(f->tw, t.data(), t.size() * sizeof(float2), cudaMemcpyHostToDevice),
+        "twiddle upload");
+    f->nx = nx;
+    f->ny = ny;
+    f->nz = nz;
+    return BVF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t bvf_fno_weight_count(const bvf_fno_dims *d)
+{
+    if (!dims_valid(d)) return 0;
+    return (size_t)d->width * d->c_in + d->width + (size_t)d->n_layers * layer_floats(*d) +
+           (size_t)d->hidden * d->width + d->hidden + (size_t)d->c_out * d->hidden + d->c_out;
+}
+
+int bvf_fno_create(bvf_fno **out, const bvf_fno_dims *d, const float *h_weights, size_t n)
+{
+    if (!out) return fno_fail(BVF_E_ARG, "bvf_fno_create: out is NULL");
+    *out = nullptr;
+    if (!dims_valid(d)) return fno_fail(BVF_E_ARG, "bvf_fno_create: dimensions out of range");
+    if (!h_weights) return fno_fail(BVF_E_ARG, "bvf_fno_create: weights are NULL");
+    if (n != bvf_fno_weight_count(d))
+        return fno_fail(BVF_E_ARG, "bvf_fno_create: weight count does not match the layout");
+    bvf_fno *f = new bvf_fno;
+    f->d = *d;
+    f->n_w = n;
+    cudaError_t e = cudaMalloc(&f->w, n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(f->w, h_weights, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(f->w);
+        delete f;
+        return fno_cuda(e, "bvf_fno_create: weights");
+    }
+    *out = f;
+    return BVF_OK;
+}
+
+int bvf_fno_destroy(bvf_fno *f)
+{
+    if (!f) return BVF_OK;
+    cudaDeviceSynchronize();
+    for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
+    free_ws(f);
+    cudaFree(f->w);
+    delete f;
+    return BVF_OK;
+}
+
+int bvf_fno_timing(bvf_fno *f, int enable)
+{
+    if (!f) return fno_fail(BVF_E_ARG, "bvf_fno_timing: NULL surrogate");
+    f->timing = enable != 0;
+    f->n_ev = 0;
+    return BVF_OK;
+}
+
+int bvf_fno_stage_times(bvf_fno *f, double *ms_out)
+{
+    if (!f || !ms_out) return fno_fail(BVF_E_ARG, "bvf_fno_stage_times: NULL argument");
+    for (int s = 0; s < BVF_FNO_STAGES; ++s) ms_out[s] = 0.0;
+    if (!f->timing || f->n_ev < 2) return BVF_OK;
+    FCK(cudaEventSynchronize(f->ev[f->n_ev - 1]), "bvf_fno_stage_times");
+    for (int i = 1; i < f->n_ev; ++i) {
+        float ms = 0.0f;
+        FCK(cudaEventElapsedTime(&ms, f->ev[i - 1], f->ev[i]), "bvf_fno_stage_times");
+        ms_out[f->ev_stage[i]] += ms;
+    }
+    return BVF_OK;
+}
+
+int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float *d_out,
+                    void *stream)
+{
+    if (!f || !d_in || !d_out) return fno_fail(BVF_E_ARG, "bvf_fno_forward: NULL argument");
+    const bvf_fno_dims &d = f->d;
+    const int m = d.modes, W = d.width;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 1024 || ny > 1024 || nz > 4096)
+        return fno_fail(BVF_E_ARG, "bvf_fno_forward: grid sizes out of range");
+    if (m > nx / 2 || 2 * m > ny || 2 * m > nz)
+        return fno_fail(BVF_E_ARG, "bvf_fno_forward: grid too small for the kept modes");
+    const long long N64 = (long long)nx * ny * nz;
+    if (N64 >= (1LL << 31)) return fno_fail(BVF_E_ARG, "bvf_fno_forward: nx*ny*nz >= 2^31");
+    const size_t in_bytes = (size_t)d.c_in * N64 * sizeof(float);
+    const size_t out_bytes = (size_t)d.c_out * N64 * sizeof(float);
+    const char *ib = reinterpret_cast<const char *>(d_in), *ob = reinterpret_cast<const char *>(d_out);
+    if (ib < ob + out_bytes && ob < ib + in_bytes)
+        return fno_fail(BVF_E_ARG, "bvf_fno_forward: input and output overlap");
+    int rc = prepare_grid(f, nx, ny, nz);
+    if (rc != BVF_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    f->last_stream = s;
+    const int N = (int)N64;
+    const int M2 = 2 * m * m, n_modes = 2 * m * M2;
+    const float2 *tx = f->tw, *ty = tx + (size_t)m * nx, *tz = ty + (size_t)2 * m * ny;
+
+    // stage events
+    const int n_ev_need = 2 + 7 * d.n_layers + 1;
+    if (f->timing) {
+        while ((int)f->ev.size() < n_ev_need) {
+            cudaEvent_t e;
+            FCK(cudaEventCreate(&e), "bvf_fno_forward: event");
+            f->ev.push_back(e);
+        }
+        f->ev_stage.assign(n_ev_need, 0);
+        f->n_ev = 0;
+        FCK(cudaEventRecord(f->ev[f->n_ev++], s), "bvf_fno_forward: event");
+    }
+    auto mark = [&](int stage) -> cudaError_t {
+        if (!f->timing) return cudaSuccess;
+        f->ev_stage[f->n_ev] = stage;
+        return cudaEventRecord(f->ev[f->n_ev++], s);
+    };
+
+    // weight offsets
+    const float *Wp = f->w, *bp = Wp + (size_t)W * d.c_in;
+    const float *lay0 = bp + W;
+    const size_t lf = layer_floats(d);
+    const float *proj = lay0 + d.n_layers * lf;
+    const float *Q1 = proj, *q1 = Q1 + (size_t)d.hidden * W, *Q2 = q1 + d.hidden,
+                *q2 = Q2 + (size_t)d.c_out * d.hidden;
+
+    const int TB = 256;
+    const int pblocks = (N + TB - 1) / TB;
+    k_lift<<<pblocks, TB, (W * d.c_in + W) * sizeof(float), s>>>(d_in, d.c_in, W, Wp, bp, f->v0,
+                                                                  N);
+    FCK(cudaGetLastError(), "bvf_fno_forward: lift");
+    FCK(mark(0), "event");
+
+    const size_t sy = (size_t)ny * m * sizeof(float2);
+    FCK(cudaFuncSetAttribute(k_dfty, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy),
+        "bvf_fno_forward: dfty smem");
+    const size_t s_out = ((size_t)W * W + W + 1) * sizeof(float) + (size_t)W * m * sizeof(float2);
+    const size_t s_prj = ((size_t)d.hidden * W + d.hidden + (size_t)d.c_out * d.hidden + d.c_out) *
+                         sizeof(float);
+    const int rows_x = W * nz * ny;
+    const int rows_p = nz * ny;
+    const int bo = std::min(256, ((nx + 31) / 32) * 32);
+
+    float *vc = f->v0, *vn = f->v1;
+    for (int l = 0; l < d.n_layers; ++l) {
+        const float *lw = lay0 + l * lf;
+        const float2 *R = reinterpret_cast<const float2 *>(lw);
+        const float *Wl = lw + (size_t)n_modes * W * W * 2, *bl = Wl + (size_t)W * W;
+        k_dftx<<<(rows_x + kXT - 1) / kXT, m * (kXT / kXR), 0, s>>>(vc, rows_x, nx, m, tx, f->A);
+        FCK(cudaGetLastError(), "bvf_fno_forward: dftx");
+        FCK(mark(1), "event");
+        k_dfty<<<W * nz, std::max(32, 2 * m * m), sy, s>>>(f->A, ny, m, ty, f->B);
+        FCK(cudaGetLastError(), "bvf_fno_forward: dfty");
+        FCK(mark(2), "event");
+        const long nh = (long)W * 2 * m * M2;
+        k_dftz<<<(unsigned)((nh + TB - 1) / TB), TB, 0, s>>>(f->B, nz, m, W, tz, f->H);
+        FCK(cudaGetLastError(), "bvf_fno_forward: dftz");
+        FCK(mark(3), "event");
+        const dim3 mb(W, 256 / W);
+        k_mix<<<(n_modes + mb.y - 1) / mb.y, mb, mb.y * W * sizeof(float2), s>>>(f->H, R, W,
+                                                                                 n_modes, f->G);
+        FCK(cudaGetLastError(), "bvf_fno_forward: mix");
+        FCK(mark(4), "event");
+        const long nb = (long)W * nz * M2;
+        k_idftz<<<(unsigned)((nb + TB - 1) / TB), TB, 0, s>>>(f->G, nz, m, W, tz, f->B);
+        FCK(cudaGetLastError(), "bvf_fno_forward: idftz");
+        FCK(mark(5), "event");
+        k_idfty<<<W * nz, TB, (size_t)M2 * sizeof(float2), s>>>(f->B, ny, m, ty, f->A);
+        FCK(cudaGetLastError(), "bvf_fno_forward: idfty");
+        FCK(mark(6), "event");
+        const int act = l < d.n_layers - 1;
+        const float invN = (float)(1.0 / (double)N64);
+        if (W <= 16)
+            k_layer_out<16><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN, act,
+                                                     tx, vn, N);
+        else if (W <= 32)
+            k_layer_out<32><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN, act,
+                                                     tx, vn, N);
+        else
+            k_layer_out<64><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN, act,
+                                                     tx, vn, N);
+        FCK(cudaGetLastError(), "bvf_fno_forward: layer_out");
+        FCK(mark(7), "event");
+        std::swap(vc, vn);
+    }
+    if (W <= 16) {
+        FCK(cudaFuncSetAttribute(k_project<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s_prj), "project smem");
+        k_project<16><<<pblocks, TB, s_prj, s>>>(vc, Q1, q1, Q2, q2, W, d.hidden, d.c_out, d_out, N);
+    } else if (W <= 32) {
+        FCK(cudaFuncSetAttribute(k_project<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s_prj), "project smem");
+        k_project<32><<<pblocks, TB, s_prj, s>>>(vc, Q1, q1, Q2, q2, W, d.hidden, d.c_out, d_out, N);
+    } else {
+        FCK(cudaFuncSetAttribute(k_project<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)s_prj), "project smem");
+        k_project<64><<<pblocks, TB, s_prj, s>>>(vc, Q1, q1, Q2, q2, W, d.hidden, d.c_out, d_out, N);
+    }
+    FCK(cudaGetLastError(), "bvf_fno_forward: project");
+    FCK(mark(8), "event");
+    return BVF_OK;
+}
+
+int bvf_fno_features(const uint8_t *d_index, const bvf_material *h_table, int n_mat,
+                     const bvf_material *h_water, int nx, int ny, int nz, double f0, int k_src,
+                     const float *d_src, double p_norm, float *d_out, void *stream)
+{
+    if (!d_index || !h_table || !h_water || !d_src || !d_out)
+        return fno_fail(BVF_E_ARG, "bvf_fno_features: NULL argument");
+    if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz >= (1LL << 31))
+        return fno_fail(BVF_E_ARG, "bvf_fno_features: bad grid");
+    if (n_mat < 1 || n_mat > BVF_MAX_MATERIALS)
+        return fno_fail(BVF_E_ARG, "bvf_fno_features: n_mat out of range");
+    if (k_src < 0 || k_src >= nz) return fno_fail(BVF_E_ARG, "bvf_fno_features: k_src outside the grid");
+    if (!(p_norm > 0.0) || !(f0 > 0.0))
+        return fno_fail(BVF_E_ARG, "bvf_fno_features: p_norm and f0 must be positive");
+    if (!(h_water->rho > 0.0) || !(h_water->cL > 0.0))
+        return fno_fail(BVF_E_MATERIAL, "bvf_fno_features: water row needs rho, cL > 0");
+    FeatTable tab;
+    std::memset(&tab, 0, sizeof(tab));
+    for (int i = 0; i < n_mat; ++i) {
+        tab.f[i][0] = (float)(h_table[i].cL / h_water->cL - 1.0);
+        tab.f[i][1] = (float)(h_table[i].rho / h_water->rho - 1.0);
+        tab.f[i][2] = (float)(h_table[i].alphaL * h_water->cL / f0);
+    }
+    const long N = (long)nx * ny * nz;
+    k_features<<<(unsigned)((N + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d_index, tab, nx, ny, nz, k_src, reinterpret_cast<const float2 *>(d_src),
+        (float)(1.0 / p_norm), d_out);
+    FCK(cudaGetLastError(), "bvf_fno_features");
+    return BVF_OK;
+}
+
+}  // extern "C"

@@ -1,5 +1,6 @@
-"""The C-ABI library loads and exports every entry point include/bvf.h
-declares; host-side validation answers without touching a GPU."""
+"""The C-ABI library loads and exports every entry point include/bvf.h and
+include/bvf_fno.h declare; host-side validation answers without touching a
+GPU."""
 import ctypes
 import os
 import re
@@ -17,8 +18,8 @@ def bvf():
     return m
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "bvf.h")).read()
+def declared_functions(header="bvf.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(bvf_[a-z0-9_]+)\s*\(", src)))
 
@@ -68,3 +69,46 @@ def test_null_pointers_rejected(bvf):
     assert L.bvf_run_acoustic(None, 1, None, None) == bvf.BVF_E_ARG
     assert L.bvf_set_materials(None, None, None, 0) == bvf.BVF_E_ARG
     L.bvf_destroy(None)
+
+
+def test_surrogate_header_symbols_are_exported(bvf):
+    from paper_2301_12727_gb300 import fno
+    names = declared_functions("bvf_fno.h")
+    assert "bvf_fno_forward" in names
+    lib = fno.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(fno.EXPORTS)
+
+
+def test_surrogate_validation_on_host(bvf):
+    from oracle import fno as ofno
+    from paper_2301_12727_gb300 import fno
+    good = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1)
+    assert fno.bvf_fno_weight_count(fno.FnoDims(**good)) == ofno.weight_count(**good)
+    for bad in (dict(good, width=30), dict(good, width=128), dict(good, modes=0),
+                dict(good, modes=17), dict(good, c_in=17), dict(good, hidden=0),
+                dict(good, c_out=9), dict(good, n_layers=0)):
+        assert fno.bvf_fno_weight_count(fno.FnoDims(**bad)) == 0
+    L = fno.lib()
+    h = ctypes.c_void_p()
+    d = fno.FnoDims(**good)
+    w = (ctypes.c_float * 4)()
+    assert L.bvf_fno_create(ctypes.byref(h), ctypes.byref(d), w, 4) == bvf.BVF_E_ARG
+    assert not h.value and L.bvf_last_error(None)
+    assert L.bvf_fno_create(ctypes.byref(h), ctypes.byref(d), None,
+                            ofno.weight_count(**good)) == bvf.BVF_E_ARG
+    assert L.bvf_fno_create(None, ctypes.byref(d), w, 4) == bvf.BVF_E_ARG
+    assert L.bvf_fno_forward(None, 8, 8, 8, None, None, None) == bvf.BVF_E_ARG
+    tab = bvf.material_array([(1000.0, 1500.0, 0, 0, 0, 0.6, 4180, 0, 0)])
+    fake = ctypes.c_void_p(16)
+    # k_src outside the grid, non-positive p_norm, bad material count: refused
+    # before any device work
+    assert L.bvf_fno_features(fake, tab, 1, tab, 8, 8, 8, 5e5, 8, fake, 1.0, fake,
+                              None) == bvf.BVF_E_ARG
+    assert L.bvf_fno_features(fake, tab, 1, tab, 8, 8, 8, 5e5, 0, fake, 0.0, fake,
+                              None) == bvf.BVF_E_ARG
+    assert L.bvf_fno_features(fake, tab, 0, tab, 8, 8, 8, 5e5, 0, fake, 1.0, fake,
+                              None) == bvf.BVF_E_ARG
+    L.bvf_fno_destroy(None)
+
