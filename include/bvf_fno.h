@@ -46,7 +46,7 @@ extern "C" {
 
 typedef struct {
     int c_in;        /* input channels, 1 .. BVF_FNO_MAX_CIN            */
-    int width;       /* channels of the Fourier layers, a multiple of 4, 4 .. BVF_FNO_MAX_WIDTH */
+    int width;       /* channels of the Fourier layers: 16, 32, 48 or 64 */
     int modes;       /* m, 1 .. BVF_FNO_MAX_MODES                        */
     int n_layers;    /* Fourier layers, 1 .. BVF_FNO_MAX_LAYERS          */
     int hidden;      /* projection width, 1 .. BVF_FNO_MAX_HIDDEN         */
@@ -71,8 +71,9 @@ int bvf_fno_destroy(bvf_fno *f);
 /* One inference: d_in [c_in][nz][ny][nx] -> d_out [c_out][nz][ny][nx], both
  * caller-owned device memory that must not overlap.  The context keeps a
  * workspace sized for the largest grid seen (two activation volumes of
- * width*nx*ny*nz floats plus the truncated spectra); a larger grid grows it
- * before the launches, which makes that call synchronous.  Errors: BVF_E_ARG
+ * width*nx*ny*nz floats plus the truncated spectra); a call on a grid other
+ * than the previous call's synchronises the device first (the workspace may
+ * grow and the twiddle tables are rebuilt).  Errors: BVF_E_ARG
  * (NULL pointers, grid too small for the modes, nx*ny*nz >= 2^31),
  * BVF_E_NOMEM, BVF_E_CUDA. */
 int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float *d_out,
@@ -97,7 +98,9 @@ int bvf_fno_features(const uint8_t *d_index, const bvf_material *h_table, int n_
  * events when timing is enabled (bvf_fno_timing); all zero otherwise.
  * Stages: 0 lift, 1 forward DFT along x, 2 along y, 3 along z, 4 mode mixing,
  * 5 inverse along z, 6 inverse along y, 7 inverse along x + pointwise + GELU,
- * 8 projection.  Synchronises `stream` of the last forward. */
+ * 8 projection.  Where a (z, y) row of every channel fits in shared memory,
+ * the forward x transform runs inside the lift and the stage-7 pass (stage 1
+ * then reads about zero).  Synchronises `stream` of the last forward. */
 #define BVF_FNO_STAGES 9
 int bvf_fno_timing(bvf_fno *f, int enable);
 int bvf_fno_stage_times(bvf_fno *f, double *ms_out);

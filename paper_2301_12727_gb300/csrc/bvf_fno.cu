@@ -47,8 +47,8 @@ int fno_cuda(cudaError_t e, const char *where)
 
 bool dims_valid(const bvf_fno_dims *d)
 {
-    return d && d->c_in >= 1 && d->c_in <= BVF_FNO_MAX_CIN && d->width >= 4 &&
-           d->width <= BVF_FNO_MAX_WIDTH && d->width % 4 == 0 && d->modes >= 1 &&
+    return d && d->c_in >= 1 && d->c_in <= BVF_FNO_MAX_CIN && d->width >= 16 &&
+           d->width <= BVF_FNO_MAX_WIDTH && d->width % 16 == 0 && d->modes >= 1 &&
            d->modes <= BVF_FNO_MAX_MODES && d->n_layers >= 1 &&
            d->n_layers <= BVF_FNO_MAX_LAYERS && d->hidden >= 1 &&
            d->hidden <= BVF_FNO_MAX_HIDDEN && d->c_out >= 1 && d->c_out <= BVF_FNO_MAX_COUT;
@@ -63,9 +63,22 @@ size_t layer_floats(const bvf_fno_dims &d)
 // signed frequency of mode slot j in [0, 2m) of a y or z axis
 __host__ __device__ __forceinline__ int slot_freq(int j, int m) { return j < m ? j : j - 2 * m; }
 
+// GELU(s) = s Phi(s) = (s/2)(1 + erf(s/sqrt 2)).  erf is Hastings' rational
+// approximation as printed in Abramowitz & Stegun, Handbook of Mathematical
+// Functions, 7.1.26: for x >= 0, erf(x) = 1 - t(a1 + t(a2 + t(a3 + t(a4 + t a5))))
+// e^{-x^2} with t = 1/(1 + p x), |error| <= 1.5e-7; odd symmetry for x < 0.
 __device__ __forceinline__ float gelu(float s)
 {
-    return 0.5f * s * (1.0f + erff(s * 0.70710678118654752f));
+    const float x = fabsf(s) * 0.70710678118654752f;
+    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.0f));
+    float q = fmaf(1.061405429f, t, -1.453152027f);
+    q = fmaf(q, t, 1.421413741f);
+    q = fmaf(q, t, -0.284496736f);
+    q = fmaf(q, t, 0.254829592f);
+    const float erfc_x = q * t * __expf(-x * x);
+    // s Phi(s): Phi(|s|) = 1 - erfc/2 for s >= 0, Phi(-|s|) = erfc/2
+    const float phi = s >= 0.0f ? 1.0f - 0.5f * erfc_x : 0.5f * erfc_x;
+    return s * phi;
 }
 
 // ------------------------------------------------------------------ lift
@@ -326,53 +339,309 @@ __global__ void k_layer_out(const float *__restrict__ v, const float2 *__restric
     }
 }
 
-// ---------------------------------------------------------------- project
-// out[k][p] = q2[k] + sum_j Q2[k][j] GELU(q1[j] + sum_c Q1[j][c] v[c][p])
-template <int WMAX>
-__global__ void k_project(const float *__restrict__ v, const float *__restrict__ Q1,
-                          const float *__restrict__ q1, const float *__restrict__ Q2,
-                          const float *__restrict__ q2, int width, int hidden, int c_out,
-                          float *__restrict__ out, int N)
+// ------------------------------------------- tensor-core tiles (TF32 x 3)
+// mma.sync m16n8k8 with TF32 operands and FP32 accumulation.  Each FP32
+// operand is split into a TF32 head and the TF32 rounding of its remainder,
+// and a b is taken as a_lo b_hi + a_hi b_lo + a_hi b_hi (the three-product
+// scheme of Ootomo and Yokota, 2022), which keeps FP32-level accuracy.
+// Fragment layout (lane = 4 g + t): A rows g, g+8 and columns t, t+4;
+// B rows t, t+4 and column g; C/D rows g, g+8 and columns 2t, 2t+1.
+__device__ __forceinline__ uint32_t tf32_rna(float x)
 {
-    extern __shared__ float s_p[];
-    float *s_q1w = s_p;                          // [hidden][width]
-    float *s_q1 = s_q1w + hidden * width;        // [hidden]
-    float *s_q2w = s_q1 + hidden;                // [c_out][hidden]
-    float *s_q2 = s_q2w + c_out * hidden;        // [c_out]
-    for (int e = threadIdx.x; e < hidden * width; e += blockDim.x) s_q1w[e] = Q1[e];
-    for (int e = threadIdx.x; e < hidden; e += blockDim.x) s_q1[e] = q1[e];
-    for (int e = threadIdx.x; e < c_out * hidden; e += blockDim.x) s_q2w[e] = Q2[e];
-    for (int e = threadIdx.x; e < c_out; e += blockDim.x) s_q2[e] = q2[e];
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
+{
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += a b in three products (small terms first)
+__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4],
+                                     const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
+                                     uint32_t bl0, uint32_t bl1)
+{
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, ah, bh0, bh1);
+}
+
+// ------------------------------------------------- tensor-core projection
+// out[k][p] = q2[k] + sum_j Q2[k][j] GELU(q1[j] + sum_c Q1[j][c] v[c][p]).
+// Persistent blocks keep Q1 (split, row pitch PQ = 4 mod 32 so that the B
+// fragment loads hit 32 distinct banks), q1 and Q2 in shared memory; each
+// warp takes 16-point tiles, loads its A fragments (16 points x width) from
+// global memory once, sweeps the hidden units 8 at a time, applies GELU on
+// the accumulators and folds them into per-lane partial outputs, which the
+// four lanes of a row group combine with shuffles.
+__host__ __device__ __forceinline__ int proj_pitch(int width)
+{
+    int p = width + 4;
+    while (p % 32 != 4) ++p;
+    return p;
+}
+
+template <int KS, int COUT>   // KS = width / 8 k-steps; COUT padded output count
+__global__ void __launch_bounds__(256, 2)
+k_project_mma(const float *__restrict__ v, const float *__restrict__ Q1,
+              const float *__restrict__ q1, const float *__restrict__ Q2,
+              const float *__restrict__ q2, int hidden, int c_out, float *__restrict__ out,
+              int N)
+{
+    constexpr int width = 8 * KS;
+    extern __shared__ __align__(16) uint32_t s_q[];
+    const int PQ = proj_pitch(width);
+    const int hp = (hidden + 7) & ~7;
+    uint32_t *qh = s_q, *ql = s_q + hp * PQ;
+    float *sq1 = reinterpret_cast<float *>(ql + hp * PQ);
+    float *sq2 = sq1 + hp;                        // [COUT][hp]
+    for (int j = threadIdx.y; j < hp; j += blockDim.y)
+        for (int c = threadIdx.x; c < width; c += blockDim.x) {
+            const float w = j < hidden ? Q1[(long)j * width + c] : 0.0f;
+            uint32_t h, l;
+            tf32_split(w, h, l);
+            qh[j * PQ + c] = h;
+            ql[j * PQ + c] = l;
+        }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+    for (int j = tid; j < hp; j += nth) sq1[j] = j < hidden ? q1[j] : 0.0f;
+    for (int e = tid; e < COUT * hp; e += nth) {
+        const int k = e / hp, j = e - k * hp;
+        sq2[e] = (k < c_out && j < hidden) ? Q2[(long)k * hidden + j] : 0.0f;
+    }
     __syncthreads();
-    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N) return;
-    float u[WMAX];
+
+    const int lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const long warp = (long)blockIdx.x * (nth / 32) + (tid >> 5);
+    const long nwarps = (long)gridDim.x * (nth / 32);
+    const long tiles = ((long)N + 15) / 16;
+    for (long tile = warp; tile < tiles; tile += nwarps) {
+        const long p0 = tile * 16;
+        const long pa = p0 + g, pb = p0 + g + 8;
+        const bool oka = pa < N, okb = pb < N;
+        uint32_t ah[KS][4], al[KS][4];
 #pragma unroll
-    for (int c = 0; c < WMAX; ++c) u[c] = c < width ? v[(long)c * N + p] : 0.0f;
-    float o[BVF_FNO_MAX_COUT];
+        for (int ks = 0; ks < KS; ++ks) {
+            const int c0 = 8 * ks + t, c1 = c0 + 4;
+            const float x0 = oka ? v[(long)c0 * N + pa] : 0.0f;
+            const float x1 = okb ? v[(long)c0 * N + pb] : 0.0f;
+            const float x2 = oka ? v[(long)c1 * N + pa] : 0.0f;
+            const float x3 = okb ? v[(long)c1 * N + pb] : 0.0f;
+            tf32_split(x0, ah[ks][0], al[ks][0]);
+            tf32_split(x1, ah[ks][1], al[ks][1]);
+            tf32_split(x2, ah[ks][2], al[ks][2]);
+            tf32_split(x3, ah[ks][3], al[ks][3]);
+        }
+        float oa[COUT], ob[COUT];
 #pragma unroll
-    for (int k = 0; k < BVF_FNO_MAX_COUT; ++k) o[k] = k < c_out ? s_q2[k] : 0.0f;
-    for (int j = 0; j < hidden; ++j) {
-        float acc = s_q1[j];
-        const float4 *w4 = reinterpret_cast<const float4 *>(s_q1w + j * width);
+        for (int k = 0; k < COUT; ++k) oa[k] = ob[k] = 0.0f;
+        for (int n0 = 0; n0 < hp; n0 += 8) {
+            const float2 bias = *reinterpret_cast<const float2 *>(sq1 + n0 + 2 * t);
+            float d[4] = {bias.x, bias.y, bias.x, bias.y};
+            const uint32_t *bh = qh + (n0 + g) * PQ + t, *bl = ql + (n0 + g) * PQ + t;
 #pragma unroll
-        for (int c = 0; c < WMAX; c += 4) {
-            if (c < width) {
-                const float4 w = w4[c / 4];
-                acc = fmaf(w.x, u[c], acc);
-                acc = fmaf(w.y, u[c + 1], acc);
-                acc = fmaf(w.z, u[c + 2], acc);
-                acc = fmaf(w.w, u[c + 3], acc);
+            for (int ks = 0; ks < KS; ++ks)
+                mma3(d, ah[ks], al[ks], bh[8 * ks], bh[8 * ks + 4], bl[8 * ks], bl[8 * ks + 4]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) d[i] = gelu(d[i]);
+#pragma unroll
+            for (int k = 0; k < COUT; ++k) {
+                const float2 w = *reinterpret_cast<const float2 *>(sq2 + k * hp + n0 + 2 * t);
+                oa[k] = fmaf(w.x, d[0], fmaf(w.y, d[1], oa[k]));
+                ob[k] = fmaf(w.x, d[2], fmaf(w.y, d[3], ob[k]));
             }
         }
-        const float h = gelu(acc);
 #pragma unroll
-        for (int k = 0; k < BVF_FNO_MAX_COUT; ++k)
-            if (k < c_out) o[k] = fmaf(s_q2w[k * hidden + j], h, o[k]);
+        for (int k = 0; k < COUT; ++k) {
+            oa[k] += __shfl_xor_sync(0xffffffffu, oa[k], 1);
+            oa[k] += __shfl_xor_sync(0xffffffffu, oa[k], 2);
+            ob[k] += __shfl_xor_sync(0xffffffffu, ob[k], 1);
+            ob[k] += __shfl_xor_sync(0xffffffffu, ob[k], 2);
+        }
+        if (t == 0) {
+#pragma unroll
+            for (int k = 0; k < COUT; ++k) {
+                if (k < c_out) {
+                    if (oka) out[(long)k * N + pa] = q2[k] + oa[k];
+                    if (okb) out[(long)k * N + pb] = q2[k] + ob[k];
+                }
+            }
+        }
     }
+}
+
+// ------------------------------------------------ tensor-core row pass
+// The row pass above as two tensor-core products per (z, y) row:
+//   phase 2: D[x][o] = sum_k X[x][k] Y[k][o], X = [v[c][x] | cos, sin of the
+//            kept kx at x], Y = [W^T ; (Re A', -Im A') s_kx], s_0 = 1/N,
+//            s_kx = 2/N, plus b, then GELU;
+//   phase 3: Anext[o][kx] = sum_x v'[o][x] (cos - i sin)(kx x 2 pi / nx),
+//            a product over x of the new row (shared memory) and the table.
+// Persistent blocks keep the split twiddle table T[j][x] (j = 2 kx for cos,
+// 2 kx + 1 for sin, zero rows up to a multiple of 8) and the split W; each
+// row brings its own spectral rows of Y.  Pitches: P = 8 mod 32 for [.][x]
+// arrays and PW = 8 mod 32 for [k][o] arrays.
+struct RowMmaLayout {
+    int P, PW, JP, sTh, sTl, sWh, sWl, sSh, sSl, sV, sb, words;
+    __host__ __device__ RowMmaLayout(int ksw, int cout, int m, int nx)
+    {
+        const int nx16 = (nx + 15) & ~15;
+        P = nx16 + ((8 - nx16 % 32) + 32) % 32;
+        PW = cout + ((8 - cout % 32) + 32) % 32;
+        JP = ((2 * m + 7) / 8) * 8;
+        sTh = 0;
+        sTl = sTh + JP * P;
+        sWh = sTl + JP * P;
+        sWl = sWh + 8 * ksw * PW;
+        sSh = sWl + 8 * ksw * PW;
+        sSl = sSh + JP * PW;
+        sV = sSl + JP * PW;
+        sb = sV + cout * P;
+        words = sb + cout;
+    }
+};
+
+template <int NT, int KSW>     // cout = 8 NT output channels; input channels padded to 8 KSW
+__global__ void __launch_bounds__(256, 2)
+k_row_mma(const float *__restrict__ vin, int cin, const float2 *Ap, const float *__restrict__ W,
+          const float *__restrict__ b, int nx, int rows, int m, float invN, int act,
+          const float2 *__restrict__ tx, float *__restrict__ vout, float2 *Anext, int N)
+{
+    constexpr int cout = 8 * NT;
+    extern __shared__ __align__(16) uint32_t s_m[];
+    const RowMmaLayout L(KSW, cout, m, nx);
+    const int P = L.P, PW = L.PW, JP = L.JP, KSS = JP / 8;
+    const int nx16 = (nx + 15) & ~15;
+    uint32_t *sTh = s_m + L.sTh, *sTl = s_m + L.sTl, *sWh = s_m + L.sWh, *sWl = s_m + L.sWl,
+             *sSh = s_m + L.sSh, *sSl = s_m + L.sSl;
+    float *sV = reinterpret_cast<float *>(s_m + L.sV), *sb = reinterpret_cast<float *>(s_m + L.sb);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const bool spec = Ap != nullptr, fwd = Anext != nullptr;
+    // block-constant operands
+    if (spec || fwd) {
+        for (int j = 0; j < JP; ++j)
+            for (int x = tid; x < P; x += nth) {
+                float val = 0.0f;
+                if (j < 2 * m && x < nx) {
+                    const float2 e = tx[(long)(j >> 1) * nx + x];
+                    val = (j & 1) ? e.y : e.x;
+                }
+                tf32_split(val, sTh[j * P + x], sTl[j * P + x]);
+            }
+    }
+    for (int k = 0; k < 8 * KSW; ++k)
+        for (int o = tid; o < PW; o += nth) {
+            const float w = (k < cin && o < cout) ? W[(long)o * cin + k] : 0.0f;
+            tf32_split(w, sWh[k * PW + o], sWl[k * PW + o]);
+        }
+    for (int o = tid; o < cout; o += nth) sb[o] = b[o];
+
+    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const long base = (long)row * nx;
+        __syncthreads();          // the previous row is done with sS and sV
+        if (spec) {
+            for (int e = tid; e < JP * PW; e += nth) {
+                const int j = e / PW, o = e - j * PW;
+                float val = 0.0f;
+                if (j < 2 * m && o < cout) {
+                    const int kx = j >> 1;
+                    const float2 a = Ap[((long)o * rows + row) * m + kx];
+                    const float sc = (kx == 0 ? 1.0f : 2.0f) * invN;
+                    val = (j & 1) ? -a.y * sc : a.x * sc;
+                }
+                tf32_split(val, sSh[e], sSl[e]);
+            }
+        }
+        __syncthreads();
+        // phase 2: 16-point tiles of the row
+        for (int mt = warp; mt < nx16 / 16; mt += nth / 32) {
+            const int xa = 16 * mt + g, xb = xa + 8;
+            float d[NT][4];
 #pragma unroll
-    for (int k = 0; k < BVF_FNO_MAX_COUT; ++k)
-        if (k < c_out) out[(long)k * N + p] = o[k];
+            for (int nt = 0; nt < NT; ++nt) {
+                const float b0 = sb[8 * nt + 2 * t], b1 = sb[8 * nt + 2 * t + 1];
+                d[nt][0] = b0;
+                d[nt][1] = b1;
+                d[nt][2] = b0;
+                d[nt][3] = b1;
+            }
+#pragma unroll
+            for (int ks = 0; ks < KSW; ++ks) {
+                const int c0 = 8 * ks + t, c1 = c0 + 4;
+                uint32_t ah[4], al[4];
+                const bool c0ok = c0 < cin, c1ok = c1 < cin;
+                tf32_split(c0ok && xa < nx ? vin[(long)c0 * N + base + xa] : 0.0f, ah[0], al[0]);
+                tf32_split(c0ok && xb < nx ? vin[(long)c0 * N + base + xb] : 0.0f, ah[1], al[1]);
+                tf32_split(c1ok && xa < nx ? vin[(long)c1 * N + base + xa] : 0.0f, ah[2], al[2]);
+                tf32_split(c1ok && xb < nx ? vin[(long)c1 * N + base + xb] : 0.0f, ah[3], al[3]);
+                const uint32_t *wh = sWh + c0 * PW + g, *wl = sWl + c0 * PW + g;
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt)
+                    mma3(d[nt], ah, al, wh[8 * nt], wh[4 * PW + 8 * nt], wl[8 * nt],
+                         wl[4 * PW + 8 * nt]);
+            }
+            if (spec) {
+                for (int ks = 0; ks < KSS; ++ks) {
+                    const int j0 = 8 * ks + t;
+                    const uint32_t ah[4] = {sTh[j0 * P + xa], sTh[j0 * P + xb],
+                                            sTh[(j0 + 4) * P + xa], sTh[(j0 + 4) * P + xb]};
+                    const uint32_t al[4] = {sTl[j0 * P + xa], sTl[j0 * P + xb],
+                                            sTl[(j0 + 4) * P + xa], sTl[(j0 + 4) * P + xb]};
+                    const uint32_t *yh = sSh + j0 * PW + g, *yl = sSl + j0 * PW + g;
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+                        mma3(d[nt], ah, al, yh[8 * nt], yh[4 * PW + 8 * nt], yl[8 * nt],
+                             yl[4 * PW + 8 * nt]);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int o = 8 * nt + 2 * t + (i & 1), x = i < 2 ? xa : xb;
+                    const float val = act ? gelu(d[nt][i]) : d[nt][i];
+                    if (x < nx) vout[(long)o * N + base + x] = val;
+                    if (fwd) sV[o * P + x] = x < nx ? val : 0.0f;
+                }
+            }
+        }
+        if (!fwd) continue;
+        __syncthreads();
+        // phase 3: forward x transform of the new row
+        const int units = (cout / 16) * KSS;
+        for (int u = warp; u < units; u += nth / 32) {
+            const int o0 = 16 * (u / KSS), n0 = 8 * (u % KSS);
+            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const float *va = sV + (o0 + g) * P + t, *vb = sV + (o0 + g + 8) * P + t;
+            const uint32_t *th = sTh + (n0 + g) * P + t, *tl = sTl + (n0 + g) * P + t;
+            for (int x0 = 0; x0 < nx16; x0 += 8) {
+                uint32_t ah[4], al[4];
+                tf32_split(va[x0], ah[0], al[0]);
+                tf32_split(vb[x0], ah[1], al[1]);
+                tf32_split(va[x0 + 4], ah[2], al[2]);
+                tf32_split(vb[x0 + 4], ah[3], al[3]);
+                mma3(d, ah, al, th[x0], th[x0 + 4], tl[x0], tl[x0 + 4]);
+            }
+            const int kx = n0 / 2 + t;
+            if (kx < m) {
+                Anext[((long)(o0 + g) * rows + row) * m + kx] = make_float2(d[0], -d[1]);
+                Anext[((long)(o0 + g + 8) * rows + row) * m + kx] = make_float2(d[2], -d[3]);
+            }
+        }
+    }
 }
 
 // --------------------------------------------------------------- features
@@ -640,19 +909,70 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
 
     const int TB = 256;
     const int pblocks = (N + TB - 1) / TB;
-    k_lift<<<pblocks, TB, (W * d.c_in + W) * sizeof(float), s>>>(d_in, d.c_in, W, Wp, bp, f->v0,
-                                                                  N);
-    FCK(cudaGetLastError(), "bvf_fno_forward: lift");
+    const int rows_p = nz * ny;
+    const float invN = (float)(1.0 / (double)N64);
+    // the row pass keeps the twiddle table and one (z, y) row of every output
+    // channel in shared memory; rows too long for that take the unfused kernels
+    const int ksw_lift = (d.c_in + 7) / 8;
+    const size_t row_bytes =
+        (size_t)std::max(RowMmaLayout(W / 8, W, m, nx).words,
+                         RowMmaLayout(ksw_lift, W, m, nx).words) * sizeof(uint32_t);
+    const bool fused = row_bytes <= 110 * 1024;
+    int dev = 0, n_sm = 0;
+    FCK(cudaGetDevice(&dev), "bvf_fno_forward: device");
+    FCK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    const int row_grid = std::min(rows_p, 2 * n_sm);
+    auto row_pass = [&](const float *vin, int cin, const float2 *Ap, const float *Wm,
+                        const float *bm, int act, float *vout, float2 *An) -> cudaError_t {
+        const int ksw = (cin + 7) / 8;
+        const size_t bytes = (size_t)RowMmaLayout(ksw, W, m, nx).words * sizeof(uint32_t);
+        cudaError_t e = cudaSuccess;
+#define BVF_ROW(NT, KSW)                                                                     \
+    e = cudaFuncSetAttribute(k_row_mma<NT, KSW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             (int)bytes);                                                     \
+    if (e == cudaSuccess)                                                                     \
+        k_row_mma<NT, KSW><<<row_grid, 256, bytes, s>>>(vin, cin, Ap, Wm, bm, nx, rows_p, m,   \
+                                                        invN, act, tx, vout, An, N);
+        if (ksw == W / 8) {
+            switch (W / 8) {
+            case 2: BVF_ROW(2, 2) break;
+            case 4: BVF_ROW(4, 4) break;
+            case 6: BVF_ROW(6, 6) break;
+            default: BVF_ROW(8, 8) break;
+            }
+        } else if (ksw == 1) {
+            switch (W / 8) {
+            case 2: BVF_ROW(2, 1) break;
+            case 4: BVF_ROW(4, 1) break;
+            case 6: BVF_ROW(6, 1) break;
+            default: BVF_ROW(8, 1) break;
+            }
+        } else {
+            switch (W / 8) {
+            case 2: BVF_ROW(2, 2) break;
+            case 4: BVF_ROW(4, 2) break;
+            case 6: BVF_ROW(6, 2) break;
+            default: BVF_ROW(8, 2) break;
+            }
+        }
+#undef BVF_ROW
+        return e != cudaSuccess ? e : cudaGetLastError();
+    };
+
+    if (fused) {
+        FCK(row_pass(d_in, d.c_in, nullptr, Wp, bp, 0, f->v0, f->A), "bvf_fno_forward: lift");
+    } else {
+        k_lift<<<pblocks, TB, (W * d.c_in + W) * sizeof(float), s>>>(d_in, d.c_in, W, Wp, bp,
+                                                                      f->v0, N);
+        FCK(cudaGetLastError(), "bvf_fno_forward: lift");
+    }
     FCK(mark(0), "event");
 
     const size_t sy = (size_t)ny * m * sizeof(float2);
     FCK(cudaFuncSetAttribute(k_dfty, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy),
         "bvf_fno_forward: dfty smem");
     const size_t s_out = ((size_t)W * W + W + 1) * sizeof(float) + (size_t)W * m * sizeof(float2);
-    const size_t s_prj = ((size_t)d.hidden * W + d.hidden + (size_t)d.c_out * d.hidden + d.c_out) *
-                         sizeof(float);
     const int rows_x = W * nz * ny;
-    const int rows_p = nz * ny;
     const int bo = std::min(256, ((nx + 31) / 32) * 32);
 
     float *vc = f->v0, *vn = f->v1;
@@ -660,8 +980,11 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
         const float *lw = lay0 + l * lf;
         const float2 *R = reinterpret_cast<const float2 *>(lw);
         const float *Wl = lw + (size_t)n_modes * W * W * 2, *bl = Wl + (size_t)W * W;
-        k_dftx<<<(rows_x + kXT - 1) / kXT, m * (kXT / kXR), 0, s>>>(vc, rows_x, nx, m, tx, f->A);
-        FCK(cudaGetLastError(), "bvf_fno_forward: dftx");
+        if (!fused) {
+            k_dftx<<<(rows_x + kXT - 1) / kXT, m * (kXT / kXR), 0, s>>>(vc, rows_x, nx, m, tx,
+                                                                       f->A);
+            FCK(cudaGetLastError(), "bvf_fno_forward: dftx");
+        }
         FCK(mark(1), "event");
         k_dfty<<<W * nz, std::max(32, 2 * m * m), sy, s>>>(f->A, ny, m, ty, f->B);
         FCK(cudaGetLastError(), "bvf_fno_forward: dfty");
@@ -683,32 +1006,55 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
         FCK(cudaGetLastError(), "bvf_fno_forward: idfty");
         FCK(mark(6), "event");
         const int act = l < d.n_layers - 1;
-        const float invN = (float)(1.0 / (double)N64);
-        if (W <= 16)
-            k_layer_out<16><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN, act,
-                                                     tx, vn, N);
-        else if (W <= 32)
-            k_layer_out<32><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN, act,
-                                                     tx, vn, N);
-        else
-            k_layer_out<64><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN, act,
-                                                     tx, vn, N);
-        FCK(cudaGetLastError(), "bvf_fno_forward: layer_out");
+        if (fused) {
+            FCK(row_pass(vc, W, f->A, Wl, bl, act, vn, act ? f->A : nullptr),
+                "bvf_fno_forward: row pass");
+        } else {
+            if (W <= 16)
+                k_layer_out<16><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN,
+                                                         act, tx, vn, N);
+            else if (W <= 32)
+                k_layer_out<32><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN,
+                                                         act, tx, vn, N);
+            else
+                k_layer_out<64><<<rows_p, bo, s_out, s>>>(vc, f->A, Wl, bl, nx, rows_p, m, W, invN,
+                                                         act, tx, vn, N);
+            FCK(cudaGetLastError(), "bvf_fno_forward: layer_out");
+        }
         FCK(mark(7), "event");
         std::swap(vc, vn);
     }
-    if (W <= 16) {
-        FCK(cudaFuncSetAttribute(k_project<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)s_prj), "project smem");
-        k_project<16><<<pblocks, TB, s_prj, s>>>(vc, Q1, q1, Q2, q2, W, d.hidden, d.c_out, d_out, N);
-    } else if (W <= 32) {
-        FCK(cudaFuncSetAttribute(k_project<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)s_prj), "project smem");
-        k_project<32><<<pblocks, TB, s_prj, s>>>(vc, Q1, q1, Q2, q2, W, d.hidden, d.c_out, d_out, N);
-    } else {
-        FCK(cudaFuncSetAttribute(k_project<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)s_prj), "project smem");
-        k_project<64><<<pblocks, TB, s_prj, s>>>(vc, Q1, q1, Q2, q2, W, d.hidden, d.c_out, d_out, N);
+    {
+        const int hp = (d.hidden + 7) & ~7, cp = d.c_out == 1 ? 1 : 8;
+        const size_t s_prj =
+            ((size_t)2 * hp * proj_pitch(W) + hp + (size_t)cp * hp) * sizeof(float);
+        const long tiles = (N64 + 15) / 16;
+        const int grid = (int)std::min<long>(tiles / 8 + 1, (long)n_sm * 4);
+        const dim3 pb(32, 8);
+        cudaError_t e = cudaSuccess;
+#define BVF_PRJ(KS, CP)                                                                     \
+    e = cudaFuncSetAttribute(k_project_mma<KS, CP>,                                         \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_prj);     \
+    if (e == cudaSuccess)                                                                   \
+        k_project_mma<KS, CP><<<grid, pb, s_prj, s>>>(vc, Q1, q1, Q2, q2, d.hidden, d.c_out, \
+                                                     d_out, N);
+        if (cp == 1) {
+            switch (W / 8) {
+            case 2: BVF_PRJ(2, 1) break;
+            case 4: BVF_PRJ(4, 1) break;
+            case 6: BVF_PRJ(6, 1) break;
+            default: BVF_PRJ(8, 1) break;
+            }
+        } else {
+            switch (W / 8) {
+            case 2: BVF_PRJ(2, 8) break;
+            case 4: BVF_PRJ(4, 8) break;
+            case 6: BVF_PRJ(6, 8) break;
+            default: BVF_PRJ(8, 8) break;
+            }
+        }
+#undef BVF_PRJ
+        FCK(e, "bvf_fno_forward: project smem");
     }
     FCK(cudaGetLastError(), "bvf_fno_forward: project");
     FCK(mark(8), "event");

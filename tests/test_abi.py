@@ -86,7 +86,8 @@ def test_surrogate_validation_on_host(bvf):
     from paper_2301_12727_gb300 import fno
     good = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1)
     assert fno.bvf_fno_weight_count(fno.FnoDims(**good)) == ofno.weight_count(**good)
-    for bad in (dict(good, width=30), dict(good, width=128), dict(good, modes=0),
+    for bad in (dict(good, width=30), dict(good, width=128), dict(good, width=8),
+                dict(good, width=20), dict(good, modes=0),
                 dict(good, modes=17), dict(good, c_in=17), dict(good, hidden=0),
                 dict(good, c_out=9), dict(good, n_layers=0)):
         assert fno.bvf_fno_weight_count(fno.FnoDims(**bad)) == 0

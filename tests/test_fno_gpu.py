@@ -40,10 +40,12 @@ def _run(mods, dims, grid, seed):
 @pytest.mark.parametrize("dims,grid", [
     (dict(c_in=8, width=16, modes=4, n_layers=3, hidden=32, c_out=2), (20, 11, 9)),
     (dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1), (40, 30, 27)),
-    (dict(c_in=3, width=8, modes=3, n_layers=2, hidden=5, c_out=3), (7, 6, 13)),
+    (dict(c_in=3, width=16, modes=3, n_layers=2, hidden=5, c_out=3), (7, 6, 13)),
     (dict(c_in=5, width=64, modes=6, n_layers=2, hidden=96, c_out=1), (37, 13, 12)),
-    (dict(c_in=16, width=20, modes=1, n_layers=1, hidden=256, c_out=8), (2, 2, 2)),
+    (dict(c_in=16, width=48, modes=1, n_layers=1, hidden=256, c_out=8), (2, 2, 2)),
     (dict(c_in=8, width=32, modes=16, n_layers=2, hidden=64, c_out=1), (33, 32, 40)),
+    # rows too long for the fused row pass (unfused kernels)
+    (dict(c_in=4, width=64, modes=16, n_layers=2, hidden=32, c_out=1), (600, 32, 33)),
 ])
 def test_gpu_surrogate_matches_oracle(mods, dims, grid):
     from oracle import fno as ofno
@@ -75,7 +77,7 @@ def test_gpu_features_match_oracle(mods):
 def test_gpu_surrogate_rejects_small_grids(mods):
     torch, fno, synth = mods
     from paper_2301_12727_gb300 import bvf
-    dims = dict(c_in=2, width=8, modes=4, n_layers=1, hidden=8, c_out=1)
+    dims = dict(c_in=2, width=16, modes=4, n_layers=1, hidden=8, c_out=1)
     net = fno.Surrogate(dims, synth.fno_weights(dims, 1))
     for grid in ((7, 8, 8), (8, 7, 8), (8, 8, 7)):          # m > nx/2 or 2m > ny, nz
         a = torch.zeros((2, grid[2], grid[1], grid[0]), device="cuda")
