@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--sweep-steps", type=int, default=200)
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the scaled-FP16-storage leg reported under mixed_precision")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the surrogate (Fourier neural operator) inference leg")
     return ap.parse_args()
 
 
@@ -243,6 +245,79 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+# Surrogate network: 4 Fourier layers, width 32, 12 modes, projection width
+# 128, run on the plan's grid.
+FNO_DIMS = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1)
+
+
+def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd):
+    """Inference time of the surrogate on the plan's feature volume (seeded
+    untrained weights: the time does not depend on their values), its stage
+    split, its HBM roofline, and the FP64 oracle timed on a 48^3 sample."""
+    import time
+    import numpy as np
+    import torch
+    from oracle import fno as ofno
+    from paper_2301_12727_gb300 import bvf, fno, synth
+    nx, ny, nz = case.nx, case.ny, case.nz
+    net = fno.Surrogate(FNO_DIMS, synth.fno_weights(FNO_DIMS, 2301))
+    idx = torch.from_numpy(case.index).cuda()
+    src = bvf.rs_plane(dict(case.bowl), nx, ny, case.dx, case.k_src * case.dx, case.f0)
+    feats = torch.empty((8, nz, ny, nx), dtype=torch.float32, device="cuda")
+    out = torch.empty((1, nz, ny, nx), dtype=torch.float32, device="cuda")
+    water = synth.water_row(case.f0)
+
+    def one():
+        fno.bvf_fno_features(idx, case.materials, water, case.f0, case.k_src, src,
+                             case.bowl["p0"], feats)
+        net(feats, out)
+
+    for _ in range(max(3, warmup)):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(5, steps)
+    e0.record()
+    for _ in range(k):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    net.timing(True)
+    one()
+    torch.cuda.synchronize()
+    stages = net.stage_times()
+    net.timing(False)
+    N = case.voxels
+    d = FNO_DIMS
+    # algorithmic bytes per inference: the features read by the lift, every
+    # activation volume written once and read once (lift, then each layer;
+    # the forward x transform is fused into the pass that writes a volume),
+    # the output written once; spectra and weights are below 2 %
+    act = 4.0 * d["width"] * N
+    bytes_inf = 4.0 * N * (d["c_in"] + d["c_out"]) + act * (2 * d["n_layers"] + 2)
+    peak, peak_kind = measured_peak_hbm()
+    # the oracle: FP64 numpy on a 48^3 sample of the same network
+    rng = np.random.default_rng(7)
+    a_small = rng.standard_normal((8, 48, 48, 48))
+    w = synth.fno_weights(FNO_DIMS, 2301).astype(np.float64)
+    t0 = time.perf_counter()
+    ofno.forward(a_small, w, **FNO_DIMS)
+    t_or = time.perf_counter() - t0
+    net.close()
+    return {"model": "Fourier neural operator, 4 layers, width 32, 12 modes, projection 128",
+            "weights": "seeded, untrained (inference time does not depend on the values)",
+            "grid": [nx, ny, nz], "ms_per_inference": ms, "voxels_per_s": N / (ms / 1e3),
+            "speedup_vs_plan": ms_plan / ms, "speedup_vs_plan_fdtd": ms_fdtd / ms,
+            "stages_ms": stages,
+            "tensor_core": "mma.sync m16n8k8 TF32, three-product FP32 split",
+            "roofline": {"bound": "hbm", "achieved": bytes_inf / (ms / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bytes_inf / (ms / 1e3) / 1e9 / peak,
+                         "peak_kind": peak_kind, "algorithmic_bytes": bytes_inf},
+            "oracle": {"voxels_per_s": 48 ** 3 / t_or, "sample": "one 48^3 inference, FP64 numpy",
+                       "cores": 1}}
+
+
 def run_bvf(args):
     import torch
     rank, world, local = dist_env()
@@ -353,6 +428,11 @@ def run_bvf(args):
                                          / max(float(ref.cem43.max()), 1e-300)}}
         pl2.close()
 
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        surrogate = surrogate_leg(case, args.steps, args.warmup, ms / args.steps,
+                                  (kt["stress_ms"] + kt["velocity_ms"]) / args.steps)
+
     # ---- roofline of the dominant kernel (stress + memory variables)
     N = case.voxels
     n_runs = 2 * args.steps
@@ -398,7 +478,7 @@ def run_bvf(args):
                              % (N * es * (9 + 6 * case.n_sls) / 1e6),
                        "EL": res.EL, "TS": res.TS},
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks,
-            "mixed_precision": mixed}
+            "mixed_precision": mixed, "surrogate": surrogate}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(case)
     if rank == 0:

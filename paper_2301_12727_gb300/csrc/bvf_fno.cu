@@ -182,13 +182,25 @@ __global__ void k_dfty(const float2 *__restrict__ A, int ny, int m,
     if (t >= 2 * m * m) return;
     const int jy = t / m, kx = t - jy * m;
     const float2 *tw = ty + (long)jy * ny;
-    float2 acc = make_float2(0.0f, 0.0f);
-    for (int y = 0; y < ny; ++y) {
-        const float2 p = cmul_tw(s_a[y * m + kx], __ldg(tw + y), -1.0f);
-        acc.x += p.x;
-        acc.y += p.y;
+    // four independent partial sums (y mod 4) for instruction-level parallelism
+    float2 acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    int y = 0;
+    for (; y + 4 <= ny; y += 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 p = cmul_tw(s_a[(y + q) * m + kx], __ldg(tw + y + q), -1.0f);
+            acc[q].x += p.x;
+            acc[q].y += p.y;
+        }
     }
-    B[(slab * 2 * m + jy) * m + kx] = acc;
+    for (; y < ny; ++y) {
+        const float2 p = cmul_tw(s_a[y * m + kx], __ldg(tw + y), -1.0f);
+        acc[0].x += p.x;
+        acc[0].y += p.y;
+    }
+    B[(slab * 2 * m + jy) * m + kx] =
+        make_float2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
+                    (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
 }
 
 // ------------------------------------------------------ forward DFT along z
