@@ -55,6 +55,8 @@ def parse():
                     help="skip the scaled-FP16-storage leg reported under mixed_precision")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate (Fourier neural operator) inference leg")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="run only the surrogate inference on --grid and print its line")
     return ap.parse_args()
 
 
@@ -250,6 +252,19 @@ def run_reference(args):
 FNO_DIMS = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1)
 
 
+def run_surrogate(args):
+    """The surrogate leg alone (one GPU): inference time on --grid."""
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    case = make_case(args, 0)
+    leg = surrogate_leg(case, args.steps, args.warmup, None, None)
+    print(json.dumps({"metric": "surrogate inference ms", "value": leg["ms_per_inference"],
+                      "unit": "ms", "higher_is_better": False, "surrogate": leg}), flush=True)
+    return 0
+
+
 def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd):
     """Inference time of the surrogate on the plan's feature volume (seeded
     untrained weights: the time does not depend on their values), its stage
@@ -308,7 +323,8 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd):
     return {"model": "Fourier neural operator, 4 layers, width 32, 12 modes, projection 128",
             "weights": "seeded, untrained (inference time does not depend on the values)",
             "grid": [nx, ny, nz], "ms_per_inference": ms, "voxels_per_s": N / (ms / 1e3),
-            "speedup_vs_plan": ms_plan / ms, "speedup_vs_plan_fdtd": ms_fdtd / ms,
+            "speedup_vs_plan": ms_plan / ms if ms_plan else None,
+            "speedup_vs_plan_fdtd": ms_fdtd / ms if ms_fdtd else None,
             "stages_ms": stages,
             "tensor_core": "mma.sync m16n8k8 TF32, three-product FP32 split",
             "roofline": {"bound": "hbm", "achieved": bytes_inf / (ms / 1e3) / 1e9, "peak": peak,
@@ -594,6 +610,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.surrogate:
+        return run_surrogate(args)
     return run_bvf(args)
 
 
