@@ -79,6 +79,11 @@ int bvf_fno_destroy(bvf_fno *f);
 int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float *d_out,
                     void *stream);
 
+/* Wait for `stream` and report: BVF_E_CUDA if a CUDA error occurred or if a
+ * kernel's bounded wait for its tensor-core results ran out since the last
+ * call (the flag is then cleared), BVF_E_ARG for a NULL surrogate. */
+int bvf_fno_synchronize(bvf_fno *f, void *stream);
+
 /* Feature volume of one placement for a surrogate with c_in =
  * BVF_FNO_FEATURES: d_out [8][nz][ny][nx] gets, per voxel of material row r
  * (d_index, uint8 on the device; h_table, n_mat rows in host memory) against

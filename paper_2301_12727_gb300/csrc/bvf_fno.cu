@@ -22,6 +22,7 @@
 
 #include "../../include/bvf_fno.h"
 #include "bvf_internal.cuh"
+#include "bvf_tma.cuh"
 
 namespace {
 
@@ -70,7 +71,7 @@ __host__ __device__ __forceinline__ int slot_freq(int j, int m) { return j < m ?
 __device__ __forceinline__ float gelu(float s)
 {
     const float x = fabsf(s) * 0.70710678118654752f;
-    const float t = __frcp_rn(fmaf(0.3275911f, x, 1.0f));
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
     float q = fmaf(1.061405429f, t, -1.453152027f);
     q = fmaf(q, t, 1.421413741f);
     q = fmaf(q, t, -0.284496736f);
@@ -390,110 +391,6 @@ __device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4],
     mma_tf32(d, ah, bh0, bh1);
 }
 
-// ------------------------------------------------- tensor-core projection
-// out[k][p] = q2[k] + sum_j Q2[k][j] GELU(q1[j] + sum_c Q1[j][c] v[c][p]).
-// Persistent blocks keep Q1 (split, row pitch PQ = 4 mod 32 so that the B
-// fragment loads hit 32 distinct banks), q1 and Q2 in shared memory; each
-// warp takes 16-point tiles, loads its A fragments (16 points x width) from
-// global memory once, sweeps the hidden units 8 at a time, applies GELU on
-// the accumulators and folds them into per-lane partial outputs, which the
-// four lanes of a row group combine with shuffles.
-__host__ __device__ __forceinline__ int proj_pitch(int width)
-{
-    int p = width + 4;
-    while (p % 32 != 4) ++p;
-    return p;
-}
-
-template <int KS, int COUT>   // KS = width / 8 k-steps; COUT padded output count
-__global__ void __launch_bounds__(256, 2)
-k_project_mma(const float *__restrict__ v, const float *__restrict__ Q1,
-              const float *__restrict__ q1, const float *__restrict__ Q2,
-              const float *__restrict__ q2, int hidden, int c_out, float *__restrict__ out,
-              int N)
-{
-    constexpr int width = 8 * KS;
-    extern __shared__ __align__(16) uint32_t s_q[];
-    const int PQ = proj_pitch(width);
-    const int hp = (hidden + 7) & ~7;
-    uint32_t *qh = s_q, *ql = s_q + hp * PQ;
-    float *sq1 = reinterpret_cast<float *>(ql + hp * PQ);
-    float *sq2 = sq1 + hp;                        // [COUT][hp]
-    for (int j = threadIdx.y; j < hp; j += blockDim.y)
-        for (int c = threadIdx.x; c < width; c += blockDim.x) {
-            const float w = j < hidden ? Q1[(long)j * width + c] : 0.0f;
-            uint32_t h, l;
-            tf32_split(w, h, l);
-            qh[j * PQ + c] = h;
-            ql[j * PQ + c] = l;
-        }
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-    for (int j = tid; j < hp; j += nth) sq1[j] = j < hidden ? q1[j] : 0.0f;
-    for (int e = tid; e < COUT * hp; e += nth) {
-        const int k = e / hp, j = e - k * hp;
-        sq2[e] = (k < c_out && j < hidden) ? Q2[(long)k * hidden + j] : 0.0f;
-    }
-    __syncthreads();
-
-    const int lane = tid & 31, g = lane >> 2, t = lane & 3;
-    const long warp = (long)blockIdx.x * (nth / 32) + (tid >> 5);
-    const long nwarps = (long)gridDim.x * (nth / 32);
-    const long tiles = ((long)N + 15) / 16;
-    for (long tile = warp; tile < tiles; tile += nwarps) {
-        const long p0 = tile * 16;
-        const long pa = p0 + g, pb = p0 + g + 8;
-        const bool oka = pa < N, okb = pb < N;
-        uint32_t ah[KS][4], al[KS][4];
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            const int c0 = 8 * ks + t, c1 = c0 + 4;
-            const float x0 = oka ? v[(long)c0 * N + pa] : 0.0f;
-            const float x1 = okb ? v[(long)c0 * N + pb] : 0.0f;
-            const float x2 = oka ? v[(long)c1 * N + pa] : 0.0f;
-            const float x3 = okb ? v[(long)c1 * N + pb] : 0.0f;
-            tf32_split(x0, ah[ks][0], al[ks][0]);
-            tf32_split(x1, ah[ks][1], al[ks][1]);
-            tf32_split(x2, ah[ks][2], al[ks][2]);
-            tf32_split(x3, ah[ks][3], al[ks][3]);
-        }
-        float oa[COUT], ob[COUT];
-#pragma unroll
-        for (int k = 0; k < COUT; ++k) oa[k] = ob[k] = 0.0f;
-        for (int n0 = 0; n0 < hp; n0 += 8) {
-            const float2 bias = *reinterpret_cast<const float2 *>(sq1 + n0 + 2 * t);
-            float d[4] = {bias.x, bias.y, bias.x, bias.y};
-            const uint32_t *bh = qh + (n0 + g) * PQ + t, *bl = ql + (n0 + g) * PQ + t;
-#pragma unroll
-            for (int ks = 0; ks < KS; ++ks)
-                mma3(d, ah[ks], al[ks], bh[8 * ks], bh[8 * ks + 4], bl[8 * ks], bl[8 * ks + 4]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) d[i] = gelu(d[i]);
-#pragma unroll
-            for (int k = 0; k < COUT; ++k) {
-                const float2 w = *reinterpret_cast<const float2 *>(sq2 + k * hp + n0 + 2 * t);
-                oa[k] = fmaf(w.x, d[0], fmaf(w.y, d[1], oa[k]));
-                ob[k] = fmaf(w.x, d[2], fmaf(w.y, d[3], ob[k]));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < COUT; ++k) {
-            oa[k] += __shfl_xor_sync(0xffffffffu, oa[k], 1);
-            oa[k] += __shfl_xor_sync(0xffffffffu, oa[k], 2);
-            ob[k] += __shfl_xor_sync(0xffffffffu, ob[k], 1);
-            ob[k] += __shfl_xor_sync(0xffffffffu, ob[k], 2);
-        }
-        if (t == 0) {
-#pragma unroll
-            for (int k = 0; k < COUT; ++k) {
-                if (k < c_out) {
-                    if (oka) out[(long)k * N + pa] = q2[k] + oa[k];
-                    if (okb) out[(long)k * N + pb] = q2[k] + ob[k];
-                }
-            }
-        }
-    }
-}
-
 // ------------------------------------------------ tensor-core row pass
 // The row pass above as two tensor-core products per (z, y) row:
 //   phase 2: D[x][o] = sum_k X[x][k] Y[k][o], X = [v[c][x] | cos, sin of the
@@ -656,6 +553,246 @@ k_row_mma(const float *__restrict__ vin, int cin, const float2 *Ap, const float 
     }
 }
 
+// ------------------------------------------------- tcgen05 (TF32, TMEM)
+// Fifth-generation tensor-core products: operands in shared memory in the
+// canonical K-major layout without swizzle (core matrices of 8 rows x 16
+// bytes, 128 contiguous bytes each; LBO = byte step between core matrices
+// along K, SBO = byte step between 8-row groups), the FP32 accumulator in
+// tensor memory, one thread issuing tcgen05.mma, completion through
+// tcgen05.commit on an mbarrier, and tcgen05.ld to bring rows back.
+namespace tc {
+
+__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((bvf::tma::saddr(p) >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;                      // descriptor version; no swizzle
+    return d;
+}
+
+// kind::tf32 instruction descriptor: D FP32, A and B TF32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     bvf::tma::saddr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     bvf::tma::saddr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 32 consecutive columns of this warp's 32 lanes: thread i of the warp gets
+// row (lane base + i), columns col .. col+31
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&r)[32])
+{
+    uint32_t u[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]),
+                   "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]),
+                   "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]),
+                   "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+                   "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]),
+                   "=r"(u[30]), "=r"(u[31])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+// byte offset of element (row, k) in a K-major TF32 operand with K columns
+__host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K)
+{
+    return (uint32_t)((((row >> 3) * (K >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
+}  // namespace tc
+
+// ------------------------------------------------ tcgen05 projection
+// out[k][p] = q2[k] + sum_j Q2[k][j] GELU(q1[j] + sum_c Q1[j][c] v[c][p]) on
+// 128-point tiles: D[128 points][HP hidden] = A[128][W] B[W][HP] in TMEM, as
+// three TF32 products (A_lo B_hi + A_hi B_lo + A_hi B_hi) per K step of 8.
+// 128 threads: thread i owns point i of the tile (A staging and epilogue).
+struct ProjTcLayout {
+    int HP, ncols, sAh, sAl, sBh, sBl, sq1, sq2, sred, bar, tmem, bytes;
+    __host__ __device__ ProjTcLayout(int width, int hidden, int c_out)
+    {
+        HP = (hidden + 15) & ~15;
+        ncols = 32;
+        while (ncols < HP) ncols *= 2;
+        const int a = 128 * width * 4, b = HP * width * 4;
+        sAh = 0;
+        sAl = sAh + a;
+        sBh = sAl + a;
+        sBl = sBh + b;
+        sq1 = sBl + b;
+        sq2 = sq1 + HP * 4;
+        sred = sq2 + c_out * HP * 4;
+        bar = (sred + c_out * 128 * 4 + 15) & ~15;
+        tmem = bar + 16;
+        bytes = tmem + 16;
+    }
+};
+
+template <int W, int COUT>     // COUT: output count rounded up to 1 or 8
+__global__ void __launch_bounds__(256, 2)
+k_project_tc(const float *__restrict__ v, const float *__restrict__ Q1, const float *__restrict__ q1,
+             const float *__restrict__ Q2, const float *__restrict__ q2, int hidden, int c_out,
+             float *__restrict__ out, int N, int *flag)
+{
+    extern __shared__ __align__(128) unsigned char s_t[];
+    const ProjTcLayout L(W, hidden, COUT);
+    const int HP = L.HP;
+    unsigned char *sAh = s_t + L.sAh, *sAl = s_t + L.sAl, *sBh = s_t + L.sBh, *sBl = s_t + L.sBl;
+    float *sq1 = reinterpret_cast<float *>(s_t + L.sq1), *sq2 = reinterpret_cast<float *>(s_t + L.sq2);
+    float *sred = reinterpret_cast<float *>(s_t + L.sred);     // [COUT][128] second-half sums
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_t + L.bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(s_t + L.tmem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int pt = tid & 127, half = tid >> 7;   // point of the tile; channel / column half
+    // B = Q1 as [HP rows][W] K-major, split; q1, Q2 (zero beyond hidden)
+    for (int e = tid; e < HP * W; e += 256) {
+        const int j = e / W, c = e - j * W;
+        const float w = j < hidden ? Q1[(long)j * W + c] : 0.0f;
+        uint32_t h, l;
+        tf32_split(w, h, l);
+        const uint32_t off = tc::kmaj_off(j, c, W);
+        *reinterpret_cast<uint32_t *>(sBh + off) = h;
+        *reinterpret_cast<uint32_t *>(sBl + off) = l;
+    }
+    for (int j = tid; j < HP; j += 256) sq1[j] = j < hidden ? q1[j] : 0.0f;
+    for (int e = tid; e < COUT * HP; e += 256) {
+        const int k = e / HP, j = e - k * HP;
+        sq2[e] = (k < c_out && j < hidden) ? Q2[(long)k * hidden + j] : 0.0f;
+    }
+    if (tid == 0) {
+        bvf::tma::mbar_init(bar, 1);
+        bvf::tma::mbar_init_fence();
+    }
+    if (warp == 0) {
+        tc::alloc(tslot, L.ncols);
+        tc::relinquish();
+    }
+    bvf::tma::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    constexpr int KS = W / 8, CH = W / 2;      // K steps; channels staged per thread
+    const uint32_t idesc = tc::idesc_tf32(128, HP);
+    const uint32_t sbo = (W / 4) * 128;
+    const long tiles = ((long)N + 127) / 128;
+    // this thread's channels of its point, loaded one tile ahead
+    float xr[CH];
+    auto load = [&](long tile) {
+        const long p = tile * 128 + pt;
+        const bool ok = p < N;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) xr[c] = ok ? v[(long)(half * CH + c) * N + p] : 0.0f;
+    };
+    if ((long)blockIdx.x < tiles) load(blockIdx.x);
+    int it = 0;
+    for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+        const long p = tile * 128 + pt;
+#pragma unroll
+        for (int c4 = 0; c4 < CH / 4; ++c4) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tf32_split(xr[4 * c4 + q], h[q], l[q]);
+            const uint32_t off = tc::kmaj_off(pt, half * CH + 4 * c4, W);
+            *reinterpret_cast<uint4 *>(sAh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(sAl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        bvf::tma::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint32_t ko = ks * 2 * 128;      // two core matrices per K step of 8
+                const uint64_t ah = tc::smem_desc(sAh + ko, 128, sbo);
+                const uint64_t al = tc::smem_desc(sAl + ko, 128, sbo);
+                const uint64_t bh = tc::smem_desc(sBh + ko, 128, sbo);
+                const uint64_t bl = tc::smem_desc(sBl + ko, 128, sbo);
+                tc::mma(tbase, al, bh, idesc, ks > 0);
+                tc::mma(tbase, ah, bl, idesc, 1);
+                tc::mma(tbase, ah, bh, idesc, 1);
+            }
+            tc::commit(bar);
+        }
+        // the next tile's loads overlap the products and this tile's epilogue
+        if (tile + gridDim.x < tiles) load(tile + gridDim.x);
+        // a warp reads tensor memory only when all its lanes saw the commit
+        const bool ready = __all_sync(0xffffffffu, bvf::tma::mbar_wait(bar, it & 1, flag));
+        tc::fence_after();
+        float o[COUT];
+#pragma unroll
+        for (int k = 0; k < COUT; ++k) o[k] = 0.0f;
+        if (ready) {
+            // 32-column chunks alternate between the two warp halves
+            for (int c0 = 32 * half; c0 < HP; c0 += 64) {
+                float r[32];
+                tc::ld32(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, r);
+                tc::wait_ld();
+                const int nv = min(32, HP - c0);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    if (i < nv) {
+                        const float h = gelu(r[i] + sq1[c0 + i]);
+#pragma unroll
+                        for (int k = 0; k < COUT; ++k) o[k] = fmaf(sq2[k * HP + c0 + i], h, o[k]);
+                    }
+                }
+            }
+        }
+        if (half) {
+#pragma unroll
+            for (int k = 0; k < COUT; ++k) sred[k * 128 + pt] = o[k];
+        }
+        tc::fence_before();
+        __syncthreads();          // TMEM, the A buffers and sred are settled
+        if (!half && p < N) {
+#pragma unroll
+            for (int k = 0; k < COUT; ++k)
+                if (k < c_out) out[(long)k * N + p] = q2[k] + o[k] + sred[k * 128 + pt];
+        }
+    }
+    tc::fence_after();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tbase, L.ncols);
+}
+
 // --------------------------------------------------------------- features
 struct FeatTable {
     float f[BVF_MAX_MATERIALS][3];     // cL/cL_w - 1, rho/rho_w - 1, alphaL cL_w / f0
@@ -695,6 +832,7 @@ struct bvf_fno {
     bvf_fno_dims d{};
     float *w = nullptr;                      // device copy of the blob
     size_t n_w = 0;
+    int *flag = nullptr;                     // device: bit 1 = a bounded wait ran out
     // grid-dependent state
     int nx = 0, ny = 0, nz = 0;
     float2 *tw = nullptr;                    // twiddle tables [m][nx], [2m][ny], [2m][nz]
@@ -826,8 +964,11 @@ int bvf_fno_create(bvf_fno **out, const bvf_fno_dims *d, const float *h_weights,
     f->n_w = n;
     cudaError_t e = cudaMalloc(&f->w, n * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(f->w, h_weights, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&f->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(f->flag, 0, sizeof(int));
     if (e != cudaSuccess) {
         cudaFree(f->w);
+        cudaFree(f->flag);
         delete f;
         return fno_cuda(e, "bvf_fno_create: weights");
     }
@@ -842,7 +983,21 @@ int bvf_fno_destroy(bvf_fno *f)
     for (cudaEvent_t e : f->ev) cudaEventDestroy(e);
     free_ws(f);
     cudaFree(f->w);
+    cudaFree(f->flag);
     delete f;
+    return BVF_OK;
+}
+
+int bvf_fno_synchronize(bvf_fno *f, void *stream)
+{
+    if (!f) return fno_fail(BVF_E_ARG, "bvf_fno_synchronize: NULL surrogate");
+    FCK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "bvf_fno_synchronize");
+    int h = 0;
+    FCK(cudaMemcpy(&h, f->flag, sizeof(int), cudaMemcpyDeviceToHost), "bvf_fno_synchronize");
+    if (h) {
+        FCK(cudaMemset(f->flag, 0, sizeof(int)), "bvf_fno_synchronize");
+        return fno_fail(BVF_E_CUDA, "bvf_fno_synchronize: a tensor-core completion wait ran out");
+    }
     return BVF_OK;
 }
 
@@ -1037,32 +1192,31 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
         std::swap(vc, vn);
     }
     {
-        const int hp = (d.hidden + 7) & ~7, cp = d.c_out == 1 ? 1 : 8;
-        const size_t s_prj =
-            ((size_t)2 * hp * proj_pitch(W) + hp + (size_t)cp * hp) * sizeof(float);
-        const long tiles = (N64 + 15) / 16;
-        const int grid = (int)std::min<long>(tiles / 8 + 1, (long)n_sm * 4);
-        const dim3 pb(32, 8);
+        const int cp = d.c_out == 1 ? 1 : 8;
+        const ProjTcLayout pl(W, d.hidden, cp);
+        const long tiles = (N64 + 127) / 128;
+        const int per_sm = std::max(1, std::min(2, 512 / pl.ncols));
+        const int grid = (int)std::min<long>(tiles, (long)n_sm * per_sm);
         cudaError_t e = cudaSuccess;
-#define BVF_PRJ(KS, CP)                                                                     \
-    e = cudaFuncSetAttribute(k_project_mma<KS, CP>,                                         \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_prj);     \
-    if (e == cudaSuccess)                                                                   \
-        k_project_mma<KS, CP><<<grid, pb, s_prj, s>>>(vc, Q1, q1, Q2, q2, d.hidden, d.c_out, \
-                                                     d_out, N);
+#define BVF_PRJ(WW, CP)                                                                      \
+    e = cudaFuncSetAttribute(k_project_tc<WW, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                             pl.bytes);                                                        \
+    if (e == cudaSuccess)                                                                      \
+        k_project_tc<WW, CP><<<grid, 256, pl.bytes, s>>>(vc, Q1, q1, Q2, q2, d.hidden, d.c_out, \
+                                                        d_out, N, f->flag);
         if (cp == 1) {
-            switch (W / 8) {
-            case 2: BVF_PRJ(2, 1) break;
-            case 4: BVF_PRJ(4, 1) break;
-            case 6: BVF_PRJ(6, 1) break;
-            default: BVF_PRJ(8, 1) break;
+            switch (W) {
+            case 16: BVF_PRJ(16, 1) break;
+            case 32: BVF_PRJ(32, 1) break;
+            case 48: BVF_PRJ(48, 1) break;
+            default: BVF_PRJ(64, 1) break;
             }
         } else {
-            switch (W / 8) {
-            case 2: BVF_PRJ(2, 8) break;
-            case 4: BVF_PRJ(4, 8) break;
-            case 6: BVF_PRJ(6, 8) break;
-            default: BVF_PRJ(8, 8) break;
+            switch (W) {
+            case 16: BVF_PRJ(16, 8) break;
+            case 32: BVF_PRJ(32, 8) break;
+            case 48: BVF_PRJ(48, 8) break;
+            default: BVF_PRJ(64, 8) break;
             }
         }
 #undef BVF_PRJ

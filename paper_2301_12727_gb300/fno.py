@@ -14,7 +14,7 @@ import numpy as np
 from . import bvf
 
 EXPORTS = ("bvf_fno_weight_count", "bvf_fno_create", "bvf_fno_destroy", "bvf_fno_forward",
-           "bvf_fno_features", "bvf_fno_timing", "bvf_fno_stage_times")
+           "bvf_fno_features", "bvf_fno_timing", "bvf_fno_stage_times", "bvf_fno_synchronize")
 N_FEATURES = 8
 N_STAGES = 9
 STAGES = ("lift", "dft_x", "dft_y", "dft_z", "mix", "idft_z", "idft_y", "out_x_pointwise",
@@ -47,6 +47,7 @@ def lib():
                                        ctypes.POINTER(bvf.Material), i, i, i, d, i, vp, d, vp, vp]
         L.bvf_fno_timing.argtypes = [vp, i]
         L.bvf_fno_stage_times.argtypes = [vp, ctypes.POINTER(d)]
+        L.bvf_fno_synchronize.argtypes = [vp, vp]
         _declared = True
     return L
 
@@ -89,6 +90,10 @@ def bvf_fno_features(index, table, water_row, f0, k_src, src, p_norm, out, strea
                                       bvf._stream(stream)))
 
 
+def bvf_fno_synchronize(h, stream=None):
+    bvf._check(lib().bvf_fno_synchronize(h, bvf._stream(stream)))
+
+
 def bvf_fno_timing(h, enable: bool):
     bvf._check(lib().bvf_fno_timing(h, 1 if enable else 0))
 
@@ -114,6 +119,9 @@ class Surrogate:
                               device=inp.device)
         bvf_fno_forward(self.h, inp, out, stream)
         return out
+
+    def synchronize(self, stream=None):
+        bvf_fno_synchronize(self.h, stream)
 
     def timing(self, enable: bool):
         bvf_fno_timing(self.h, enable)

@@ -31,7 +31,7 @@ def _run(mods, dims, grid, seed):
     a = synth.fno_inputs(dims["c_in"], nx, ny, nz, seed + 1)
     net = fno.Surrogate(dims, w)
     out = net(torch.from_numpy(a).cuda())
-    torch.cuda.synchronize()
+    net.synchronize()
     got = out.cpu().numpy()
     net.close()
     return w, a, got
@@ -105,7 +105,7 @@ def test_gpu_full_size_shift_equivariance(mods):
     u = net(a).clone()
     sh = (5, -17, 31)
     us = net(torch.roll(a, sh, dims=(1, 2, 3)).contiguous())
-    torch.cuda.synchronize()
+    net.synchronize()
     d = (us - torch.roll(u, sh, dims=(1, 2, 3))).abs().max().item()
     assert d <= 5 * TOL * u.abs().max().item()
     net.close()
@@ -123,7 +123,7 @@ def test_gpu_full_size_constant_field_is_the_mlp(mods):
     a = torch.from_numpy(np.broadcast_to(a0[:, None, None, None].astype(np.float32),
                                          (8, nz, ny, nx)).copy()).cuda()
     u = net(a)
-    torch.cuda.synchronize()
+    net.synchronize()
     p = ofno.unpack(w.astype(np.float64), **FULL)
     v = p["Wp"] @ a0.astype(np.float32).astype(np.float64) + p["bp"]
     for l, lay in enumerate(p["layers"]):
