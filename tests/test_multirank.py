@@ -43,7 +43,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_weak_scaling_bookkeeping():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
     (s0, ms0, rate0, vox), (s1, ms1, rate1, _) = out[0], out[1]
