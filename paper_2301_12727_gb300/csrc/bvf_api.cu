@@ -60,6 +60,7 @@ struct bvf_ctx {
     unsigned *scratch_u = nullptr;
     float *T2 = nullptr, *Q = nullptr, *cemf = nullptr;
     ThermCoef *tlut = nullptr;
+    float *kface = nullptr;      // [n_mat][n_mat] face conductivities of the BHTE
     // host mirror
     std::vector<bvf_material> table;
     std::vector<MatDerived> derived;
@@ -437,7 +438,8 @@ void bvf_destroy(bvf_ctx *c)
 {
     if (!c) return;
     void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut, c->buoy,
-                    c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->cemf, c->tlut};
+                    c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->cemf, c->tlut,
+                    c->kface};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -813,10 +815,22 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
         CK(cudaMalloc(&c->Q, c->N * sizeof(float)), "thermal buffers");
         CK(cudaMalloc(&c->cemf, c->N * sizeof(float)), "thermal buffers");
         CK(cudaMalloc(&c->tlut, BVF_MAX_MATERIALS * sizeof(ThermCoef)), "thermal buffers");
+        CK(cudaMalloc(&c->kface, (size_t)BVF_MAX_MATERIALS * BVF_MAX_MATERIALS * sizeof(float)),
+           "thermal buffers");
     }
+    // harmonic-mean face conductivity of every material pair (Sec. 2.4 FTCS
+    // stencil), in FP64 then rounded once
+    std::vector<float> kf((size_t)n_mat * n_mat);
+    for (int a = 0; a < n_mat; ++a)
+        for (int b = 0; b < n_mat; ++b) {
+            const double ka = c->table[a].k_th, kb = c->table[b].k_th;
+            kf[(size_t)a * n_mat + b] = (ka + kb > 0.0) ? (float)(2.0 * ka * kb / (ka + kb)) : 0.0f;
+        }
     CK(cudaMemsetAsync(c->cemf, 0, c->N * sizeof(float), s), "thermal buffers");
     CK(cudaMemcpyAsync(c->tlut, tl.data(), n_mat * sizeof(ThermCoef), cudaMemcpyHostToDevice, s),
        "thermal lut");
+    CK(cudaMemcpyAsync(c->kface, kf.data(), kf.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+       "thermal face table");
     CK(launch_heat_source(c->index, c->tlut, n_mat, d_amp, th->p_scale, c->Q, c->N, s), "heat source");
     c->launches++;
     ThParams p{};
@@ -829,6 +843,7 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     p.dt60 = (float)(th->dt / 60.0);
     p.idx = c->index;
     p.lut = c->tlut;
+    p.kface = c->kface;
     p.n_mat = n_mat;
     p.Q = c->Q;
     p.Tmax = d_Tmax;

@@ -171,10 +171,6 @@ __global__ void k_heat_source(const uint8_t *__restrict__ idx, const ThermCoef *
 // held.  Face conductivity: harmonic mean 2 k_c k_n / (k_c + k_n).
 constexpr int kThermChunk = 16;
 
-__device__ __forceinline__ float face_k(float kc, float kn)
-{
-    return 2.0f * kc * kn * __frcp_rn(kc + kn);
-}
 
 __global__ void __launch_bounds__(256) k_thermal(ThParams p)
 {
@@ -223,13 +219,15 @@ __global__ void __launch_bounds__(256) k_thermal(ThParams p)
             Tn = p.T_a;
         } else {
             const ThermCoef c = s_th[cur.mc];
-            const float kc = c.k, Tc = cur.Tc;
-            float lap = face_k(kc, s_th[cur.mw].k) * (cur.Tw - Tc);
-            lap += face_k(kc, s_th[cur.me].k) * (cur.Te - Tc);
-            lap += face_k(kc, s_th[cur.ms].k) * (cur.Ts - Tc);
-            lap += face_k(kc, s_th[cur.mq].k) * (cur.Tq - Tc);
-            lap += face_k(kc, s_th[mm].k) * (Tm - Tc);
-            lap += face_k(kc, s_th[nxt.mc].k) * (nxt.Tc - Tc);
+            const float Tc = cur.Tc;
+            // face conductivities 2 k_a k_b / (k_a + k_b) from the pair table
+            const float *kf = p.kface + cur.mc * p.n_mat;
+            float lap = __ldg(kf + cur.mw) * (cur.Tw - Tc);
+            lap += __ldg(kf + cur.me) * (cur.Te - Tc);
+            lap += __ldg(kf + cur.ms) * (cur.Ts - Tc);
+            lap += __ldg(kf + cur.mq) * (cur.Tq - Tc);
+            lap += __ldg(kf + mm) * (Tm - Tc);
+            lap += __ldg(kf + nxt.mc) * (nxt.Tc - Tc);
             const float rhs = lap * p.inv_dx2 - c.perfw * (Tc - p.T_a) + p.dc * cur.Q;
             Tn = Tc + p.dt * rhs * c.inv_rhoc;
         }

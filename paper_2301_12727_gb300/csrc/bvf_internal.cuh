@@ -136,6 +136,7 @@ struct ThParams {
     float dt, inv_dx2, T_a, dc, dt60;
     const uint8_t *idx;
     const ThermCoef *lut;
+    const float *kface;      // [n_mat][n_mat] harmonic-mean face conductivity (FP64-derived)
     int n_mat;
     const float *T;
     float *Tn;
