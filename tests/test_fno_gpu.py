@@ -133,3 +133,44 @@ def test_gpu_full_size_constant_field_is_the_mlp(mods):
     got = u.cpu().numpy()
     assert np.abs(got - ref[:, None, None, None]).max() <= 10 * TOL * max(1.0, abs(ref).max())
     net.close()
+
+
+def test_gpu_one_context_across_grid_changes_is_bit_identical(mods):
+    """A context reused on another grid regrows its workspace and rebuilds its
+    twiddle tables: every call equals a fresh context's, bit for bit."""
+    torch, fno, synth = mods
+    dims = dict(c_in=8, width=32, modes=6, n_layers=2, hidden=32, c_out=1)
+    w = synth.fno_weights(dims, 13)
+    grids = [(24, 20, 16), (40, 36, 30), (24, 20, 16)]
+    ins = [torch.from_numpy(synth.fno_inputs(8, *g, seed=20 + i)).cuda() for i, g in enumerate(grids)]
+    shared = fno.Surrogate(dims, w)
+    got = [shared(a).clone() for a in ins]
+    shared.synchronize()
+    shared.close()
+    for a, u in zip(ins, got):
+        fresh = fno.Surrogate(dims, w)
+        ref = fresh(a)
+        fresh.synchronize()
+        fresh.close()
+        assert torch.equal(u, ref)
+
+
+def test_gpu_stage_times_cover_the_inference(mods):
+    torch, fno, synth = mods
+    dims = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1)
+    net = fno.Surrogate(dims, synth.fno_weights(dims, 3))
+    a = torch.from_numpy(synth.fno_inputs(8, 64, 48, 40, 4)).cuda()
+    net(a)
+    net.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net(a)
+    e1.record()
+    net.synchronize()
+    st = net.stage_times()
+    total = e0.elapsed_time(e1)
+    assert set(st) == set(fno.STAGES)
+    assert all(v >= 0.0 for v in st.values())
+    assert 0.5 * total <= sum(st.values()) <= 1.05 * total
+    net.timing(False)
+    net.close()
