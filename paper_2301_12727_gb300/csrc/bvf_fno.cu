@@ -458,21 +458,44 @@ k_row_mma(const float *__restrict__ vin, int cin, const float2 *Ap, const float 
     for (int o = tid; o < cout; o += nth) sb[o] = b[o];
 
     const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    // rows j >= 2m and columns o >= cout of the spectral part of Y stay zero
+    if (spec) {
+        for (int e = tid; e < JP * PW; e += nth) {
+            const int j = e / PW, o = e - j * PW;
+            if (j >= 2 * m || o >= cout) tf32_split(0.0f, sSh[e], sSl[e]);
+        }
+    }
+    // the (o, kx) pairs of A' a thread converts, loaded one row ahead
+    constexpr int PRE = (8 * NT * BVF_FNO_MAX_MODES + 255) / 256;
+    float2 pre[PRE];
+    auto load_pairs = [&](int r) {
+#pragma unroll
+        for (int i = 0; i < PRE; ++i) {
+            const int e = tid + i * nth;
+            if (e < cout * m) {
+                const int o = e / m, kx = e - o * m;
+                pre[i] = Ap[((long)o * rows + r) * m + kx];
+            }
+        }
+    };
+    if (spec && (int)blockIdx.x < rows) load_pairs(blockIdx.x);
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const long base = (long)row * nx;
         __syncthreads();          // the previous row is done with sS and sV
         if (spec) {
-            for (int e = tid; e < JP * PW; e += nth) {
-                const int j = e / PW, o = e - j * PW;
-                float val = 0.0f;
-                if (j < 2 * m && o < cout) {
-                    const int kx = j >> 1;
-                    const float2 a = Ap[((long)o * rows + row) * m + kx];
+            // this row's spectral rows of Y from the pairs loaded one row ahead
+#pragma unroll
+            for (int i = 0; i < PRE; ++i) {
+                const int e = tid + i * nth;
+                if (e < cout * m) {
+                    const int o = e / m, kx = e - o * m;
                     const float sc = (kx == 0 ? 1.0f : 2.0f) * invN;
-                    val = (j & 1) ? -a.y * sc : a.x * sc;
+                    tf32_split(pre[i].x * sc, sSh[(2 * kx) * PW + o], sSl[(2 * kx) * PW + o]);
+                    tf32_split(-pre[i].y * sc, sSh[(2 * kx + 1) * PW + o],
+                               sSl[(2 * kx + 1) * PW + o]);
                 }
-                tf32_split(val, sSh[e], sSl[e]);
             }
+            if (row + (int)gridDim.x < rows) load_pairs(row + gridDim.x);
         }
         __syncthreads();
         // phase 2: 16-point tiles of the row
