@@ -5,13 +5,19 @@
 //
 // The truncated FFT of a Fourier layer is done as direct DFT sums over the
 // kept modes, one axis at a time, because only m of the n frequencies of
-// each axis survive: along x a block stages 128 rows in chunks of 32 samples
-// in shared memory and each thread owns one frequency of 8 rows; the y and z
-// stages and their inverses run on the truncated spectra (a few MB,
-// L2-resident).  Twiddles come from per-grid tables e^{2 pi i f j / n}
-// computed in FP64 on the host.  The last
-// inverse (along x) is fused with the pointwise channel mix W v + b and the
-// GELU into one pass that reads v and writes the next layer's v once.
+// each axis survive.  Twiddles come from per-grid tables e^{2 pi i f j / n}
+// computed in FP64 on the host.  Per layer:
+//   - the y and z transforms, the mode mix and their inverses run on the
+//     truncated spectra (a few MB, L2-resident);
+//   - one row pass per (z, y) row does the inverse x transform, W v + b and
+//     GELU as one tensor-core product, keeps the new row in shared memory
+//     and takes the next layer's forward x transform from it, so v is read
+//     and written once per layer (k_row_mma, mma.sync TF32);
+//   - the lift is the same row pass without the spectral term.
+// The projection runs on the fifth-generation tensor cores (k_project_tc:
+// tcgen05.mma into TMEM, tcgen05.ld epilogue with GELU).  Every product uses
+// the three-term TF32 split, which keeps FP32 accuracy.  Rows too long for
+// shared memory take unfused SIMT kernels (k_lift, k_dftx, k_layer_out).
 #include <cuda_runtime.h>
 
 #include <algorithm>
