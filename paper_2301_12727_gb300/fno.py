@@ -139,3 +139,33 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+def predict_amplitude(net: Surrogate, index, table, water_row, f0, k_src, src, p0, amp_range,
+                      fdtd=None, stream=None):
+    """Amplitude field (Pa, [nz, ny, nx]) of one placement from the surrogate,
+    with the FDTD as fallback.
+
+    The features of the placement (bvf_fno_features) go through the network,
+    whose output is the amplitude divided by the bowl's surface pressure p0.
+    The prediction is kept when it is finite everywhere and its maximum lies
+    inside amp_range = (lo, hi), the focal amplitudes (in units of p0) that the
+    training data covered; otherwise `fdtd()` (a callable returning the FDTD
+    amplitude field) is called instead, and if it is None a RuntimeError is
+    raised.  Returns (amp, "surrogate" | "fdtd")."""
+    import torch
+    nz, ny, nx = index.shape
+    feats = torch.empty((N_FEATURES, nz, ny, nx), dtype=torch.float32, device=index.device)
+    bvf_fno_features(index, table, water_row, f0, k_src, src, p0, feats, stream)
+    out = net(feats, stream=stream)
+    net.synchronize(stream)
+    u = out[0]
+    ok = bool(torch.isfinite(u).all())
+    if ok:
+        mx = float(u.max())
+        ok = amp_range[0] <= mx <= amp_range[1]
+    if ok:
+        return u * float(p0), "surrogate"
+    if fdtd is None:
+        raise RuntimeError("surrogate prediction outside its trained range and no FDTD fallback")
+    return fdtd(), "fdtd"

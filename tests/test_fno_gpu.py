@@ -174,3 +174,33 @@ def test_gpu_stage_times_cover_the_inference(mods):
     assert 0.5 * total <= sum(st.values()) <= 1.05 * total
     net.timing(False)
     net.close()
+
+
+def test_gpu_prediction_falls_back_to_the_fdtd(mods):
+    """predict_amplitude keeps an in-range prediction and calls the FDTD for
+    one whose maximum leaves the trained range."""
+    torch, fno, synth = mods
+    from paper_2301_12727_gb300 import bvf
+    c = synth.slab_case(n=32, n_steps=10, n_pml=4, k_src=6)
+    dims = dict(c_in=8, width=16, modes=4, n_layers=2, hidden=16, c_out=1)
+    net = fno.Surrogate(dims, synth.fno_weights(dims, 31))
+    idx = torch.from_numpy(c.index).cuda()
+    src = torch.zeros((c.ny, c.nx, 2), dtype=torch.float32, device="cuda")
+    src[..., 0] = 1e4
+    water = synth.water_row(c.f0)
+    calls = []
+
+    def fdtd():
+        calls.append(1)
+        return torch.full(c.index.shape, 7.0, dtype=torch.float32, device="cuda")
+
+    amp, how = fno.predict_amplitude(net, idx, c.materials, water, c.f0, c.k_src, src, 1e4,
+                                     (-1e30, 1e30), fdtd)
+    assert how == "surrogate" and not calls and torch.isfinite(amp).all()
+    amp2, how2 = fno.predict_amplitude(net, idx, c.materials, water, c.f0, c.k_src, src, 1e4,
+                                       (1e29, 1e30), fdtd)
+    assert how2 == "fdtd" and calls == [1] and float(amp2.max()) == 7.0
+    with pytest.raises(RuntimeError):
+        fno.predict_amplitude(net, idx, c.materials, water, c.f0, c.k_src, src, 1e4,
+                              (1e29, 1e30), None)
+    net.close()
