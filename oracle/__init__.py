@@ -9,7 +9,9 @@ Parity status per function (pins live in tests/test_oracle_pins.py):
   material_coefs   pinned (Q(w0) and phase speed from the complex modulus)
   acoustic_run     pinned (exact discrete plane waves, energy conservation,
                    SLS relaxation vs the continuum ODE, attenuation of a point
-                   source, normal-incidence reflection, CFL, mirror symmetry)
+                   source, normal-incidence reflection, CFL, mirror symmetry;
+                   index conventions against a second, array-form FP64
+                   implementation on small random media, tests/second_oracle.py)
   rs_plane         pinned (O'Neil on-axis field of a spherical bowl)
   rs_elements      pinned (single-element magnitude; coherent sum of a steered
                    array at its target)

@@ -1,0 +1,94 @@
+"""Index conventions of the C oracle pinned against a second FP64
+implementation in array form (tests/second_oracle.py) on small grids: random
+heterogeneous media (fluid cells with mu = 0 included), random initial
+velocities, stresses and memory variables, one and two SLS mechanisms, and a
+plane burst source.  Every field agrees to 1e-12 of its largest value after a
+few steps, so a wrong neighbour, a swapped staggering, a misplaced shear cell
+or a dropped memory-variable term in either would show."""
+import numpy as np
+import pytest
+
+from tests import second_oracle as so
+
+
+def _media(rng):
+    # rho, cL, cS, alphaL, alphaS, k, c_th, perf, heat_frac
+    return np.array([[1000.0, 1500.0, 0.0, 0.0, 0.0, 0.6, 4180, 0, 0],
+                     [1900.0, 2850.0, 1450.0, 180.0, 360.0, 0.32, 1300, 0, 0.16],
+                     [1050.0, 1560.0, 0.0, 40.0, 0.0, 0.5, 3600, 0, 1],
+                     [1700.0, 2300.0, 1100.0, 120.0, 240.0, 0.4, 1500, 0, 0.16]])
+
+
+def _setup(orc, shape, L, seed):
+    rng = np.random.default_rng(seed)
+    mat = _media(rng)
+    nz, ny, nx = shape
+    index = rng.integers(0, len(mat), size=shape).astype(np.uint8)
+    dx, f0 = 0.5e-3, 5e5
+    rc, coef, ts = orc.material_coefs(mat, f0, 1.0, L)
+    assert rc == 0
+    dt = 0.3 * orc.courant_limit() * dx / 3200.0
+    A = orc.Acoustic(nx, ny, nz, dx, dt, index, mat, f0, n_sls=L, n_pml=0)
+    st = np.zeros_like(A.state)
+    st[:9 + 6 * L] = rng.standard_normal((9 + 6 * L,) + shape)
+    st[0][:, :, -1] = 0.0           # ghost half points of each axis
+    st[1][:, -1, :] = 0.0
+    st[2][-1, :, :] = 0.0
+    A.state[:] = st
+    return A, mat, index, coef, ts, dx, dt, f0, st[:9 + 6 * L].copy()
+
+
+@pytest.mark.parametrize("shape,L", [((10, 12, 14), 2), ((9, 11, 8), 1), ((20, 6, 7), 2)])
+def test_random_state_steps_agree(orc, shape, L):
+    A, mat, index, coef, ts, dx, dt, f0, s = _setup(orc, shape, L, seed=sum(shape) + L)
+    n_steps = 3
+    assert A.run(n_steps, peak_from=-1) == 0
+    for n in range(n_steps):
+        s = so.step(s, index, mat[:, 0], coef, ts, dt, dx, n)
+    for f in range(9 + 6 * L):
+        ref = A.state[f]
+        scale = max(np.abs(ref).max(), 1e-300)
+        assert np.abs(s[f] - ref).max() <= 1e-12 * scale, f
+
+
+def test_plane_burst_source_agrees(orc):
+    shape, L = (12, 10, 11), 2
+    A, mat, index, coef, ts, dx, dt, f0, _ = _setup(orc, shape, L, seed=3)
+    A.state[:] = 0.0
+    rng = np.random.default_rng(4)
+    plane = (rng.standard_normal(shape[1:]) + 1j * rng.standard_normal(shape[1:])) * 1e3
+    k_src, n_cycles = 4, 2
+    A.set_source(plane, k_src, 1500.0, orc.ENV_BURST, n_cycles)
+    n_steps = 6
+    assert A.run(n_steps, peak_from=-1) == 0
+    s = np.zeros((9 + 6 * L,) + shape)
+
+    def env(t):
+        return 1.0 if 0.0 <= t < n_cycles / f0 else 0.0
+
+    for n in range(n_steps):
+        s = so.step(s, index, mat[:, 0], coef, ts, dt, dx, n, src=plane, k_src=k_src,
+                    c0=1500.0, f0=f0, env=env)
+    for f in range(9 + 6 * L):
+        ref = A.state[f]
+        scale = max(np.abs(ref).max(), 1e-300)
+        assert np.abs(s[f] - ref).max() <= 1e-12 * scale, f
+    assert np.abs(A.state[3]).max() > 0.0
+
+
+def test_second_oracle_catches_a_shifted_stencil(orc):
+    """The comparison is sharp: the same step with D- taken at s+1/2 instead
+    of s (a one-cell staggering slip) differs from the C oracle by O(1)."""
+    shape, L = (8, 9, 10), 1
+    A, mat, index, coef, ts, dx, dt, f0, s = _setup(orc, shape, L, seed=9)
+    assert A.run(1, peak_from=-1) == 0
+    good = so.step(s, index, mat[:, 0], coef, ts, dt, dx, 0)
+    orig = so.d_minus
+    try:
+        so.d_minus = lambda f, axis, h: so.d_plus(f, axis, h)
+        bad = so.step(s, index, mat[:, 0], coef, ts, dt, dx, 0)
+    finally:
+        so.d_minus = orig
+    ref = A.state[3]
+    assert np.abs(good[3] - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.abs(bad[3] - ref).max() > 1e-3 * np.abs(ref).max()
