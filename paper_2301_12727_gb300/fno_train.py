@@ -193,7 +193,11 @@ def main(argv=None):
             rows.append(focal_metrics(out, yte[i], args.dx))
     net.close()
     rows = np.array(rows)
+    # focal amplitudes (units of p0) the training set covers: the range that
+    # fno.predict_amplitude accepts before it falls back to the FDTD
+    tmax = ytr.flatten(1).max(dim=1).values
     res = {"grid": list(grid), "dx_m": args.dx, "f0_hz": args.f0, "dims": d,
+           "train_focal_range_p0": [float(tmax.min()), float(tmax.max())],
            "train_cases": args.train, "test_cases": args.test, "epochs": args.epochs,
            "data_s": t_data, "train_s": t_train, "train_loss_first_last": [hist[0], hist[-1]],
            "test_rel_l2_median": float(np.median(rows[:, 0])),
