@@ -13,8 +13,14 @@ It is written from the scheme's definition, not from the C loops:
 * Crank-Nicolson memory variables;
 * the soft stress source at (n + 1/2) dt.
 
-CPML is left out (n_pml = 0). The per-material relaxed moduli and tau come
-from the oracle's fit, which is pinned separately (Q and phase speed).
+With `cpml` given, each derivative normal to an absorbing slab is replaced
+by df + psi, psi <- b psi + a df. (a, b) are the Komatitsch-Martin profile
+(kappa = 1, d = d0 xi^2, alpha = pi f0 (1 - xi)), taken at the integer point
+for a D- derivative and at the half point for a D+ one.  The 18 psi arrays
+follow the state's ordering: (vx, vy, vz) x (x, y, z); the normal strains;
+then the shear pairs xy (y, x), xz (z, x), yz (z, y).  The per-material
+relaxed moduli and tau come from the oracle's fit, which is pinned separately
+(Q and phase speed).
 """
 from __future__ import annotations
 
@@ -77,25 +83,69 @@ def _below_last(shape, axis):
     return m
 
 
+def cpml_profile(n, P, h, dt, f0, R, cmax, half):
+    """(a, b) along an axis of n points at the integer (half=False) or half
+    points; zero outside the two slabs of P cells."""
+    pos2 = 2.0 * np.arange(n) + (1.0 if half else 0.0)
+    xi = np.maximum((2.0 * P - pos2) / (2.0 * P), (pos2 - 2.0 * (n - 1 - P)) / (2.0 * P))
+    inside = xi > 0.0
+    xi = np.clip(xi, 0.0, 1.0)
+    d = (-3.0 * cmax * np.log(R) / (2.0 * P * h)) * xi * xi
+    al = np.pi * f0 * (1.0 - xi)
+    b = np.where(inside, np.exp(-(d + al) * dt), 0.0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        a = np.where(inside & (d + al > 0.0), d * (b - 1.0) / (d + al), 0.0)
+    return a, b
+
+
 def step(state, index, rho, coef, ts, dt, h, n, src=None, k_src=0, c0=1500.0, f0=5e5,
-         env=None):
-    """Advance state [9 + 6L][nz][ny][nx] by one step n -> n+1 (new array)."""
+         env=None, cpml=None):
+    """Advance state [9 + 6L (+18 psi)][nz][ny][nx] by one step n -> n+1 (new
+    array).  cpml: dict (P, R, cmax) for absorbing slabs of P cells."""
     st = state.copy()
     L = len(ts)
     shape = index.shape
+    prof = {}
+    if cpml is not None:
+        for axis in range(3):
+            for half in (False, True):
+                a, b = cpml_profile(shape[axis], cpml["P"], h, dt, f0, cpml["R"], cpml["cmax"], half)
+                bshape = [1, 1, 1]
+                bshape[axis] = shape[axis]
+                prof[(axis, half)] = (a.reshape(bshape), b.reshape(bshape))
+
+    def absorb(df, q, axis, half, mask=None):
+        """df + psi with psi_q updated where the slab coefficients are non-zero."""
+        if cpml is None:
+            return df
+        a, b = prof[(axis, half)]
+        a, b = np.broadcast_to(a, shape), np.broadcast_to(b, shape)
+        psi = st[9 + 6 * L + q]
+        active = (a != 0.0) | (b != 0.0)
+        if mask is not None:
+            active = active & mask
+        new = b * psi + a * df
+        psi[active] = new[active]
+        return np.where(active, df + new, df)
     vx, vy, vz = st[0], st[1], st[2]
     sxx, syy, szz, sxy, sxz, syz = st[3], st[4], st[5], st[6], st[7], st[8]
     r = st[9:9 + 6 * L].reshape(L, 6, *shape)
     rv = rho[index]
     piR, muR, tP, tS = (coef[:, c][index] for c in range(4))
 
-    # velocities (faces s + 1/2; the last face of each axis is a ghost)
-    for comp, axis, terms in ((vx, 2, (d_plus(sxx, 2, h), d_minus(sxy, 1, h), d_minus(sxz, 0, h))),
-                              (vy, 1, (d_minus(sxy, 2, h), d_plus(syy, 1, h), d_minus(syz, 0, h))),
-                              (vz, 0, (d_minus(sxz, 2, h), d_minus(syz, 1, h), d_plus(szz, 0, h)))):
-        b = 2.0 / (rv + _next(rv, axis))
-        upd = comp + dt * b * ((terms[0] + terms[1]) + terms[2])
+    # velocities (faces s + 1/2; the last face of each axis is a ghost).  Each
+    # term: (derivative, psi slot, axis, taken at the half point)
+    for comp, axis, q0, terms in (
+            (vx, 2, 0, ((d_plus(sxx, 2, h), 2, True), (d_minus(sxy, 1, h), 1, False),
+                        (d_minus(sxz, 0, h), 0, False))),
+            (vy, 1, 3, ((d_minus(sxy, 2, h), 2, False), (d_plus(syy, 1, h), 1, True),
+                        (d_minus(syz, 0, h), 0, False))),
+            (vz, 0, 6, ((d_minus(sxz, 2, h), 2, False), (d_minus(syz, 1, h), 1, False),
+                        (d_plus(szz, 0, h), 0, True)))):
         m = _below_last(shape, axis)
+        t = [absorb(df, q0 + i, ax, half, m) for i, (df, ax, half) in enumerate(terms)]
+        b = 2.0 / (rv + _next(rv, axis))
+        upd = comp + dt * b * ((t[0] + t[1]) + t[2])
         comp[m] = upd[m]
 
     hh = dt / (2.0 * np.asarray(ts))
@@ -111,7 +161,8 @@ def step(state, index, rho, coef, ts, dt, h, n, src=None, k_src=0, c0=1500.0, f0
         return total
 
     # normal stresses at the cell centres
-    e = (d_minus(vx, 2, h), d_minus(vy, 1, h), d_minus(vz, 0, h))
+    e = (absorb(d_minus(vx, 2, h), 9, 2, False), absorb(d_minus(vy, 1, h), 10, 1, False),
+         absorb(d_minus(vz, 0, h), 11, 0, False))
     th = (e[0] + e[1]) + e[2]
     for c, sig in enumerate((sxx, syy, szz)):
         dev = th - e[c]
@@ -120,9 +171,19 @@ def step(state, index, rho, coef, ts, dt, h, n, src=None, k_src=0, c0=1500.0, f0
         sig += dt * (Psi + 0.5 * relax(c, The))
 
     # shear stresses on the edges: (component, first axis, second axis, strain)
-    for c, sig, a1, a2, ev in ((3, sxy, 2, 1, d_plus(vx, 1, h) + d_plus(vy, 2, h)),
-                               (4, sxz, 2, 0, d_plus(vx, 0, h) + d_plus(vz, 2, h)),
-                               (5, syz, 1, 0, d_plus(vy, 0, h) + d_plus(vz, 1, h))):
+    def shear_strain(c, a1, a2):
+        m = _below_last(shape, a1) & _below_last(shape, a2)
+        if c == 3:
+            return (absorb(d_plus(vx, 1, h), 12, 1, True, m) +
+                    absorb(d_plus(vy, 2, h), 13, 2, True, m))
+        if c == 4:
+            return (absorb(d_plus(vx, 0, h), 14, 0, True, m) +
+                    absorb(d_plus(vz, 2, h), 15, 2, True, m))
+        return (absorb(d_plus(vy, 0, h), 16, 0, True, m) +
+                absorb(d_plus(vz, 1, h), 17, 1, True, m))
+
+    for c, sig, a1, a2 in ((3, sxy, 2, 1), (4, sxz, 2, 0), (5, syz, 1, 0)):
+        ev = shear_strain(c, a1, a2)
         u00, t00 = muR, tS
         u10, t10 = _next(muR, a1), _next(tS, a1)
         u01, t01 = _next(muR, a2), _next(tS, a2)
