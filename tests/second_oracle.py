@@ -209,3 +209,38 @@ def step(state, index, rho, coef, ts, dt, h, n, src=None, k_src=0, c0=1500.0, f0
         for sig in (sxx, syy, szz):
             sig[k_src] -= (2.0 * c0 * dt / h) * sv
     return st
+
+
+def bhte_run(T0, index, mat, h, amp, p_scale, dt, n_on, n_off, duty, T_a=37.0,
+             rhob_cb=1050.0 * 3617.0):
+    """Pennes BHTE in array form (Sec. 2.4): forward Euler, 7-point stencil
+    with the harmonic-mean face conductivity, borders held at T_a, perfusion,
+    the duty-cycled source during the first n_on steps, then T_max and CEM43
+    (R = 0.5 at T >= 43, else 0.25) after every step.  Returns (T, Tmax, cem)."""
+    rho, cL, aL = mat[:, 0][index], mat[:, 1][index], mat[:, 3][index]
+    k, cth, perf, heat = (mat[:, c][index] for c in (5, 6, 7, 8))
+    Q = heat * aL * (p_scale * amp) ** 2 / (rho * cL)
+    border = np.zeros(index.shape, dtype=bool)
+    border[0], border[-1] = True, True
+    border[:, 0], border[:, -1] = True, True
+    border[:, :, 0], border[:, :, -1] = True, True
+    T = T0.copy()
+    Tmax, cem = T.copy(), np.zeros(index.shape)
+    inv_h2 = 1.0 / (h * h)
+    for n in range(n_on + n_off):
+        dc = duty if n < n_on else 0.0
+        lap = np.zeros(index.shape)
+        # faces in the order -x, +x, -y, +y, -z, +z (np.roll wraps only at the
+        # borders, which are overwritten below)
+        for axis, shift in ((2, 1), (2, -1), (1, 1), (1, -1), (0, 1), (0, -1)):
+            kn = np.roll(k, shift, axis=axis)
+            Tn_b = np.roll(T, shift, axis=axis)
+            lap = lap + (2.0 * k * kn / (k + kn)) * (Tn_b - T)
+        rhs = lap * inv_h2 - perf * rhob_cb * (T - T_a) + dc * Q
+        Tn = T + dt * rhs / (rho * cth)
+        Tn[border] = T_a
+        T = Tn
+        Tmax = np.maximum(Tmax, T)
+        R = np.where(T >= 43.0, 0.5, 0.25)
+        cem = cem + dt / 60.0 * np.power(R, 43.0 - T)
+    return T, Tmax, cem

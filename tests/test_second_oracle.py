@@ -123,3 +123,26 @@ def test_cpml_slabs_agree(orc, shape, L, P):
         ref = A.state[f]
         scale = max(np.abs(ref).max(), 1e-300)
         assert np.abs(s[f] - ref).max() <= 1e-12 * scale, f
+
+
+def test_bhte_array_form_agrees(orc):
+    """The C oracle's BHTE against the array-form step on random heterogeneous
+    tissue, a random acoustic field and a starting temperature spread over
+    37 .. 46 C (both CEM43 bases): T, T_max and CEM43 to 1e-12."""
+    rng = np.random.default_rng(17)
+    # rho, cL, cS, alphaL, alphaS, k, c_th, perf, heat_frac
+    mat = np.array([[1000.0, 1500.0, 0.0, 0.0, 0.0, 0.6, 4180.0, 0.0, 1.0],
+                    [1041.0, 1562.0, 0.0, 35.0, 0.0, 0.51, 3630.0, 0.008, 1.0],
+                    [1850.0, 2800.0, 1500.0, 85.0, 170.0, 0.32, 1300.0, 0.0005, 0.16],
+                    [1116.0, 1537.0, 0.0, 23.0, 0.0, 0.37, 3390.0, 0.002, 1.0]])
+    shape = (10, 12, 14)
+    index = rng.integers(0, len(mat), size=shape).astype(np.uint8)
+    amp = rng.uniform(0.0, 2e6, size=shape)
+    T0 = rng.uniform(37.0, 46.0, size=shape)
+    dx, dt = 0.5e-3, 0.02
+    rc, T, Tmax, cem = orc.bhte_run(index, mat, dx, amp, 1.0, dt, 5, 3, 0.3, T_init=T0)
+    assert rc == 0
+    T2, Tmax2, cem2 = so.bhte_run(T0, index, mat, dx, amp, 1.0, dt, 5, 3, 0.3)
+    for a, b in ((T2, T), (Tmax2, Tmax), (cem2, cem)):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert (cem > 0).all() and np.abs(T - T0).max() > 1e-3
