@@ -146,3 +146,28 @@ def test_bhte_array_form_agrees(orc):
     for a, b in ((T2, T), (Tmax2, Tmax), (cem2, cem)):
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
     assert (cem > 0).all() and np.abs(T - T0).max() > 1e-3
+
+
+def test_capture_array_form_agrees(orc):
+    """Peak and FP64 DFT capture: after each step n -> n+1 the pressure
+    p = -(sxx + syy + szz)/3 enters max |p| and C += p cos(w t), S += p sin(w t)
+    at t = (n+1) dt; the C oracle's maps equal the array-form sums to 1e-12."""
+    shape, L = (9, 10, 11), 2
+    A, mat, index, coef, ts, dx, dt, f0, s = _setup(orc, shape, L, seed=23)
+    n_steps, dft_start = 6, 3
+    assert A.run(n_steps, peak_from=2, dft_start=dft_start, dft_steps=n_steps) == 0
+    peak = np.zeros(shape)
+    C, S = np.zeros(shape), np.zeros(shape)
+    w = 2.0 * np.pi * f0
+    for n in range(n_steps):
+        s = so.step(s, index, mat[:, 0], coef, ts, dt, dx, n)
+        stp = n + 1
+        p = -(s[3] + s[4] + s[5]) / 3.0
+        if stp >= 2:
+            peak = np.maximum(peak, np.abs(p))
+        if stp >= dft_start:
+            C += p * np.cos(w * stp * dt)
+            S += p * np.sin(w * stp * dt)
+    for a, b in ((peak, A.peak), (C, A.dftC), (S, A.dftS)):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    assert np.abs(A.dftS).max() > 0.0
