@@ -175,7 +175,8 @@ __device__ __forceinline__ float2 cmul_tw(float2 a, float2 t, float s)
 
 // ------------------------------------------------------ forward DFT along y
 // B[c][z][jy][kx] = sum_y A[c][z][y][kx] e^{-2 pi i f(jy) y / ny}; one block
-// per (c, z) slab, one thread per (jy, kx).
+// per (c, z) slab; each thread takes the mode slots jy and jy + m of one kx
+// (the same A column against two twiddle rows).
 __global__ void k_dfty(const float2 *__restrict__ A, int ny, int m,
                        const float2 *__restrict__ ty, float2 *__restrict__ B)
 {
@@ -186,28 +187,34 @@ __global__ void k_dfty(const float2 *__restrict__ A, int ny, int m,
     for (int e = threadIdx.x; e < ny * m; e += blockDim.x) s_a[e] = a[e];
     __syncthreads();
     const int t = threadIdx.x;
-    if (t >= 2 * m * m) return;
-    const int jy = t / m, kx = t - jy * m;
-    const float2 *tw = ty + (long)jy * ny;
-    // four independent partial sums (y mod 4) for instruction-level parallelism
-    float2 acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    if (t >= m * m) return;
+    const int jy = t / m, kx = t - jy * m;           // jy in [0, m); the pair is jy + m
+    const float2 *tw0 = ty + (long)jy * ny, *tw1 = ty + (long)(jy + m) * ny;
+    float2 a0[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, a1[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
     int y = 0;
-    for (; y + 4 <= ny; y += 4) {
+    for (; y + 2 <= ny; y += 2) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float2 p = cmul_tw(s_a[(y + q) * m + kx], __ldg(tw + y + q), -1.0f);
-            acc[q].x += p.x;
-            acc[q].y += p.y;
+        for (int q = 0; q < 2; ++q) {
+            const float2 v = s_a[(y + q) * m + kx];
+            const float2 p0 = cmul_tw(v, __ldg(tw0 + y + q), -1.0f);
+            const float2 p1 = cmul_tw(v, __ldg(tw1 + y + q), -1.0f);
+            a0[q].x += p0.x;
+            a0[q].y += p0.y;
+            a1[q].x += p1.x;
+            a1[q].y += p1.y;
         }
     }
     for (; y < ny; ++y) {
-        const float2 p = cmul_tw(s_a[y * m + kx], __ldg(tw + y), -1.0f);
-        acc[0].x += p.x;
-        acc[0].y += p.y;
+        const float2 v = s_a[y * m + kx];
+        const float2 p0 = cmul_tw(v, __ldg(tw0 + y), -1.0f);
+        const float2 p1 = cmul_tw(v, __ldg(tw1 + y), -1.0f);
+        a0[0].x += p0.x;
+        a0[0].y += p0.y;
+        a1[0].x += p1.x;
+        a1[0].y += p1.y;
     }
-    B[(slab * 2 * m + jy) * m + kx] =
-        make_float2((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x),
-                    (acc[0].y + acc[1].y) + (acc[2].y + acc[3].y));
+    B[(slab * 2 * m + jy) * m + kx] = make_float2(a0[0].x + a0[1].x, a0[0].y + a0[1].y);
+    B[(slab * 2 * m + jy + m) * m + kx] = make_float2(a1[0].x + a1[1].x, a1[0].y + a1[1].y);
 }
 
 // ------------------------------------------------------ forward DFT along z
@@ -288,15 +295,24 @@ __global__ void k_idfty(const float2 *__restrict__ Bp, int ny, int m,
     for (int e = threadIdx.x; e < M2; e += blockDim.x) s_b[e] = Bp[slab * M2 + e];
     __syncthreads();
     float2 *out = Ap + slab * ny * m;
-    for (int e = threadIdx.x; e < ny * m; e += blockDim.x) {
-        const int y = e / m, kx = e - y * m;
-        float2 acc = make_float2(0.0f, 0.0f);
+    // two y per thread (y0, y0 + 1) share each spectral value
+    const int npairs = (ny + 1) / 2;
+    for (int e = threadIdx.x; e < npairs * m; e += blockDim.x) {
+        const int yp = e / m, kx = e - yp * m;
+        const int y0 = 2 * yp, y1 = y0 + 1 < ny ? y0 + 1 : y0;
+        float2 acc0 = make_float2(0.0f, 0.0f), acc1 = make_float2(0.0f, 0.0f);
         for (int jy = 0; jy < 2 * m; ++jy) {
-            const float2 p = cmul_tw(s_b[jy * m + kx], __ldg(ty + (long)jy * ny + y), 1.0f);
-            acc.x += p.x;
-            acc.y += p.y;
+            const float2 b = s_b[jy * m + kx];
+            const float2 *tw = ty + (long)jy * ny;
+            const float2 p0 = cmul_tw(b, __ldg(tw + y0), 1.0f);
+            const float2 p1 = cmul_tw(b, __ldg(tw + y1), 1.0f);
+            acc0.x += p0.x;
+            acc0.y += p0.y;
+            acc1.x += p1.x;
+            acc1.y += p1.y;
         }
-        out[e] = acc;
+        out[y0 * m + kx] = acc0;
+        if (y0 + 1 < ny) out[(y0 + 1) * m + kx] = acc1;
     }
 }
 
@@ -1182,7 +1198,7 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
             FCK(cudaGetLastError(), "bvf_fno_forward: dftx");
         }
         FCK(mark(1), "event");
-        k_dfty<<<W * nz, std::max(32, 2 * m * m), sy, s>>>(f->A, ny, m, ty, f->B);
+        k_dfty<<<W * nz, std::max(32, ((m * m + 31) / 32) * 32), sy, s>>>(f->A, ny, m, ty, f->B);
         FCK(cudaGetLastError(), "bvf_fno_forward: dfty");
         FCK(mark(2), "event");
         const long nh = (long)W * 2 * m * M2;
