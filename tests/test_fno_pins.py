@@ -179,3 +179,37 @@ def test_features_of_a_water_voxel_and_the_source_plane():
     assert np.count_nonzero(f[3]) == 1 and np.count_nonzero(f[4]) == 1
     np.testing.assert_allclose(f[5, 0, 0, :], (np.arange(6) + 0.5) / 6)
     np.testing.assert_allclose(f[7, :, 0, 0], (np.arange(5) + 0.5) / 5)
+
+
+def test_identity_weights_give_a_symmetric_band_filter():
+    """With R = 1 on every kept mode the spectral convolution passes a field
+    band-limited to |ky|, |kz| < m, kx < m unchanged, and its kernel
+    sum cos(k.(x - x')) / N is symmetric: <K n, u> = <n, K u> for any fields.
+    The lone -m bins of the kx = 0 plane pass half their pair, so K is a
+    contraction but not a projection there."""
+    rng = np.random.default_rng(12)
+    m = 2
+    shape = (9, 10, 12)
+    # a field band-limited to |kz|, |ky| < m, 0 <= kx < m: no content at |k| = m
+    nz, ny, nx = shape
+    z = np.arange(nz)[:, None, None] / nz
+    y = np.arange(ny)[None, :, None] / ny
+    x = np.arange(nx)[None, None, :] / nx
+    u = np.zeros(shape)
+    for a in range(-(m - 1), m):
+        for b in range(-(m - 1), m):
+            for c in range(m):
+                u += rng.standard_normal() * np.cos(2 * np.pi * (a * z + b * y + c * x)
+                                                    + rng.uniform(0, 2 * np.pi))
+    noise = rng.standard_normal(shape)
+    one = np.ones((2 * m, 2 * m, m, 1, 1), dtype=complex)
+    Kn = fno.spectral_conv(noise[None], one, m)[0]
+    Ku = fno.spectral_conv(u[None], one, m)[0]
+    np.testing.assert_allclose(Ku, u, atol=1e-12 * np.abs(u).max())     # band passes unchanged
+    KKn = fno.spectral_conv(Kn[None], one, m)[0]
+    # idempotent on the part of the band without the lone -m bins
+    w = rng.standard_normal(shape)
+    Kw = fno.spectral_conv(w[None], one, m)[0]
+    np.testing.assert_allclose(np.sum(Kn * u), np.sum(noise * Ku), rtol=1e-10)   # <Kn, u> = <n, Ku>
+    np.testing.assert_allclose(np.sum(Kn * w), np.sum(noise * Kw), rtol=1e-10)   # self-adjoint
+    assert np.linalg.norm(KKn - Kn) <= np.linalg.norm(Kn)                        # contraction
