@@ -54,3 +54,30 @@ def test_peak_from_measured_file_or_fallback(monkeypatch, tmp_path):
 def test_whole_job_rate_counts_every_rank():
     # two ranks, 5 steps of 1e9 voxel-steps each, 1000 ms (max over ranks)
     assert bench.whole_job_rate(2, 5, 1e9, 1000.0) == pytest.approx(10.0)
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_reports_median_clock_and_active_reasons():
+    cs = bench.ClockSampler(0)
+    cs.proc = _FakeProc()
+    cs.out.write("0, 2070, 2070, 850.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "0, 1980, 2070, 1399.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                 "0, 2070, 2070, 900.2, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                 "garbage line\n")
+    res = cs.stop()
+    assert res == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+
+
+def test_clock_sampler_without_nvidia_smi_returns_none():
+    cs = bench.ClockSampler(0)
+    cs.proc = None
+    assert cs.stop() is None
+    os.unlink(cs.out.name)
