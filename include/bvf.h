@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define BVF_VERSION 2
+#define BVF_VERSION 3
 
 #define BVF_OK 0
 #define BVF_E_ARG (-1)        /* NULL pointer, bad size, bad option, call order */
@@ -54,6 +54,7 @@ extern "C" {
 #define BVF_E_NOMEM (-4)      /* device allocation failed                        */
 #define BVF_E_CUDA (-5)       /* a CUDA runtime call failed                      */
 #define BVF_E_UNSTABLE (-6)   /* a non-finite pressure was detected              */
+#define BVF_E_TIMEOUT (-7)    /* the call's wall-clock budget was spent          */
 
 #define BVF_ENV_NONE 0        /* no source                                       */
 #define BVF_ENV_BURST 1       /* rectangular burst of n_cycles                   */
@@ -233,12 +234,61 @@ int bvf_reset(bvf_ctx *ctx, void *stream);
 /* Advance n_steps acoustic steps (velocity, then stress + memory variables +
  * source + capture per step) on `stream`.  Requires bvf_set_materials.  The
  * capture window (NULL = none) refers to the context's absolute step count.
- * Non-finite pressure sets a device flag reported by bvf_synchronize. */
+ * Non-finite pressure sets a device flag reported by bvf_synchronize.  With a
+ * time budget (bvf_set_time_budget) the call may return BVF_E_TIMEOUT after
+ * fewer steps, having waited for them (bvf_get_stats gives the count). */
 int bvf_run_acoustic(bvf_ctx *ctx, int n_steps, const bvf_capture *cap, void *stream);
 
+/* Wall-clock budget (seconds, 0 = none, the default) of each later
+ * bvf_run_acoustic and bvf_run_thermal call on this context: failure
+ * detection for planning services, which must not wait without bound on one
+ * plan (the paper's pipeline runs each step to completion).  Every 32 steps
+ * the call compares the time since it began with the budget, keeping at most
+ * two such chunks queued ahead of the host; once the budget is spent it waits
+ * for the queued steps and returns BVF_E_TIMEOUT.  The context then holds the
+ * state after every step that ran (consistent and resumable: a later call
+ * continues from it).  Work already on the GPU is never cancelled, so a call
+ * can overrun its budget by up to two chunks of steps. */
+int bvf_set_time_budget(bvf_ctx *ctx, double seconds);
+
 /* Wait for `stream` and report: BVF_E_UNSTABLE if a non-finite pressure was
- * seen since the last reset, BVF_E_CUDA on an asynchronous CUDA error. */
+ * seen since the last reset; BVF_E_CUDA on an asynchronous CUDA error, or when
+ * a TMA copy of an acoustic kernel did not complete within its wait bound
+ * (the blocks concerned stop after draining the copies they issued; their
+ * results are incomplete, the context stays usable, and bvf_reset clears the
+ * report). */
 int bvf_synchronize(bvf_ctx *ctx, void *stream);
+
+/* Size in bytes of a snapshot of the context's acoustic state. */
+int bvf_state_bytes(const bvf_ctx *ctx, size_t *out);
+
+/* Snapshot of everything an acoustic run continues from: the velocities,
+ * stresses and memory variables, the CPML memories, the peak map, the FP64 DFT
+ * sums, the step counter, the number of captured DFT steps and the
+ * non-finite / time-out flag (checkpoint and resume of a long run; the paper
+ * runs each simulation in one go).  Not included: materials, source and
+ * capture settings, which the caller sets again before loading.  d_buf: device
+ * memory of at least bvf_state_bytes bytes, caller-owned; the layout is a
+ * 256-byte header (library version, grid, time step, frequency, SLS count,
+ * storage, counters) then the arrays.  bvf_state_save is stream-ordered and
+ * asynchronous.  bvf_state_load first waits for `stream` to read the header,
+ * rejects (BVF_E_ARG) a snapshot of another library version, grid, time step,
+ * frequency, SLS count or storage, then enqueues the copies; a run continued
+ * from a loaded snapshot equals the uninterrupted run bit for bit. */
+int bvf_state_save(bvf_ctx *ctx, void *d_buf, size_t bytes, void *stream);
+int bvf_state_load(bvf_ctx *ctx, const void *d_buf, size_t bytes, void *stream);
+
+/* Test hook of the bounded TMA waits (the paper has no counterpart).  Arms the
+ * next acoustic step so that `kernel` (1 = velocity, 2 = stress) of the
+ * TMA-fed pair arms the mbarrier of the look-ahead copies it would issue at
+ * plane `plane` of its z-chunk but issues none of them; the waits for that
+ * data then run out after wait_limit polls (0: the library's bound of 2^22).
+ * The blocks concerned stop after draining every copy they did issue, so no
+ * copy is left in flight, and bvf_synchronize reports BVF_E_CUDA; after
+ * bvf_reset the context runs normally.  kernel = 0 disarms.  BVF_E_ARG if the
+ * context does not use that TMA-fed kernel (nx % 16 != 0 or more than 2 SLS
+ * mechanisms) or the plane is outside the grid. */
+int bvf_test_withhold_copy(bvf_ctx *ctx, int kernel, int plane, unsigned wait_limit);
 
 /* Copy one state array (BVF_FIELD_* id, nx*ny*nz floats) out of / into the
  * context.  Used to start from a prescribed state and to inspect every field. */
@@ -291,10 +341,10 @@ int bvf_transmission(int nx, int ny, int nz,
  * results and errors as bvf_transmission; each table may hold at most
  * BVF_MAX_MATERIALS rows (BVF_E_ARG beyond that).  Its temporaries live in one
  * fixed array of about 4 KiB inside the library, present on every GPU that
- * loads it until the process exits; the first call on a device looks up that
- * array's address, so make it before any stream capture.  All calls share the
- * array: calls that overlap on the GPU (e.g. unordered streams) race.
- * Synchronous: waits for `stream`. */
+ * loads it until the process exits; each call looks up that array's address
+ * on the current device.  All calls share the array: calls that overlap on
+ * the GPU (e.g. unordered streams) race.  Synchronous: copies the tables from
+ * host memory and waits for `stream` before returning. */
 int bvf_transmission_noalloc(int nx, int ny, int nz,
                              const uint8_t *d_idx_a, const bvf_material *h_mat_a, int n_a,
                              const double *d_amp_a,
@@ -324,6 +374,33 @@ int bvf_get_kernel_times(bvf_ctx *ctx, bvf_kernel_times *out);
  * Context-free; asynchronous on `stream` (the elements are copied first). */
 int bvf_rs_elements(const double *h_elem, int ne, double p0, double c0, int nx, int ny,
                     double dx, double z_plane, double f0, float *d_out, void *stream);
+
+/* Elements of a spherical cap for bvf_rs_elements: aperture, radius of
+ * curvature, apex and axis from `bowl` (its other fields are unused); ring r
+ * of n_rings rings of equal polar-angle width holds n_inner (r + 1) equal
+ * elements, each carrying the area of its patch of the cap, weight 1 + 0i.
+ * h_elem: NULL to count only, else room for the count (rows of six doubles as
+ * in bvf_rs_elements); *n_out receives the count.  Host only, synchronous. */
+int bvf_bowl_array(const bvf_bowl *bowl, int n_rings, int n_inner, double *h_elem, int *n_out);
+
+/* Steering weights (geometric focusing of a phased array on a target, in a
+ * medium of speed c0): w_e = exp(+i k r_e), k = 2 pi f0 / c0, r_e the distance
+ * from element e to `target` (three doubles, metres), written into columns 4
+ * and 5 of the ne rows of h_elem, so every element's wave reaches the target
+ * in phase.  Host only, synchronous. */
+int bvf_steer_weights(double *h_elem, int ne, const double *target, double f0, double c0);
+
+/* Time-reversal (phase-conjugation) source plane through the context's medium
+ * (aberration correction for transcranial focusing, Sec. 2.3 source plane): a
+ * CW point source (one-cycle ramp) of unit amplitude at voxel (ti, tj, tk)
+ * runs n_steps steps; the FP64 complex amplitude P it leaves on plane k_src
+ * over the last two periods is captured, and conj(P) / max|P| is written to
+ * d_plane (nx*ny complex values as interleaved float pairs, caller-owned
+ * device memory), ready for bvf_set_source.  The context's state and capture
+ * are reset before and after, and its source is cleared.  Needs n_steps > two
+ * periods.  Synchronous: waits for `stream`. */
+int bvf_time_reversal_plane(bvf_ctx *ctx, int ti, int tj, int tk, int k_src, int n_steps,
+                            double c0, float *d_plane, void *stream);
 
 /* ---- one placement end to end --------------------------------------------
  * The paper's transcranial and thermal steps for one transducer placement

@@ -668,6 +668,8 @@ int orc_bhte_run(int nx, int ny, int nz, double dx, const uint8_t *index, const 
                     Tn[q] = T[q] + dt * rhs / (m[M_RHO] * m[M_CTH]);
                 }
         memcpy(T, Tn, sizeof(double) * N);
+        /* independent per voxel: the same arithmetic in any thread order */
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < N; ++q) {
             if (T[q] > Tmax[q]) Tmax[q] = T[q];
             double R = (T[q] >= 43.0) ? 0.5 : 0.25;

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbvf.so")
 
 BVF_OK, BVF_E_ARG, BVF_E_CFL, BVF_E_MATERIAL = 0, -1, -2, -3
-BVF_E_NOMEM, BVF_E_CUDA, BVF_E_UNSTABLE = -4, -5, -6
+BVF_E_NOMEM, BVF_E_CUDA, BVF_E_UNSTABLE, BVF_E_TIMEOUT = -4, -5, -6, -7
 BVF_ENV_NONE, BVF_ENV_BURST, BVF_ENV_RAMP_CW = 0, 1, 2
 FIELDS = ("vx", "vy", "vz", "sxx", "syy", "szz", "sxy", "sxz", "syz")
 EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bvf_destroy",
@@ -29,7 +29,9 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_transmission", "bvf_get_stats", "bvf_kernel_timing", "bvf_get_kernel_times",
            "bvf_transmission_noalloc", "bvf_batch_create", "bvf_batch_destroy", "bvf_batch_run",
            "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams", "bvf_plan",
-           "bvf_rs_elements")
+           "bvf_rs_elements", "bvf_set_time_budget", "bvf_state_bytes", "bvf_state_save",
+           "bvf_state_load", "bvf_test_withhold_copy", "bvf_bowl_array", "bvf_steer_weights",
+           "bvf_time_reversal_plane")
 
 
 class BvfError(RuntimeError):
@@ -149,6 +151,14 @@ def lib():
         L.bvf_plan.argtypes = [vp, vp, vp, ctypes.POINTER(Material), i, ctypes.POINTER(Material),
                                ctypes.POINTER(Bowl), i, ctypes.POINTER(PlanParams), vp, vp, vp, vp,
                                vp, ctypes.POINTER(PlanOut), vp]
+        L.bvf_set_time_budget.argtypes = [vp, d]
+        L.bvf_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.bvf_state_save.argtypes = [vp, vp, ctypes.c_size_t, vp]
+        L.bvf_state_load.argtypes = [vp, vp, ctypes.c_size_t, vp]
+        L.bvf_test_withhold_copy.argtypes = [vp, i, i, ctypes.c_uint]
+        L.bvf_bowl_array.argtypes = [ctypes.POINTER(Bowl), i, i, vp, ctypes.POINTER(i)]
+        L.bvf_steer_weights.argtypes = [vp, i, vp, d, d]
+        L.bvf_time_reversal_plane.argtypes = [vp, i, i, i, i, i, d, vp, vp]
         _lib = L
     return _lib
 
@@ -314,6 +324,56 @@ def bvf_get_kernel_times(ctx) -> KernelTimes:
     return t
 
 
+def bvf_set_time_budget(ctx, seconds):
+    _check(lib().bvf_set_time_budget(ctx, float(seconds)), ctx)
+
+
+def bvf_state_bytes(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().bvf_state_bytes(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def bvf_state_save(ctx, buf, stream=None):
+    import torch
+    _check(lib().bvf_state_save(ctx, _ptr(buf, torch.uint8), buf.numel(), _stream(stream)), ctx)
+
+
+def bvf_state_load(ctx, buf, stream=None):
+    import torch
+    _check(lib().bvf_state_load(ctx, _ptr(buf, torch.uint8), buf.numel(), _stream(stream)), ctx)
+
+
+def bvf_test_withhold_copy(ctx, kernel, plane, wait_limit=0):
+    _check(lib().bvf_test_withhold_copy(ctx, kernel, plane, wait_limit), ctx)
+
+
+def bvf_bowl_array(bowl: Bowl, n_rings, n_inner) -> np.ndarray:
+    """Rows (x, y, z, area, 1, 0) of a spherical cap's elements."""
+    n = ctypes.c_int()
+    _check(lib().bvf_bowl_array(ctypes.byref(bowl), n_rings, n_inner, None, ctypes.byref(n)))
+    out = np.zeros((n.value, 6))
+    _check(lib().bvf_bowl_array(ctypes.byref(bowl), n_rings, n_inner,
+                                out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+    return out
+
+
+def bvf_steer_weights(elements, target, f0, c0=1500.0) -> np.ndarray:
+    """A copy of the element rows with steering weights exp(+i k r) towards target."""
+    el = np.array(elements, dtype=np.float64).reshape(-1, 6)
+    tg = np.ascontiguousarray(np.asarray(target, dtype=np.float64).reshape(3))
+    _check(lib().bvf_steer_weights(el.ctypes.data_as(ctypes.c_void_p), el.shape[0],
+                                   tg.ctypes.data_as(ctypes.c_void_p), f0, c0))
+    return el
+
+
+def bvf_time_reversal_plane(ctx, target_ijk, k_src, n_steps, c0, out, stream=None):
+    import torch
+    i, j, k = (int(v) for v in target_ijk)
+    _check(lib().bvf_time_reversal_plane(ctx, i, j, k, k_src, n_steps, c0,
+                                         _ptr(out, torch.float32), _stream(stream)), ctx)
+
+
 # ---- convenience ---------------------------------------------------------
 class Solver:
     """One libbvf context on the current CUDA device."""
@@ -418,6 +478,19 @@ class Solver:
 
     def stats(self) -> Stats:
         return bvf_get_stats(self.ctx)
+
+    def set_time_budget(self, seconds):
+        bvf_set_time_budget(self.ctx, seconds)
+
+    def save_state(self, stream=None):
+        """Snapshot of the acoustic state in a fresh uint8 CUDA tensor."""
+        import torch
+        buf = torch.empty(bvf_state_bytes(self.ctx), dtype=torch.uint8, device="cuda")
+        bvf_state_save(self.ctx, buf, stream)
+        return buf
+
+    def load_state(self, buf, stream=None):
+        bvf_state_load(self.ctx, buf, stream)
 
     def kernel_timing(self, enable: bool):
         bvf_kernel_timing(self.ctx, enable)

@@ -77,7 +77,8 @@ struct VelLayout {
     static constexpr int off_c = off_b + RB * SB * ES;        // szz: k-1 .. k+3 (+1 spare)
     static constexpr int off_i = off_c + RC * TZZ * ES;       // index: k .. k+2
     static constexpr int off_bar = off_i + RI * IT_SLOT;
-    static constexpr int off_end = off_bar + 16;
+    static constexpr int off_abort = off_bar + 16;             // int: plane whose wait ran out
+    static constexpr int off_end = off_abort + 16;
     static size_t bytes(int) { return off_end; }
     static_assert(R % RA == 0 && R % RB == 0 && R % RC == 0 && R % RI == 0,
                   "ring depths must divide the unroll period");
@@ -87,12 +88,32 @@ struct VelLayout {
                   "TMA destinations must stay 128-byte aligned");
 };
 
+// Time-out of a bounded ring wait.  The thread whose wait ran out records
+// the plane in the block's abort word; every thread reads that word right
+// after the next block barrier, so all of them leave the plane loop at the
+// same point and no copy is issued after it.  Thread 0 then waits, again
+// bounded, for the phases the block has armed (planes a .. a + ahead, at most
+// one per barrier), sets bit 2 of the context flag and the tile ends.
+// Barrier and parity of a plane t = pl - k0 of the chunk: velocity ring
+// bar t % 2, phase t / 2; stress ring bar t % 3, phase t / 3.
+template <int NBAR>
+__device__ __forceinline__ void drain_after_timeout(uint64_t *bars, int a, int ahead, int k0,
+                                                    int k1, unsigned limit, int *flag)
+{
+    for (int pl = a; pl <= a + ahead && pl < k1; ++pl) {
+        const int t = pl - k0;
+        tma::mbar_wait(&bars[t % NBAR], (unsigned)(t / NBAR) & 1u, limit);
+    }
+    atomicOr(flag, 2);
+}
+
 // One tile (bx, by) of the grid over z-chunk bz.  REUSE: the block runs
 // further tiles afterwards (persistent batch kernel), so its mbarriers are
 // invalidated at the end and the first copies are fenced against the
-// previous tile's reads of the same shared memory.
+// previous tile's reads of the same shared memory.  Returns true (in every
+// thread) when a ring wait ran out; the tile's results are then incomplete.
 template <typename T, bool REUSE>
-__device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityTmaMaps &tm,
+__device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityTmaMaps &tm,
                                               int kchunk, int bx, int by, int bz,
                                               unsigned char *smb)
 {
@@ -102,6 +123,7 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
     constexpr int TXX = Lay::TXX, TYY = Lay::TYY, TZZ = Lay::TZZ;
     const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(smb + Lay::off_abort);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x0 = bx * TX, y0 = by * TY;
@@ -113,6 +135,7 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
         tma::mbar_init(&bars[0], 1);
         tma::mbar_init(&bars[1], 1);
         tma::mbar_init_fence();
+        *s_abort = -1;
     }
     __syncthreads();
 
@@ -177,20 +200,27 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
     const int dox = ny * p.W, doy = p.W * nx;
 
     unsigned mpar = 0;                              // parity of (k - k0) / R
-    for (int kb = k0; kb < k1; kb += Lay::R, mpar ^= 1u) {
+    bool stop = false;
+    for (int kb = k0; kb < k1 && !stop; kb += Lay::R, mpar ^= 1u) {
 #pragma unroll
         for (int u = 0; u < Lay::R; ++u) {
             const int k = kb + u;
             if (k >= k1) break;
             __syncthreads();
+            if (*s_abort >= 0) {      // a wait of the previous plane ran out
+                stop = true;
+                break;
+            }
             if (tid == 0 && k + 1 < k1) {
                 tma::fence_async_smem();
                 uint64_t *bar = &bars[(u + 1) & 1];
                 tma::mbar_expect_tx(bar, A_BYTES + B_BYTES + C_BYTES + IT);
-                ldA(k + 1, (u + 1) % Lay::RA, bar);
-                ldB(k + 2, (u + 4) % Lay::RB, bar);
-                ldC(k + 3, (u + 4) % Lay::RC, bar);
-                ldI(k + 2, (u + 2) % Lay::RI, bar);
+                if (!(p.hold == 1 && k == p.hold_plane)) {
+                    ldA(k + 1, (u + 1) % Lay::RA, bar);
+                    ldB(k + 2, (u + 4) % Lay::RB, bar);
+                    ldC(k + 3, (u + 4) % Lay::RC, bar);
+                    ldI(k + 2, (u + 2) % Lay::RI, bar);
+                }
             }
             float nux = 0.0f, nuy = 0.0f, nuz = 0.0f;
             if (live && k + 1 < k1) {
@@ -218,7 +248,8 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
                     for (int c = 0; c < 3; ++c) qz[c] = p.psz[c * Szs + oz];
                 }
             }
-            const bool ready = tma::mbar_wait(&bars[u & 1], mpar ^ ((u >> 1) & 1u), p.flag);
+            const bool ready = tma::mbar_wait(&bars[u & 1], mpar ^ ((u >> 1) & 1u), p.wait_limit);
+            if (!ready) *s_abort = k;
             if (ready && live) {
                 // fixed slots of this unrolled copy
                 const T *A = smt + (Lay::off_a / Lay::ES) + (u % Lay::RA) * Lay::SA;
@@ -300,6 +331,9 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
             oy += doy;
         }
     }
+    __syncthreads();
+    const int ab = *s_abort;
+    if (ab >= 0 && tid == 0) drain_after_timeout<2>(bars, ab, 1, k0, k1, p.wait_limit, p.flag);
     if (REUSE) {
         __syncthreads();
         if (tid == 0) {
@@ -307,6 +341,7 @@ __device__ __forceinline__ void velocity_tile(const AcParams &p, const VelocityT
             tma::mbar_inval(&bars[1]);
         }
     }
+    return ab >= 0;
 }
 
 template <typename T>
@@ -331,15 +366,16 @@ struct StressLayout {
     static constexpr int off_v = 0;                           // vx, vy, vz: k-2 .. k+4
     static constexpr int off_i = off_v + RV * 3 * VT * ES;    // index: k .. k+3
     static constexpr int off_bar = off_i + RI * IT_SLOT;
+    static constexpr int off_abort = off_bar + 24;            // int: plane whose wait ran out
     static constexpr int off_lut = off_bar + 32;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(st::StressCoef); }
     static_assert((VT * ES) % 128 == 0 && off_i % 128 == 0,
                   "TMA destinations must stay 128-byte aligned");
 };
 
-// One tile (bx, by) over z-chunk bz; REUSE as for velocity_tile.
+// One tile (bx, by) over z-chunk bz; REUSE and the result as for velocity_tile.
 template <int L, typename T, bool REUSE>
-__device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMaps &tm,
+__device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMaps &tm,
                                             const StepParam &st, int kchunk, int bx, int by,
                                             int bz, unsigned char *smb)
 {
@@ -348,6 +384,7 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
     constexpr int VW = Bx::BW, VT = Bx::VT;
     const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(smb + Lay::off_abort);
     st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -360,6 +397,7 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
     if (tid == 0) {
         for (int b = 0; b < 3; ++b) tma::mbar_init(&bars[b], 1);
         tma::mbar_init_fence();
+        *s_abort = -1;
     }
     __syncthreads();
 
@@ -369,6 +407,7 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
     auto issue = [&](int kk, uint64_t *bar, bool first) {
         const unsigned nv = first ? 5 : 1;
         tma::mbar_expect_tx(bar, nv * 3 * VT_BYTES + (first ? 2 : 1) * IT);
+        if (p.hold == 2 && kk == p.hold_plane + 2) return;    // test hook: armed, none issued
         for (int pl = first ? kk - 2 : kk + 2; pl <= kk + 2; ++pl)
             for (int a = 0; a < 3; ++a)
                 tma::load3d(smb + oV(pl) + a * VT_BYTES, &tm.v[a], x0 - Bx::XO, y0 - 2, pl, bar);
@@ -410,6 +449,7 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
     int it = 0;
     for (int k = k0; k < k1; ++k, ++it) {
         __syncthreads();
+        if (*s_abort >= 0) break;        // a wait of the previous plane ran out
         if (tid == 0 && k + 2 < k1) {
             tma::fence_async_smem();
             issue(k + 2, &bars[(it + 2) % 3], false);
@@ -459,7 +499,8 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
                 dS = p.dftS[q];
             }
         }
-        const bool ready = tma::mbar_wait(&bars[it % 3], (it / 3) & 1, p.flag);
+        const bool ready = tma::mbar_wait(&bars[it % 3], (it / 3) & 1, p.wait_limit);
+        if (!ready) *s_abort = k;
         if (ready && lv) {
             const int vm2 = vM2, vm1 = vM1, vp1 = vP1, vp2 = vP2;
             const unsigned char *I0 = smb + iK;
@@ -578,11 +619,15 @@ __device__ __forceinline__ void stress_tile(const AcParams &p, const StressTmaMa
         march(std::true_type{});
     else
         march(std::false_type{});
+    __syncthreads();
+    const int ab = *s_abort;
+    if (ab >= 0 && tid == 0) drain_after_timeout<3>(bars, ab, 2, k0, k1, p.wait_limit, p.flag);
     if (REUSE) {
         __syncthreads();
         if (tid == 0)
             for (int b = 0; b < 3; ++b) tma::mbar_inval(&bars[b]);
     }
+    return ab >= 0;
 }
 
 template <int L, int MINB, typename T>
@@ -659,8 +704,9 @@ __global__ void __launch_bounds__(NTH, 5)
             tma::tensormap_acquire(&bp.vm[d].idx);
         }
         const int li = ws.w - bp.block0[d], tx_ = bp.tiles_x[d], txy = tx_ * bp.tiles_y[d];
-        velocity_tile<T, true>(bp.p[d], bp.vm[d], bp.kchunk[d], li % tx_, (li % txy) / tx_,
-                               li / txy, smb);
+        if (velocity_tile<T, true>(bp.p[d], bp.vm[d], bp.kchunk[d], li % tx_, (li % txy) / tx_,
+                                   li / txy, smb))
+            break;
     }
 }
 
@@ -688,8 +734,9 @@ __global__ void __launch_bounds__(NTH, MINB)
             __syncthreads();
         }
         const int li = ws.w - bp.block0[d], tx_ = bp.tiles_x[d], txy = tx_ * bp.tiles_y[d];
-        stress_tile<L, T, true>(bp.p[d], bp.sm[d], sq, bp.kchunk[d], li % tx_,
-                                (li % txy) / tx_, li / txy, smb);
+        if (stress_tile<L, T, true>(bp.p[d], bp.sm[d], sq, bp.kchunk[d], li % tx_,
+                                    (li % txy) / tx_, li / txy, smb))
+            break;
     }
 }
 

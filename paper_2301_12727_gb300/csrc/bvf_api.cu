@@ -7,6 +7,7 @@
 // reference).  All per-voxel work runs in the kernels of bvf_acoustic.cu and
 // bvf_aux.cu.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -19,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include "bvf_internal.cuh"
+#include "bvf_tma.cuh"
 
 using namespace bvf;
 
@@ -84,6 +86,12 @@ struct bvf_ctx {
     size_t ev_used = 0;
     double vel_ms = 0.0, str_ms = 0.0;
     long long vel_n = 0, str_n = 0;
+    // wall-clock budget of one bvf_run_acoustic / bvf_run_thermal call (s, 0 = none)
+    double budget_s = 0.0;
+    cudaEvent_t budget_ev[2] = {nullptr, nullptr};
+    // test hook of the bounded TMA waits, applied to the next acoustic step
+    int hold = 0, hold_plane = -1;
+    unsigned hold_limit = 0;
 };
 
 struct bvf_batch {
@@ -372,6 +380,9 @@ AcParams make_params(bvf_ctx *c)
     p.dftS = c->dftS;
     p.flag = c->flag;
     p.kchunk = c->kchunk;
+    p.wait_limit = tma::kWaitLimit;
+    p.hold = 0;
+    p.hold_plane = -1;
     p.src_scale = (float)(2.0 * c->c0 * c->g.dt / c->g.dx / c->s_sig);
     return p;
 }
@@ -407,6 +418,78 @@ int ensure_dft(bvf_ctx *c, cudaStream_t s)
     return BVF_OK;
 }
 
+// Wall-clock budget of a run call.  Every kBudgetChunk steps the call records
+// an event, waits for the event of the chunk before (so at most two chunks
+// are queued ahead of the host) and compares the time since the call began
+// with the budget.  Without a budget nothing is recorded or waited for.
+constexpr int kBudgetChunk = 32;
+struct Budget {
+    bvf_ctx *c;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    int slot = 0;
+    bool armed[2] = {false, false};
+    // before step `it` of the call: BVF_OK to go on, BVF_E_TIMEOUT (after the
+    // queued work has finished) once the budget is spent
+    int check(int it, cudaStream_t s, const char *what)
+    {
+        if (!(c->budget_s > 0.0) || it == 0 || it % kBudgetChunk) return BVF_OK;
+        for (int b = 0; b < 2; ++b)
+            if (!c->budget_ev[b]) CK(cudaEventCreateWithFlags(&c->budget_ev[b], cudaEventDisableTiming),
+                                      "time budget");
+        CK(cudaEventRecord(c->budget_ev[slot], s), "time budget");
+        armed[slot] = true;
+        slot ^= 1;
+        if (armed[slot]) CK(cudaEventSynchronize(c->budget_ev[slot]), "time budget");
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el < c->budget_s) return BVF_OK;
+        CK(cudaStreamSynchronize(s), "time budget");
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "%s: wall-clock budget of %.3g s spent after %d steps of this call "
+                      "(%.3g s); the context holds the state after them",
+                      what, c->budget_s, it, el);
+        return fail(c, BVF_E_TIMEOUT, buf);
+    }
+};
+
+// Snapshot layout of bvf_state_save: a 256-byte header, then the state
+// arrays, CPML memories, peak map, the two FP64 DFT sums and the device flag,
+// each section starting on a 256-byte boundary.
+constexpr uint64_t kStateMagic = 0x3176617473667662ull;   // "bvfstav1"
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, nx, ny, nz, L, h16, has_dft, pad;
+    int64_t steps, dft_count;
+    double dx, dt, f0;
+    uint64_t bytes;
+    char reserved[256 - 8 - 9 * 4 - 2 * 8 - 3 * 8 - 8];
+};
+static_assert(sizeof(StateHeader) == 256, "state header is 256 bytes");
+
+struct StateSections {
+    size_t fields, psi, peak, dft, flag, total;
+    size_t off_fields, off_psi, off_peak, off_C, off_S, off_flag;
+};
+StateSections state_sections(const bvf_ctx *c)
+{
+    auto up = [](size_t n) { return (n + 255) & ~(size_t)255; };
+    StateSections t{};
+    t.fields = (9 + 6 * (size_t)c->L) * c->fstride * c->es;
+    t.psi = kNumCpmlSlots * (c->slab_x + c->slab_y + c->slab_z) * sizeof(float);
+    t.peak = c->N * sizeof(float);
+    t.dft = c->N * sizeof(double);
+    t.flag = sizeof(int);
+    t.off_fields = 256;
+    t.off_psi = t.off_fields + up(t.fields);
+    t.off_peak = t.off_psi + up(t.psi);
+    t.off_C = t.off_peak + up(t.peak);
+    t.off_S = t.off_C + up(t.dft);
+    t.off_flag = t.off_S + up(t.dft);
+    t.total = t.off_flag + 256;
+    return t;
+}
+
 }  // namespace
 
 extern "C" {
@@ -425,6 +508,7 @@ const char *bvf_strerror(int code)
     case BVF_E_NOMEM: return "device allocation failed";
     case BVF_E_CUDA: return "CUDA error";
     case BVF_E_UNSTABLE: return "non-finite pressure detected";
+    case BVF_E_TIMEOUT: return "wall-clock budget of the call spent";
     default: return "unknown status";
     }
 }
@@ -443,6 +527,8 @@ void bvf_destroy(bvf_ctx *c)
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->budget_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -674,8 +760,20 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
         if (rc != BVF_OK) return rc;
     }
     AcParams p = make_params(c);
+    Budget budget{c};
     for (int it = 0; it < n_steps; ++it) {
+        const int rb = budget.check(it, s, "bvf_run_acoustic");
+        if (rb != BVF_OK) return rb;
         p.st = step_param(c, cp, c->steps);
+        if (c->hold) {                       // test hook: this one step only
+            p.hold = c->hold;
+            p.hold_plane = c->hold_plane;
+            p.wait_limit = c->hold_limit ? c->hold_limit : tma::kWaitLimit;
+            c->hold = 0;
+        } else {
+            p.hold = 0;
+            p.wait_limit = tma::kWaitLimit;
+        }
         auto vel = [&]() {
             return c->tma ? launch_velocity_tma(p, c->vmaps, s) : launch_velocity(p, s);
         };
@@ -851,7 +949,16 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     p.cem = d_cem43;
     const int total = th->n_on + th->n_off;
     float *a = d_T, *b = c->T2;
+    Budget budget{c};
     for (int n = 0; n < total; ++n) {
+        const int rb = budget.check(n, s, "bvf_run_thermal");
+        if (rb != BVF_OK) {
+            // the last completed step's temperature goes to d_T
+            if (a != d_T)
+                CK(cudaMemcpy(d_T, a, c->N * sizeof(float), cudaMemcpyDeviceToDevice), "T out");
+            c->thermal_steps += n;
+            return rb;
+        }
         p.dc = (n < th->n_on) ? (float)th->duty : 0.0f;
         p.flush = ((n + 1) % 32 == 0 || n + 1 == total) ? 1 : 0;
         p.T = a;
@@ -1376,6 +1483,211 @@ int bvf_get_stats(const bvf_ctx *c, bvf_stats *out)
     // byte in each kernel and the FP32 peak map (read + write)
     out->bytes_per_voxel_step = (double)c->es * (12 + 15 + 12 * c->L) + 2.0 + 8.0;
     return BVF_OK;
+}
+
+// ---- call budget, time-out test hook, snapshots ---------------------------
+
+int bvf_set_time_budget(bvf_ctx *c, double seconds)
+{
+    if (!c || !(seconds >= 0.0) || std::isinf(seconds))
+        return fail(c, BVF_E_ARG, "bvf_set_time_budget: bad context or budget");
+    c->budget_s = seconds;
+    return BVF_OK;
+}
+
+int bvf_test_withhold_copy(bvf_ctx *c, int kernel, int plane, unsigned wait_limit)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_test_withhold_copy: NULL context");
+    if (kernel == 0) {
+        c->hold = 0;
+        return BVF_OK;
+    }
+    if ((kernel != 1 && kernel != 2) || plane < 0 || plane >= c->g.nz)
+        return fail(c, BVF_E_ARG, "bvf_test_withhold_copy: kernel must be 1 or 2, plane inside the grid");
+    if (!(kernel == 1 ? c->tma : c->tma_stress))
+        return fail(c, BVF_E_ARG, "bvf_test_withhold_copy: this context does not use the TMA-fed kernel");
+    c->hold = kernel;
+    c->hold_plane = plane;
+    c->hold_limit = wait_limit;
+    return BVF_OK;
+}
+
+int bvf_state_bytes(const bvf_ctx *c, size_t *out)
+{
+    if (!c || !out) return fail(nullptr, BVF_E_ARG, "bvf_state_bytes: NULL argument");
+    *out = state_sections(c).total;
+    return BVF_OK;
+}
+
+int bvf_state_save(bvf_ctx *c, void *d_buf, size_t bytes, void *stream)
+{
+    if (!c || !d_buf) return fail(c, BVF_E_ARG, "bvf_state_save: NULL argument");
+    const StateSections t = state_sections(c);
+    if (bytes < t.total) return fail(c, BVF_E_ARG, "bvf_state_save: buffer smaller than bvf_state_bytes");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *b = static_cast<char *>(d_buf);
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.version = BVF_VERSION;
+    h.nx = c->g.nx;
+    h.ny = c->g.ny;
+    h.nz = c->g.nz;
+    h.L = c->L;
+    h.h16 = c->h16;
+    h.has_dft = c->dftC ? 1 : 0;
+    h.steps = c->steps;
+    h.dft_count = c->dft_count;
+    h.dx = c->g.dx;
+    h.dt = c->g.dt;
+    h.f0 = c->ph.f0;
+    h.bytes = t.total;
+    // pageable source: the copy is staged before the call returns
+    CK(cudaMemcpyAsync(b, &h, sizeof h, cudaMemcpyHostToDevice, s), "bvf_state_save");
+    CK(cudaMemcpyAsync(b + t.off_fields, c->fields, t.fields, cudaMemcpyDeviceToDevice, s), "bvf_state_save");
+    if (t.psi) CK(cudaMemcpyAsync(b + t.off_psi, c->psi, t.psi, cudaMemcpyDeviceToDevice, s), "bvf_state_save");
+    CK(cudaMemcpyAsync(b + t.off_peak, c->peak, t.peak, cudaMemcpyDeviceToDevice, s), "bvf_state_save");
+    if (c->dftC) {
+        CK(cudaMemcpyAsync(b + t.off_C, c->dftC, t.dft, cudaMemcpyDeviceToDevice, s), "bvf_state_save");
+        CK(cudaMemcpyAsync(b + t.off_S, c->dftS, t.dft, cudaMemcpyDeviceToDevice, s), "bvf_state_save");
+    } else {
+        CK(cudaMemsetAsync(b + t.off_C, 0, 2 * (t.off_S - t.off_C), s), "bvf_state_save");
+    }
+    CK(cudaMemcpyAsync(b + t.off_flag, c->flag, t.flag, cudaMemcpyDeviceToDevice, s), "bvf_state_save");
+    return BVF_OK;
+}
+
+int bvf_state_load(bvf_ctx *c, const void *d_buf, size_t bytes, void *stream)
+{
+    if (!c || !d_buf) return fail(c, BVF_E_ARG, "bvf_state_load: NULL argument");
+    const StateSections t = state_sections(c);
+    if (bytes < t.total) return fail(c, BVF_E_ARG, "bvf_state_load: buffer smaller than bvf_state_bytes");
+    cudaStream_t s = (cudaStream_t)stream;
+    const char *b = static_cast<const char *>(d_buf);
+    StateHeader h{};
+    CK(cudaMemcpyAsync(&h, b, sizeof h, cudaMemcpyDeviceToHost, s), "bvf_state_load");
+    CK(cudaStreamSynchronize(s), "bvf_state_load");
+    if (h.magic != kStateMagic || h.version != BVF_VERSION || h.bytes != t.total)
+        return fail(c, BVF_E_ARG, "bvf_state_load: not a snapshot of this library version and layout");
+    if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.L != c->L || h.h16 != c->h16 ||
+        h.dx != c->g.dx || h.dt != c->g.dt || h.f0 != c->ph.f0)
+        return fail(c, BVF_E_ARG, "bvf_state_load: snapshot of a different grid, time step, "
+                                  "frequency, SLS count or storage");
+    if (h.has_dft) {
+        const int rc = ensure_dft(c, s);
+        if (rc != BVF_OK) return rc;
+    }
+    CK(cudaMemcpyAsync(c->fields, b + t.off_fields, t.fields, cudaMemcpyDeviceToDevice, s), "bvf_state_load");
+    if (t.psi) CK(cudaMemcpyAsync(c->psi, b + t.off_psi, t.psi, cudaMemcpyDeviceToDevice, s), "bvf_state_load");
+    CK(cudaMemcpyAsync(c->peak, b + t.off_peak, t.peak, cudaMemcpyDeviceToDevice, s), "bvf_state_load");
+    if (c->dftC) {
+        CK(cudaMemcpyAsync(c->dftC, b + t.off_C, t.dft, cudaMemcpyDeviceToDevice, s), "bvf_state_load");
+        CK(cudaMemcpyAsync(c->dftS, b + t.off_S, t.dft, cudaMemcpyDeviceToDevice, s), "bvf_state_load");
+    }
+    CK(cudaMemcpyAsync(c->flag, b + t.off_flag, t.flag, cudaMemcpyDeviceToDevice, s), "bvf_state_load");
+    c->steps = h.steps;
+    c->dft_count = (int)h.dft_count;
+    return BVF_OK;
+}
+
+// ---- phased sources ---------------------------------------------------------
+
+int bvf_bowl_array(const bvf_bowl *bw, int n_rings, int n_inner, double *h_elem, int *n_out)
+{
+    if (!bw || !n_out || n_rings < 1 || n_inner < 1)
+        return fail(nullptr, BVF_E_ARG, "bvf_bowl_array: bad argument");
+    const double a = 0.5 * bw->aperture, R = bw->roc;
+    if (!(a > 0.0) || !(R >= a)) return fail(nullptr, BVF_E_ARG, "bvf_bowl_array: need 0 < aperture/2 <= roc");
+    double ux = bw->dir[0], uy = bw->dir[1], uz = bw->dir[2];
+    const double nrm = std::sqrt(ux * ux + uy * uy + uz * uz);
+    if (!(nrm > 0.0)) return fail(nullptr, BVF_E_ARG, "bvf_bowl_array: zero direction");
+    ux /= nrm; uy /= nrm; uz /= nrm;
+    // rotation taking +z to the axis: about z x u by the angle between them
+    double kx = -uy, ky = ux;
+    const double sn = std::sqrt(kx * kx + ky * ky), cs = uz;
+    if (sn > 0.0) { kx /= sn; ky /= sn; }
+    const double thmax = std::asin(a / R);
+    int n = 0;
+    for (int r = 0; r < n_rings; ++r) {
+        const double t0 = thmax * r / n_rings, t1 = thmax * (r + 1) / n_rings, tc = 0.5 * (t0 + t1);
+        const int m = n_inner * (r + 1);
+        const double area = 2.0 * kPi * R * R * (std::cos(t0) - std::cos(t1)) / m;
+        for (int e = 0; e < m; ++e, ++n) {
+            if (!h_elem) continue;
+            const double ph = 2.0 * kPi * (e + 0.5) / m;
+            const double px = R * std::sin(tc) * std::cos(ph), py = R * std::sin(tc) * std::sin(ph);
+            const double pz = R * (1.0 - std::cos(tc));
+            const double kp = kx * px + ky * py;
+            const double cx = ky * pz, cy = -kx * pz, cz = kx * py - ky * px;
+            double *row = h_elem + 6 * (size_t)n;
+            row[0] = bw->apex[0] + px * cs + cx * sn + kx * kp * (1.0 - cs);
+            row[1] = bw->apex[1] + py * cs + cy * sn + ky * kp * (1.0 - cs);
+            row[2] = bw->apex[2] + pz * cs + cz * sn;
+            row[3] = area;
+            row[4] = 1.0;
+            row[5] = 0.0;
+        }
+    }
+    *n_out = n;
+    return BVF_OK;
+}
+
+int bvf_steer_weights(double *h_elem, int ne, const double *target, double f0, double c0)
+{
+    if (!h_elem || !target || ne < 1 || !(f0 > 0.0) || !(c0 > 0.0))
+        return fail(nullptr, BVF_E_ARG, "bvf_steer_weights: bad argument");
+    const double k = 2.0 * kPi * f0 / c0;
+    for (int e = 0; e < ne; ++e) {
+        double *row = h_elem + 6 * (size_t)e;
+        const double dx = row[0] - target[0], dy = row[1] - target[1], dz = row[2] - target[2];
+        const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+        row[4] = std::cos(k * r);
+        row[5] = std::sin(k * r);
+    }
+    return BVF_OK;
+}
+
+int bvf_time_reversal_plane(bvf_ctx *c, int ti, int tj, int tk, int k_src, int n_steps, double c0,
+                            float *d_plane, void *stream)
+{
+    if (!c || !d_plane) return fail(c, BVF_E_ARG, "bvf_time_reversal_plane: NULL argument");
+    const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+    if (ti < 0 || ti >= nx || tj < 0 || tj >= ny || tk < 0 || tk >= nz || k_src < 0 || k_src >= nz)
+        return fail(c, BVF_E_ARG, "bvf_time_reversal_plane: target or source plane outside the grid");
+    const int M = (int)std::lround(1.0 / (c->ph.f0 * c->g.dt));
+    if (M < 1 || n_steps < 2 * M + 1)
+        return fail(c, BVF_E_ARG, "bvf_time_reversal_plane: need n_steps > two periods");
+    if (!(c0 > 0.0)) return fail(c, BVF_E_ARG, "bvf_time_reversal_plane: bad c0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t plane = (size_t)nx * ny;
+    // temporaries: the point source plane and the 8-byte maximum
+    char *tmp = nullptr;
+    const size_t src_bytes = (plane * sizeof(float2) + 255) & ~(size_t)255;
+    CK(cudaMallocAsync((void **)&tmp, src_bytes + 256, s), "bvf_time_reversal_plane: temporaries");
+    float2 *src = reinterpret_cast<float2 *>(tmp);
+    unsigned long long *d_max = reinterpret_cast<unsigned long long *>(tmp + src_bytes);
+    auto done = [&](int code) {
+        cudaFreeAsync(tmp, s);
+        return code;
+    };
+    static const float one[2] = {1.0f, 0.0f};
+    cudaError_t e = cudaMemsetAsync(src, 0, plane * sizeof(float2), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(src + (size_t)tj * nx + ti, one, sizeof one, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "bvf_time_reversal_plane: source"));
+    int rc = bvf_reset(c, stream);
+    if (rc == BVF_OK) rc = bvf_set_source(c, tk, reinterpret_cast<float *>(src), c0, BVF_ENV_RAMP_CW, 0, stream);
+    const bvf_capture cap{-1, n_steps - 2 * M + 1, 2 * M};
+    if (rc == BVF_OK) rc = bvf_run_acoustic(c, n_steps, &cap, stream);
+    if (rc != BVF_OK) return done(rc);
+    e = launch_conj_plane(c->dftC + (size_t)k_src * plane, c->dftS + (size_t)k_src * plane, plane,
+                          d_max, reinterpret_cast<float2 *>(d_plane), s);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "bvf_time_reversal_plane: conjugate plane"));
+    c->launches += 2;
+    rc = bvf_synchronize(c, stream);
+    if (rc != BVF_OK) return done(rc);
+    if ((rc = bvf_reset(c, stream)) != BVF_OK) return done(rc);
+    bvf_set_source(c, 0, nullptr, c0, BVF_ENV_NONE, 0, stream);
+    return done(BVF_OK);
 }
 
 }  // extern "C"

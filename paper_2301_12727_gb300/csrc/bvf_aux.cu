@@ -315,7 +315,44 @@ __global__ void __launch_bounds__(1024) k_plane_sums(
     }
 }
 
+// Time-reversal (phase-conjugation) plane from the FP64 DFT sums of one
+// z-plane: with amplitude 2 |C - iS| / N and phase atan2(-S, C) the captured
+// complex amplitude is P = (2/N)(C - iS), so conj(P) / max|P| over the plane is
+// (C + iS) / max |C + iS|.  First pass: the largest |C + iS|^2 of the plane
+// (non-negative doubles order like their bit patterns, so one 64-bit
+// atomicMax keeps it); second pass: the normalised conjugate.
+__global__ void k_plane_absmax(const double *__restrict__ C, const double *__restrict__ S,
+                               size_t n, unsigned long long *out)
+{
+    double m = 0.0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        m = fmax(m, C[q] * C[q] + S[q] * S[q]);
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void k_conj_normalise(const double *__restrict__ C, const double *__restrict__ S,
+                                 size_t n, const unsigned long long *mx, float2 *__restrict__ out)
+{
+    const double m2 = __longlong_as_double((long long)*mx);
+    const double inv = m2 > 0.0 ? 1.0 / sqrt(m2) : 0.0;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        out[q] = make_float2((float)(C[q] * inv), (float)(S[q] * inv));
+}
+
 }  // namespace
+
+cudaError_t launch_conj_plane(const double *C, const double *S, size_t n,
+                              unsigned long long *d_max, float2 *out, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_plane_absmax<<<blocks_for(n), kThreads, 0, s>>>(C, S, n, d_max);
+    k_conj_normalise<<<blocks_for(n), kThreads, 0, s>>>(C, S, n, d_max, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_index_max(const uint8_t *idx, size_t n, unsigned *d_out, cudaStream_t s)
 {

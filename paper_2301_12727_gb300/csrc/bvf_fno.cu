@@ -767,6 +767,7 @@ k_project_tc(const float *__restrict__ v, const float *__restrict__ Q1, const fl
     };
     if ((long)blockIdx.x < tiles) load(blockIdx.x);
     int it = 0;
+    bool gave_up = false;
     for (long tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
         const long p = tile * 128 + pt;
 #pragma unroll
@@ -799,7 +800,8 @@ k_project_tc(const float *__restrict__ v, const float *__restrict__ Q1, const fl
         // the next tile's loads overlap the products and this tile's epilogue
         if (tile + gridDim.x < tiles) load(tile + gridDim.x);
         // a warp reads tensor memory only when all its lanes saw the commit
-        const bool ready = __all_sync(0xffffffffu, bvf::tma::mbar_wait(bar, it & 1, flag));
+        const bool ready =
+            __all_sync(0xffffffffu, bvf::tma::mbar_wait(bar, it & 1, bvf::tma::kWaitLimit));
         tc::fence_after();
         float o[COUT];
 #pragma unroll
@@ -826,12 +828,22 @@ k_project_tc(const float *__restrict__ v, const float *__restrict__ Q1, const fl
             for (int k = 0; k < COUT; ++k) sred[k * 128 + pt] = o[k];
         }
         tc::fence_before();
-        __syncthreads();          // TMEM, the A buffers and sred are settled
+        // TMEM, the A buffers and sred are settled; every thread learns
+        // whether some warp's wait for the products ran out
+        gave_up = __syncthreads_or(!ready) != 0;
         if (!half && p < N) {
 #pragma unroll
             for (int k = 0; k < COUT; ++k)
                 if (k < c_out) out[(long)k * N + p] = q2[k] + o[k] + sred[k * 128 + pt];
         }
+        // after a time-out no further product is issued: the block waits,
+        // bounded, for the products in flight, frees its tensor memory and
+        // ends (the flag makes bvf_fno_synchronize report it)
+        if (gave_up) break;
+    }
+    if (gave_up && tid == 0) {
+        bvf::tma::mbar_wait(bar, it & 1, bvf::tma::kWaitLimit);
+        atomicOr(flag, 2);
     }
     tc::fence_after();
     __syncthreads();

@@ -92,6 +92,14 @@ struct AcParams {
     StepParam st;        // this step's source and capture parameters
     int *flag;
     int kchunk;          // z-planes per block (0 = default_kchunk)
+    // bounded TMA waits: polls per mbarrier wait before a block gives up
+    // (sets bit 2 of *flag, issues no further copies, drains the copies it
+    // has issued, and stops).  hold = 1 (velocity) or 2 (stress) makes that
+    // kernel arm the barrier of its look-ahead copies at plane hold_plane but
+    // issue none of them, so the wait that follows runs out with nothing in
+    // flight: the test hook of the time-out path (0 = off).
+    unsigned wait_limit;
+    int hold, hold_plane;
 };
 
 // Tensor maps of the TMA-fed acoustic kernels (x-y boxes of one z-plane).
@@ -183,6 +191,8 @@ cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float 
 cudaError_t launch_rs_weighted(const float4 *el, const float2 *wt, int ne, int nx, int ny,
                                float dx, float zp, float k_over_pi, double pref, float2 *out,
                                cudaStream_t s);
+cudaError_t launch_conj_plane(const double *C, const double *S, size_t n,
+                              unsigned long long *d_max, float2 *out, cudaStream_t s);
 cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_mat,
                                const double *amp, double p_scale, float *Q, size_t n,
                                cudaStream_t s);

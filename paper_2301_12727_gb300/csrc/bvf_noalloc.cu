@@ -16,13 +16,14 @@
 // example on two streams without ordering between them) use the same array and
 // race; order such calls on one stream or synchronise between them.
 //
-// The first call on each device looks up the array's device address
-// (cudaGetSymbolAddress, with that device current); make that first call
-// before any stream capture on the device.
+// Every call looks up the array's device address on the current device
+// (cudaGetSymbolAddress, with that device current).  The address is not
+// cached: a cached one would dangle once the device's context is torn down and
+// the library's module loaded again (cudaDeviceReset), and the look-up is cheap
+// once the module is loaded.  The call waits for its stream before returning.
 #include <cmath>
 #include <cstddef>
 #include <cstring>
-#include <mutex>
 
 #include "bvf_internal.cuh"
 
@@ -44,10 +45,6 @@ constexpr size_t kScratchBytes = sizeof(TransmissionScratch);   // 4136 bytes
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_addr[kMaxDevices] = {};   // device address of g_scratch, per device
-
 // failures are reported through bvf_last_error(NULL), like every context-free call
 int noalloc_fail(int code, const char *msg)
 {
@@ -55,23 +52,15 @@ int noalloc_fail(int code, const char *msg)
     return code;
 }
 
-// Device address of the scratch array on the current device.  The first call
-// on each device looks it up (the host-side name g_scratch is not a device
-// address and must never be handed to a kernel).
+// Device address of the scratch array on the current device, looked up at
+// each call (the host-side name g_scratch is not a device address and must
+// never be handed to a kernel).
 cudaError_t scratch_on_current_device(TransmissionScratch **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = static_cast<TransmissionScratch *>(g_addr[dev]);
+    *out = static_cast<TransmissionScratch *>(p);
     return cudaSuccess;
 }
 

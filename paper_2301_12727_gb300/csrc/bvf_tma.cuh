@@ -57,14 +57,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
     return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; on time-out sets bit 2 of
-// *flag and returns false (the caller skips its work but keeps every barrier).
+// Bounded wait for the phase of the given parity: at most `limit` polls, then
+// false (the phase has not completed).  The caller records the time-out and
+// stops issuing copies; see the acoustic and projection kernels.
 constexpr unsigned kWaitLimit = 1u << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int *flag)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit)
 {
-    for (unsigned it = 0; it < kWaitLimit; ++it)
+    for (unsigned it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(flag, 2);
     return false;
 }
 

@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -38,9 +40,10 @@ def test_every_declared_symbol_is_exported(bvf):
 
 
 def test_version_and_constants(bvf):
-    assert bvf.bvf_version() == 2
+    assert bvf.bvf_version() == 3
     assert bvf.bvf_courant_limit() == pytest.approx(6 / (7 * 3 ** 0.5), rel=1e-15)
     assert bvf.lib().bvf_strerror(-2).decode().startswith("time step")
+    assert bvf.lib().bvf_strerror(bvf.BVF_E_TIMEOUT).decode().startswith("wall-clock")
 
 
 @pytest.mark.parametrize("grid,phys", [
@@ -68,6 +71,13 @@ def test_null_pointers_rejected(bvf):
     assert L.bvf_rs_plane(None, 4, 4, 1e-3, 0.0, 5e5, None, None) == bvf.BVF_E_ARG
     assert L.bvf_run_acoustic(None, 1, None, None) == bvf.BVF_E_ARG
     assert L.bvf_set_materials(None, None, None, 0) == bvf.BVF_E_ARG
+    assert L.bvf_set_time_budget(None, 1.0) == bvf.BVF_E_ARG
+    assert L.bvf_state_bytes(None, None) == bvf.BVF_E_ARG
+    assert L.bvf_state_save(None, None, 0, None) == bvf.BVF_E_ARG
+    assert L.bvf_state_load(None, None, 0, None) == bvf.BVF_E_ARG
+    assert L.bvf_test_withhold_copy(None, 1, 0, 0) == bvf.BVF_E_ARG
+    assert L.bvf_time_reversal_plane(None, 0, 0, 0, 0, 10, 1500.0, None, None) == bvf.BVF_E_ARG
+    assert L.bvf_steer_weights(None, 1, None, 5e5, 1500.0) == bvf.BVF_E_ARG
     L.bvf_destroy(None)
 
 
@@ -113,3 +123,58 @@ def test_surrogate_validation_on_host(bvf):
                               None) == bvf.BVF_E_ARG
     L.bvf_fno_destroy(None)
 
+
+
+# ---- host-only phased-source helpers (no GPU): pinned to cap geometry and to
+# the in-phase arrival that defines steering
+
+def test_bowl_array_lies_on_the_cap_and_tiles_its_area(bvf):
+    """Every element sits on the sphere of radius roc about the centre of
+    curvature (apex + roc * axis), inside the aperture, and the element areas
+    add up to the cap area 2 pi R^2 (1 - cos theta_max), for a tilted axis."""
+    a_d, R = 24e-3, 22e-3
+    apex = np.array([1e-3, -2e-3, 3e-3])
+    u = np.array([0.3, -0.2, 1.0])
+    u /= np.linalg.norm(u)
+    bowl = bvf.Bowl(a_d, R, tuple(apex), tuple(u), 0.0, 1500.0, 0.0)
+    el = bvf.bvf_bowl_array(bowl, 7, 6)
+    assert el.shape == (6 * 7 * 8 // 2, 6)
+    centre = apex + R * u
+    np.testing.assert_allclose(np.linalg.norm(el[:, :3] - centre, axis=1), R, rtol=1e-12)
+    # polar angle of each element about the axis, seen from the centre
+    cosang = ((centre - el[:, :3]) @ u) / R
+    thmax = np.arcsin(0.5 * a_d / R)
+    assert (cosang >= np.cos(thmax) - 1e-12).all()
+    np.testing.assert_allclose(el[:, 3].sum(), 2 * np.pi * R * R * (1 - np.cos(thmax)), rtol=1e-12)
+    assert (el[:, 4] == 1.0).all() and (el[:, 5] == 0.0).all()
+    # counting call
+    n = ctypes.c_int()
+    assert bvf.lib().bvf_bowl_array(ctypes.byref(bowl), 7, 6, None, ctypes.byref(n)) == 0
+    assert n.value == el.shape[0]
+    assert bvf.lib().bvf_bowl_array(ctypes.byref(bowl), 0, 6, None, ctypes.byref(n)) == bvf.BVF_E_ARG
+
+
+def test_steer_weights_bring_every_element_in_phase_at_the_target(bvf):
+    """With w_e from bvf_steer_weights, every element's monochromatic wave
+    w_e exp(-i k r_e) / r_e reaches the target with zero phase, so the coherent
+    sum there equals sum 1/r_e (its largest possible magnitude); other points
+    see less."""
+    rng = np.random.default_rng(4)
+    el = np.column_stack([rng.uniform(-0.01, 0.01, 50), rng.uniform(-0.01, 0.01, 50),
+                          rng.uniform(-0.03, -0.02, 50), np.ones(50), np.ones(50), np.zeros(50)])
+    f0, c0 = 5e5, 1500.0
+    k = 2 * np.pi * f0 / c0
+    tgt = np.array([2e-3, -1e-3, 0.01])
+    st = bvf.bvf_steer_weights(el, tgt, f0, c0)
+    assert st.shape == el.shape and np.array_equal(st[:, :4], el[:, :4])
+    w = st[:, 4] + 1j * st[:, 5]
+    np.testing.assert_allclose(np.abs(w), 1.0, rtol=1e-14)
+
+    def field(x):
+        r = np.linalg.norm(st[:, :3] - x, axis=1)
+        return np.sum(w * np.exp(-1j * k * r) / r), np.sum(1.0 / r)
+
+    p, bound = field(tgt)
+    assert abs(p - bound) < 1e-10 * bound
+    p2, bound2 = field(tgt + np.array([1.5e-3, 0.0, 0.0]))
+    assert abs(p2) < 0.9 * bound2

@@ -1,6 +1,8 @@
 """Multi-element phased sources: the weighted-element Rayleigh field against
-the oracle, geometric steering in water, and time-reversal refocusing
-through a skull phantom."""
+the oracle, geometric steering in water (the steered field against the
+oracle's FDTD, and the focus position), and time reversal (the conjugated
+plane against the oracle's own point-source capture, and refocusing through a
+skull phantom)."""
 import numpy as np
 import pytest
 
@@ -81,7 +83,7 @@ def test_gpu_time_reversal_refocuses_through_the_skull(mods):
     tgt = (36, 30, 46)
     M = c.steps_per_period
     n = int(1.5 * c.nz * c.dx / 1500.0 / c.dt) + 4 * M
-    plane = phased.time_reversal_plane(s, tgt, c.k_src, c.f0, c.dt, n)
+    plane = phased.time_reversal_plane(s, tgt, c.k_src, n)
     s.set_source(1e4 * plane, c.k_src, 1500.0, bvf.BVF_ENV_RAMP_CW)
     s.run(n, dft_start=n - 2 * M + 1, dft_steps=2 * M)
     s.synchronize()
@@ -90,3 +92,65 @@ def test_gpu_time_reversal_refocuses_through_the_skull(mods):
     got = argmax3(np.where(beyond, amp, 0.0))[::-1]
     assert np.abs(got - np.array(tgt)).max() <= 2, got
     s.close()
+
+
+def test_gpu_time_reversal_plane_matches_oracle(mods, orc):
+    """bvf_time_reversal_plane against the oracle: the same CW point source
+    (one-cycle ramp) at the target behind a small skull phantom, run in FP64;
+    its complex amplitude on the source plane over the last two periods,
+    conjugated and divided by its largest magnitude, equals the library's
+    plane to 2e-4 of that largest magnitude (FP32 fields over ~300 steps)."""
+    bvf, phased, synth = mods
+    c = synth.skull_case(48, 48, 40, dx=0.5e-3, n_steps=10, aperture=20e-3, roc=18e-3,
+                         n_pml=4, seed=9)
+    s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+    s.set_materials(c.index, c.materials)
+    tgt = (27, 21, 33)
+    M = c.steps_per_period
+    n = int(1.2 * c.nz * c.dx / 1500.0 / c.dt) + 3 * M
+    got = phased.time_reversal_plane(s, tgt, c.k_src, n).cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    st = s.stats()
+    assert st.steps == 0                       # reset afterwards
+    s.close()
+    A = orc.Acoustic(c.nx, c.ny, c.nz, c.dx, c.dt, c.index, c.materials, c.f0, n_sls=2,
+                     n_pml=c.n_pml)
+    pt = np.zeros((c.ny, c.nx), dtype=np.complex128)
+    pt[tgt[1], tgt[0]] = 1.0
+    A.set_source(pt, tgt[2], 1500.0, orc.ENV_RAMP_CW)
+    assert A.run(n, peak_from=-1, dft_start=n - 2 * M + 1, dft_steps=2 * M) == 0
+    amp, ph = A.amp_phase(2 * M)
+    P = amp[c.k_src] * np.exp(1j * ph[c.k_src])
+    ref = np.conj(P) / np.abs(P).max()
+    assert np.abs(got).max() == pytest.approx(1.0, abs=1e-6)
+    assert np.abs(got - ref).max() < 2e-4
+
+
+def test_gpu_steered_field_matches_oracle(mods, orc):
+    """A steered 84-element cap in water: the library's weighted Rayleigh plane
+    and FDTD amplitude against the oracle's Rayleigh plane and FP64 FDTD with
+    the same weights (relative L2 of the amplitude < 1e-4)."""
+    bvf, phased, synth = mods
+    nx = ny = 48
+    nz, dx, f0, n_pml = 40, 0.5e-3, 5e5, 4
+    k_src = n_pml + 2
+    dt, M = synth.choose_dt(dx, 1500.0, f0)
+    apex = (23.5 * dx, 23.5 * dx, k_src * dx - 5e-3)
+    base = phased.bowl_array(16e-3, 16e-3, apex, n_rings=6, n_inner=4)
+    el = phased.steer(base, np.array([28.0, 21.0, 26.0]) * dx, f0)
+    plane = bvf.bvf_rs_elements(el, 1e4, 1500.0, nx, ny, dx, k_src * dx, f0)
+    s = bvf.Solver(nx, ny, nz, dx, dt, f0, n_sls=0, n_pml=n_pml)
+    idx = np.zeros((nz, ny, nx), np.uint8)
+    s.set_materials(idx, [synth.water_row(f0)])
+    s.set_source(plane, k_src, 1500.0, bvf.BVF_ENV_RAMP_CW)
+    n = int(1.2 * nz * dx / 1500.0 / dt) + 3 * M
+    s.run(n, dft_start=n - 2 * M + 1, dft_steps=2 * M)
+    s.synchronize()
+    amp = s.amp_phase()[0].cpu().numpy()
+    s.close()
+    ref_plane = orc.rs_elements(el, 1e4, 1500.0, nx, ny, dx, k_src * dx, f0)
+    A = orc.Acoustic(nx, ny, nz, dx, dt, idx, [synth.water_row(f0)], f0, n_sls=0, n_pml=n_pml)
+    A.set_source(ref_plane, k_src, 1500.0, orc.ENV_RAMP_CW)
+    assert A.run(n, peak_from=-1, dft_start=n - 2 * M + 1, dft_steps=2 * M) == 0
+    ref = A.amp_phase(2 * M)[0]
+    assert np.linalg.norm(amp - ref) / np.linalg.norm(ref) < 1e-4
