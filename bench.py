@@ -55,6 +55,8 @@ def parse():
                     help="skip the scaled-FP16-storage leg reported under mixed_precision")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate (Fourier neural operator) inference leg")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 250 / 700 kHz mixed-precision leg (config3)")
     ap.add_argument("--surrogate", action="store_true",
                     help="run only the surrogate inference on --grid and print its line")
     return ap.parse_args()
@@ -81,6 +83,16 @@ def whole_job_rate(world, steps, units_per_step, ms):
     """Units all ranks processed per second, in billions (each rank runs its
     own plans: weak scaling)."""
     return world * steps * units_per_step / (ms / 1e3) / 1e9
+
+
+def bench_config(case, storage):
+    """The workload as both arms name it (descriptors only, no results)."""
+    es = 4 if storage == "f32" else 2
+    return {"workload": workload(case), "grid": [case.nx, case.ny, case.nz],
+            "fdtd_steps": case.n_steps, "runs_per_step": 2, "n_sls": case.n_sls,
+            "n_pml": case.n_pml, "dft_cycles": case.dft_cycles, "storage": storage,
+            "l2": "inputs larger than L2 (state %.0f MB per run)"
+                  % (case.voxels * es * (9 + 6 * case.n_sls) / 1e6)}
 
 
 def make_case(args, rank):
@@ -236,10 +248,11 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sec / max(len(times), 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload(case), "sample": "each step: %d FDTD steps on the full grid"
-                       % times[-1]["steps"]},
+            "config": bench_config(case, args.storage),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"],
-                             "kind": "oracle", "sample": base["sample"]},
+                             "kind": "oracle", "sample": base["sample"] +
+                             "; each bench step: %d FDTD steps on the full grid"
+                             % times[-1]["steps"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -340,9 +353,81 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
             "cpu_baseline": base}
 
 
+def _config3_case(f0):
+    from paper_2301_12727_gb300 import synth
+    return synth.config3_case(f0, *synth.CONFIG3_GRIDS[f0])
+
+
+def config3_leg(cases):
+    """Mixed-precision workload family (9 points per wavelength, 250 kHz on
+    128 x 128 x 108 and 700 kHz on 360 x 360 x 300, transit + 10 cycles, then
+    the BHTE): one warm-up and one timed plan per storage; plan throughput,
+    FDTD kernel time, the FP16-over-FP32 speed-ups, and every output's
+    difference from the FP64 oracle's stored results (planes through the
+    focus, tests/golden/config3_*.npz, written by the oracle alone)."""
+    import torch
+    from paper_2301_12727_gb300 import plan as planmod, synth
+    from tests.golden import config3 as ref3
+    out = {}
+    for f0 in sorted(cases):
+        c = cases[f0]
+        reg = synth.thermal_regime(c.dx, c.materials)
+        regime = planmod.ThermalRegime(dt=reg["dt"], duty=reg["duty"])
+        idx = torch.from_numpy(c.index).cuda()
+        try:
+            meta, ref = ref3.load(f0)
+        except OSError:
+            meta = ref = None          # the oracle's result file is not there
+        vs = 2 * c.n_steps * c.voxels
+        rec = {"grid": [c.nx, c.ny, c.nz], "dx_mm": c.dx * 1e3, "fdtd_steps": c.n_steps,
+               "dft_cycles": c.dft_cycles, "thermal_dt_s": reg["dt"],
+               "voxel_steps_per_plan": vs}
+        for storage in ("f32", "f16"):
+            pl = planmod.Planner(c, storage=storage)
+            pl.run(idx, c.materials, c.bowl, regime)
+            torch.cuda.synchronize()
+            pl.kernel_timing(True)
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = pl.run(idx, c.materials, c.bowl, regime)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            kt = pl.kernel_times()
+            pl.kernel_timing(False)
+            amp, ph = pl.skull.amp_phase()
+            maps = dict(p=pl.skull.pressure(), peak=r.peak, amp=amp, phase=ph, Tmax=r.Tmax,
+                        cem=r.cem43)
+            errs = (ref3.errors(meta, ref, maps, dict(EL=r.EL, TS=r.TS, z_m=r.z_m))
+                    if meta is not None else None)
+            rec[storage] = {"value": vs / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_plan": ms,
+                            "fdtd_kernel_ms": kt["stress_ms"] + kt["velocity_ms"],
+                            "errors_vs_fp64_oracle": errs}
+            del maps, amp, ph, r
+            pl.close()
+        rec["speedup_f16_vs_f32"] = rec["f32"]["ms_per_plan"] / rec["f16"]["ms_per_plan"]
+        rec["fdtd_kernel_speedup_f16_vs_f32"] = (rec["f32"]["fdtd_kernel_ms"]
+                                                 / rec["f16"]["fdtd_kernel_ms"])
+        out["%dkHz" % int(round(f0 / 1e3))] = rec
+        del idx
+        torch.cuda.empty_cache()
+    out["oracle_reference"] = ("FP64 oracle, whole runs on the full grids, stored as planes "
+                               "through the focus (tests/golden/make_config3_reference.py)")
+    return out
+
+
 def run_bvf(args):
     import torch
     rank, world, local = dist_env()
+    c3_future = None
+    if rank == 0 and not args.no_config3:
+        # the config-3 phantoms are generated on the host cores while the
+        # headline is timed (a spawned process: no CUDA state is inherited)
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        c3_pool = cf.ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context("spawn"))
+        c3_future = {f0: c3_pool.submit(_config3_case, f0) for f0 in (250e3, 700e3)}
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
@@ -371,7 +456,6 @@ def run_bvf(args):
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    planner.kernel_timing(True)
     l0 = planner.launches()
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -384,6 +468,18 @@ def run_bvf(args):
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     launches = planner.launches() - l0
+    # kernel roofline pass: the same plans with the water run after the skull
+    # run (not beside it), so that the CUDA events recorded around every
+    # launch on its stream bracket that kernel alone
+    roof_plans = 2
+    planner.kernel_timing(True)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(roof_plans):
+        planner.run(idx_dev, mats, bowl, serial=True)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    ms_serial_plan = r0.elapsed_time(r1) / roof_plans
     kt = planner.kernel_times()
     planner.kernel_timing(False)
     # thermal + auxiliary kernels are counted through the context counters;
@@ -450,15 +546,20 @@ def run_bvf(args):
                                          / max(float(ref.cem43.max()), 1e-300)}}
         pl2.close()
 
+    config3 = None
+    if c3_future is not None:
+        config3 = config3_leg({f0: fut.result() for f0, fut in c3_future.items()})
+        c3_pool.shutdown()
+
     surrogate = None
     if not args.no_surrogate and rank == 0:
         surrogate = surrogate_leg(case, args.steps, args.warmup, ms / args.steps,
-                                  (kt["stress_ms"] + kt["velocity_ms"]) / args.steps,
+                                  (kt["stress_ms"] + kt["velocity_ms"]) / roof_plans,
                                   cpu_baseline=not args.no_cpu_baseline)
 
     # ---- roofline of the dominant kernel (stress + memory variables)
     N = case.voxels
-    n_runs = 2 * args.steps
+    n_runs = 2 * roof_plans          # FDTD runs of the roofline pass
     es = 4.0 if args.storage == "f32" else 2.0      # bytes per state element
     # stress: read 3 v, read + write 6 sigma and 12 memory variables, index
     # byte, FP32 peak read + write (+ FP64 C, S read + write in the DFT window);
@@ -487,21 +588,23 @@ def run_bvf(args):
                               "min_bytes_per_voxel": 42.0 * es + 9.0,
                               "achieved_design": design, "frac_design": design / peak,
                               "achieved_min": minimum, "frac_min": minimum / peak},
-                "fdtd_share_of_step": (kt["stress_ms"] + kt["velocity_ms"]) / ms}
+                "fdtd_share_of_serial_plan": (kt["stress_ms"] + kt["velocity_ms"]) / roof_plans
+                                             / ms_serial_plan,
+                "timing": "per-launch CUDA events on the launching stream in a separate pass of "
+                          "%d plans with the two FDTD runs serialised (the headline plans run "
+                          "the water companion concurrently and record no per-launch events)"
+                          % roof_plans,
+                "plan_ms_serial": ms_serial_plan, "plan_ms_concurrent": ms / args.steps,
+                "concurrency_gain": ms_serial_plan / (ms / args.steps)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "f32" else "f16 storage, f32 arithmetic",
             "data": "synthetic",
-            "config": {"workload": workload(case), "grid": [case.nx, case.ny, case.nz],
-                       "fdtd_steps": case.n_steps, "runs_per_step": 2, "n_sls": case.n_sls,
-                       "n_pml": case.n_pml, "dft_cycles": case.dft_cycles,
-                       "storage": args.storage,
-                       "l2": "inputs larger than L2 (state %.0f MB per run)"
-                             % (N * es * (9 + 6 * case.n_sls) / 1e6),
-                       "EL": res.EL, "TS": res.TS},
+            "config": bench_config(case, args.storage),
+            "results": {"EL": res.EL, "TS": res.TS, "z_m": res.z_m},
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks,
-            "mixed_precision": mixed, "surrogate": surrogate}
+            "mixed_precision": mixed, "config3": config3, "surrogate": surrogate}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(case)
     if rank == 0:

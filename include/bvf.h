@@ -415,6 +415,9 @@ typedef struct {
     int dft_start, dft_steps;    /* amplitude window, whole periods (see bvf_capture) */
     double i_sppa;               /* requested brain I_SPPA (W/m^2); <= 0 selects 5e4 */
     bvf_thermal thermal;         /* regime; its p_scale is ignored (computed) */
+    int serial;                  /* 0: the water run on a second stream of the skull
+                                    context, concurrent with the skull run; 1: both
+                                    on `stream`, one after the other */
 } bvf_plan_params;
 
 typedef struct {
@@ -425,7 +428,11 @@ typedef struct {
 } bvf_plan_result;
 
 /* skull, water: two contexts on the same grid (the water context's materials
- * are set here to the one row h_water with an all-zero index).  d_index
+ * are set here to the one row h_water with an all-zero index).  The two FDTD
+ * runs are independent: by default the water run goes to a second stream
+ * (owned by the skull context) forked from and joined back into `stream`, so
+ * their kernels share the GPU; results are bit for bit those of the serial
+ * order.  d_index
  * (nx*ny*nz bytes) and h_table/n_mat: the skull run's material volume and
  * table.  Outputs, caller-owned device buffers of nx*ny*nz elements: d_peak
  * (float, max |p| of the skull run), d_amp (FP64 skull amplitude at the drive

@@ -80,7 +80,7 @@ class Thermal(ctypes.Structure):
 
 class PlanParams(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int), ("dft_start", ctypes.c_int), ("dft_steps", ctypes.c_int),
-                ("i_sppa", ctypes.c_double), ("thermal", Thermal)]
+                ("i_sppa", ctypes.c_double), ("thermal", Thermal), ("serial", ctypes.c_int)]
 
 
 class PlanOut(ctypes.Structure):

@@ -92,6 +92,9 @@ struct bvf_ctx {
     // test hook of the bounded TMA waits, applied to the next acoustic step
     int hold = 0, hold_plane = -1;
     unsigned hold_limit = 0;
+    // second stream and fork/join events of bvf_plan's concurrent water run
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 struct bvf_batch {
@@ -529,6 +532,9 @@ void bvf_destroy(bvf_ctx *c)
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : c->budget_ev)
         if (e) cudaEventDestroy(e);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side) cudaStreamDestroy(c->side);
     delete c;
 }
 
@@ -1177,7 +1183,12 @@ int bvf_plan(bvf_ctx *skull, bvf_ctx *water, const uint8_t *d_index, const bvf_m
         release();
         return cuda_fail(nullptr, e, "bvf_plan: temporaries");
     }
+    bool forked = false;      // work on the skull context's second stream not yet joined
     auto done = [&](int code) {
+        if (forked) {         // join before the temporaries are released on `stream`
+            cudaEventRecord(skull->join_ev, skull->side);
+            cudaStreamWaitEvent(s, skull->join_ev, 0);
+        }
         release();
         return code;
     };
@@ -1185,15 +1196,38 @@ int bvf_plan(bvf_ctx *skull, bvf_ctx *water, const uint8_t *d_index, const bvf_m
     if ((rc = bvf_rs_plane(bowl, g.nx, g.ny, g.dx, k_src * g.dx, skull->ph.f0, src, stream)) != BVF_OK)
         return done(rc);
     const bvf_capture cap{0, pp->dft_start, pp->dft_steps};
+    // the water run on the skull context's second stream, forked after the
+    // source plane exists and joined before the reductions (serial: `stream`)
+    void *ws = stream;
+    if (!pp->serial) {
+        if (!skull->side) {
+            e = cudaStreamCreateWithFlags(&skull->side, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&skull->fork_ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&skull->join_ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return done(cuda_fail(nullptr, e, "bvf_plan: second stream"));
+        }
+        e = cudaEventRecord(skull->fork_ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(skull->side, skull->fork_ev, 0);
+        if (e != cudaSuccess) return done(cuda_fail(nullptr, e, "bvf_plan: fork"));
+        ws = skull->side;
+        forked = true;
+    }
     bvf_ctx *runs[2] = {skull, water};
     for (bvf_ctx *c : runs) {
-        if ((rc = bvf_reset(c, stream)) != BVF_OK) return done(rc);
-        if ((rc = bvf_set_source(c, k_src, src, bowl->c0, BVF_ENV_RAMP_CW, 0, stream)) != BVF_OK)
+        void *cs = (c == water) ? ws : stream;
+        if ((rc = bvf_reset(c, cs)) != BVF_OK) return done(rc);
+        if ((rc = bvf_set_source(c, k_src, src, bowl->c0, BVF_ENV_RAMP_CW, 0, cs)) != BVF_OK)
             return done(rc);
-        if ((rc = bvf_run_acoustic(c, pp->n_steps, &cap, stream)) != BVF_OK) return done(rc);
+        if ((rc = bvf_run_acoustic(c, pp->n_steps, &cap, cs)) != BVF_OK) return done(rc);
     }
     if ((rc = bvf_get_amp_phase(skull, d_amp, nullptr, stream)) != BVF_OK) return done(rc);
-    if ((rc = bvf_get_amp_phase(water, amp_w, nullptr, stream)) != BVF_OK) return done(rc);
+    if ((rc = bvf_get_amp_phase(water, amp_w, nullptr, ws)) != BVF_OK) return done(rc);
+    if (forked) {
+        forked = false;
+        e = cudaEventRecord(skull->join_ev, skull->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, skull->join_ev, 0);
+        if (e != cudaSuccess) return done(cuda_fail(nullptr, e, "bvf_plan: join"));
+    }
     if ((rc = bvf_get_peak(skull, d_peak, stream)) != BVF_OK) return done(rc);
     for (bvf_ctx *c : runs)
         if ((rc = bvf_synchronize(c, stream)) != BVF_OK) return done(rc);

@@ -94,10 +94,11 @@ class Planner:
                     stress_ms=a.stress_ms + b.stress_ms)
 
     def run(self, index, materials, bowl: dict, regime: ThermalRegime | None = None,
-            i_sppa_brain: float = I_SPPA_BRAIN_DEFAULT) -> PlanResult:
+            i_sppa_brain: float = I_SPPA_BRAIN_DEFAULT, serial: bool = False) -> PlanResult:
         """index: (nz, ny, nx) uint8 CUDA tensor; materials: (n, 9) rows; bowl:
         aperture, roc, apex, dir, p0 (see bvf_bowl).  One bvf_plan call; the
-        outputs are fresh tensors of this run."""
+        outputs are fresh tensors of this run.  serial: run the water
+        companion after the skull run instead of beside it (same results)."""
         import torch
         c = self.case
         regime = regime or ThermalRegime()
@@ -109,7 +110,8 @@ class Planner:
         cem = torch.empty(shape, dtype=torch.float64, device="cuda")
         th = bvf.Thermal(regime.dt, regime.n_on, regime.n_off, regime.duty, regime.T_a,
                          regime.rhob_cb, 0.0)
-        pp = bvf.PlanParams(c.n_steps, c.dft_start, c.dft_steps, i_sppa_brain, th)
+        pp = bvf.PlanParams(c.n_steps, c.dft_start, c.dft_steps, i_sppa_brain, th,
+                            1 if serial else 0)
         r = bvf.bvf_plan(self.skull, self.water, index, materials, self.water_table[0],
                          dict(bowl), c.k_src, pp, peak, amp, T, Tmax, cem)
         return PlanResult(peak, amp, None, Tmax, cem, r.EL, r.TS, r.z_m, r.Iw_max, r.p_scale,

@@ -239,6 +239,33 @@ def skull_case(nx: int = 240, ny: int = 240, nz: int = 200, dx: float = 0.5e-3,
                 mats, k_src, 2, plane=None, bowl=bowl, n_pml=n_pml, dft_cycles=dft_cycles)
 
 
+def config3_case(f0: float, nx: int, ny: int, nz: int, seed: int = 1234) -> Case:
+    """Mixed-precision workload family: the skull phantom at 9 points per
+    water wavelength (dx = 1500 / (9 f0): 0.667 mm at 250 kHz, 0.238 mm at
+    700 kHz), run for the transit of 1.3 x the domain depth plus 10 cycles that
+    enter the FP64 amplitude window."""
+    return skull_case(nx, ny, nz, dx=1500.0 / (9.0 * f0), f0=f0, n_steps=None, seed=seed,
+                      dft_cycles=10)
+
+
+# Config-3 grids: the same physical domain (85 x 85 x 72 mm) at 250 and 700 kHz.
+CONFIG3_GRIDS = {250e3: (128, 128, 108), 700e3: (360, 360, 300)}
+
+
+def thermal_regime(dx: float, materials=None) -> dict:
+    """Exposure of Sec. 4.1.1 (40 s on at 30 % duty cycle, 80 s off) with the
+    largest thermal step among 0.1, 0.05, 0.025 ... s that keeps the explicit
+    scheme stable on every tissue, dt <= dx^2 min(rho c_th / k_th) / 6."""
+    rows = np.asarray(materials if materials is not None else
+                      [water_row(0.0), skin_row(0.0), brain_row(0.0)], dtype=np.float64)
+    lim = dx * dx * float((rows[:, 0] * rows[:, 6] / rows[:, 5]).min()) / 6.0
+    dt = 0.1
+    while dt > lim:
+        dt *= 0.5
+    return dict(dt=dt, n_on=int(round(40.0 / dt)), n_off=int(round(80.0 / dt)), duty=0.3,
+                T_a=37.0, rhob_cb=1050.0 * 3617.0)
+
+
 def water_like(case: Case) -> Case:
     """The same grid, source and run filled with water only (the companion run
     used for the energy-loss factor, Sec. 2.3 / Sec. 2.4)."""
