@@ -22,10 +22,17 @@ namespace bvf {
 
 namespace {
 
-using st::dbw;
-using st::dfw;
 using st::cpml;
 using st::slab_pos;
+
+__device__ __forceinline__ float dfw(float a, float b, float c, float d, st::Dx x)
+{
+    return st::dfw<float>(a, b, c, d, x);
+}
+__device__ __forceinline__ float dbw(float a, float b, float c, float d, st::Dx x)
+{
+    return st::dbw<float>(a, b, c, d, x);
+}
 
 constexpr int TX = 32, TY = 8, H = 2;
 constexpr int SW = TX + 2 * H;           // tile row length (36)
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (xs >= 0) d1 = cpml(p.psx + 0 * Sxs + qx, pmlx[p.nmax + g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 0 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 0 * Szs + qz, pmlz[k], d3);
-                ux += st::vel_increment(dt, p.buoy, p.n_mat, m0, mx, d1, d2, d3);
+                ux = st::vel_step(dt, st::buoyancy(p.buoy, p.n_mat, m0, mx), ux, d1, d2, d3);
                 st::stv(vx + q, ux);
             }
             if (jy1) {
@@ -186,7 +193,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (xs >= 0) d1 = cpml(p.psx + 1 * Sxs + qx, pmlx[g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 1 * Sys + qy, pmly[p.nmax + g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 1 * Szs + qz, pmlz[k], d3);
-                uy += st::vel_increment(dt, p.buoy, p.n_mat, m0, my, d1, d2, d3);
+                uy = st::vel_step(dt, st::buoyancy(p.buoy, p.n_mat, m0, my), uy, d1, d2, d3);
                 st::stv(vy + q, uy);
             }
             if (kz1) {
@@ -196,7 +203,7 @@ __global__ void __launch_bounds__(NTH, 3) k_velocity(AcParams p, int kchunk)
                 if (xs >= 0) d1 = cpml(p.psx + 2 * Sxs + qx, pmlx[g.i], d1);
                 if (ys >= 0) d2 = cpml(p.psy + 2 * Sys + qy, pmly[g.j], d2);
                 if (zs >= 0) d3 = cpml(p.psz + 2 * Szs + qz, pmlz[p.nmax + k], d3);
-                uz += st::vel_increment(dt, p.buoy, p.n_mat, m0, mz, d1, d2, d3);
+                uz = st::vel_step(dt, st::buoyancy(p.buoy, p.n_mat, m0, mz), uz, d1, d2, d3);
                 st::stv(vz + q, uz);
             }
         }
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
             float srcv = 0.0f;
             if ((p.st.flags & kStepSource) && k == p.k_src) {
                 const float2 a = p.src[g.col];
-                srcv = p.src_scale * fmaf(a.x, p.st.src_ws, a.y * p.st.src_wc);
+                srcv = st::source_value<float>(p.src_scale, a.x, a.y, p.st.src_ws, p.st.src_wc);
             }
             st::normal_update<L>(p, c0, exx, eyy, ezz, srcv, sv, rv);
             const float pr = st::pressure(sv);
@@ -306,21 +313,21 @@ __global__ void __launch_bounds__(NTH, L <= 2 ? 3 : 2) k_stress(AcParams p, int 
                 float b = dfw(tvy[c - 1], tvy[c], tvy[c + 1], tvy[c + 2], ix);
                 if (ys >= 0) a = cpml(p.psy + 4 * Sys + qy, pmly[p.nmax + g.j], a);
                 if (xs >= 0) b = cpml(p.psx + 4 * Sxs + qx, pmlx[p.nmax + g.i], b);
-                shear(3, m10, m01, m11, a + b);
+                shear(3, m10, m01, m11, st::vadd(a, b));
             }
             if (dxz) {                               // sxz at (i+1/2, j, k+1/2)
                 float a = dfw(ax0, ax1, ax2, ax3, ix);
                 float b = dfw(tvz[c - 1], tvz[c], tvz[c + 1], tvz[c + 2], ix);
                 if (zs >= 0) a = cpml(p.psz + 4 * Szs + qz, pmlz[p.nmax + k], a);
                 if (xs >= 0) b = cpml(p.psx + 5 * Sxs + qx, pmlx[p.nmax + g.i], b);
-                shear(4, m10, mz0, mz1, a + b);
+                shear(4, m10, mz0, mz1, st::vadd(a, b));
             }
             if (dyz) {                               // syz at (i, j+1/2, k+1/2)
                 float a = dfw(ay0, ay1, ay2, ay3, ix);
                 float b = dfw(tvz[c - SW], tvz[c], tvz[c + SW], tvz[c + 2 * SW], ix);
                 if (zs >= 0) a = cpml(p.psz + 5 * Szs + qz, pmlz[p.nmax + k], a);
                 if (ys >= 0) b = cpml(p.psy + 5 * Sys + qy, pmly[p.nmax + g.j], b);
-                shear(5, m01, mz0, mzy, a + b);
+                shear(5, m01, mz0, mzy, st::vadd(a, b));
             }
 
             // ---- stores

@@ -2,27 +2,39 @@
 //
 // Same arithmetic as the direct kernels in bvf_acoustic.cu, but every array
 // moves between HBM and shared memory through the tensor-memory accelerator:
-//   * a block of 32 x 8 threads owns one x-y tile and walks a chunk of z;
+//   * a block owns one 32 x 8 x-y tile and walks a chunk of z; in the
+//     velocity kernel (16 x 8 threads) thread (tx, ty) updates the voxel pair
+//     (x0 + 2 tx, x0 + 2 tx + 1) of row y0 + ty, in the stress kernel (32 x 8
+//     threads) one voxel each;
 //   * stencil inputs arrive as halo'd boxes (the tile plus XO columns on each
 //     side in x and 2 rows in y; out-of-range elements zero-filled by the TMA,
 //     which gives the zero ghosts) held in per-array rings of z-planes that
 //     serve the 4-point z-stencils as well;
 //   * the 1-byte material index arrives as 48 x 9 boxes (planes k and k+1);
+//   * velocity pairs: a y- or z-stencil is four paired shared-memory reads,
+//     an x-stencil three (elements -2 .. +3 around the pair); the velocities
+//     and the y- and z-slab CPML memories move as paired global accesses; the
+//     FP32 arithmetic runs on the packed FP32x2 instructions (bit for bit two
+//     single-voxel evaluations, see bvf_stencil.cuh); buoyancies and the
+//     x-slab CPML stay per voxel.  This halves the velocity kernel's
+//     instructions, which bound it.  The stress kernel is bound by the latency
+//     of its per-voxel streams instead: it keeps one voxel per thread (64
+//     registers, 32 resident warps per SM) and prefetches the next plane's
+//     streams into L2;
 //   * velocity kernel: each stress array arrives in a box with exactly the
 //     halo its stencil needs; the velocities go straight to registers and
 //     back; copies for plane k+1 are issued while plane k is computed;
 //   * stress kernel: the velocity and index rings run two planes ahead; the
-//     per-voxel arrays (stresses, memory variables, peak map, FP64 DFT sums)
-//     go straight to registers with loads issued at the top of each plane and
-//     back with coalesced stores, which keeps shared memory small enough for
-//     four resident blocks per SM;
+//     per-voxel arrays go straight to registers with loads issued at the top
+//     of each plane and back with coalesced stores;
 //   * one thread issues every copy; one __syncthreads and one bounded mbarrier
 //     wait per plane.
 // The state is stored as T = float or __half (scaled FP16 storage; the
 // arithmetic is FP32 either way).  A TMA box must start on a 16-byte boundary
 // in x, so the x-halo is XO = 16 / sizeof(T) columns: 4 floats or 8 halves.
-// Used when rows are whole multiples of 16 bytes of the index (nx % 16 == 0)
-// and L <= 2.
+// Used when rows are whole multiples of 16 bytes of the index (nx % 16 == 0,
+// so every pair lies inside the grid and every paired access is aligned) and
+// L <= 2.
 #include <cuda_fp16.h>
 
 #include <type_traits>
@@ -36,10 +48,15 @@ namespace {
 
 using st::dbw;
 using st::dfw;
+using st::pair;
 using st::slab_pos;
 using st::tof;
+using st::splat;
+using st::vadd;
 
-constexpr int TX = 32, TY = 8, NTH = TX * TY;
+constexpr int TX = 32, TY = 8;                      // voxels of a tile
+constexpr int PX = TX / 2;                          // threads per tile row (a pair each)
+constexpr int NTH = PX * TY;                        // 128
 constexpr int IW = 48, IH = 9, IT = IW * IH;        // index box: x0 .. x0+47, y0 .. y0+8
 constexpr int IT_SLOT = 512;                        // bytes per index slot
 
@@ -52,6 +69,55 @@ struct Box {
     static constexpr int VH = TY + 4;                 // 2 rows each side
     static constexpr int VT = BW * VH;                // full-halo box (elements)
 };
+
+// the pair of elements (x, x+1) at an even offset of a shared-memory box
+template <typename T>
+__device__ __forceinline__ float2 lds2(const T *p)
+{
+    return st::ld2(p);
+}
+
+// x-stencils of a pair from three aligned pair reads a = (f[-2], f[-1]),
+// b = (f[0], f[1]), c = (f[2], f[3]) around the pair's first voxel:
+// D+ at x + 1/2 reads f[-1 .. 2] (first voxel) and f[0 .. 3] (second),
+// D- at x reads f[-2 .. 1] and f[-1 .. 2].
+__device__ __forceinline__ float2 dfw_x(float2 a, float2 b, float2 c, st::Dx d)
+{
+    return st::dfw<float2>(pair(a.y, b.x), b, pair(b.y, c.x), c, d);
+}
+__device__ __forceinline__ float2 dbw_x(float2 a, float2 b, float2 c, st::Dx d)
+{
+    return st::dbw<float2>(a, pair(a.y, b.x), b, pair(b.y, c.x), d);
+}
+
+// one lane of a pair
+__device__ __forceinline__ float lane(float2 v, int l) { return l ? v.y : v.x; }
+__device__ __forceinline__ void set_lane(float2 &v, int l, float x)
+{
+    if (l)
+        v.y = x;
+    else
+        v.x = x;
+}
+
+// Time-out of a bounded ring wait.  The thread whose wait ran out records
+// the plane in the block's abort word; every thread reads that word right
+// after the next block barrier, so all of them leave the plane loop at the
+// same point and no copy is issued after it.  Thread 0 then waits, again
+// bounded, for the phases the block has armed (planes a .. a + ahead, at most
+// one per barrier), sets bit 2 of the context flag and the tile ends.
+// Barrier and parity of a plane t = pl - k0 of the chunk: velocity ring
+// bar t % 2, phase t / 2; stress ring bar t % 3, phase t / 3.
+template <int NBAR>
+__device__ __forceinline__ void drain_after_timeout(uint64_t *bars, int a, int ahead, int k0,
+                                                    int k1, unsigned limit, int *flag)
+{
+    for (int pl = a; pl <= a + ahead && pl < k1; ++pl) {
+        const int t = pl - k0;
+        tma::mbar_wait(&bars[t % NBAR], (unsigned)(t / NBAR) & 1u, limit);
+    }
+    atomicOr(flag, 2);
+}
 
 // ---------------------------------------------------------------- velocity
 // Each stress array arrives in a box holding the halo its stencil reads:
@@ -88,25 +154,6 @@ struct VelLayout {
                   "TMA destinations must stay 128-byte aligned");
 };
 
-// Time-out of a bounded ring wait.  The thread whose wait ran out records
-// the plane in the block's abort word; every thread reads that word right
-// after the next block barrier, so all of them leave the plane loop at the
-// same point and no copy is issued after it.  Thread 0 then waits, again
-// bounded, for the phases the block has armed (planes a .. a + ahead, at most
-// one per barrier), sets bit 2 of the context flag and the tile ends.
-// Barrier and parity of a plane t = pl - k0 of the chunk: velocity ring
-// bar t % 2, phase t / 2; stress ring bar t % 3, phase t / 3.
-template <int NBAR>
-__device__ __forceinline__ void drain_after_timeout(uint64_t *bars, int a, int ahead, int k0,
-                                                    int k1, unsigned limit, int *flag)
-{
-    for (int pl = a; pl <= a + ahead && pl < k1; ++pl) {
-        const int t = pl - k0;
-        tma::mbar_wait(&bars[t % NBAR], (unsigned)(t / NBAR) & 1u, limit);
-    }
-    atomicOr(flag, 2);
-}
-
 // One tile (bx, by) of the grid over z-chunk bz.  REUSE: the block runs
 // further tiles afterwards (persistent batch kernel), so its mbarriers are
 // invalidated at the end and the first copies are fenced against the
@@ -125,11 +172,11 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
     volatile int *s_abort = reinterpret_cast<volatile int *>(smb + Lay::off_abort);
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PX + tx;
     const int x0 = bx * TX, y0 = by * TY;
-    const int i = x0 + tx, j = y0 + ty;
+    const int i = x0 + 2 * tx, j = y0 + ty;         // the pair (i, i+1) of row j
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const bool live = i < nx && j < ny;
+    const bool live = i < nx && j < ny;              // nx is even: i + 1 < nx as well
     const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
     if (tid == 0) {
         tma::mbar_init(&bars[0], 1);
@@ -173,29 +220,33 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
 
     const st::Dx ix = st::make_dx(p.inv_dx);
     const float dt = p.dtv;
-    // per-thread centres inside a slot (elements): x-halo box, y-halo box,
-    // full-halo box, plain box; index box (bytes)
-    const int cx = ty * XW + tx + Bx::XO;
-    const int cy = (ty + 2) * YW + tx;
-    const int cxy = (ty + 2) * VW + tx + Bx::XO;
-    const int cI = ty * IW + tx;
-    const int xs = slab_pos(i, nx, p.P), ys = slab_pos(j, ny, p.P);
+    // per-thread centres inside a slot (elements, all even): x-halo box,
+    // y-halo box, full-halo box, plain box; index box (bytes)
+    const int cx = ty * XW + 2 * tx + Bx::XO;
+    const int cy = (ty + 2) * YW + 2 * tx;
+    const int cxy = (ty + 2) * VW + 2 * tx + Bx::XO;
+    const int cz = ty * TX + 2 * tx;
+    const int cI = ty * IW + 2 * tx;
+    const int xs[2] = {slab_pos(i, nx, p.P), slab_pos(i + 1, nx, p.P)};
+    const int ys = slab_pos(j, ny, p.P);
     const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
     const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
     T *__restrict__ vxg = static_cast<T *>(p.vx);
     T *__restrict__ vyg = static_cast<T *>(p.vy);
     T *__restrict__ vzg = static_cast<T *>(p.vz);
-    const bool ix1 = i < nx - 1, jy1 = j < ny - 1;
+    // the pair's second voxel is not the last point in x (the first never is)
+    const bool ix1 = i + 1 < nx - 1, jy1 = j < ny - 1;
     const int plane = nx * ny, col = j * nx + i;
     // velocities of the plane being computed, loaded one plane ahead
-    float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+    float2 ux = pair(0.0f, 0.0f), uy = ux, uz = ux;
     if (live) {
-        ux = tof(vxg[k0 * plane + col]);
-        uy = tof(vyg[k0 * plane + col]);
-        uz = tof(vzg[k0 * plane + col]);
+        ux = st::ld2(vxg + k0 * plane + col);
+        uy = st::ld2(vyg + k0 * plane + col);
+        uz = st::ld2(vzg + k0 * plane + col);
     }
-    int q = k0 * plane + col;                       // this voxel in plane k
-    int ox = (k0 * ny + j) * p.W + xs;              // in the x-slab (xs >= 0)
+    int q = k0 * plane + col;                       // this pair in plane k
+    int ox[2] = {(k0 * ny + j) * p.W + xs[0],       // in the x-slab (xs >= 0)
+                 (k0 * ny + j) * p.W + xs[1]};
     int oy = (k0 * p.W + ys) * nx + i;              // in the y-slab (ys >= 0)
     const int dox = ny * p.W, doy = p.W * nx;
 
@@ -222,33 +273,38 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
                     ldI(k + 2, (u + 2) % Lay::RI, bar);
                 }
             }
-            float nux = 0.0f, nuy = 0.0f, nuz = 0.0f;
+            float2 nux = pair(0.0f, 0.0f), nuy = nux, nuz = nux;
             if (live && k + 1 < k1) {
-                nux = tof(vxg[q + plane]);
-                nuy = tof(vyg[q + plane]);
-                nuz = tof(vzg[q + plane]);
+                nux = st::ld2(vxg + q + plane);
+                nuy = st::ld2(vyg + q + plane);
+                nuz = st::ld2(vzg + q + plane);
             }
-            // CPML memories of this voxel (components 0-2 of each slab it lies
-            // in), all loads issued together before the ring wait
+            // CPML memories of this pair (components 0-2 of each slab it lies
+            // in), all loads issued together before the ring wait; the x-slab
+            // is per voxel, the y- and z-slabs per pair
             const int zs = slab_pos(k, nz, p.P);
             const int oz = zs * plane + col;
-            float qx[3] = {0.0f, 0.0f, 0.0f}, qy[3] = {0.0f, 0.0f, 0.0f},
-                  qz[3] = {0.0f, 0.0f, 0.0f};
+            float qx[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+            float2 qy[3] = {pair(0.0f, 0.0f), pair(0.0f, 0.0f), pair(0.0f, 0.0f)};
+            float2 qz[3] = {qy[0], qy[0], qy[0]};
             if (live) {
-                if (xs >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) qx[c] = p.psx[c * Sxs + ox];
-                }
+                for (int l = 0; l < 2; ++l)
+                    if (xs[l] >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) qx[l][c] = p.psx[c * Sxs + ox[l]];
+                    }
                 if (ys >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) qy[c] = p.psy[c * Sys + oy];
+                    for (int c = 0; c < 3; ++c) qy[c] = st::ld2(p.psy + c * Sys + oy);
                 }
                 if (zs >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) qz[c] = p.psz[c * Szs + oz];
+                    for (int c = 0; c < 3; ++c) qz[c] = st::ld2(p.psz + c * Szs + oz);
                 }
             }
-            const bool ready = tma::mbar_wait(&bars[u & 1], mpar ^ ((u >> 1) & 1u), p.wait_limit);
+            const bool ready =
+                tma::mbar_wait(&bars[u & 1], mpar ^ ((u >> 1) & 1u), p.wait_limit);
             if (!ready) *s_abort = k;
             if (ready && live) {
                 // fixed slots of this unrolled copy
@@ -258,10 +314,10 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
                 const T *Bm1 = smt + Lay::off_b / Lay::ES + ((u + 1) % Lay::RB) * Lay::SB;
                 const T *B0 = smt + Lay::off_b / Lay::ES + ((u + 2) % Lay::RB) * Lay::SB;
                 const T *Bp1 = smt + Lay::off_b / Lay::ES + ((u + 3) % Lay::RB) * Lay::SB;
-                const T *Cm1 = smt + Lay::off_c / Lay::ES + ((u + 0) % Lay::RC) * TZZ + tid;
-                const T *C0 = smt + Lay::off_c / Lay::ES + ((u + 1) % Lay::RC) * TZZ + tid;
-                const T *Cp1 = smt + Lay::off_c / Lay::ES + ((u + 2) % Lay::RC) * TZZ + tid;
-                const T *Cp2 = smt + Lay::off_c / Lay::ES + ((u + 3) % Lay::RC) * TZZ + tid;
+                const T *Cm1 = smt + Lay::off_c / Lay::ES + ((u + 0) % Lay::RC) * TZZ + cz;
+                const T *C0 = smt + Lay::off_c / Lay::ES + ((u + 1) % Lay::RC) * TZZ + cz;
+                const T *Cp1 = smt + Lay::off_c / Lay::ES + ((u + 2) % Lay::RC) * TZZ + cz;
+                const T *Cp2 = smt + Lay::off_c / Lay::ES + ((u + 3) % Lay::RC) * TZZ + cz;
                 const unsigned char *I0 = smb + Lay::off_i + (u % Lay::RI) * IT_SLOT + cI;
                 const unsigned char *I1 = smb + Lay::off_i + ((u + 1) % Lay::RI) * IT_SLOT + cI;
                 const T *XZ = B0 + cx, *YZ = B0 + TXX + cy;
@@ -269,65 +325,75 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
 
                 // all three components are computed; ghost points (the last
                 // half point of each axis) are simply not stored
-                float ax1 = dfw(tof(XX[-1]), tof(XX[0]), tof(XX[1]), tof(XX[2]), ix);
-                float ax2 = dbw(tof(XY[-2 * VW]), tof(XY[-VW]), tof(XY[0]), tof(XY[VW]), ix);
-                float ax3 = dbw(tof(Bm2[cx]), tof(Bm1[cx]), tof(XZ[0]), tof(Bp1[cx]), ix);
-                float ay1 = dbw(tof(XY[-2]), tof(XY[-1]), tof(XY[0]), tof(XY[1]), ix);
-                float ay2 = dfw(tof(YY[-YW]), tof(YY[0]), tof(YY[YW]), tof(YY[2 * YW]), ix);
-                float ay3 = dbw(tof(Bm2[TXX + cy]), tof(Bm1[TXX + cy]), tof(YZ[0]),
-                                tof(Bp1[TXX + cy]), ix);
-                float az1 = dbw(tof(XZ[-2]), tof(XZ[-1]), tof(XZ[0]), tof(XZ[1]), ix);
-                float az2 = dbw(tof(YZ[-2 * YW]), tof(YZ[-YW]), tof(YZ[0]), tof(YZ[YW]), ix);
-                float az3 = dfw(tof(*Cm1), tof(*C0), tof(*Cp1), tof(*Cp2), ix);
-                if (xs >= 0) {
-                    const float2 h = __ldg(&pmlx[p.nmax + i]), w = __ldg(&pmlx[i]);
-                    float t = fmaf(h.x, ax1, h.y * qx[0]);
-                    if (ix1) p.psx[ox] = t;
-                    ax1 += t;
-                    t = fmaf(w.x, ay1, w.y * qx[1]);
-                    if (jy1) p.psx[Sxs + ox] = t;
-                    ay1 += t;
-                    t = fmaf(w.x, az1, w.y * qx[2]);
-                    if (kz1) p.psx[2 * Sxs + ox] = t;
-                    az1 += t;
+                float2 ax1 = dfw_x(lds2(XX - 2), lds2(XX), lds2(XX + 2), ix);
+                float2 ax2 = st::dbw<float2>(lds2(XY - 2 * VW), lds2(XY - VW), lds2(XY),
+                                             lds2(XY + VW), ix);
+                float2 ax3 = st::dbw<float2>(lds2(Bm2 + cx), lds2(Bm1 + cx), lds2(XZ),
+                                             lds2(Bp1 + cx), ix);
+                float2 ay1 = dbw_x(lds2(XY - 2), lds2(XY), lds2(XY + 2), ix);
+                float2 ay2 = st::dfw<float2>(lds2(YY - YW), lds2(YY), lds2(YY + YW),
+                                             lds2(YY + 2 * YW), ix);
+                float2 ay3 = st::dbw<float2>(lds2(Bm2 + TXX + cy), lds2(Bm1 + TXX + cy), lds2(YZ),
+                                             lds2(Bp1 + TXX + cy), ix);
+                float2 az1 = dbw_x(lds2(XZ - 2), lds2(XZ), lds2(XZ + 2), ix);
+                float2 az2 = st::dbw<float2>(lds2(YZ - 2 * YW), lds2(YZ - YW), lds2(YZ),
+                                             lds2(YZ + YW), ix);
+                float2 az3 = st::dfw<float2>(lds2(Cm1), lds2(C0), lds2(Cp1), lds2(Cp2), ix);
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    if (xs[l] < 0) continue;
+                    const float2 h = __ldg(&pmlx[p.nmax + i + l]), w = __ldg(&pmlx[i + l]);
+                    float t, d;
+                    d = st::cpml_v(qx[l][0], h.x, h.y, lane(ax1, l), t);
+                    if (l == 0 || ix1) p.psx[ox[l]] = t;
+                    set_lane(ax1, l, d);
+                    d = st::cpml_v(qx[l][1], w.x, w.y, lane(ay1, l), t);
+                    if (jy1) p.psx[Sxs + ox[l]] = t;
+                    set_lane(ay1, l, d);
+                    d = st::cpml_v(qx[l][2], w.x, w.y, lane(az1, l), t);
+                    if (kz1) p.psx[2 * Sxs + ox[l]] = t;
+                    set_lane(az1, l, d);
                 }
                 if (ys >= 0) {
                     const float2 h = __ldg(&pmly[p.nmax + j]), w = __ldg(&pmly[j]);
-                    float t = fmaf(w.x, ax2, w.y * qy[0]);
-                    if (ix1) p.psy[oy] = t;
-                    ax2 += t;
-                    t = fmaf(h.x, ay2, h.y * qy[1]);
-                    if (jy1) p.psy[Sys + oy] = t;
-                    ay2 += t;
-                    t = fmaf(w.x, az2, w.y * qy[2]);
-                    if (kz1) p.psy[2 * Sys + oy] = t;
-                    az2 += t;
+                    float2 t;
+                    ax2 = st::cpml_v(qy[0], splat<float2>(w.x), splat<float2>(w.y), ax2, t);
+                    st::st2_or_1(p.psy + oy, t, ix1);
+                    ay2 = st::cpml_v(qy[1], splat<float2>(h.x), splat<float2>(h.y), ay2, t);
+                    if (jy1) st::st2(p.psy + Sys + oy, t);
+                    az2 = st::cpml_v(qy[2], splat<float2>(w.x), splat<float2>(w.y), az2, t);
+                    if (kz1) st::st2(p.psy + 2 * Sys + oy, t);
                 }
                 if (zs >= 0) {
                     const float2 h = __ldg(&pmlz[p.nmax + k]), w = __ldg(&pmlz[k]);
-                    float t = fmaf(w.x, ax3, w.y * qz[0]);
-                    if (ix1) p.psz[oz] = t;
-                    ax3 += t;
-                    t = fmaf(w.x, ay3, w.y * qz[1]);
-                    if (jy1) p.psz[Szs + oz] = t;
-                    ay3 += t;
-                    t = fmaf(h.x, az3, h.y * qz[2]);
-                    if (kz1) p.psz[2 * Szs + oz] = t;
-                    az3 += t;
+                    float2 t;
+                    ax3 = st::cpml_v(qz[0], splat<float2>(w.x), splat<float2>(w.y), ax3, t);
+                    st::st2_or_1(p.psz + oz, t, ix1);
+                    ay3 = st::cpml_v(qz[1], splat<float2>(w.x), splat<float2>(w.y), ay3, t);
+                    if (jy1) st::st2(p.psz + Szs + oz, t);
+                    az3 = st::cpml_v(qz[2], splat<float2>(h.x), splat<float2>(h.y), az3, t);
+                    if (kz1) st::st2(p.psz + 2 * Szs + oz, t);
                 }
-                const int m0 = I0[0], nm = p.n_mat;
-                const float nvx = ux + st::vel_increment(dt, p.buoy, nm, m0, I0[1], ax1, ax2, ax3);
-                const float nvy = uy + st::vel_increment(dt, p.buoy, nm, m0, I0[IW], ay1, ay2, ay3);
-                const float nvz = uz + st::vel_increment(dt, p.buoy, nm, m0, I1[0], az1, az2, az3);
-                if (ix1) st::stv(vxg + q, nvx);
-                if (jy1) st::stv(vyg + q, nvy);
-                if (kz1) st::stv(vzg + q, nvz);
+                // buoyancy of each voxel's velocity point from the two cells'
+                // materials: (i, i+1), (j, j+1), (k, k+1)
+                const int nm = p.n_mat;
+                const int ma = I0[0], mb = I0[1];
+                const float2 bxv = pair(st::buoyancy(p.buoy, nm, ma, mb),
+                                        st::buoyancy(p.buoy, nm, mb, I0[2]));
+                const float2 byv = pair(st::buoyancy(p.buoy, nm, ma, I0[IW]),
+                                        st::buoyancy(p.buoy, nm, mb, I0[IW + 1]));
+                const float2 bzv = pair(st::buoyancy(p.buoy, nm, ma, I1[0]),
+                                        st::buoyancy(p.buoy, nm, mb, I1[1]));
+                st::st2_or_1(vxg + q, st::vel_step(dt, bxv, ux, ax1, ax2, ax3), ix1);
+                if (jy1) st::st2(vyg + q, st::vel_step(dt, byv, uy, ay1, ay2, ay3));
+                if (kz1) st::st2(vzg + q, st::vel_step(dt, bzv, uz, az1, az2, az3));
             }
             ux = nux;
             uy = nuy;
             uz = nuz;
             q += plane;
-            ox += dox;
+            ox[0] += dox;
+            ox[1] += dox;
             oy += doy;
         }
     }
@@ -345,7 +411,7 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTH, 5)
+__global__ void __launch_bounds__(NTH, 6)
     k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
                    const __grid_constant__ VelocityTmaMaps tm)
 {
@@ -373,6 +439,11 @@ struct StressLayout {
                   "TMA destinations must stay 128-byte aligned");
 };
 
+// One voxel per thread (block of 32 x 8 threads, 256): the stress update is
+// bound by the latency of its per-voxel streams rather than by issue, and
+// one voxel per thread keeps 64 registers and 32 resident warps per SM.
+constexpr int SNTH = TX * TY;
+
 // One tile (bx, by) over z-chunk bz; REUSE and the result as for velocity_tile.
 template <int L, typename T, bool REUSE>
 __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMaps &tm,
@@ -393,7 +464,7 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;
     const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
-    for (int m = tid; m < p.n_mat; m += NTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
+    for (int m = tid; m < p.n_mat; m += SNTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
     if (tid == 0) {
         for (int b = 0; b < 3; ++b) tma::mbar_init(&bars[b], 1);
         tma::mbar_init_fence();
@@ -439,6 +510,42 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
         vP2 = vP1 + 3 * VT;
     int iK = ibase + ci, iK1 = iK + IT_SLOT;
 
+    // L2 prefetch of the next plane's per-voxel rows.  A tile row of one
+    // stream is 32 elements (stresses, the peak map), 32 L (the memory
+    // variables of a component, mechanisms adjacent) or 32 doubles (the DFT
+    // sums); its 128-byte lines are numbered over all streams and thread
+    // (row r, slot a) prefetches line a of row y0 + r.  Every line starts at
+    // an element of the row segment, inside its array.
+    const int pf_r = tid >> 5, pf_a = tid & 31;
+    const bool pk_on = (st.flags & kStepPeak) != 0, dft_on = (st.flags & kStepDft) != 0;
+    constexpr int LS = (32 * (int)sizeof(T) + 127) / 128;              // lines of a stress row
+    constexpr int LM = (32 * (L > 0 ? L : 1) * (int)sizeof(T) + 127) / 128;   // of a memory row
+    const int n_lines = 6 * LS + (L > 0 ? 6 * LM : 0) + (pk_on ? 1 : 0) + (dft_on ? 4 : 0);
+    const T *st0 = static_cast<const T *>(p.sxx);     // stresses: consecutive arrays, fstride apart
+    auto prefetch_plane = [&](int kp) {
+        if (kp >= k1 || y0 + pf_r >= ny || pf_a >= n_lines) return;
+        const size_t e = (size_t)kp * nx * ny + (size_t)(y0 + pf_r) * nx + x0;
+        int a = pf_a;
+        const char *ln;
+        if (a < 6 * LS) {
+            ln = reinterpret_cast<const char *>(st0 + (size_t)(a / LS) * p.fstride + e) + (a % LS) * 128;
+        } else if ((a -= 6 * LS) < (L > 0 ? 6 * LM : 0)) {
+            ln = reinterpret_cast<const char *>(mem + mem_index(0, a / LM, e, p.fstride, L)) +
+                 (a % LM) * 128;
+        } else {
+            a -= (L > 0 ? 6 * LM : 0);
+            if (pk_on && a == 0) {
+                ln = reinterpret_cast<const char *>(p.peak + e);
+            } else {
+                a -= pk_on ? 1 : 0;                    // 0, 1: dftC lines; 2, 3: dftS lines
+                if ((a & 1) && x0 + 16 >= nx) return;
+                ln = reinterpret_cast<const char *>(((a >> 1) ? p.dftS : p.dftC) + e) + (a & 1) * 128;
+            }
+        }
+        tma::prefetch_l2(ln);
+    };
+    prefetch_plane(k0);
+
     // Blocks whose tile touches no CPML slab in x or y and holds no ghost
     // or out-of-grid point run a copy of the loop without that code.
     const bool edge = !(x0 >= p.P && x0 + TX - 1 < nx - p.P - 1 && y0 >= p.P &&
@@ -454,6 +561,7 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
             tma::fence_async_smem();
             issue(k + 2, &bars[(it + 2) % 3], false);
         }
+        prefetch_plane(k + 1);
         const int q = k * (nx * ny) + j * nx + i;
         // per-voxel loads first, in flight while the ring wait and the
         // derivatives proceed
@@ -522,7 +630,7 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
             float srcv = 0.0f;
             if ((st.flags & kStepSource) && k == p.k_src) {
                 const float2 a = p.src[j * nx + i];
-                srcv = p.src_scale * fmaf(a.x, st.src_ws, a.y * st.src_wc);
+                srcv = st::source_value<float>(p.src_scale, a.x, a.y, st.src_ws, st.src_wc);
             }
             st::normal_update<L>(p, c0, exx, eyy, ezz, srcv, sv, rv);
             const float pr = st::pressure(sv);
@@ -536,34 +644,34 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
                 float b = dfw(tof(smt[vy - 1]), tof(smt[vy]), tof(smt[vy + 1]), tof(smt[vy + 2]), ix);
                 if (EDGE && ys >= 0) {
                     const float2 h = __ldg(&pmly[p.nmax + j]);
-                    const float t = fmaf(h.x, a, h.y * qy[1]);
+                    float t;
+                    a = st::cpml_v(qy[1], h.x, h.y, a, t);
                     if (dxy) p.psy[4 * Sys + oy] = t;
-                    a += t;
                 }
                 if (EDGE && xs >= 0) {
                     const float2 h = __ldg(&pmlx[p.nmax + i]);
-                    const float t = fmaf(h.x, b, h.y * qx[1]);
+                    float t;
+                    b = st::cpml_v(qx[1], h.x, h.y, b, t);
                     if (dxy) p.psx[4 * Sxs + ox] = t;
-                    b += t;
                 }
-                st::shear_update<L>(p, s_lut, c0, m00, I0[1], I0[IW], I0[IW + 1], a + b, 3, sv, rv);
+                st::shear_update<L>(p, s_lut, c0, m00, I0[1], I0[IW], I0[IW + 1], st::vadd(a, b), 3, sv, rv);
             }
             {                                        // sxz at (i+1/2, j, k+1/2)
                 float a = dfw(tof(smt[vm1]), tof(smt[vx]), tof(smt[vp1]), tof(smt[vp2]), ix);
                 float b = dfw(tof(smt[vz - 1]), tof(smt[vz]), tof(smt[vz + 1]), tof(smt[vz + 2]), ix);
                 if (zs >= 0) {
                     const float2 h = __ldg(&pmlz[p.nmax + k]);
-                    const float t = fmaf(h.x, a, h.y * qz[1]);
+                    float t;
+                    a = st::cpml_v(qz[1], h.x, h.y, a, t);
                     if (dxz) p.psz[4 * Szs + oz] = t;
-                    a += t;
                 }
                 if (EDGE && xs >= 0) {
                     const float2 h = __ldg(&pmlx[p.nmax + i]);
-                    const float t = fmaf(h.x, b, h.y * qx[2]);
+                    float t;
+                    b = st::cpml_v(qx[2], h.x, h.y, b, t);
                     if (dxz) p.psx[5 * Sxs + ox] = t;
-                    b += t;
                 }
-                st::shear_update<L>(p, s_lut, c0, m00, I0[1], I1[0], I1[1], a + b, 4, sv, rv);
+                st::shear_update<L>(p, s_lut, c0, m00, I0[1], I1[0], I1[1], st::vadd(a, b), 4, sv, rv);
             }
             {                                        // syz at (i, j+1/2, k+1/2)
                 float a = dfw(tof(smt[vm1 + VT]), tof(smt[vy]), tof(smt[vp1 + VT]),
@@ -572,17 +680,17 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
                               tof(smt[vz + 2 * VW]), ix);
                 if (zs >= 0) {
                     const float2 h = __ldg(&pmlz[p.nmax + k]);
-                    const float t = fmaf(h.x, a, h.y * qz[2]);
+                    float t;
+                    a = st::cpml_v(qz[2], h.x, h.y, a, t);
                     if (dyz) p.psz[5 * Szs + oz] = t;
-                    a += t;
                 }
                 if (EDGE && ys >= 0) {
                     const float2 h = __ldg(&pmly[p.nmax + j]);
-                    const float t = fmaf(h.x, b, h.y * qy[2]);
+                    float t;
+                    b = st::cpml_v(qy[2], h.x, h.y, b, t);
                     if (dyz) p.psy[5 * Sys + oy] = t;
-                    b += t;
                 }
-                st::shear_update<L>(p, s_lut, c0, m00, I0[IW], I1[0], I1[IW], a + b, 5, sv, rv);
+                st::shear_update<L>(p, s_lut, c0, m00, I0[IW], I1[0], I1[IW], st::vadd(a, b), 5, sv, rv);
             }
 
             // ---- results (ghost points are not written)
@@ -596,7 +704,7 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
                 const bool w = cc < 3 || (cc == 3 && dxy) || (cc == 4 && dxz) || (cc == 5 && dyz);
                 if (!w) continue;
                 if constexpr (L == 2)
-                    st::st2(mem + mem_index(0, cc, q, p.fstride, 2), rv[0][cc], rv[1][cc]);
+                    st::st2(mem + mem_index(0, cc, q, p.fstride, 2), pair(rv[0][cc], rv[1][cc]));
                 else if constexpr (L == 1)
                     st::stv(mem + mem_index(0, cc, q, p.fstride, 1), rv[0][cc]);
             }
@@ -631,7 +739,7 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
 }
 
 template <int L, int MINB, typename T>
-__global__ void __launch_bounds__(NTH, MINB)
+__global__ void __launch_bounds__(SNTH, MINB)
     k_stress_tma(const __grid_constant__ AcParams p, int kchunk,
                  const __grid_constant__ StressTmaMaps tm)
 {
@@ -685,12 +793,12 @@ __device__ __forceinline__ void walk_next(WalkState &ws, const BatchParams &bp)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTH, 5)
+__global__ void __launch_bounds__(NTH, 6)
     k_velocity_batch(const __grid_constant__ BatchParams bp, const int *step_ctr)
 {
     extern __shared__ __align__(1024) unsigned char smb[];
     __shared__ WalkState ws;
-    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int tid = threadIdx.y * PX + threadIdx.x;
     walk_begin(ws, step_ctr, tid);
     for (;;) {
         __syncthreads();
@@ -711,7 +819,7 @@ __global__ void __launch_bounds__(NTH, 5)
 }
 
 template <int L, int MINB, typename T>
-__global__ void __launch_bounds__(NTH, MINB)
+__global__ void __launch_bounds__(SNTH, MINB)
     k_stress_batch(const __grid_constant__ BatchParams bp, const int *step_ctr)
 {
     extern __shared__ __align__(1024) unsigned char smb[];
@@ -758,7 +866,7 @@ static cudaError_t launch_velocity_tma_t(const AcParams &p, const VelocityTmaMap
     cudaError_t e = cudaFuncSetAttribute(k_velocity_tma<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_velocity_tma<T><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    k_velocity_tma<T><<<grid_tma(p, kc), dim3(PX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
 }
 
@@ -790,8 +898,8 @@ static cudaError_t launch_stress_tma_l(const AcParams &p, const StressTmaMaps &t
     }
 }
 
-// Four resident blocks per SM (64 registers, about 46 KB of shared memory in
-// FP32 storage).
+// Four resident blocks of 256 threads per SM (64 registers, about 46 KB of
+// shared memory each in FP32 storage).
 cudaError_t launch_stress_tma(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     return p.h16 ? launch_stress_tma_l<__half>(p, tm, s) : launch_stress_tma_l<float>(p, tm, s);
@@ -812,7 +920,7 @@ static cudaError_t batch_prepare_t(int n_mat_max, int *gv, int *gs)
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bv, k_velocity_batch<T>, NTH, smv);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stress_batch<L, 4, T>, NTH, sms);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_stress_batch<L, 4, T>, SNTH, sms);
     if (e != cudaSuccess) return e;
     *gv = sm_count * (bv > 0 ? bv : 1);
     *gs = sm_count * (bs > 0 ? bs : 1);
@@ -824,7 +932,7 @@ static cudaError_t launch_batch_t(const BatchParams &bp, int n_mat_max, int *d_s
                                   cudaStream_t s)
 {
     const size_t smv = VelLayout<T>::bytes(n_mat_max), sms = StressLayout<L, T>::bytes(n_mat_max);
-    k_velocity_batch<T><<<gv, dim3(TX, TY, 1), smv, s>>>(bp, d_step);
+    k_velocity_batch<T><<<gv, dim3(PX, TY, 1), smv, s>>>(bp, d_step);
     k_stress_batch<L, 4, T><<<gs, dim3(TX, TY, 1), sms, s>>>(bp, d_step);
     k_step_advance<<<1, 1, 0, s>>>(d_step);
     return cudaGetLastError();

@@ -355,7 +355,7 @@ AcParams make_params(bvf_ctx *c)
     for (int l = 0; l < c->L; ++l) {
         const double h = c->g.dt / (2.0 * c->tau_sigma[l]);
         p.ca[l] = (float)((1.0 - h) / (1.0 + h));
-        p.cb[l] = (float)((c->g.dt / c->tau_sigma[l]) / (1.0 + h) * (c->s_v / c->s_r));
+        p.ncb[l] = -(float)((c->g.dt / c->tau_sigma[l]) / (1.0 + h) * (c->s_v / c->s_r));
     }
     p.idx = c->index;
     p.lut = c->lut;

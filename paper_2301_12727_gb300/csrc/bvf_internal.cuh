@@ -62,7 +62,8 @@ enum { kStepSource = 1, kStepPeak = 2, kStepDft = 4 };
 // arithmetic on the stored values (all scales 1 for float storage):
 //   velocity  dtv = dt S_sigma / S_v
 //   stress    dt (the stress step) = dt S_v / S_sigma, memory-variable sum
-//             weight rh = S_r / (2 S_v), cb_l divided by S_r / S_v
+//             weight rh = S_r / (2 S_v), cb_l divided by S_r / S_v (held
+//             negated: ncb_l = -cb_l)
 //   source    src_scale divided by S_sigma
 // Captured p (peak map, DFT sums) is in units of S_sigma.
 struct AcParams {
@@ -72,7 +73,7 @@ struct AcParams {
     int n_mat;
     int h16;             // state stored as scaled FP16
     float dt, dtv, inv_dx, Lf, rh;
-    float ca[BVF_MAX_SLS], cb[BVF_MAX_SLS];
+    float ca[BVF_MAX_SLS], ncb[BVF_MAX_SLS];
     const uint8_t *idx;
     const MatCoef *lut;
     const float *buoy;   // 2 / (rho_a + rho_b) of every material pair, [a * n_mat + b]

@@ -68,6 +68,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
     return false;
 }
 
+// bring the 128-byte line holding p into L2 ahead of its use (no register
+// result; the address lies inside an allocation)
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // order this thread's generic-proxy shared-memory accesses before later
 // async-proxy (TMA) accesses
 __device__ __forceinline__ void fence_async_smem()
