@@ -110,6 +110,75 @@ int bvf_fno_features(const uint8_t *d_index, const bvf_material *h_table, int n_
 int bvf_fno_timing(bvf_fno *f, int enable);
 int bvf_fno_stage_times(bvf_fno *f, double *ms_out);
 
+/* ---- BF16 tensor-core product ---------------------------------------------
+ * C = alpha A B + beta C (+ bias) (-> GELU) on the fifth-generation tensor
+ * cores: A, B and C are FP32 arrays in device memory, the operands are
+ * rounded to BF16 and the products accumulate in FP32.  The surrogate's BF16
+ * inference and its training are built from this product (no counterpart in
+ * the paper).  Element (m, k) of A is A[b sab + m sam + k sak] for batch b,
+ * (k, n) of B is B[b sbb + k sbk + n sbn], (m, n) of C is C[b scb + m scm +
+ * n scn]; any strides (elements), so transposed and batched views need no
+ * copies.  bias_mode 1 adds bias[n], 2 adds bias[m]; act 1 applies GELU and,
+ * when C_pre is not NULL, stores the value before GELU there (same strides as
+ * C); act 2 multiplies the result by GELU'(C_pre) (the backward of act 1, with
+ * C_pre holding the forward pre-activation).  ksplit > 1 splits K over that many blocks that add alpha A B into C
+ * atomically (then beta must be 1, with no bias and no activation).
+ * d_flag: a device int that receives bit 2 if a bounded wait for the tensor
+ * cores ran out (the blocks concerned leave their tile of C unwritten).
+ * Asynchronous on `stream`.  Errors: BVF_E_ARG, BVF_E_CUDA. */
+typedef struct bvf_gemm {
+    const float *A;
+    long long sam, sak, sab;
+    const float *B;
+    long long sbk, sbn, sbb;
+    float *C;
+    long long scm, scn, scb;
+    float *C_pre;
+    const float *bias;
+    int bias_mode;
+    int M, N, K, batch, ksplit;
+    float alpha, beta;
+    int act;           /* 0 none, 1 GELU, 2 times GELU'(C_pre) */
+} bvf_gemm;
+int bvf_gemm_bf16(const bvf_gemm *g, int *d_flag, void *stream);
+
+/* ---- BF16 inference and training ----------------------------------------
+ * The same network with every contraction on the BF16 tensor-core product
+ * (bvf_gemm_bf16): the lift, W v + b and the projection as channel products;
+ * each Fourier layer's truncated transform as three products (x: real ->
+ * kept modes, y and z: complex, as real 2 x 2 blocks) with axis permutes in
+ * between, the inverse likewise with the real-inverse weights c(kx)/N (c = 1
+ * for kx = 0, 2 otherwise); the mode mix in FP32 (no counterpart in the
+ * paper: planning-time inference and training of the surrogate).  A context
+ * is sized for one grid and up to max_batch samples and keeps FP32 master
+ * weights, their gradient, Adam moments and every activation the backward pass
+ * needs.  Inputs [batch][c_in][nz][ny][nx], outputs [batch][c_out][...],
+ * FP32 device memory.
+ *
+ * Loss of a batch (bvf_fno_bf16_gradient / _adam): the mean over samples of
+ * the relative L2 error ||out_0 - target|| / ||target|| of output channel 0
+ * (d_target [batch][nz][ny][nx]), plus, if c_out >= 2, el_weight times the
+ * mean squared difference between the spatial mean of output channel 1 and
+ * d_el[b] (the sample's transmission efficiency E_L; NULL when el_weight is
+ * 0).  d_grad (n floats, the blob layout, may be NULL) receives the gradient;
+ * *h_loss (may be NULL) the loss, which makes the call wait for `stream`.
+ * bvf_fno_bf16_adam takes one Adam step (beta1 0.9, beta2 0.999, eps 1e-8,
+ * learning rate lr) on the context's weights; bvf_fno_bf16_weights copies them
+ * out (synchronous).  bvf_fno_bf16_synchronize reports BVF_E_CUDA if a bounded
+ * tensor-core wait ran out.  Errors: BVF_E_ARG, BVF_E_NOMEM, BVF_E_CUDA. */
+typedef struct bvf_fno_bf16 bvf_fno_bf16;
+int bvf_fno_bf16_create(bvf_fno_bf16 **out, const bvf_fno_dims *d, const float *h_weights, size_t n,
+                        int nx, int ny, int nz, int max_batch);
+int bvf_fno_bf16_destroy(bvf_fno_bf16 *t);
+int bvf_fno_bf16_forward(bvf_fno_bf16 *t, int batch, const float *d_in, float *d_out, void *stream);
+int bvf_fno_bf16_gradient(bvf_fno_bf16 *t, int batch, const float *d_in, const float *d_target,
+                          const float *d_el, double el_weight, float *d_grad, double *h_loss,
+                          void *stream);
+int bvf_fno_bf16_adam(bvf_fno_bf16 *t, int batch, const float *d_in, const float *d_target,
+                      const float *d_el, double el_weight, double lr, double *h_loss, void *stream);
+int bvf_fno_bf16_weights(bvf_fno_bf16 *t, float *h_weights);
+int bvf_fno_bf16_synchronize(bvf_fno_bf16 *t, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

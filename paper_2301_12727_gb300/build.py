@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbvf.so")
 SOURCES = ("bvf_api.cu", "bvf_acoustic.cu", "bvf_acoustic_tma.cu", "bvf_aux.cu",
-           "bvf_noalloc.cu", "bvf_fno.cu")
+           "bvf_noalloc.cu", "bvf_fno.cu", "bvf_gemm_bf16.cu",
+           "bvf_fno_bf16.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-cudart", "shared", "--expt-relaxed-constexpr"]

@@ -28,6 +28,7 @@
 
 #include "../../include/bvf_fno.h"
 #include "bvf_internal.cuh"
+#include "bvf_tc.cuh"
 #include "bvf_tma.cuh"
 
 namespace {
@@ -598,90 +599,7 @@ k_row_mma(const float *__restrict__ vin, int cin, const float2 *Ap, const float 
     }
 }
 
-// ------------------------------------------------- tcgen05 (TF32, TMEM)
-// Fifth-generation tensor-core products: operands in shared memory in the
-// canonical K-major layout without swizzle (core matrices of 8 rows x 16
-// bytes, 128 contiguous bytes each; LBO = byte step between core matrices
-// along K, SBO = byte step between 8-row groups), the FP32 accumulator in
-// tensor memory, one thread issuing tcgen05.mma, completion through
-// tcgen05.commit on an mbarrier, and tcgen05.ld to bring rows back.
-namespace tc {
-
-__device__ __forceinline__ uint64_t smem_desc(const void *p, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = (uint64_t)((bvf::tma::saddr(p) >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;                      // descriptor version; no swizzle
-    return d;
-}
-
-// kind::tf32 instruction descriptor: D FP32, A and B TF32, both K-major
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void alloc(uint32_t *dst, uint32_t ncols)
-{
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     bvf::tma::saddr(dst)),
-                 "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void relinquish()
-{
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void dealloc(uint32_t taddr, uint32_t ncols)
-{
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int acc)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-                 : "memory");
-}
-__device__ __forceinline__ void commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     bvf::tma::saddr(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// 32 consecutive columns of this warp's 32 lanes: thread i of the warp gets
-// row (lane base + i), columns col .. col+31
-__device__ __forceinline__ void ld32(uint32_t taddr, float (&r)[32])
-{
-    uint32_t u[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]),
-                   "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]),
-                   "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]),
-                   "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
-                   "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]),
-                   "=r"(u[30]), "=r"(u[31])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
-}
-
-// byte offset of element (row, k) in a K-major TF32 operand with K columns
-__host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K)
-{
-    return (uint32_t)((((row >> 3) * (K >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
-}
-
-}  // namespace tc
+// tcgen05 helpers (descriptors, TMEM, products): bvf_tc.cuh
 
 // ------------------------------------------------ tcgen05 projection
 // out[k][p] = q2[k] + sum_j Q2[k][j] GELU(q1[j] + sum_c Q1[j][c] v[c][p]) on

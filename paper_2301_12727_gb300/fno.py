@@ -14,7 +14,10 @@ import numpy as np
 from . import bvf
 
 EXPORTS = ("bvf_fno_weight_count", "bvf_fno_create", "bvf_fno_destroy", "bvf_fno_forward",
-           "bvf_fno_features", "bvf_fno_timing", "bvf_fno_stage_times", "bvf_fno_synchronize")
+           "bvf_fno_features", "bvf_fno_timing", "bvf_fno_stage_times", "bvf_fno_synchronize",
+           "bvf_gemm_bf16", "bvf_fno_bf16_create", "bvf_fno_bf16_destroy", "bvf_fno_bf16_forward",
+           "bvf_fno_bf16_gradient", "bvf_fno_bf16_adam", "bvf_fno_bf16_weights",
+           "bvf_fno_bf16_synchronize")
 N_FEATURES = 8
 N_STAGES = 9
 STAGES = ("lift", "dft_x", "dft_y", "dft_z", "mix", "idft_z", "idft_y", "out_x_pointwise",
@@ -27,6 +30,18 @@ class FnoDims(ctypes.Structure):
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Gemm(ctypes.Structure):
+    """bvf_gemm (include/bvf_fno.h): strided views of FP32 device arrays."""
+    _fields_ = [("A", ctypes.c_void_p), ("sam", ctypes.c_longlong), ("sak", ctypes.c_longlong),
+                ("sab", ctypes.c_longlong), ("B", ctypes.c_void_p), ("sbk", ctypes.c_longlong),
+                ("sbn", ctypes.c_longlong), ("sbb", ctypes.c_longlong), ("C", ctypes.c_void_p),
+                ("scm", ctypes.c_longlong), ("scn", ctypes.c_longlong), ("scb", ctypes.c_longlong),
+                ("C_pre", ctypes.c_void_p), ("bias", ctypes.c_void_p), ("bias_mode", ctypes.c_int),
+                ("M", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int),
+                ("batch", ctypes.c_int), ("ksplit", ctypes.c_int), ("alpha", ctypes.c_float),
+                ("beta", ctypes.c_float), ("act", ctypes.c_int)]
 
 
 _declared = False
@@ -48,8 +63,34 @@ def lib():
         L.bvf_fno_timing.argtypes = [vp, i]
         L.bvf_fno_stage_times.argtypes = [vp, ctypes.POINTER(d)]
         L.bvf_fno_synchronize.argtypes = [vp, vp]
+        L.bvf_gemm_bf16.argtypes = [ctypes.POINTER(Gemm), vp, vp]
+        L.bvf_fno_bf16_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(FnoDims), vp,
+                                          ctypes.c_size_t, i, i, i, i]
+        L.bvf_fno_bf16_destroy.argtypes = [vp]
+        L.bvf_fno_bf16_forward.argtypes = [vp, i, vp, vp, vp]
+        L.bvf_fno_bf16_gradient.argtypes = [vp, i, vp, vp, vp, d, vp, ctypes.POINTER(d), vp]
+        L.bvf_fno_bf16_adam.argtypes = [vp, i, vp, vp, vp, d, d, ctypes.POINTER(d), vp]
+        L.bvf_fno_bf16_weights.argtypes = [vp, vp]
+        L.bvf_fno_bf16_synchronize.argtypes = [vp, vp]
         _declared = True
     return L
+
+
+def bvf_gemm_bf16(A, a_strides, B, b_strides, C, c_strides, M, N, K, batch=1, ksplit=1,
+                  alpha=1.0, beta=0.0, bias=None, bias_mode=0, act=0, C_pre=None, flag=None,
+                  stream=None):
+    """C = alpha A B + beta C (+ bias) (-> GELU) with BF16 operands on the tensor
+    cores; strides in elements as (m, k, batch), (k, n, batch), (m, n, batch).
+    flag: a one-element int32 CUDA tensor receiving bit 2 on a timed-out wait."""
+    import torch
+    ptr = lambda t: t.data_ptr() if t is not None else None
+    g = Gemm(ptr(A), *a_strides, ptr(B), *b_strides, ptr(C), *c_strides, ptr(C_pre), ptr(bias),
+             bias_mode, M, N, K, batch, ksplit, alpha, beta, act)
+    if flag is None:
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bvf._check(lib().bvf_gemm_bf16(ctypes.byref(g), ctypes.c_void_p(flag.data_ptr()),
+                                   bvf._stream(stream)))
+    return flag
 
 
 def bvf_fno_weight_count(dims: FnoDims) -> int:
@@ -169,3 +210,72 @@ def predict_amplitude(net: Surrogate, index, table, water_row, f0, k_src, src, p
     if fdtd is None:
         raise RuntimeError("surrogate prediction outside its trained range and no FDTD fallback")
     return fdtd(), "fdtd"
+
+
+class Bf16Net:
+    """The surrogate with BF16 tensor-core products (bvf_fno_bf16_*): inference
+    of batches of feature volumes and training (loss gradient, Adam steps) on
+    one grid.  Argument marshalling only."""
+
+    def __init__(self, dims, weights, grid, max_batch=1):
+        self.dims = dims if isinstance(dims, FnoDims) else FnoDims(**dims)
+        self.nx, self.ny, self.nz = grid
+        self.max_batch = max_batch
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        h = ctypes.c_void_p()
+        bvf._check(lib().bvf_fno_bf16_create(ctypes.byref(h), ctypes.byref(self.dims),
+                                             w.ctypes.data_as(ctypes.c_void_p), w.size, self.nx,
+                                             self.ny, self.nz, max_batch))
+        self.h = h
+        self.n_w = w.size
+
+    def close(self):
+        if self.h:
+            lib().bvf_fno_bf16_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, x, out=None, stream=None):
+        """x: [batch, c_in, nz, ny, nx] float32 CUDA tensor."""
+        import torch
+        b = x.shape[0]
+        if out is None:
+            out = torch.empty((b, self.dims.c_out, self.nz, self.ny, self.nx), dtype=torch.float32,
+                              device="cuda")
+        bvf._check(lib().bvf_fno_bf16_forward(self.h, b, bvf._ptr(x, torch.float32),
+                                              bvf._ptr(out, torch.float32), bvf._stream(stream)))
+        return out
+
+    def gradient(self, x, target, el=None, el_weight=0.0, stream=None):
+        """(loss, gradient as a float32 CUDA tensor in the blob layout)."""
+        import torch
+        g = torch.empty(self.n_w, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_double()
+        bvf._check(lib().bvf_fno_bf16_gradient(
+            self.h, x.shape[0], bvf._ptr(x, torch.float32), bvf._ptr(target, torch.float32),
+            bvf._ptr(el, torch.float32) if el is not None else None, float(el_weight),
+            bvf._ptr(g, torch.float32), ctypes.byref(loss), bvf._stream(stream)))
+        return loss.value, g
+
+    def adam(self, x, target, lr, el=None, el_weight=0.0, stream=None):
+        """One Adam step on a batch; returns the batch loss before the step."""
+        import torch
+        loss = ctypes.c_double()
+        bvf._check(lib().bvf_fno_bf16_adam(
+            self.h, x.shape[0], bvf._ptr(x, torch.float32), bvf._ptr(target, torch.float32),
+            bvf._ptr(el, torch.float32) if el is not None else None, float(el_weight), float(lr),
+            ctypes.byref(loss), bvf._stream(stream)))
+        return loss.value
+
+    def weights(self):
+        w = np.empty(self.n_w, dtype=np.float32)
+        bvf._check(lib().bvf_fno_bf16_weights(self.h, w.ctypes.data_as(ctypes.c_void_p)))
+        return w
+
+    def synchronize(self, stream=None):
+        bvf._check(lib().bvf_fno_bf16_synchronize(self.h, bvf._stream(stream)))
