@@ -179,6 +179,11 @@ int bvf_fno_bf16_adam(bvf_fno_bf16 *t, int batch, const float *d_in, const float
 int bvf_fno_bf16_weights(bvf_fno_bf16 *t, float *h_weights);
 int bvf_fno_bf16_synchronize(bvf_fno_bf16 *t, void *stream);
 
+/* Mean of n floats of device memory (FP64 sum): the transmission efficiency
+ * E_L read from the spatial mean of a surrogate output channel.  Waits for
+ * `stream`.  Errors: BVF_E_ARG, BVF_E_CUDA. */
+int bvf_fno_mean(const float *d_x, size_t n, double *h_mean, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

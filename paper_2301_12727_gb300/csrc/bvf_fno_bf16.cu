@@ -243,6 +243,17 @@ __global__ void k_loss_grad(const float *__restrict__ out, const float *__restri
     }
 }
 
+// sum of n floats into *out (FP64)
+__global__ void k_sum(const float *__restrict__ x, size_t n, double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        acc += x[i];
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m1,
                        float *__restrict__ m2, size_t n, float lr, float b1, float b2, float eps,
                        float c1, float c2)
@@ -770,6 +781,26 @@ int bvf_fno_bf16_weights(bvf_fno_bf16 *t, float *h_weights)
     BCK(cudaDeviceSynchronize(), "bvf_fno_bf16_weights");
     BCK(cudaMemcpy(h_weights, t->w, t->n_w * sizeof(float), cudaMemcpyDeviceToHost),
         "bvf_fno_bf16_weights");
+    return BVF_OK;
+}
+
+int bvf_fno_mean(const float *d_x, size_t n, double *h_mean, void *stream)
+{
+    if (!d_x || !h_mean || n == 0) return b16_fail(BVF_E_ARG, "bvf_fno_mean: bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *d = nullptr;
+    BCK(cudaMallocAsync((void **)&d, sizeof(double), s), "bvf_fno_mean");
+    double h = 0.0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(double), s);
+    if (e == cudaSuccess) {
+        k_sum<<<grid_for((long long)n), 256, 0, s>>>(d_x, n, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    BCK(e, "bvf_fno_mean");
+    *h_mean = h / (double)n;
     return BVF_OK;
 }
 

@@ -17,7 +17,7 @@ EXPORTS = ("bvf_fno_weight_count", "bvf_fno_create", "bvf_fno_destroy", "bvf_fno
            "bvf_fno_features", "bvf_fno_timing", "bvf_fno_stage_times", "bvf_fno_synchronize",
            "bvf_gemm_bf16", "bvf_fno_bf16_create", "bvf_fno_bf16_destroy", "bvf_fno_bf16_forward",
            "bvf_fno_bf16_gradient", "bvf_fno_bf16_adam", "bvf_fno_bf16_weights",
-           "bvf_fno_bf16_synchronize")
+           "bvf_fno_bf16_synchronize", "bvf_fno_mean")
 N_FEATURES = 8
 N_STAGES = 9
 STAGES = ("lift", "dft_x", "dft_y", "dft_z", "mix", "idft_z", "idft_y", "out_x_pointwise",
@@ -72,6 +72,7 @@ def lib():
         L.bvf_fno_bf16_adam.argtypes = [vp, i, vp, vp, vp, d, d, ctypes.POINTER(d), vp]
         L.bvf_fno_bf16_weights.argtypes = [vp, vp]
         L.bvf_fno_bf16_synchronize.argtypes = [vp, vp]
+        L.bvf_fno_mean.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(d), vp]
         _declared = True
     return L
 
@@ -210,6 +211,15 @@ def predict_amplitude(net: Surrogate, index, table, water_row, f0, k_src, src, p
     if fdtd is None:
         raise RuntimeError("surrogate prediction outside its trained range and no FDTD fallback")
     return fdtd(), "fdtd"
+
+
+def bvf_fno_mean(x, stream=None) -> float:
+    """Mean of a float32 CUDA tensor (e.g. the transmission channel of an output)."""
+    import torch
+    v = ctypes.c_double()
+    bvf._check(lib().bvf_fno_mean(bvf._ptr(x, torch.float32), x.numel(), ctypes.byref(v),
+                                  bvf._stream(stream)))
+    return v.value
 
 
 class Bf16Net:

@@ -1,17 +1,25 @@
-"""Training of the surrogate on FDTD fields (offline tool).
+"""Training of the surrogate on fields the FDTD of this library computes,
+with the library's hand-written BF16 tensor-core kernels (offline tool).
 
-Training data come from the CUDA FDTD of this package (bvf.Solver): seeded
-synthetic skulls with tilted bowls (synth.sweep_case), the FP64 amplitude of
-the ramped-CW field over the capture window as the target (divided by the
-bowl's surface pressure), and the feature volume of bvf_fno_features as the
-input.  The network is the one of include/bvf_fno.h, trained with PyTorch
-autograd: an offline step, not the planning-time path.  The trained weights
-are exported in the flat blob layout and evaluated through the CUDA inference
-(fno.Surrogate) on held-out skulls: relative L2 error of the field, error of
-the focal amplitude (the field maximum) and distance between the predicted
-and the FDTD focus.
+Data: seeded synthetic skulls with tilted bowls (synth.sweep_case) on one
+grid; each placement runs one plan of the library (bvf_plan through
+plan.Planner: the skull FDTD and its water companion, E_L on the plane of
+maximal water intensity; no thermal step).  Targets: output channel 0 is the
+FP64 skull-run amplitude over the capture window divided by the bowl's
+surface pressure, channel 1's spatial mean is the transmission efficiency
+E_L.  Inputs: the 8-channel feature volume of bvf_fno_features.
 
-    python -m paper_2301_12727_gb300.fno_train --train 400 --test 40 --epochs 30
+Training: bvf_fno_bf16_adam (forward, loss, backward and the Adam step all in
+the library's BF16 kernels; no autograd, no framework FFT), one-cycle
+learning rate.  Evaluation on held-out skulls with the trained weights,
+through both CUDA inference paths (TF32 three-product and BF16): relative L2
+error of the field, error of the focal amplitude (the field maximum),
+distance between the predicted and the FDTD focus, and the E_L error; then
+the time of one plan of the library on the same grid against one surrogate
+inference (feature volume + network), i.e. the speed-up on the workload the
+accuracy is measured on.
+
+    python -m paper_2301_12727_gb300.fno_train --train 1000 --test 100 --epochs 20
 """
 from __future__ import annotations
 
@@ -22,98 +30,62 @@ import time
 
 import numpy as np
 
+FEATURES = 8
+
 
 def make_dataset(n, seed, grid, dx, f0, dft_cycles=6):
-    """n (features, target) pairs on one grid; returns CUDA tensors
-    [n, 8, nz, ny, nx] and [n, 1, nz, ny, nx] (float32)."""
+    """n placements on one grid: features [n, 8, nz, ny, nx], amplitude / p0
+    [n, nz, ny, nx] (float32 CUDA tensors) and E_L [n] (float32)."""
     import torch
-    from . import bvf, fno, synth
+    from . import bvf, fno, plan, synth
     nx, ny, nz = grid
-    feats = torch.empty((n, 8, nz, ny, nx), dtype=torch.float32, device="cuda")
-    amps = torch.empty((n, 1, nz, ny, nx), dtype=torch.float32, device="cuda")
+    feats = torch.empty((n, FEATURES, nz, ny, nx), dtype=torch.float32, device="cuda")
+    amps = torch.empty((n, nz, ny, nx), dtype=torch.float32, device="cuda")
+    els = torch.empty(n, dtype=torch.float32, device="cuda")
     rng = np.random.default_rng(seed)
-    sol = None
+    planner, dt0 = None, None
+    no_heat = plan.ThermalRegime(t_on=0.0, t_off=0.0)
     for i in range(n):
         spec = dict(nx=nx, ny=ny, nz=nz, f0=f0, dx=dx, tilt_deg=float(rng.uniform(-15.0, 15.0)),
                     seed=int(seed) * 100000 + i)
         c = synth.sweep_case(spec, dft_cycles=dft_cycles)
-        if sol is None:
-            sol = bvf.Solver(nx, ny, nz, dx, c.dt, f0, n_sls=c.n_sls, n_pml=c.n_pml)
-            dt0 = c.dt
+        if planner is None:
+            planner, dt0 = plan.Planner(c), c.dt
         if c.dt != dt0:
             raise RuntimeError("time step differs between cases of one grid")
+        planner.case = c
         idx = torch.from_numpy(c.index).cuda()
-        sol.reset()
-        sol.set_materials(idx, c.materials)
-        plane = bvf.rs_plane(c.bowl, nx, ny, dx, c.k_src * dx, f0)
-        sol.set_source(plane, c.k_src, c.c0, bvf.BVF_ENV_RAMP_CW)
-        sol.run(c.n_steps, peak_from=-1, dft_start=c.dft_start, dft_steps=c.dft_steps)
-        amp, _ = sol.amp_phase()
-        amps[i, 0] = (amp / c.bowl["p0"]).float()
-        fno.bvf_fno_features(idx, c.materials, synth.water_row(f0), f0, c.k_src, plane,
+        r = planner.run(idx, c.materials, c.bowl, no_heat)
+        amps[i] = (r.amp / c.bowl["p0"]).float()
+        els[i] = r.EL
+        src = bvf.rs_plane(c.bowl, nx, ny, dx, c.k_src * dx, f0)
+        fno.bvf_fno_features(idx, c.materials, synth.water_row(f0), f0, c.k_src, src,
                              c.bowl["p0"], feats[i])
-    sol.synchronize()
-    sol.close()
-    return feats, amps
+    torch.cuda.synchronize()
+    planner.close()
+    return feats, amps, els
 
 
-class TorchFNO:
-    """The network of include/bvf_fno.h as PyTorch parameters (for training)."""
+def initial_weights(d, seed):
+    """Seeded weights (synth.fno_weights) with the spectral blocks scaled down
+    by the width once more (R ~ 1/width^2), which keeps the first steps stable."""
+    from . import synth
+    w = synth.fno_weights(d, seed).astype(np.float64)
+    W, m, ci = d["width"], d["modes"], d["c_in"]
+    pos = W * ci + W
+    nR = (2 * m) * (2 * m) * m * W * W * 2
+    for _ in range(d["n_layers"]):
+        w[pos:pos + nR] /= W
+        pos += nR + W * W + W
+    return w.astype(np.float32)
 
-    def __init__(self, d, seed=0, device="cuda"):
-        import torch
-        g = torch.Generator().manual_seed(seed)
-        self.d = d
-        w, m, ci, h, co = d["width"], d["modes"], d["c_in"], d["hidden"], d["c_out"]
 
-        def p(*shape, scale):
-            return (torch.randn(*shape, generator=g) * scale).to(device).requires_grad_()
-
-        self.Wp, self.bp = p(w, ci, scale=1 / math.sqrt(ci)), p(w, scale=0.1)
-        self.R, self.W, self.b = [], [], []
-        for _ in range(d["n_layers"]):
-            self.R.append(p(2 * m, 2 * m, m, w, w, 2, scale=1.0 / (w * w)))
-            self.W.append(p(w, w, scale=1 / math.sqrt(w)))
-            self.b.append(p(w, scale=0.1))
-        self.Q1, self.q1 = p(h, w, scale=1 / math.sqrt(w)), p(h, scale=0.1)
-        self.Q2, self.q2 = p(co, h, scale=1 / math.sqrt(h)), p(co, scale=0.1)
-
-    def params(self):
-        out = [self.Wp, self.bp]
-        for l in range(self.d["n_layers"]):
-            out += [self.R[l], self.W[l], self.b[l]]
-        return out + [self.Q1, self.q1, self.Q2, self.q2]
-
-    def blob(self) -> np.ndarray:
-        """Weights in the flat layout of include/bvf_fno.h (same order as params)."""
-        return np.concatenate([t.detach().float().cpu().numpy().ravel()
-                               for t in self.params()]).astype(np.float32)
-
-    def spectral(self, v, R):
-        import torch
-        m = self.d["modes"]
-        B, C, nz, ny, nx = v.shape
-        j = torch.arange(2 * m, device=v.device)
-        iz = torch.where(j < m, j, j - 2 * m) % nz
-        iy = torch.where(j < m, j, j - 2 * m) % ny
-        vh = torch.fft.rfftn(v, dim=(2, 3, 4))
-        kept = vh[:, :, iz][:, :, :, iy][..., :m]
-        out_k = torch.einsum("bczyk,zykco->bozyk", kept, torch.view_as_complex(R))
-        full = torch.zeros((B, R.shape[4], nz, ny, nx // 2 + 1), dtype=vh.dtype, device=v.device)
-        full[:, :, iz[:, None], iy[None, :], :m] = out_k
-        return torch.fft.irfftn(full, s=(nz, ny, nx), dim=(2, 3, 4))
-
-    def __call__(self, a):
-        import torch
-        import torch.nn.functional as F
-        v = torch.einsum("oi,bizyx->bozyx", self.Wp, a) + self.bp[None, :, None, None, None]
-        L = self.d["n_layers"]
-        for l in range(L):
-            s = (self.spectral(v, self.R[l]) + torch.einsum("oc,bczyx->bozyx", self.W[l], v)
-                 + self.b[l][None, :, None, None, None])
-            v = F.gelu(s) if l < L - 1 else s
-        h = F.gelu(torch.einsum("hc,bczyx->bhzyx", self.Q1, v) + self.q1[None, :, None, None, None])
-        return torch.einsum("oh,bhzyx->bozyx", self.Q2, h) + self.q2[None, :, None, None, None]
+def one_cycle(step, total, lr_max, warm=0.3):
+    """Learning rate: linear warm-up over the first 30 %, then cosine decay."""
+    if step < warm * total:
+        return lr_max * (0.04 + 0.96 * step / (warm * total))
+    t = (step - warm * total) / max(1.0, (1.0 - warm) * total)
+    return lr_max * (0.02 + 0.98 * 0.5 * (1.0 + math.cos(math.pi * t)))
 
 
 def focal_metrics(pred, true, dx):
@@ -126,14 +98,58 @@ def focal_metrics(pred, true, dx):
     return rl2, abs(pp - pt) / pt, float(np.linalg.norm((ip - it) * dx))
 
 
+def time_plan_vs_surrogate(grid, dx, f0, d, weights, seed, reps=5):
+    """Milliseconds of one plan of the library (both FDTD runs, E_L, the 40 s /
+    30 % / 80 s BHTE) and of one surrogate inference (features + network, TF32
+    and BF16 paths) on the same placement."""
+    import torch
+    from . import bvf, fno, plan, synth
+    nx, ny, nz = grid
+    spec = dict(nx=nx, ny=ny, nz=nz, f0=f0, dx=dx, tilt_deg=5.0, seed=seed)
+    c = synth.sweep_case(spec, dft_cycles=6)
+    pl = plan.Planner(c)
+    idx = torch.from_numpy(c.index).cuda()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_plan = timed(lambda: pl.run(idx, c.materials, c.bowl))
+    pl.close()
+    src = bvf.rs_plane(c.bowl, nx, ny, dx, c.k_src * dx, f0)
+    feats = torch.empty((FEATURES, nz, ny, nx), dtype=torch.float32, device="cuda")
+    out = torch.empty((d["c_out"], nz, ny, nx), dtype=torch.float32, device="cuda")
+    tf32 = fno.Surrogate(d, weights)
+    bf = fno.Bf16Net(d, weights, grid, max_batch=1)
+
+    def feat():
+        fno.bvf_fno_features(idx, c.materials, synth.water_row(f0), f0, c.k_src, src,
+                             c.bowl["p0"], feats)
+
+    ms_tf32 = timed(lambda: (feat(), tf32(feats, out)))
+    ms_bf16 = timed(lambda: (feat(), bf.forward(feats[None], out[None])))
+    tf32.close()
+    bf.close()
+    return ms_plan, ms_tf32, ms_bf16
+
+
 def main(argv=None):
     import torch
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=400)
-    ap.add_argument("--test", type=int, default=40)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--train", type=int, default=1000)
+    ap.add_argument("--test", type=int, default=100)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--el-weight", type=float, default=10.0)
     ap.add_argument("--grid", default="64,64,96")
     ap.add_argument("--dx", type=float, default=1e-3)
     ap.add_argument("--f0", type=float, default=2.5e5)
@@ -147,65 +163,77 @@ def main(argv=None):
     _b.build()
     from . import fno
     grid = tuple(int(v) for v in args.grid.split(","))
-    d = dict(c_in=8, width=args.width, modes=args.modes, n_layers=args.layers,
-             hidden=args.hidden, c_out=1)
+    d = dict(c_in=FEATURES, width=args.width, modes=args.modes, n_layers=args.layers,
+             hidden=args.hidden, c_out=2)
     t0 = time.time()
-    xtr, ytr = make_dataset(args.train, args.seed, grid, args.dx, args.f0)
-    xte, yte = make_dataset(args.test, args.seed + 1, grid, args.dx, args.f0)
+    xtr, ytr, etr = make_dataset(args.train, args.seed, grid, args.dx, args.f0)
+    xte, yte, ete = make_dataset(args.test, args.seed + 1, grid, args.dx, args.f0)
     t_data = time.time() - t0
 
-    model = TorchFNO(d, seed=args.seed)
-    opt = torch.optim.Adam(model.params(), lr=args.lr)
+    net = fno.Bf16Net(d, initial_weights(d, args.seed), grid, max_batch=args.batch)
     steps_per_epoch = max(1, args.train // args.batch)
     total = args.epochs * steps_per_epoch
-    sched = torch.optim.lr_scheduler.OneCycleLR(opt, max_lr=args.lr, total_steps=total)
     gen = torch.Generator(device="cpu").manual_seed(args.seed)
     t1 = time.time()
-    hist = []
+    hist, step = [], 0
     for ep in range(args.epochs):
         perm = torch.randperm(args.train, generator=gen)
         run = 0.0
         for k in range(steps_per_epoch):
             sel = perm[k * args.batch:(k + 1) * args.batch].cuda()
-            x, y = xtr[sel], ytr[sel]
-            p = model(x)
-            num = torch.linalg.vector_norm((p - y).flatten(1), dim=1)
-            den = torch.linalg.vector_norm(y.flatten(1), dim=1)
-            loss = (num / den).mean()
-            opt.zero_grad(set_to_none=True)
-            loss.backward()
-            opt.step()
-            sched.step()
-            run += float(loss.detach())
+            x, y, e = xtr[sel].contiguous(), ytr[sel].contiguous(), etr[sel].contiguous()
+            run += net.adam(x, y, one_cycle(step, total, args.lr), e, args.el_weight)
+            step += 1
         hist.append(run / steps_per_epoch)
-    torch.cuda.synchronize()
+    net.synchronize()
     t_train = time.time() - t1
+    w = net.weights()
+    net.close()
 
-    # held-out skulls through the CUDA inference with the exported weights
-    net = fno.Surrogate(d, model.blob())
-    rows = []
-    cons = 0.0
+    # held-out skulls through both CUDA inference paths with the trained weights
+    tf32 = fno.Surrogate(d, w)
+    bf = fno.Bf16Net(d, w, grid, max_batch=1)
+    rows, el_err, agree = [], [], 0.0
     with torch.no_grad():
         for i in range(args.test):
-            out = net(xte[i].contiguous())
-            pt = model(xte[i:i + 1])[0]
-            cons = max(cons, float((out - pt).abs().max() / pt.abs().max()))
-            rows.append(focal_metrics(out, yte[i], args.dx))
-    net.close()
-    rows = np.array(rows)
-    # focal amplitudes (units of p0) the training set covers: the range that
-    # fno.predict_amplitude accepts before it falls back to the FDTD
-    tmax = ytr.flatten(1).max(dim=1).values
+            o32 = tf32(xte[i].contiguous())
+            o16 = bf.forward(xte[i:i + 1].contiguous())[0]
+            agree = max(agree, float((o32[0] - o16[0]).abs().max() / o32[0].abs().max()))
+            r32 = focal_metrics(o32[0], yte[i], args.dx)
+            r16 = focal_metrics(o16[0], yte[i], args.dx)
+            el32 = fno.bvf_fno_mean(o32[1].contiguous())
+            el16 = fno.bvf_fno_mean(o16[1].contiguous())
+            rows.append(r32 + r16)
+            el_err.append((abs(el32 - float(ete[i])) / float(ete[i]),
+                           abs(el16 - float(ete[i])) / float(ete[i])))
+    tf32.close()
+    bf.close()
+    rows, el_err = np.array(rows), np.array(el_err)
+    ms_plan, ms_tf32, ms_bf16 = time_plan_vs_surrogate(grid, args.dx, args.f0, d, w, 999)
+    q = lambda a, p: float(np.quantile(a, p))
+    tr_max = ytr.flatten(1).max(dim=1).values
     res = {"grid": list(grid), "dx_m": args.dx, "f0_hz": args.f0, "dims": d,
-           "train_focal_range_p0": [float(tmax.min()), float(tmax.max())],
+           "training": "bvf_fno_bf16_adam: BF16 tensor-core forward and backward, FP32 master "
+                       "weights, Adam, one-cycle lr %.1e, batch %d" % (args.lr, args.batch),
+           "train_focal_range_p0": [float(tr_max.min()), float(tr_max.max())],
            "train_cases": args.train, "test_cases": args.test, "epochs": args.epochs,
            "data_s": t_data, "train_s": t_train, "train_loss_first_last": [hist[0], hist[-1]],
-           "test_rel_l2_median": float(np.median(rows[:, 0])),
-           "test_focal_amp_err_median": float(np.median(rows[:, 1])),
-           "test_focal_amp_err_p90": float(np.quantile(rows[:, 1], 0.9)),
-           "test_focus_dist_mm_median": float(np.median(rows[:, 2]) * 1e3),
-           "test_focus_dist_mm_p90": float(np.quantile(rows[:, 2], 0.9) * 1e3),
-           "cuda_vs_torch_max_rel": cons}
+           "tf32": {"rel_l2_median": q(rows[:, 0], 0.5),
+                    "focal_amp_err_median": q(rows[:, 1], 0.5),
+                    "focal_amp_err_p90": q(rows[:, 1], 0.9),
+                    "focus_dist_mm_median": q(rows[:, 2], 0.5) * 1e3,
+                    "focus_dist_mm_p90": q(rows[:, 2], 0.9) * 1e3,
+                    "EL_rel_err_median": q(el_err[:, 0], 0.5), "EL_rel_err_p90": q(el_err[:, 0], 0.9)},
+           "bf16": {"rel_l2_median": q(rows[:, 3], 0.5),
+                    "focal_amp_err_median": q(rows[:, 4], 0.5),
+                    "focal_amp_err_p90": q(rows[:, 4], 0.9),
+                    "focus_dist_mm_median": q(rows[:, 5], 0.5) * 1e3,
+                    "EL_rel_err_median": q(el_err[:, 1], 0.5), "EL_rel_err_p90": q(el_err[:, 1], 0.9)},
+           "tf32_vs_bf16_max_rel": agree,
+           "same_workload_timing_ms": {"plan": ms_plan, "surrogate_tf32": ms_tf32,
+                                       "surrogate_bf16": ms_bf16,
+                                       "speedup_tf32": ms_plan / ms_tf32,
+                                       "speedup_bf16": ms_plan / ms_bf16}}
     print(json.dumps(res), flush=True)
     return 0
 

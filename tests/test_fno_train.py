@@ -1,23 +1,34 @@
-"""The training model of the surrogate (PyTorch, offline tool) computes the
-network of the FP64 oracle, and exports its weights in the oracle's blob
-layout: its forward on CPU matches oracle/fno.py with the exported blob."""
+"""Host logic of the surrogate's training tool (the training itself runs in
+the library's BF16 kernels, checked in tests/test_fno_bf16_gpu.py): the
+initial weights scale exactly the spectral blocks of the blob layout, and the
+learning-rate schedule warms up, peaks at lr_max and decays."""
 import numpy as np
-import pytest
 
 
-def test_training_model_matches_the_oracle_on_cpu():
-    torch = pytest.importorskip("torch")
+def test_initial_weights_scale_only_the_spectral_blocks():
     from oracle import fno as ofno
-    from paper_2301_12727_gb300.fno_train import TorchFNO
+    from paper_2301_12727_gb300 import synth
+    from paper_2301_12727_gb300.fno_train import initial_weights
     d = dict(c_in=3, width=16, modes=2, n_layers=3, hidden=8, c_out=2)
-    model = TorchFNO(d, seed=3, device="cpu")
-    for t in model.params():        # double precision for the comparison
-        t.data = t.data.double()
-    rng = np.random.default_rng(1)
-    a = rng.standard_normal((1, 3, 6, 5, 8))
-    with torch.no_grad():
-        got = model(torch.from_numpy(a))[0].numpy()
-    blob = np.concatenate([t.detach().numpy().ravel() for t in model.params()])
-    assert blob.size == ofno.weight_count(**d)
-    ref = ofno.forward(a[0], blob, **d)
-    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-10)
+    w0 = synth.fno_weights(d, 4).astype(np.float64)
+    w1 = initial_weights(d, 4).astype(np.float64)
+    assert w1.size == ofno.weight_count(**d)
+    p0 = ofno.unpack(w0, **d)
+    p1 = ofno.unpack(w1, **d)
+    for key in ("Wp", "bp", "Q1", "q1", "Q2", "q2"):
+        np.testing.assert_array_equal(p0[key], p1[key])
+    for l0, l1 in zip(p0["layers"], p1["layers"]):
+        np.testing.assert_allclose(l1["R"], l0["R"] / d["width"], rtol=1e-6)
+        np.testing.assert_array_equal(l0["W"], l1["W"])
+        np.testing.assert_array_equal(l0["b"], l1["b"])
+
+
+def test_one_cycle_schedule():
+    from paper_2301_12727_gb300.fno_train import one_cycle
+    total, lr = 1000, 2e-3
+    lrs = np.array([one_cycle(s, total, lr) for s in range(total)])
+    assert lrs.max() <= lr * (1 + 1e-12)
+    peak = int(np.argmax(lrs))
+    assert abs(peak - 300) <= 1
+    assert np.all(np.diff(lrs[:peak]) > 0) and np.all(np.diff(lrs[peak + 1:]) <= 0)
+    assert lrs[0] < 0.1 * lr and lrs[-1] < 0.05 * lr
