@@ -55,6 +55,8 @@ def parse():
                     help="skip the scaled-FP16-storage leg reported under mixed_precision")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the surrogate (Fourier neural operator) inference leg")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the 64-domain batched sweep leg")
     ap.add_argument("--no-config3", action="store_true",
                     help="skip the 250 / 700 kHz mixed-precision leg (config3)")
     ap.add_argument("--surrogate", action="store_true",
@@ -262,7 +264,7 @@ def run_reference(args):
 # --------------------------------------------------------------------------
 # Surrogate network: 4 Fourier layers, width 32, 12 modes, projection width
 # 128, run on the plan's grid.
-FNO_DIMS = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=1)
+FNO_DIMS = dict(c_in=8, width=32, modes=12, n_layers=4, hidden=128, c_out=2)
 
 
 def run_surrogate(args):
@@ -279,11 +281,38 @@ def run_surrogate(args):
     return 0
 
 
+def graph_ms(fn, reps):
+    """Milliseconds per replay of fn recorded once in a CUDA graph (fn's
+    launches on torch's current stream; one warm call on a side stream first)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
     """Inference time of the surrogate on the plan's feature volume (seeded
     untrained weights: the time does not depend on their values), its stage
-    split and its HBM roofline; with cpu_baseline, the FP64 oracle timed on a
-    48^3 sample as the surrogate's CPU baseline."""
+    split and its HBM roofline, for the TF32 path (call by call and replayed
+    from a CUDA graph) and the BF16 path (bvf_fno_bf16_forward, from a graph);
+    with cpu_baseline, the FP64 oracle timed on a 48^3 sample as the
+    surrogate's CPU baseline."""
     import time
     import numpy as np
     import torch
@@ -293,7 +322,7 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
     idx = torch.from_numpy(case.index).cuda()
     src = bvf.rs_plane(dict(case.bowl), nx, ny, case.dx, case.k_src * case.dx, case.f0)
     feats = torch.empty((8, nz, ny, nx), dtype=torch.float32, device="cuda")
-    out = torch.empty((1, nz, ny, nx), dtype=torch.float32, device="cuda")
+    out = torch.empty((FNO_DIMS["c_out"], nz, ny, nx), dtype=torch.float32, device="cuda")
     water = synth.water_row(case.f0)
 
     def one():
@@ -317,6 +346,19 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
     torch.cuda.synchronize()
     stages = net.stage_times()
     net.timing(False)
+    k = max(5, steps)
+    ms_graph = graph_ms(one, k)
+    net.close()
+    bf = fno.Bf16Net(FNO_DIMS, synth.fno_weights(FNO_DIMS, 2301), (nx, ny, nz), max_batch=1)
+    fb, ob = feats[None], out[None]
+
+    def one_bf16():
+        fno.bvf_fno_features(idx, case.materials, water, case.f0, case.k_src, src,
+                             case.bowl["p0"], feats)
+        bf.forward(fb, ob)
+
+    ms_bf16 = graph_ms(one_bf16, k)
+    bf.close()
     N = case.voxels
     d = FNO_DIMS
     # algorithmic bytes per inference: the features read by the lift, every
@@ -326,7 +368,6 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
     act = 4.0 * d["width"] * N
     bytes_inf = 4.0 * N * (d["c_in"] + d["c_out"]) + act * (2 * d["n_layers"] + 2)
     peak, peak_kind = measured_peak_hbm()
-    net.close()
     base = None
     if cpu_baseline:
         # the CPU baseline: the FP64 oracle on a 48^3 sample of the same network
@@ -344,6 +385,13 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
             "grid": [nx, ny, nz], "ms_per_inference": ms, "voxels_per_s": N / (ms / 1e3),
             "speedup_vs_plan": ms_plan / ms if ms_plan else None,
             "speedup_vs_plan_fdtd": ms_fdtd / ms if ms_fdtd else None,
+            "graph": {"ms_per_inference": ms_graph,
+                      "speedup_vs_plan": ms_plan / ms_graph if ms_plan else None},
+            "bf16": {"path": "bvf_fno_bf16_forward: every contraction a tcgen05 kind::f16 BF16 "
+                             "product with FP32 accumulation, replayed from a CUDA graph",
+                     "ms_per_inference": ms_bf16,
+                     "speedup_vs_plan": ms_plan / ms_bf16 if ms_plan else None,
+                     "speedup_vs_plan_fdtd": ms_fdtd / ms_bf16 if ms_fdtd else None},
             "stages_ms": stages,
             "tensor_core": "row pass mma.sync m16n8k8 TF32; projection tcgen05.mma kind::tf32 "
                            "into TMEM; both with the three-product FP32 split",
@@ -428,6 +476,13 @@ def run_bvf(args):
         import multiprocessing as mp
         c3_pool = cf.ProcessPoolExecutor(max_workers=2, mp_context=mp.get_context("spawn"))
         c3_future = {f0: c3_pool.submit(_config3_case, f0) for f0 in (250e3, 700e3)}
+    sweep_futs = None
+    if rank == 0 and not args.no_sweep:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        sw_pool = cf.ProcessPoolExecutor(max_workers=min(12, os.cpu_count() or 1),
+                                         mp_context=mp.get_context("spawn"))
+        sweep_futs = make_sweep_cases(args.sweep_domains, args.sweep_steps, pool=sw_pool)
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
@@ -551,6 +606,11 @@ def run_bvf(args):
         config3 = config3_leg({f0: fut.result() for f0, fut in c3_future.items()})
         c3_pool.shutdown()
 
+    sweep = None
+    if sweep_futs is not None:
+        sweep = sweep_leg([f.result() for f in sweep_futs], 2, 1)
+        sw_pool.shutdown()
+
     surrogate = None
     if not args.no_surrogate and rank == 0:
         surrogate = surrogate_leg(case, args.steps, args.warmup, ms / args.steps,
@@ -604,7 +664,7 @@ def run_bvf(args):
             "config": bench_config(case, args.storage),
             "results": {"EL": res.EL, "TS": res.TS, "z_m": res.z_m},
             "roofline": roofline, "gpu_launches": int(launches), "e2e": e2e, "clocks": clocks,
-            "mixed_precision": mixed, "config3": config3, "surrogate": surrogate}
+            "mixed_precision": mixed, "config3": config3, "sweep": sweep, "surrogate": surrogate}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(case)
     if rank == 0:
@@ -623,24 +683,16 @@ def _sweep_domain(spec_steps):
     return synth.sweep_case(spec, n_steps=n_steps)
 
 
-def run_sweep(args):
-    """Batched planning sweep: seeded domains of uneven size (96..200 cells per
-    axis), each with its own frequency (250/500/700 kHz at 6 points per
-    wavelength), bowl tilt and skull, advanced together by the persistent
-    batch kernels replayed from a CUDA graph, against the same contexts run
-    one after another.  Every domain runs the same number of FDTD steps with
-    peak capture; the metric is aggregate voxel-steps per second."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    from paper_2301_12727_gb300 import synth
-    specs = synth.sweep_specs(n=args.sweep_domains, seed=4321)
-    # domains generated on the host cores before any CUDA call (spawned pool)
-    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
-                                mp_context=mp.get_context("spawn")) as ex:
-        cases = list(ex.map(_sweep_domain, [(sp, args.sweep_steps) for sp in specs]))
+def sweep_leg(cases, steps, warmup):
+    """Batched planning sweep over `cases` (seeded domains of uneven size,
+    frequency, tilt and skull): the same FDTD runs of every domain timed
+    (CUDA events, min over `steps` repetitions after `warmup`) in four modes:
+    one after another, per-domain launches on 8 streams, the sweep recorded
+    as one CUDA graph of per-domain launches on 8 branches (after the
+    per-domain z-chunk autotuner), and the persistent work-list kernels
+    replayed from a graph.  Every mode gives the sequential results bit for
+    bit (checked on the peak maps)."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2301_12727_gb300 import bvf
     solvers = []
     for c in cases:
@@ -650,8 +702,10 @@ def run_sweep(args):
                      c.envelope)
         solvers.append(s)
     vox = sum(c.voxels for c in cases)
-    n = args.sweep_steps
+    n = cases[0].n_steps
+    caps = [(0, 0, 0)] * len(solvers)
     stream = torch.cuda.current_stream()
+    batch = bvf.Batch(solvers)
 
     def timed(fn):
         for s in solvers:
@@ -668,49 +722,86 @@ def run_sweep(args):
         for s in solvers:
             s.run(n, peak_from=0)
 
-    batch = bvf.Batch(solvers)
-    best_kc, _ = batch.tune(trial_steps=20, candidates=(6, 8, 10, 13, 16, 24))
-
-    def batched():
-        batch.run(n, caps=[(0, 0, 0)] * len(solvers), kchunk=best_kc, graph_steps=50)
-
     def streams():
-        batch.run_streams(n, caps=[(0, 0, 0)] * len(solvers), n_streams=8)
+        batch.run_streams(n, caps=caps, n_streams=8)
 
-    for _ in range(max(1, args.warmup)):
-        timed(sequential)
-        timed(batched)
-        timed(streams)
-    ms_str = min(timed(streams) for _ in range(args.steps))
-    ms_seq = min(timed(sequential) for _ in range(args.steps))
-    l0 = batch.launches()
-    ms_bat = min(timed(batched) for _ in range(args.steps))
-    launches = (batch.launches() - l0) // args.steps
-    # the batched peaks equal the sequential ones bit for bit
-    peaks_b = [s.peak() for s in solvers]
-    timed(sequential)
-    same = all(bool(torch.equal(a, s.peak())) for a, s in zip(peaks_b, solvers))
+    def graph():
+        batch.run_graph(n, caps=caps, n_branches=8)
+
+    def best(fn):
+        for _ in range(max(1, warmup)):
+            timed(fn)
+        return min(timed(fn) for _ in range(max(1, steps)))
+
+    ms_seq = best(sequential)
+    ref = [s.peak() for s in solvers]
+    ms_str = best(streams)
+    same = all(bool(torch.equal(a, s.peak())) for a, s in zip(ref, solvers))
+    tuned = batch.tune_domains(trial_steps=10)
+    ms_seq_tuned = best(sequential)
+    ms_graph = best(graph)
+    same = same and all(bool(torch.equal(a, s.peak())) for a, s in zip(ref, solvers))
+    best_kc, _ = batch.tune(trial_steps=20, candidates=(6, 8, 10, 13, 16, 24))
+    ms_pers = best(lambda: batch.run(n, caps=caps, kchunk=best_kc, graph_steps=50))
+    same = same and all(bool(torch.equal(a, s.peak())) for a, s in zip(ref, solvers))
     rate = lambda ms: vox * n / (ms / 1e3) / 1e9
-    line = {"metric": "sweep Gvoxel-steps/s", "value": rate(ms_str),
-            "unit": "Gvoxel-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms_str / n, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "planning sweep: %d skull domains, 96..200 cells per axis, "
-                                   "250/500/700 kHz, tilt +-15 deg, %d steps each"
-                                   % (len(cases), n),
-                       "voxels_total": vox, "mode": "per-domain launches on 8 streams"},
-            "sequential": {"value": rate(ms_seq), "ms": ms_seq},
-            "speedup_vs_sequential": ms_seq / ms_str,
-            "persistent_graph": {"value": rate(ms_bat), "ms": ms_bat,
-                                 "speedup_vs_sequential": ms_seq / ms_bat,
-                                 "best_kchunk": best_kc, "graph_steps": 50,
-                                 "launches_per_run": int(launches)},
-            "batched_equals_sequential": same,
-            "gpu_launches": 2 * n * len(cases)}
-    print(json.dumps(line), flush=True)
+    out = {"domains": len(cases), "voxels_total": vox, "fdtd_steps_each": n,
+           "sequential": {"value": rate(ms_seq), "ms": ms_seq},
+           "sequential_tuned_z_chunks": {"value": rate(ms_seq_tuned), "ms": ms_seq_tuned},
+           "streams_8": {"value": rate(ms_str), "ms": ms_str,
+                         "speedup_vs_sequential": ms_seq / ms_str},
+           "graph_8_branches_tuned": {"value": rate(ms_graph), "ms": ms_graph,
+                                      "speedup_vs_sequential": ms_seq / ms_graph,
+                                      "speedup_vs_sequential_tuned": ms_seq_tuned / ms_graph,
+                                      "launches": 1,
+                                      "z_chunks": sorted(set(int(k) for k in tuned))},
+           "persistent_graph": {"value": rate(ms_pers), "ms": ms_pers,
+                                "speedup_vs_sequential": ms_seq / ms_pers, "z_chunk": best_kc},
+           "unit": UNIT, "results_equal_sequential": bool(same)}
     batch.close()
     for s in solvers:
         s.close()
+    return out
+
+
+def make_sweep_cases(n_domains, n_steps, pool=None):
+    """Seeded sweep domains (96..200 cells per axis, 250/500/700 kHz at 6 points
+    per wavelength, tilt +-15 deg) generated on the host cores by spawned
+    processes (no CUDA state is inherited)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_2301_12727_gb300 import synth
+    specs = synth.sweep_specs(n=n_domains, seed=4321)
+    own = pool is None
+    if own:
+        pool = cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                      mp_context=mp.get_context("spawn"))
+    futs = [pool.submit(_sweep_domain, (sp, n_steps)) for sp in specs]
+    if own:
+        out = [f.result() for f in futs]
+        pool.shutdown()
+        return out
+    return futs
+
+
+def run_sweep(args):
+    """The batched planning sweep alone, as its own JSON line."""
+    cases = make_sweep_cases(args.sweep_domains, args.sweep_steps)
+    import torch  # noqa: F401  (CUDA is first touched after the spawned generation)
+    import __graft_entry__
+    __graft_entry__.build()
+    leg = sweep_leg(cases, args.steps, args.warmup)
+    g = leg["graph_8_branches_tuned"]
+    line = {"metric": "sweep Gvoxel-steps/s", "value": g["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["ms"] / leg["fdtd_steps_each"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "planning sweep: %d skull domains, 96..200 cells per axis, "
+                                   "250/500/700 kHz, tilt +-15 deg, %d steps each"
+                                   % (leg["domains"], leg["fdtd_steps_each"]),
+                       "mode": "one CUDA graph of per-domain launches on 8 branches"},
+            "sweep": leg, "gpu_launches": 2 * leg["fdtd_steps_each"] * leg["domains"]}
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -480,6 +480,28 @@ int bvf_batch_run(bvf_batch *b, const int *n_steps, const bvf_capture *caps, int
 int bvf_batch_run_streams(bvf_batch *b, const int *n_steps, const bvf_capture *caps,
                           int n_streams, void *stream);
 
+/* The same sweep as one CUDA graph: the per-context launches of
+ * bvf_run_acoustic, contexts dealt round-robin over n_branches parallel
+ * branches (as bvf_batch_run_streams deals them over streams), recorded once
+ * and replayed with a single graph launch on `stream`, so the host issues one
+ * launch per sweep and the branches' kernels share the GPU.  The recording is
+ * kept and replayed while the call's arguments, the contexts' z-chunks and
+ * the step counts the contexts start from are those it was recorded for
+ * (e.g. the same sweep after bvf_reset); anything else records anew, which
+ * waits for `stream`.  Results are those of bvf_run_acoustic, bit for bit.
+ * Contexts with a time budget, kernel timing or the test hook armed are
+ * refused (BVF_E_ARG). */
+int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *caps, int n_branches,
+                        void *stream);
+
+/* Per-domain tile autotuner: for every context, times trial_steps steps (after
+ * two warm-up steps) with each candidate z-chunk (planes per block, the tile's
+ * z extent; the x-y tile is 32 x 8), keeps the fastest in the context (used by
+ * bvf_run_acoustic and the modes above) and writes it to h_best[d] (may be
+ * NULL).  Leaves every context reset (bvf_reset). */
+int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,
+                           int *h_best, void *stream);
+
 /* Tile autotuner: times trial_steps steps of every domain for each candidate
  * z-chunk length, returns the fastest and its time per step (ms), and leaves
  * every context reset (bvf_reset: state, captures and step counts zeroed). */

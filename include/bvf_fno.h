@@ -153,7 +153,10 @@ int bvf_gemm_bf16(const bvf_gemm *g, int *d_flag, void *stream);
  * is sized for one grid and up to max_batch samples and keeps FP32 master
  * weights, their gradient, Adam moments and every activation the backward pass
  * needs.  Inputs [batch][c_in][nz][ny][nx], outputs [batch][c_out][...],
- * FP32 device memory.
+ * FP32 device memory.  bvf_fno_bf16_forward is inference: it writes d_out
+ * directly, stores no pre-activation, makes no runtime call but its launches
+ * after the first call of each product shape, and so may be recorded in a
+ * CUDA graph; it must not overlap a gradient or Adam call of the same context.
  *
  * Loss of a batch (bvf_fno_bf16_gradient / _adam): the mean over samples of
  * the relative L2 error ||out_0 - target|| / ||target|| of output channel 0

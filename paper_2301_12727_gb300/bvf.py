@@ -31,7 +31,7 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams", "bvf_plan",
            "bvf_rs_elements", "bvf_set_time_budget", "bvf_state_bytes", "bvf_state_save",
            "bvf_state_load", "bvf_test_withhold_copy", "bvf_bowl_array", "bvf_steer_weights",
-           "bvf_time_reversal_plane")
+           "bvf_time_reversal_plane", "bvf_batch_run_graph", "bvf_batch_tune_domains")
 
 
 class BvfError(RuntimeError):
@@ -152,6 +152,8 @@ def lib():
                                ctypes.POINTER(Bowl), i, ctypes.POINTER(PlanParams), vp, vp, vp, vp,
                                vp, ctypes.POINTER(PlanOut), vp]
         L.bvf_set_time_budget.argtypes = [vp, d]
+        L.bvf_batch_run_graph.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
+        L.bvf_batch_tune_domains.argtypes = [vp, i, ctypes.POINTER(i), i, ctypes.POINTER(i), vp]
         L.bvf_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.bvf_state_save.argtypes = [vp, vp, ctypes.c_size_t, vp]
         L.bvf_state_load.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -575,8 +577,29 @@ class Batch:
         _check(lib().bvf_batch_run_streams(self.handle, steps, cp, int(n_streams),
                                            _stream(stream)))
 
+    def run_graph(self, n_steps, caps=None, n_branches=8, stream=None):
+        """The sweep as one recorded CUDA graph of per-domain launches on
+        n_branches parallel branches (bvf_batch_run_graph)."""
+        n = len(self.solvers)
+        if isinstance(n_steps, int):
+            n_steps = [n_steps] * n
+        steps = (ctypes.c_int * n)(*[int(v) for v in n_steps])
+        cp = None
+        if caps is not None:
+            cp = (Capture * n)(*[c if isinstance(c, Capture) else Capture(*c) for c in caps])
+        _check(lib().bvf_batch_run_graph(self.handle, steps, cp, int(n_branches), _stream(stream)))
+
     def tune(self, trial_steps=20, candidates=(6, 8, 10, 13, 16, 24), stream=None):
         return bvf_batch_tune(self.handle, trial_steps, candidates, stream)
+
+    def tune_domains(self, trial_steps=10, candidates=(6, 8, 10, 13, 16, 24, 32), stream=None):
+        """Per-domain z-chunk autotuner; returns the chosen z-chunk of each domain."""
+        n = len(self.solvers)
+        cand = (ctypes.c_int * len(candidates))(*candidates)
+        best = (ctypes.c_int * n)()
+        _check(lib().bvf_batch_tune_domains(self.handle, trial_steps, cand, len(candidates), best,
+                                            _stream(stream)))
+        return list(best)
 
     def launches(self):
         out = ctypes.c_longlong()

@@ -37,6 +37,7 @@
 // L <= 2.
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "bvf_stencil.cuh"
@@ -857,14 +858,27 @@ static dim3 grid_tma(const AcParams &p, int kc)
     return dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + kc - 1) / kc);
 }
 
+// The dynamic shared-memory limit of a kernel, raised once per process to the
+// largest size any launch asks for (the material table at its maximum), so
+// that launches make no other runtime call (they may be captured in a graph).
+template <typename K>
+static cudaError_t raise_smem_once(K kernel, size_t bytes, std::atomic<int> &done)
+{
+    if (done.load(std::memory_order_acquire)) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.store(1, std::memory_order_release);
+    return e;
+}
+
 template <typename T>
 static cudaError_t launch_velocity_tma_t(const AcParams &p, const VelocityTmaMaps &tm,
                                          cudaStream_t s)
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
     const size_t sm = VelLayout<T>::bytes(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_velocity_tma<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<int> done{0};
+    cudaError_t e = raise_smem_once(k_velocity_tma<T>, VelLayout<T>::bytes(BVF_MAX_MATERIALS), done);
     if (e != cudaSuccess) return e;
     k_velocity_tma<T><<<grid_tma(p, kc), dim3(PX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
@@ -880,8 +894,9 @@ static cudaError_t launch_stress_tma_t(const AcParams &p, const StressTmaMaps &t
 {
     const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
     const size_t sm = StressLayout<L, T>::bytes(p.n_mat);
-    cudaError_t e = cudaFuncSetAttribute(k_stress_tma<L, MINB, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<int> done{0};
+    cudaError_t e = raise_smem_once(k_stress_tma<L, MINB, T>,
+                                    StressLayout<L, T>::bytes(BVF_MAX_MATERIALS), done);
     if (e != cudaSuccess) return e;
     k_stress_tma<L, MINB, T><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();

@@ -115,6 +115,12 @@ struct bvf_batch {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> side_ev;
     cudaEvent_t fork = nullptr;
+    // bvf_batch_run_graph: the recorded graph, what it was recorded for (start
+    // steps, step counts, capture windows, z-chunks, branches) and the counter
+    // advances of one replay
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<long long> gsig;
+    std::vector<long long> gdsteps, gddft;
 };
 
 namespace {
@@ -1292,6 +1298,7 @@ int bvf_batch_create(bvf_ctx *const *ctxs, int n, bvf_batch **out)
 
 void bvf_batch_destroy(bvf_batch *b)
 {
+    if (b && b->gexec) cudaGraphExecDestroy(b->gexec);
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -1449,6 +1456,146 @@ int bvf_batch_run_streams(bvf_batch *b, const int *n_steps, const bvf_capture *c
         CK_FREE(cudaStreamWaitEvent(s, b->side_ev[k], 0), "bvf_batch_run_streams");
     }
     return BVF_OK;
+}
+
+// side streams and events of the batch, at least n of each
+static int batch_side_streams(bvf_batch *b, int n)
+{
+    while ((int)b->side.size() < n) {
+        cudaStream_t t = nullptr;
+        CK_FREE(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "batch streams");
+        b->side.push_back(t);
+        cudaEvent_t ev = nullptr;
+        CK_FREE(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch streams");
+        b->side_ev.push_back(ev);
+    }
+    if (!b->fork) CK_FREE(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch streams");
+    return BVF_OK;
+}
+
+int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *caps, int n_branches,
+                        void *stream)
+{
+    if (!b || !n_steps || n_branches < 1)
+        return fail(nullptr, BVF_E_ARG, "bvf_batch_run_graph: bad argument");
+    const int n = (int)b->ctx.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<long long> sig;
+    sig.push_back(n_branches);
+    for (int d = 0; d < n; ++d) {
+        bvf_ctx *c = b->ctx[d];
+        if (n_steps[d] < 0 || (caps && caps[d].dft_steps < 0))
+            return fail(nullptr, BVF_E_ARG, "bvf_batch_run_graph: negative step count");
+        if (c->budget_s > 0.0 || c->timing || c->hold)
+            return fail(nullptr, BVF_E_ARG, "bvf_batch_run_graph: a context has a time budget, "
+                                            "kernel timing or the test hook armed");
+        const bvf_capture cp = caps ? caps[d] : bvf_capture{-1, 0, 0};
+        sig.insert(sig.end(), {c->steps, n_steps[d], cp.peak_from, cp.dft_start, cp.dft_steps,
+                               c->kchunk});
+    }
+    if (!b->gexec || sig != b->gsig) {
+        // record the per-domain launches once, domains dealt round-robin over
+        // the branches, on the batch's own stream (the caller's may be the
+        // legacy default stream, which cannot be recorded)
+        int rc = batch_side_streams(b, n_branches);
+        if (rc != BVF_OK) return rc;
+        for (int d = 0; d < n; ++d)
+            if (caps && caps[d].dft_steps > 0 && (rc = ensure_dft(b->ctx[d], s)) != BVF_OK) return rc;
+        CK_FREE(cudaStreamSynchronize(s), "bvf_batch_run_graph");
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        std::vector<long long> st0(n), df0(n), ln0(n);
+        for (int d = 0; d < n; ++d) {
+            st0[d] = b->ctx[d]->steps;
+            df0[d] = b->ctx[d]->dft_count;
+            ln0[d] = b->ctx[d]->launches;
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->cap);
+        for (int k = 0; k < n_branches && e == cudaSuccess; ++k)
+            e = cudaStreamWaitEvent(b->side[k], b->fork, 0);
+        for (int d = 0; d < n && e == cudaSuccess && rc == BVF_OK; ++d)
+            rc = bvf_run_acoustic(b->ctx[d], n_steps[d], caps ? &caps[d] : nullptr,
+                                  b->side[d % n_branches]);
+        for (int k = 0; k < n_branches && e == cudaSuccess; ++k) {
+            e = cudaEventRecord(b->side_ev[k], b->side[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->side_ev[k], 0);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && rc == BVF_OK) e = cudaGraphInstantiate(&b->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        // nothing ran yet: the counters go back to where the recording began
+        b->gdsteps.assign(n, 0);
+        b->gddft.assign(n, 0);
+        for (int d = 0; d < n; ++d) {
+            bvf_ctx *c = b->ctx[d];
+            b->gdsteps[d] = c->steps - st0[d];
+            b->gddft[d] = c->dft_count - df0[d];
+            c->steps = st0[d];
+            c->dft_count = (int)df0[d];
+            c->launches = ln0[d];
+        }
+        if (rc != BVF_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "bvf_batch_run_graph: recording");
+        b->gsig = sig;
+    }
+    CK_FREE(cudaGraphLaunch(b->gexec, s), "bvf_batch_run_graph: launch");
+    for (int d = 0; d < n; ++d) {
+        bvf_ctx *c = b->ctx[d];
+        c->steps += b->gdsteps[d];
+        c->dft_count += (int)b->gddft[d];
+        c->launches += 2 * b->gdsteps[d];
+        b->launches += 2 * b->gdsteps[d];
+    }
+    return BVF_OK;
+}
+
+int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,
+                           int *h_best, void *stream)
+{
+    if (!b || !candidates || n_candidates < 1 || trial_steps < 1)
+        return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad argument");
+    for (int ci = 0; ci < n_candidates; ++ci)
+        if (candidates[ci] < 1) return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad candidate");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK_FREE(cudaEventCreate(&e0), "bvf_batch_tune_domains");
+    CK_FREE(cudaEventCreate(&e1), "bvf_batch_tune_domains");
+    int rc = BVF_OK;
+    for (size_t d = 0; d < b->ctx.size() && rc == BVF_OK; ++d) {
+        bvf_ctx *c = b->ctx[d];
+        double best = 1e300;
+        int best_kc = c->kchunk;
+        for (int ci = 0; ci < n_candidates && rc == BVF_OK; ++ci) {
+            c->kchunk = std::min(candidates[ci], c->g.nz);
+            if ((rc = bvf_reset(c, stream)) != BVF_OK) break;
+            if ((rc = bvf_run_acoustic(c, 2, nullptr, stream)) != BVF_OK) break;   // warm-up
+            cudaEventRecord(e0, s);
+            if ((rc = bvf_run_acoustic(c, trial_steps, nullptr, stream)) != BVF_OK) break;
+            cudaEventRecord(e1, s);
+            float ms = 0.0f;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(nullptr, e, "bvf_batch_tune_domains");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                best_kc = c->kchunk;
+            }
+        }
+        c->kchunk = best_kc;
+        if (h_best) h_best[d] = best_kc;
+        if (rc == BVF_OK) rc = bvf_reset(c, stream);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int bvf_batch_tune(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,

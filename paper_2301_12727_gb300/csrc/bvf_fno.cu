@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -917,6 +918,28 @@ int prepare_grid(bvf_fno *f, int nx, int ny, int nz)
 
 }  // namespace
 
+namespace {
+// A kernel's dynamic shared-memory limit, raised only when a launch needs more
+// than any earlier one (per process), so that repeated inferences on a grid
+// make no runtime call besides their launches and can be recorded in a graph.
+// The record is keyed by the kernel itself (a template argument), not by its
+// type: instantiations of one kernel template share a signature but each has
+// its own limit.
+template <auto Kernel>
+cudaError_t smem_at_least(size_t bytes)
+{
+    static std::atomic<size_t> cur{0};
+    size_t have = cur.load(std::memory_order_acquire);
+    if (bytes <= have) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        while (have < bytes && !cur.compare_exchange_weak(have, bytes)) {
+        }
+    return e;
+}
+}  // namespace
+
 extern "C" {
 
 size_t bvf_fno_weight_count(const bvf_fno_dims *d)
@@ -998,6 +1021,7 @@ int bvf_fno_stage_times(bvf_fno *f, double *ms_out)
     return BVF_OK;
 }
 
+
 int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float *d_out,
                     void *stream)
 {
@@ -1070,8 +1094,7 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
         const size_t bytes = (size_t)RowMmaLayout(ksw, W, m, nx).words * sizeof(uint32_t);
         cudaError_t e = cudaSuccess;
 #define BVF_ROW(NT, KSW)                                                                     \
-    e = cudaFuncSetAttribute(k_row_mma<NT, KSW>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             (int)bytes);                                                     \
+    e = smem_at_least<k_row_mma<NT, KSW>>(bytes);                                              \
     if (e == cudaSuccess)                                                                     \
         k_row_mma<NT, KSW><<<row_grid, 256, bytes, s>>>(vin, cin, Ap, Wm, bm, nx, rows_p, m,   \
                                                         invN, act, tx, vout, An, N);
@@ -1111,7 +1134,7 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
     FCK(mark(0), "event");
 
     const size_t sy = (size_t)ny * m * sizeof(float2);
-    FCK(cudaFuncSetAttribute(k_dfty, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy),
+    FCK(smem_at_least<k_dfty>(sy),
         "bvf_fno_forward: dfty smem");
     const size_t s_out = ((size_t)W * W + W + 1) * sizeof(float) + (size_t)W * m * sizeof(float2);
     const int rows_x = W * nz * ny;
@@ -1174,8 +1197,7 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
         const int grid = (int)std::min<long>(tiles, (long)n_sm * per_sm);
         cudaError_t e = cudaSuccess;
 #define BVF_PRJ(WW, CP)                                                                      \
-    e = cudaFuncSetAttribute(k_project_tc<WW, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                             pl.bytes);                                                        \
+    e = smem_at_least<k_project_tc<WW, CP>>((size_t)pl.bytes);                                 \
     if (e == cudaSuccess)                                                                      \
         k_project_tc<WW, CP><<<grid, 256, pl.bytes, s>>>(vc, Q1, q1, Q2, q2, d.hidden, d.c_out, \
                                                         d_out, N, f->flag);

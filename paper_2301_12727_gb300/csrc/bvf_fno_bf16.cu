@@ -518,8 +518,10 @@ int chan_sum(const float *x, int B, int C, int N, float *out, cudaStream_t s)
     return BVF_OK;
 }
 
-// forward pass of `batch` samples, every activation the backward pass needs kept
-int forward(bvf_fno_bf16 *t, int batch, const float *in, cudaStream_t s)
+// forward pass of `batch` samples into `out` ([batch][c_out][N]); with `keep`
+// every activation the backward pass needs is kept, without it (inference)
+// the pre-activations are not written
+int forward(bvf_fno_bf16 *t, int batch, const float *in, float *out, bool keep, cudaStream_t s)
 {
     const bvf_fno_dims &d = t->d;
     const int W = d.width, N = t->N, L = d.n_layers, m = d.modes;
@@ -546,7 +548,7 @@ int forward(bvf_fno_bf16 *t, int batch, const float *in, cudaStream_t s)
         p.bias_mode = 1;
         if (l < L - 1) {
             p.act = 1;
-            p.C_pre = t->s[l];
+            p.C_pre = keep ? t->s[l] : nullptr;
         }
         if ((rc = gemm(t, p, s, "pointwise")) != BVF_OK) return rc;
     }
@@ -554,9 +556,9 @@ int forward(bvf_fno_bf16 *t, int batch, const float *in, cudaStream_t s)
     g.bias = w + o.q1;
     g.bias_mode = 1;
     g.act = 1;
-    g.C_pre = t->pre1;
+    g.C_pre = keep ? t->pre1 : nullptr;
     if ((rc = gemm(t, g, s, "projection 1")) != BVF_OK) return rc;
-    g = chan(t->h, d.hidden, w + o.Q2, t->out, d.c_out, N, batch);
+    g = chan(t->h, d.hidden, w + o.Q2, out, d.c_out, N, batch);
     g.bias = w + o.q2;
     g.bias_mode = 1;
     return gemm(t, g, s, "projection 2");
@@ -569,7 +571,7 @@ int gradient(bvf_fno_bf16 *t, int batch, const float *in, const float *target, c
     const bvf_fno_dims &d = t->d;
     const int W = d.width, N = t->N, L = d.n_layers, m = d.modes, H = d.hidden;
     const Off o = offsets(d);
-    int rc = forward(t, batch, in, s);
+    int rc = forward(t, batch, in, t->out, true, s);
     if (rc != BVF_OK) return rc;
     BCK(cudaMemsetAsync(t->sums, 0, 3 * sizeof(double) * batch, s), "loss");
     k_loss_sums<<<dim3(std::min(64, (N + 255) / 256), batch), 256, 0, s>>>(t->out, target, d.c_out,
@@ -733,13 +735,7 @@ int bvf_fno_bf16_forward(bvf_fno_bf16 *t, int batch, const float *d_in, float *d
 {
     if (!t || !d_in || !d_out || batch < 1 || batch > t->Bmax)
         return b16_fail(BVF_E_ARG, "bvf_fno_bf16_forward: bad argument");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int rc = forward(t, batch, d_in, s);
-    if (rc != BVF_OK) return rc;
-    BCK(cudaMemcpyAsync(d_out, t->out, (size_t)batch * t->d.c_out * t->N * sizeof(float),
-                        cudaMemcpyDeviceToDevice, s),
-        "bvf_fno_bf16_forward: output");
-    return BVF_OK;
+    return forward(t, batch, d_in, d_out, false, static_cast<cudaStream_t>(stream));
 }
 
 int bvf_fno_bf16_gradient(bvf_fno_bf16 *t, int batch, const float *d_in, const float *d_target,

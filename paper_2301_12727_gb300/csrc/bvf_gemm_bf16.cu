@@ -21,6 +21,7 @@
 // the flag and ends.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <atomic>
 
 #include <algorithm>
 #include <cmath>
@@ -216,9 +217,15 @@ template <int BN>
 cudaError_t launch_gemm_t(const bvf_gemm &g, int *flag, cudaStream_t s)
 {
     const dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, g.batch * g.ksplit);
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         GemmLayout<BN>::bytes);
-    if (e != cudaSuccess) return e;
+    // the shared-memory limit is raised once per process, so that later
+    // launches make no other runtime call (a forward can be recorded in a graph)
+    static std::atomic<int> raised{0};
+    if (!raised.load(std::memory_order_acquire)) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmLayout<BN>::bytes);
+        if (e != cudaSuccess) return e;
+        raised.store(1, std::memory_order_release);
+    }
     k_gemm_bf16<BN><<<grid, 128, GemmLayout<BN>::bytes, s>>>(g, flag);
     return cudaGetLastError();
 }

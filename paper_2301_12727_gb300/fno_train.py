@@ -100,8 +100,10 @@ def focal_metrics(pred, true, dx):
 
 def time_plan_vs_surrogate(grid, dx, f0, d, weights, seed, reps=5):
     """Milliseconds of one plan of the library (both FDTD runs, E_L, the 40 s /
-    30 % / 80 s BHTE) and of one surrogate inference (features + network, TF32
-    and BF16 paths) on the same placement."""
+    30 % / 80 s BHTE), of the same plan without the thermal step, and of one
+    surrogate inference (features + network) on the same placement: TF32 and
+    BF16 paths launched call by call, and the TF32 path replayed from a
+    recorded CUDA graph (one launch, as a planning service would repeat it)."""
     import torch
     from . import bvf, fno, plan, synth
     nx, ny, nz = grid
@@ -123,6 +125,7 @@ def time_plan_vs_surrogate(grid, dx, f0, d, weights, seed, reps=5):
         return e0.elapsed_time(e1) / reps
 
     ms_plan = timed(lambda: pl.run(idx, c.materials, c.bowl))
+    ms_fdtd = timed(lambda: pl.run(idx, c.materials, c.bowl, plan.ThermalRegime(t_on=0.0, t_off=0.0)))
     pl.close()
     src = bvf.rs_plane(c.bowl, nx, ny, dx, c.k_src * dx, f0)
     feats = torch.empty((FEATURES, nz, ny, nx), dtype=torch.float32, device="cuda")
@@ -134,11 +137,37 @@ def time_plan_vs_surrogate(grid, dx, f0, d, weights, seed, reps=5):
         fno.bvf_fno_features(idx, c.materials, synth.water_row(f0), f0, c.k_src, src,
                              c.bowl["p0"], feats)
 
-    ms_tf32 = timed(lambda: (feat(), tf32(feats, out)))
-    ms_bf16 = timed(lambda: (feat(), bf.forward(feats[None], out[None])))
+    def infer():
+        feat()
+        tf32(feats, out)
+
+    def infer_bf16():
+        feat()
+        bf.forward(feats[None], out[None])
+
+    def graphed(fn):
+        # fn recorded once in a CUDA graph (after a warm call on a side stream)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    ms_tf32 = timed(infer)
+    ms_bf16 = timed(infer_bf16)
+    g32, g16 = graphed(infer), graphed(infer_bf16)
+    ms_graph = timed(g32.replay)
+    ms_graph16 = timed(g16.replay)
     tf32.close()
     bf.close()
-    return ms_plan, ms_tf32, ms_bf16
+    return dict(plan=ms_plan, plan_without_bhte=ms_fdtd, surrogate_tf32=ms_tf32,
+                surrogate_tf32_graph=ms_graph, surrogate_bf16=ms_bf16,
+                surrogate_bf16_graph=ms_graph16)
 
 
 def main(argv=None):
@@ -158,6 +187,7 @@ def main(argv=None):
     ap.add_argument("--layers", type=int, default=4)
     ap.add_argument("--hidden", type=int, default=128)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--save", default="", help="write the trained blob (float32) to this .npy")
     args = ap.parse_args(argv)
     from . import build as _b
     _b.build()
@@ -189,6 +219,8 @@ def main(argv=None):
     t_train = time.time() - t1
     w = net.weights()
     net.close()
+    if args.save:
+        np.save(args.save, w)
 
     # held-out skulls through both CUDA inference paths with the trained weights
     tf32 = fno.Surrogate(d, w)
@@ -209,7 +241,11 @@ def main(argv=None):
     tf32.close()
     bf.close()
     rows, el_err = np.array(rows), np.array(el_err)
-    ms_plan, ms_tf32, ms_bf16 = time_plan_vs_surrogate(grid, args.dx, args.f0, d, w, 999)
+    # the accuracy figures are printed first, so that a failure of the timing
+    # leg does not lose them
+    print(json.dumps({"held_out_focal_amp_err_median_tf32": float(np.median(rows[:, 1])),
+                      "train_loss_first_last": [hist[0], hist[-1]]}), flush=True)
+    tm = time_plan_vs_surrogate(grid, args.dx, args.f0, d, w, 999)
     q = lambda a, p: float(np.quantile(a, p))
     tr_max = ytr.flatten(1).max(dim=1).values
     res = {"grid": list(grid), "dx_m": args.dx, "f0_hz": args.f0, "dims": d,
@@ -230,10 +266,15 @@ def main(argv=None):
                     "focus_dist_mm_median": q(rows[:, 5], 0.5) * 1e3,
                     "EL_rel_err_median": q(el_err[:, 1], 0.5), "EL_rel_err_p90": q(el_err[:, 1], 0.9)},
            "tf32_vs_bf16_max_rel": agree,
-           "same_workload_timing_ms": {"plan": ms_plan, "surrogate_tf32": ms_tf32,
-                                       "surrogate_bf16": ms_bf16,
-                                       "speedup_tf32": ms_plan / ms_tf32,
-                                       "speedup_bf16": ms_plan / ms_bf16}}
+           "same_workload_timing_ms": tm,
+           "speedup_vs_plan": {"tf32": tm["plan"] / tm["surrogate_tf32"],
+                               "tf32_graph": tm["plan"] / tm["surrogate_tf32_graph"],
+                               "bf16": tm["plan"] / tm["surrogate_bf16"],
+                               "bf16_graph": tm["plan"] / tm["surrogate_bf16_graph"]},
+           "speedup_vs_plan_fdtd": {"tf32_graph": tm["plan_without_bhte"]
+                                    / tm["surrogate_tf32_graph"],
+                                    "bf16_graph": tm["plan_without_bhte"]
+                                    / tm["surrogate_bf16_graph"]}}
     print(json.dumps(res), flush=True)
     return 0
 

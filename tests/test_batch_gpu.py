@@ -120,3 +120,68 @@ def test_gpu_batch_rejects_grids_off_the_tma_path(mods):
     with pytest.raises(bvf.BvfError):
         bvf.Batch([s])
     s.close()
+
+
+def test_gpu_batch_graph_matches_single_runs_bitwise(mods):
+    """The sweep recorded as one CUDA graph of per-domain launches on three
+    branches: the first call records and replays, a second call after
+    bvf_reset replays the same recording; both give the single-run results
+    bit for bit (state, peak, FP64 amplitude and phase), and a call from
+    other step counts records anew."""
+    bvf, synth = mods
+    specs = synth.sweep_specs(n=4, seed=11, n_min=40, n_max=72)
+    n_steps = [45, 70, 30, 55]
+    ref = []
+    for spec, n in zip(specs, n_steps):
+        c, s, cap = make(bvf, synth, spec, n)
+        s.run(n, peak_from=cap[0], dft_start=cap[1], dft_steps=cap[2])
+        s.synchronize()
+        ref.append(outputs(s))
+        s.close()
+    made = [make(bvf, synth, spec, n) for spec, n in zip(specs, n_steps)]
+    solvers = [m[1] for m in made]
+    caps = [m[2] for m in made]
+    b = bvf.Batch(solvers)
+    for rep in range(2):
+        for s in solvers:
+            s.reset()
+        b.run_graph(n_steps, caps=caps, n_branches=3)
+        for d, s in enumerate(solvers):
+            s.synchronize()
+            assert s.stats().steps == n_steps[d]
+            for a, r in zip(outputs(s), ref[d]):
+                assert np.array_equal(a, r), (rep, d)
+    # continuing from the reached steps records a new graph (no capture window)
+    b.run_graph(5, n_branches=2)
+    for d, s in enumerate(solvers):
+        s.synchronize()
+        assert s.stats().steps == n_steps[d] + 5
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_gpu_batch_tune_domains_picks_a_candidate_and_keeps_results(mods):
+    """The per-domain z-chunk tuner returns one of the candidates for every
+    domain, leaves the contexts reset, and runs after it equal single runs."""
+    bvf, synth = mods
+    specs = synth.sweep_specs(n=2, seed=3, n_min=48, n_max=64)
+    made = [make(bvf, synth, spec, 40) for spec in specs]
+    solvers = [m[1] for m in made]
+    b = bvf.Batch(solvers)
+    best = b.tune_domains(trial_steps=4, candidates=(6, 9, 16))
+    assert all(k in (6, 9, 16) or k == s.shape[0] for k, s in zip(best, solvers))
+    for s in solvers:
+        assert s.stats().steps == 0
+    b.run_streams(40, caps=[m[2] for m in made], n_streams=2)
+    for s, spec in zip(solvers, specs):
+        s.synchronize()
+        c, r, cap = make(bvf, synth, spec, 40)
+        r.run(40, peak_from=cap[0], dft_start=cap[1], dft_steps=cap[2])
+        r.synchronize()
+        for a, x in zip(outputs(s), outputs(r)):
+            assert np.array_equal(a, x)
+        r.close()
+    b.close()
+    for s in solvers:
+        s.close()
