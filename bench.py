@@ -686,11 +686,11 @@ def _sweep_domain(spec_steps):
 def sweep_leg(cases, steps, warmup):
     """Batched planning sweep over `cases` (seeded domains of uneven size,
     frequency, tilt and skull): the same FDTD runs of every domain timed
-    (CUDA events, min over `steps` repetitions after `warmup`) in four modes:
-    one after another, per-domain launches on 8 streams, the sweep recorded
-    as one CUDA graph of per-domain launches on 8 branches (after the
-    per-domain z-chunk autotuner), and the persistent work-list kernels
-    replayed from a graph.  Every mode gives the sequential results bit for
+    (CUDA events, min over `steps` repetitions after `warmup`) in five modes:
+    one after another (with the default and with the tuned z-chunks),
+    per-domain launches on 8 streams, the sweep recorded as one CUDA graph of
+    per-domain launches on 8 branches (after the per-domain z-chunk
+    autotuner), and the persistent work-list kernels replayed from a graph.  Every mode gives the sequential results bit for
     bit (checked on the peak maps)."""
     import torch
     from paper_2301_12727_gb300 import bvf
