@@ -687,10 +687,11 @@ def sweep_leg(cases, steps, warmup):
     """Batched planning sweep over `cases` (seeded domains of uneven size,
     frequency, tilt and skull): the same FDTD runs of every domain timed
     (CUDA events, min over `steps` repetitions after `warmup`) in five modes:
-    one after another (with the default and with the tuned z-chunks),
+    one after another (with the default and with the tuned tiles),
     per-domain launches on 8 streams, the sweep recorded as one CUDA graph of
-    per-domain launches on 8 branches (after the per-domain z-chunk
-    autotuner), and the persistent work-list kernels replayed from a graph.  Every mode gives the sequential results bit for
+    per-domain launches on 8 branches (after the per-domain tile autotuner:
+    rows of the x-y tile and z-planes per block), and the persistent
+    work-list kernels replayed from a graph.  Every mode gives the sequential results bit for
     bit (checked on the peak maps)."""
     import torch
     from paper_2301_12727_gb300 import bvf
@@ -747,14 +748,16 @@ def sweep_leg(cases, steps, warmup):
     rate = lambda ms: vox * n / (ms / 1e3) / 1e9
     out = {"domains": len(cases), "voxels_total": vox, "fdtd_steps_each": n,
            "sequential": {"value": rate(ms_seq), "ms": ms_seq},
-           "sequential_tuned_z_chunks": {"value": rate(ms_seq_tuned), "ms": ms_seq_tuned},
+           "sequential_tuned_tiles": {"value": rate(ms_seq_tuned), "ms": ms_seq_tuned},
            "streams_8": {"value": rate(ms_str), "ms": ms_str,
                          "speedup_vs_sequential": ms_seq / ms_str},
            "graph_8_branches_tuned": {"value": rate(ms_graph), "ms": ms_graph,
                                       "speedup_vs_sequential": ms_seq / ms_graph,
                                       "speedup_vs_sequential_tuned": ms_seq_tuned / ms_graph,
                                       "launches": 1,
-                                      "z_chunks": sorted(set(int(k) for k in tuned))},
+                                      "tiles_chosen": {"%dx%d" % (t, k): sum(1 for x in tuned
+                                                                          if x == (t, k))
+                                                       for t, k in sorted(set(tuned))}},
            "persistent_graph": {"value": rate(ms_pers), "ms": ms_pers,
                                 "speedup_vs_sequential": ms_seq / ms_pers, "z_chunk": best_kc},
            "unit": UNIT, "results_equal_sequential": bool(same)}

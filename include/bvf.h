@@ -239,6 +239,21 @@ int bvf_reset(bvf_ctx *ctx, void *stream);
  * fewer steps, having waited for them (bvf_get_stats gives the count). */
 int bvf_run_acoustic(bvf_ctx *ctx, int n_steps, const bvf_capture *cap, void *stream);
 
+/* Tile of the TMA-fed acoustic kernels (no counterpart in the paper: how the
+ * grid is cut into blocks, which changes no result, bit for bit).  A block
+ * owns an x-y tile 32 voxels wide and tile_y rows high (4, 8 or 16; 0 = 8)
+ * and marches kchunk z-planes (0 = a default that fills the GPU about six
+ * times).  Heights other than 8 apply to contexts with two SLS mechanisms
+ * (n_sls = 2, the method's); other contexts use 8.  bvf_set_tile keeps the
+ * choice in the context for later bvf_run_acoustic calls; bvf_get_tile
+ * reports the height and z-chunk the kernels use.  Errors: BVF_E_ARG. */
+typedef struct bvf_tile {
+    int tile_y;
+    int kchunk;
+} bvf_tile;
+int bvf_set_tile(bvf_ctx *ctx, int tile_y, int kchunk);
+int bvf_get_tile(const bvf_ctx *ctx, bvf_tile *out);
+
 /* Wall-clock budget (seconds, 0 = none, the default) of each later
  * bvf_run_acoustic and bvf_run_thermal call on this context: failure
  * detection for planning services, which must not wait without bound on one
@@ -485,7 +500,7 @@ int bvf_batch_run_streams(bvf_batch *b, const int *n_steps, const bvf_capture *c
  * branches (as bvf_batch_run_streams deals them over streams), recorded once
  * and replayed with a single graph launch on `stream`, so the host issues one
  * launch per sweep and the branches' kernels share the GPU.  The recording is
- * kept and replayed while the call's arguments, the contexts' z-chunks and
+ * kept and replayed while the call's arguments, the contexts' tiles and
  * the step counts the contexts start from are those it was recorded for
  * (e.g. the same sweep after bvf_reset); anything else records anew, which
  * waits for `stream`.  Results are those of bvf_run_acoustic, bit for bit.
@@ -495,12 +510,15 @@ int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *cap
                         void *stream);
 
 /* Per-domain tile autotuner: for every context, times trial_steps steps (after
- * two warm-up steps) with each candidate z-chunk (planes per block, the tile's
- * z extent; the x-y tile is 32 x 8), keeps the fastest in the context (used by
- * bvf_run_acoustic and the modes above) and writes it to h_best[d] (may be
- * NULL).  Leaves every context reset (bvf_reset). */
-int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,
-                           int *h_best, void *stream);
+ * two warm-up steps) with each candidate tile (bvf_tile: rows of the x-y tile
+ * and z-planes per block; candidates with a height other than 0 or 8 are
+ * skipped for contexts without two SLS mechanisms), keeps the fastest in the
+ * context (as bvf_set_tile; used by bvf_run_acoustic and the run modes above)
+ * and writes it to h_best[d] (may be NULL).  Leaves every context reset
+ * (bvf_reset).  Errors: BVF_E_ARG (a height other than 0, 4, 8, 16 or a
+ * negative z-chunk). */
+int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candidates,
+                           int n_candidates, bvf_tile *h_best, void *stream);
 
 /* Tile autotuner: times trial_steps steps of every domain for each candidate
  * z-chunk length, returns the fastest and its time per step (ms), and leaves

@@ -31,7 +31,8 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_batch_tune", "bvf_batch_launches", "bvf_batch_run_streams", "bvf_plan",
            "bvf_rs_elements", "bvf_set_time_budget", "bvf_state_bytes", "bvf_state_save",
            "bvf_state_load", "bvf_test_withhold_copy", "bvf_bowl_array", "bvf_steer_weights",
-           "bvf_time_reversal_plane", "bvf_batch_run_graph", "bvf_batch_tune_domains")
+           "bvf_time_reversal_plane", "bvf_batch_run_graph", "bvf_batch_tune_domains",
+           "bvf_set_tile", "bvf_get_tile")
 
 
 class BvfError(RuntimeError):
@@ -86,6 +87,14 @@ class PlanParams(ctypes.Structure):
 class PlanOut(ctypes.Structure):
     _fields_ = [("EL", ctypes.c_double), ("TS", ctypes.c_double), ("Iw_max", ctypes.c_double),
                 ("p_scale", ctypes.c_double), ("z_m", ctypes.c_int)]
+
+
+class Tile(ctypes.Structure):
+    _fields_ = [("tile_y", ctypes.c_int), ("kchunk", ctypes.c_int)]
+
+
+# candidates of the per-domain tile autotuner: (rows of the x-y tile, z-planes per block)
+TILE_CANDIDATES = tuple((t, k) for t in (8, 4, 16) for k in (6, 8, 10, 13, 16, 24))
 
 
 class Stats(ctypes.Structure):
@@ -153,7 +162,10 @@ def lib():
                                vp, ctypes.POINTER(PlanOut), vp]
         L.bvf_set_time_budget.argtypes = [vp, d]
         L.bvf_batch_run_graph.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
-        L.bvf_batch_tune_domains.argtypes = [vp, i, ctypes.POINTER(i), i, ctypes.POINTER(i), vp]
+        L.bvf_batch_tune_domains.argtypes = [vp, i, ctypes.POINTER(Tile), i, ctypes.POINTER(Tile),
+                                             vp]
+        L.bvf_set_tile.argtypes = [vp, i, i]
+        L.bvf_get_tile.argtypes = [vp, ctypes.POINTER(Tile)]
         L.bvf_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.bvf_state_save.argtypes = [vp, vp, ctypes.c_size_t, vp]
         L.bvf_state_load.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -484,6 +496,16 @@ class Solver:
     def set_time_budget(self, seconds):
         bvf_set_time_budget(self.ctx, seconds)
 
+    def set_tile(self, tile_y=0, kchunk=0):
+        """Rows of the x-y tile (0, 4, 8, 16) and z-planes per block (0 = default)."""
+        _check(lib().bvf_set_tile(self.ctx, int(tile_y), int(kchunk)), self.ctx)
+
+    def tile(self):
+        """(tile_y, kchunk) the kernels use."""
+        t = Tile()
+        _check(lib().bvf_get_tile(self.ctx, ctypes.byref(t)), self.ctx)
+        return t.tile_y, t.kchunk
+
     def save_state(self, stream=None):
         """Snapshot of the acoustic state in a fresh uint8 CUDA tensor."""
         import torch
@@ -592,14 +614,15 @@ class Batch:
     def tune(self, trial_steps=20, candidates=(6, 8, 10, 13, 16, 24), stream=None):
         return bvf_batch_tune(self.handle, trial_steps, candidates, stream)
 
-    def tune_domains(self, trial_steps=10, candidates=(6, 8, 10, 13, 16, 24, 32), stream=None):
-        """Per-domain z-chunk autotuner; returns the chosen z-chunk of each domain."""
+    def tune_domains(self, trial_steps=10, candidates=TILE_CANDIDATES, stream=None):
+        """Per-domain tile autotuner over (tile rows, z-chunk) pairs; returns
+        the chosen (tile_y, kchunk) of each domain."""
         n = len(self.solvers)
-        cand = (ctypes.c_int * len(candidates))(*candidates)
-        best = (ctypes.c_int * n)()
+        cand = (Tile * len(candidates))(*[Tile(int(t), int(k)) for t, k in candidates])
+        best = (Tile * n)()
         _check(lib().bvf_batch_tune_domains(self.handle, trial_steps, cand, len(candidates), best,
                                             _stream(stream)))
-        return list(best)
+        return [(b.tile_y, b.kchunk) for b in best]
 
     def launches(self):
         out = ctypes.c_longlong()

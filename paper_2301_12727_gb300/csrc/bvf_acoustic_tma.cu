@@ -19,8 +19,8 @@
 //     x-slab CPML stay per voxel.  This halves the velocity kernel's
 //     instructions, which bound it.  The stress kernel is bound by the latency
 //     of its per-voxel streams instead: it keeps one voxel per thread (64
-//     registers, 32 resident warps per SM) and prefetches the next plane's
-//     streams into L2;
+//     registers, 32 resident warps per SM) and, with FP32 storage,
+//     prefetches the next plane's streams into L2;
 //   * velocity kernel: each stress array arrives in a box with exactly the
 //     halo its stencil needs; the velocities go straight to registers and
 //     back; copies for plane k+1 are issued while plane k is computed;
@@ -55,19 +55,26 @@ using st::tof;
 using st::splat;
 using st::vadd;
 
-constexpr int TX = 32, TY = 8;                      // voxels of a tile
+// A tile is TX = 32 voxels wide and TH rows high, TH = 4, 8 or 16 (a template
+// parameter of the single-domain kernels, chosen per context; the persistent
+// batch kernels use TY).
+constexpr int TX = 32, TY = 8;                      // width, default height
 constexpr int PX = TX / 2;                          // threads per tile row (a pair each)
 constexpr int NTH = PX * TY;                        // 128
-constexpr int IW = 48, IH = 9, IT = IW * IH;        // index box: x0 .. x0+47, y0 .. y0+8
-constexpr int IT_SLOT = 512;                        // bytes per index slot
+constexpr int IW = 48;                              // index box: x0 .. x0+47
+// Index box of a tile of height TH: rows y0 .. y0+TH, in a 128-byte ring slot.
+template <int TH>
+struct Idx {
+    static constexpr int H = TH + 1, BYTES = IW * H, SLOT = (BYTES + 127) / 128 * 128;
+};
 
 // Box geometry of a storage type: x-halo XO columns each side, so halo'd
 // boxes are BW = 32 + 2 XO wide (40 floats / 48 halves = 160 / 96 bytes).
-template <typename T>
+template <typename T, int TH = TY>
 struct Box {
     static constexpr int XO = 16 / (int)sizeof(T);
     static constexpr int BW = TX + 2 * XO;
-    static constexpr int VH = TY + 4;                 // 2 rows each side
+    static constexpr int VH = TH + 4;                 // 2 rows each side
     static constexpr int VT = BW * VH;                // full-halo box (elements)
 };
 
@@ -129,13 +136,13 @@ __device__ __forceinline__ void drain_after_timeout(uint64_t *bars, int a, int a
 // The plane loop is unrolled by the ring period R = 6 (every ring depth
 // divides it), so each unrolled copy reads fixed ring slots: every shared
 // memory access is one of five per-thread centres plus a constant.
-template <typename T>
+template <typename T, int TH = TY>
 struct VelLayout {
-    using B = Box<T>;
+    using B = Box<T, TH>;
     static constexpr int R = 6;                               // ring period = unroll
     static constexpr int RA = 2, RB = 6, RC = 6, RI = 3;      // ring depths (divide R)
-    static constexpr int XW = B::BW, XH = TY, YW = TX, YH = TY + 4;
-    static constexpr int TXX = XW * XH, TYY = YW * YH, TXY = B::VT, TZZ = TX * TY;
+    static constexpr int XW = B::BW, XH = TH, YW = TX, YH = TH + 4;
+    static constexpr int TXX = XW * XH, TYY = YW * YH, TXY = B::VT, TZZ = TX * TH;
     static constexpr int SA = TXX + TYY + TXY;                // elements per A slot (sxx, syy, sxy)
     static constexpr int SB = TXX + TYY;                      // B slot (sxz, syz)
     static constexpr int ES = (int)sizeof(T);
@@ -143,7 +150,7 @@ struct VelLayout {
     static constexpr int off_b = off_a + RA * SA * ES;        // k-2 .. k+2 (+1 spare)
     static constexpr int off_c = off_b + RB * SB * ES;        // szz: k-1 .. k+3 (+1 spare)
     static constexpr int off_i = off_c + RC * TZZ * ES;       // index: k .. k+2
-    static constexpr int off_bar = off_i + RI * IT_SLOT;
+    static constexpr int off_bar = off_i + RI * Idx<TH>::SLOT;
     static constexpr int off_abort = off_bar + 16;             // int: plane whose wait ran out
     static constexpr int off_end = off_abort + 16;
     static size_t bytes(int) { return off_end; }
@@ -160,13 +167,14 @@ struct VelLayout {
 // invalidated at the end and the first copies are fenced against the
 // previous tile's reads of the same shared memory.  Returns true (in every
 // thread) when a ring wait ran out; the tile's results are then incomplete.
-template <typename T, bool REUSE>
+template <typename T, bool REUSE, int TH = TY>
 __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityTmaMaps &tm,
                                               int kchunk, int bx, int by, int bz,
                                               unsigned char *smb)
 {
-    using Lay = VelLayout<T>;
-    using Bx = Box<T>;
+    using Lay = VelLayout<T, TH>;
+    using Bx = Box<T, TH>;
+    constexpr int IT = Idx<TH>::BYTES, IT_SLOT = Idx<TH>::SLOT;
     constexpr int XW = Lay::XW, YW = Lay::YW, VW = Bx::BW;
     constexpr int TXX = Lay::TXX, TYY = Lay::TYY, TZZ = Lay::TZZ;
     const T *smt = reinterpret_cast<const T *>(smb);
@@ -174,7 +182,7 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
     volatile int *s_abort = reinterpret_cast<volatile int *>(smb + Lay::off_abort);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PX + tx;
-    const int x0 = bx * TX, y0 = by * TY;
+    const int x0 = bx * TX, y0 = by * TH;
     const int i = x0 + 2 * tx, j = y0 + ty;         // the pair (i, i+1) of row j
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;              // nx is even: i + 1 < nx as well
@@ -411,13 +419,15 @@ __device__ __forceinline__ bool velocity_tile(const AcParams &p, const VelocityT
     return ab >= 0;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NTH, 6)
+// six resident blocks of 128 threads per SM at the default height (80
+// registers); the thread count times blocks per SM is kept for other heights
+template <typename T, int TH>
+__global__ void __launch_bounds__(PX * TH, 6 * TY / TH)
     k_velocity_tma(const __grid_constant__ AcParams p, int kchunk,
                    const __grid_constant__ VelocityTmaMaps tm)
 {
     extern __shared__ __align__(1024) unsigned char smb[];
-    velocity_tile<T, false>(p, tm, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
+    velocity_tile<T, false, TH>(p, tm, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
 }
 
 // ------------------------------------------------------------------ stress
@@ -426,13 +436,13 @@ __global__ void __launch_bounds__(NTH, 6)
 // variables, peak map, FP64 DFT sums) are read straight into registers at the
 // top of each plane, so their latency overlaps the ring wait and the
 // derivatives, and written back with coalesced stores.
-template <int L, typename T>
+template <int L, typename T, int TH = TY>
 struct StressLayout {
-    static constexpr int VT = Box<T>::VT, ES = (int)sizeof(T);
+    static constexpr int VT = Box<T, TH>::VT, ES = (int)sizeof(T);
     static constexpr int RV = 7, RI = 4;                      // ring depths
     static constexpr int off_v = 0;                           // vx, vy, vz: k-2 .. k+4
     static constexpr int off_i = off_v + RV * 3 * VT * ES;    // index: k .. k+3
-    static constexpr int off_bar = off_i + RI * IT_SLOT;
+    static constexpr int off_bar = off_i + RI * Idx<TH>::SLOT;
     static constexpr int off_abort = off_bar + 24;            // int: plane whose wait ran out
     static constexpr int off_lut = off_bar + 32;
     static size_t bytes(int n_mat) { return off_lut + (size_t)n_mat * sizeof(st::StressCoef); }
@@ -446,13 +456,14 @@ struct StressLayout {
 constexpr int SNTH = TX * TY;
 
 // One tile (bx, by) over z-chunk bz; REUSE and the result as for velocity_tile.
-template <int L, typename T, bool REUSE>
+template <int L, typename T, bool REUSE, int TH = TY>
 __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMaps &tm,
                                             const StepParam &st, int kchunk, int bx, int by,
                                             int bz, unsigned char *smb)
 {
-    using Lay = StressLayout<L, T>;
-    using Bx = Box<T>;
+    using Lay = StressLayout<L, T, TH>;
+    using Bx = Box<T, TH>;
+    constexpr int IT = Idx<TH>::BYTES, IT_SLOT = Idx<TH>::SLOT, NT = TX * TH;
     constexpr int VW = Bx::BW, VT = Bx::VT;
     const T *smt = reinterpret_cast<const T *>(smb);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
@@ -460,12 +471,12 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
     st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(smb + Lay::off_lut);
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x0 = bx * TX, y0 = by * TY;
+    const int x0 = bx * TX, y0 = by * TH;
     const int i = x0 + tx, j = y0 + ty;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const bool live = i < nx && j < ny;
     const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
-    for (int m = tid; m < p.n_mat; m += SNTH) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
+    for (int m = tid; m < p.n_mat; m += NT) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
     if (tid == 0) {
         for (int b = 0; b < 3; ++b) tma::mbar_init(&bars[b], 1);
         tma::mbar_init_fence();
@@ -516,7 +527,10 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
     // variables of a component, mechanisms adjacent) or 32 doubles (the DFT
     // sums); its 128-byte lines are numbered over all streams and thread
     // (row r, slot a) prefetches line a of row y0 + r.  Every line starts at
-    // an element of the row segment, inside its array.
+    // an element of the row segment, inside its array.  FP32 storage only:
+    // with FP16 storage the kernel is bound by issue, not by the latency of
+    // its streams, and the prefetch's instructions cost more than it saves.
+    constexpr bool PREFETCH = sizeof(T) == 4;
     const int pf_r = tid >> 5, pf_a = tid & 31;
     const bool pk_on = (st.flags & kStepPeak) != 0, dft_on = (st.flags & kStepDft) != 0;
     constexpr int LS = (32 * (int)sizeof(T) + 127) / 128;              // lines of a stress row
@@ -545,12 +559,12 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
         }
         tma::prefetch_l2(ln);
     };
-    prefetch_plane(k0);
+    if (PREFETCH) prefetch_plane(k0);
 
     // Blocks whose tile touches no CPML slab in x or y and holds no ghost
     // or out-of-grid point run a copy of the loop without that code.
     const bool edge = !(x0 >= p.P && x0 + TX - 1 < nx - p.P - 1 && y0 >= p.P &&
-                        y0 + TY - 1 < ny - p.P - 1);
+                        y0 + TH - 1 < ny - p.P - 1);
     auto march = [&](auto edge_tag) {
     constexpr bool EDGE = decltype(edge_tag)::value;
     const bool lv = EDGE ? live : true;
@@ -562,7 +576,7 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
             tma::fence_async_smem();
             issue(k + 2, &bars[(it + 2) % 3], false);
         }
-        prefetch_plane(k + 1);
+        if (PREFETCH) prefetch_plane(k + 1);
         const int q = k * (nx * ny) + j * nx + i;
         // per-voxel loads first, in flight while the ring wait and the
         // derivatives proceed
@@ -739,13 +753,394 @@ __device__ __forceinline__ bool stress_tile(const AcParams &p, const StressTmaMa
     return ab >= 0;
 }
 
-template <int L, int MINB, typename T>
-__global__ void __launch_bounds__(SNTH, MINB)
+// ------------------------------------------------ stress, FP16 storage, pairs
+// With FP16 storage the stress update is bound by issue, so it takes the
+// velocity kernel's layout instead: 16 x 8 threads, thread (tx, ty) owns the
+// voxel pair (x0 + 2 tx, x0 + 2 tx + 1) of row y0 + ty.  The pair's streams
+// stay packed as loaded (a half2 per stress, the four halves of a
+// component's two memory variables as one 8-byte word) and are unpacked
+// where they are used, so two voxels' streams take the registers one voxel's
+// take in FP32.  The rings, the copies and every arithmetic step are those of
+// stress_tile on FP32x2 pairs (bit for bit the same results).
+constexpr int kStressH2Blocks = 5;   // resident blocks of 128 threads per SM (96 registers)
+
+__device__ __forceinline__ float2 h2f(__half2 v) { return __half22float2(v); }
+__device__ __forceinline__ __half2 f2h(float2 v) { return __floats2half2_rn(v.x, v.y); }
+
+// the two mechanisms of a component for both voxels: halves
+// (q, 0), (q, 1), (q + 1, 0), (q + 1, 1) of one 8-byte word
+__device__ __forceinline__ void unpack_mem2(uint2 w, float2 &r0, float2 &r1)
+{
+    const float2 a = h2f(*reinterpret_cast<const __half2 *>(&w.x));   // (q,0), (q,1)
+    const float2 b = h2f(*reinterpret_cast<const __half2 *>(&w.y));   // (q+1,0), (q+1,1)
+    r0 = make_float2(a.x, b.x);
+    r1 = make_float2(a.y, b.y);
+}
+__device__ __forceinline__ uint2 pack_mem2(float2 r0, float2 r1)
+{
+    const __half2 a = __floats2half2_rn(r0.x, r1.x), b = __floats2half2_rn(r0.y, r1.y);
+    uint2 w;
+    w.x = *reinterpret_cast<const unsigned *>(&a);
+    w.y = *reinterpret_cast<const unsigned *>(&b);
+    return w;
+}
+
+template <int L, bool REUSE, int TH = TY>
+__device__ __forceinline__ bool stress_tile_h2(const AcParams &p, const StressTmaMaps &tm,
+                                               const StepParam &st, int kchunk, int bx, int by,
+                                               int bz, unsigned char *smb)
+{
+    using T = __half;
+    using Lay = StressLayout<L, T, TH>;
+    using Bx = Box<T, TH>;
+    constexpr int IT = Idx<TH>::BYTES, IT_SLOT = Idx<TH>::SLOT, NT = PX * TH;
+    constexpr int VW = Bx::BW, VT = Bx::VT;
+    const T *smt = reinterpret_cast<const T *>(smb);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smb + Lay::off_bar);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(smb + Lay::off_abort);
+    st::StressCoef *s_lut = reinterpret_cast<st::StressCoef *>(smb + Lay::off_lut);
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * PX + tx;
+    const int x0 = bx * TX, y0 = by * TH;
+    const int i = x0 + 2 * tx, j = y0 + ty;           // the pair (i, i+1) of row j
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const bool live = i < nx && j < ny;                // nx is even: i + 1 < nx as well
+    const int k0 = bz * kchunk, k1 = min(nz, k0 + kchunk);
+    for (int m = tid; m < p.n_mat; m += NT) s_lut[m] = st::make_stress_coef(p.lut[m], p.Lf);
+    if (tid == 0) {
+        for (int b = 0; b < 3; ++b) tma::mbar_init(&bars[b], 1);
+        tma::mbar_init_fence();
+        *s_abort = -1;
+    }
+    __syncthreads();
+
+    constexpr unsigned VT_BYTES = VT * Lay::ES;
+    auto oV = [&](int pl) { return Lay::off_v + ((pl - k0 + 2) % Lay::RV) * 3 * (int)VT_BYTES; };
+    auto oI = [&](int pl) { return Lay::off_i + ((pl - k0) % Lay::RI) * IT_SLOT; };   // bytes
+    auto issue = [&](int kk, uint64_t *bar, bool first) {
+        const unsigned nv = first ? 5 : 1;
+        tma::mbar_expect_tx(bar, nv * 3 * VT_BYTES + (first ? 2 : 1) * IT);
+        if (p.hold == 2 && kk == p.hold_plane + 2) return;    // test hook: armed, none issued
+        for (int pl = first ? kk - 2 : kk + 2; pl <= kk + 2; ++pl)
+            for (int a = 0; a < 3; ++a)
+                tma::load3d(smb + oV(pl) + a * VT_BYTES, &tm.v[a], x0 - Bx::XO, y0 - 2, pl, bar);
+        for (int pl = first ? kk : kk + 1; pl <= kk + 1; ++pl)
+            tma::load3d(smb + oI(pl), &tm.idx, x0, y0, pl, bar);
+    };
+    if (tid == 0) {
+        if (REUSE) tma::fence_async_smem();
+        issue(k0, &bars[0], true);
+        if (k0 + 1 < k1) issue(k0 + 1, &bars[1], false);
+    }
+
+    const st::Dx ix = st::make_dx(p.inv_dx);
+    const int cv = (ty + 2) * VW + 2 * tx + Bx::XO;    // even: every pair read is aligned
+    const int ci = ty * IW + 2 * tx;
+    const int xs[2] = {slab_pos(i, nx, p.P), slab_pos(i + 1, nx, p.P)};
+    const int ys = slab_pos(j, ny, p.P);
+    const int Sxs = nz * ny * p.W, Sys = nz * p.W * nx, Szs = p.W * ny * nx;
+    const float2 *pmlx = p.pml, *pmly = p.pml + 2 * p.nmax, *pmlz = p.pml + 4 * p.nmax;
+    T *const gs[6] = {static_cast<T *>(p.sxx), static_cast<T *>(p.syy), static_cast<T *>(p.szz),
+                      static_cast<T *>(p.sxy), static_cast<T *>(p.sxz), static_cast<T *>(p.syz)};
+    T *__restrict__ mem = static_cast<T *>(p.mem);
+    // the pair's second voxel is not the last point in x (the first never is)
+    const bool ix1 = i + 1 < nx - 1;
+
+    const int vbase = Lay::off_v / Lay::ES, vend = vbase + Lay::RV * 3 * VT;
+    const int ibase = Lay::off_i, iend = ibase + Lay::RI * IT_SLOT;
+    int vM2 = vbase + cv, vM1 = vM2 + 3 * VT, vK = vM1 + 3 * VT, vP1 = vK + 3 * VT,
+        vP2 = vP1 + 3 * VT;
+    int iK = ibase + ci, iK1 = iK + IT_SLOT;
+
+    const bool edge = !(x0 >= p.P && x0 + TX - 1 < nx - p.P - 1 && y0 >= p.P &&
+                        y0 + TH - 1 < ny - p.P - 1);
+    auto march = [&](auto edge_tag) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    const bool lv = EDGE ? live : true;
+    int it = 0;
+    for (int k = k0; k < k1; ++k, ++it) {
+        __syncthreads();
+        if (*s_abort >= 0) break;        // a wait of the previous plane ran out
+        if (tid == 0 && k + 2 < k1) {
+            tma::fence_async_smem();
+            issue(k + 2, &bars[(it + 2) % 3], false);
+        }
+        const int q = k * (nx * ny) + j * nx + i;
+        // the pair's streams, packed, in flight while the ring wait and the
+        // derivatives proceed
+        __half2 sp[6];
+        [[maybe_unused]] uint2 rp[6];      // L = 2: one word per component
+        [[maybe_unused]] __half2 rp1[6];   // L = 1
+        float2 pk = make_float2(0.0f, 0.0f);
+        double2 dC = make_double2(0.0, 0.0), dS = dC;
+        const int zs = slab_pos(k, nz, p.P);
+        const int ox[2] = {(k * ny + j) * p.W + xs[0], (k * ny + j) * p.W + xs[1]};
+        const int oy = (k * p.W + ys) * nx + i, oz = (zs * ny + j) * nx + i;
+        float qx[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+        float2 qy[3] = {pair(0.0f, 0.0f), pair(0.0f, 0.0f), pair(0.0f, 0.0f)};
+        float2 qz[3] = {qy[0], qy[0], qy[0]};
+        if (lv) {
+            if (EDGE) {
+#pragma unroll
+                for (int l = 0; l < 2; ++l)
+                    if (xs[l] >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) qx[l][c] = p.psx[(3 + c) * Sxs + ox[l]];
+                    }
+                if (ys >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) qy[c] = st::ld2(p.psy + (3 + c) * Sys + oy);
+                }
+            }
+            if (zs >= 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) qz[c] = st::ld2(p.psz + (3 + c) * Szs + oz);
+            }
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) sp[cc] = *reinterpret_cast<const __half2 *>(gs[cc] + q);
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) {
+                if constexpr (L == 2)
+                    rp[cc] = *reinterpret_cast<const uint2 *>(mem + mem_index(0, cc, q, p.fstride, 2));
+                else if constexpr (L == 1)
+                    rp1[cc] = *reinterpret_cast<const __half2 *>(mem + mem_index(0, cc, q, p.fstride, 1));
+            }
+            if (st.flags & kStepPeak) pk = *reinterpret_cast<const float2 *>(p.peak + q);
+            if (st.flags & kStepDft) {
+                dC = *reinterpret_cast<const double2 *>(p.dftC + q);
+                dS = *reinterpret_cast<const double2 *>(p.dftS + q);
+            }
+        }
+        const bool ready = tma::mbar_wait(&bars[it % 3], (it / 3) & 1, p.wait_limit);
+        if (!ready) *s_abort = k;
+        if (ready && lv) {
+            const int vm2 = vM2, vm1 = vM1, vp1 = vP1, vp2 = vP2;
+            const unsigned char *I0 = smb + iK;
+            const unsigned char *I1 = smb + iK1;
+            const bool jy1 = !EDGE || j < ny - 1, kz1 = k < nz - 1;
+            const int ma = I0[0], mb = I0[1];
+            const st::StressCoef &ca = s_lut[ma], &cb = s_lut[mb];
+            const int vx = vK, vy = vK + VT, vz = vK + 2 * VT;
+            // a component's stress and memory variables are unpacked just
+            // before its update and stored right after it
+            float2 sv[6], rv[L > 0 ? L : 1][6];
+            auto unpack = [&](int cc) {
+                sv[cc] = h2f(sp[cc]);
+                if constexpr (L == 2)
+                    unpack_mem2(rp[cc], rv[0][cc], rv[1][cc]);
+                else if constexpr (L == 1)
+                    rv[0][cc] = h2f(rp1[cc]);
+            };
+            auto put_s = [&](int cc, bool both) {
+                if (both)
+                    *reinterpret_cast<__half2 *>(gs[cc] + q) = f2h(sv[cc]);
+                else
+                    gs[cc][q] = __float2half_rn(sv[cc].x);
+            };
+            auto put_r = [&](int cc, bool both) {
+                if constexpr (L == 2) {
+                    const uint2 w = pack_mem2(rv[0][cc], rv[1][cc]);
+                    T *r = mem + mem_index(0, cc, q, p.fstride, 2);
+                    if (both)
+                        *reinterpret_cast<uint2 *>(r) = w;
+                    else
+                        *reinterpret_cast<unsigned *>(r) = w.x;
+                } else if constexpr (L == 1) {
+                    T *r = mem + mem_index(0, cc, q, p.fstride, 1);
+                    if (both)
+                        *reinterpret_cast<__half2 *>(r) = f2h(rv[0][cc]);
+                    else
+                        *r = __float2half_rn(rv[0][cc].x);
+                }
+            };
+
+            // ---- normal stresses at (i, j, k), (i + 1, j, k)
+            float2 exx = dbw_x(lds2(smt + vx - 2), lds2(smt + vx), lds2(smt + vx + 2), ix);
+            float2 eyy = st::dbw<float2>(lds2(smt + vy - 2 * VW), lds2(smt + vy - VW),
+                                         lds2(smt + vy), lds2(smt + vy + VW), ix);
+            float2 ezz = st::dbw<float2>(lds2(smt + vm2 + 2 * VT), lds2(smt + vm1 + 2 * VT),
+                                         lds2(smt + vz), lds2(smt + vp1 + 2 * VT), ix);
+            if (EDGE) {
+#pragma unroll
+                for (int l = 0; l < 2; ++l)
+                    if (xs[l] >= 0)
+                        set_lane(exx, l, st::cpml_pre(p.psx + 3 * Sxs + ox[l], qx[l][0],
+                                                      __ldg(&pmlx[i + l]), lane(exx, l)));
+                if (ys >= 0) {
+                    const float2 w = __ldg(&pmly[j]);
+                    float2 t;
+                    eyy = st::cpml_v(qy[0], splat<float2>(w.x), splat<float2>(w.y), eyy, t);
+                    st::st2(p.psy + 3 * Sys + oy, t);
+                }
+            }
+            if (zs >= 0) {
+                const float2 w = __ldg(&pmlz[k]);
+                float2 t;
+                ezz = st::cpml_v(qz[0], splat<float2>(w.x), splat<float2>(w.y), ezz, t);
+                st::st2(p.psz + 3 * Szs + oz, t);
+            }
+            float2 srcv = pair(0.0f, 0.0f);
+            if ((st.flags & kStepSource) && k == p.k_src) {
+                const float4 a = *reinterpret_cast<const float4 *>(p.src + j * nx + i);
+                srcv = st::source_value<float2>(p.src_scale, pair(a.x, a.z), pair(a.y, a.w),
+                                                st.src_ws, st.src_wc);
+            }
+            unpack(0);
+            unpack(1);
+            unpack(2);
+            st::normal_update<L, float2>(p, pair(ca.piU, cb.piU), pair(ca.piT, cb.piT),
+                                         pair(ca.nmu2U, cb.nmu2U), pair(ca.nmu2T, cb.nmu2T), exx,
+                                         eyy, ezz, srcv, sv, rv);
+            const float2 pr = st::pressure(sv);
+            if (!isfinite(pr.x) || !isfinite(pr.y)) atomicOr(p.flag, 1);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                put_s(cc, true);
+                put_r(cc, true);
+            }
+
+            // ---- shear stresses (ghost points computed, not stored)
+            auto coef = [&](int mb0, int md0, int mf0, int mb1, int md1, int mf1, float2 &psic,
+                            float2 &thec) {
+                st::shear_coef(s_lut, ca, ma, mb0, md0, mf0, p.Lf, psic.x, thec.x);
+                st::shear_coef(s_lut, cb, mb, mb1, md1, mf1, p.Lf, psic.y, thec.y);
+            };
+            {                                        // sxy at (i+1/2, j+1/2, k)
+                float2 a = st::dfw<float2>(lds2(smt + vx - VW), lds2(smt + vx),
+                                           lds2(smt + vx + VW), lds2(smt + vx + 2 * VW), ix);
+                float2 b = dfw_x(lds2(smt + vy - 2), lds2(smt + vy), lds2(smt + vy + 2), ix);
+                if (EDGE && ys >= 0) {
+                    const float2 h = __ldg(&pmly[p.nmax + j]);
+                    float2 t;
+                    a = st::cpml_v(qy[1], splat<float2>(h.x), splat<float2>(h.y), a, t);
+                    if (jy1) st::st2_or_1(p.psy + 4 * Sys + oy, t, ix1);
+                }
+                if (EDGE) {
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        if (xs[l] < 0) continue;
+                        const float2 h = __ldg(&pmlx[p.nmax + i + l]);
+                        float t;
+                        set_lane(b, l, st::cpml_v(qx[l][1], h.x, h.y, lane(b, l), t));
+                        if (jy1 && (l == 0 || ix1)) p.psx[4 * Sxs + ox[l]] = t;
+                    }
+                }
+                float2 psic, thec;
+                coef(mb, I0[IW], I0[IW + 1], I0[2], I0[IW + 1], I0[IW + 2], psic, thec);
+                unpack(3);
+                st::shear_update<L, float2>(p, psic, thec, st::vadd(a, b), 3, sv, rv);
+                if (jy1) {
+                    put_s(3, ix1);
+                    put_r(3, ix1);
+                }
+            }
+            {                                        // sxz at (i+1/2, j, k+1/2)
+                float2 a = st::dfw<float2>(lds2(smt + vm1), lds2(smt + vx), lds2(smt + vp1),
+                                           lds2(smt + vp2), ix);
+                float2 b = dfw_x(lds2(smt + vz - 2), lds2(smt + vz), lds2(smt + vz + 2), ix);
+                if (zs >= 0) {
+                    const float2 h = __ldg(&pmlz[p.nmax + k]);
+                    float2 t;
+                    a = st::cpml_v(qz[1], splat<float2>(h.x), splat<float2>(h.y), a, t);
+                    if (kz1) st::st2_or_1(p.psz + 4 * Szs + oz, t, ix1);
+                }
+                if (EDGE) {
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        if (xs[l] < 0) continue;
+                        const float2 h = __ldg(&pmlx[p.nmax + i + l]);
+                        float t;
+                        set_lane(b, l, st::cpml_v(qx[l][2], h.x, h.y, lane(b, l), t));
+                        if (kz1 && (l == 0 || ix1)) p.psx[5 * Sxs + ox[l]] = t;
+                    }
+                }
+                float2 psic, thec;
+                coef(mb, I1[0], I1[1], I0[2], I1[1], I1[2], psic, thec);
+                unpack(4);
+                st::shear_update<L, float2>(p, psic, thec, st::vadd(a, b), 4, sv, rv);
+                if (kz1) {
+                    put_s(4, ix1);
+                    put_r(4, ix1);
+                }
+            }
+            {                                        // syz at (i, j+1/2, k+1/2)
+                float2 a = st::dfw<float2>(lds2(smt + vm1 + VT), lds2(smt + vy),
+                                           lds2(smt + vp1 + VT), lds2(smt + vp2 + VT), ix);
+                float2 b = st::dfw<float2>(lds2(smt + vz - VW), lds2(smt + vz),
+                                           lds2(smt + vz + VW), lds2(smt + vz + 2 * VW), ix);
+                if (zs >= 0) {
+                    const float2 h = __ldg(&pmlz[p.nmax + k]);
+                    float2 t;
+                    a = st::cpml_v(qz[2], splat<float2>(h.x), splat<float2>(h.y), a, t);
+                    if (jy1 && kz1) st::st2(p.psz + 5 * Szs + oz, t);
+                }
+                if (EDGE && ys >= 0) {
+                    const float2 h = __ldg(&pmly[p.nmax + j]);
+                    float2 t;
+                    b = st::cpml_v(qy[2], splat<float2>(h.x), splat<float2>(h.y), b, t);
+                    if (jy1 && kz1) st::st2(p.psy + 5 * Sys + oy, t);
+                }
+                float2 psic, thec;
+                coef(I0[IW], I1[0], I1[IW], I0[IW + 1], I1[1], I1[IW + 1], psic, thec);
+                unpack(5);
+                st::shear_update<L, float2>(p, psic, thec, st::vadd(a, b), 5, sv, rv);
+                if (jy1 && kz1) {
+                    put_s(5, true);
+                    put_r(5, true);
+                }
+            }
+
+            // ---- capture (ghost points are not written above)
+            if (st.flags & kStepPeak)
+                *reinterpret_cast<float2 *>(p.peak + q) =
+                    make_float2(fmaxf(pk.x, fabsf(pr.x)), fmaxf(pk.y, fabsf(pr.y)));
+            if (st.flags & kStepDft) {
+                *reinterpret_cast<double2 *>(p.dftC + q) =
+                    make_double2(fma((double)pr.x, st.cw, dC.x), fma((double)pr.y, st.cw, dC.y));
+                *reinterpret_cast<double2 *>(p.dftS + q) =
+                    make_double2(fma((double)pr.x, st.sw, dS.x), fma((double)pr.y, st.sw, dS.y));
+            }
+        }
+        // rotate the ring positions to plane k+1
+        vM2 = vM1; vM1 = vK; vK = vP1; vP1 = vP2;
+        vP2 += 3 * VT;
+        if (vP2 >= vend) vP2 -= Lay::RV * 3 * VT;
+        iK = iK1;
+        iK1 += IT_SLOT;
+        if (iK1 >= iend) iK1 -= Lay::RI * IT_SLOT;
+    }
+    };
+    if (edge)
+        march(std::true_type{});
+    else
+        march(std::false_type{});
+    __syncthreads();
+    const int ab = *s_abort;
+    if (ab >= 0 && tid == 0) drain_after_timeout<3>(bars, ab, 2, k0, k1, p.wait_limit, p.flag);
+    if (REUSE) {
+        __syncthreads();
+        if (tid == 0)
+            for (int b = 0; b < 3; ++b) tma::mbar_inval(&bars[b]);
+    }
+    return ab >= 0;
+}
+
+template <int L, int MINB, int TH>
+__global__ void __launch_bounds__(PX * TH, MINB)
+    k_stress_tma_h2(const __grid_constant__ AcParams p, int kchunk,
+                    const __grid_constant__ StressTmaMaps tm)
+{
+    extern __shared__ __align__(1024) unsigned char smb[];
+    stress_tile_h2<L, false, TH>(p, tm, p.st, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
+}
+
+template <int L, int MINB, typename T, int TH>
+__global__ void __launch_bounds__(TX * TH, MINB)
     k_stress_tma(const __grid_constant__ AcParams p, int kchunk,
                  const __grid_constant__ StressTmaMaps tm)
 {
     extern __shared__ __align__(1024) unsigned char smb[];
-    stress_tile<L, T, false>(p, tm, p.st, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
+    stress_tile<L, T, false, TH>(p, tm, p.st, kchunk, blockIdx.x, blockIdx.y, blockIdx.z, smb);
 }
 
 // ------------------------------------------------------------------ batch
@@ -853,9 +1248,10 @@ __global__ void k_step_advance(int *ctr) { *ctr += 1; }
 
 }  // namespace
 
+template <int TH = TY>
 static dim3 grid_tma(const AcParams &p, int kc)
 {
-    return dim3((p.nx + TX - 1) / TX, (p.ny + TY - 1) / TY, (p.nz + kc - 1) / kc);
+    return dim3((p.nx + TX - 1) / TX, (p.ny + TH - 1) / TH, (p.nz + kc - 1) / kc);
 }
 
 // The dynamic shared-memory limit of a kernel, raised once per process to the
@@ -871,34 +1267,64 @@ static cudaError_t raise_smem_once(K kernel, size_t bytes, std::atomic<int> &don
     return e;
 }
 
-template <typename T>
+static int chunk_of(const AcParams &p, int th)
+{
+    return p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz, th);
+}
+
+template <typename T, int TH>
 static cudaError_t launch_velocity_tma_t(const AcParams &p, const VelocityTmaMaps &tm,
                                          cudaStream_t s)
 {
-    const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
-    const size_t sm = VelLayout<T>::bytes(p.n_mat);
+    const int kc = chunk_of(p, TH);
+    const size_t sm = VelLayout<T, TH>::bytes(p.n_mat);
     static std::atomic<int> done{0};
-    cudaError_t e = raise_smem_once(k_velocity_tma<T>, VelLayout<T>::bytes(BVF_MAX_MATERIALS), done);
+    cudaError_t e = raise_smem_once(k_velocity_tma<T, TH>,
+                                    VelLayout<T, TH>::bytes(BVF_MAX_MATERIALS), done);
     if (e != cudaSuccess) return e;
-    k_velocity_tma<T><<<grid_tma(p, kc), dim3(PX, TY, 1), sm, s>>>(p, kc, tm);
+    k_velocity_tma<T, TH><<<grid_tma<TH>(p, kc), dim3(PX, TH, 1), sm, s>>>(p, kc, tm);
     return cudaGetLastError();
+}
+
+// tile heights other than TY are built for L = 2 (the method's two
+// mechanisms); other L take TY
+template <typename T>
+static cudaError_t launch_velocity_tma_h(const AcParams &p, const VelocityTmaMaps &tm,
+                                         cudaStream_t s)
+{
+    if (p.L == 2 && p.tile_y == 4) return launch_velocity_tma_t<T, 4>(p, tm, s);
+    if (p.L == 2 && p.tile_y == 16) return launch_velocity_tma_t<T, 16>(p, tm, s);
+    return launch_velocity_tma_t<T, TY>(p, tm, s);
 }
 
 cudaError_t launch_velocity_tma(const AcParams &p, const VelocityTmaMaps &tm, cudaStream_t s)
 {
-    return p.h16 ? launch_velocity_tma_t<__half>(p, tm, s) : launch_velocity_tma_t<float>(p, tm, s);
+    return p.h16 ? launch_velocity_tma_h<__half>(p, tm, s) : launch_velocity_tma_h<float>(p, tm, s);
 }
 
-template <int L, int MINB, typename T>
+// Resident blocks per SM at height TH: the thread count times blocks per SM
+// of the default height (four blocks of 256 threads for the scalar tile, five
+// of 128 for the paired FP16 tile) is kept, so are the registers per thread.
+template <int L, typename T, int TH>
 static cudaError_t launch_stress_tma_t(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
-    const int kc = p.kchunk > 0 ? p.kchunk : default_kchunk_tma(p.nx, p.ny, p.nz);
-    const size_t sm = StressLayout<L, T>::bytes(p.n_mat);
+    const int kc = chunk_of(p, TH);
+    const size_t sm = StressLayout<L, T, TH>::bytes(p.n_mat);
     static std::atomic<int> done{0};
-    cudaError_t e = raise_smem_once(k_stress_tma<L, MINB, T>,
-                                    StressLayout<L, T>::bytes(BVF_MAX_MATERIALS), done);
-    if (e != cudaSuccess) return e;
-    k_stress_tma<L, MINB, T><<<grid_tma(p, kc), dim3(TX, TY, 1), sm, s>>>(p, kc, tm);
+    if constexpr (std::is_same<T, __half>::value && L > 0) {
+        // FP16 storage: the paired tile (see stress_tile_h2)
+        constexpr int MB = kStressH2Blocks * TY / TH > 0 ? kStressH2Blocks * TY / TH : 1;
+        cudaError_t e = raise_smem_once(k_stress_tma_h2<L, MB, TH>,
+                                        StressLayout<L, T, TH>::bytes(BVF_MAX_MATERIALS), done);
+        if (e != cudaSuccess) return e;
+        k_stress_tma_h2<L, MB, TH><<<grid_tma<TH>(p, kc), dim3(PX, TH, 1), sm, s>>>(p, kc, tm);
+    } else {
+        constexpr int MB = 4 * TY / TH;
+        cudaError_t e = raise_smem_once(k_stress_tma<L, MB, T, TH>,
+                                        StressLayout<L, T, TH>::bytes(BVF_MAX_MATERIALS), done);
+        if (e != cudaSuccess) return e;
+        k_stress_tma<L, MB, T, TH><<<grid_tma<TH>(p, kc), dim3(TX, TH, 1), sm, s>>>(p, kc, tm);
+    }
     return cudaGetLastError();
 }
 
@@ -906,9 +1332,12 @@ template <typename T>
 static cudaError_t launch_stress_tma_l(const AcParams &p, const StressTmaMaps &tm, cudaStream_t s)
 {
     switch (p.L) {
-    case 0: return launch_stress_tma_t<0, 4, T>(p, tm, s);
-    case 1: return launch_stress_tma_t<1, 4, T>(p, tm, s);
-    case 2: return launch_stress_tma_t<2, 4, T>(p, tm, s);
+    case 0: return launch_stress_tma_t<0, T, TY>(p, tm, s);
+    case 1: return launch_stress_tma_t<1, T, TY>(p, tm, s);
+    case 2:
+        if (p.tile_y == 4) return launch_stress_tma_t<2, T, 4>(p, tm, s);
+        if (p.tile_y == 16) return launch_stress_tma_t<2, T, 16>(p, tm, s);
+        return launch_stress_tma_t<2, T, TY>(p, tm, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -983,9 +1412,10 @@ cudaError_t launch_batch_step(const BatchParams &bp, int L, int h16, int n_mat_m
 // z-chunk length of the TMA kernels: about six waves of four resident blocks
 // per SM on 152 SMs (13 planes on the 240 x 240 x 200 grid; 8 to 16 measure
 // within 3 % of each other there, 25 is 13 % slower).
-int default_kchunk_tma(int nx, int ny, int nz)
+int default_kchunk_tma(int nx, int ny, int nz, int tile_y)
 {
-    const long long tiles = (long long)((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    const int th = tile_y > 0 ? tile_y : TY;
+    const long long tiles = (long long)((nx + TX - 1) / TX) * ((ny + th - 1) / th);
     const long long target = 152LL * 4 * 6;
     long long chunks = (target + tiles - 1) / tiles;
     if (chunks < 1) chunks = 1;

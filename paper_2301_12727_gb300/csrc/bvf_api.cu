@@ -74,10 +74,13 @@ struct bvf_ctx {
     long long steps = 0, launches = 0, thermal_steps = 0;
     double courant = 0.0;
     int kchunk = 0;                   // z-planes per block (0 = default)
+    int tile_y = 0;                   // rows of an x-y tile (0 = 8; 4 or 16 with L = 2)
     bool tma = false;                 // velocity kernel fed by TMA
     bool tma_stress = false;          // stress kernel fed by TMA
-    StressTmaMaps smaps{};
+    StressTmaMaps smaps{};            // boxes of 8-row tiles
     VelocityTmaMaps vmaps{};
+    StressTmaMaps smaps_x[2]{};       // boxes of 4- and 16-row tiles
+    VelocityTmaMaps vmaps_x[2]{};
     std::string err;
     // per-launch event timing of the acoustic kernels
     bool timing = false;
@@ -324,16 +327,26 @@ void setup_maps(bvf_ctx *c)
     const size_t es = c->es;
     const unsigned bw = 32 + 2 * (unsigned)(16 / es);   // halo'd box width: 16 bytes each side
     auto fld = [&](int f) { return field_ptr(c, f); };
-    bool ok = true;
-    for (int v = 0; v < 3; ++v)
-        ok = ok && encode_map(&c->smaps.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, ST, es, bw, 12);
-    // velocity kernel boxes: the halo each stress array's stencil reads
-    const unsigned w6[6] = {bw, 32, 32, bw, bw, 32}, h6[6] = {8, 12, 8, 12, 8, 12};
-    for (int g6 = 0; g6 < 6; ++g6)
-        ok = ok && encode_map(&c->vmaps.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, ST, es, w6[g6],
-                              h6[g6]);
-    ok = ok && encode_map(&c->smaps.idx, c->index, nx, ny, nz, U8, 1, 48, 9);
-    c->vmaps.idx = c->smaps.idx;
+    // the boxes of tiles th rows high: velocities th + 4 rows (stress
+    // kernel), each stress array the halo its stencil reads (velocity
+    // kernel), the index th + 1 rows
+    auto encode_for = [&](unsigned th, StressTmaMaps &sm, VelocityTmaMaps &vm) {
+        bool ok = true;
+        for (int v = 0; v < 3; ++v)
+            ok = ok && encode_map(&sm.v[v], fld(BVF_FIELD_VX + v), nx, ny, nz, ST, es, bw, th + 4);
+        const unsigned w6[6] = {bw, 32, 32, bw, bw, 32},
+                       h6[6] = {th, th + 4, th, th + 4, th, th + 4};
+        for (int g6 = 0; g6 < 6; ++g6)
+            ok = ok && encode_map(&vm.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, ST, es, w6[g6],
+                                  h6[g6]);
+        ok = ok && encode_map(&sm.idx, c->index, nx, ny, nz, U8, 1, 48, th + 1);
+        vm.idx = sm.idx;
+        return ok;
+    };
+    bool ok = encode_for(8, c->smaps, c->vmaps);
+    if (c->L == 2)
+        ok = ok && encode_for(4, c->smaps_x[0], c->vmaps_x[0]) &&
+             encode_for(16, c->smaps_x[1], c->vmaps_x[1]);
     c->tma = ok;
     // BVF_STRESS_TMA=0 keeps the stress kernel on the direct path
     const char *st = std::getenv("BVF_STRESS_TMA");
@@ -389,6 +402,7 @@ AcParams make_params(bvf_ctx *c)
     p.dftS = c->dftS;
     p.flag = c->flag;
     p.kchunk = c->kchunk;
+    p.tile_y = (c->L == 2 && (c->tile_y == 4 || c->tile_y == 16)) ? c->tile_y : 8;
     p.wait_limit = tma::kWaitLimit;
     p.hold = 0;
     p.hold_plane = -1;
@@ -786,12 +800,12 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
             p.hold = 0;
             p.wait_limit = tma::kWaitLimit;
         }
-        auto vel = [&]() {
-            return c->tma ? launch_velocity_tma(p, c->vmaps, s) : launch_velocity(p, s);
-        };
-        auto str = [&]() {
-            return c->tma_stress ? launch_stress_tma(p, c->smaps, s) : launch_stress(p, s);
-        };
+        // the tensor maps whose boxes match the tile height
+        const int tx = p.tile_y == 4 ? 0 : (p.tile_y == 16 ? 1 : -1);
+        const VelocityTmaMaps &vm = tx < 0 ? c->vmaps : c->vmaps_x[tx];
+        const StressTmaMaps &sm = tx < 0 ? c->smaps : c->smaps_x[tx];
+        auto vel = [&]() { return c->tma ? launch_velocity_tma(p, vm, s) : launch_velocity(p, s); };
+        auto str = [&]() { return c->tma_stress ? launch_stress_tma(p, sm, s) : launch_stress(p, s); };
         if (c->timing) {
             if (c->ev_used + 3 > 3072) CK(drain_events(c), "kernel timing");
             cudaEvent_t e0, e1, e2;
@@ -911,7 +925,6 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     double dt_lim = 1e300;
     for (int m = 0; m < n_mat; ++m) {
         const bvf_material &r = c->table[m];
-        tl[m].k = (float)r.k_th;
         tl[m].inv_rhoc = (float)(1.0 / (r.rho * r.c_th));
         tl[m].perfw = (float)(r.perf * th->rhob_cb);
         tl[m].qfac = (float)(r.heat_frac * r.alphaL / (r.rho * r.cL));
@@ -936,6 +949,9 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
             const double ka = c->table[a].k_th, kb = c->table[b].k_th;
             kf[(size_t)a * n_mat + b] = (ka + kb > 0.0) ? (float)(2.0 * ka * kb / (ka + kb)) : 0.0f;
         }
+    // the diagonal rides with each material's coefficients: the kernels take
+    // it for a voxel whose six neighbours share its material
+    for (int m = 0; m < n_mat; ++m) tl[m].k = kf[(size_t)m * n_mat + m];
     CK(cudaMemsetAsync(c->cemf, 0, c->N * sizeof(float), s), "thermal buffers");
     CK(cudaMemcpyAsync(c->tlut, tl.data(), n_mat * sizeof(ThermCoef), cudaMemcpyHostToDevice, s),
        "thermal lut");
@@ -961,6 +977,27 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     p.cem = d_cem43;
     const int total = th->n_on + th->n_off;
     float *a = d_T, *b = c->T2;
+    // TMA-fed steps where the index rows are whole multiples of 16 bytes and
+    // both temperature buffers can be mapped (BVF_NO_TMA forces the direct
+    // kernel); one map per temperature buffer, chosen per step
+    ThermTmaMaps tmaps[2];
+    bool th_tma = false;
+    if (c->g.nx % 16 == 0 && !std::getenv("BVF_NO_TMA")) {
+        const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+        const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+        th_tma = encode_map(&tmaps[0].T, d_T, nx, ny, nz, F32, 4, 40, 18) &&
+                 encode_map(&tmaps[1].T, c->T2, nx, ny, nz, F32, 4, 40, 18) &&
+                 encode_map(&tmaps[0].idx, c->index, nx, ny, nz, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1,
+                            64, 18) &&
+                 encode_map(&tmaps[0].Q, c->Q, nx, ny, nz, F32, 4, 32, 16) &&
+                 encode_map(&tmaps[0].Tmax, d_Tmax, nx, ny, nz, F32, 4, 32, 16) &&
+                 encode_map(&tmaps[0].cemf, c->cemf, nx, ny, nz, F32, 4, 32, 16);
+        tmaps[1].idx = tmaps[0].idx;
+        tmaps[1].Q = tmaps[0].Q;
+        tmaps[1].Tmax = tmaps[0].Tmax;
+        tmaps[1].cemf = tmaps[0].cemf;
+    }
+    p.kz = thermal_kchunk(c->g.nx, c->g.ny, c->g.nz, th_tma, n_mat);
     Budget budget{c};
     for (int n = 0; n < total; ++n) {
         const int rb = budget.check(n, s, "bvf_run_thermal");
@@ -975,7 +1012,8 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
         p.flush = ((n + 1) % 32 == 0 || n + 1 == total) ? 1 : 0;
         p.T = a;
         p.Tn = b;
-        CK(launch_thermal_step(p, s), "thermal kernel");
+        CK(launch_thermal_step(p, th_tma ? &tmaps[a == d_T ? 0 : 1] : nullptr, c->flag, s),
+           "thermal kernel");
         c->launches++;
         std::swap(a, b);
     }
@@ -1491,7 +1529,7 @@ int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *cap
                                             "kernel timing or the test hook armed");
         const bvf_capture cp = caps ? caps[d] : bvf_capture{-1, 0, 0};
         sig.insert(sig.end(), {c->steps, n_steps[d], cp.peak_from, cp.dft_start, cp.dft_steps,
-                               c->kchunk});
+                               c->kchunk, c->tile_y});
     }
     if (!b->gexec || sig != b->gsig) {
         // record the per-domain launches once, domains dealt round-robin over
@@ -1554,13 +1592,15 @@ int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *cap
     return BVF_OK;
 }
 
-int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,
-                           int *h_best, void *stream)
+int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candidates,
+                           int n_candidates, bvf_tile *h_best, void *stream)
 {
     if (!b || !candidates || n_candidates < 1 || trial_steps < 1)
         return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad argument");
     for (int ci = 0; ci < n_candidates; ++ci)
-        if (candidates[ci] < 1) return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad candidate");
+        if (candidates[ci].kchunk < 0 || !(candidates[ci].tile_y == 0 || candidates[ci].tile_y == 4 ||
+                                            candidates[ci].tile_y == 8 || candidates[ci].tile_y == 16))
+            return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad candidate");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK_FREE(cudaEventCreate(&e0), "bvf_batch_tune_domains");
@@ -1569,9 +1609,13 @@ int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const int *candidates,
     for (size_t d = 0; d < b->ctx.size() && rc == BVF_OK; ++d) {
         bvf_ctx *c = b->ctx[d];
         double best = 1e300;
-        int best_kc = c->kchunk;
+        bvf_tile best_t{c->tile_y, c->kchunk};
         for (int ci = 0; ci < n_candidates && rc == BVF_OK; ++ci) {
-            c->kchunk = std::min(candidates[ci], c->g.nz);
+            // heights other than 8 run with L = 2 only: other contexts skip them
+            const int ty = candidates[ci].tile_y;
+            if (ty != 0 && ty != 8 && c->L != 2) continue;
+            c->tile_y = ty;
+            c->kchunk = std::min(candidates[ci].kchunk, c->g.nz);
             if ((rc = bvf_reset(c, stream)) != BVF_OK) break;
             if ((rc = bvf_run_acoustic(c, 2, nullptr, stream)) != BVF_OK) break;   // warm-up
             cudaEventRecord(e0, s);
@@ -1586,16 +1630,37 @@ int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const int *candidates,
             }
             if (ms < best) {
                 best = ms;
-                best_kc = c->kchunk;
+                best_t = bvf_tile{c->tile_y, c->kchunk};
             }
         }
-        c->kchunk = best_kc;
-        if (h_best) h_best[d] = best_kc;
+        c->tile_y = best_t.tile_y;
+        c->kchunk = best_t.kchunk;
+        if (h_best) h_best[d] = best_t;
         if (rc == BVF_OK) rc = bvf_reset(c, stream);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+int bvf_set_tile(bvf_ctx *c, int tile_y, int kchunk)
+{
+    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_set_tile: NULL context");
+    if (!(tile_y == 0 || tile_y == 4 || tile_y == 8 || tile_y == 16) || kchunk < 0)
+        return fail(c, BVF_E_ARG, "bvf_set_tile: tile_y must be 0, 4, 8 or 16 and kchunk >= 0");
+    c->tile_y = tile_y;
+    c->kchunk = kchunk;
+    return BVF_OK;
+}
+
+int bvf_get_tile(const bvf_ctx *c, bvf_tile *out)
+{
+    if (!c || !out) return fail(nullptr, BVF_E_ARG, "bvf_get_tile: NULL argument");
+    out->tile_y = (c->L == 2 && (c->tile_y == 4 || c->tile_y == 16)) ? c->tile_y : 8;
+    out->kchunk = c->kchunk > 0 ? std::min(c->kchunk, c->g.nz)
+                                : (c->tma ? default_kchunk_tma(c->g.nx, c->g.ny, c->g.nz, out->tile_y)
+                                          : default_kchunk(c->g.nx, c->g.ny, c->g.nz));
+    return BVF_OK;
 }
 
 int bvf_batch_tune(bvf_batch *b, int trial_steps, const int *candidates, int n_candidates,

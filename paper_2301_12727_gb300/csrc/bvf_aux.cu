@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 
 #include "bvf_stencil.cuh"
+#include "bvf_tma.cuh"
 
 namespace bvf {
 
@@ -168,9 +169,58 @@ __global__ void k_heat_source(const uint8_t *__restrict__ idx, const ThermCoef *
 // material of the voxel and its four in-plane neighbours, Q, T_max, the dose
 // partial) is loaded one plane ahead, so those loads are in flight while the
 // previous plane is computed; the z-neighbours come from the planes already
-// held.  Face conductivity: harmonic mean 2 k_c k_n / (k_c + k_n).
-constexpr int kThermChunk = 16;
+// held.  Face conductivity: harmonic mean 2 k_c k_n / (k_c + k_n).  The
+// chunk length p.kz comes from thermal_kchunk.
 
+// One interior voxel's forward-Euler step: T + dt (div(k grad T) - w_b c_b
+// (T - T_a) + DC Q) / (rho c), the six face terms summed in the order
+// x-, x+, y-, y+, z-, z+ (k_f from the pair table of the centre material c;
+// where all six neighbours share c's material, its diagonal entry, held in
+// c.k, serves every face without a table read).  Explicit round-to-nearest
+// operations, so the direct and TMA kernels agree bit for bit.
+__device__ __forceinline__ float thermal_update(const ThParams &p, const ThermCoef &c, int mc,
+                                                const float *kf, float Tc, float Tw, int mw,
+                                                float Te, int me, float Ts, int ms, float Tq,
+                                                int mq, float Tm, int mm, float Tp, int mp, float Q)
+{
+    float kw, ke, ks, kq, km, kp;
+    if (mw == mc && me == mc && ms == mc && mq == mc && mm == mc && mp == mc) {
+        kw = ke = ks = kq = km = kp = c.k;
+    } else {
+        kw = __ldg(kf + mw);
+        ke = __ldg(kf + me);
+        ks = __ldg(kf + ms);
+        kq = __ldg(kf + mq);
+        km = __ldg(kf + mm);
+        kp = __ldg(kf + mp);
+    }
+    float lap = __fmul_rn(kw, __fsub_rn(Tw, Tc));
+    lap = __fmaf_rn(ke, __fsub_rn(Te, Tc), lap);
+    lap = __fmaf_rn(ks, __fsub_rn(Ts, Tc), lap);
+    lap = __fmaf_rn(kq, __fsub_rn(Tq, Tc), lap);
+    lap = __fmaf_rn(km, __fsub_rn(Tm, Tc), lap);
+    lap = __fmaf_rn(kp, __fsub_rn(Tp, Tc), lap);
+    const float perf = __fmul_rn(c.perfw, __fsub_rn(Tc, p.T_a));
+    const float rhs = __fmaf_rn(p.dc, Q, __fmaf_rn(lap, p.inv_dx2, -perf));
+    return __fmaf_rn(__fmul_rn(p.dt, rhs), c.inv_rhoc, Tc);
+}
+
+// T_max and the CEM43 partial of a voxel after its step (dose rate R^(43-T)
+// per minute, R = 1/2 at T >= 43 C, 1/4 below: exp2(l2r (43 - T)) with
+// l2r = -1 or -2); every 32nd step the FP32 partial goes into the FP64 sum.
+__device__ __forceinline__ void thermal_outputs(const ThParams &p, size_t q, float Tn, float Tmax,
+                                                float cemf)
+{
+    p.Tmax[q] = fmaxf(Tmax, Tn);
+    const float l2r = (Tn >= 43.0f) ? -1.0f : -2.0f;
+    const float part = __fmaf_rn(p.dt60, exp2f(__fmul_rn(l2r, __fsub_rn(43.0f, Tn))), cemf);
+    if (p.flush) {
+        p.cem[q] += (double)part;
+        p.cemf[q] = 0.0f;
+    } else {
+        p.cemf[q] = part;
+    }
+}
 
 __global__ void __launch_bounds__(256) k_thermal(ThParams p)
 {
@@ -182,7 +232,7 @@ __global__ void __launch_bounds__(256) k_thermal(ThParams p)
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     if (i >= nx || j >= ny) return;
-    const int k0 = blockIdx.z * kThermChunk, k1 = min(nz, k0 + kThermChunk);
+    const int k0 = blockIdx.z * p.kz, k1 = min(nz, k0 + p.kz);
     const int SZ = nx * ny, col = j * nx + i;
     const bool xy_border = i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
     const float *__restrict__ T = p.T;
@@ -218,32 +268,158 @@ __global__ void __launch_bounds__(256) k_thermal(ThParams p)
         if (xy_border || k == 0 || k == nz - 1) {
             Tn = p.T_a;
         } else {
-            const ThermCoef c = s_th[cur.mc];
-            const float Tc = cur.Tc;
             // face conductivities 2 k_a k_b / (k_a + k_b) from the pair table
-            const float *kf = p.kface + cur.mc * p.n_mat;
-            float lap = __ldg(kf + cur.mw) * (cur.Tw - Tc);
-            lap += __ldg(kf + cur.me) * (cur.Te - Tc);
-            lap += __ldg(kf + cur.ms) * (cur.Ts - Tc);
-            lap += __ldg(kf + cur.mq) * (cur.Tq - Tc);
-            lap += __ldg(kf + mm) * (Tm - Tc);
-            lap += __ldg(kf + nxt.mc) * (nxt.Tc - Tc);
-            const float rhs = lap * p.inv_dx2 - c.perfw * (Tc - p.T_a) + p.dc * cur.Q;
-            Tn = Tc + p.dt * rhs * c.inv_rhoc;
+            Tn = thermal_update(p, s_th[cur.mc], cur.mc, p.kface + cur.mc * p.n_mat, cur.Tc, cur.Tw,
+                                cur.mw, cur.Te, cur.me, cur.Ts, cur.ms, cur.Tq, cur.mq, Tm, mm,
+                                nxt.Tc, nxt.mc, cur.Q);
         }
         p.Tn[q] = Tn;
-        p.Tmax[q] = fmaxf(cur.Tmax, Tn);
-        const float l2r = (Tn >= 43.0f) ? -1.0f : -2.0f;
-        const float part = cur.cemf + p.dt60 * exp2f(l2r * (43.0f - Tn));
-        if (p.flush) {
-            p.cem[q] += (double)part;
-            p.cemf[q] = 0.0f;
-        } else {
-            p.cemf[q] = part;
-        }
+        thermal_outputs(p, q, Tn, cur.Tmax, cur.cemf);
         Tm = cur.Tc;
         mm = cur.mc;
         cur = nxt;
+    }
+}
+
+// TMA-fed step (grids with nx % 16 == 0).  A block of 32 x 8 threads owns a
+// 32 x 16 x-y tile (thread (tx, ty) the voxels of rows ty and ty + 8) and
+// walks a z-chunk.  Every input of a plane arrives through the tensor-memory
+// accelerator in a four-plane shared-memory ring: T and the material index
+// as halo'd boxes (T: x0-4 .. x0+35, index: x0-16 .. x0+47, both
+// y0-1 .. y0+16; a TMA box starts on a 16-byte boundary, out-of-range
+// elements read as zero and only feed border voxels, which are held at T_a),
+// Q, T_max and the dose partial as 32 x 16 boxes.  Plane k reads planes k-1,
+// k, k+1 of the ring while plane k+2 is in flight, so the kernel's loads run
+// two planes ahead of its arithmetic; results are stored directly.  One
+// thread issues the copies; waits are bounded as in the acoustic kernels (a
+// time-out sets bit 2 of the flag after the block's armed copies have
+// landed).
+constexpr int kThRing = 4;                                             // planes k-1 .. k+2
+constexpr int kThTileY = 16;
+constexpr int kThTW = 40, kThTH = kThTileY + 2, kThTBytes = kThTW * kThTH * 4;   // 2880 B
+constexpr int kThTSlot = 2944;                                         // 23 x 128 B
+constexpr int kThIW = 64, kThIBytes = kThIW * kThTH;                   // 1152 B
+constexpr int kThVBytes = 32 * kThTileY * 4;                           // Q, T_max, partial: 2048 B
+constexpr int kThSlot = kThTSlot + kThIBytes + 3 * kThVBytes;          // one plane: 10240 B
+constexpr int kThOffBar = kThRing * kThSlot;
+constexpr int kThOffAbort = kThOffBar + 8 * kThRing;
+constexpr int kThOffLut = (kThOffAbort + (int)sizeof(int) + 15) / 16 * 16;
+constexpr unsigned kThPlaneBytes = kThTBytes + kThIBytes + 3 * kThVBytes;
+static_assert(kThTSlot % 128 == 0 && kThTSlot >= kThTBytes && kThIBytes % 128 == 0 &&
+                  kThVBytes % 128 == 0 && kThSlot % 128 == 0 && kThOffLut % 16 == 0,
+              "ring slots 128-byte aligned, coefficients 16");
+
+__global__ void __launch_bounds__(256, 5)
+    k_thermal_tma(ThParams p, const __grid_constant__ ThermTmaMaps tm, int *flag)
+{
+    extern __shared__ __align__(128) unsigned char smb[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smb + kThOffBar);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(smb + kThOffAbort);
+    ThermCoef *s_th = reinterpret_cast<ThermCoef *>(smb + kThOffLut);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    for (int m = tid; m < p.n_mat; m += 256) s_th[m] = p.lut[m];
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kThTileY, i = x0 + tx;
+    const int k0 = blockIdx.z * p.kz, k1 = min(nz, k0 + p.kz);
+    if (tid == 0) {
+        for (int b = 0; b < kThRing; ++b) tma::mbar_init(&bars[b], 1);
+        tma::mbar_init_fence();
+        *s_abort = -1;
+    }
+    __syncthreads();
+    // plane pl of the chunk's window k0-1 .. k1 sits in slot (pl - k0 + 1) % 4,
+    // the (pl - k0 + 1) / 4-th phase of that slot's barrier; a slot holds T,
+    // the index, Q, T_max and the partial of its plane, in that order
+    auto slot = [&](int pl) { return (pl - k0 + 1) & (kThRing - 1); };
+    auto parity = [&](int pl) { return (unsigned)((pl - k0 + 1) >> 2) & 1u; };
+    auto issue = [&](int pl) {
+        uint64_t *bar = &bars[slot(pl)];
+        unsigned char *d = smb + slot(pl) * kThSlot;
+        // the per-voxel streams only for the chunk's own planes; its two
+        // neighbour planes supply T and the index
+        const bool own = pl >= k0 && pl < k1;
+        tma::mbar_expect_tx(bar, own ? kThPlaneBytes : (unsigned)(kThTBytes + kThIBytes));
+        tma::load3d(d, &tm.T, x0 - 4, y0 - 1, pl, bar);
+        tma::load3d(d + kThTSlot, &tm.idx, x0 - 16, y0 - 1, pl, bar);
+        if (own) {
+            tma::load3d(d + kThTSlot + kThIBytes, &tm.Q, x0, y0, pl, bar);
+            tma::load3d(d + kThTSlot + kThIBytes + kThVBytes, &tm.Tmax, x0, y0, pl, bar);
+            tma::load3d(d + kThTSlot + kThIBytes + 2 * kThVBytes, &tm.cemf, x0, y0, pl, bar);
+        }
+    };
+    auto wait = [&](int pl) { return tma::mbar_wait(&bars[slot(pl)], parity(pl), tma::kWaitLimit); };
+    const int first_last = min(k1, k0 + 2);
+    if (tid == 0)
+        for (int pl = k0 - 1; pl <= first_last; ++pl) issue(pl);
+    int issued = first_last;
+
+    // the thread's two voxels: rows j = y0 + ty + 8 h, h = 0, 1
+    bool live[2], border[2];
+    int ct[2], ci[2], cv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int j = y0 + ty + 8 * h;
+        live[h] = i < nx && j < ny;
+        border[h] = i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
+        ct[h] = (ty + 8 * h + 1) * kThTW + tx + 4;
+        ci[h] = (ty + 8 * h + 1) * kThIW + tx + 16;
+        cv[h] = (ty + 8 * h) * 32 + tx;
+    }
+    const size_t SZ = (size_t)nx * ny;
+    size_t q0 = (size_t)k0 * SZ + (size_t)(y0 + ty) * nx + i;     // row ty of plane k
+    const size_t q8 = (size_t)8 * nx;                                // row ty + 8
+    for (int k = k0; k < k1; ++k, q0 += SZ) {
+        __syncthreads();
+        if (*s_abort >= 0) break;                 // a wait of the previous plane ran out
+        if (k + 2 <= k1 && k + 2 > issued) {      // into the slot plane k-2 has freed
+            if (tid == 0) {
+                tma::fence_async_smem();
+                issue(k + 2);
+            }
+            issued = k + 2;
+        }
+        bool ready = true;
+        if (k == k0) ready = wait(k0 - 1) && wait(k0);
+        ready = ready && wait(k + 1);
+        if (!ready) *s_abort = k;
+        if (!ready) continue;                     // leaves at the next barrier
+        const unsigned char *S0 = smb + slot(k) * kThSlot;
+        const unsigned char *Sz0 = smb + slot(k - 1) * kThSlot;
+        const unsigned char *Sz1 = smb + slot(k + 1) * kThSlot;
+        const float *T0 = reinterpret_cast<const float *>(S0);
+        const float *Tz0 = reinterpret_cast<const float *>(Sz0);
+        const float *Tz1 = reinterpret_cast<const float *>(Sz1);
+        const unsigned char *I0 = S0 + kThTSlot, *Iz0 = Sz0 + kThTSlot, *Iz1 = Sz1 + kThTSlot;
+        const float *V0 = reinterpret_cast<const float *>(S0 + kThTSlot + kThIBytes);
+        const bool zb = k == 0 || k == nz - 1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!live[h]) continue;
+            const float Q = V0[cv[h]], Tmax = V0[cv[h] + kThVBytes / 4],
+                        cemf = V0[cv[h] + kThVBytes / 2];
+            float Tn;
+            if (border[h] || zb) {
+                Tn = p.T_a;
+            } else {
+                const int c = ct[h], d = ci[h];
+                const int mc = I0[d];
+                Tn = thermal_update(p, s_th[mc], mc, p.kface + mc * p.n_mat, T0[c], T0[c - 1],
+                                    I0[d - 1], T0[c + 1], I0[d + 1], T0[c - kThTW], I0[d - kThIW],
+                                    T0[c + kThTW], I0[d + kThIW], Tz0[c], Iz0[d], Tz1[c], Iz1[d],
+                                    Q);
+            }
+            const size_t q = q0 + h * q8;
+            p.Tn[q] = Tn;
+            thermal_outputs(p, q, Tn, Tmax, cemf);
+        }
+    }
+    __syncthreads();
+    const int ab = *s_abort;
+    if (ab >= 0 && tid == 0) {
+        // every armed phase from the one that ran out on has landed before
+        // the block's shared memory is released
+        for (int pl = max(k0 - 1, ab - 1); pl <= issued; ++pl) wait(pl);
+        atomicOr(flag, 2);
     }
 }
 
@@ -445,11 +621,47 @@ cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_m
     return cudaGetLastError();
 }
 
-cudaError_t launch_thermal_step(const ThParams &p, cudaStream_t s)
+// The z-chunk of a BHTE launch: blocks of a chunk run in waves of
+// (resident blocks per SM) x (SMs); a block's time is about its planes plus
+// two (the z-neighbour planes and the pipeline fill), so the chunk length kz
+// in 4 .. 32 that minimises waves(kz) x (kz + 2) is taken.
+int thermal_kchunk(int nx, int ny, int nz, bool tma, int n_mat)
+{
+    int dev = 0, n_sm = 152, per_sm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = tma ? kThOffLut + n_mat * sizeof(ThermCoef) : n_mat * sizeof(ThermCoef);
+    const cudaError_t e =
+        tma ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_thermal_tma, 256, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_thermal, 256, smem);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    const long long tiles = (long long)((nx + 31) / 32) * ((ny + (tma ? kThTileY : 8) - 1) /
+                                                           (tma ? kThTileY : 8));
+    const long long slots = (long long)per_sm * n_sm;
+    int best = 16;
+    long long best_cost = -1;
+    for (int kz = 4; kz <= 32; ++kz) {
+        const long long blocks = tiles * ((nz + kz - 1) / kz);
+        const long long cost = ((blocks + slots - 1) / slots) * (kz + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = kz;
+        }
+    }
+    return best < nz ? best : (nz > 0 ? nz : 1);
+}
+
+cudaError_t launch_thermal_step(const ThParams &p, const ThermTmaMaps *tm, int *flag,
+                               cudaStream_t s)
 {
     dim3 blk(32, 8, 1);
-    dim3 grd((p.nx + 31) / 32, (p.ny + 7) / 8, (p.nz + kThermChunk - 1) / kThermChunk);
-    k_thermal<<<grd, blk, p.n_mat * sizeof(ThermCoef), s>>>(p);
+    dim3 grd((p.nx + 31) / 32, (p.ny + 7) / 8, (p.nz + p.kz - 1) / p.kz);
+    if (tm) {
+        grd.y = (p.ny + kThTileY - 1) / kThTileY;
+        k_thermal_tma<<<grd, blk, kThOffLut + p.n_mat * sizeof(ThermCoef), s>>>(p, *tm, flag);
+    } else {
+        k_thermal<<<grd, blk, p.n_mat * sizeof(ThermCoef), s>>>(p);
+    }
     return cudaGetLastError();
 }
 

@@ -30,7 +30,9 @@ struct MatCoef {
 
 // Per-material constants of the BHTE kernel.
 struct ThermCoef {
-    float k;         // conductivity
+    float k;         // face conductivity between two cells of this material: the
+                     // diagonal entry of the BHTE pair table (the harmonic mean of k_th
+                     // with itself, derived in FP64 and rounded once)
     float inv_rhoc;  // 1 / (rho c_th)
     float perfw;     // perf * rhob_cb
     float qfac;      // heat_frac * alphaL / (rho cL)
@@ -101,6 +103,9 @@ struct AcParams {
     // flight: the test hook of the time-out path (0 = off).
     unsigned wait_limit;
     int hold, hold_plane;
+    // rows of an x-y tile of the TMA-fed kernels: 4, 8 or 16 (0: 8); heights
+    // other than 8 are taken with L = 2 only
+    int tile_y;
 };
 
 // Tensor maps of the TMA-fed acoustic kernels (x-y boxes of one z-plane).
@@ -154,6 +159,7 @@ struct ThParams {
     float *cemf;
     double *cem;
     int flush;
+    int kz;                  // z-planes per block (thermal_kchunk)
 };
 
 // message returned by bvf_last_error(NULL) for a failed context-free call
@@ -161,7 +167,7 @@ void set_context_free_error(const char *msg);
 
 // z-planes per block of the z-marching acoustic kernels for a grid
 int default_kchunk(int nx, int ny, int nz);
-int default_kchunk_tma(int nx, int ny, int nz);
+int default_kchunk_tma(int nx, int ny, int nz, int tile_y = 8);
 
 // Persistent batch kernels: one velocity and one stress launch advance every
 // domain of `dom` by one step (the step number is read from *d_step, which a
@@ -197,7 +203,17 @@ cudaError_t launch_conj_plane(const double *C, const double *S, size_t n,
 cudaError_t launch_heat_source(const uint8_t *idx, const ThermCoef *lut, int n_mat,
                                const double *amp, double p_scale, float *Q, size_t n,
                                cudaStream_t s);
-cudaError_t launch_thermal_step(const ThParams &p, cudaStream_t s);
+// Tensor maps of the TMA-fed BHTE step: the input temperature (40 x 18 x 1
+// float box), the material index (64 x 18 x 1 byte box), and the heat
+// source, T_max and the FP32 dose partial (32 x 16 x 1 float boxes).
+struct ThermTmaMaps {
+    CUtensorMap T, idx, Q, Tmax, cemf;
+};
+// z-planes per block of the BHTE kernels for a grid (tma: the TMA-fed kernel)
+int thermal_kchunk(int nx, int ny, int nz, bool tma, int n_mat);
+// one BHTE step; tm == NULL takes the direct kernel
+cudaError_t launch_thermal_step(const ThParams &p, const ThermTmaMaps *tm, int *flag,
+                               cudaStream_t s);
 cudaError_t launch_intensity_argmax(const uint8_t *idx, const double *zw, const double *amp,
                                     size_t n, unsigned long long *d_best, cudaStream_t s);
 cudaError_t launch_intensity_argmin_index(const uint8_t *idx, const double *zw,

@@ -162,15 +162,19 @@ def test_gpu_batch_graph_matches_single_runs_bitwise(mods):
 
 
 def test_gpu_batch_tune_domains_picks_a_candidate_and_keeps_results(mods):
-    """The per-domain z-chunk tuner returns one of the candidates for every
-    domain, leaves the contexts reset, and runs after it equal single runs."""
+    """The per-domain tile tuner returns one of the candidate (rows, z-chunk)
+    pairs for every domain and keeps it in the context, leaves the contexts
+    reset, and runs after it equal single runs with the default tile."""
     bvf, synth = mods
     specs = synth.sweep_specs(n=2, seed=3, n_min=48, n_max=64)
     made = [make(bvf, synth, spec, 40) for spec in specs]
     solvers = [m[1] for m in made]
     b = bvf.Batch(solvers)
-    best = b.tune_domains(trial_steps=4, candidates=(6, 9, 16))
-    assert all(k in (6, 9, 16) or k == s.shape[0] for k, s in zip(best, solvers))
+    cand = ((8, 6), (4, 9), (16, 16), (16, 5))
+    best = b.tune_domains(trial_steps=4, candidates=cand)
+    for (t, k), s in zip(best, solvers):
+        assert (t, k) in cand or (t, min(k, s.shape[0])) in [(a, min(c, s.shape[0])) for a, c in cand]
+        assert s.tile() == (t, k)
     for s in solvers:
         assert s.stats().steps == 0
     b.run_streams(40, caps=[m[2] for m in made], n_streams=2)

@@ -55,17 +55,18 @@ def assert_same(a, b):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
-def test_withheld_copy_times_out_and_context_recovers(mods, kernel):
-    """Kernel 1 (velocity) or 2 (stress) arms the barrier of the copies it
-    would issue at plane 3 of the first z-chunk but issues none: every block of
-    that chunk gives up after its bounded wait, drains the copies it did issue
-    and stops.  bvf_synchronize reports BVF_E_CUDA with the time-out message;
-    after bvf_reset the context's next 30 steps equal a fresh context's."""
+@pytest.mark.parametrize("kernel,storage", [(1, "f32"), (2, "f32"), (2, "f16")])
+def test_withheld_copy_times_out_and_context_recovers(mods, kernel, storage):
+    """Kernel 1 (velocity) or 2 (stress; with FP16 storage the paired stress
+    tile) arms the barrier of the copies it would issue at plane 3 of the
+    first z-chunk but issues none: every block of that chunk gives up after
+    its bounded wait, drains the copies it did issue and stops.
+    bvf_synchronize reports BVF_E_CUDA with the time-out message; after
+    bvf_reset the context's next 30 steps equal a fresh context's."""
     import torch
     bvf, synth = mods
     c = small_case(synth)
-    s = make_solver(bvf, c)
+    s = make_solver(bvf, c, storage)
     bvf.bvf_test_withhold_copy(s.ctx, kernel, 3, 4096)
     s.run(2, peak_from=0)
     with pytest.raises(bvf.BvfError) as ei:
@@ -77,7 +78,7 @@ def test_withheld_copy_times_out_and_context_recovers(mods, kernel):
     s.run(30, peak_from=0)
     s.synchronize()
     got = snapshot(bvf, s, with_dft=False)
-    ref = make_solver(bvf, c)
+    ref = make_solver(bvf, c, storage)
     ref.run(30, peak_from=0)
     ref.synchronize()
     assert_same(got, snapshot(bvf, ref, with_dft=False))

@@ -227,6 +227,39 @@ def test_gpu_thermal_matches_oracle(bvf, orc):
     assert rel_l2(cem.cpu().numpy(), cr) < 1e-3
 
 
+def test_gpu_thermal_tma_matches_oracle_and_direct_kernel(bvf, orc, monkeypatch):
+    """The TMA-fed BHTE step (nx % 16 == 0) on a grid with a ragged y tile
+    and a ragged last z-chunk: T, T_max and CEM43 against the oracle, and bit
+    for bit against the direct kernel on the same inputs (the flush of the
+    FP32 dose partial included: 301 steps)."""
+    import torch
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(48, 37, 30, dx=0.5e-3, n_steps=10, n_pml=4, seed=11)
+    z, y, x = np.meshgrid(np.arange(c.nz), np.arange(c.ny), np.arange(c.nx), indexing="ij")
+    amp = 4e6 * np.exp(-((z - 17) ** 2 / 30.0 + (y - 18) ** 2 / 12.0 + (x - 23) ** 2 / 12.0))
+    dt, n_on, n_off, duty = 0.05, 201, 100, 0.3
+    out = {}
+    for kernel in ("tma", "direct"):
+        if kernel == "direct":
+            monkeypatch.setenv("BVF_NO_TMA", "1")
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml)
+        s.set_materials(c.index, c.materials)
+        T, Tmax, cem = s.thermal(torch.from_numpy(amp).cuda(), dt, n_on, n_off, duty)
+        torch.cuda.synchronize()
+        out[kernel] = (T.cpu().numpy(), Tmax.cpu().numpy(), cem.cpu().numpy())
+        s.close()
+    monkeypatch.delenv("BVF_NO_TMA", raising=False)
+    for a, b in zip(out["tma"], out["direct"]):
+        np.testing.assert_array_equal(a, b)
+    rc, Tr, Tmr, cr = orc.bhte_run(c.index, c.materials, c.dx, amp, 1.0, dt, n_on, n_off, duty)
+    assert rc == 0
+    T, Tmax, cem = out["tma"]
+    assert Tmr.max() > 40.0
+    assert rel_l2(T - 37.0, Tr - 37.0) < TOL
+    assert rel_l2(Tmax - 37.0, Tmr - 37.0) < TOL
+    assert rel_l2(cem, cr) < 1e-3
+
+
 def test_gpu_transmission_matches_oracle(bvf, orc):
     """E_L (Eq. 2) and z_m from the same FP64 maps on both sides."""
     import torch
@@ -418,6 +451,48 @@ def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch, storage):
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_gpu_tile_heights_agree_bitwise(bvf, storage):
+    """The TMA-fed kernels cut the grid into x-y tiles 4, 8 or 16 rows high
+    (bvf_set_tile); the tiling changes no arithmetic, so every field, the peak
+    map and the FP64 DFT agree bit for bit with the default tile, on a grid
+    whose y extent (45) leaves a partial tile at every height, with CPML
+    slabs, a source plane and z-chunks of several lengths."""
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(64, 45, 36, dx=0.5e-3, n_steps=90, aperture=16e-3, roc=16e-3, n_pml=5)
+    outs = []
+    for tile_y, kc in ((8, 0), (4, 0), (16, 0), (4, 5), (16, 7), (8, 3)):
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml,
+                       storage=storage)
+        s.set_tile(tile_y, kc)
+        assert s.tile()[0] == tile_y
+        s.set_materials(c.index, c.materials)
+        s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
+                     c.c0, c.envelope)
+        s.run(c.n_steps, peak_from=10, dft_start=c.n_steps - 45, dft_steps=46)
+        s.synchronize()
+        amp, ph = s.amp_phase()
+        outs.append([s.field(f).cpu().numpy() for f in range(21)] +
+                    [s.peak().cpu().numpy(), amp.cpu().numpy(), ph.cpu().numpy()])
+        s.close()
+    assert np.abs(outs[0][21]).max() > 0
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_gpu_set_tile_rejects_bad_heights(bvf):
+    s = bvf.Solver(32, 16, 16, 1e-3, 1e-7, 5e5, n_sls=2, n_pml=0)
+    for bad in ((3, 0), (32, 0), (8, -1)):
+        with pytest.raises(bvf.BvfError):
+            s.set_tile(*bad)
+    s.close()
+    s1 = bvf.Solver(32, 16, 16, 1e-3, 1e-7, 5e5, n_sls=1, n_pml=0)
+    s1.set_tile(16, 0)
+    assert s1.tile()[0] == 8          # heights other than 8 need two SLS mechanisms
+    s1.close()
 
 
 # --------------------------------------------------------------------------
