@@ -686,12 +686,13 @@ def _sweep_domain(spec_steps):
 def sweep_leg(cases, steps, warmup):
     """Batched planning sweep over `cases` (seeded domains of uneven size,
     frequency, tilt and skull): the same FDTD runs of every domain timed
-    (CUDA events, min over `steps` repetitions after `warmup`) in five modes:
+    (CUDA events, min over `steps` repetitions after `warmup`) in six modes:
     one after another (with the default and with the tuned tiles),
     per-domain launches on 8 streams, the sweep recorded as one CUDA graph of
-    per-domain launches on 8 branches (after the per-domain tile autotuner:
-    rows of the x-y tile and z-planes per block), and the persistent
-    work-list kernels replayed from a graph.  Every mode gives the sequential results bit for
+    per-domain launches on 8 branches (with the default tiles, and with the
+    tile of the graph-mode autotuner), and the persistent work-list kernels
+    replayed from a graph; the sequential runs are timed again with the
+    tiles of the per-domain autotuner.  Every mode gives the sequential results bit for
     bit (checked on the peak maps)."""
     import torch
     from paper_2301_12727_gb300 import bvf
@@ -738,8 +739,11 @@ def sweep_leg(cases, steps, warmup):
     ref = [s.peak() for s in solvers]
     ms_str = best(streams)
     same = all(bool(torch.equal(a, s.peak())) for a, s in zip(ref, solvers))
+    ms_graph_default = best(graph)
+    same = same and all(bool(torch.equal(a, s.peak())) for a, s in zip(ref, solvers))
     tuned = batch.tune_domains(trial_steps=10)
     ms_seq_tuned = best(sequential)
+    gtile, _ = batch.tune_graph(trial_steps=20, n_branches=8)
     ms_graph = best(graph)
     same = same and all(bool(torch.equal(a, s.peak())) for a, s in zip(ref, solvers))
     best_kc, _ = batch.tune(trial_steps=20, candidates=(6, 8, 10, 13, 16, 24))
@@ -748,16 +752,20 @@ def sweep_leg(cases, steps, warmup):
     rate = lambda ms: vox * n / (ms / 1e3) / 1e9
     out = {"domains": len(cases), "voxels_total": vox, "fdtd_steps_each": n,
            "sequential": {"value": rate(ms_seq), "ms": ms_seq},
-           "sequential_tuned_tiles": {"value": rate(ms_seq_tuned), "ms": ms_seq_tuned},
+           "sequential_tuned_tiles": {"value": rate(ms_seq_tuned), "ms": ms_seq_tuned,
+                                      "tiles_chosen": {"stress %d / velocity %d rows, z %d" % t:
+                                                       sum(1 for x in tuned if x == t)
+                                                       for t in sorted(set(tuned))}},
            "streams_8": {"value": rate(ms_str), "ms": ms_str,
                          "speedup_vs_sequential": ms_seq / ms_str},
+           "graph_8_branches": {"value": rate(ms_graph_default), "ms": ms_graph_default,
+                                "speedup_vs_sequential": ms_seq / ms_graph_default, "launches": 1,
+                                "tiles": "defaults (stress 8, velocity 16 rows)"},
            "graph_8_branches_tuned": {"value": rate(ms_graph), "ms": ms_graph,
                                       "speedup_vs_sequential": ms_seq / ms_graph,
                                       "speedup_vs_sequential_tuned": ms_seq_tuned / ms_graph,
                                       "launches": 1,
-                                      "tiles_chosen": {"%dx%d" % (t, k): sum(1 for x in tuned
-                                                                          if x == (t, k))
-                                                       for t, k in sorted(set(tuned))}},
+                                      "tile": "stress %d / velocity %d rows, z %d" % gtile},
            "persistent_graph": {"value": rate(ms_pers), "ms": ms_pers,
                                 "speedup_vs_sequential": ms_seq / ms_pers, "z_chunk": best_kc},
            "unit": UNIT, "results_equal_sequential": bool(same)}

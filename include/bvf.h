@@ -239,19 +239,22 @@ int bvf_reset(bvf_ctx *ctx, void *stream);
  * fewer steps, having waited for them (bvf_get_stats gives the count). */
 int bvf_run_acoustic(bvf_ctx *ctx, int n_steps, const bvf_capture *cap, void *stream);
 
-/* Tile of the TMA-fed acoustic kernels (no counterpart in the paper: how the
+/* Tiles of the TMA-fed acoustic kernels (no counterpart in the paper: how the
  * grid is cut into blocks, which changes no result, bit for bit).  A block
- * owns an x-y tile 32 voxels wide and tile_y rows high (4, 8 or 16; 0 = 8)
- * and marches kchunk z-planes (0 = a default that fills the GPU about six
- * times).  Heights other than 8 apply to contexts with two SLS mechanisms
- * (n_sls = 2, the method's); other contexts use 8.  bvf_set_tile keeps the
- * choice in the context for later bvf_run_acoustic calls; bvf_get_tile
- * reports the height and z-chunk the kernels use.  Errors: BVF_E_ARG. */
+ * owns an x-y tile 32 voxels wide and stress_rows (stress kernel) or
+ * velocity_rows (velocity kernel) rows high, 4, 8 or 16, and marches kchunk
+ * z-planes.  0 selects the default: 8 rows for the stress and 16 for the
+ * velocity kernel, and a z-chunk that fills the GPU about six times.  Heights
+ * other than 8 apply to contexts with two SLS mechanisms (n_sls = 2, the
+ * method's); other contexts use 8.  bvf_set_tile keeps the choice for later
+ * bvf_run_acoustic calls; bvf_get_tile reports the heights and the stress
+ * kernel's z-chunk the kernels use.  Errors: BVF_E_ARG. */
 typedef struct bvf_tile {
-    int tile_y;
+    int stress_rows;
+    int velocity_rows;
     int kchunk;
 } bvf_tile;
-int bvf_set_tile(bvf_ctx *ctx, int tile_y, int kchunk);
+int bvf_set_tile(bvf_ctx *ctx, const bvf_tile *tile);
 int bvf_get_tile(const bvf_ctx *ctx, bvf_tile *out);
 
 /* Wall-clock budget (seconds, 0 = none, the default) of each later
@@ -510,15 +513,27 @@ int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *cap
                         void *stream);
 
 /* Per-domain tile autotuner: for every context, times trial_steps steps (after
- * two warm-up steps) with each candidate tile (bvf_tile: rows of the x-y tile
- * and z-planes per block; candidates with a height other than 0 or 8 are
- * skipped for contexts without two SLS mechanisms), keeps the fastest in the
- * context (as bvf_set_tile; used by bvf_run_acoustic and the run modes above)
- * and writes it to h_best[d] (may be NULL).  Leaves every context reset
- * (bvf_reset).  Errors: BVF_E_ARG (a height other than 0, 4, 8, 16 or a
- * negative z-chunk). */
+ * two warm-up steps) with each candidate tile (bvf_tile: rows of the stress
+ * and velocity kernels' x-y tiles and z-planes per block; candidates with a
+ * height other than 0 or 8 are skipped for contexts without two SLS
+ * mechanisms), keeps the fastest in the context (as bvf_set_tile; used by
+ * bvf_run_acoustic and the run modes above) and writes it to h_best[d] (may
+ * be NULL).  Leaves every context reset (bvf_reset).  Errors: BVF_E_ARG (a
+ * height other than 0, 4, 8, 16 or a negative z-chunk). */
 int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candidates,
                            int n_candidates, bvf_tile *h_best, void *stream);
+
+/* Tile autotuner of the graph mode: the same tile for every context, chosen
+ * by timing, for each candidate, a replay of bvf_batch_run_graph (trial_steps
+ * steps per context, no capture, n_branches branches) after one recording
+ * replay; the domains then share the GPU, so the fastest tile under
+ * concurrency differs from the one each domain prefers alone
+ * (bvf_batch_tune_domains).  Keeps the fastest in every context, writes it to
+ * *h_best and its time per step (ms) to *h_ms (may be NULL), and leaves every
+ * context reset.  Errors: BVF_E_ARG. */
+int bvf_batch_tune_graph(bvf_batch *b, int trial_steps, const bvf_tile *candidates,
+                         int n_candidates, int n_branches, bvf_tile *h_best, double *h_ms,
+                         void *stream);
 
 /* Tile autotuner: times trial_steps steps of every domain for each candidate
  * z-chunk length, returns the fastest and its time per step (ms), and leaves

@@ -32,7 +32,7 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_rs_elements", "bvf_set_time_budget", "bvf_state_bytes", "bvf_state_save",
            "bvf_state_load", "bvf_test_withhold_copy", "bvf_bowl_array", "bvf_steer_weights",
            "bvf_time_reversal_plane", "bvf_batch_run_graph", "bvf_batch_tune_domains",
-           "bvf_set_tile", "bvf_get_tile")
+           "bvf_set_tile", "bvf_get_tile", "bvf_batch_tune_graph")
 
 
 class BvfError(RuntimeError):
@@ -90,11 +90,13 @@ class PlanOut(ctypes.Structure):
 
 
 class Tile(ctypes.Structure):
-    _fields_ = [("tile_y", ctypes.c_int), ("kchunk", ctypes.c_int)]
+    _fields_ = [("stress_rows", ctypes.c_int), ("velocity_rows", ctypes.c_int),
+                ("kchunk", ctypes.c_int)]
 
 
-# candidates of the per-domain tile autotuner: (rows of the x-y tile, z-planes per block)
-TILE_CANDIDATES = tuple((t, k) for t in (8, 4, 16) for k in (6, 8, 10, 13, 16, 24))
+# candidates of the per-domain tile autotuner: (stress rows, velocity rows, z-planes per block)
+TILE_CANDIDATES = tuple((s, v, k) for s, v in ((8, 16), (8, 8), (16, 16))
+                        for k in (6, 8, 10, 13, 16))
 
 
 class Stats(ctypes.Structure):
@@ -164,7 +166,9 @@ def lib():
         L.bvf_batch_run_graph.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
         L.bvf_batch_tune_domains.argtypes = [vp, i, ctypes.POINTER(Tile), i, ctypes.POINTER(Tile),
                                              vp]
-        L.bvf_set_tile.argtypes = [vp, i, i]
+        L.bvf_set_tile.argtypes = [vp, ctypes.POINTER(Tile)]
+        L.bvf_batch_tune_graph.argtypes = [vp, i, ctypes.POINTER(Tile), i, i, ctypes.POINTER(Tile),
+                                           ctypes.POINTER(ctypes.c_double), vp]
         L.bvf_get_tile.argtypes = [vp, ctypes.POINTER(Tile)]
         L.bvf_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
         L.bvf_state_save.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -496,15 +500,17 @@ class Solver:
     def set_time_budget(self, seconds):
         bvf_set_time_budget(self.ctx, seconds)
 
-    def set_tile(self, tile_y=0, kchunk=0):
-        """Rows of the x-y tile (0, 4, 8, 16) and z-planes per block (0 = default)."""
-        _check(lib().bvf_set_tile(self.ctx, int(tile_y), int(kchunk)), self.ctx)
+    def set_tile(self, stress_rows=0, velocity_rows=0, kchunk=0):
+        """Rows of the stress and velocity kernels' x-y tiles (0 = default, 4,
+        8, 16) and z-planes per block (0 = default)."""
+        t = Tile(int(stress_rows), int(velocity_rows), int(kchunk))
+        _check(lib().bvf_set_tile(self.ctx, ctypes.byref(t)), self.ctx)
 
     def tile(self):
-        """(tile_y, kchunk) the kernels use."""
+        """(stress rows, velocity rows, z-chunk) the kernels use."""
         t = Tile()
         _check(lib().bvf_get_tile(self.ctx, ctypes.byref(t)), self.ctx)
-        return t.tile_y, t.kchunk
+        return t.stress_rows, t.velocity_rows, t.kchunk
 
     def save_state(self, stream=None):
         """Snapshot of the acoustic state in a fresh uint8 CUDA tensor."""
@@ -615,14 +621,24 @@ class Batch:
         return bvf_batch_tune(self.handle, trial_steps, candidates, stream)
 
     def tune_domains(self, trial_steps=10, candidates=TILE_CANDIDATES, stream=None):
-        """Per-domain tile autotuner over (tile rows, z-chunk) pairs; returns
-        the chosen (tile_y, kchunk) of each domain."""
+        """Per-domain tile autotuner over (stress rows, velocity rows, z-chunk)
+        candidates; returns the chosen triple of each domain."""
         n = len(self.solvers)
-        cand = (Tile * len(candidates))(*[Tile(int(t), int(k)) for t, k in candidates])
+        cand = (Tile * len(candidates))(*[Tile(int(a), int(b), int(k)) for a, b, k in candidates])
         best = (Tile * n)()
         _check(lib().bvf_batch_tune_domains(self.handle, trial_steps, cand, len(candidates), best,
                                             _stream(stream)))
-        return [(b.tile_y, b.kchunk) for b in best]
+        return [(b.stress_rows, b.velocity_rows, b.kchunk) for b in best]
+
+    def tune_graph(self, trial_steps=20, candidates=TILE_CANDIDATES, n_branches=8, stream=None):
+        """Graph-mode tile autotuner (one tile for all domains, timed under
+        concurrency); returns ((stress rows, velocity rows, z-chunk), ms per step)."""
+        cand = (Tile * len(candidates))(*[Tile(int(a), int(b), int(k)) for a, b, k in candidates])
+        best, ms = Tile(), ctypes.c_double()
+        _check(lib().bvf_batch_tune_graph(self.handle, trial_steps, cand, len(candidates),
+                                          int(n_branches), ctypes.byref(best), ctypes.byref(ms),
+                                          _stream(stream)))
+        return (best.stress_rows, best.velocity_rows, best.kchunk), ms.value
 
     def launches(self):
         out = ctypes.c_longlong()

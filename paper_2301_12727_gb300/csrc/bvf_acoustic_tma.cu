@@ -852,8 +852,9 @@ __device__ __forceinline__ bool stress_tile_h2(const AcParams &p, const StressTm
         vP2 = vP1 + 3 * VT;
     int iK = ibase + ci, iK1 = iK + IT_SLOT;
 
-    const bool edge = !(x0 >= p.P && x0 + TX - 1 < nx - p.P - 1 && y0 >= p.P &&
-                        y0 + TH - 1 < ny - p.P - 1);
+    // one copy of the plane loop for every tile: the paired tile's code is
+    // large, and an interior-tile copy without the CPML code costs more in
+    // instruction fetch than the CPML branches it saves
     auto march = [&](auto edge_tag) {
     constexpr bool EDGE = decltype(edge_tag)::value;
     const bool lv = EDGE ? live : true;
@@ -1110,10 +1111,7 @@ __device__ __forceinline__ bool stress_tile_h2(const AcParams &p, const StressTm
         if (iK1 >= iend) iK1 -= Lay::RI * IT_SLOT;
     }
     };
-    if (edge)
-        march(std::true_type{});
-    else
-        march(std::false_type{});
+    march(std::true_type{});
     __syncthreads();
     const int ab = *s_abort;
     if (ab >= 0 && tid == 0) drain_after_timeout<3>(bars, ab, 2, k0, k1, p.wait_limit, p.flag);
@@ -1292,8 +1290,8 @@ template <typename T>
 static cudaError_t launch_velocity_tma_h(const AcParams &p, const VelocityTmaMaps &tm,
                                          cudaStream_t s)
 {
-    if (p.L == 2 && p.tile_y == 4) return launch_velocity_tma_t<T, 4>(p, tm, s);
-    if (p.L == 2 && p.tile_y == 16) return launch_velocity_tma_t<T, 16>(p, tm, s);
+    if (p.L == 2 && p.tile_yv == 4) return launch_velocity_tma_t<T, 4>(p, tm, s);
+    if (p.L == 2 && p.tile_yv == 16) return launch_velocity_tma_t<T, 16>(p, tm, s);
     return launch_velocity_tma_t<T, TY>(p, tm, s);
 }
 

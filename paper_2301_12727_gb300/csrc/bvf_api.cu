@@ -74,7 +74,7 @@ struct bvf_ctx {
     long long steps = 0, launches = 0, thermal_steps = 0;
     double courant = 0.0;
     int kchunk = 0;                   // z-planes per block (0 = default)
-    int tile_y = 0;                   // rows of an x-y tile (0 = 8; 4 or 16 with L = 2)
+    bvf_tile tile{0, 0, 0};           // tile of the TMA kernels (bvf_set_tile; 0 = default)
     bool tma = false;                 // velocity kernel fed by TMA
     bool tma_stress = false;          // stress kernel fed by TMA
     StressTmaMaps smaps{};            // boxes of 8-row tiles
@@ -353,6 +353,24 @@ void setup_maps(bvf_ctx *c)
     c->tma_stress = ok && !(st && st[0] == '0');
 }
 
+bool tile_valid(const bvf_tile &t)
+{
+    auto rows_ok = [](int r) { return r == 0 || r == 4 || r == 8 || r == 16; };
+    return rows_ok(t.stress_rows) && rows_ok(t.velocity_rows) && t.kchunk >= 0;
+}
+
+// The rows each TMA kernel uses: the context's choice, else 8 for the stress
+// and 16 for the velocity kernel (the faster heights on the bench workload);
+// 8 for both without two SLS mechanisms.
+bvf_tile effective_tile(const bvf_ctx *c)
+{
+    bvf_tile t{8, 8, c->kchunk};
+    if (c->L != 2) return t;
+    t.stress_rows = c->tile.stress_rows ? c->tile.stress_rows : 8;
+    t.velocity_rows = c->tile.velocity_rows ? c->tile.velocity_rows : 16;
+    return t;
+}
+
 AcParams make_params(bvf_ctx *c)
 {
     AcParams p{};
@@ -402,7 +420,9 @@ AcParams make_params(bvf_ctx *c)
     p.dftS = c->dftS;
     p.flag = c->flag;
     p.kchunk = c->kchunk;
-    p.tile_y = (c->L == 2 && (c->tile_y == 4 || c->tile_y == 16)) ? c->tile_y : 8;
+    const bvf_tile t = effective_tile(c);
+    p.tile_y = t.stress_rows;
+    p.tile_yv = t.velocity_rows;
     p.wait_limit = tma::kWaitLimit;
     p.hold = 0;
     p.hold_plane = -1;
@@ -800,10 +820,11 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
             p.hold = 0;
             p.wait_limit = tma::kWaitLimit;
         }
-        // the tensor maps whose boxes match the tile height
-        const int tx = p.tile_y == 4 ? 0 : (p.tile_y == 16 ? 1 : -1);
-        const VelocityTmaMaps &vm = tx < 0 ? c->vmaps : c->vmaps_x[tx];
-        const StressTmaMaps &sm = tx < 0 ? c->smaps : c->smaps_x[tx];
+        // the tensor maps whose boxes match each kernel's tile height
+        const int tv = p.tile_yv == 4 ? 0 : (p.tile_yv == 16 ? 1 : -1);
+        const int ts = p.tile_y == 4 ? 0 : (p.tile_y == 16 ? 1 : -1);
+        const VelocityTmaMaps &vm = tv < 0 ? c->vmaps : c->vmaps_x[tv];
+        const StressTmaMaps &sm = ts < 0 ? c->smaps : c->smaps_x[ts];
         auto vel = [&]() { return c->tma ? launch_velocity_tma(p, vm, s) : launch_velocity(p, s); };
         auto str = [&]() { return c->tma_stress ? launch_stress_tma(p, sm, s) : launch_stress(p, s); };
         if (c->timing) {
@@ -1529,7 +1550,7 @@ int bvf_batch_run_graph(bvf_batch *b, const int *n_steps, const bvf_capture *cap
                                             "kernel timing or the test hook armed");
         const bvf_capture cp = caps ? caps[d] : bvf_capture{-1, 0, 0};
         sig.insert(sig.end(), {c->steps, n_steps[d], cp.peak_from, cp.dft_start, cp.dft_steps,
-                               c->kchunk, c->tile_y});
+                               c->kchunk, c->tile.stress_rows, c->tile.velocity_rows});
     }
     if (!b->gexec || sig != b->gsig) {
         // record the per-domain launches once, domains dealt round-robin over
@@ -1598,8 +1619,7 @@ int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candid
     if (!b || !candidates || n_candidates < 1 || trial_steps < 1)
         return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad argument");
     for (int ci = 0; ci < n_candidates; ++ci)
-        if (candidates[ci].kchunk < 0 || !(candidates[ci].tile_y == 0 || candidates[ci].tile_y == 4 ||
-                                            candidates[ci].tile_y == 8 || candidates[ci].tile_y == 16))
+        if (!tile_valid(candidates[ci]))
             return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_domains: bad candidate");
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1609,13 +1629,16 @@ int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candid
     for (size_t d = 0; d < b->ctx.size() && rc == BVF_OK; ++d) {
         bvf_ctx *c = b->ctx[d];
         double best = 1e300;
-        bvf_tile best_t{c->tile_y, c->kchunk};
+        bvf_tile best_t = c->tile;
         for (int ci = 0; ci < n_candidates && rc == BVF_OK; ++ci) {
+            const bvf_tile cand = candidates[ci];
             // heights other than 8 run with L = 2 only: other contexts skip them
-            const int ty = candidates[ci].tile_y;
-            if (ty != 0 && ty != 8 && c->L != 2) continue;
-            c->tile_y = ty;
-            c->kchunk = std::min(candidates[ci].kchunk, c->g.nz);
+            if (c->L != 2 && ((cand.stress_rows != 0 && cand.stress_rows != 8) ||
+                              (cand.velocity_rows != 0 && cand.velocity_rows != 8)))
+                continue;
+            c->tile = cand;
+            c->tile.kchunk = std::min(cand.kchunk, c->g.nz);
+            c->kchunk = c->tile.kchunk;
             if ((rc = bvf_reset(c, stream)) != BVF_OK) break;
             if ((rc = bvf_run_acoustic(c, 2, nullptr, stream)) != BVF_OK) break;   // warm-up
             cudaEventRecord(e0, s);
@@ -1630,10 +1653,10 @@ int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candid
             }
             if (ms < best) {
                 best = ms;
-                best_t = bvf_tile{c->tile_y, c->kchunk};
+                best_t = c->tile;
             }
         }
-        c->tile_y = best_t.tile_y;
+        c->tile = best_t;
         c->kchunk = best_t.kchunk;
         if (h_best) h_best[d] = best_t;
         if (rc == BVF_OK) rc = bvf_reset(c, stream);
@@ -1643,22 +1666,80 @@ int bvf_batch_tune_domains(bvf_batch *b, int trial_steps, const bvf_tile *candid
     return rc;
 }
 
-int bvf_set_tile(bvf_ctx *c, int tile_y, int kchunk)
+int bvf_batch_tune_graph(bvf_batch *b, int trial_steps, const bvf_tile *candidates,
+                         int n_candidates, int n_branches, bvf_tile *h_best, double *h_ms,
+                         void *stream)
 {
-    if (!c) return fail(nullptr, BVF_E_ARG, "bvf_set_tile: NULL context");
-    if (!(tile_y == 0 || tile_y == 4 || tile_y == 8 || tile_y == 16) || kchunk < 0)
-        return fail(c, BVF_E_ARG, "bvf_set_tile: tile_y must be 0, 4, 8 or 16 and kchunk >= 0");
-    c->tile_y = tile_y;
-    c->kchunk = kchunk;
+    if (!b || !candidates || n_candidates < 1 || trial_steps < 1 || n_branches < 1 || !h_best)
+        return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_graph: bad argument");
+    for (int ci = 0; ci < n_candidates; ++ci)
+        if (!tile_valid(candidates[ci]))
+            return fail(nullptr, BVF_E_ARG, "bvf_batch_tune_graph: bad candidate");
+    const size_t n = b->ctx.size();
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK_FREE(cudaEventCreate(&e0), "bvf_batch_tune_graph");
+    CK_FREE(cudaEventCreate(&e1), "bvf_batch_tune_graph");
+    const std::vector<int> steps(n, trial_steps);
+    double best = 1e300;
+    bvf_tile best_t = candidates[0];
+    int rc = BVF_OK;
+    for (int ci = 0; ci < n_candidates && rc == BVF_OK; ++ci) {
+        for (bvf_ctx *c : b->ctx) {
+            c->tile = candidates[ci];
+            c->kchunk = candidates[ci].kchunk;
+        }
+        // one replay records the graph (and warms up), the second is timed
+        for (int rep = 0; rep < 2 && rc == BVF_OK; ++rep) {
+            for (bvf_ctx *c : b->ctx)
+                if ((rc = bvf_reset(c, stream)) != BVF_OK) break;
+            if (rc != BVF_OK) break;
+            if (rep == 1) cudaEventRecord(e0, s);
+            rc = bvf_batch_run_graph(b, steps.data(), nullptr, n_branches, stream);
+            if (rc == BVF_OK && rep == 1) cudaEventRecord(e1, s);
+        }
+        if (rc != BVF_OK) break;
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(nullptr, e, "bvf_batch_tune_graph");
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            best_t = candidates[ci];
+        }
+    }
+    for (bvf_ctx *c : b->ctx) {
+        c->tile = best_t;
+        c->kchunk = best_t.kchunk;
+        if (rc == BVF_OK) rc = bvf_reset(c, stream);
+    }
+    *h_best = best_t;
+    if (h_ms) *h_ms = best / trial_steps;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int bvf_set_tile(bvf_ctx *c, const bvf_tile *t)
+{
+    if (!c || !t) return fail(c, BVF_E_ARG, "bvf_set_tile: NULL argument");
+    if (!tile_valid(*t))
+        return fail(c, BVF_E_ARG, "bvf_set_tile: rows must be 0, 4, 8 or 16 and kchunk >= 0");
+    c->tile = *t;
+    c->kchunk = t->kchunk;
     return BVF_OK;
 }
 
 int bvf_get_tile(const bvf_ctx *c, bvf_tile *out)
 {
     if (!c || !out) return fail(nullptr, BVF_E_ARG, "bvf_get_tile: NULL argument");
-    out->tile_y = (c->L == 2 && (c->tile_y == 4 || c->tile_y == 16)) ? c->tile_y : 8;
+    *out = effective_tile(c);
     out->kchunk = c->kchunk > 0 ? std::min(c->kchunk, c->g.nz)
-                                : (c->tma ? default_kchunk_tma(c->g.nx, c->g.ny, c->g.nz, out->tile_y)
+                                : (c->tma ? default_kchunk_tma(c->g.nx, c->g.ny, c->g.nz,
+                                                               out->stress_rows)
                                           : default_kchunk(c->g.nx, c->g.ny, c->g.nz));
     return BVF_OK;
 }

@@ -103,9 +103,9 @@ struct AcParams {
     // flight: the test hook of the time-out path (0 = off).
     unsigned wait_limit;
     int hold, hold_plane;
-    // rows of an x-y tile of the TMA-fed kernels: 4, 8 or 16 (0: 8); heights
-    // other than 8 are taken with L = 2 only
-    int tile_y;
+    // rows of an x-y tile of the TMA-fed stress and velocity kernels: 4, 8 or
+    // 16 (heights other than 8 with L = 2 only)
+    int tile_y, tile_yv;
 };
 
 // Tensor maps of the TMA-fed acoustic kernels (x-y boxes of one z-plane).

@@ -170,11 +170,11 @@ def test_gpu_batch_tune_domains_picks_a_candidate_and_keeps_results(mods):
     made = [make(bvf, synth, spec, 40) for spec in specs]
     solvers = [m[1] for m in made]
     b = bvf.Batch(solvers)
-    cand = ((8, 6), (4, 9), (16, 16), (16, 5))
+    cand = ((8, 16, 6), (4, 8, 9), (16, 16, 16), (8, 4, 5))
     best = b.tune_domains(trial_steps=4, candidates=cand)
-    for (t, k), s in zip(best, solvers):
-        assert (t, k) in cand or (t, min(k, s.shape[0])) in [(a, min(c, s.shape[0])) for a, c in cand]
-        assert s.tile() == (t, k)
+    for (sr, vr, k), s in zip(best, solvers):
+        assert (sr, vr, k) in [(a, v, min(c, s.shape[0])) for a, v, c in cand]
+        assert s.tile() == (sr, vr, k)
     for s in solvers:
         assert s.stats().steps == 0
     b.run_streams(40, caps=[m[2] for m in made], n_streams=2)
@@ -182,6 +182,35 @@ def test_gpu_batch_tune_domains_picks_a_candidate_and_keeps_results(mods):
         s.synchronize()
         c, r, cap = make(bvf, synth, spec, 40)
         r.run(40, peak_from=cap[0], dft_start=cap[1], dft_steps=cap[2])
+        r.synchronize()
+        for a, x in zip(outputs(s), outputs(r)):
+            assert np.array_equal(a, x)
+        r.close()
+    b.close()
+    for s in solvers:
+        s.close()
+
+
+def test_gpu_batch_tune_graph_picks_a_candidate_and_keeps_results(mods):
+    """The graph-mode tuner gives every context the same candidate tile, leaves
+    them reset, and the graph run after it equals single runs with the
+    default tiles bit for bit."""
+    bvf, synth = mods
+    specs = synth.sweep_specs(n=3, seed=5, n_min=48, n_max=64)
+    made = [make(bvf, synth, spec, 30) for spec in specs]
+    solvers = [m[1] for m in made]
+    b = bvf.Batch(solvers)
+    cand = ((8, 16, 6), (8, 8, 12), (16, 16, 0))
+    tile, ms = b.tune_graph(trial_steps=4, candidates=cand, n_branches=2)
+    assert tile in cand and ms > 0
+    for s in solvers:
+        assert s.stats().steps == 0
+        assert s.tile()[:2] == tile[:2]
+    b.run_graph(30, caps=[m[2] for m in made], n_branches=2)
+    for s, spec in zip(solvers, specs):
+        s.synchronize()
+        c, r, cap = make(bvf, synth, spec, 30)
+        r.run(30, peak_from=cap[0], dft_start=cap[1], dft_steps=cap[2])
         r.synchronize()
         for a, x in zip(outputs(s), outputs(r)):
             assert np.array_equal(a, x)

@@ -455,19 +455,21 @@ def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch, storage):
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_gpu_tile_heights_agree_bitwise(bvf, storage):
-    """The TMA-fed kernels cut the grid into x-y tiles 4, 8 or 16 rows high
-    (bvf_set_tile); the tiling changes no arithmetic, so every field, the peak
-    map and the FP64 DFT agree bit for bit with the default tile, on a grid
-    whose y extent (45) leaves a partial tile at every height, with CPML
-    slabs, a source plane and z-chunks of several lengths."""
+    """The TMA-fed kernels cut the grid into x-y tiles 4, 8 or 16 rows high,
+    chosen per kernel (bvf_set_tile); the tiling changes no arithmetic, so
+    every field, the peak map and the FP64 DFT agree bit for bit with the
+    default tiles (stress 8, velocity 16 rows), on a grid whose y extent (45)
+    leaves a partial tile at every height, with CPML slabs, a source plane and
+    z-chunks of several lengths."""
     from paper_2301_12727_gb300 import synth
     c = synth.skull_case(64, 45, 36, dx=0.5e-3, n_steps=90, aperture=16e-3, roc=16e-3, n_pml=5)
     outs = []
-    for tile_y, kc in ((8, 0), (4, 0), (16, 0), (4, 5), (16, 7), (8, 3)):
+    for sr, vr, kc in ((0, 0, 0), (8, 8, 0), (4, 4, 0), (16, 16, 0), (4, 16, 5), (16, 4, 7),
+                       (8, 8, 3)):
         s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml,
                        storage=storage)
-        s.set_tile(tile_y, kc)
-        assert s.tile()[0] == tile_y
+        s.set_tile(sr, vr, kc)
+        assert s.tile()[:2] == (sr or 8, vr or 16)
         s.set_materials(c.index, c.materials)
         s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
                      c.c0, c.envelope)
@@ -485,13 +487,13 @@ def test_gpu_tile_heights_agree_bitwise(bvf, storage):
 
 def test_gpu_set_tile_rejects_bad_heights(bvf):
     s = bvf.Solver(32, 16, 16, 1e-3, 1e-7, 5e5, n_sls=2, n_pml=0)
-    for bad in ((3, 0), (32, 0), (8, -1)):
+    for bad in ((3, 8, 0), (8, 32, 0), (8, 8, -1)):
         with pytest.raises(bvf.BvfError):
             s.set_tile(*bad)
     s.close()
     s1 = bvf.Solver(32, 16, 16, 1e-3, 1e-7, 5e5, n_sls=1, n_pml=0)
-    s1.set_tile(16, 0)
-    assert s1.tile()[0] == 8          # heights other than 8 need two SLS mechanisms
+    s1.set_tile(16, 16, 0)
+    assert s1.tile()[:2] == (8, 8)    # heights other than 8 need two SLS mechanisms
     s1.close()
 
 
