@@ -299,13 +299,15 @@ int bvf_state_load(bvf_ctx *ctx, const void *d_buf, size_t bytes, void *stream);
 /* Test hook of the bounded TMA waits (the paper has no counterpart).  Arms the
  * next acoustic step so that `kernel` (1 = velocity, 2 = stress) of the
  * TMA-fed pair arms the mbarrier of the look-ahead copies it would issue at
- * plane `plane` of its z-chunk but issues none of them; the waits for that
+ * plane `plane` of its z-chunk but issues none of them, or (kernel = 3) the
+ * first step of the next bvf_run_thermal so that the TMA-fed BHTE kernel arms
+ * plane `plane`'s barrier but issues none of its copies; the waits for that
  * data then run out after wait_limit polls (0: the library's bound of 2^22).
  * The blocks concerned stop after draining every copy they did issue, so no
  * copy is left in flight, and bvf_synchronize reports BVF_E_CUDA; after
  * bvf_reset the context runs normally.  kernel = 0 disarms.  BVF_E_ARG if the
- * context does not use that TMA-fed kernel (nx % 16 != 0 or more than 2 SLS
- * mechanisms) or the plane is outside the grid. */
+ * context does not use that TMA-fed kernel (nx % 8 != 0, or more than 2 SLS
+ * mechanisms for kernels 1 and 2) or the plane is outside the grid. */
 int bvf_test_withhold_copy(bvf_ctx *ctx, int kernel, int plane, unsigned wait_limit);
 
 /* Copy one state array (BVF_FIELD_* id, nx*ny*nz floats) out of / into the
@@ -473,7 +475,7 @@ int bvf_plan(bvf_ctx *skull, bvf_ctx *water, const uint8_t *d_index, const bvf_m
  * it serves sweeps over placements and frequencies.
  *
  * bvf_batch_create: the contexts stay owned by the caller and must outlive
- * the batch; each needs its materials set, nx % 16 == 0 and at most 2 SLS
+ * the batch; each needs its materials set, nx % 8 == 0 and at most 2 SLS
  * mechanisms, and all share the SLS count and storage type (BVF_E_ARG
  * otherwise).  Sources are taken from the contexts at each run. */
 typedef struct bvf_batch bvf_batch;

@@ -32,9 +32,10 @@
 // The state is stored as T = float or __half (scaled FP16 storage; the
 // arithmetic is FP32 either way).  A TMA box must start on a 16-byte boundary
 // in x, so the x-halo is XO = 16 / sizeof(T) columns: 4 floats or 8 halves.
-// Used when rows are whole multiples of 16 bytes of the index (nx % 16 == 0,
-// so every pair lies inside the grid and every paired access is aligned) and
-// L <= 2.
+// Used when nx % 8 == 0 (state rows are whole multiples of 16 bytes in both
+// storages, every pair lies inside the grid and every paired access is
+// aligned; the index is mapped from a copy with rows padded to 16 bytes when
+// nx % 16 != 0) and L <= 2.
 #include <cuda_fp16.h>
 
 #include <atomic>

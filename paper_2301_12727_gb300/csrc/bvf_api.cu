@@ -63,6 +63,10 @@ struct bvf_ctx {
     float *T2 = nullptr, *Q = nullptr, *cemf = nullptr;
     ThermCoef *tlut = nullptr;
     float *kface = nullptr;      // [n_mat][n_mat] face conductivities of the BHTE
+    // the material index with rows padded to a multiple of 16 bytes, read by
+    // the tensor maps when nx % 16 != 0 (a TMA row stride is whole 16-byte units)
+    uint8_t *index_p = nullptr;
+    size_t index_pitch = 0;
     // host mirror
     std::vector<bvf_material> table;
     std::vector<MatDerived> derived;
@@ -304,8 +308,9 @@ bool encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, CUtensorMapD
 {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
+    const size_t row = (size_t)nx * es;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es};
+    const cuuint64_t strides[2] = {(cuuint64_t)row, (cuuint64_t)row * ny};
     const cuuint32_t box[3] = {bx, by, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, type, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -313,20 +318,24 @@ bool encode_map(CUtensorMap *m, void *base, int nx, int ny, int nz, CUtensorMapD
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Tensor maps of the TMA-fed kernels.  They need rows of the 1-byte index that
-// are whole multiples of 16 bytes (nx % 16 == 0) and at most 2 SLS mechanisms;
-// other grids use the direct kernels.
+// Tensor maps of the TMA-fed kernels.  They need state rows that are whole
+// multiples of 16 bytes in both storages and an even nx for the voxel pairs
+// (nx % 8 == 0; the index is read from its padded copy when nx % 16 != 0) and
+// at most 2 SLS mechanisms; other grids use the direct kernels.
 void setup_maps(bvf_ctx *c)
 {
     c->tma = false;
     c->tma_stress = false;
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
-    if (nx % 16 != 0 || c->L > 2 || std::getenv("BVF_NO_TMA")) return;
+    if (nx % 8 != 0 || c->L > 2 || std::getenv("BVF_NO_TMA")) return;
     const auto ST = c->h16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     const size_t es = c->es;
     const unsigned bw = 32 + 2 * (unsigned)(16 / es);   // halo'd box width: 16 bytes each side
     auto fld = [&](int f) { return field_ptr(c, f); };
+    // the padded index copy is mapped over its whole padded rows: the pad
+    // bytes are zero, the value the out-of-range fill gives past nx
+    const int idx_nx = c->index_p ? (int)c->index_pitch : nx;
     // the boxes of tiles th rows high: velocities th + 4 rows (stress
     // kernel), each stress array the halo its stencil reads (velocity
     // kernel), the index th + 1 rows
@@ -339,7 +348,8 @@ void setup_maps(bvf_ctx *c)
         for (int g6 = 0; g6 < 6; ++g6)
             ok = ok && encode_map(&vm.sg[g6], fld(BVF_FIELD_SXX + g6), nx, ny, nz, ST, es, w6[g6],
                                   h6[g6]);
-        ok = ok && encode_map(&sm.idx, c->index, nx, ny, nz, U8, 1, 48, th + 1);
+        ok = ok && encode_map(&sm.idx, c->index_p ? c->index_p : c->index, idx_nx, ny, nz, U8, 1,
+                              48, th + 1);
         vm.idx = sm.idx;
         return ok;
     };
@@ -566,7 +576,7 @@ void bvf_destroy(bvf_ctx *c)
     if (!c) return;
     void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut, c->buoy,
                     c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->cemf, c->tlut,
-                    c->kface};
+                    c->kface, c->index_p};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -650,6 +660,14 @@ int bvf_create(const bvf_grid *grid, const bvf_physics *phys, bvf_ctx **out)
         (e = cudaMemset(c->flag, 0, sizeof(int))) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess)
         return cleanup(cuda_fail(nullptr, e, "bvf_create: zero fill"));
+    if (g.nx % 8 == 0 && g.nx % 16 != 0) {
+        c->index_pitch = (size_t)(g.nx + 15) / 16 * 16;
+        const size_t bytes = c->index_pitch * g.ny * g.nz;
+        if ((e = cudaMalloc(&c->index_p, bytes)) != cudaSuccess ||
+            (e = cudaMemset(c->index_p, 0, bytes)) != cudaSuccess ||
+            (e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cleanup(cuda_fail(nullptr, e, "bvf_create: padded index"));
+    }
     setup_maps(c);
     *out = c;
     return BVF_OK;
@@ -723,6 +741,10 @@ int bvf_set_materials(bvf_ctx *c, const uint8_t *d_index, const bvf_material *h_
                 pml[((size_t)ax * 2 + h) * c->nmax + s] = make_float2((float)a, (float)b);
             }
     CK(cudaMemcpy(c->index, d_index, c->N, cudaMemcpyDeviceToDevice), "copy index");
+    if (c->index_p)
+        CK(cudaMemcpy2D(c->index_p, c->index_pitch, c->index, c->g.nx, c->g.nx,
+                        (size_t)c->g.ny * c->g.nz, cudaMemcpyDeviceToDevice),
+           "copy padded index");
     CK(cudaMemcpy(c->lut, lut.data(), n_mat * sizeof(MatCoef), cudaMemcpyHostToDevice), "copy lut");
     // buoyancy at a velocity point between cells of materials a and b: 2 / (rho_a + rho_b)
     std::vector<float> buoy((size_t)n_mat * n_mat);
@@ -811,7 +833,7 @@ int bvf_run_acoustic(bvf_ctx *c, int n_steps, const bvf_capture *cap, void *stre
         const int rb = budget.check(it, s, "bvf_run_acoustic");
         if (rb != BVF_OK) return rb;
         p.st = step_param(c, cp, c->steps);
-        if (c->hold) {                       // test hook: this one step only
+        if (c->hold == 1 || c->hold == 2) {  // test hook: this one step only
             p.hold = c->hold;
             p.hold_plane = c->hold_plane;
             p.wait_limit = c->hold_limit ? c->hold_limit : tma::kWaitLimit;
@@ -1003,13 +1025,14 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     // kernel); one map per temperature buffer, chosen per step
     ThermTmaMaps tmaps[2];
     bool th_tma = false;
-    if (c->g.nx % 16 == 0 && !std::getenv("BVF_NO_TMA")) {
+    if (c->g.nx % 8 == 0 && !std::getenv("BVF_NO_TMA")) {
         const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
         const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
         th_tma = encode_map(&tmaps[0].T, d_T, nx, ny, nz, F32, 4, 40, 18) &&
                  encode_map(&tmaps[1].T, c->T2, nx, ny, nz, F32, 4, 40, 18) &&
-                 encode_map(&tmaps[0].idx, c->index, nx, ny, nz, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1,
-                            64, 18) &&
+                 encode_map(&tmaps[0].idx, c->index_p ? c->index_p : c->index,
+                            c->index_p ? (int)c->index_pitch : nx, ny, nz,
+                            CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, 64, 18) &&
                  encode_map(&tmaps[0].Q, c->Q, nx, ny, nz, F32, 4, 32, 16) &&
                  encode_map(&tmaps[0].Tmax, d_Tmax, nx, ny, nz, F32, 4, 32, 16) &&
                  encode_map(&tmaps[0].cemf, c->cemf, nx, ny, nz, F32, 4, 32, 16);
@@ -1031,6 +1054,13 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
         }
         p.dc = (n < th->n_on) ? (float)th->duty : 0.0f;
         p.flush = ((n + 1) % 32 == 0 || n + 1 == total) ? 1 : 0;
+        p.wait_limit = tma::kWaitLimit;
+        p.hold_plane = -1;
+        if (n == 0 && c->hold == 3) {        // test hook: the first step only
+            p.hold_plane = c->hold_plane;
+            p.wait_limit = c->hold_limit ? c->hold_limit : tma::kWaitLimit;
+            c->hold = 0;
+        }
         p.T = a;
         p.Tn = b;
         CK(launch_thermal_step(p, th_tma ? &tmaps[a == d_T ? 0 : 1] : nullptr, c->flag, s),
@@ -1331,7 +1361,7 @@ int bvf_batch_create(bvf_ctx *const *ctxs, int n, bvf_batch **out)
             return fail(nullptr, BVF_E_ARG, "bvf_batch_create: NULL context or materials not set");
         if (!c->tma || !c->tma_stress)
             return fail(nullptr, BVF_E_ARG,
-                        "bvf_batch_create: every grid needs nx % 16 == 0 and at most 2 SLS");
+                        "bvf_batch_create: every grid needs nx % 8 == 0 and at most 2 SLS");
         if (c->L != ctxs[0]->L || c->h16 != ctxs[0]->h16)
             return fail(nullptr, BVF_E_ARG,
                         "bvf_batch_create: contexts differ in SLS count or storage");
@@ -1829,9 +1859,11 @@ int bvf_test_withhold_copy(bvf_ctx *c, int kernel, int plane, unsigned wait_limi
         c->hold = 0;
         return BVF_OK;
     }
-    if ((kernel != 1 && kernel != 2) || plane < 0 || plane >= c->g.nz)
-        return fail(c, BVF_E_ARG, "bvf_test_withhold_copy: kernel must be 1 or 2, plane inside the grid");
-    if (!(kernel == 1 ? c->tma : c->tma_stress))
+    if ((kernel < 1 || kernel > 3) || plane < 0 || plane >= c->g.nz)
+        return fail(c, BVF_E_ARG,
+                    "bvf_test_withhold_copy: kernel must be 1, 2 or 3, plane inside the grid");
+    if (kernel < 3 ? !(kernel == 1 ? c->tma : c->tma_stress)
+                   : (c->g.nx % 8 != 0 || std::getenv("BVF_NO_TMA") != nullptr))
         return fail(c, BVF_E_ARG, "bvf_test_withhold_copy: this context does not use the TMA-fed kernel");
     c->hold = kernel;
     c->hold_plane = plane;

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k_thermal(ThParams p)
     }
 }
 
-// TMA-fed step (grids with nx % 16 == 0).  A block of 32 x 8 threads owns a
+// TMA-fed step (grids with nx % 8 == 0).  A block of 32 x 8 threads owns a
 // 32 x 16 x-y tile (thread (tx, ty) the voxels of rows ty and ty + 8) and
 // walks a z-chunk.  Every input of a plane arrives through the tensor-memory
 // accelerator in a four-plane shared-memory ring: T and the material index
@@ -339,6 +339,7 @@ __global__ void __launch_bounds__(256, 5)
         // neighbour planes supply T and the index
         const bool own = pl >= k0 && pl < k1;
         tma::mbar_expect_tx(bar, own ? kThPlaneBytes : (unsigned)(kThTBytes + kThIBytes));
+        if (p.hold_plane >= 0 && pl == p.hold_plane) return;   // test hook: armed, none issued
         tma::load3d(d, &tm.T, x0 - 4, y0 - 1, pl, bar);
         tma::load3d(d + kThTSlot, &tm.idx, x0 - 16, y0 - 1, pl, bar);
         if (own) {
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(256, 5)
             tma::load3d(d + kThTSlot + kThIBytes + 2 * kThVBytes, &tm.cemf, x0, y0, pl, bar);
         }
     };
-    auto wait = [&](int pl) { return tma::mbar_wait(&bars[slot(pl)], parity(pl), tma::kWaitLimit); };
+    auto wait = [&](int pl) { return tma::mbar_wait(&bars[slot(pl)], parity(pl), p.wait_limit); };
     const int first_last = min(k1, k0 + 2);
     if (tid == 0)
         for (int pl = k0 - 1; pl <= first_last; ++pl) issue(pl);

@@ -160,6 +160,12 @@ struct ThParams {
     double *cem;
     int flush;
     int kz;                  // z-planes per block (thermal_kchunk)
+    // bounded waits of the TMA-fed step: polls per wait; hold_plane >= 0 makes
+    // the kernel arm that plane's barrier but issue none of its copies (the
+    // test hook of the time-out path; negative = off: plane -1, the one below
+    // the grid, is loaded as zeros by the first z-chunk)
+    unsigned wait_limit;
+    int hold_plane;
 };
 
 // message returned by bvf_last_error(NULL) for a failed context-free call

@@ -27,7 +27,7 @@ def mods():
 
 
 def small_case(synth, nx=48, ny=48, nz=40):
-    # nx % 16 == 0: the TMA-fed kernels run; z-chunks of 8 planes
+    # nx % 8 == 0: the TMA-fed kernels run
     return synth.skull_case(nx, ny, nz, dx=0.5e-3, n_steps=90, aperture=20e-3, roc=18e-3,
                             n_pml=4, seed=11, dft_cycles=1)
 
@@ -87,17 +87,48 @@ def test_withheld_copy_times_out_and_context_recovers(mods, kernel, storage):
     torch.cuda.synchronize()
 
 
+def test_withheld_copy_of_the_bhte_step_times_out_and_context_recovers(mods):
+    """Kernel 3: the first step of the next thermal call arms the ring barrier
+    of plane 5 but issues none of its copies; the blocks that wait for it give
+    up, drain and flag the time-out, bvf_synchronize reports BVF_E_CUDA, and
+    after bvf_reset a thermal call equals a fresh context's bit for bit."""
+    import torch
+    bvf, synth = mods
+    c = small_case(synth)
+    z, y, x = np.meshgrid(np.arange(c.nz), np.arange(c.ny), np.arange(c.nx), indexing="ij")
+    amp = torch.from_numpy(3e6 * np.exp(-((z - 20) ** 2 + (y - 24) ** 2 + (x - 24) ** 2) / 40.0)).cuda()
+    s = make_solver(bvf, c)
+    bvf.bvf_test_withhold_copy(s.ctx, 3, 5, 4096)
+    s.thermal(amp, 0.05, 10, 5, 0.3)
+    with pytest.raises(bvf.BvfError) as ei:
+        s.synchronize()
+    assert ei.value.code == bvf.BVF_E_CUDA
+    assert "wait limit" in str(ei.value)
+    s.reset()
+    got = [t.cpu().numpy() for t in s.thermal(amp, 0.05, 10, 5, 0.3)]
+    s.synchronize()
+    ref = make_solver(bvf, c)
+    want = [t.cpu().numpy() for t in ref.thermal(amp, 0.05, 10, 5, 0.3)]
+    ref.synchronize()
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+    s.close()
+    ref.close()
+    torch.cuda.synchronize()
+
+
 def test_withhold_hook_rejects_direct_kernels_and_bad_planes(mods):
     bvf, synth = mods
-    c = synth.skull_case(40, 40, 24, dx=0.5e-3, n_steps=10, aperture=16e-3, roc=15e-3, n_pml=3)
-    s = make_solver(bvf, c)           # nx % 16 != 0: direct kernels
-    with pytest.raises(bvf.BvfError) as ei:
-        bvf.bvf_test_withhold_copy(s.ctx, 1, 3, 64)
-    assert ei.value.code == bvf.BVF_E_ARG
+    c = synth.skull_case(42, 40, 24, dx=0.5e-3, n_steps=10, aperture=16e-3, roc=15e-3, n_pml=3)
+    s = make_solver(bvf, c)           # nx % 8 != 0: direct kernels
+    for kernel in (1, 3):
+        with pytest.raises(bvf.BvfError) as ei:
+            bvf.bvf_test_withhold_copy(s.ctx, kernel, 3, 64)
+        assert ei.value.code == bvf.BVF_E_ARG
     s.close()
     c = small_case(synth)
     s = make_solver(bvf, c)
-    for kernel, plane in ((3, 2), (1, -1), (2, c.nz)):
+    for kernel, plane in ((4, 2), (1, -1), (2, c.nz), (3, c.nz)):
         with pytest.raises(bvf.BvfError):
             bvf.bvf_test_withhold_copy(s.ctx, kernel, plane, 64)
     bvf.bvf_test_withhold_copy(s.ctx, 0, 0, 0)      # disarm is always accepted

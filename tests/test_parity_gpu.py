@@ -228,7 +228,7 @@ def test_gpu_thermal_matches_oracle(bvf, orc):
 
 
 def test_gpu_thermal_tma_matches_oracle_and_direct_kernel(bvf, orc, monkeypatch):
-    """The TMA-fed BHTE step (nx % 16 == 0) on a grid with a ragged y tile
+    """The TMA-fed BHTE step (nx % 8 == 0) on a grid with a ragged y tile
     and a ragged last z-chunk: T, T_max and CEM43 against the oracle, and bit
     for bit against the direct kernel on the same inputs (the flush of the
     FP32 dose partial included: 301 steps)."""
@@ -420,7 +420,7 @@ def test_gpu_zchunk_invariance(bvf, monkeypatch, nx):
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_gpu_tma_and_direct_paths_agree_bitwise(bvf, monkeypatch, storage):
-    """Grids with nx % 16 == 0 run the TMA-fed kernels (tiles, rings and
+    """Grids with nx % 8 == 0 run the TMA-fed kernels (tiles, rings and
     in-place stages moved by the tensor-memory accelerator); other shapes, or
     BVF_NO_TMA, run the direct kernels.  Same arithmetic, so every field, the
     peak map and the FP64 DFT agree bit for bit, across z-chunk lengths (chunk
@@ -483,6 +483,44 @@ def test_gpu_tile_heights_agree_bitwise(bvf, storage):
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_gpu_tma_path_on_rows_of_eight_agrees_with_direct_kernels(bvf, monkeypatch, storage):
+    """nx = 72 (a multiple of 8, not of 16): the TMA-fed kernels run, their
+    index maps reading a copy with rows padded to 16 bytes; every field, the
+    peak map and the FP64 DFT equal the direct kernels' bit for bit, and so do
+    the BHTE outputs."""
+    import torch
+    from paper_2301_12727_gb300 import synth
+    c = synth.skull_case(72, 41, 30, dx=0.5e-3, n_steps=80, aperture=16e-3, roc=16e-3, n_pml=5)
+    z, y, x = np.meshgrid(np.arange(c.nz), np.arange(c.ny), np.arange(c.nx), indexing="ij")
+    amp = torch.from_numpy(3e6 * np.exp(-((z - 15) ** 2 + (y - 20) ** 2 + (x - 36) ** 2) / 40.0)).cuda()
+    outs = []
+    for no_tma in (False, True):
+        if no_tma:
+            monkeypatch.setenv("BVF_NO_TMA", "1")
+        s = bvf.Solver(c.nx, c.ny, c.nz, c.dx, c.dt, c.f0, n_sls=2, n_pml=c.n_pml,
+                       storage=storage)
+        s.set_materials(c.index, c.materials)
+        if not no_tma:      # the hook is accepted only by a context on the TMA kernels
+            bvf.bvf_test_withhold_copy(s.ctx, 1, 3, 64)
+            bvf.bvf_test_withhold_copy(s.ctx, 0, 0, 0)
+        s.set_source(bvf.rs_plane(c.bowl, c.nx, c.ny, c.dx, c.k_src * c.dx, c.f0), c.k_src,
+                     c.c0, c.envelope)
+        s.run(c.n_steps, peak_from=10, dft_start=c.n_steps - 45, dft_steps=46)
+        s.synchronize()
+        amp_, ph = s.amp_phase()
+        T = s.thermal(amp, 0.05, 40, 20, 0.3)
+        s.synchronize()
+        outs.append([s.field(f).cpu().numpy() for f in range(21)] +
+                    [s.peak().cpu().numpy(), amp_.cpu().numpy(), ph.cpu().numpy()] +
+                    [t.cpu().numpy() for t in T])
+        s.close()
+    monkeypatch.delenv("BVF_NO_TMA", raising=False)
+    assert np.abs(outs[0][21]).max() > 0
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
 
 
 def test_gpu_set_tile_rejects_bad_heights(bvf):
