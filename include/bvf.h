@@ -265,8 +265,10 @@ int bvf_get_tile(const bvf_ctx *ctx, bvf_tile *out);
  * two such chunks queued ahead of the host; once the budget is spent it waits
  * for the queued steps and returns BVF_E_TIMEOUT.  The context then holds the
  * state after every step that ran (consistent and resumable: a later call
- * continues from it).  Work already on the GPU is never cancelled, so a call
- * can overrun its budget by up to two chunks of steps. */
+ * continues from it; an acoustic run continues bit for bit, a thermal run to
+ * within one FP32 rounding of T at the stop, since the call hands T back in
+ * C, see bvf_run_thermal).  Work already on the GPU is never cancelled, so a
+ * call can overrun its budget by up to two chunks of steps. */
 int bvf_set_time_budget(bvf_ctx *ctx, double seconds);
 
 /* Wait for `stream` and report: BVF_E_UNSTABLE if a non-finite pressure was
@@ -334,8 +336,10 @@ int bvf_get_amp_phase(bvf_ctx *ctx, double *d_amp, double *d_phase, void *stream
  * receives the final one; d_Tmax (in/out, float) and d_cem43 (in/out, FP64)
  * accumulate max T and sum dt/60 R^(43-T) (R = 0.5 at T >= 43, else 0.25) after
  * every step (the dose increments of up to 32 consecutive steps are summed in
- * FP32 before each addition to the FP64 dose).  Errors: BVF_E_ARG (including
- * dt above the explicit limit). */
+ * FP32 before each addition to the FP64 dose).  The kernels advance the rise
+ * T - T_a in FP32 (finer than T near 37 C by about 2^10); d_T and d_Tmax are
+ * converted on entry and back on exit, one FP32 rounding each.  Errors:
+ * BVF_E_ARG (including dt above the explicit limit). */
 int bvf_run_thermal(bvf_ctx *ctx, const bvf_thermal *th, const double *d_amp, float *d_T,
                     float *d_Tmax, double *d_cem43, void *stream);
 

@@ -1008,7 +1008,7 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     p.nz = c->g.nz;
     p.dt = (float)th->dt;
     p.inv_dx2 = (float)(1.0 / (c->g.dx * c->g.dx));
-    p.T_a = (float)th->T_a;
+    p.rise43 = (float)(43.0 - th->T_a);
     p.dt60 = (float)(th->dt / 60.0);
     p.idx = c->index;
     p.lut = c->tlut;
@@ -1042,15 +1042,28 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
         tmaps[1].cemf = tmaps[0].cemf;
     }
     p.kz = thermal_kchunk(c->g.nx, c->g.ny, c->g.nz, th_tma, n_mat);
+    // the kernels advance the rise T - T_a (see ThParams); T and T_max are
+    // converted in the caller's buffers on entry and back on every exit
+    const float Ta = (float)th->T_a;
+    CK(launch_add_const(d_T, -Ta, c->N, s), "rise in");
+    CK(launch_add_const(d_Tmax, -Ta, c->N, s), "rise in");
+    c->launches += 2;
+    auto to_celsius = [&](const float *cur) -> int {
+        if (cur != d_T)
+            CK(cudaMemcpyAsync(d_T, cur, c->N * sizeof(float), cudaMemcpyDeviceToDevice, s), "T out");
+        CK(launch_add_const(d_T, Ta, c->N, s), "rise out");
+        CK(launch_add_const(d_Tmax, Ta, c->N, s), "rise out");
+        c->launches += 2;
+        return BVF_OK;
+    };
     Budget budget{c};
     for (int n = 0; n < total; ++n) {
         const int rb = budget.check(n, s, "bvf_run_thermal");
         if (rb != BVF_OK) {
             // the last completed step's temperature goes to d_T
-            if (a != d_T)
-                CK(cudaMemcpy(d_T, a, c->N * sizeof(float), cudaMemcpyDeviceToDevice), "T out");
+            const int rc = to_celsius(a);
             c->thermal_steps += n;
-            return rb;
+            return rc != BVF_OK ? rc : rb;
         }
         p.dc = (n < th->n_on) ? (float)th->duty : 0.0f;
         p.flush = ((n + 1) % 32 == 0 || n + 1 == total) ? 1 : 0;
@@ -1068,7 +1081,8 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
         c->launches++;
         std::swap(a, b);
     }
-    if (a != d_T) CK(cudaMemcpyAsync(d_T, a, c->N * sizeof(float), cudaMemcpyDeviceToDevice, s), "T out");
+    const int rc = to_celsius(a);
+    if (rc != BVF_OK) return rc;
     c->thermal_steps += total;
     return BVF_OK;
 }

@@ -164,7 +164,8 @@ __global__ void k_heat_source(const uint8_t *__restrict__ idx, const ThermCoef *
     }
 }
 
-// Pennes forward-Euler step; border voxels held at T_a; T_max and CEM43 fused.
+// Pennes forward-Euler step on the rise; border voxels held at T_a (rise 0);
+// T_max and CEM43 fused.
 // A 32 x 8 block walks a chunk of z.  Every value plane k needs (T and the
 // material of the voxel and its four in-plane neighbours, Q, T_max, the dose
 // partial) is loaded one plane ahead, so those loads are in flight while the
@@ -172,8 +173,10 @@ __global__ void k_heat_source(const uint8_t *__restrict__ idx, const ThermCoef *
 // held.  Face conductivity: harmonic mean 2 k_c k_n / (k_c + k_n).  The
 // chunk length p.kz comes from thermal_kchunk.
 
-// One interior voxel's forward-Euler step: T + dt (div(k grad T) - w_b c_b
-// (T - T_a) + DC Q) / (rho c), the six face terms summed in the order
+// One interior voxel's forward-Euler step on the rise theta = T - T_a:
+// theta + dt (div(k grad theta) - w_b c_b theta + DC Q) / (rho c) (T_a is
+// constant, so the diffusion of theta is that of T), the six face terms
+// summed in the order
 // x-, x+, y-, y+, z-, z+ (k_f from the pair table of the centre material c;
 // where all six neighbours share c's material, its diagonal entry, held in
 // c.k, serves every face without a table read).  Explicit round-to-nearest
@@ -200,20 +203,21 @@ __device__ __forceinline__ float thermal_update(const ThParams &p, const ThermCo
     lap = __fmaf_rn(kq, __fsub_rn(Tq, Tc), lap);
     lap = __fmaf_rn(km, __fsub_rn(Tm, Tc), lap);
     lap = __fmaf_rn(kp, __fsub_rn(Tp, Tc), lap);
-    const float perf = __fmul_rn(c.perfw, __fsub_rn(Tc, p.T_a));
+    const float perf = __fmul_rn(c.perfw, Tc);
     const float rhs = __fmaf_rn(p.dc, Q, __fmaf_rn(lap, p.inv_dx2, -perf));
     return __fmaf_rn(__fmul_rn(p.dt, rhs), c.inv_rhoc, Tc);
 }
 
-// T_max and the CEM43 partial of a voxel after its step (dose rate R^(43-T)
-// per minute, R = 1/2 at T >= 43 C, 1/4 below: exp2(l2r (43 - T)) with
-// l2r = -1 or -2); every 32nd step the FP32 partial goes into the FP64 sum.
+// The maximum rise and the CEM43 partial of a voxel after its step (dose
+// rate R^(43-T) per minute, R = 1/2 at T >= 43 C, 1/4 below: exp2(l2r
+// (rise43 - theta)) with l2r = -1 or -2); every 32nd step the FP32 partial
+// goes into the FP64 sum.
 __device__ __forceinline__ void thermal_outputs(const ThParams &p, size_t q, float Tn, float Tmax,
                                                 float cemf)
 {
     p.Tmax[q] = fmaxf(Tmax, Tn);
-    const float l2r = (Tn >= 43.0f) ? -1.0f : -2.0f;
-    const float part = __fmaf_rn(p.dt60, exp2f(__fmul_rn(l2r, __fsub_rn(43.0f, Tn))), cemf);
+    const float l2r = (Tn >= p.rise43) ? -1.0f : -2.0f;
+    const float part = __fmaf_rn(p.dt60, exp2f(__fmul_rn(l2r, __fsub_rn(p.rise43, Tn))), cemf);
     if (p.flush) {
         p.cem[q] += (double)part;
         p.cemf[q] = 0.0f;
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(256) k_thermal(ThParams p)
         else { nxt.Tc = 0.0f; nxt.mc = 0; }
         float Tn;
         if (xy_border || k == 0 || k == nz - 1) {
-            Tn = p.T_a;
+            Tn = 0.0f;
         } else {
             // face conductivities 2 k_a k_b / (k_a + k_b) from the pair table
             Tn = thermal_update(p, s_th[cur.mc], cur.mc, p.kface + cur.mc * p.n_mat, cur.Tc, cur.Tw,
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(256, 5)
                         cemf = V0[cv[h] + kThVBytes / 2];
             float Tn;
             if (border[h] || zb) {
-                Tn = p.T_a;
+                Tn = 0.0f;
             } else {
                 const int c = ct[h], d = ci[h];
                 const int mc = I0[d];
@@ -572,6 +576,19 @@ cudaError_t launch_field_in(const float *in, int h16, size_t stride, float inv_s
     else
         k_field_in<float><<<blocks_for(n), kThreads, 0, s>>>(in, stride, inv_scale,
                                                             static_cast<float *>(f), n);
+    return cudaGetLastError();
+}
+
+__global__ void k_add_const(float *__restrict__ x, float c, size_t n)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        x[q] = __fadd_rn(x[q], c);
+}
+
+cudaError_t launch_add_const(float *x, float c, size_t n, cudaStream_t s)
+{
+    k_add_const<<<blocks_for(n), kThreads, 0, s>>>(x, c, n);
     return cudaGetLastError();
 }
 

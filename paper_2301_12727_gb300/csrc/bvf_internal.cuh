@@ -145,9 +145,14 @@ static_assert(sizeof(BatchParams) <= 32000, "batch parameters must fit a kernel 
 // One BHTE step.  The CEM43 increments of consecutive steps are summed in an
 // FP32 partial (cemf) and added to the FP64 dose on `flush` steps (every 32
 // steps and the last), which keeps FP64 arithmetic out of most steps.
+// The BHTE kernels advance the rise theta = T - T_a (the arterial
+// temperature), not T: near 37 C an FP32 T carries 3.8e-6 C ulps, against
+// which the per-step increments round; the rise is small and keeps ~2^10
+// times finer resolution.  bvf_run_thermal converts on entry and exit.
 struct ThParams {
     int nx, ny, nz;
-    float dt, inv_dx2, T_a, dc, dt60;
+    float dt, inv_dx2, dc, dt60;
+    float rise43;            // 43 C - T_a: the CEM43 threshold as a rise
     const uint8_t *idx;
     const ThermCoef *lut;
     const float *kface;      // [n_mat][n_mat] harmonic-mean face conductivity (FP64-derived)
@@ -197,6 +202,8 @@ cudaError_t launch_field_in(const float *in, int h16, size_t stride, float inv_s
                             size_t n, cudaStream_t s);
 cudaError_t launch_scale_copy(const float *in, float scale, float *out, size_t n, cudaStream_t s);
 cudaError_t launch_fill(float *out, float value, size_t n, cudaStream_t s);
+// x[i] += c (round to nearest)
+cudaError_t launch_add_const(float *x, float c, size_t n, cudaStream_t s);
 cudaError_t launch_amp_phase(const double *C, const double *S, size_t n, int count, double scale,
                              double *amp, double *ph, cudaStream_t s);
 cudaError_t launch_rs(const float4 *el, int ne, int nx, int ny, float dx, float zp, float k_over_pi,

@@ -11,12 +11,16 @@ grids) and stored as planes through the focus; the run is compared with them
 element by element.
 
 Tolerances.  FP32 storage: the accuracy target's 1e-4 relative L2 on pressure,
-peak and amplitude; 1e-3 rad of phase in the beam; 1e-4 on E_L; 2e-3 C on
-T_max; 2e-3 relative on CEM43.  FP16 storage (11 significant bits, relative
-rounding 4.9e-4 per stored value): the 1 % peak-pressure bound of the
-mixed-precision target for the peak and amplitude maps, the focal peak and
-E_L; 1e-2 rad of phase; 1e-2 C on T_max; 2e-2 on CEM43.  The measured
-errors are printed."""
+peak and amplitude; 1e-3 rad of phase in the beam; 1e-4 on E_L.  FP16 storage
+(11 significant bits, relative rounding 4.9e-4 per stored value): the 1 %
+peak-pressure bound of the mixed-precision target for the peak and amplitude
+maps, the focal peak and E_L; 1e-2 rad of phase.  Thermal outputs, in either
+storage: the temperature is an FP32 sum of n small increments on T near
+37 C, where an FP32 value carries a rounding of at most half an ulp,
+32 * 2^-24 C = 2^-19 C = 1.9e-6 C, per step; so T_max may differ by up to
+n * 1.9e-6 C (at least 2e-3 C), and CEM43, whose rate R^(43 - T) moves by
+ln 4 = 1.39 per C, by 1.39 times that, relative (at least 2e-3).  The
+measured errors are printed."""
 import json
 
 import numpy as np
@@ -26,10 +30,17 @@ pytestmark = pytest.mark.gpu
 
 TOL = {
     "f32": dict(p_rel_l2=1e-4, peak_rel_l2=1e-4, amp_rel_l2=1e-4, phase=1e-3, EL=1e-4,
-                focal=1e-4, Tmax=2e-3, cem=2e-3),
+                focal=1e-4),
     "f16": dict(p_rel_l2=1e-2, peak_rel_l2=1e-2, amp_rel_l2=1e-2, phase=1e-2, EL=1e-2,
-                focal=1e-2, Tmax=1e-2, cem=2e-2),
+                focal=1e-2),
 }
+
+
+def thermal_tol(n_thermal_steps):
+    """(T_max in C, CEM43 relative) bounds of an FP32 temperature summed over
+    n steps near 37 C (see the module header)."""
+    t = max(2e-3, n_thermal_steps * 2.0 ** -19)
+    return t, max(2e-3, np.log(4.0) * t)
 
 _cases = {}
 
@@ -80,5 +91,7 @@ def test_config3_plan_against_the_fp64_oracle(f0, storage):
     assert e["phase_max_abs_rad_in_beam"] < t["phase"]
     assert e["EL_rel"] < t["EL"]
     assert e["z_m"][0] == e["z_m"][1]
-    assert e["Tmax_max_abs_C"] < t["Tmax"]
-    assert e["cem_rel_l2"] < t["cem"] and e["cem43_max_rel"] < t["cem"]
+    reg = meta["regime"]
+    t_T, t_cem = thermal_tol(reg["n_on"] + reg["n_off"])
+    assert e["Tmax_max_abs_C"] < t_T
+    assert e["cem_rel_l2"] < t_cem and e["cem43_max_rel"] < t_cem
