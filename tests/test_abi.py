@@ -78,6 +78,12 @@ def test_null_pointers_rejected(bvf):
     assert L.bvf_test_withhold_copy(None, 1, 0, 0) == bvf.BVF_E_ARG
     assert L.bvf_time_reversal_plane(None, 0, 0, 0, 0, 10, 1500.0, None, None) == bvf.BVF_E_ARG
     assert L.bvf_steer_weights(None, 1, None, 5e5, 1500.0) == bvf.BVF_E_ARG
+    t = bvf.Tile(8, 16, 0)
+    assert L.bvf_set_tile(None, ctypes.byref(t)) == bvf.BVF_E_ARG
+    assert L.bvf_get_tile(None, ctypes.byref(t)) == bvf.BVF_E_ARG
+    assert L.bvf_batch_tune_domains(None, 1, ctypes.byref(t), 1, None, None) == bvf.BVF_E_ARG
+    assert L.bvf_batch_tune_graph(None, 1, ctypes.byref(t), 1, 8, ctypes.byref(t), None,
+                                  None) == bvf.BVF_E_ARG
     L.bvf_destroy(None)
 
 
