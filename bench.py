@@ -544,22 +544,21 @@ def run_bvf(args):
     vox_per_plan = res.voxel_steps
     value = whole_job_rate(world, args.steps, vox_per_plan, ms)
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the C-ABI call with host buffers (bvf_plan_host:
+    # the index copied in from pinned host memory and the peak, T_max and
+    # CEM43 maps copied out inside the call, every plan)
     e2e = None
     if not args.no_e2e:
         idx_host = torch.from_numpy(case.index).pin_memory()
         out_peak = torch.empty(case.index.shape, dtype=torch.float32).pin_memory()
         out_tmax = torch.empty(case.index.shape, dtype=torch.float32).pin_memory()
         out_cem = torch.empty(case.index.shape, dtype=torch.float64).pin_memory()
+        planner.run_host(idx_host, mats, bowl, out_peak, out_tmax, out_cem)      # staging
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(args.steps):
-            idx_d = idx_host.to("cuda", non_blocking=True)
-            r = planner.run(idx_d, mats, bowl)
-            out_peak.copy_(r.peak, non_blocking=True)
-            out_tmax.copy_(r.Tmax, non_blocking=True)
-            out_cem.copy_(r.cem43, non_blocking=True)
+            planner.run_host(idx_host, mats, bowl, out_peak, out_tmax, out_cem)
         f1.record(stream)
         barrier()
         ms_e2e = max_over_ranks(f0.elapsed_time(f1), pg, "cuda")

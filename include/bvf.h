@@ -468,6 +468,19 @@ int bvf_plan(bvf_ctx *skull, bvf_ctx *water, const uint8_t *d_index, const bvf_m
              const bvf_plan_params *pp, float *d_peak, double *d_amp, float *d_T, float *d_Tmax,
              double *d_cem43, bvf_plan_result *out, void *stream);
 
+/* bvf_plan with host buffers (no counterpart in the paper: the call a planning
+ * service makes per placement).  h_index (nx*ny*nz bytes) is copied to the
+ * skull context's device staging on `stream`, the plan runs as bvf_plan, and
+ * the peak map, the final temperature (h_T, may be NULL), T_max and CEM43 are
+ * copied back into the caller's host buffers before the call returns.  Host
+ * buffers should be page-locked (cudaHostAlloc / cudaHostRegister) for the
+ * copies to run at full speed.  The staging (29 bytes per voxel) is allocated
+ * on the first call and owned by the skull context.  Errors as bvf_plan. */
+int bvf_plan_host(bvf_ctx *skull, bvf_ctx *water, const uint8_t *h_index,
+                  const bvf_material *h_table, int n_mat, const bvf_material *h_water,
+                  const bvf_bowl *bowl, int k_src, const bvf_plan_params *pp, float *h_peak,
+                  float *h_T, float *h_Tmax, double *h_cem43, bvf_plan_result *out, void *stream);
+
 /* ---- batched planning sweeps -------------------------------------------
  * Several contexts (different grids, materials, sources, frequencies; the
  * paper repeats its acoustic step for each transducer placement, Sec. 2.3)

@@ -32,7 +32,7 @@ EXPORTS = ("bvf_version", "bvf_courant_limit", "bvf_strerror", "bvf_create", "bv
            "bvf_rs_elements", "bvf_set_time_budget", "bvf_state_bytes", "bvf_state_save",
            "bvf_state_load", "bvf_test_withhold_copy", "bvf_bowl_array", "bvf_steer_weights",
            "bvf_time_reversal_plane", "bvf_batch_run_graph", "bvf_batch_tune_domains",
-           "bvf_set_tile", "bvf_get_tile", "bvf_batch_tune_graph")
+           "bvf_set_tile", "bvf_get_tile", "bvf_batch_tune_graph", "bvf_plan_host")
 
 
 class BvfError(RuntimeError):
@@ -162,6 +162,10 @@ def lib():
         L.bvf_plan.argtypes = [vp, vp, vp, ctypes.POINTER(Material), i, ctypes.POINTER(Material),
                                ctypes.POINTER(Bowl), i, ctypes.POINTER(PlanParams), vp, vp, vp, vp,
                                vp, ctypes.POINTER(PlanOut), vp]
+        L.bvf_plan_host.argtypes = [vp, vp, vp, ctypes.POINTER(Material), i,
+                                    ctypes.POINTER(Material), ctypes.POINTER(Bowl), i,
+                                    ctypes.POINTER(PlanParams), vp, vp, vp, vp,
+                                    ctypes.POINTER(PlanOut), vp]
         L.bvf_set_time_budget.argtypes = [vp, d]
         L.bvf_batch_run_graph.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(Capture), i, vp]
         L.bvf_batch_tune_domains.argtypes = [vp, i, ctypes.POINTER(Tile), i, ctypes.POINTER(Tile),
@@ -658,6 +662,36 @@ class Batch:
 
 
 # ---- one placement end to end ----------------------------------------------
+def _host_ptr(a, dtype):
+    """Address of a contiguous host array (numpy, or a CPU torch tensor)."""
+    import numpy as np
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous %s array" % np.dtype(dtype).name)
+        return ctypes.c_void_p(a.ctypes.data)
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def bvf_plan_host(skull, water, h_index, table, water_row, bowl, k_src, params, h_peak, h_T,
+                  h_Tmax, h_cem, stream=None):
+    """bvf_plan with host buffers (numpy arrays or pinned CPU tensors);
+    returns a PlanOut."""
+    import numpy as np
+    tab = material_array(table)
+    wat = material_array([water_row])
+    b = bowl if isinstance(bowl, Bowl) else make_bowl(bowl)
+    out = PlanOut()
+    _check(lib().bvf_plan_host(skull.ctx, water.ctx, _host_ptr(h_index, np.uint8), tab, len(tab),
+                               wat, ctypes.byref(b), int(k_src), ctypes.byref(params),
+                               _host_ptr(h_peak, np.float32),
+                               _host_ptr(h_T, np.float32) if h_T is not None else None,
+                               _host_ptr(h_Tmax, np.float32), _host_ptr(h_cem, np.float64),
+                               ctypes.byref(out), _stream(stream)))
+    return out
+
+
 def bvf_plan(skull, water, index, table, water_row, bowl, k_src, params, peak, amp, T, Tmax, cem,
              stream=None):
     """Returns a PlanOut; outputs land in the given CUDA tensors."""

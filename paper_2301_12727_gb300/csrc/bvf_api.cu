@@ -67,6 +67,10 @@ struct bvf_ctx {
     // the tensor maps when nx % 16 != 0 (a TMA row stride is whole 16-byte units)
     uint8_t *index_p = nullptr;
     size_t index_pitch = 0;
+    // device staging of bvf_plan_host (allocated on its first call)
+    uint8_t *h_index_d = nullptr;
+    float *h_peak_d = nullptr, *h_T_d = nullptr, *h_Tmax_d = nullptr;
+    double *h_amp_d = nullptr, *h_cem_d = nullptr;
     // host mirror
     std::vector<bvf_material> table;
     std::vector<MatDerived> derived;
@@ -576,7 +580,8 @@ void bvf_destroy(bvf_ctx *c)
     if (!c) return;
     void *bufs[] = {c->fields, c->psi, c->peak, c->dftC, c->dftS, c->index, c->lut, c->buoy,
                     c->pml, c->src, c->flag, c->scratch_u, c->T2, c->Q, c->cemf, c->tlut,
-                    c->kface, c->index_p};
+                    c->kface, c->index_p, c->h_index_d, c->h_peak_d, c->h_T_d, c->h_Tmax_d,
+                    c->h_amp_d, c->h_cem_d};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -1084,6 +1089,41 @@ int bvf_run_thermal(bvf_ctx *c, const bvf_thermal *th, const double *d_amp, floa
     const int rc = to_celsius(a);
     if (rc != BVF_OK) return rc;
     c->thermal_steps += total;
+    return BVF_OK;
+}
+
+int bvf_plan_host(bvf_ctx *skull, bvf_ctx *water, const uint8_t *h_index,
+                  const bvf_material *h_table, int n_mat, const bvf_material *h_water,
+                  const bvf_bowl *bowl, int k_src, const bvf_plan_params *pp, float *h_peak,
+                  float *h_T, float *h_Tmax, double *h_cem43, bvf_plan_result *out, void *stream)
+{
+    if (!skull || !h_index || !h_peak || !h_Tmax || !h_cem43)
+        return fail(skull, BVF_E_ARG, "bvf_plan_host: NULL argument");
+    bvf_ctx *c = skull;
+    const size_t N = c->N;
+    if (!c->h_index_d) {
+        CK(cudaMalloc(&c->h_index_d, N), "bvf_plan_host: staging");
+        CK(cudaMalloc(&c->h_peak_d, N * sizeof(float)), "bvf_plan_host: staging");
+        CK(cudaMalloc(&c->h_T_d, N * sizeof(float)), "bvf_plan_host: staging");
+        CK(cudaMalloc(&c->h_Tmax_d, N * sizeof(float)), "bvf_plan_host: staging");
+        CK(cudaMalloc(&c->h_amp_d, N * sizeof(double)), "bvf_plan_host: staging");
+        CK(cudaMalloc(&c->h_cem_d, N * sizeof(double)), "bvf_plan_host: staging");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(c->h_index_d, h_index, N, cudaMemcpyHostToDevice, s), "bvf_plan_host: index in");
+    const int rc = bvf_plan(skull, water, c->h_index_d, h_table, n_mat, h_water, bowl, k_src, pp,
+                            c->h_peak_d, c->h_amp_d, c->h_T_d, c->h_Tmax_d, c->h_cem_d, out, stream);
+    if (rc != BVF_OK) return rc;
+    CK(cudaMemcpyAsync(h_peak, c->h_peak_d, N * sizeof(float), cudaMemcpyDeviceToHost, s),
+       "bvf_plan_host: peak out");
+    if (h_T)
+        CK(cudaMemcpyAsync(h_T, c->h_T_d, N * sizeof(float), cudaMemcpyDeviceToHost, s),
+           "bvf_plan_host: T out");
+    CK(cudaMemcpyAsync(h_Tmax, c->h_Tmax_d, N * sizeof(float), cudaMemcpyDeviceToHost, s),
+       "bvf_plan_host: T_max out");
+    CK(cudaMemcpyAsync(h_cem43, c->h_cem_d, N * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "bvf_plan_host: CEM43 out");
+    CK(cudaStreamSynchronize(s), "bvf_plan_host");
     return BVF_OK;
 }
 

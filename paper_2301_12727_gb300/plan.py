@@ -116,3 +116,19 @@ class Planner:
                          dict(bowl), c.k_src, pp, peak, amp, T, Tmax, cem)
         return PlanResult(peak, amp, None, Tmax, cem, r.EL, r.TS, r.z_m, r.Iw_max, r.p_scale,
                           2 * c.n_steps * c.voxels)
+
+    def run_host(self, index, materials, bowl: dict, peak, Tmax, cem, T=None,
+                 regime: ThermalRegime | None = None,
+                 i_sppa_brain: float = I_SPPA_BRAIN_DEFAULT, serial: bool = False):
+        """The same plan with host buffers (bvf_plan_host): index (nz, ny, nx)
+        uint8 and the outputs peak, Tmax (float32), cem (float64) and T
+        (float32, optional) are host arrays or pinned CPU tensors; the copies
+        run inside the call.  Returns the PlanOut scalars."""
+        c = self.case
+        regime = regime or ThermalRegime()
+        th = bvf.Thermal(regime.dt, regime.n_on, regime.n_off, regime.duty, regime.T_a,
+                         regime.rhob_cb, 0.0)
+        pp = bvf.PlanParams(c.n_steps, c.dft_start, c.dft_steps, i_sppa_brain, th,
+                            1 if serial else 0)
+        return bvf.bvf_plan_host(self.skull, self.water, index, materials, self.water_table[0],
+                                 dict(bowl), c.k_src, pp, peak, T, Tmax, cem)

@@ -84,6 +84,8 @@ def test_null_pointers_rejected(bvf):
     assert L.bvf_batch_tune_domains(None, 1, ctypes.byref(t), 1, None, None) == bvf.BVF_E_ARG
     assert L.bvf_batch_tune_graph(None, 1, ctypes.byref(t), 1, 8, ctypes.byref(t), None,
                                   None) == bvf.BVF_E_ARG
+    assert L.bvf_plan_host(None, None, None, None, 0, None, None, 0, None, None, None, None,
+                           None, None, None) == bvf.BVF_E_ARG
     L.bvf_destroy(None)
 
 

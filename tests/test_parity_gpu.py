@@ -604,6 +604,31 @@ def test_gpu_f16_fields_round_trip_through_the_storage_scales(bvf):
     s.close()
 
 
+def test_gpu_plan_with_host_buffers_equals_the_device_call(bvf):
+    """bvf_plan_host (host index in, host maps out, the copies inside the
+    call) gives bvf_plan's maps and scalars bit for bit, on repeated calls."""
+    import torch
+    from paper_2301_12727_gb300 import plan, synth
+    c = synth.skull_case(64, 48, 40, dx=0.5e-3, n_steps=4 * 46, aperture=20e-3, roc=18e-3,
+                         dft_cycles=2, n_pml=5, seed=8)
+    regime = plan.ThermalRegime(t_on=1.0, t_off=0.5, dt=0.1)
+    pl = plan.Planner(c)
+    r = pl.run(torch.from_numpy(c.index).cuda(), c.materials, c.bowl, regime=regime)
+    want = [r.peak.cpu().numpy(), r.Tmax.cpu().numpy(), r.cem43.cpu().numpy()]
+    h_idx = torch.from_numpy(c.index).pin_memory()
+    peak = torch.empty(c.index.shape, dtype=torch.float32).pin_memory()
+    Tmax = torch.empty_like(peak).pin_memory()
+    T = torch.empty_like(peak).pin_memory()
+    cem = torch.empty(c.index.shape, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        out = pl.run_host(h_idx, c.materials, c.bowl, peak, Tmax, cem, T=T, regime=regime)
+        assert out.EL == r.EL and out.z_m == r.z_m and out.p_scale == r.p_scale
+        for a, b in zip((peak.numpy(), Tmax.numpy(), cem.numpy()), want):
+            assert np.array_equal(a, b)
+    assert T.numpy().max() > regime.T_a
+    pl.close()
+
+
 def test_gpu_plan_call_equals_the_step_by_step_sequence(bvf):
     """bvf_plan (one C-ABI call) gives exactly what the separate calls give:
     skull and water runs, E_L, T_S, z_m, I_w,max, the scaling and the BHTE."""
