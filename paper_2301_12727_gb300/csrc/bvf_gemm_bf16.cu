@@ -46,6 +46,7 @@ struct GemmLayout {
     static constexpr int off_bar = 2 * STAGE;
     static constexpr int off_tmem = off_bar + 16;
     static constexpr int bytes = off_tmem + 16;
+    static_assert(2 * STAGE >= 4 * 32 * 33 * 4, "the epilogue's transpose buffers fit the stages");
     static constexpr uint32_t SBO = GSEG * 128;      // byte step between 8-row groups
 };
 
@@ -170,9 +171,37 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ bvf_g
         }
     } else {
         tc::fence_after();
+        // element (mm, n) of the tile: alpha, beta C, bias, activation, store
+        auto finish = [&](int mm, int n, float acc) {
+            float *cp = g.C + (long long)b * g.scb + (long long)mm * g.scm + (long long)n * g.scn;
+            float *pp = g.C_pre ? g.C_pre + (long long)b * g.scb + (long long)mm * g.scm +
+                                      (long long)n * g.scn
+                                : nullptr;
+            float v = g.alpha * acc;
+            if (g.ksplit > 1) {
+                if (nc > 0) atomicAdd(cp, v);
+                return;
+            }
+            if (g.beta != 0.0f) v = fmaf(g.beta, *cp, v);
+            if (g.bias_mode == 1) v += __ldg(g.bias + n);
+            else if (g.bias_mode == 2) v += __ldg(g.bias + mm);
+            if (g.act == 1) {
+                if (pp) *pp = v;
+                v = gelu_exact(v);
+            } else if (g.act == 2) {
+                v *= gelu_grad(*pp);
+            }
+            *cp = v;
+        };
+        // Thread `lane` of a warp holds row warp * 32 + lane of the tile.  With
+        // the columns of C contiguous (scn == 1) each warp transposes its
+        // 32 x 32 block through shared memory (the stage buffers, free now
+        // that every product has completed) so that a warp's stores cover 32
+        // consecutive columns of one row; otherwise (rows contiguous) it
+        // stores straight from the accumulator row.
+        const bool by_rows = g.scn == 1 && g.ksplit == 1;
+        float *wbuf = reinterpret_cast<float *>(sm) + warp * (32 * 33);
         const int m = m0 + warp * 32 + lane;
-        float *crow = g.C + (long long)b * g.scb + (long long)m * g.scm;
-        float *prow = g.C_pre ? g.C_pre + (long long)b * g.scb + (long long)m * g.scm : nullptr;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
             float r[32];
@@ -183,27 +212,23 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ bvf_g
 #pragma unroll
                 for (int i = 0; i < 32; ++i) r[i] = 0.0f;
             }
-            if (m >= g.M) continue;
+            if (by_rows) {
+                __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int n = n0 + c0 + i;
-                if (n < g.N) {
-                    float *cp = crow + (long long)n * g.scn;
-                    float v = g.alpha * r[i];
-                    if (g.ksplit > 1) {
-                        if (nc > 0) atomicAdd(cp, v);
-                    } else {
-                        if (g.beta != 0.0f) v = fmaf(g.beta, *cp, v);
-                        if (g.bias_mode == 1) v += __ldg(g.bias + n);
-                        else if (g.bias_mode == 2) v += __ldg(g.bias + m);
-                        if (g.act == 1) {
-                            if (prow) prow[(long long)n * g.scn] = v;
-                            v = gelu_exact(v);
-                        } else if (g.act == 2) {
-                            v *= gelu_grad(prow[(long long)n * g.scn]);
-                        }
-                        *cp = v;
-                    }
+                for (int i = 0; i < 32; ++i) wbuf[lane * 33 + i] = r[i];
+                __syncwarp();
+                const int n = n0 + c0 + lane;
+#pragma unroll 4
+                for (int i = 0; i < 32; ++i) {
+                    const int mm = m0 + warp * 32 + i;
+                    if (mm < g.M && n < g.N) finish(mm, n, wbuf[i * 33 + lane]);
+                }
+            } else {
+                if (m >= g.M) continue;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int n = n0 + c0 + i;
+                    if (n < g.N) finish(m, n, r[i]);
                 }
             }
         }
