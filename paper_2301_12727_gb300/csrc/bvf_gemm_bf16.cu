@@ -38,15 +38,18 @@ namespace {
 constexpr int GK = 64;                 // K chunk (BF16 elements): 128 bytes per row
 constexpr int GSEG = GK / 8;           // 16-byte core-matrix rows per tile row and chunk
 
-template <int BN>
+// NS shared-memory stages of GK-wide K chunks: two overlap the staging of a
+// chunk with the products of the previous one; products of a single chunk
+// (K <= GK) take one, so twice as many blocks fit per SM.
+template <int BN, int NS>
 struct GemmLayout {
     static constexpr int A_BYTES = 128 * GK * 2;
     static constexpr int B_BYTES = BN * GK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int off_bar = 2 * STAGE;
+    static constexpr int off_bar = NS * STAGE;
     static constexpr int off_tmem = off_bar + 16;
     static constexpr int bytes = off_tmem + 16;
-    static_assert(2 * STAGE >= 4 * 32 * 33 * 4, "the epilogue's transpose buffers fit the stages");
+    static_assert(NS * STAGE >= 4 * 32 * 33 * 4, "the epilogue's transpose buffers fit the stages");
     static constexpr uint32_t SBO = GSEG * 128;      // byte step between 8-row groups
 };
 
@@ -99,11 +102,11 @@ __device__ __forceinline__ float gelu_grad(float s)
            s * 0.39894228040143268f * expf(-0.5f * s * s);
 }
 
-template <int BN>
+template <int BN, int NS>
 __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ bvf_gemm g, int *flag)
 {
     extern __shared__ __align__(128) unsigned char sm[];
-    using Lay = GemmLayout<BN>;
+    using Lay = GemmLayout<BN, NS>;
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + Lay::off_bar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + Lay::off_tmem);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -133,10 +136,10 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ bvf_g
     bool bad = false;
     int nc = 0;                             // chunks whose products were issued
     for (int c = c_begin; c < c_end; ++c, ++nc) {
-        const int st = nc & 1;
+        const int st = nc % NS;
         unsigned char *sa = sm + st * Lay::STAGE, *sb = sa + Lay::A_BYTES;
-        if (nc >= 2) {                      // the products of chunk nc - 2 read this stage
-            const bool ok = tma::mbar_wait(&bar[st], ((nc - 2) >> 1) & 1, tma::kWaitLimit);
+        if (nc >= NS) {                     // the products of chunk nc - NS read this stage
+            const bool ok = tma::mbar_wait(&bar[st], ((nc - NS) / NS) & 1, tma::kWaitLimit);
             if (__syncthreads_or(!ok)) {
                 bad = true;
                 break;
@@ -160,13 +163,13 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ bvf_g
     }
     if (!bad && nc > 0) {                   // the last commit covers every earlier product
         const int last = nc - 1;
-        const bool ok = tma::mbar_wait(&bar[last & 1], (last >> 1) & 1, tma::kWaitLimit);
+        const bool ok = tma::mbar_wait(&bar[last % NS], (last / NS) & 1, tma::kWaitLimit);
         bad = __syncthreads_or(!ok) != 0;
     }
     if (bad) {
         if (tid == 0) {
             const int last = nc - 1;
-            if (last >= 0) tma::mbar_wait(&bar[last & 1], (last >> 1) & 1, tma::kWaitLimit);
+            if (last >= 0) tma::mbar_wait(&bar[last % NS], (last / NS) & 1, tma::kWaitLimit);
             atomicOr(flag, 2);
         }
     } else {
@@ -238,8 +241,8 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(const __grid_constant__ bvf_g
     if (warp == 0) tc::dealloc(tbase, BN);
 }
 
-template <int BN>
-cudaError_t launch_gemm_t(const bvf_gemm &g, int *flag, cudaStream_t s)
+template <int BN, int NS>
+cudaError_t launch_gemm_ns(const bvf_gemm &g, int *flag, cudaStream_t s)
 {
     const dim3 grid((g.M + 127) / 128, (g.N + BN - 1) / BN, g.batch * g.ksplit);
     // the shared-memory limit is raised once per process, so that later
@@ -247,12 +250,21 @@ cudaError_t launch_gemm_t(const bvf_gemm &g, int *flag, cudaStream_t s)
     static std::atomic<int> raised{0};
     if (!raised.load(std::memory_order_acquire)) {
         const cudaError_t e = cudaFuncSetAttribute(
-            k_gemm_bf16<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmLayout<BN>::bytes);
+            k_gemm_bf16<BN, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            GemmLayout<BN, NS>::bytes);
         if (e != cudaSuccess) return e;
         raised.store(1, std::memory_order_release);
     }
-    k_gemm_bf16<BN><<<grid, 128, GemmLayout<BN>::bytes, s>>>(g, flag);
+    k_gemm_bf16<BN, NS><<<grid, 128, GemmLayout<BN, NS>::bytes, s>>>(g, flag);
     return cudaGetLastError();
+}
+
+// one stage when the product is a single K chunk
+template <int BN>
+cudaError_t launch_gemm_t(const bvf_gemm &g, int *flag, cudaStream_t s)
+{
+    const int per_split = ((g.K + GK - 1) / GK + g.ksplit - 1) / g.ksplit;
+    return per_split <= 1 ? launch_gemm_ns<BN, 1>(g, flag, s) : launch_gemm_ns<BN, 2>(g, flag, s);
 }
 
 }  // namespace
