@@ -269,11 +269,15 @@ cudaError_t launch_gemm_t(const bvf_gemm &g, int *flag, cudaStream_t s)
 
 }  // namespace
 
-// BN: the smallest tile width of 32, 64, 128, 256 that holds N (256 beyond)
+// BN: the smallest tile width of 32, 64, 128, 256 that holds N (256 beyond),
+// at most 64 for a single-chunk product
 cudaError_t launch_gemm_bf16(const bvf_gemm &g, int *flag, cudaStream_t s)
 {
     if (g.N <= 32) return launch_gemm_t<32>(g, flag, s);
-    if (g.N <= 64) return launch_gemm_t<64>(g, flag, s);
+    // a single-chunk product restages its small A tile per N tile but keeps
+    // 64 TMEM columns per block, so up to 8 blocks share an SM's 512
+    const int per_split = ((g.K + GK - 1) / GK + g.ksplit - 1) / g.ksplit;
+    if (g.N <= 64 || per_split <= 1) return launch_gemm_t<64>(g, flag, s);
     if (g.N <= 128) return launch_gemm_t<128>(g, flag, s);
     return launch_gemm_t<256>(g, flag, s);
 }
