@@ -9,14 +9,15 @@
 // computed in FP64 on the host.  Per layer:
 //   - the y and z transforms, the mode mix and their inverses run on the
 //     truncated spectra (a few MB, L2-resident);
-//   - one row pass per (z, y) row does the inverse x transform, W v + b and
-//     GELU as one tensor-core product, keeps the new row in shared memory
-//     and takes the next layer's forward x transform from it, so v is read
-//     and written once per layer (k_row_mma, mma.sync TF32);
-//   - the lift is the same row pass without the spectral term.
-// The projection runs on the fifth-generation tensor cores (k_project_tc:
-// tcgen05.mma into TMEM, tcgen05.ld epilogue with GELU).  Every product uses
-// the three-term TF32 split, which keeps FP32 accuracy.  Rows too long for
+//   - the layer output (inverse x transform, W v + b and GELU) is one
+//     tensor-core product per 128-point tile of a (z, y) row (k_row_tc), and
+//     the next layer's forward x transform is one tall product over all rows
+//     of the new v (k_dftx_tc);
+//   - the lift is the layer output without the spectral term.
+// The projection is a tensor-core product with GELU in its epilogue
+// (k_project_tc).  All three run on the fifth-generation tensor cores
+// (tcgen05.mma into TMEM, tcgen05.ld epilogues), and every product uses the
+// three-term TF32 split, which keeps FP32 accuracy.  Rows too long for
 // shared memory take unfused SIMT kernels (k_lift, k_dftx, k_layer_out).
 #include <cuda_runtime.h>
 
@@ -377,12 +378,10 @@ __global__ void k_layer_out(const float *__restrict__ v, const float2 *__restric
 }
 
 // ------------------------------------------- tensor-core tiles (TF32 x 3)
-// mma.sync m16n8k8 with TF32 operands and FP32 accumulation.  Each FP32
-// operand is split into a TF32 head and the TF32 rounding of its remainder,
-// and a b is taken as a_lo b_hi + a_hi b_lo + a_hi b_hi (the three-product
-// scheme of Ootomo and Yokota, 2022), which keeps FP32-level accuracy.
-// Fragment layout (lane = 4 g + t): A rows g, g+8 and columns t, t+4;
-// B rows t, t+4 and column g; C/D rows g, g+8 and columns 2t, 2t+1.
+// Each FP32 operand of a tensor-core product is split into a TF32 head and
+// the TF32 rounding of its remainder, and a b is taken as
+// a_lo b_hi + a_hi b_lo + a_hi b_hi (the three-product scheme of Ootomo and
+// Yokota, 2022), which keeps FP32-level accuracy.
 __device__ __forceinline__ uint32_t tf32_rna(float x)
 {
     uint32_t r;
@@ -396,208 +395,437 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
     lo = tf32_rna(x - __uint_as_float(hi));
 }
 
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1)
+// the three products of one K step: D (+)= A_lo B_hi + A_hi B_lo + A_hi B_hi
+__device__ __forceinline__ void mma3_tc(uint32_t d, uint64_t ah, uint64_t al, uint64_t bh,
+                                        uint64_t bl, uint32_t idesc, int acc)
 {
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
-                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+    tc::mma(d, al, bh, idesc, acc);
+    tc::mma(d, ah, bl, idesc, 1);
+    tc::mma(d, ah, bh, idesc, 1);
 }
 
-// d += a b in three products (small terms first)
-__device__ __forceinline__ void mma3(float (&d)[4], const uint32_t (&ah)[4],
-                                     const uint32_t (&al)[4], uint32_t bh0, uint32_t bh1,
-                                     uint32_t bl0, uint32_t bl1)
-{
-    mma_tf32(d, al, bh0, bh1);
-    mma_tf32(d, ah, bl0, bl1);
-    mma_tf32(d, ah, bh0, bh1);
-}
-
-// ------------------------------------------------ tensor-core row pass
-// The row pass above as two tensor-core products per (z, y) row:
-//   phase 2: D[x][o] = sum_k X[x][k] Y[k][o], X = [v[c][x] | cos, sin of the
-//            kept kx at x], Y = [W^T ; (Re A', -Im A') s_kx], s_0 = 1/N,
-//            s_kx = 2/N, plus b, then GELU;
-//   phase 3: Anext[o][kx] = sum_x v'[o][x] (cos - i sin)(kx x 2 pi / nx),
-//            a product over x of the new row (shared memory) and the table.
-// Persistent blocks keep the split twiddle table T[j][x] (j = 2 kx for cos,
-// 2 kx + 1 for sin, zero rows up to a multiple of 8) and the split W; each
-// row brings its own spectral rows of Y.  Pitches: P = 8 mod 32 for [.][x]
-// arrays and PW = 8 mod 32 for [k][o] arrays.
-struct RowMmaLayout {
-    int P, PW, JP, sTh, sTl, sWh, sWl, sSh, sSl, sV, sb, words;
-    __host__ __device__ RowMmaLayout(int ksw, int cout, int m, int nx)
+// ------------------------------------------------ tcgen05 layer output
+// The output of a Fourier layer (or of the lift) on 128-point tiles of one
+// (z, y) row, points x = 128 t .. 128 t + 127:
+//   D[x][o] = sum_c v[c][x] W[o][c] + sum_j T[j][x] S[j][o]     (TMEM)
+//   vout[o][x] = act(D[x][o] + b[o])
+// T[j][x] holds cos and sin of the kept kx at x (j = 2 kx, 2 kx + 1) and S
+// the row's spectral pairs S[2 kx][o] = Re A'(o, kx) s_kx,
+// S[2 kx + 1][o] = -Im A'(o, kx) s_kx with s_0 = 1/N and s_kx = 2/N: the
+// real inverse DFT along x of the kept half spectrum.  The lift is the same
+// product without the spectral term.
+// Operands sit in shared memory in the canonical K-major layout: A = the
+// tile's input channels (staged, split, each tile) and T (all x tiles of a
+// row, staged once per block); B = W (once per block) and S (once per row).
+// 256 threads: thread i stages point i mod 128 of its half of the channels
+// and, in the epilogue, reads half of the output channels of that point.
+struct RowTcLayout {
+    int JP, nxt, sAh, sAl, sTh, sTl, sBh, sBl, sSh, sSl, sb, bar, tmem, bytes;
+    __host__ __device__ RowTcLayout(int width, int kc, int m, int nx, bool spec)
     {
-        const int nx16 = (nx + 15) & ~15;
-        P = nx16 + ((8 - nx16 % 32) + 32) % 32;
-        PW = cout + ((8 - cout % 32) + 32) % 32;
         JP = ((2 * m + 7) / 8) * 8;
-        sTh = 0;
-        sTl = sTh + JP * P;
-        sWh = sTl + JP * P;
-        sWl = sWh + 8 * ksw * PW;
-        sSh = sWl + 8 * ksw * PW;
-        sSl = sSh + JP * PW;
-        sV = sSl + JP * PW;
-        sb = sV + cout * P;
-        words = sb + cout;
+        nxt = (nx + 127) / 128;
+        const int a = 128 * kc * 4, t = spec ? nxt * 128 * JP * 4 : 0, bw = width * kc * 4,
+                  s = spec ? width * JP * 4 : 0;
+        sAh = 0;
+        sAl = sAh + a;
+        sTh = sAl + a;
+        sTl = sTh + t;
+        sBh = sTl + t;
+        sBl = sBh + bw;
+        sSh = sBl + bw;
+        sSl = sSh + s;
+        sb = sSl + s;
+        bar = (sb + width * 4 + 15) & ~15;
+        tmem = bar + 16;
+        bytes = tmem + 16;
     }
 };
 
-template <int NT, int KSW>     // cout = 8 NT output channels; input channels padded to 8 KSW
+template <int W, int KC>     // W output channels; input channels padded to KC (a multiple of 8)
 __global__ void __launch_bounds__(256, 2)
-k_row_mma(const float *__restrict__ vin, int cin, const float2 *Ap, const float *__restrict__ W,
-          const float *__restrict__ b, int nx, int rows, int m, float invN, int act,
-          const float2 *__restrict__ tx, float *__restrict__ vout, float2 *Anext, int N)
+k_row_tc(const float *__restrict__ vin, int cin, const float2 *__restrict__ Ap,
+         const float *__restrict__ Wm, const float *__restrict__ b, int nx, int rows, int m,
+         float invN, int act, const float2 *__restrict__ tx, float *__restrict__ vout, int N,
+         int *flag)
 {
-    constexpr int cout = 8 * NT;
-    extern __shared__ __align__(16) uint32_t s_m[];
-    const RowMmaLayout L(KSW, cout, m, nx);
-    const int P = L.P, PW = L.PW, JP = L.JP, KSS = JP / 8;
-    const int nx16 = (nx + 15) & ~15;
-    uint32_t *sTh = s_m + L.sTh, *sTl = s_m + L.sTl, *sWh = s_m + L.sWh, *sWl = s_m + L.sWl,
-             *sSh = s_m + L.sSh, *sSl = s_m + L.sSl;
-    float *sV = reinterpret_cast<float *>(s_m + L.sV), *sb = reinterpret_cast<float *>(s_m + L.sb);
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const bool spec = Ap != nullptr, fwd = Anext != nullptr;
-    // block-constant operands
-    if (spec || fwd) {
-        for (int j = 0; j < JP; ++j)
-            for (int x = tid; x < P; x += nth) {
-                float val = 0.0f;
-                if (j < 2 * m && x < nx) {
-                    const float2 e = tx[(long)(j >> 1) * nx + x];
-                    val = (j & 1) ? e.y : e.x;
-                }
-                tf32_split(val, sTh[j * P + x], sTl[j * P + x]);
-            }
+    static_assert(W % 16 == 0 && W <= 64 && KC % 8 == 0, "tile shape");
+    extern __shared__ __align__(128) unsigned char s_r[];
+    const bool spec = Ap != nullptr;
+    const RowTcLayout L(W, KC, m, nx, spec);
+    const int JP = L.JP, nxt = L.nxt;
+    unsigned char *sAh = s_r + L.sAh, *sAl = s_r + L.sAl, *sTh = s_r + L.sTh, *sTl = s_r + L.sTl,
+                  *sBh = s_r + L.sBh, *sBl = s_r + L.sBl, *sSh = s_r + L.sSh, *sSl = s_r + L.sSl;
+    float *sb = reinterpret_cast<float *>(s_r + L.sb);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_r + L.bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(s_r + L.tmem);
+    const int tid = threadIdx.x, warp = tid >> 5, pt = tid & 127, half = tid >> 7;
+    constexpr int NCOLS = W <= 32 ? 32 : 64;
+    // block-constant operands: W (zero beyond cin), T (zero beyond 2m and nx),
+    // the zero rows j >= 2m of S, b
+    for (int e = tid; e < W * KC; e += 256) {
+        const int o = e / KC, c = e - o * KC;
+        uint32_t h, l;
+        tf32_split(c < cin ? Wm[(long)o * cin + c] : 0.0f, h, l);
+        const uint32_t off = tc::kmaj_off(o, c, KC);
+        *reinterpret_cast<uint32_t *>(sBh + off) = h;
+        *reinterpret_cast<uint32_t *>(sBl + off) = l;
     }
-    for (int k = 0; k < 8 * KSW; ++k)
-        for (int o = tid; o < PW; o += nth) {
-            const float w = (k < cin && o < cout) ? W[(long)o * cin + k] : 0.0f;
-            tf32_split(w, sWh[k * PW + o], sWl[k * PW + o]);
-        }
-    for (int o = tid; o < cout; o += nth) sb[o] = b[o];
-
-    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
-    // rows j >= 2m and columns o >= cout of the spectral part of Y stay zero
     if (spec) {
-        for (int e = tid; e < JP * PW; e += nth) {
-            const int j = e / PW, o = e - j * PW;
-            if (j >= 2 * m || o >= cout) tf32_split(0.0f, sSh[e], sSl[e]);
+        for (int e = tid; e < nxt * 128 * JP; e += 256) {
+            const int t = e / (128 * JP), r = e - t * 128 * JP, xl = r / JP, j = r - xl * JP;
+            const int x = 128 * t + xl;
+            float val = 0.0f;
+            if (j < 2 * m && x < nx) {
+                const float2 c = tx[(long)(j >> 1) * nx + x];
+                val = (j & 1) ? c.y : c.x;
+            }
+            uint32_t h, l;
+            tf32_split(val, h, l);
+            const uint32_t off = (uint32_t)(t * 128 * JP * 4) + tc::kmaj_off(xl, j, JP);
+            *reinterpret_cast<uint32_t *>(sTh + off) = h;
+            *reinterpret_cast<uint32_t *>(sTl + off) = l;
+        }
+        for (int e = tid; e < W * JP; e += 256) {
+            const int o = e / JP, j = e - o * JP;
+            if (j >= 2 * m) {
+                const uint32_t off = tc::kmaj_off(o, j, JP);
+                *reinterpret_cast<uint32_t *>(sSh + off) = 0u;
+                *reinterpret_cast<uint32_t *>(sSl + off) = 0u;
+            }
         }
     }
-    // the (o, kx) pairs of A' a thread converts, loaded one row ahead
-    constexpr int PRE = (8 * NT * BVF_FNO_MAX_MODES + 255) / 256;
+    for (int o = tid; o < W; o += 256) sb[o] = b[o];
+    if (tid == 0) {
+        bvf::tma::mbar_init(bar, 1);
+        bvf::tma::mbar_init_fence();
+    }
+    if (warp == 0) {
+        tc::alloc(tslot, NCOLS);
+        tc::relinquish();
+    }
+    bvf::tma::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t idesc = tc::idesc_tf32(128, W);
+    constexpr int CH = KC / 2;                  // channels a thread stages
+    constexpr uint32_t SBO_A = (KC / 4) * 128;
+    const uint32_t sbo_t = (uint32_t)(JP / 4) * 128;
+    // this thread's channels of its point of a tile, loaded one tile ahead
+    float xr[CH];
+    auto load_v = [&](int row, int t) {
+        const int x = 128 * t + pt;
+        const bool ok = x < nx;
+        const long p = (long)row * nx + x;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int ch = half * CH + c;
+            xr[c] = (ok && ch < cin) ? vin[(long)ch * N + p] : 0.0f;
+        }
+    };
+    // the (o, kx) pairs of A' this thread converts, loaded one row ahead
+    constexpr int PRE = (W * BVF_FNO_MAX_MODES + 255) / 256;
     float2 pre[PRE];
-    auto load_pairs = [&](int r) {
+    auto load_pairs = [&](int row) {
 #pragma unroll
         for (int i = 0; i < PRE; ++i) {
-            const int e = tid + i * nth;
-            if (e < cout * m) {
+            const int e = tid + i * 256;
+            if (e < W * m) {
                 const int o = e / m, kx = e - o * m;
-                pre[i] = Ap[((long)o * rows + r) * m + kx];
+                pre[i] = Ap[((long)o * rows + row) * m + kx];
             }
         }
     };
-    if (spec && (int)blockIdx.x < rows) load_pairs(blockIdx.x);
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const long base = (long)row * nx;
-        __syncthreads();          // the previous row is done with sS and sV
-        if (spec) {
-            // this row's spectral rows of Y from the pairs loaded one row ahead
+    int row = blockIdx.x, t = 0, it = 0;
+    if (row < rows) {
+        load_v(row, 0);
+        if (spec) load_pairs(row);
+    }
+    bool gave_up = false;
+    while (row < rows) {
+        // stage the tile's channels (and, for a new row, its spectral pairs)
+#pragma unroll
+        for (int c4 = 0; c4 < CH / 4; ++c4) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tf32_split(xr[4 * c4 + q], h[q], l[q]);
+            const uint32_t off = tc::kmaj_off(pt, half * CH + 4 * c4, KC);
+            *reinterpret_cast<uint4 *>(sAh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4 *>(sAl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+        if (spec && t == 0) {
 #pragma unroll
             for (int i = 0; i < PRE; ++i) {
-                const int e = tid + i * nth;
-                if (e < cout * m) {
+                const int e = tid + i * 256;
+                if (e < W * m) {
                     const int o = e / m, kx = e - o * m;
                     const float sc = (kx == 0 ? 1.0f : 2.0f) * invN;
-                    tf32_split(pre[i].x * sc, sSh[(2 * kx) * PW + o], sSl[(2 * kx) * PW + o]);
-                    tf32_split(-pre[i].y * sc, sSh[(2 * kx + 1) * PW + o],
-                               sSl[(2 * kx + 1) * PW + o]);
+                    uint32_t h0, l0, h1, l1;
+                    tf32_split(pre[i].x * sc, h0, l0);
+                    tf32_split(-pre[i].y * sc, h1, l1);
+                    const uint32_t off = tc::kmaj_off(o, 2 * kx, JP);
+                    *reinterpret_cast<uint2 *>(sSh + off) = make_uint2(h0, h1);
+                    *reinterpret_cast<uint2 *>(sSl + off) = make_uint2(l0, l1);
                 }
             }
-            if (row + (int)gridDim.x < rows) load_pairs(row + gridDim.x);
         }
+        bvf::tma::fence_async_smem();
+        tc::fence_before();
         __syncthreads();
-        // phase 2: 16-point tiles of the row
-        for (int mt = warp; mt < nx16 / 16; mt += nth / 32) {
-            const int xa = 16 * mt + g, xb = xa + 8;
-            float d[NT][4];
+        if (tid == 0) {
+            tc::fence_after();
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
-                const float b0 = sb[8 * nt + 2 * t], b1 = sb[8 * nt + 2 * t + 1];
-                d[nt][0] = b0;
-                d[nt][1] = b1;
-                d[nt][2] = b0;
-                d[nt][3] = b1;
-            }
-#pragma unroll
-            for (int ks = 0; ks < KSW; ++ks) {
-                const int c0 = 8 * ks + t, c1 = c0 + 4;
-                uint32_t ah[4], al[4];
-                const bool c0ok = c0 < cin, c1ok = c1 < cin;
-                tf32_split(c0ok && xa < nx ? vin[(long)c0 * N + base + xa] : 0.0f, ah[0], al[0]);
-                tf32_split(c0ok && xb < nx ? vin[(long)c0 * N + base + xb] : 0.0f, ah[1], al[1]);
-                tf32_split(c1ok && xa < nx ? vin[(long)c1 * N + base + xa] : 0.0f, ah[2], al[2]);
-                tf32_split(c1ok && xb < nx ? vin[(long)c1 * N + base + xb] : 0.0f, ah[3], al[3]);
-                const uint32_t *wh = sWh + c0 * PW + g, *wl = sWl + c0 * PW + g;
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt)
-                    mma3(d[nt], ah, al, wh[8 * nt], wh[4 * PW + 8 * nt], wl[8 * nt],
-                         wl[4 * PW + 8 * nt]);
+            for (int ks = 0; ks < KC / 8; ++ks) {
+                const uint32_t ko = ks * 2 * 128;      // two core matrices per K step of 8
+                mma3_tc(tbase, tc::smem_desc(sAh + ko, 128, SBO_A),
+                        tc::smem_desc(sAl + ko, 128, SBO_A), tc::smem_desc(sBh + ko, 128, SBO_A),
+                        tc::smem_desc(sBl + ko, 128, SBO_A), idesc, ks > 0);
             }
             if (spec) {
-                for (int ks = 0; ks < KSS; ++ks) {
-                    const int j0 = 8 * ks + t;
-                    const uint32_t ah[4] = {sTh[j0 * P + xa], sTh[j0 * P + xb],
-                                            sTh[(j0 + 4) * P + xa], sTh[(j0 + 4) * P + xb]};
-                    const uint32_t al[4] = {sTl[j0 * P + xa], sTl[j0 * P + xb],
-                                            sTl[(j0 + 4) * P + xa], sTl[(j0 + 4) * P + xb]};
-                    const uint32_t *yh = sSh + j0 * PW + g, *yl = sSl + j0 * PW + g;
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-                        mma3(d[nt], ah, al, yh[8 * nt], yh[4 * PW + 8 * nt], yl[8 * nt],
-                             yl[4 * PW + 8 * nt]);
+                const uint32_t to = (uint32_t)(t * 128 * JP * 4);
+                for (int ks = 0; ks < JP / 8; ++ks) {
+                    const uint32_t ko = ks * 2 * 128;
+                    mma3_tc(tbase, tc::smem_desc(sTh + to + ko, 128, sbo_t),
+                            tc::smem_desc(sTl + to + ko, 128, sbo_t),
+                            tc::smem_desc(sSh + ko, 128, sbo_t), tc::smem_desc(sSl + ko, 128, sbo_t),
+                            idesc, 1);
                 }
             }
+            tc::commit(bar);
+        }
+        // the next tile's loads overlap the products and this tile's epilogue
+        int nrow = row, nt = t + 1;
+        if (nt == nxt) {
+            nt = 0;
+            nrow = row + gridDim.x;
+        }
+        if (nrow < rows) {
+            load_v(nrow, nt);
+            if (spec && nt == 0) load_pairs(nrow);
+        }
+        const bool ready =
+            __all_sync(0xffffffffu, bvf::tma::mbar_wait(bar, it & 1, bvf::tma::kWaitLimit));
+        tc::fence_after();
+        if (ready) {
+            const int x = 128 * t + pt;
+            const long p = (long)row * nx + x;
 #pragma unroll
-            for (int nt = 0; nt < NT; ++nt) {
+            for (int c0 = 0; c0 < W / 2; c0 += 8) {
+                float r[8];
+                tc::ld8(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * (W / 2) + c0),
+                        r);
+                tc::wait_ld();
+                if (x < nx) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int o = 8 * nt + 2 * t + (i & 1), x = i < 2 ? xa : xb;
-                    const float val = act ? gelu(d[nt][i]) : d[nt][i];
-                    if (x < nx) vout[(long)o * N + base + x] = val;
-                    if (fwd) sV[o * P + x] = x < nx ? val : 0.0f;
+                    for (int i = 0; i < 8; ++i) {
+                        const int o = half * (W / 2) + c0 + i;
+                        const float val = r[i] + sb[o];
+                        vout[(long)o * N + p] = act ? gelu(val) : val;
+                    }
                 }
             }
         }
-        if (!fwd) continue;
-        __syncthreads();
-        // phase 3: forward x transform of the new row
-        const int units = (cout / 16) * KSS;
-        for (int u = warp; u < units; u += nth / 32) {
-            const int o0 = 16 * (u / KSS), n0 = 8 * (u % KSS);
-            float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            const float *va = sV + (o0 + g) * P + t, *vb = sV + (o0 + g + 8) * P + t;
-            const uint32_t *th = sTh + (n0 + g) * P + t, *tl = sTl + (n0 + g) * P + t;
-            for (int x0 = 0; x0 < nx16; x0 += 8) {
-                uint32_t ah[4], al[4];
-                tf32_split(va[x0], ah[0], al[0]);
-                tf32_split(vb[x0], ah[1], al[1]);
-                tf32_split(va[x0 + 4], ah[2], al[2]);
-                tf32_split(vb[x0 + 4], ah[3], al[3]);
-                mma3(d, ah, al, th[x0], th[x0 + 4], tl[x0], tl[x0 + 4]);
-            }
-            const int kx = n0 / 2 + t;
-            if (kx < m) {
-                Anext[((long)(o0 + g) * rows + row) * m + kx] = make_float2(d[0], -d[1]);
-                Anext[((long)(o0 + g + 8) * rows + row) * m + kx] = make_float2(d[2], -d[3]);
-            }
-        }
+        tc::fence_before();
+        // tensor memory and the staged operands are free again; every thread
+        // learns whether some warp's wait for the products ran out
+        gave_up = __syncthreads_or(!ready) != 0;
+        // after a time-out no further product is issued: the block waits,
+        // bounded, for the products in flight, frees its tensor memory and
+        // ends (the flag makes bvf_fno_synchronize report it)
+        if (gave_up) break;
+        row = nrow;
+        t = nt;
+        ++it;
     }
+    if (gave_up && tid == 0) {
+        bvf::tma::mbar_wait(bar, it & 1, bvf::tma::kWaitLimit);
+        atomicOr(flag, 2);
+    }
+    tc::fence_after();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tbase, NCOLS);
+}
+
+// ------------------------------------------------ tcgen05 forward x transform
+// A[i][kx] = sum_x v[i][x] e^{-2 pi i kx x / nx} for every row i = (c, z, y)
+// of v (row-major, nx per row) as one tall product on 128-row tiles:
+//   D[i][j] = sum_x v[i][x] T[j][x],  A[i][kx] = (D[i][2 kx], -D[i][2 kx + 1])
+// with T[j][x] = cos, sin (2 pi kx x / nx) for j = 2 kx, 2 kx + 1 (zero rows
+// up to NB, a multiple of 16).  x runs in chunks of 16 through two staged
+// buffers (A, split, K-major); T is resident, split, for the whole row.  The
+// next chunk's loads are issued before the current chunk is staged.
+constexpr int kDxC = 16;     // x per chunk
+
+struct DftxTcLayout {
+    int nxp, sA, sB, bar, tmem, bytes;
+    __host__ __device__ DftxTcLayout(int nb, int nx)
+    {
+        nxp = ((nx + kDxC - 1) / kDxC) * kDxC;
+        const int a = 128 * kDxC * 4;                // one split half of one stage
+        sA = 0;                                      // [stage][hi, lo]
+        sB = sA + 4 * a;                             // [hi, lo] of NB x nxp
+        bar = sB + 2 * nb * nxp * 4;
+        tmem = bar + 16;
+        bytes = tmem + 16;
+    }
+};
+
+template <int NB, bool VEC>     // NB: T rows (16 or 32); VEC: rows start on 16 bytes (nx % 4 == 0)
+__global__ void __launch_bounds__(256, 2)
+k_dftx_tc(const float *__restrict__ v, long R, int nx, int m, const float2 *__restrict__ tx,
+          float2 *__restrict__ A, int *flag)
+{
+    extern __shared__ __align__(128) unsigned char s_d[];
+    const DftxTcLayout L(NB, nx);
+    const int nxp = L.nxp, nch = nxp / kDxC;
+    unsigned char *sA = s_d + L.sA, *sBh = s_d + L.sB, *sBl = sBh + NB * nxp * 4;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_d + L.bar);     // one per stage
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(s_d + L.tmem);
+    constexpr int SA = 128 * kDxC * 4;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < NB * nxp; e += 256) {
+        const int j = e / nxp, x = e - j * nxp;
+        float val = 0.0f;
+        if (j < 2 * m && x < nx) {
+            const float2 c = tx[(long)(j >> 1) * nx + x];
+            val = (j & 1) ? c.y : c.x;
+        }
+        uint32_t h, l;
+        tf32_split(val, h, l);
+        const uint32_t off = tc::kmaj_off(j, x, nxp);
+        *reinterpret_cast<uint32_t *>(sBh + off) = h;
+        *reinterpret_cast<uint32_t *>(sBl + off) = l;
+    }
+    if (tid == 0) {
+        bvf::tma::mbar_init(&bar[0], 1);
+        bvf::tma::mbar_init(&bar[1], 1);
+        bvf::tma::mbar_init_fence();
+    }
+    if (warp == 0) {
+        tc::alloc(tslot, 32);
+        tc::relinquish();
+    }
+    bvf::tma::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+    const uint32_t idesc = tc::idesc_tf32(128, NB);
+    constexpr uint32_t SBO_A = (kDxC / 4) * 128;
+    const uint32_t sbo_b = (uint32_t)(nxp / 4) * 128;
+    // warp w stages rows 16 w .. 16 w + 15 of a chunk: 8 rows by 4 groups of
+    // 4 x per access (512 contiguous bytes in shared memory)
+    const int r_lo = 16 * warp + (lane & 7), kg = lane >> 3;
+    const long tiles = (R + 127) / 128;
+    auto load = [&](long tile, int ch, float4 (&dst)[2]) {
+        const int x = ch * kDxC + 4 * kg;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const long i = tile * 128 + r_lo + 8 * q;
+            const float *src = v + i * nx + x;
+            if (VEC) {
+                dst[q] = (i < R && x < nx) ? *reinterpret_cast<const float4 *>(src)
+                                           : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            } else {
+                const bool ok = i < R;
+                dst[q] = make_float4(ok && x < nx ? src[0] : 0.0f, ok && x + 1 < nx ? src[1] : 0.0f,
+                                     ok && x + 2 < nx ? src[2] : 0.0f,
+                                     ok && x + 3 < nx ? src[3] : 0.0f);
+            }
+        }
+    };
+    float4 cur[2], nxt[2];
+    long tile = blockIdx.x;
+    if (tile < tiles) load(tile, 0, cur);
+    int gc = 0;                 // chunks issued by this block
+    bool gave_up = false;
+    for (; tile < tiles && !gave_up; tile += gridDim.x) {
+        for (int ch = 0; ch < nch; ++ch, ++gc) {
+            long ntile = tile;
+            int nc = ch + 1;
+            if (nc == nch) {
+                nc = 0;
+                ntile = tile + gridDim.x;
+            }
+            if (ntile < tiles) load(ntile, nc, nxt);
+            const int st = gc & 1;
+            // the products that read this stage two chunks ago are done
+            bool ok = true;
+            if (gc >= 2)
+                ok = __all_sync(0xffffffffu, bvf::tma::mbar_wait(&bar[st], ((gc - 2) >> 1) & 1,
+                                                                 bvf::tma::kWaitLimit));
+            tc::fence_after();
+            unsigned char *ah = sA + st * 2 * SA, *al = ah + SA;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint32_t h[4], l[4];
+                tf32_split(cur[q].x, h[0], l[0]);
+                tf32_split(cur[q].y, h[1], l[1]);
+                tf32_split(cur[q].z, h[2], l[2]);
+                tf32_split(cur[q].w, h[3], l[3]);
+                const uint32_t off = tc::kmaj_off(r_lo + 8 * q, 4 * kg, kDxC);
+                *reinterpret_cast<uint4 *>(ah + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4 *>(al + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+            bvf::tma::fence_async_smem();
+            tc::fence_before();
+            if (__syncthreads_or(!ok)) {
+                gave_up = true;
+                break;
+            }
+            if (tid == 0) {
+                tc::fence_after();
+#pragma unroll
+                for (int ks = 0; ks < kDxC / 8; ++ks) {
+                    const uint32_t ko = ks * 2 * 128, kb = (ch * (kDxC / 8) + ks) * 2 * 128;
+                    mma3_tc(tbase, tc::smem_desc(ah + ko, 128, SBO_A),
+                            tc::smem_desc(al + ko, 128, SBO_A), tc::smem_desc(sBh + kb, 128, sbo_b),
+                            tc::smem_desc(sBl + kb, 128, sbo_b), idesc, ch > 0 || ks > 0);
+                }
+                tc::commit(&bar[st]);
+            }
+            cur[0] = nxt[0];
+            cur[1] = nxt[1];
+        }
+        if (gave_up) break;
+        // epilogue: the tile's last chunk is done, so is every product of it
+        const int lst = (gc - 1) & 1;
+        const bool ready = __all_sync(
+            0xffffffffu, bvf::tma::mbar_wait(&bar[lst], ((gc - 1) >> 1) & 1, bvf::tma::kWaitLimit));
+        tc::fence_after();
+        if (ready) {
+            const int half = tid >> 7;
+            const long i = tile * 128 + (tid & 127);
+#pragma unroll
+            for (int c0 = 0; c0 < NB / 2; c0 += 8) {
+                float r[8];
+                tc::ld8(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(half * (NB / 2) + c0),
+                        r);
+                tc::wait_ld();
+                if (i < R) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int kx = (half * (NB / 2) + c0) / 2 + q;
+                        if (kx < m) A[i * m + kx] = make_float2(r[2 * q], -r[2 * q + 1]);
+                    }
+                }
+            }
+        }
+        tc::fence_before();
+        gave_up = __syncthreads_or(!ready) != 0;
+    }
+    // after a time-out no further product is issued: wait, bounded, for the
+    // last one issued, free tensor memory, flag it
+    if (gave_up && tid == 0) {
+        if (gc > 0)
+            bvf::tma::mbar_wait(&bar[(gc - 1) & 1], ((gc - 1) >> 1) & 1, bvf::tma::kWaitLimit);
+        atomicOr(flag, 2);
+    }
+    tc::fence_after();
+    __syncthreads();
+    if (warp == 0) tc::dealloc(tbase, 32);
 }
 
 // tcgen05 helpers (descriptors, TMEM, products): bvf_tc.cuh
@@ -938,6 +1166,46 @@ cudaError_t smem_at_least(size_t bytes)
         }
     return e;
 }
+
+template <int W, int KC>
+cudaError_t launch_row_tc_k(int grid, int bytes, cudaStream_t s, const float *vin, int cin,
+                            const float2 *Ap, const float *Wm, const float *bm, int nx, int rows,
+                            int m, float invN, int act, const float2 *tx, float *vout, int N,
+                            int *flag)
+{
+    cudaError_t e = smem_at_least<k_row_tc<W, KC>>((size_t)bytes);
+    if (e != cudaSuccess) return e;
+    k_row_tc<W, KC><<<grid, 256, bytes, s>>>(vin, cin, Ap, Wm, bm, nx, rows, m, invN, act, tx,
+                                             vout, N, flag);
+    return cudaGetLastError();
+}
+
+// input channels padded to 8 or 16 (the lift) or to W (a Fourier layer)
+template <int W>
+cudaError_t launch_row_tc(int kc, int grid, int bytes, cudaStream_t s, const float *vin, int cin,
+                          const float2 *Ap, const float *Wm, const float *bm, int nx, int rows,
+                          int m, float invN, int act, const float2 *tx, float *vout, int N,
+                          int *flag)
+{
+    if (kc == 8)
+        return launch_row_tc_k<W, 8>(grid, bytes, s, vin, cin, Ap, Wm, bm, nx, rows, m, invN, act,
+                                     tx, vout, N, flag);
+    if (kc == 16 || W == 16)
+        return launch_row_tc_k<W, 16>(grid, bytes, s, vin, cin, Ap, Wm, bm, nx, rows, m, invN,
+                                      act, tx, vout, N, flag);
+    return launch_row_tc_k<W, W>(grid, bytes, s, vin, cin, Ap, Wm, bm, nx, rows, m, invN, act,
+                                 tx, vout, N, flag);
+}
+
+template <int NB, bool VEC>
+cudaError_t launch_dftx_tc(int grid, int bytes, cudaStream_t s, const float *v, long R, int nx,
+                           int m, const float2 *tx, float2 *A, int *flag)
+{
+    cudaError_t e = smem_at_least<k_dftx_tc<NB, VEC>>((size_t)bytes);
+    if (e != cudaSuccess) return e;
+    k_dftx_tc<NB, VEC><<<grid, 256, bytes, s>>>(v, R, nx, m, tx, A, flag);
+    return cudaGetLastError();
+}
 }  // namespace
 
 extern "C" {
@@ -1077,51 +1345,49 @@ int bvf_fno_forward(bvf_fno *f, int nx, int ny, int nz, const float *d_in, float
     const int pblocks = (N + TB - 1) / TB;
     const int rows_p = nz * ny;
     const float invN = (float)(1.0 / (double)N64);
-    // the row pass keeps the twiddle table and one (z, y) row of every output
-    // channel in shared memory; rows too long for that take the unfused kernels
-    const int ksw_lift = (d.c_in + 7) / 8;
-    const size_t row_bytes =
-        (size_t)std::max(RowMmaLayout(W / 8, W, m, nx).words,
-                         RowMmaLayout(ksw_lift, W, m, nx).words) * sizeof(uint32_t);
-    const bool fused = row_bytes <= 110 * 1024;
+    // the row pass: k_row_tc (layer output: inverse x transform, W v + b,
+    // GELU) and, when a further layer follows, k_dftx_tc (its forward x
+    // transform); grids whose rows do not fit shared memory take the unfused
+    // kernels
+    const int kc_lift = ((d.c_in + 7) / 8) * 8;
+    const int nb = 2 * m <= 16 ? 16 : 32;
+    const DftxTcLayout dl(nb, nx);
+    constexpr int kSmemCap = 200 * 1024;
+    const bool fused = RowTcLayout(W, W, m, nx, true).bytes <= kSmemCap &&
+                       RowTcLayout(W, kc_lift, m, nx, false).bytes <= kSmemCap &&
+                       dl.bytes <= kSmemCap;
     int dev = 0, n_sm = 0;
     FCK(cudaGetDevice(&dev), "bvf_fno_forward: device");
     FCK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "sm count");
-    const int row_grid = std::min(rows_p, 2 * n_sm);
+    // resident blocks per SM: two where shared memory allows (launch bounds)
+    auto blocks_per_sm = [](int bytes) {
+        return std::max(1, std::min(2, (227 * 1024) / (bytes + 1024)));
+    };
     auto row_pass = [&](const float *vin, int cin, const float2 *Ap, const float *Wm,
                         const float *bm, int act, float *vout, float2 *An) -> cudaError_t {
-        const int ksw = (cin + 7) / 8;
-        const size_t bytes = (size_t)RowMmaLayout(ksw, W, m, nx).words * sizeof(uint32_t);
-        cudaError_t e = cudaSuccess;
-#define BVF_ROW(NT, KSW)                                                                     \
-    e = smem_at_least<k_row_mma<NT, KSW>>(bytes);                                              \
-    if (e == cudaSuccess)                                                                     \
-        k_row_mma<NT, KSW><<<row_grid, 256, bytes, s>>>(vin, cin, Ap, Wm, bm, nx, rows_p, m,   \
-                                                        invN, act, tx, vout, An, N);
-        if (ksw == W / 8) {
-            switch (W / 8) {
-            case 2: BVF_ROW(2, 2) break;
-            case 4: BVF_ROW(4, 4) break;
-            case 6: BVF_ROW(6, 6) break;
-            default: BVF_ROW(8, 8) break;
-            }
-        } else if (ksw == 1) {
-            switch (W / 8) {
-            case 2: BVF_ROW(2, 1) break;
-            case 4: BVF_ROW(4, 1) break;
-            case 6: BVF_ROW(6, 1) break;
-            default: BVF_ROW(8, 1) break;
-            }
-        } else {
-            switch (W / 8) {
-            case 2: BVF_ROW(2, 2) break;
-            case 4: BVF_ROW(4, 2) break;
-            case 6: BVF_ROW(6, 2) break;
-            default: BVF_ROW(8, 2) break;
-            }
+        const int kc = Ap ? W : kc_lift;
+        const RowTcLayout rl(W, kc, m, nx, Ap != nullptr);
+        const int grid = std::min(rows_p, n_sm * blocks_per_sm(rl.bytes));
+        cudaError_t e;
+#define BVF_ROW(WW)                                                                            \
+    e = launch_row_tc<WW>(kc, grid, rl.bytes, s, vin, cin, Ap, Wm, bm, nx, rows_p, m, invN, act, \
+                          tx, vout, N, f->flag)
+        switch (W) {
+        case 16: BVF_ROW(16); break;
+        case 32: BVF_ROW(32); break;
+        case 48: BVF_ROW(48); break;
+        default: BVF_ROW(64); break;
         }
 #undef BVF_ROW
-        return e != cudaSuccess ? e : cudaGetLastError();
+        if (e != cudaSuccess || !An) return e;
+        const long R = (long)W * rows_p, tiles = (R + 127) / 128;
+        const int g2 = (int)std::min<long>(tiles, (long)n_sm * blocks_per_sm(dl.bytes));
+        const bool vec = nx % 4 == 0;
+        if (nb == 16)
+            return vec ? launch_dftx_tc<16, true>(g2, dl.bytes, s, vout, R, nx, m, tx, An, f->flag)
+                       : launch_dftx_tc<16, false>(g2, dl.bytes, s, vout, R, nx, m, tx, An, f->flag);
+        return vec ? launch_dftx_tc<32, true>(g2, dl.bytes, s, vout, R, nx, m, tx, An, f->flag)
+                   : launch_dftx_tc<32, false>(g2, dl.bytes, s, vout, R, nx, m, tx, An, f->flag);
     };
 
     if (fused) {

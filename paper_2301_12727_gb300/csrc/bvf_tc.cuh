@@ -101,6 +101,18 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&r)[32])
     for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
 
+// 8 consecutive columns of this warp's 32 lanes (the narrow form of ld32)
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&r)[8])
+{
+    uint32_t u[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]),
+                   "=r"(u[6]), "=r"(u[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = __uint_as_float(u[i]);
+}
+
 // byte offset of element (row, k) in a K-major TF32 operand with K columns
 __host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k, int K)
 {
