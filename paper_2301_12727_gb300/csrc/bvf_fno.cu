@@ -378,21 +378,17 @@ __global__ void k_layer_out(const float *__restrict__ v, const float2 *__restric
 }
 
 // ------------------------------------------- tensor-core tiles (TF32 x 3)
-// Each FP32 operand of a tensor-core product is split into a TF32 head and
-// the TF32 rounding of its remainder, and a b is taken as
-// a_lo b_hi + a_hi b_lo + a_hi b_hi (the three-product scheme of Ootomo and
-// Yokota, 2022), which keeps FP32-level accuracy.
-__device__ __forceinline__ uint32_t tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
+// Each FP32 operand of a tensor-core product is split into a TF32 head and a
+// remainder, and a b is taken as a_lo b_hi + a_hi b_lo + a_hi b_hi (the
+// three-product scheme of Ootomo and Yokota, 2022), which keeps FP32-level
+// accuracy.  The head is x with its low 13 mantissa bits cleared (a TF32
+// value exactly); the remainder x - head is exact in FP32, below 2^-10 |x|,
+// and the tensor core reads it at TF32 precision (relative error 2^-10 at
+// most), so each product is off by about 3 * 2^-20 of |a b|.
 __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
 {
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - __uint_as_float(hi));
+    hi = __float_as_uint(x) & 0xFFFFE000u;
+    lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 // the three products of one K step: D (+)= A_lo B_hi + A_hi B_lo + A_hi B_hi
