@@ -393,8 +393,9 @@ def surrogate_leg(case, steps, warmup, ms_plan, ms_fdtd, cpu_baseline=True):
                      "speedup_vs_plan": ms_plan / ms_bf16 if ms_plan else None,
                      "speedup_vs_plan_fdtd": ms_fdtd / ms_bf16 if ms_fdtd else None},
             "stages_ms": stages,
-            "tensor_core": "row pass mma.sync m16n8k8 TF32; projection tcgen05.mma kind::tf32 "
-                           "into TMEM; both with the three-product FP32 split",
+            "tensor_core": "layer output (k_row_tc), forward x transform (k_dftx_tc) and "
+                           "projection (k_project_tc): tcgen05.mma kind::tf32 into TMEM, "
+                           "all with the three-product FP32 split",
             "roofline": {"bound": "hbm", "achieved": bytes_inf / (ms / 1e3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": bytes_inf / (ms / 1e3) / 1e9 / peak,
                          "peak_kind": peak_kind, "algorithmic_bytes": bytes_inf},
