@@ -91,6 +91,28 @@ __device__ __forceinline__ float gelu(float s)
     return s * phi;
 }
 
+// The same GELU on two values at once: the polynomial, the products and the
+// final scaling on the packed FP32x2 multiply / fused multiply-add of sm_100
+// and later (half the instructions); the reciprocal and the exponential stay
+// per value.
+__device__ __forceinline__ float2 gelu2(float2 s)
+{
+    const float2 k = make_float2(0.70710678118654752f, 0.70710678118654752f);
+    const float2 x = __fmul2_rn(make_float2(fabsf(s.x), fabsf(s.y)), k);
+    const float2 den = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), x, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    float2 q = __ffma2_rn(make_float2(1.061405429f, 1.061405429f), t,
+                          make_float2(-1.453152027f, -1.453152027f));
+    q = __ffma2_rn(q, t, make_float2(1.421413741f, 1.421413741f));
+    q = __ffma2_rn(q, t, make_float2(-0.284496736f, -0.284496736f));
+    q = __ffma2_rn(q, t, make_float2(0.254829592f, 0.254829592f));
+    const float2 e = make_float2(__expf(-x.x * x.x), __expf(-x.y * x.y));
+    const float2 h = __fmul2_rn(__fmul2_rn(__fmul2_rn(q, t), e), make_float2(0.5f, 0.5f));
+    const float2 phi =
+        make_float2(s.x >= 0.0f ? 1.0f - h.x : h.x, s.y >= 0.0f ? 1.0f - h.y : h.y);
+    return __fmul2_rn(s, phi);
+}
+
 // ------------------------------------------------------------------ lift
 __global__ void k_lift(const float *__restrict__ a, int c_in, int width,
                        const float *__restrict__ Wp, const float *__restrict__ bp,
@@ -615,10 +637,12 @@ k_row_tc(const float *__restrict__ vin, int cin, const float2 *__restrict__ Ap,
                 tc::wait_ld();
                 if (x < nx) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                    for (int i = 0; i < 8; i += 2) {
                         const int o = half * (W / 2) + c0 + i;
-                        const float val = r[i] + sb[o];
-                        vout[(long)o * N + p] = act ? gelu(val) : val;
+                        float2 val = make_float2(r[i] + sb[o], r[i + 1] + sb[o + 1]);
+                        if (act) val = gelu2(val);
+                        vout[(long)o * N + p] = val.x;
+                        vout[(long)(o + 1) * N + p] = val.y;
                     }
                 }
             }
@@ -957,11 +981,15 @@ k_project_tc(const float *__restrict__ v, const float *__restrict__ Q1, const fl
                 tc::wait_ld();
                 const int nv = min(32, HP - c0);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
+                for (int i = 0; i < 32; i += 2) {      // nv is a multiple of 16
                     if (i < nv) {
-                        const float h = gelu(r[i] + sq1[c0 + i]);
+                        const float2 h =
+                            gelu2(make_float2(r[i] + sq1[c0 + i], r[i + 1] + sq1[c0 + i + 1]));
 #pragma unroll
-                        for (int k = 0; k < COUT; ++k) o[k] = fmaf(sq2[k * HP + c0 + i], h, o[k]);
+                        for (int k = 0; k < COUT; ++k) {
+                            o[k] = fmaf(sq2[k * HP + c0 + i], h.x, o[k]);
+                            o[k] = fmaf(sq2[k * HP + c0 + i + 1], h.y, o[k]);
+                        }
                     }
                 }
             }
